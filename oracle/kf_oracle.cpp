@@ -1,0 +1,969 @@
+// kf_oracle.cpp -- TEST INFRASTRUCTURE, NOT PRODUCT CODE.
+//
+// A plain, slow, FP64 CPU Kalman-filter track fitter. Only tests/, the smoke()
+// entry of __graft_entry__.py and the CPU-baseline leg of bench.py may load it.
+// It shares no code, header, table or constant generator with the CUDA fitter.
+//
+// What it computes (paper Sec. 2, "Implementation", second paragraph): for each
+// track candidate, the Kalman-filter fit with 4th-order Runge-Kutta-Nystrom (RKN)
+// propagation and Jacobian transport between surfaces (refs Nystrom 1925,
+// Bugge-Myrheim 1981, Lund et al. 2009a/b, Yeo et al. 2024), a gain-matrix update
+// with a chi2 from the covariance-weighted spatial residual (ref Fruhwirth 1987),
+// and the Rauch-Tung-Striebel (RTS) smoother (ref Rauch-Tung-Striebel 1965) so that
+// the first-measurement parameters use every measurement. Material effects assume a
+// muon (paper Sec. 3, first paragraph). The paper prints no formula for any of these;
+// each formula below is the textbook form of the cited method, and every reading that
+// the paper leaves open is marked "Reading:".
+//
+// Style: every matrix is a full dense array and every product is a plain triple
+// loop; no structure (sparsity, symmetry, packing) is exploited, so that a reader can
+// check each line against the textbook formula.
+//
+// Parity unpinned (conventions fixed by reading, the same on both sides):
+//   * the density-effect term of the Bethe formula (high-energy asymptote);
+//   * the field gradient dB/dr, neglected in the Jacobian (exact in a uniform field).
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+namespace {
+
+const double kKappa = 2.99792458e-4;  // c in GeV / (T mm): curvature = kKappa * B / p
+const double kPi = 3.14159265358979323846;
+const double kMe = 0.51099895e-3;     // electron mass, GeV
+const double kBetheK = 0.307075;      // 4 pi N_A r_e^2 m_e c^2, MeV cm^2 / mol
+
+// Per-track status bits (values fixed by the library interface).
+const uint32_t kMaxSteps = 1u << 0;
+const uint32_t kSurfaceMissed = 1u << 1;
+const uint32_t kParticleStopped = 1u << 2;
+const uint32_t kUpdateNotSpd = 1u << 3;
+const uint32_t kSmootherNotSpd = 1u << 4;
+const uint32_t kTooFewHits = 1u << 5;
+const uint32_t kOutOfField = 1u << 6;
+const uint32_t kBadInput = 1u << 7;
+const uint32_t kStepUnderflow = 1u << 8;
+const uint32_t kNonFinite = 1u << 9;
+const uint32_t kFatal = ~(kTooFewHits | kOutOfField);
+
+struct Surface {
+  double u[3], v[3], n[3];  // local axes and normal (global frame); n = u x v
+  double c[3];              // centre
+  double t;                 // thickness, mm (0: no material)
+  double X0;                // radiation length, mm
+};
+
+struct Field {
+  int kind;  // 0 uniform, 1 r-z grid
+  double B[3];
+  int nr, nz;
+  double r0, dr, z0, dz;
+  const float* Br;  // [nz][nr]
+  const float* Bz;  // [nz][nr]
+};
+
+struct Opts {
+  double tol;       // RKN local error tolerance, mm
+  double h_max;     // largest step, mm
+  double h_min;     // smallest step-size control value, mm
+  double surf_tol;  // distance to the target plane at which propagation stops, mm
+  double mass;      // particle hypothesis, GeV
+  uint32_t max_steps;
+  double ZA, I_eV, rho, hwp_eV;  // material: Z/A, mean excitation, density g/cm3, plasma energy
+};
+
+// ---------------------------------------------------------------- dense algebra
+void matmul(const double* A, const double* B, double* C, int n, int k, int m) {
+  // C (n x m) = A (n x k) * B (k x m)
+  std::vector<double> tmp(n * m, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < m; ++j) {
+      double s = 0.0;
+      for (int l = 0; l < k; ++l) s += A[i * k + l] * B[l * m + j];
+      tmp[i * m + j] = s;
+    }
+  std::memcpy(C, tmp.data(), sizeof(double) * n * m);
+}
+
+void transpose(const double* A, double* At, int n, int m) {
+  // At (m x n) = A (n x m)^T
+  std::vector<double> tmp(n * m);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < m; ++j) tmp[j * n + i] = A[i * m + j];
+  std::memcpy(At, tmp.data(), sizeof(double) * n * m);
+}
+
+// Cholesky C = L L^T of an n x n matrix; false if not positive definite.
+bool cholesky(const double* C, double* L, int n) {
+  for (int i = 0; i < n * n; ++i) L[i] = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double d = C[j * n + j];
+    for (int k = 0; k < j; ++k) d -= L[j * n + k] * L[j * n + k];
+    if (!(d > 0.0)) return false;
+    L[j * n + j] = std::sqrt(d);
+    for (int i = j + 1; i < n; ++i) {
+      double s = C[i * n + j];
+      for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];
+      L[i * n + j] = s / L[j * n + j];
+    }
+  }
+  return true;
+}
+
+// Inverse of an SPD matrix by solving C X = I with its Cholesky factor.
+bool spd_inverse(const double* C, double* Ci, int n) {
+  std::vector<double> L(n * n);
+  if (!cholesky(C, L.data(), n)) return false;
+  for (int col = 0; col < n; ++col) {
+    std::vector<double> y(n), x(n);
+    for (int i = 0; i < n; ++i) {  // L y = e_col
+      double s = (i == col) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
+      y[i] = s / L[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {  // L^T x = y
+      double s = y[i];
+      for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * x[k];
+      x[i] = s / L[i * n + i];
+    }
+    for (int i = 0; i < n; ++i) Ci[i * n + col] = x[i];
+  }
+  return true;
+}
+
+void symmetrize(double* C, int n) {
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) {
+      double a = 0.5 * (C[i * n + j] + C[j * n + i]);
+      C[i * n + j] = a;
+      C[j * n + i] = a;
+    }
+}
+
+double wrap_phi(double phi) {
+  // Reading: phi is kept in (-pi, pi].
+  while (phi > kPi) phi -= 2.0 * kPi;
+  while (phi <= -kPi) phi += 2.0 * kPi;
+  return phi;
+}
+
+void cross(const double a[3], const double b[3], double out[3]) {
+  out[0] = a[1] * b[2] - a[2] * b[1];
+  out[1] = a[2] * b[0] - a[0] * b[2];
+  out[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// Matrix M(B) with M(B) T = T x B.
+void cross_matrix(const double B[3], double M[9]) {
+  M[0] = 0.0;   M[1] = B[2];  M[2] = -B[1];
+  M[3] = -B[2]; M[4] = 0.0;   M[5] = B[0];
+  M[6] = B[1];  M[7] = -B[0]; M[8] = 0.0;
+}
+
+// ---------------------------------------------------------------- field
+// Uniform field, or bilinear interpolation in (r, z) of a tabulated solenoid map with
+// B_x = B_r x / r, B_y = B_r y / r. Outside the grid B = 0 and the flag is raised.
+void field_at(const Field& f, const double x[3], double B[3], bool* out_of_map) {
+  if (f.kind == 0) {
+    B[0] = f.B[0]; B[1] = f.B[1]; B[2] = f.B[2];
+    return;
+  }
+  double r = std::sqrt(x[0] * x[0] + x[1] * x[1]);
+  double fr = (r - f.r0) / f.dr;
+  double fz = (x[2] - f.z0) / f.dz;
+  if (!(fr >= 0.0 && fr <= double(f.nr - 1) && fz >= 0.0 && fz <= double(f.nz - 1))) {
+    B[0] = B[1] = B[2] = 0.0;
+    *out_of_map = true;
+    return;
+  }
+  int ir = int(std::floor(fr));
+  int iz = int(std::floor(fz));
+  if (ir > f.nr - 2) ir = f.nr - 2;
+  if (iz > f.nz - 2) iz = f.nz - 2;
+  double a = fr - ir, b = fz - iz;
+  double w00 = (1.0 - a) * (1.0 - b), w01 = a * (1.0 - b), w10 = (1.0 - a) * b, w11 = a * b;
+  int i00 = iz * f.nr + ir, i01 = i00 + 1, i10 = i00 + f.nr, i11 = i10 + 1;
+  double br = w00 * double(f.Br[i00]) + w01 * double(f.Br[i01]) + w10 * double(f.Br[i10]) + w11 * double(f.Br[i11]);
+  double bz = w00 * double(f.Bz[i00]) + w01 * double(f.Bz[i01]) + w10 * double(f.Bz[i10]) + w11 * double(f.Bz[i11]);
+  if (r > 0.0) {
+    B[0] = br * x[0] / r;
+    B[1] = br * x[1] / r;
+  } else {
+    B[0] = 0.0;
+    B[1] = 0.0;
+  }
+  B[2] = bz;
+}
+
+// ---------------------------------------------------------------- RKN4 step
+// One 4th-order Runge-Kutta-Nystrom step of length h for d2r/ds2 = kappa*lam*T x B(r)
+// (Bugge-Myrheim / Lund 2009a form), with the 7x7 derivative D of the discrete map
+// x = (r, T, lam) -> x' taken through the stages (Lund 2009b). dB/dr is neglected.
+// The local error estimate is eps = h^2 * || k1 - k2 - k3 + k4 ||_1 (Lund 2009a).
+struct Step {
+  double r[3], T[3];
+  double D[49];
+  double eps;
+  double dTds[3];  // k1 of the step (dT/ds at the start point)
+};
+
+void rkn_step(const Field& f, const double r[3], const double T[3], double lam, double h, Step& out,
+              bool* oof) {
+  double B1[3], B2[3], B4[3];
+  field_at(f, r, B1, oof);
+  double k1[3], k2[3], k3[3], k4[3], T2[3], T3[3], T4[3], r2[3], r4[3], c[3];
+  cross(T, B1, c);
+  for (int i = 0; i < 3; ++i) k1[i] = kKappa * lam * c[i];
+  for (int i = 0; i < 3; ++i) {
+    r2[i] = r[i] + 0.5 * h * T[i] + 0.125 * h * h * k1[i];
+    T2[i] = T[i] + 0.5 * h * k1[i];
+  }
+  field_at(f, r2, B2, oof);
+  cross(T2, B2, c);
+  for (int i = 0; i < 3; ++i) k2[i] = kKappa * lam * c[i];
+  for (int i = 0; i < 3; ++i) T3[i] = T[i] + 0.5 * h * k2[i];
+  cross(T3, B2, c);
+  for (int i = 0; i < 3; ++i) k3[i] = kKappa * lam * c[i];
+  for (int i = 0; i < 3; ++i) {
+    r4[i] = r[i] + h * T[i] + 0.5 * h * h * k3[i];
+    T4[i] = T[i] + h * k3[i];
+  }
+  field_at(f, r4, B4, oof);
+  cross(T4, B4, c);
+  for (int i = 0; i < 3; ++i) k4[i] = kKappa * lam * c[i];
+
+  for (int i = 0; i < 3; ++i) {
+    out.r[i] = r[i] + h * T[i] + h * h / 6.0 * (k1[i] + k2[i] + k3[i]);
+    out.T[i] = T[i] + h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+    out.dTds[i] = k1[i];
+  }
+  double e = 0.0;
+  for (int i = 0; i < 3; ++i) e += std::fabs(k1[i] - k2[i] - k3[i] + k4[i]);
+  out.eps = h * h * e;
+
+  // Stage derivatives w.r.t. T (3x3) and lam (3x1), by the chain rule.
+  double M1[9], M2[9], M4[9], I3[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  cross_matrix(B1, M1);
+  cross_matrix(B2, M2);
+  cross_matrix(B4, M4);
+  double dk1T[9], dk2T[9], dk3T[9], dk4T[9], dT2T[9], dT3T[9], dT4T[9];
+  double dk1l[3], dk2l[3], dk3l[3], dk4l[3], dT2l[3], dT3l[3], dT4l[3];
+  double tmp[9], c1[3], c2[3], c3[3], c4[3];
+  for (int i = 0; i < 9; ++i) dk1T[i] = kKappa * lam * M1[i];
+  cross(T, B1, c1);
+  for (int i = 0; i < 3; ++i) dk1l[i] = kKappa * c1[i];
+  for (int i = 0; i < 9; ++i) dT2T[i] = I3[i] + 0.5 * h * dk1T[i];
+  for (int i = 0; i < 3; ++i) dT2l[i] = 0.5 * h * dk1l[i];
+  matmul(M2, dT2T, tmp, 3, 3, 3);
+  for (int i = 0; i < 9; ++i) dk2T[i] = kKappa * lam * tmp[i];
+  cross(T2, B2, c2);
+  matmul(M2, dT2l, tmp, 3, 3, 1);
+  for (int i = 0; i < 3; ++i) dk2l[i] = kKappa * c2[i] + kKappa * lam * tmp[i];
+  for (int i = 0; i < 9; ++i) dT3T[i] = I3[i] + 0.5 * h * dk2T[i];
+  for (int i = 0; i < 3; ++i) dT3l[i] = 0.5 * h * dk2l[i];
+  matmul(M2, dT3T, tmp, 3, 3, 3);
+  for (int i = 0; i < 9; ++i) dk3T[i] = kKappa * lam * tmp[i];
+  cross(T3, B2, c3);
+  matmul(M2, dT3l, tmp, 3, 3, 1);
+  for (int i = 0; i < 3; ++i) dk3l[i] = kKappa * c3[i] + kKappa * lam * tmp[i];
+  for (int i = 0; i < 9; ++i) dT4T[i] = I3[i] + h * dk3T[i];
+  for (int i = 0; i < 3; ++i) dT4l[i] = h * dk3l[i];
+  matmul(M4, dT4T, tmp, 3, 3, 3);
+  for (int i = 0; i < 9; ++i) dk4T[i] = kKappa * lam * tmp[i];
+  cross(T4, B4, c4);
+  matmul(M4, dT4l, tmp, 3, 3, 1);
+  for (int i = 0; i < 3; ++i) dk4l[i] = kKappa * c4[i] + kKappa * lam * tmp[i];
+
+  // D = [[I, dr'/dT, dr'/dlam], [0, dT'/dT, dT'/dlam], [0, 0, 1]]
+  for (int i = 0; i < 49; ++i) out.D[i] = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    out.D[i * 7 + i] = 1.0;
+    for (int j = 0; j < 3; ++j) {
+      double id = (i == j) ? 1.0 : 0.0;
+      out.D[i * 7 + 3 + j] = h * id + h * h / 6.0 * (dk1T[i * 3 + j] + dk2T[i * 3 + j] + dk3T[i * 3 + j]);
+      out.D[(3 + i) * 7 + 3 + j] =
+          id + h / 6.0 * (dk1T[i * 3 + j] + 2.0 * dk2T[i * 3 + j] + 2.0 * dk3T[i * 3 + j] + dk4T[i * 3 + j]);
+    }
+    out.D[i * 7 + 6] = h * h / 6.0 * (dk1l[i] + dk2l[i] + dk3l[i]);
+    out.D[(3 + i) * 7 + 6] = h / 6.0 * (dk1l[i] + 2.0 * dk2l[i] + 2.0 * dk3l[i] + dk4l[i]);
+  }
+  out.D[6 * 7 + 6] = 1.0;
+}
+
+// ---------------------------------------------------------------- propagation to a plane
+// Adaptive RKN stepping from (r, T, lam) to the plane of surface s.
+// Reading (step control, after Lund 2009a): before each step the straight-line path
+// s_l = n.(c - r) / n.T to the plane is computed; the step is s_l if |s_l| < h_ctrl,
+// else h_ctrl with the sign of s_l. A step with eps > tol is rejected and h_ctrl becomes
+// |h| * max(1/4, (tol/eps)^(1/4)); an accepted step that was limited by h_ctrl sets
+// h_ctrl = min(h_max, h_ctrl * min(4, (tol/eps)^(1/4))). Propagation stops when
+// |n.(r - c)| <= surf_tol. Reading: a plane more than 1 mm behind the start point (first
+// straight-line path s_l < -1 mm, or not finite) is a miss; overlapping modules can be crossed
+// within a fraction of a millimetre, and the update may then leave the next plane just behind.
+struct PropState {
+  double h_ctrl;
+  uint32_t attempts;  // all step attempts, this track
+  uint32_t rejected;  // rejected attempts, this track
+};
+
+double quarter_root_clamped(double q, double lo, double hi) {
+  // clamp(q^(1/4), lo, hi) with q^(1/4) taken as sqrt(sqrt(q)).
+  double f = std::sqrt(std::sqrt(q));
+  if (f < lo) f = lo;
+  if (f > hi) f = hi;
+  return f;
+}
+
+uint32_t propagate(const Field& f, const Opts& o, const Surface& s, double r[3], double T[3], double lam,
+                   double Dtot[49], double dxds[7], PropState& ps) {
+  uint32_t status = 0;
+  for (int i = 0; i < 49; ++i) Dtot[i] = (i % 8 == 0) ? 1.0 : 0.0;
+  bool first = true;
+  uint32_t n_here = 0;
+  for (;;) {
+    double diff[3] = {s.c[0] - r[0], s.c[1] - r[1], s.c[2] - r[2]};
+    double dist = dot3(s.n, diff);
+    if (std::fabs(dist) <= o.surf_tol) break;
+    double sl = dist / dot3(s.n, T);
+    if (first && !(sl > -1.0 && std::isfinite(sl))) return status | kSurfaceMissed;
+    first = false;
+    if (n_here >= o.max_steps) return status | kMaxSteps;
+    ++n_here;
+    ++ps.attempts;
+    bool limited = !(std::fabs(sl) < ps.h_ctrl);
+    double h = limited ? std::copysign(ps.h_ctrl, sl) : sl;
+    Step st;
+    bool oof = false;
+    rkn_step(f, r, T, lam, h, st, &oof);
+    if (st.eps > o.tol) {
+      ++ps.rejected;
+      ps.h_ctrl = std::fabs(h) * quarter_root_clamped(o.tol / st.eps, 0.25, 4.0);
+      if (ps.h_ctrl < o.h_min) return status | kStepUnderflow;
+      continue;
+    }
+    if (oof) status |= kOutOfField;
+    for (int i = 0; i < 3; ++i) {
+      r[i] = st.r[i];
+      T[i] = st.T[i];
+    }
+    matmul(st.D, Dtot, Dtot, 7, 7, 7);
+    if (limited) {
+      double fac = (st.eps > 0.0) ? quarter_root_clamped(o.tol / st.eps, 0.25, 4.0) : 4.0;
+      ps.h_ctrl = std::min(o.h_max, ps.h_ctrl * fac);
+    }
+  }
+  // dx/ds at the end point: (T, kappa*lam*T x B(r), 0).
+  double B[3], c[3];
+  bool oof = false;
+  field_at(f, r, B, &oof);
+  if (oof) status |= kOutOfField;
+  cross(T, B, c);
+  for (int i = 0; i < 3; ++i) {
+    dxds[i] = T[i];
+    dxds[3 + i] = kKappa * lam * c[i];
+  }
+  dxds[6] = 0.0;
+  return status;
+}
+
+// ---------------------------------------------------------------- parametrisation
+// Bound parameters on a plane: (l0, l1, phi, theta, q/p), with (l0, l1) = (u.(r-c), v.(r-c)),
+// T = (sin th cos ph, sin th sin ph, cos th). Free parameters: (r, T, q/p).
+void bound_to_free(const Surface& s, const double p[5], double r[3], double T[3]) {
+  for (int i = 0; i < 3; ++i) r[i] = s.c[i] + p[0] * s.u[i] + p[1] * s.v[i];
+  T[0] = std::sin(p[3]) * std::cos(p[2]);
+  T[1] = std::sin(p[3]) * std::sin(p[2]);
+  T[2] = std::cos(p[3]);
+}
+
+// Reading: T is renormalised only here, when converting to bound parameters.
+void free_to_bound(const Surface& s, const double r[3], const double T[3], double lam, double p[5]) {
+  double d[3] = {r[0] - s.c[0], r[1] - s.c[1], r[2] - s.c[2]};
+  double nT = std::sqrt(dot3(T, T));
+  double t[3] = {T[0] / nT, T[1] / nT, T[2] / nT};
+  p[0] = dot3(s.u, d);
+  p[1] = dot3(s.v, d);
+  p[2] = std::atan2(t[1], t[0]);
+  p[3] = std::acos(t[2]);
+  p[4] = lam;
+}
+
+// d(free)/d(bound), 7x5.
+void jac_bound_to_free(const Surface& s, const double p[5], double J[35]) {
+  for (int i = 0; i < 35; ++i) J[i] = 0.0;
+  double sp = std::sin(p[2]), cp = std::cos(p[2]), st = std::sin(p[3]), ct = std::cos(p[3]);
+  for (int i = 0; i < 3; ++i) {
+    J[i * 5 + 0] = s.u[i];
+    J[i * 5 + 1] = s.v[i];
+  }
+  J[3 * 5 + 2] = -st * sp;
+  J[4 * 5 + 2] = st * cp;
+  J[5 * 5 + 2] = 0.0;
+  J[3 * 5 + 3] = ct * cp;
+  J[4 * 5 + 3] = ct * sp;
+  J[5 * 5 + 3] = -st;
+  J[6 * 5 + 4] = 1.0;
+}
+
+// d(bound)/d(free), 5x7, at the target plane (angles from the normalised direction).
+// The angle rows are the tangent-space gradients of phi and theta.
+void jac_free_to_bound(const Surface& s, const double T[3], double J[35]) {
+  for (int i = 0; i < 35; ++i) J[i] = 0.0;
+  double nT = std::sqrt(dot3(T, T));
+  double t[3] = {T[0] / nT, T[1] / nT, T[2] / nT};
+  double phi = std::atan2(t[1], t[0]), th = std::acos(t[2]);
+  double sp = std::sin(phi), cp = std::cos(phi), st = std::sin(th), ct = std::cos(th);
+  for (int i = 0; i < 3; ++i) {
+    J[0 * 7 + i] = s.u[i];
+    J[1 * 7 + i] = s.v[i];
+  }
+  J[2 * 7 + 3] = -sp / st;
+  J[2 * 7 + 4] = cp / st;
+  J[3 * 7 + 3] = ct * cp;
+  J[3 * 7 + 4] = ct * sp;
+  J[3 * 7 + 5] = -st;
+  J[4 * 7 + 6] = 1.0;
+}
+
+// Path correction at the plane: the free state moves along dx/ds by
+// ds = -n.dr / n.T when the intersection shifts, so P = I - dxds (n,0,0)^T / (n.T).
+void path_correction(const Surface& s, const double T[3], const double dxds[7], double P[49]) {
+  double nT = dot3(s.n, T);
+  for (int i = 0; i < 7; ++i)
+    for (int j = 0; j < 7; ++j) {
+      double nj = (j < 3) ? s.n[j] : 0.0;
+      P[i * 7 + j] = ((i == j) ? 1.0 : 0.0) - dxds[i] * nj / nT;
+    }
+}
+
+// ---------------------------------------------------------------- material
+// Highland (PDG) r.m.s. plane scattering angle for a path x in a layer of radiation
+// length X0: theta0 = 13.6 MeV / (beta c p) * sqrt(x/X0) * (1 + 0.038 ln(x / (X0 beta^2))).
+double highland(double p, double beta, double x, double X0) {
+  return 0.0136 / (beta * p) * std::sqrt(x / X0) * (1.0 + 0.038 * std::log(x / (X0 * beta * beta)));
+}
+
+// Mean energy loss rate (Bethe, PDG) in MeV cm^2 / g for a unit-charge particle of mass m.
+// Reading: density effect delta/2 = max(0, ln(hbar omega_p / I) + ln(beta gamma) - 1/2),
+// the high-energy asymptote; no shell correction.
+double bethe(double p, double m, const Opts& o) {
+  double E = std::sqrt(p * p + m * m);
+  double beta2 = (p * p) / (E * E);
+  double gamma = E / m;
+  double bg2 = (p / m) * (p / m);
+  double me_m = kMe / m;
+  double wmax = 2.0 * kMe * bg2 / (1.0 + 2.0 * gamma * me_m + me_m * me_m);  // GeV
+  double I = o.I_eV * 1e-9;                                                   // GeV
+  double half_delta = std::log(o.hwp_eV / o.I_eV) + 0.5 * std::log(bg2) - 0.5;
+  if (half_delta < 0.0) half_delta = 0.0;
+  return kBetheK * o.ZA / beta2 * (0.5 * std::log(2.0 * kMe * bg2 * wmax / (I * I)) - beta2 - half_delta);
+}
+
+// Thin-layer material at surface s, applied to the filtered state after the update.
+// Adds theta0^2 / sin^2(theta) to Var(phi) and theta0^2 to Var(theta) (Q, full 5x5), and
+// lowers |p| by the mean energy loss. Reading: no energy-loss variance; the material
+// Jacobian is the identity.
+uint32_t material(const Surface& s, const Opts& o, double p[5], double Q[25]) {
+  for (int i = 0; i < 25; ++i) Q[i] = 0.0;
+  if (!(s.t > 0.0)) return 0;
+  double r[3], T[3];
+  bound_to_free(s, p, r, T);
+  double x = s.t / std::fabs(dot3(s.n, T));
+  double mom = 1.0 / std::fabs(p[4]);
+  double E = std::sqrt(mom * mom + o.mass * o.mass);
+  double beta = mom / E;
+  double th0 = highland(mom, beta, x, s.X0);
+  double sth = std::sin(p[3]);
+  Q[2 * 5 + 2] = th0 * th0 / (sth * sth);
+  Q[3 * 5 + 3] = th0 * th0;
+  double dE = bethe(mom, o.mass, o) * o.rho * (x * 0.1) * 1e-3;  // GeV
+  double E2 = E - dE;
+  if (!(E2 > o.mass)) return kParticleStopped;
+  double mom2 = std::sqrt(E2 * E2 - o.mass * o.mass);
+  p[4] = std::copysign(1.0 / mom2, p[4]);
+  return 0;
+}
+
+// ---------------------------------------------------------------- Kalman update
+// Gain-matrix update with H = [I2 0]: S = V + H C H^T, K = C H^T S^-1, p' = p + K r,
+// C' = (I - K H) C (I - K H)^T + K V K^T (Joseph form), chi2 = r^T S^-1 r with the
+// predicted residual r = m - H p.
+uint32_t kf_update(const double m[2], const double V[4], double p[5], double C[25], double* chi2) {
+  double H[10] = {1, 0, 0, 0, 0, 0, 1, 0, 0, 0};
+  double Ht[10];
+  transpose(H, Ht, 2, 5);
+  double HC[10], S[4], CHt[10];
+  matmul(H, C, HC, 2, 5, 5);
+  matmul(HC, Ht, S, 2, 5, 2);
+  for (int i = 0; i < 4; ++i) S[i] += V[i];
+  double det = S[0] * S[3] - S[1] * S[2];
+  if (!(S[0] > 0.0 && det > 0.0)) return kUpdateNotSpd;
+  double Si[4] = {S[3] / det, -S[1] / det, -S[2] / det, S[0] / det};
+  matmul(C, Ht, CHt, 5, 5, 2);
+  double K[10];
+  matmul(CHt, Si, K, 5, 2, 2);
+  double Hp[2];
+  matmul(H, p, Hp, 2, 5, 1);
+  double res[2] = {m[0] - Hp[0], m[1] - Hp[1]};
+  double Kr[5];
+  matmul(K, res, Kr, 5, 2, 1);
+  for (int i = 0; i < 5; ++i) p[i] += Kr[i];
+  double Sr[2];
+  matmul(Si, res, Sr, 2, 2, 1);
+  *chi2 = res[0] * Sr[0] + res[1] * Sr[1];
+  double IKH[25], KH[25];
+  matmul(K, H, KH, 5, 2, 5);
+  for (int i = 0; i < 25; ++i) IKH[i] = ((i % 6) == 0 ? 1.0 : 0.0) - KH[i];
+  double IKHt[25], A[25], B[25], Kt[10], KV[10], KVKt[25];
+  transpose(IKH, IKHt, 5, 5);
+  matmul(IKH, C, A, 5, 5, 5);
+  matmul(A, IKHt, B, 5, 5, 5);
+  transpose(K, Kt, 5, 2);
+  matmul(K, V, KV, 5, 2, 2);
+  matmul(KV, Kt, KVKt, 5, 2, 5);
+  for (int i = 0; i < 25; ++i) C[i] = B[i] + KVKt[i];
+  symmetrize(C, 5);
+  return 0;
+}
+
+// ---------------------------------------------------------------- RTS smoother
+// Backward pass k = N-2 .. 0 over stored filtered (pf, Cf) and predicted (pp, Cp) states
+// and transport Jacobians J[k+1] (k -> k+1):
+//   A_k = Cf_k J_{k+1}^T Cp_{k+1}^-1,
+//   ps_k = pf_k + A_k (ps_{k+1} - pp_{k+1}),
+//   Cs_k = Cf_k + A_k (Cs_{k+1} - Cp_{k+1}) A_k^T   (symmetrised).
+// The phi component of a parameter difference is wrapped to (-pi, pi].
+uint32_t rts(int N, const double* pf, const double* Cf, const double* pp, const double* Cp, const double* J,
+             double* ps, double* Cs) {
+  std::memcpy(ps + (N - 1) * 5, pf + (N - 1) * 5, sizeof(double) * 5);
+  std::memcpy(Cs + (N - 1) * 25, Cf + (N - 1) * 25, sizeof(double) * 25);
+  for (int k = N - 2; k >= 0; --k) {
+    double Cpi[25], Jt[25], A[25], At[25], tmp[25], dC[25], dCs[25];
+    if (!spd_inverse(Cp + (k + 1) * 25, Cpi, 5)) return kSmootherNotSpd;
+    transpose(J + (k + 1) * 25, Jt, 5, 5);
+    matmul(Cf + k * 25, Jt, tmp, 5, 5, 5);
+    matmul(tmp, Cpi, A, 5, 5, 5);
+    double dp[5], Adp[5];
+    for (int i = 0; i < 5; ++i) dp[i] = ps[(k + 1) * 5 + i] - pp[(k + 1) * 5 + i];
+    dp[2] = wrap_phi(dp[2]);
+    matmul(A, dp, Adp, 5, 5, 1);
+    for (int i = 0; i < 5; ++i) ps[k * 5 + i] = pf[k * 5 + i] + Adp[i];
+    ps[k * 5 + 2] = wrap_phi(ps[k * 5 + 2]);
+    for (int i = 0; i < 25; ++i) dC[i] = Cs[(k + 1) * 25 + i] - Cp[(k + 1) * 25 + i];
+    transpose(A, At, 5, 5);
+    matmul(A, dC, tmp, 5, 5, 5);
+    matmul(tmp, At, dCs, 5, 5, 5);
+    for (int i = 0; i < 25; ++i) Cs[k * 25 + i] = Cf[k * 25 + i] + dCs[i];
+    symmetrize(Cs + k * 25, 5);
+  }
+  return 0;
+}
+
+// ---------------------------------------------------------------- one track
+void unpack_cov(const double* packed, double C[25]) {
+  int idx = 0;
+  for (int i = 0; i < 5; ++i)
+    for (int j = i; j < 5; ++j) {
+      C[i * 5 + j] = packed[idx];
+      C[j * 5 + i] = packed[idx];
+      ++idx;
+    }
+}
+
+void pack_cov(const double C[25], double* packed) {
+  int idx = 0;
+  for (int i = 0; i < 5; ++i)
+    for (int j = i; j < 5; ++j) packed[idx++] = C[i * 5 + j];
+}
+
+struct TrackIn {
+  uint32_t N;
+  const double* meas;  // [N][5]: loc0, loc1, V00, V01, V11
+  const uint32_t* sid;
+  const double* seed_par;  // [5]
+  const double* seed_cov;  // [15]
+};
+
+struct TrackOut {
+  double par[5], cov[15], chi2;
+  int32_t ndf;
+  uint32_t status;
+  uint32_t attempts, rejected;
+};
+
+void fill_nan(TrackOut& out) {
+  double nan = std::nan("");
+  for (int i = 0; i < 5; ++i) out.par[i] = nan;
+  for (int i = 0; i < 15; ++i) out.cov[i] = nan;
+  out.chi2 = nan;
+}
+
+bool all_finite(const double* a, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+struct States {
+  std::vector<double> pp, Cp, pf, Cf, J, ps, Cs;
+};
+
+void fit_track(const Surface* surf, uint32_t n_surf, const Field& f, const Opts& o, const TrackIn& in,
+               TrackOut& out, States* keep = nullptr) {
+  const int N = int(in.N);
+  out.status = 0;
+  out.attempts = out.rejected = 0;
+  out.ndf = 2 * N;
+  if (N == 0) {
+    std::memcpy(out.par, in.seed_par, sizeof(double) * 5);
+    std::memcpy(out.cov, in.seed_cov, sizeof(double) * 15);
+    out.chi2 = 0.0;
+    out.status = kTooFewHits;
+    return;
+  }
+  for (int k = 0; k < N; ++k)
+    if (in.sid[k] >= n_surf) {
+      fill_nan(out);
+      out.status = kBadInput;
+      return;
+    }
+  if (!all_finite(in.seed_par, 5) || !all_finite(in.seed_cov, 15)) {
+    fill_nan(out);
+    out.status = kNonFinite;
+    return;
+  }
+  std::vector<double> pp(N * 5), Cp(N * 25), pf(N * 5), Cf(N * 25), J(N * 25, 0.0), ps(N * 5), Cs(N * 25);
+  std::memcpy(&pp[0], in.seed_par, sizeof(double) * 5);
+  unpack_cov(in.seed_cov, &Cp[0]);
+  PropState prop{o.h_max, 0, 0};
+  double chi2 = 0.0;
+  uint32_t status = 0;
+  for (int k = 0; k < N; ++k) {
+    const Surface& sk = surf[in.sid[k]];
+    if (k > 0) {
+      const Surface& sprev = surf[in.sid[k - 1]];
+      double pm[5], Q[25];
+      std::memcpy(pm, &pf[(k - 1) * 5], sizeof(pm));
+      status |= material(sprev, o, pm, Q);
+      if (status & kFatal) break;
+      double r[3], T[3], Dtot[49], dxds[7], Jb2f[35], Jf2b[35], P[49], tmp[49], t75[35], t55[25];
+      bound_to_free(sprev, pm, r, T);
+      jac_bound_to_free(sprev, pm, Jb2f);
+      status |= propagate(f, o, sk, r, T, pm[4], Dtot, dxds, prop);
+      if (status & kFatal) break;
+      jac_free_to_bound(sk, T, Jf2b);
+      path_correction(sk, T, dxds, P);
+      matmul(P, Dtot, tmp, 7, 7, 7);
+      matmul(tmp, Jb2f, t75, 7, 7, 5);
+      matmul(Jf2b, t75, &J[k * 25], 5, 7, 5);
+      free_to_bound(sk, r, T, pm[4], &pp[k * 5]);
+      double CQ[25], Jt[25];
+      for (int i = 0; i < 25; ++i) CQ[i] = Cf[(k - 1) * 25 + i] + Q[i];
+      transpose(&J[k * 25], Jt, 5, 5);
+      matmul(&J[k * 25], CQ, t55, 5, 5, 5);
+      matmul(t55, Jt, &Cp[k * 25], 5, 5, 5);
+      symmetrize(&Cp[k * 25], 5);
+    }
+    const double* mk = in.meas + 5 * k;
+    double m[2] = {mk[0], mk[1]};
+    double V[4] = {mk[2], mk[3], mk[3], mk[4]};
+    std::memcpy(&pf[k * 5], &pp[k * 5], sizeof(double) * 5);
+    std::memcpy(&Cf[k * 25], &Cp[k * 25], sizeof(double) * 25);
+    double c2 = 0.0;
+    status |= kf_update(m, V, &pf[k * 5], &Cf[k * 25], &c2);
+    if (status & kFatal) break;
+    chi2 += c2;
+    pf[k * 5 + 2] = wrap_phi(pf[k * 5 + 2]);
+    if (!(pf[k * 5 + 3] > 0.0 && pf[k * 5 + 3] < kPi)) {
+      status |= kNonFinite;
+      break;
+    }
+  }
+  out.attempts = prop.attempts;
+  out.rejected = prop.rejected;
+  if (!(status & kFatal)) status |= rts(N, &pf[0], &Cf[0], &pp[0], &Cp[0], &J[0], &ps[0], &Cs[0]);
+  if (!(status & kFatal)) {
+    double L[25];
+    if (!cholesky(&Cs[0], L, 5)) status |= kSmootherNotSpd;
+  }
+  if (!(status & kFatal)) {
+    std::memcpy(out.par, &ps[0], sizeof(double) * 5);
+    pack_cov(&Cs[0], out.cov);
+    out.chi2 = chi2;
+    if (!all_finite(out.par, 5) || !all_finite(out.cov, 15) || !std::isfinite(chi2)) status |= kNonFinite;
+  }
+  if (status & kFatal) fill_nan(out);
+  if (N < 3) status |= kTooFewHits;
+  out.status = status;
+  if (keep) {
+    keep->pp = pp; keep->Cp = Cp; keep->pf = pf; keep->Cf = Cf; keep->J = J; keep->ps = ps; keep->Cs = Cs;
+  }
+}
+
+}  // namespace
+
+// ================================================================ C interface
+extern "C" {
+
+struct orc_field {
+  int kind;
+  double B[3];
+  int nr, nz;
+  double r0, dr, z0, dz;
+  const float* Br;
+  const float* Bz;
+};
+
+struct orc_opts {
+  double tol, h_max, h_min, surf_tol, mass;
+  uint32_t max_steps;
+  double ZA, I_eV, rho, hwp_eV;
+};
+
+static Field to_field(const orc_field* f) {
+  Field F;
+  F.kind = f->kind;
+  for (int i = 0; i < 3; ++i) F.B[i] = f->B[i];
+  F.nr = f->nr; F.nz = f->nz;
+  F.r0 = f->r0; F.dr = f->dr; F.z0 = f->z0; F.dz = f->dz;
+  F.Br = f->Br; F.Bz = f->Bz;
+  return F;
+}
+
+static Opts to_opts(const orc_opts* o) {
+  Opts O;
+  O.tol = o->tol; O.h_max = o->h_max; O.h_min = o->h_min; O.surf_tol = o->surf_tol; O.mass = o->mass;
+  O.max_steps = o->max_steps;
+  O.ZA = o->ZA; O.I_eV = o->I_eV; O.rho = o->rho; O.hwp_eV = o->hwp_eV;
+  return O;
+}
+
+// surfaces: [n][14] = u[3], v[3], n[3], c[3], t, X0
+static std::vector<Surface> to_surfaces(const double* s, uint32_t n) {
+  std::vector<Surface> out(n);
+  for (uint32_t i = 0; i < n; ++i) {
+    const double* q = s + 14 * i;
+    for (int j = 0; j < 3; ++j) {
+      out[i].u[j] = q[j];
+      out[i].v[j] = q[3 + j];
+      out[i].n[j] = q[6 + j];
+      out[i].c[j] = q[9 + j];
+    }
+    out[i].t = q[12];
+    out[i].X0 = q[13];
+  }
+  return out;
+}
+
+// Fit n_tracks tracks. meas: [n_meas][5] (loc0, loc1, V00, V01, V11); seed_par [n][5];
+// seed_cov [n][15] packed upper triangle; outputs in the same AoS layouts.
+// steps (nullable): [n][2] = step attempts, rejected attempts. n_threads >= 1.
+int orc_fit(const double* surfaces, uint32_t n_surf, const orc_field* field, const orc_opts* opts,
+            uint32_t n_tracks, const uint32_t* offsets, const double* meas, const uint32_t* sid,
+            const double* seed_par, const double* seed_cov, double* out_par, double* out_cov, double* chi2,
+            int32_t* ndf, uint32_t* status, uint32_t* steps, int n_threads) {
+  std::vector<Surface> surf = to_surfaces(surfaces, n_surf);
+  Field F = to_field(field);
+  Opts O = to_opts(opts);
+  auto work = [&](uint32_t lo, uint32_t hi) {
+    for (uint32_t i = lo; i < hi; ++i) {
+      TrackIn in;
+      uint32_t a = offsets[i], b = offsets[i + 1];
+      TrackOut out;
+      if (b < a) {
+        fill_nan(out);
+        out.status = kBadInput;
+        out.ndf = -5;
+        out.attempts = out.rejected = 0;
+      } else {
+        in.N = b - a;
+        in.meas = meas + 5 * size_t(a);
+        in.sid = sid + a;
+        in.seed_par = seed_par + 5 * size_t(i);
+        in.seed_cov = seed_cov + 15 * size_t(i);
+        fit_track(surf.data(), n_surf, F, O, in, out);
+      }
+      std::memcpy(out_par + 5 * size_t(i), out.par, sizeof(double) * 5);
+      std::memcpy(out_cov + 15 * size_t(i), out.cov, sizeof(double) * 15);
+      chi2[i] = out.chi2;
+      ndf[i] = out.ndf;
+      status[i] = out.status;
+      if (steps) {
+        steps[2 * size_t(i)] = out.attempts;
+        steps[2 * size_t(i) + 1] = out.rejected;
+      }
+    }
+  };
+  if (n_threads <= 1 || n_tracks < 2) {
+    work(0, n_tracks);
+    return 0;
+  }
+  std::vector<std::thread> th;
+  uint32_t per = (n_tracks + n_threads - 1) / n_threads;
+  for (int t = 0; t < n_threads; ++t) {
+    uint32_t lo = std::min<uint32_t>(n_tracks, t * per), hi = std::min<uint32_t>(n_tracks, lo + per);
+    if (lo < hi) th.emplace_back(work, lo, hi);
+  }
+  for (auto& x : th) x.join();
+  return 0;
+}
+
+// ---- component entry points used by the oracle's own pins
+
+void orc_field_at(const orc_field* field, const double* x, uint32_t n, double* B, uint8_t* oof) {
+  Field F = to_field(field);
+  for (uint32_t i = 0; i < n; ++i) {
+    bool o = false;
+    field_at(F, x + 3 * i, B + 3 * i, &o);
+    oof[i] = o ? 1 : 0;
+  }
+}
+
+// n_steps fixed steps of length h; writes the final (r, T) and the accumulated 7x7 D.
+void orc_rkn_fixed(const orc_field* field, const double* r0, const double* T0, double lam, double h,
+                   uint32_t n_steps, double* r_out, double* T_out, double* D_out) {
+  Field F = to_field(field);
+  double r[3] = {r0[0], r0[1], r0[2]}, T[3] = {T0[0], T0[1], T0[2]};
+  double D[49];
+  for (int i = 0; i < 49; ++i) D[i] = (i % 8 == 0) ? 1.0 : 0.0;
+  for (uint32_t s = 0; s < n_steps; ++s) {
+    Step st;
+    bool oof = false;
+    rkn_step(F, r, T, lam, h, st, &oof);
+    for (int i = 0; i < 3; ++i) {
+      r[i] = st.r[i];
+      T[i] = st.T[i];
+    }
+    matmul(st.D, D, D, 7, 7, 7);
+  }
+  std::memcpy(r_out, r, sizeof(r));
+  std::memcpy(T_out, T, sizeof(T));
+  if (D_out) std::memcpy(D_out, D, sizeof(D));
+}
+
+// One RKN step: writes r', T', eps.
+void orc_rkn_step(const orc_field* field, const double* r, const double* T, double lam, double h,
+                  double* r_out, double* T_out, double* eps) {
+  Field F = to_field(field);
+  Step st;
+  bool oof = false;
+  rkn_step(F, r, T, lam, h, st, &oof);
+  std::memcpy(r_out, st.r, sizeof(st.r));
+  std::memcpy(T_out, st.T, sizeof(st.T));
+  *eps = st.eps;
+}
+
+// Bound -> bound transport from surface a to surface b (no material, no update):
+// par_out = f(par_in), J = d par_out / d par_in (5x5 row-major). Returns the status bits.
+uint32_t orc_transport(const double* surfaces, uint32_t a, uint32_t b, const orc_field* field,
+                       const orc_opts* opts, const double* par_in, double* par_out, double* J,
+                       uint32_t* attempts) {
+  std::vector<Surface> surf = to_surfaces(surfaces, std::max(a, b) + 1);
+  Field F = to_field(field);
+  Opts O = to_opts(opts);
+  double r[3], T[3], Dtot[49], dxds[7], Jb2f[35], Jf2b[35], P[49], tmp[49], t75[35];
+  bound_to_free(surf[a], par_in, r, T);
+  jac_bound_to_free(surf[a], par_in, Jb2f);
+  PropState ps{O.h_max, 0, 0};
+  uint32_t st = propagate(F, O, surf[b], r, T, par_in[4], Dtot, dxds, ps);
+  if (attempts) *attempts = ps.attempts;
+  if (st & kFatal) return st;
+  jac_free_to_bound(surf[b], T, Jf2b);
+  path_correction(surf[b], T, dxds, P);
+  matmul(P, Dtot, tmp, 7, 7, 7);
+  matmul(tmp, Jb2f, t75, 7, 7, 5);
+  matmul(Jf2b, t75, J, 5, 7, 5);
+  free_to_bound(surf[b], r, T, par_in[4], par_out);
+  return st;
+}
+
+// Material model at one surface: theta0, and the q/p after the mean energy loss.
+uint32_t orc_material(const double* surface14, const orc_opts* opts, const double* par, double* theta0,
+                      double* qop_after, double* dedx_mev_cm2_g) {
+  std::vector<Surface> s = to_surfaces(surface14, 1);
+  Opts O = to_opts(opts);
+  double p[5], Q[25];
+  std::memcpy(p, par, sizeof(p));
+  uint32_t st = material(s[0], O, p, Q);
+  *theta0 = std::sqrt(Q[3 * 5 + 3]);
+  *qop_after = p[4];
+  double mom = 1.0 / std::fabs(par[4]);
+  *dedx_mev_cm2_g = bethe(mom, O.mass, O);
+  return st;
+}
+
+// Linear-Gaussian chain through the oracle's own update and smoother: states x_k in R^5
+// with x_k = J_k (x_{k-1} + w_{k-1}), w ~ N(0, Q_{k-1}), measured by H = [I2 0] with
+// covariance V_k; prior x_0 ~ N(p0, C0). Writes the smoothed mean/cov of every state
+// (ps [N][5], Cs [N][25]) and the chi2 sum. Returns status bits.
+uint32_t orc_linear_chain(int N, const double* J, const double* Q, const double* p0, const double* C0,
+                          const double* m, const double* V, double* ps, double* Cs, double* chi2_out,
+                          double* pf_out, double* Cf_out) {
+  std::vector<double> pp(N * 5), Cp(N * 25), pf(N * 5), Cf(N * 25);
+  std::memcpy(&pp[0], p0, sizeof(double) * 5);
+  std::memcpy(&Cp[0], C0, sizeof(double) * 25);
+  double chi2 = 0.0;
+  uint32_t st = 0;
+  for (int k = 0; k < N; ++k) {
+    if (k > 0) {
+      const double* Jk = J + 25 * k;
+      double CQ[25], Jt[25], t[25];
+      for (int i = 0; i < 25; ++i) CQ[i] = Cf[(k - 1) * 25 + i] + Q[(k - 1) * 25 + i];
+      matmul(Jk, &pf[(k - 1) * 5], &pp[k * 5], 5, 5, 1);
+      transpose(Jk, Jt, 5, 5);
+      matmul(Jk, CQ, t, 5, 5, 5);
+      matmul(t, Jt, &Cp[k * 25], 5, 5, 5);
+      symmetrize(&Cp[k * 25], 5);
+    }
+    std::memcpy(&pf[k * 5], &pp[k * 5], sizeof(double) * 5);
+    std::memcpy(&Cf[k * 25], &Cp[k * 25], sizeof(double) * 25);
+    double c2 = 0.0, mm[2] = {m[2 * k], m[2 * k + 1]};
+    st |= kf_update(mm, V + 4 * k, &pf[k * 5], &Cf[k * 25], &c2);
+    chi2 += c2;
+  }
+  // The linear chain has no angle wrap: undo wrap_phi's effect by keeping |phi| small.
+  st |= rts(N, &pf[0], &Cf[0], &pp[0], &Cp[0], J, ps, Cs);
+  *chi2_out = chi2;
+  if (pf_out) std::memcpy(pf_out, &pf[0], sizeof(double) * 5 * N);
+  if (Cf_out) std::memcpy(Cf_out, &Cf[0], sizeof(double) * 25 * N);
+  return st;
+}
+
+// Fits one track and exports its per-measurement states: predicted (pp [N][5], Cp [N][25]),
+// filtered (pf, Cf), smoothed (ps, Cs) and the transport Jacobians J [N][25] (J[0] unused).
+uint32_t orc_fit_states(const double* surfaces, uint32_t n_surf, const orc_field* field, const orc_opts* opts,
+                        uint32_t N, const double* meas, const uint32_t* sid, const double* seed_par,
+                        const double* seed_cov, double* pp, double* Cp, double* pf, double* Cf, double* J,
+                        double* ps, double* Cs, double* chi2) {
+  std::vector<Surface> surf = to_surfaces(surfaces, n_surf);
+  Field F = to_field(field);
+  Opts O = to_opts(opts);
+  TrackIn in{N, meas, sid, seed_par, seed_cov};
+  TrackOut out;
+  States st;
+  fit_track(surf.data(), n_surf, F, O, in, out, &st);
+  if (st.pp.size() == size_t(N) * 5) {
+    std::memcpy(pp, st.pp.data(), sizeof(double) * 5 * N);
+    std::memcpy(Cp, st.Cp.data(), sizeof(double) * 25 * N);
+    std::memcpy(pf, st.pf.data(), sizeof(double) * 5 * N);
+    std::memcpy(Cf, st.Cf.data(), sizeof(double) * 25 * N);
+    std::memcpy(J, st.J.data(), sizeof(double) * 25 * N);
+    std::memcpy(ps, st.ps.data(), sizeof(double) * 5 * N);
+    std::memcpy(Cs, st.Cs.data(), sizeof(double) * 25 * N);
+  }
+  *chi2 = out.chi2;
+  return out.status;
+}
+
+// One gain-matrix update (for the chi2 identity pin).
+uint32_t orc_update(const double* m, const double* V, double* p, double* C, double* chi2) {
+  return kf_update(m, V, p, C, chi2);
+}
+
+}  // extern "C"

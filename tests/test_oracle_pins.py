@@ -1,0 +1,318 @@
+"""Pins of the CPU oracle against what the mathematics and the physics fix (no GPU).
+
+Each pin is an independent definition, not a retyped oracle formula:
+  * RKN propagation vs the analytic helix of a charged particle in a uniform field;
+  * the RKN local-error order and error-estimate order;
+  * the transported Jacobian vs central finite differences of the oracle's own propagator;
+  * Kalman update + RTS smoother vs the batch Gaussian posterior of a linear chain;
+  * the per-hit chi2 identity (predicted-residual form = filtered-residual form);
+  * noise-free tracks fit back to truth;
+  * pulls N(0,1) and chi2/ndf = 1 on smeared tracks (statistical pin of the whole fit);
+  * the Bethe minimum-ionisation value of silicon (PDG table);
+  * Highland scaling with beta*p.
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+KAPPA = 2.99792458e-4  # GeV / (T mm)
+
+
+def uniform(bz=2.0, B=None):
+    return oracle.make_field(0, B if B is not None else (0.0, 0.0, bz))
+
+
+# ------------------------------------------------------------------ propagation
+def helix_exact(r, T, lam, B, s):
+    """Charged-particle motion in a uniform field: T rotates about B at rate kappa*lam*|B|."""
+    B = np.asarray(B, float)
+    Bm = np.linalg.norm(B)
+    b = B / Bm
+    a = KAPPA * lam * Bm  # dT/ds = a T x b
+    tpar = np.dot(T, b) * b
+    tperp = T - tpar
+    bxt = np.cross(b, T)
+    r_s = r + tpar * s + tperp * np.sin(a * s) / a + bxt * (np.cos(a * s) - 1.0) / a
+    T_s = tpar + tperp * np.cos(a * s) - bxt * np.sin(a * s)
+    return r_s, T_s
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_rkn_matches_analytic_helix(seed):
+    rng = np.random.default_rng(seed)
+    B = rng.normal(size=3)
+    B *= 2.0 / np.linalg.norm(B)
+    T = rng.normal(size=3)
+    T /= np.linalg.norm(T)
+    r = rng.normal(size=3) * 100
+    lam = rng.choice([-1, 1]) / rng.uniform(0.5, 5.0)  # q/p, 1/GeV
+    h, n = 1.0, 1000
+    ro, To, _ = oracle.rkn_fixed(uniform(B=B), r, T, lam, h, n)
+    re, Te = helix_exact(r, T, lam, B, h * n)
+    assert np.max(np.abs(ro - re)) / (h * n) < 1e-9
+    assert np.max(np.abs(To - Te)) < 1e-9
+
+
+def test_rkn_local_error_is_fifth_order_and_estimate_fourth_order():
+    B = (0.0, 0.0, 2.0)
+    T = np.array([0.6, 0.0, 0.8])
+    r = np.zeros(3)
+    lam = 2.0
+    errs, ests = [], []
+    for h in (40.0, 20.0, 10.0):
+        ro, _, eps = oracle.rkn_step(uniform(B=B), r, T, lam, h)
+        re, _ = helix_exact(r, T, lam, B, h)
+        errs.append(np.linalg.norm(ro - re))
+        ests.append(eps)
+    # halving h divides the local position error by ~2^5 and the estimate by ~2^4
+    for i in range(2):
+        assert 25 < errs[i] / errs[i + 1] < 40
+        assert 14 < ests[i] / ests[i + 1] < 18
+    # the estimate bounds the true local error in this regime
+    assert all(e < 10 * x for e, x in zip(errs, ests))
+
+
+def _fd_jacobian(surf, a, b, fld, opts, par, steps):
+    J = np.zeros((5, 5))
+    for j in range(5):
+        dp = np.zeros(5)
+        dp[j] = steps[j]
+        up, _, s1, _ = oracle.transport(surf, a, b, fld, opts, par + dp)
+        dn, _, s2, _ = oracle.transport(surf, a, b, fld, opts, par - dp)
+        assert s1 == 0 and s2 == 0
+        d = up - dn
+        d[2] = (d[2] + np.pi) % (2 * np.pi) - np.pi
+        J[:, j] = d / (2 * steps[j])
+    return J
+
+
+@pytest.mark.parametrize("case", ["telescope", "barrel"])
+def test_transport_jacobian_matches_finite_differences(case):
+    opts = oracle.Options(tol=1e-10)
+    if case == "telescope":
+        g = synth.telescope_geometry()
+        pairs = [(0, 1), (2, 5), (0, 8)]
+        par = np.array([1.3, -2.1, 0.05, np.pi / 2 - 0.03, 1.0 / 1.7])
+    else:
+        g = synth.barrel_endcap_geometry()
+        w = synth.barrel_workload(n_events=1, lo=20, hi=20, seed=11, fld=synth.uniform_field(2.0),
+                                  geom=g, mass=synth.MUON_MASS)
+        t = w.tracks
+        k = int(np.argmax(t.hits_per_track()))
+        a0 = t.offsets[k]
+        pairs = [(int(t.sid[a0]), int(t.sid[a0 + 1])), (int(t.sid[a0 + 1]), int(t.sid[a0 + 4]))]
+        par = t.truth[k].copy()
+    fld = uniform(2.0)
+    surf = g.table
+    scale_in = np.array([1.0, 1.0, 1e-3, 1e-3, 1e-2 * abs(par[4])])
+    for a, b in pairs:
+        p = par.copy()
+        if case == "barrel" and a != pairs[0][0]:
+            p, _, _, _ = oracle.transport(surf, pairs[0][0], a, fld, opts, par)
+        _, J, st, _ = oracle.transport(surf, a, b, fld, opts, p)
+        assert st == 0
+        steps = np.array([1e-3, 1e-3, 1e-6, 1e-6, 1e-6 * abs(p[4])])
+        Jfd = _fd_jacobian(surf, a, b, fld, opts, p, steps)
+        Jn = J * scale_in[None, :] / scale_in[:, None]
+        Jfdn = Jfd * scale_in[None, :] / scale_in[:, None]
+        err = np.abs(Jn - Jfdn)
+        assert np.all(err <= 1e-6 * np.maximum(1.0, np.abs(Jn))), (a, b, err.max())
+
+
+# ------------------------------------------------------------------ update + smoother
+def _batch_posterior(J, L, p0, C0, m, V, upto=None):
+    """Posterior of x_0..x_{N-1} for x_k = J_k (x_{k-1} + L_{k-1} xi_{k-1}), xi ~ N(0, I),
+    x_0 ~ N(p0, C0), m_k = H x_k + N(0, V_k): one dense least-squares solve in the variables
+    z = (x_0, xi_0, ..., xi_{N-2}). Returns means, covariances and the minimum objective."""
+    N = m.shape[0]
+    r = L.shape[2]
+    nz = 5 + r * (N - 1)
+    A = [np.zeros((5, nz)) for _ in range(N)]
+    A[0][:, :5] = np.eye(5)
+    for k in range(1, N):
+        E = A[k - 1].copy()
+        E[:, 5 + r * (k - 1):5 + r * k] += L[k - 1]
+        A[k] = J[k] @ E
+    H = np.zeros((2, 5))
+    H[0, 0] = H[1, 1] = 1
+    C0i = np.linalg.inv(C0)
+    Lam = np.zeros((nz, nz))
+    eta = np.zeros(nz)
+    Lam[:5, :5] += C0i
+    eta[:5] += C0i @ p0
+    Lam[5:, 5:] += np.eye(nz - 5)
+    last = N if upto is None else upto + 1
+    for k in range(last):
+        HA = H @ A[k]
+        Vi = np.linalg.inv(V[k])
+        Lam += HA.T @ Vi @ HA
+        eta += HA.T @ Vi @ m[k]
+    S = np.linalg.inv(Lam)
+    mu = S @ eta
+    obj = (mu[:5] - p0) @ C0i @ (mu[:5] - p0) + mu[5:] @ mu[5:]
+    for k in range(last):
+        res = m[k] - H @ A[k] @ mu
+        obj += res @ np.linalg.inv(V[k]) @ res
+    means = np.array([A[k] @ mu for k in range(N)])
+    covs = np.array([A[k] @ S @ A[k].T for k in range(N)])
+    return means, covs, obj
+
+
+@pytest.mark.parametrize("seed,rank", [(0, 2), (1, 2), (2, 5), (3, 5), (4, 1)])
+def test_update_and_rts_equal_batch_gaussian_posterior(seed, rank):
+    rng = np.random.default_rng(seed)
+    N = 7
+    J = np.array([np.eye(5) + 0.2 * rng.normal(size=(5, 5)) for _ in range(N)])
+    L = 0.05 * rng.normal(size=(N, 5, rank))
+    Q = np.einsum("kij,klj->kil", L, L)
+    p0 = 0.1 * rng.normal(size=5)
+    X = rng.normal(size=(5, 5))
+    C0 = X @ X.T * 0.05 + 0.01 * np.eye(5)
+    m = 0.1 * rng.normal(size=(N, 2))
+    V = []
+    for _ in range(N):
+        Y = rng.normal(size=(2, 2))
+        V.append(Y @ Y.T * 0.01 + 0.002 * np.eye(2))
+    V = np.array(V)
+    ps, Cs, chi2, st, pf, Cf = oracle.linear_chain(J, Q, p0, C0, m, V)
+    assert st == 0
+    means, covs, obj = _batch_posterior(J, L, p0, C0, m, V)
+    np.testing.assert_allclose(ps, means, rtol=0, atol=1e-11 * (1 + np.abs(means).max()))
+    np.testing.assert_allclose(Cs, covs, rtol=0, atol=1e-11 * np.abs(covs).max())
+    assert abs(chi2 - obj) <= 1e-10 * max(1.0, obj)
+    # the forward filter at k is the posterior given m_0..m_k
+    for k in (0, 3, N - 1):
+        mk, ck, _ = _batch_posterior(J, L, p0, C0, m, V, upto=k)
+        np.testing.assert_allclose(pf[k], mk[k], atol=1e-11)
+        np.testing.assert_allclose(Cf[k], ck[k], atol=1e-11 * np.abs(ck[k]).max())
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_update_chi2_predicted_equals_filtered_residual_form(seed):
+    rng = np.random.default_rng(100 + seed)
+    X = rng.normal(size=(5, 5))
+    C = X @ X.T + 0.1 * np.eye(5)
+    p = rng.normal(size=5)
+    Y = rng.normal(size=(2, 2))
+    V = Y @ Y.T * 0.1 + 0.01 * np.eye(2)
+    m = rng.normal(size=2)
+    p2, C2, chi2, st = oracle.update(m, V, p, C)
+    assert st == 0
+    rf = m - p2[:2]
+    R = V - C2[:2, :2]
+    chi2_f = rf @ np.linalg.solve(R, rf)
+    assert abs(chi2 - chi2_f) < 1e-10 * max(1.0, chi2)
+    # the posterior is the Gaussian product: C2^-1 = C^-1 + H^T V^-1 H
+    H = np.zeros((2, 5))
+    H[0, 0] = H[1, 1] = 1
+    np.testing.assert_allclose(np.linalg.inv(C2), np.linalg.inv(C) + H.T @ np.linalg.inv(V) @ H,
+                               rtol=1e-9, atol=1e-9)
+
+
+# ------------------------------------------------------------------ whole fit
+def test_noise_free_tracks_fit_back_to_truth(n_threads):
+    w = synth.barrel_workload(n_events=1, lo=500, hi=500, seed=21, mass=synth.MUON_MASS, ms=0,
+                              sigma_hit=0.0, seed_smear=0)
+    r = oracle.fit_tracks(w, oracle.Options(tol=1e-9), n_threads=n_threads)
+    assert np.all(r.status == 0)
+    d = r.par - w.tracks.truth
+    assert np.max(np.abs(d[:, :2])) < 1e-7      # mm
+    assert np.max(np.abs(d[:, 2:4])) < 1e-8     # rad
+    assert np.max(np.abs(d[:, 4] / w.tracks.truth[:, 4])) < 1e-7
+    assert np.max(r.chi2) < 1e-6
+
+
+def _pulls(w, r):
+    ok = r.status == 0
+    C = oracle.unpack(r.cov[ok])
+    sig = np.sqrt(np.einsum("nii->ni", C))
+    d = r.par[ok] - w.tracks.truth[ok]
+    d[:, 2] = (d[:, 2] + np.pi) % (2 * np.pi) - np.pi
+    return d / sig, r.chi2[ok] / r.ndf[ok], ok
+
+
+@pytest.mark.slow
+def test_pulls_unit_normal_and_chi2_on_solenoid_map_muons(n_threads):
+    scipy_stats = pytest.importorskip("scipy.stats")
+    w = synth.solenoid_muon_workload(100000, seed=3)
+    r = oracle.fit_tracks(w, n_threads=n_threads)
+    pull, c, ok = _pulls(w, r)
+    assert ok.mean() > 0.999
+    assert np.all(np.abs(pull.mean(0)) < 0.02)
+    assert np.all(np.abs(pull.std(0) - 1.0) < 0.01)
+    assert abs(c.mean() - 1.0) < 0.01
+    pv = scipy_stats.chi2.sf(r.chi2[ok], r.ndf[ok])
+    assert scipy_stats.kstest(pv, "uniform").statistic < 0.01
+
+
+def test_pulls_on_telescope_scattering_dominated(n_threads):
+    # p in 1-2 GeV: the Highland term dominates the angular resolution of 9 planes
+    w = synth.telescope_workload(20000, seed=5, pmin=1.0, pmax=2.0)
+    r = oracle.fit_tracks(w, n_threads=n_threads)
+    pull, c, ok = _pulls(w, r)
+    assert ok.all()
+    assert np.all(np.abs(pull.std(0) - 1.0) < 0.025)
+    assert abs(c.mean() - 1.0) < 0.02
+
+
+# ------------------------------------------------------------------ material
+def test_bethe_minimum_ionisation_silicon():
+    ref = json.load(open(os.path.join(GOLDEN, "pdg_silicon.json")))
+    plane = synth.telescope_geometry().table[0]
+    opts = oracle.Options()
+    ps = np.geomspace(0.15, 3.0, 400)
+    dedx = np.array([oracle.material(plane, opts, [0, 0, 0, np.pi / 2, 1.0 / p])[2] for p in ps])
+    k = int(np.argmin(dedx))
+    bg = ps[k] / oracle.MUON_MASS
+    assert 2.5 < bg < 4.5
+    assert abs(dedx[k] / ref["dEdx_min_MeV_cm2_g"] - 1.0) < 0.02
+
+
+def test_highland_scales_as_inverse_beta_p_and_energy_loss_lowers_momentum():
+    plane = synth.telescope_geometry().table[0]
+    opts = oracle.Options()
+    m = oracle.MUON_MASS
+    prev = None
+    for p in (0.5, 1.0, 3.0, 10.0, 50.0):
+        th0, qop, dedx, st = oracle.material(plane, opts, [0, 0, 0, np.pi / 2, 1.0 / p])
+        beta = p / np.hypot(p, m)
+        # theta0 * beta * p depends on p only through the small log(beta^2) term
+        val = th0 * beta * p
+        if prev is not None:
+            assert abs(val / prev - 1.0) < 0.02
+        prev = val
+        assert st == 0 and 1.0 / qop < p
+        # mean loss through 0.3 mm of Si is ~0.1 MeV for a minimum-ionising muon
+        assert 0.08e-3 < p - 1.0 / qop < 0.2e-3
+    # oblique incidence: x = t / |cos| raises theta0
+    th_n = oracle.material(plane, opts, [0, 0, 0, np.pi / 2, 1.0])[0]
+    th_o = oracle.material(plane, opts, [0, 0, 0.5, np.pi / 2, 1.0])[0]
+    assert th_o > th_n
+
+
+# ------------------------------------------------------------------ field
+def test_field_lookup_bilinear_is_exact_for_linear_maps():
+    nr, nz = 21, 31
+    r = np.arange(nr) * 5.0
+    z = -75.0 + np.arange(nz) * 5.0
+    Rg, Zg = np.meshgrid(r, z)
+    Br = (0.001 * Rg + 0.0005 * Zg).astype(np.float32)
+    Bz = (2.0 - 0.0002 * Rg + 0.0001 * Zg).astype(np.float32)
+    f = oracle.make_field(1, (0, 0, 0), nr, nz, 0.0, 5.0, -75.0, 5.0, Br, Bz)
+    rng = np.random.default_rng(0)
+    x = np.column_stack([rng.uniform(-60, 60, 200), rng.uniform(-60, 60, 200), rng.uniform(-70, 70, 200)])
+    B, oof = oracle.field_at(f, x)
+    rr = np.hypot(x[:, 0], x[:, 1])
+    inside = rr <= 100.0
+    br = 0.001 * rr + 0.0005 * x[:, 2]
+    np.testing.assert_allclose(B[inside, 0], (br * x[:, 0] / rr)[inside], rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(B[inside, 2], (2.0 - 0.0002 * rr + 0.0001 * x[:, 2])[inside], rtol=1e-6)
+    assert np.all(oof[~inside] == 1) and np.all(oof[inside] == 0)
+    assert np.all(B[~inside] == 0)
