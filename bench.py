@@ -1,0 +1,323 @@
+"""Benchmark: fitted tracks/s of the GB300 Kalman-filter fitter on the barrel + endcap batch.
+
+Workload (one "step" = one fit of the whole batch): 50 events of U{2000..20000} pions
+(pT log-uniform 0.5-100 GeV, eta U(+-3), vertex z ~ N(0, 50 mm)) in a 10-layer barrel +
+2 x 7-disk endcap silicon detector (0.3 mm modules), uniform 2 T along z, fitted under the
+muon hypothesis in one launch; about 6.1e5 tracks and 7.0e6 measurements (synthetic data
+standing in for the paper's ttbar events in the Open Data Detector). Inputs (~0.4 GB) are
+larger than L2, so no flush is needed between steps.
+
+Lines printed (rank 0): one JSON object. ``--impl reference`` times the CPU oracle instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "fitted tracks/s on 1 GB300: mixed+learned vs plain FP64, at fixed pull error"
+WORKLOAD = "barrel_endcap_50ev_uniform2T_pions"
+
+# FP64 work per unit of the fit kernel (flops: add/sub/mul = 1, fma = 2, div/sqrt = 1,
+# sin/cos/atan2/acos/log = 1; derivation in the design doc). Units: accepted RKN step,
+# rejected step attempt, propagated measurement (k >= 1), track.
+FLOP_STEP_ACCEPTED = 236
+FLOP_STEP_REJECTED = 44
+FLOP_HIT = 1046
+FLOP_TRACK = 260
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--variant", default="auto", choices=["auto", "fp64", "mixed"])
+    ap.add_argument("--events", type=int, default=50)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload(events: int, rank: int):
+    # weak scaling: every rank fits its own batch of the same shape (seed offset by rank)
+    return synth.barrel_workload(n_events=events, seed=2 + 1000 * rank)
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        except OSError:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def fp64_peak_tflops(sm_mhz: float | None):
+    """FP64 (CUDA-core) peak of GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA/clk/SM
+    (4 flop/clk/SM; 1.26 TFLOP/s at the 2070 MHz maximum clock)."""
+    mhz = sm_mhz or 2070.0
+    return 152 * 4 * mhz * 1e6 / 1e12
+
+
+def cpu_baseline(w, max_seconds: float = 20.0):
+    """The CPU oracle as it stands on this host's cores, on a bounded sample of the workload."""
+    import oracle
+    t = w.tracks
+    cores = os.cpu_count() or 1
+    n_try = 4000
+    rng = np.random.default_rng(0)
+    while True:
+        idx = np.sort(rng.choice(t.n_tracks, size=min(n_try, t.n_tracks), replace=False))
+        sub = t.subset(idx)
+        t0 = time.perf_counter()
+        oracle.fit_tracks(w, tracks=sub, n_threads=cores)
+        dt = time.perf_counter() - t0
+        if dt > 0.25 * max_seconds or n_try >= t.n_tracks:
+            break
+        n_try = int(min(t.n_tracks, n_try * max(2.0, 0.3 * max_seconds / max(dt, 1e-3))))
+    return {"value": len(idx) / dt, "unit": "tracks/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(idx)} tracks drawn uniformly from the {t.n_tracks}-track batch, "
+                      f"fit in {dt:.2f} s on {cores} threads"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle  # noqa: F401
+    w = make_workload(args.events, 0)
+    t = w.tracks
+    cores = os.cpu_count() or 1
+    # each step fits a bounded sample sized to keep the whole run within minutes
+    per_step = min(t.n_tracks, 20000)
+    rng = np.random.default_rng(1)
+    subs = [t.subset(np.sort(rng.choice(t.n_tracks, per_step, replace=False)))
+            for _ in range(min(args.steps, 4))]
+    import oracle as orc
+    for i in range(args.warmup):
+        orc.fit_tracks(w, tracks=subs[i % len(subs)], n_threads=cores)
+    times = []
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        orc.fit_tracks(w, tracks=subs[i % len(subs)], n_threads=cores)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = per_step * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "tracks/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "tracks_per_step": per_step,
+                                        "sample": "bounded sample of the batch per step",
+                                        "l2": "inputs on the host"},
+        "cpu_baseline": {"value": value, "unit": "tracks/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} tracks per step from the {t.n_tracks}-track batch"},
+        "e2e": {"value": value, "unit": "tracks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import torch
+    import paper_2505_22822_gb300 as tkf
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w = make_workload(args.events, rank)
+    t = w.tracks
+    n_tracks, n_meas = t.n_tracks, t.n_hits
+    ctx = tkf.Context(local)
+    geo = tkf.Geometry.from_table(ctx, w.geometry.table)
+    fld = tkf.Field.from_desc(ctx, w.field)
+    host = tkf.Batch.from_arrays(t.offsets, t.meas, t.sid, t.seed_par, t.seed_cov)
+    dev = host.to(f"cuda:{local}")
+    variant = "fp64" if args.variant == "auto" else args.variant
+    opts = tkf.Options(precision=tkf.MIXED if variant == "mixed" else tkf.FP64, mass=w.mass)
+    out = tkf.alloc_outputs(n_tracks, dev.offsets.device, steps=True)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        tkf.fit(ctx, geo, fld, dev, opts, out=out, stream=stream)
+    torch.cuda.synchronize()
+    # work counted from this batch's step counters (identical every step)
+    st = out.steps.cpu().numpy().astype(np.int64)
+    attempts, rejected = int(st[0].sum()), int(st[1].sum())
+    status = out.status.cpu().numpy().view(np.uint32)
+    hits_k1 = int((np.diff(t.offsets.astype(np.int64)) - 1).clip(min=0).sum())
+    flops = (FLOP_STEP_ACCEPTED * (attempts - rejected) + FLOP_STEP_REJECTED * rejected +
+             FLOP_HIT * hits_k1 + FLOP_TRACK * n_tracks)
+
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            tkf.fit(ctx, geo, fld, dev, opts, out=out, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms_max = ms
+    if dist is not None:
+        tt = torch.tensor([ms], device=f"cuda:{local}")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_max = float(tt.item())
+    clocks = clk.summary()
+
+    # end to end through the host entry point: pinned host inputs -> fit -> host outputs
+    e2e = None
+    if not args.no_e2e:
+        pinned = host.to("cpu", pin=True)
+        hout = tkf.Result(torch.empty((5, n_tracks), dtype=torch.float64).pin_memory(),
+                          torch.empty((15, n_tracks), dtype=torch.float64).pin_memory(),
+                          torch.empty(n_tracks, dtype=torch.float64).pin_memory(),
+                          torch.empty(n_tracks, dtype=torch.int32).pin_memory(),
+                          torch.empty(n_tracks, dtype=torch.int32).pin_memory(), None)
+        for _ in range(max(1, args.warmup)):
+            tkf.fit_host(ctx, geo, fld, pinned, opts, out=hout, stream=stream)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            tkf.fit_host(ctx, geo, fld, pinned, opts, out=hout, stream=stream)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        if dist is not None:
+            tt = torch.tensor([e2e_s], device=f"cuda:{local}")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        h2d = host.nbytes()
+        d2h = n_tracks * (5 * 8 + 15 * 8 + 8 + 4 + 4)
+        e2e = {"value": ws * n_tracks / e2e_s, "unit": "tracks/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peak = fp64_peak_tflops(None)
+    achieved = flops / (ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC,
+        "value": ws * n_tracks / (ms_max * 1e-3),
+        "unit": "tracks/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_max,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if variant == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "variant": variant, "tracks_per_gpu": n_tracks,
+                   "measurements_per_gpu": n_meas, "events_per_gpu": args.events,
+                   "field": "uniform 2 T along z", "l2": "inputs 0.41 GB > L2, no flush",
+                   "fit_status_ok": float(np.mean(status == 0))},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "note": "FP64 CUDA-core pipe; peak derived from 152 SMs x 4 flop/clk x 2070 MHz"},
+        "clocks": clocks,
+        "work": {"step_attempts": attempts, "rejected": rejected, "hits_propagated": hits_k1,
+                 "fp64_flop_per_launch": flops},
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

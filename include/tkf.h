@@ -1,0 +1,221 @@
+/*
+ * tkf.h -- C interface of the batched Kalman-filter track fitter for NVIDIA GB300 (sm_103a).
+ *
+ * The library fits track candidates as the paper describes its fitting stage (Sec. 2,
+ * "Implementation", second paragraph): each track's parameters and covariance are
+ * propagated between detector surfaces with the 4th-order Runge-Kutta-Nystrom method and
+ * Jacobian transport, the Kalman filter adds each measurement with a chi2 from the
+ * covariance-weighted spatial residual, and the Rauch-Tung-Striebel smoother makes the
+ * parameters at the first measurement use every measurement. Material effects assume a
+ * muon (Sec. 3, first paragraph). Geometry and field are uploaded once; per batch, only
+ * measurements and seeds go in and fitted parameters come out (Sec. 2, third paragraph).
+ *
+ * Conventions
+ *   Units: mm, GeV, tesla, radians; q/p in e/GeV.
+ *   Bound parameters on a surface: (l0, l1, phi, theta, q/p), where (l0, l1) are the
+ *   coordinates of the intersection along the surface's local axes u and v, and the unit
+ *   direction is (sin(theta) cos(phi), sin(theta) sin(phi), cos(theta)); phi in (-pi, pi].
+ *   Covariances are stored as the 15-element upper triangle in row-major order:
+ *   (00, 01, 02, 03, 04, 11, 12, 13, 14, 22, 23, 24, 33, 34, 44).
+ *   Device arrays are structure-of-arrays: component j of track i is at [j * n_tracks + i].
+ *
+ * Errors
+ *   Every entry point returns a tkf_status. An argument error returns a nonzero code and
+ *   enqueues nothing; tkf_last_error() then describes it. Numerical failures of single
+ *   tracks never fail a call: they are reported in that track's status word.
+ *
+ * Threading
+ *   A context is used by one host thread at a time. Handles are freed by the matching
+ *   *_destroy call, after all work that uses them has completed.
+ */
+#ifndef TKF_H_
+#define TKF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum tkf_status {
+  TKF_OK = 0,
+  TKF_ERR_INVALID_ARG = 1, /* null pointer, bad size, bad option, bad layout */
+  TKF_ERR_BAD_HANDLE = 2,  /* handle null or from another context/device */
+  TKF_ERR_DEVICE = 3,      /* no usable CUDA device, or a CUDA call failed */
+  TKF_ERR_OOM = 4,         /* device or host allocation failed */
+  TKF_ERR_UNSUPPORTED = 5  /* valid request this build cannot serve */
+} tkf_status;
+
+/* Per-track status bits written to tkf_fit_outputs.status. A track with any bit other than
+ * TKF_TRACK_TOO_FEW_HITS or TKF_TRACK_OUT_OF_FIELD set has NaN parameters, covariance and
+ * chi2. */
+#define TKF_TRACK_MAX_STEPS (1u << 0)        /* more than max_steps step attempts to one surface */
+#define TKF_TRACK_SURFACE_MISSED (1u << 1)   /* next surface more than 1 mm behind, or parallel */
+#define TKF_TRACK_PARTICLE_STOPPED (1u << 2) /* mean energy loss left E <= mass */
+#define TKF_TRACK_UPDATE_NOT_SPD (1u << 3)   /* residual covariance S not positive definite */
+#define TKF_TRACK_SMOOTHER_NOT_SPD (1u << 4) /* smoothed covariance not positive definite */
+#define TKF_TRACK_TOO_FEW_HITS (1u << 5)     /* fewer than 3 measurements (ndf < 6) */
+#define TKF_TRACK_OUT_OF_FIELD (1u << 6)     /* a field sample fell outside the map (B = 0 used) */
+#define TKF_TRACK_BAD_INPUT (1u << 7)        /* surface id out of range, or offsets decreasing */
+#define TKF_TRACK_STEP_UNDERFLOW (1u << 8)   /* step size control fell below h_min */
+#define TKF_TRACK_NON_FINITE (1u << 9)       /* NaN/Inf in the seed or the result, theta left (0, pi) */
+
+typedef struct tkf_context_s* tkf_context;
+typedef struct tkf_geometry_s* tkf_geometry;
+typedef struct tkf_field_s* tkf_field;
+typedef struct tkf_mlp_s* tkf_mlp;
+
+/* ---------------------------------------------------------------------------- context */
+
+/* Creates a context on CUDA device `device` (the caller's current device if < 0). The
+ * context owns a small device workspace (grown on demand, reused) and its launch settings.
+ * Errors: TKF_ERR_INVALID_ARG (out == NULL), TKF_ERR_DEVICE (no such device),
+ * TKF_ERR_UNSUPPORTED (device is not compute capability 10.3). */
+tkf_status tkf_context_create(int device, tkf_context* out);
+void tkf_context_destroy(tkf_context ctx);
+
+/* Text of the last error on this context (valid until the next call on it). A NULL
+ * context returns the last error of a create call. */
+const char* tkf_last_error(tkf_context ctx);
+
+/* ---------------------------------------------------------------------------- geometry */
+
+/* One planar detector surface (paper Sec. 2: tracking geometry resident on the device). */
+typedef struct tkf_surface_desc {
+  double rot[9];     /* row-major 3x3 rotation; its columns are u, v and n = u x v (global frame) */
+  double center[3];  /* origin of the local frame, mm */
+  double thickness;  /* mm; 0 disables material effects on this surface */
+  double x0;         /* radiation length of its material, mm */
+} tkf_surface_desc;
+
+/* Material constants of every surface (Bethe mean energy loss). */
+typedef struct tkf_material {
+  double z_over_a;        /* Z/A */
+  double i_ev;            /* mean excitation energy, eV */
+  double rho_g_cm3;       /* density, g/cm^3 */
+  double hbar_omega_p_ev; /* plasma energy, eV (density-effect term) */
+} tkf_material;
+
+/* Silicon: Z/A 0.49848, I 173 eV, rho 2.329 g/cm^3, plasma energy 31.05 eV (PDG). */
+void tkf_material_silicon(tkf_material* m);
+
+/* Copies `n` host surface descriptions to device memory owned by the new handle (uploaded
+ * once, paper Sec. 2). `material` may be NULL (silicon). The copy is synchronous.
+ * Errors: TKF_ERR_INVALID_ARG (NULL pointers, n == 0, a rotation that is not orthonormal
+ * to 1e-9, thickness < 0, x0 <= 0), TKF_ERR_OOM, TKF_ERR_DEVICE. */
+tkf_status tkf_geometry_create(tkf_context ctx, const tkf_surface_desc* surfaces, uint32_t n,
+                               const tkf_material* material, tkf_geometry* out);
+void tkf_geometry_destroy(tkf_geometry geo);
+
+/* ---------------------------------------------------------------------------- field */
+
+typedef enum tkf_field_kind {
+  TKF_FIELD_UNIFORM = 0, /* constant b_tesla */
+  TKF_FIELD_RZ_GRID = 1  /* axially symmetric map: B_r, B_z on an (r, z) grid */
+} tkf_field_kind;
+
+/* Magnetic field (paper Sec. 3: a 2 T solenoid along z). For TKF_FIELD_RZ_GRID the nodes
+ * are r = r0 + i dr (i < nr) and z = z0 + j dz (j < nz); br and bz are host arrays of
+ * nz * nr floats, row-major [j][i], in tesla. The field at a point is the bilinear
+ * interpolation in (r, z), with B_x = B_r x / r, B_y = B_r y / r (0 on the axis); outside
+ * the grid it is 0 and the track is flagged TKF_TRACK_OUT_OF_FIELD. */
+typedef struct tkf_field_desc {
+  int kind;           /* tkf_field_kind */
+  double b_tesla[3];  /* TKF_FIELD_UNIFORM */
+  uint32_t nr, nz;    /* TKF_FIELD_RZ_GRID: >= 2 each */
+  double r0, dr, z0, dz;
+  const float* br;
+  const float* bz;
+} tkf_field_desc;
+
+/* Copies the field to device memory owned by the new handle (synchronous).
+ * Errors: TKF_ERR_INVALID_ARG (NULL, unknown kind, nr or nz < 2, dr or dz <= 0, r0 < 0,
+ * NULL grid arrays), TKF_ERR_OOM, TKF_ERR_DEVICE. */
+tkf_status tkf_field_create(tkf_context ctx, const tkf_field_desc* desc, tkf_field* out);
+void tkf_field_destroy(tkf_field field);
+
+/* ---------------------------------------------------------------------------- fit */
+
+typedef enum tkf_precision {
+  TKF_FP64 = 0,  /* every step in FP64 */
+  TKF_MIXED = 1  /* propagation and transport in FP32 around FP64 anchors; update and
+                    smoother in FP64 */
+} tkf_precision;
+
+typedef enum tkf_step_mode {
+  TKF_STEP_ADAPTIVE = 0, /* RKN step-size control from the local error estimate */
+  TKF_STEP_LEARNED = 1   /* a small MLP proposes each step; the error estimate still judges */
+} tkf_step_mode;
+
+typedef struct tkf_fit_options {
+  int precision;       /* tkf_precision */
+  int step_mode;       /* tkf_step_mode */
+  double tol;          /* RKN local error tolerance, mm (default 1e-4) */
+  double h_max;        /* largest step, mm (default 1000) */
+  double h_min;        /* smallest step-size control value, mm (default 1e-4) */
+  double surf_tol;     /* propagation stops within this distance of the target plane, mm (1e-9) */
+  uint32_t max_steps;  /* step attempts per surface (default 10000) */
+  double mass;         /* particle hypothesis, GeV (default: muon, 0.1056583755) */
+  tkf_mlp mlp;         /* step proposer for TKF_STEP_LEARNED, else NULL */
+} tkf_fit_options;
+
+void tkf_fit_options_default(tkf_fit_options* opts);
+
+/* Inputs of one batch, all DEVICE pointers owned by the caller (read only).
+ * Track i has the measurements offsets[i] .. offsets[i+1]-1, ordered along the track.
+ * Measurement m: local position (loc0[m], loc1[m]) on surface sid[m] and its covariance
+ * [[v00, v01], [v01, v11]] (mm^2). The seed of track i is given on the surface of its
+ * first measurement: seed_par (5 x n_tracks) and seed_cov (15 x n_tracks, packed). */
+typedef struct tkf_fit_inputs {
+  uint32_t n_tracks;
+  uint64_t n_meas;
+  const uint32_t* offsets; /* n_tracks + 1 */
+  const double* loc0;
+  const double* loc1;
+  const double* v00;
+  const double* v01;
+  const double* v11;
+  const uint32_t* sid;
+  const double* seed_par;
+  const double* seed_cov;
+} tkf_fit_inputs;
+
+/* Outputs, DEVICE pointers owned by the caller (written). par (5 x n) and cov (15 x n) are
+ * the smoothed parameters and covariance on the surface of the first measurement; chi2 is
+ * the sum over measurements of the predicted-residual chi2, the first one taken against the
+ * seed; ndf = 2 * (number of measurements) (the seed enters as a prior). steps, if not NULL,
+ * receives 2 x n counters: step attempts [0, n) and rejected attempts [n, 2n). */
+typedef struct tkf_fit_outputs {
+  double* par;
+  double* cov;
+  double* chi2;
+  int32_t* ndf;
+  uint32_t* status;
+  uint32_t* steps;
+} tkf_fit_outputs;
+
+/* Fits every track of the batch, asynchronously on `stream` (a cudaStream_t; NULL is the
+ * legacy default stream). Nothing is copied between host and device. Device pointers must
+ * be 8-byte aligned and stay valid until the stream reaches this work.
+ * Errors (nothing enqueued): TKF_ERR_INVALID_ARG (NULL required pointers, n_meas too large
+ * for 32-bit offsets, bad options, misaligned pointers), TKF_ERR_BAD_HANDLE,
+ * TKF_ERR_UNSUPPORTED (TKF_STEP_LEARNED without an mlp), TKF_ERR_DEVICE (launch failure).
+ * Offsets are read on the device: a decreasing pair flags TKF_TRACK_BAD_INPUT. */
+tkf_status tkf_fit(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf_fit_options* opts,
+                   const tkf_fit_inputs* in, const tkf_fit_outputs* out, void* stream);
+
+/* The same fit from HOST arrays: copies the inputs to a device staging area owned by the
+ * context (grown on demand), fits, and copies the outputs back, all enqueued on `stream`;
+ * the call synchronizes the stream before returning. Page-locked host memory gives
+ * asynchronous copies. Pointers as in tkf_fit_inputs / tkf_fit_outputs but in host
+ * memory. Errors as tkf_fit, plus TKF_ERR_OOM. */
+tkf_status tkf_fit_host(tkf_context ctx, tkf_geometry geo, tkf_field field,
+                        const tkf_fit_options* opts, const tkf_fit_inputs* host_in,
+                        const tkf_fit_outputs* host_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TKF_H_ */

@@ -82,8 +82,9 @@ def lib():
         L = ctypes.CDLL(_SO)
         vp, d, u32 = ctypes.c_void_p, ctypes.c_double, ctypes.c_uint32
         L.orc_fit.restype = ctypes.c_int
-        L.orc_fit.argtypes = [vp, u32, ctypes.POINTER(OField), ctypes.POINTER(OOpts), u32, vp, vp, vp,
-                              vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int]
+        L.orc_fit.argtypes = [vp, u32, ctypes.POINTER(OField), ctypes.POINTER(OOpts), u32, ctypes.c_uint64,
+                              vp, vp, vp,
+                              vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int]
         L.orc_field_at.argtypes = [ctypes.POINTER(OField), vp, u32, vp, vp]
         L.orc_rkn_fixed.argtypes = [ctypes.POINTER(OField), vp, vp, d, d, u32, vp, vp, vp]
         L.orc_rkn_step.argtypes = [ctypes.POINTER(OField), vp, vp, d, d, vp, vp, vp]
@@ -147,6 +148,7 @@ class FitResult:
     ndf: np.ndarray
     status: np.ndarray
     steps: np.ndarray
+    cov_filt0: np.ndarray
 
 
 def fit(surfaces: np.ndarray, fld: OField, opts: Options, offsets, meas, sid, seed_par, seed_cov,
@@ -162,11 +164,12 @@ def fit(surfaces: np.ndarray, fld: OField, opts: Options, offsets, meas, sid, se
     par, cov = np.zeros((n, 5)), np.zeros((n, 15))
     chi2, ndf = np.zeros(n), np.zeros(n, np.int32)
     status, steps = np.zeros(n, np.uint32), np.zeros((n, 2), np.uint32)
+    cf0 = np.zeros((n, 15))
     o = opts._c()
-    L.orc_fit(_p(s), s.shape[0], ctypes.byref(fld), ctypes.byref(o), n, _p(offsets), _p(meas),
+    L.orc_fit(_p(s), s.shape[0], ctypes.byref(fld), ctypes.byref(o), n, meas.shape[0], _p(offsets), _p(meas),
               _p(sid), _p(seed_par), _p(seed_cov), _p(par), _p(cov), _p(chi2), _p(ndf), _p(status),
-              _p(steps), int(n_threads))
-    return FitResult(par, cov, chi2, ndf, status, steps)
+              _p(steps), _p(cf0), int(n_threads))
+    return FitResult(par, cov, chi2, ndf, status, steps, cf0)
 
 
 def fit_tracks(workload, opts: Options | None = None, n_threads: int = 1, tracks=None) -> FitResult:

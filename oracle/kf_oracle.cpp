@@ -303,7 +303,7 @@ void rkn_step(const Field& f, const double r[3], const double T[3], double lam, 
 // else h_ctrl with the sign of s_l. A step with eps > tol is rejected and h_ctrl becomes
 // |h| * max(1/4, (tol/eps)^(1/4)); an accepted step that was limited by h_ctrl sets
 // h_ctrl = min(h_max, h_ctrl * min(4, (tol/eps)^(1/4))). Propagation stops when
-// |n.(r - c)| <= surf_tol. Reading: a plane more than 1 mm behind the start point (first
+// |n.(r - c)| <= surf_tol, closing the rest with a straight step. Reading: a plane more than 1 mm behind the start point (first
 // straight-line path s_l < -1 mm, or not finite) is a miss; overlapping modules can be crossed
 // within a fraction of a millimetre, and the update may then leave the next plane just behind.
 struct PropState {
@@ -329,7 +329,13 @@ uint32_t propagate(const Field& f, const Opts& o, const Surface& s, double r[3],
   for (;;) {
     double diff[3] = {s.c[0] - r[0], s.c[1] - r[1], s.c[2] - r[2]};
     double dist = dot3(s.n, diff);
-    if (std::fabs(dist) <= o.surf_tol) break;
+    if (std::fabs(dist) <= o.surf_tol) {
+      // Reading: the remaining distance (at most surf_tol) is closed by a straight step along
+      // T, so that the end point lies on the plane whichever side of surf_tol it stopped.
+      double sl = dist / dot3(s.n, T);
+      for (int i = 0; i < 3; ++i) r[i] += sl * T[i];
+      break;
+    }
     double sl = dist / dot3(s.n, T);
     if (first && !(sl > -1.0 && std::isfinite(sl))) return status | kSurfaceMissed;
     first = false;
@@ -592,6 +598,7 @@ struct TrackIn {
 
 struct TrackOut {
   double par[5], cov[15], chi2;
+  double cov_filt0[15];  // filtered covariance at the first surface
   int32_t ndf;
   uint32_t status;
   uint32_t attempts, rejected;
@@ -620,6 +627,7 @@ void fit_track(const Surface* surf, uint32_t n_surf, const Field& f, const Opts&
   out.status = 0;
   out.attempts = out.rejected = 0;
   out.ndf = 2 * N;
+  for (int i = 0; i < 15; ++i) out.cov_filt0[i] = std::nan("");
   if (N == 0) {
     std::memcpy(out.par, in.seed_par, sizeof(double) * 5);
     std::memcpy(out.cov, in.seed_cov, sizeof(double) * 15);
@@ -679,6 +687,7 @@ void fit_track(const Surface* surf, uint32_t n_surf, const Field& f, const Opts&
     status |= kf_update(m, V, &pf[k * 5], &Cf[k * 25], &c2);
     if (status & kFatal) break;
     chi2 += c2;
+    if (k == 0) pack_cov(&Cf[0], out.cov_filt0);
     pf[k * 5 + 2] = wrap_phi(pf[k * 5 + 2]);
     if (!(pf[k * 5 + 3] > 0.0 && pf[k * 5 + 3] < kPi)) {
       status |= kNonFinite;
@@ -763,11 +772,12 @@ static std::vector<Surface> to_surfaces(const double* s, uint32_t n) {
 
 // Fit n_tracks tracks. meas: [n_meas][5] (loc0, loc1, V00, V01, V11); seed_par [n][5];
 // seed_cov [n][15] packed upper triangle; outputs in the same AoS layouts.
-// steps (nullable): [n][2] = step attempts, rejected attempts. n_threads >= 1.
+// steps (nullable): [n][2] = step attempts, rejected attempts. cov_filt0 (nullable): [n][15]
+// filtered covariance at the first surface. n_threads >= 1.
 int orc_fit(const double* surfaces, uint32_t n_surf, const orc_field* field, const orc_opts* opts,
-            uint32_t n_tracks, const uint32_t* offsets, const double* meas, const uint32_t* sid,
+            uint32_t n_tracks, uint64_t n_meas, const uint32_t* offsets, const double* meas, const uint32_t* sid,
             const double* seed_par, const double* seed_cov, double* out_par, double* out_cov, double* chi2,
-            int32_t* ndf, uint32_t* status, uint32_t* steps, int n_threads) {
+            int32_t* ndf, uint32_t* status, uint32_t* steps, double* cov_filt0, int n_threads) {
   std::vector<Surface> surf = to_surfaces(surfaces, n_surf);
   Field F = to_field(field);
   Opts O = to_opts(opts);
@@ -776,10 +786,11 @@ int orc_fit(const double* surfaces, uint32_t n_surf, const orc_field* field, con
       TrackIn in;
       uint32_t a = offsets[i], b = offsets[i + 1];
       TrackOut out;
-      if (b < a) {
+      if (b < a || b > n_meas) {
         fill_nan(out);
+        for (int j = 0; j < 15; ++j) out.cov_filt0[j] = std::nan("");
         out.status = kBadInput;
-        out.ndf = -5;
+        out.ndf = 0;
         out.attempts = out.rejected = 0;
       } else {
         in.N = b - a;
@@ -798,6 +809,7 @@ int orc_fit(const double* surfaces, uint32_t n_surf, const orc_field* field, con
         steps[2 * size_t(i)] = out.attempts;
         steps[2 * size_t(i) + 1] = out.rejected;
       }
+      if (cov_filt0) std::memcpy(cov_filt0 + 15 * size_t(i), out.cov_filt0, sizeof(double) * 15);
     }
   };
   if (n_threads <= 1 || n_tracks < 2) {

@@ -1,0 +1,429 @@
+"""Python binding of libtkf.so, the GB300 (sm_103a) batched Kalman-filter track fitter.
+
+Argument marshalling only: every step of the fit runs in the CUDA kernels behind the C
+interface declared in include/tkf.h. PyTorch provides device memory and streams. There is
+no CPU fallback: without the compiled library or a GB300 device the calls raise.
+
+    import paper_2505_22822_gb300 as tkf
+    ctx = tkf.Context(0)
+    geo = tkf.Geometry(ctx, rot, center, thickness, x0)
+    fld = tkf.Field.uniform(ctx, (0, 0, 2.0))
+    out = tkf.fit(ctx, geo, fld, batch)      # batch: tkf.Batch of CUDA tensors
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_HERE)
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libtkf.so")
+_SOURCES = ["tkf_api.cu", "tkf_fit.cu"]
+_lib = None
+
+NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
+              "-Xcompiler", "-fPIC"]
+
+FP64, MIXED = 0, 1
+STEP_ADAPTIVE, STEP_LEARNED = 0, 1
+FIELD_UNIFORM, FIELD_RZ_GRID = 0, 1
+
+TRACK_STATUS = {
+    "MAX_STEPS": 1 << 0, "SURFACE_MISSED": 1 << 1, "PARTICLE_STOPPED": 1 << 2,
+    "UPDATE_NOT_SPD": 1 << 3, "SMOOTHER_NOT_SPD": 1 << 4, "TOO_FEW_HITS": 1 << 5,
+    "OUT_OF_FIELD": 1 << 6, "BAD_INPUT": 1 << 7, "STEP_UNDERFLOW": 1 << 8, "NON_FINITE": 1 << 9,
+}
+FATAL_MASK = ~(TRACK_STATUS["TOO_FEW_HITS"] | TRACK_STATUS["OUT_OF_FIELD"]) & 0xFFFFFFFF
+
+
+class TkfError(RuntimeError):
+    pass
+
+
+def _nvcc() -> str:
+    for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if c and (os.path.isabs(c) and os.path.exists(c) or not os.path.isabs(c)):
+            return c
+    return "nvcc"
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compiles libtkf.so in-tree for sm_103a (translation units in parallel, then linked)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    csrc = os.path.join(_HERE, "csrc")
+    inc = os.path.join(_ROOT, "include")
+    deps = [os.path.join(csrc, f) for f in os.listdir(csrc)] + [os.path.join(inc, "tkf.h")]
+    newest = max(os.path.getmtime(d) for d in deps)
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= newest:
+        return _SO
+    nvcc = _nvcc()
+    procs, objs = [], []
+    for src in _SOURCES:
+        obj = os.path.join(_BUILD, src.replace(".cu", ".o"))
+        objs.append(obj)
+        cmd = [nvcc, *NVCC_FLAGS, "-I", inc, "-c", os.path.join(csrc, src), "-o", obj]
+        if verbose:
+            cmd += ["-Xptxas", "-v"]
+        procs.append(subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT))
+    for p, src in zip(procs, _SOURCES):
+        out, _ = p.communicate()
+        if p.returncode != 0:
+            raise TkfError(f"nvcc failed on {src}:\n{out.decode()}")
+        if verbose:
+            print(out.decode())
+    tmp = _SO + ".tmp"
+    subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared",
+                           "-cudart", "shared", "-o", tmp, *objs])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+# ---------------------------------------------------------------------------- C structs
+class SurfaceDesc(ctypes.Structure):
+    _fields_ = [("rot", ctypes.c_double * 9), ("center", ctypes.c_double * 3),
+                ("thickness", ctypes.c_double), ("x0", ctypes.c_double)]
+
+
+class Material(ctypes.Structure):
+    _fields_ = [("z_over_a", ctypes.c_double), ("i_ev", ctypes.c_double),
+                ("rho_g_cm3", ctypes.c_double), ("hbar_omega_p_ev", ctypes.c_double)]
+
+
+class FieldDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("b_tesla", ctypes.c_double * 3), ("nr", ctypes.c_uint32),
+                ("nz", ctypes.c_uint32), ("r0", ctypes.c_double), ("dr", ctypes.c_double),
+                ("z0", ctypes.c_double), ("dz", ctypes.c_double), ("br", ctypes.c_void_p),
+                ("bz", ctypes.c_void_p)]
+
+
+class FitOptions(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("step_mode", ctypes.c_int), ("tol", ctypes.c_double),
+                ("h_max", ctypes.c_double), ("h_min", ctypes.c_double),
+                ("surf_tol", ctypes.c_double), ("max_steps", ctypes.c_uint32),
+                ("mass", ctypes.c_double), ("mlp", ctypes.c_void_p)]
+
+
+class FitInputs(ctypes.Structure):
+    _fields_ = [("n_tracks", ctypes.c_uint32), ("n_meas", ctypes.c_uint64),
+                ("offsets", ctypes.c_void_p), ("loc0", ctypes.c_void_p), ("loc1", ctypes.c_void_p),
+                ("v00", ctypes.c_void_p), ("v01", ctypes.c_void_p), ("v11", ctypes.c_void_p),
+                ("sid", ctypes.c_void_p), ("seed_par", ctypes.c_void_p),
+                ("seed_cov", ctypes.c_void_p)]
+
+
+class FitOutputs(ctypes.Structure):
+    _fields_ = [("par", ctypes.c_void_p), ("cov", ctypes.c_void_p), ("chi2", ctypes.c_void_p),
+                ("ndf", ctypes.c_void_p), ("status", ctypes.c_void_p), ("steps", ctypes.c_void_p)]
+
+
+# C entry points and their signatures (argument types), as declared in include/tkf.h.
+_VP = ctypes.c_void_p
+_SIGNATURES = {
+    "tkf_context_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_VP)]),
+    "tkf_context_destroy": (None, [_VP]),
+    "tkf_last_error": (ctypes.c_char_p, [_VP]),
+    "tkf_material_silicon": (None, [ctypes.POINTER(Material)]),
+    "tkf_geometry_create": (ctypes.c_int, [_VP, ctypes.POINTER(SurfaceDesc), ctypes.c_uint32,
+                                           ctypes.POINTER(Material), ctypes.POINTER(_VP)]),
+    "tkf_geometry_destroy": (None, [_VP]),
+    "tkf_field_create": (ctypes.c_int, [_VP, ctypes.POINTER(FieldDesc), ctypes.POINTER(_VP)]),
+    "tkf_field_destroy": (None, [_VP]),
+    "tkf_fit_options_default": (None, [ctypes.POINTER(FitOptions)]),
+    "tkf_fit": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(FitOptions), ctypes.POINTER(FitInputs),
+                               ctypes.POINTER(FitOutputs), _VP]),
+    "tkf_fit_host": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(FitOptions),
+                                    ctypes.POINTER(FitInputs), ctypes.POINTER(FitOutputs), _VP]),
+}
+
+
+def lib(build_if_missing: bool = True):
+    """Loads libtkf.so (building it first if needed); raises if it cannot be loaded."""
+    global _lib
+    if _lib is None:
+        if build_if_missing:
+            build()
+        if not os.path.exists(_SO):
+            raise TkfError(f"{_SO} is missing: run paper_2505_22822_gb300.build()")
+        L = ctypes.CDLL(_SO)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code: int, ctx_handle=None, what: str = ""):
+    if code != 0:
+        msg = lib().tkf_last_error(ctx_handle)
+        raise TkfError(f"{what} failed with status {code}: {msg.decode() if msg else ''}")
+
+
+# ---------------------------------------------------------------------------- handles
+class Context:
+    def __init__(self, device: int = 0):
+        h = _VP()
+        _check(lib().tkf_context_create(device, ctypes.byref(h)), None, "tkf_context_create")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().tkf_context_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Geometry:
+    """Planar surfaces: ``rot`` [n, 9] row-major (columns u, v, n), ``center`` [n, 3] mm,
+    ``thickness`` [n] mm, ``x0`` [n] mm; ``material`` (Z/A, I eV, rho g/cm3, plasma eV)."""
+
+    def __init__(self, ctx: Context, rot, center, thickness, x0, material=None):
+        rot = np.ascontiguousarray(rot, dtype=np.float64).reshape(-1, 9)
+        n = rot.shape[0]
+        center = np.ascontiguousarray(center, dtype=np.float64).reshape(n, 3)
+        thickness = np.broadcast_to(np.asarray(thickness, dtype=np.float64), (n,))
+        x0 = np.broadcast_to(np.asarray(x0, dtype=np.float64), (n,))
+        arr = (SurfaceDesc * n)()
+        buf = np.frombuffer(arr, dtype=np.float64).reshape(n, 14)
+        buf[:, 0:9] = rot
+        buf[:, 9:12] = center
+        buf[:, 12] = thickness
+        buf[:, 13] = x0
+        mat = None
+        if material is not None:
+            mat = Material(*[float(v) for v in material])
+        h = _VP()
+        _check(lib().tkf_geometry_create(ctx.handle, arr, n, ctypes.byref(mat) if mat else None,
+                                         ctypes.byref(h)), ctx.handle, "tkf_geometry_create")
+        self.handle, self.ctx, self.n = h, ctx, n
+
+    @classmethod
+    def from_table(cls, ctx: Context, table: np.ndarray, material=None) -> "Geometry":
+        """From a [n, >=14] table u[3] v[3] n[3] c[3] thickness x0."""
+        t = np.asarray(table, dtype=np.float64)
+        R = np.stack([t[:, 0:3], t[:, 3:6], t[:, 6:9]], axis=2).reshape(-1, 9)
+        return cls(ctx, R, t[:, 9:12], t[:, 12], t[:, 13], material)
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None):
+                lib().tkf_geometry_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+class Field:
+    def __init__(self, ctx: Context, desc: FieldDesc, keep=()):
+        h = _VP()
+        _check(lib().tkf_field_create(ctx.handle, ctypes.byref(desc), ctypes.byref(h)), ctx.handle,
+               "tkf_field_create")
+        self.handle, self.ctx, self.kind = h, ctx, desc.kind
+
+    @classmethod
+    def uniform(cls, ctx: Context, b_tesla=(0.0, 0.0, 2.0)) -> "Field":
+        d = FieldDesc()
+        d.kind = FIELD_UNIFORM
+        for i in range(3):
+            d.b_tesla[i] = float(b_tesla[i])
+        return cls(ctx, d)
+
+    @classmethod
+    def rz_grid(cls, ctx: Context, br, bz, r0, dr, z0, dz) -> "Field":
+        br = np.ascontiguousarray(br, dtype=np.float32)
+        bz = np.ascontiguousarray(bz, dtype=np.float32)
+        d = FieldDesc()
+        d.kind = FIELD_RZ_GRID
+        d.nz, d.nr = br.shape
+        d.r0, d.dr, d.z0, d.dz = r0, dr, z0, dz
+        d.br = br.ctypes.data_as(_VP)
+        d.bz = bz.ctypes.data_as(_VP)
+        return cls(ctx, d, keep=(br, bz))
+
+    @classmethod
+    def from_desc(cls, ctx: Context, f) -> "Field":
+        """From an object with kind, B, nr, nz, r0, dr, z0, dz, Br, Bz attributes."""
+        if f.kind == FIELD_UNIFORM:
+            return cls.uniform(ctx, f.B)
+        return cls.rz_grid(ctx, f.Br, f.Bz, f.r0, f.dr, f.z0, f.dz)
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None):
+                lib().tkf_field_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+@dataclass
+class Options:
+    precision: int = FP64
+    step_mode: int = STEP_ADAPTIVE
+    tol: float = 1e-4
+    h_max: float = 1000.0
+    h_min: float = 1e-4
+    surf_tol: float = 1e-9
+    max_steps: int = 10000
+    mass: float = 0.1056583755
+
+    def c(self) -> FitOptions:
+        o = FitOptions()
+        lib().tkf_fit_options_default(ctypes.byref(o))
+        o.precision, o.step_mode = self.precision, self.step_mode
+        o.tol, o.h_max, o.h_min, o.surf_tol = self.tol, self.h_max, self.h_min, self.surf_tol
+        o.max_steps, o.mass = self.max_steps, self.mass
+        return o
+
+
+# ---------------------------------------------------------------------------- batches
+_IN_FIELDS = ("offsets", "loc0", "loc1", "v00", "v01", "v11", "sid", "seed_par", "seed_cov")
+
+
+@dataclass
+class Batch:
+    """Fit inputs in the library's layout: offsets [n+1] u32, loc0/loc1/v00/v01/v11 [m] f64,
+    sid [m] u32, seed_par [5, n] f64, seed_cov [15, n] f64 (numpy on the host, or torch)."""
+    offsets: object
+    loc0: object
+    loc1: object
+    v00: object
+    v01: object
+    v11: object
+    sid: object
+    seed_par: object
+    seed_cov: object
+
+    @property
+    def n_tracks(self) -> int:
+        return int(self.offsets.shape[0]) - 1
+
+    @property
+    def n_meas(self) -> int:
+        return int(self.loc0.shape[0])
+
+    @classmethod
+    def from_arrays(cls, offsets, meas, sid, seed_par, seed_cov) -> "Batch":
+        """From track-major arrays: meas [m, 5] (loc0, loc1, V00, V01, V11), seed_par [n, 5],
+        seed_cov [n, 15]. Returns host (numpy) arrays in the library layout."""
+        meas = np.asarray(meas, dtype=np.float64)
+        c = np.ascontiguousarray
+        return cls(c(offsets, dtype=np.uint32), c(meas[:, 0]), c(meas[:, 1]), c(meas[:, 2]),
+                   c(meas[:, 3]), c(meas[:, 4]), c(sid, dtype=np.uint32),
+                   c(np.asarray(seed_par, dtype=np.float64).T), c(np.asarray(seed_cov, dtype=np.float64).T))
+
+    def to(self, device, pin: bool = False) -> "Batch":
+        import torch
+        vals = {}
+        for k in _IN_FIELDS:
+            v = getattr(self, k)
+            t = torch.from_numpy(np.ascontiguousarray(v)) if isinstance(v, np.ndarray) else v
+            if t.dtype == torch.uint32:
+                t = t.view(torch.int32)
+            if device == "cpu" and pin:
+                t = t.pin_memory()
+            else:
+                t = t.to(device)
+            vals[k] = t
+        return Batch(**vals)
+
+    def nbytes(self) -> int:
+        return int(sum(getattr(self, k).nbytes if isinstance(getattr(self, k), np.ndarray)
+                       else getattr(self, k).numel() * getattr(self, k).element_size()
+                       for k in _IN_FIELDS))
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _inputs_struct(b: Batch) -> FitInputs:
+    s = FitInputs()
+    s.n_tracks = b.n_tracks
+    s.n_meas = b.n_meas
+    for k in _IN_FIELDS:
+        setattr(s, k, _ptr(getattr(b, k)))
+    return s
+
+
+@dataclass
+class Result:
+    par: object      # [5, n]
+    cov: object      # [15, n]
+    chi2: object     # [n]
+    ndf: object      # [n]
+    status: object   # [n]
+    steps: object    # [2, n] or None
+
+
+def alloc_outputs(n: int, device, steps: bool = True) -> Result:
+    import torch
+    kw = dict(device=device)
+    return Result(torch.empty((5, n), dtype=torch.float64, **kw),
+                  torch.empty((15, n), dtype=torch.float64, **kw),
+                  torch.empty((n,), dtype=torch.float64, **kw),
+                  torch.empty((n,), dtype=torch.int32, **kw),
+                  torch.empty((n,), dtype=torch.int32, **kw),
+                  torch.empty((2, n), dtype=torch.int32, **kw) if steps else None)
+
+
+def _outputs_struct(r: Result) -> FitOutputs:
+    s = FitOutputs()
+    s.par, s.cov, s.chi2 = _ptr(r.par), _ptr(r.cov), _ptr(r.chi2)
+    s.ndf, s.status, s.steps = _ptr(r.ndf), _ptr(r.status), _ptr(r.steps)
+    return s
+
+
+def fit(ctx: Context, geo: Geometry, field: Field, batch: Batch, opts: Options | None = None,
+        out: Result | None = None, stream=None, steps: bool = True) -> Result:
+    """Enqueues the fit of a batch of CUDA tensors on ``stream`` (default: torch's current
+    stream) and returns the output tensors (valid once the stream reaches the work)."""
+    import torch
+    dev = batch.offsets.device
+    if dev.type != "cuda":
+        raise TkfError("fit() needs CUDA tensors; use fit_host() for host arrays")
+    out = out or alloc_outputs(batch.n_tracks, dev, steps)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    o = (opts or Options()).c()
+    _check(lib().tkf_fit(ctx.handle, geo.handle, field.handle, ctypes.byref(o),
+                         ctypes.byref(_inputs_struct(batch)), ctypes.byref(_outputs_struct(out)),
+                         _VP(stream.cuda_stream)), ctx.handle, "tkf_fit")
+    return out
+
+
+def fit_host(ctx: Context, geo: Geometry, field: Field, batch: Batch, opts: Options | None = None,
+             out: Result | None = None, stream=None, steps: bool = True) -> Result:
+    """Fits a batch of host arrays (numpy or pinned CPU tensors) through tkf_fit_host:
+    host-to-device copies, the fit and device-to-host copies on one stream; returns when the
+    results are in the host buffers."""
+    n = batch.n_tracks
+    if out is None:
+        out = Result(np.empty((5, n)), np.empty((15, n)), np.empty(n), np.empty(n, np.int32),
+                     np.empty(n, np.uint32), np.empty((2, n), np.uint32) if steps else None)
+    o = (opts or Options()).c()
+    s = stream.cuda_stream if stream is not None else None
+    _check(lib().tkf_fit_host(ctx.handle, geo.handle, field.handle, ctypes.byref(o),
+                              ctypes.byref(_inputs_struct(batch)), ctypes.byref(_outputs_struct(out)),
+                              _VP(s) if s else None), ctx.handle, "tkf_fit_host")
+    return out
+
+
+def exported_symbols() -> list[str]:
+    return sorted(_SIGNATURES)

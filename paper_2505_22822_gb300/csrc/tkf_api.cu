@@ -1,0 +1,422 @@
+// tkf_api.cu -- the C interface declared in include/tkf.h: handles, validation, launches.
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "tkf_internal.cuh"
+
+namespace {
+
+thread_local std::string g_create_error;
+
+tkf_status fail(tkf_context ctx, tkf_status code, const std::string& msg) {
+  if (ctx)
+    ctx->last_error = msg;
+  else
+    g_create_error = msg;
+  return code;
+}
+
+tkf_status cuda_fail(tkf_context ctx, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(ctx, e == cudaErrorMemoryAllocation ? TKF_ERR_OOM : TKF_ERR_DEVICE, m);
+}
+
+// Makes the context's device current for the duration of a call and restores the caller's.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+tkf_status tkf_context_create(int device, tkf_context* out) {
+  if (!out) return fail(nullptr, TKF_ERR_INVALID_ARG, "tkf_context_create: out is NULL");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    return fail(nullptr, TKF_ERR_DEVICE, std::string("tkf_context_create: no CUDA device (") +
+                                             (e == cudaSuccess ? "count 0" : cudaGetErrorString(e)) + ")");
+  }
+  if (device < 0) {
+    if (cudaGetDevice(&device) != cudaSuccess) return fail(nullptr, TKF_ERR_DEVICE, "cudaGetDevice failed");
+  }
+  if (device >= n) return fail(nullptr, TKF_ERR_DEVICE, "tkf_context_create: device index out of range");
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess)
+    return fail(nullptr, TKF_ERR_DEVICE, "cudaGetDeviceProperties failed");
+  if (!(prop.major == 10 && prop.minor == 3))
+    return fail(nullptr, TKF_ERR_UNSUPPORTED,
+                "tkf_context_create: this library is built for sm_103a (GB300); device is sm_" +
+                    std::to_string(prop.major) + std::to_string(prop.minor));
+  tkf_context c = new (std::nothrow) tkf_context_s();
+  if (!c) return fail(nullptr, TKF_ERR_OOM, "tkf_context_create: host allocation failed");
+  c->device = device;
+  *out = c;
+  return TKF_OK;
+}
+
+void tkf_context_destroy(tkf_context ctx) {
+  if (!ctx) return;
+  if (ctx->stage) {
+    DeviceGuard g(ctx->device);
+    cudaFree(ctx->stage);
+  }
+  delete ctx;
+}
+
+const char* tkf_last_error(tkf_context ctx) {
+  return ctx ? ctx->last_error.c_str() : g_create_error.c_str();
+}
+
+void tkf_material_silicon(tkf_material* m) {
+  if (!m) return;
+  m->z_over_a = 0.49848;
+  m->i_ev = 173.0;
+  m->rho_g_cm3 = 2.329;
+  m->hbar_omega_p_ev = 31.05;
+}
+
+tkf_status tkf_geometry_create(tkf_context ctx, const tkf_surface_desc* s, uint32_t n, const tkf_material* mat,
+                               tkf_geometry* out) {
+  if (!ctx) return fail(nullptr, TKF_ERR_BAD_HANDLE, "tkf_geometry_create: NULL context");
+  if (!out || !s || n == 0) return fail(ctx, TKF_ERR_INVALID_ARG, "tkf_geometry_create: NULL pointer or n == 0");
+  *out = nullptr;
+  tkf_material m;
+  if (mat)
+    m = *mat;
+  else
+    tkf_material_silicon(&m);
+  if (!(m.z_over_a > 0 && m.i_ev > 0 && m.rho_g_cm3 > 0 && m.hbar_omega_p_ev > 0))
+    return fail(ctx, TKF_ERR_INVALID_ARG, "tkf_geometry_create: material constants must be positive");
+  double* host = new (std::nothrow) double[size_t(n) * tkf::kSurfStride];
+  if (!host) return fail(ctx, TKF_ERR_OOM, "tkf_geometry_create: host allocation failed");
+  for (uint32_t i = 0; i < n; ++i) {
+    const tkf_surface_desc& d = s[i];
+    double col[3][3];  // col[c] = column c of rot
+    for (int c = 0; c < 3; ++c)
+      for (int r = 0; r < 3; ++r) col[c][r] = d.rot[r * 3 + c];
+    bool ok = true;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        double dp = col[a][0] * col[b][0] + col[a][1] * col[b][1] + col[a][2] * col[b][2];
+        if (fabs(dp - (a == b ? 1.0 : 0.0)) > 1e-9) ok = false;
+      }
+    // n must be u x v (right-handed frame)
+    double cx = col[0][1] * col[1][2] - col[0][2] * col[1][1];
+    double cy = col[0][2] * col[1][0] - col[0][0] * col[1][2];
+    double cz = col[0][0] * col[1][1] - col[0][1] * col[1][0];
+    if (fabs(cx - col[2][0]) > 1e-9 || fabs(cy - col[2][1]) > 1e-9 || fabs(cz - col[2][2]) > 1e-9) ok = false;
+    if (!ok || !(d.thickness >= 0.0) || !(d.x0 > 0.0) || !isfinite(d.center[0]) || !isfinite(d.center[1]) ||
+        !isfinite(d.center[2])) {
+      delete[] host;
+      return fail(ctx, TKF_ERR_INVALID_ARG,
+                  "tkf_geometry_create: surface " + std::to_string(i) +
+                      " has a non-orthonormal or left-handed frame, negative thickness or x0 <= 0");
+    }
+    double* o = host + size_t(i) * tkf::kSurfStride;
+    for (int r = 0; r < 3; ++r) {
+      o[r] = col[0][r];
+      o[3 + r] = col[1][r];
+      o[6 + r] = col[2][r];
+      o[9 + r] = d.center[r];
+    }
+    o[12] = d.thickness;
+    o[13] = d.x0;
+    o[14] = d.thickness / d.x0;
+    o[15] = 0.0;
+  }
+  DeviceGuard g(ctx->device);
+  if (!g.ok) {
+    delete[] host;
+    return fail(ctx, TKF_ERR_DEVICE, "tkf_geometry_create: cudaSetDevice failed");
+  }
+  double* dev = nullptr;
+  cudaError_t e = cudaMalloc(&dev, size_t(n) * tkf::kSurfStride * sizeof(double));
+  if (e != cudaSuccess) {
+    delete[] host;
+    return cuda_fail(ctx, e, "tkf_geometry_create: cudaMalloc");
+  }
+  e = cudaMemcpy(dev, host, size_t(n) * tkf::kSurfStride * sizeof(double), cudaMemcpyHostToDevice);
+  delete[] host;
+  if (e != cudaSuccess) {
+    cudaFree(dev);
+    return cuda_fail(ctx, e, "tkf_geometry_create: cudaMemcpy");
+  }
+  tkf_geometry h = new (std::nothrow) tkf_geometry_s();
+  if (!h) {
+    cudaFree(dev);
+    return fail(ctx, TKF_ERR_OOM, "tkf_geometry_create: host allocation failed");
+  }
+  h->ctx = ctx;
+  h->device = ctx->device;
+  h->d_surf = dev;
+  h->n = n;
+  h->mat.z_over_a = m.z_over_a;
+  h->mat.i_ev = m.i_ev;
+  h->mat.rho = m.rho_g_cm3;
+  h->mat.hwp_ev = m.hbar_omega_p_ev;
+  h->mat.log_hwp_over_i = log(m.hbar_omega_p_ev / m.i_ev);
+  *out = h;
+  return TKF_OK;
+}
+
+void tkf_geometry_destroy(tkf_geometry geo) {
+  if (!geo) return;
+  DeviceGuard g(geo->device);
+  cudaFree(geo->d_surf);
+  delete geo;
+}
+
+tkf_status tkf_field_create(tkf_context ctx, const tkf_field_desc* d, tkf_field* out) {
+  if (!ctx) return fail(nullptr, TKF_ERR_BAD_HANDLE, "tkf_field_create: NULL context");
+  if (!d || !out) return fail(ctx, TKF_ERR_INVALID_ARG, "tkf_field_create: NULL pointer");
+  *out = nullptr;
+  tkf::FieldDev f{};
+  f.kind = d->kind;
+  float2* dev = nullptr;
+  if (d->kind == TKF_FIELD_UNIFORM) {
+    for (int i = 0; i < 3; ++i) {
+      if (!isfinite(d->b_tesla[i])) return fail(ctx, TKF_ERR_INVALID_ARG, "tkf_field_create: non-finite field");
+      f.b[i] = d->b_tesla[i];
+    }
+  } else if (d->kind == TKF_FIELD_RZ_GRID) {
+    if (d->nr < 2 || d->nz < 2 || !(d->dr > 0) || !(d->dz > 0) || !(d->r0 >= 0) || !d->br || !d->bz ||
+        !isfinite(d->z0))
+      return fail(ctx, TKF_ERR_INVALID_ARG,
+                  "tkf_field_create: grid needs nr, nz >= 2, dr, dz > 0, r0 >= 0 and both arrays");
+    size_t cnt = size_t(d->nr) * d->nz;
+    if (cnt > (size_t(1) << 31)) return fail(ctx, TKF_ERR_INVALID_ARG, "tkf_field_create: grid too large");
+    float2* host = new (std::nothrow) float2[cnt];
+    if (!host) return fail(ctx, TKF_ERR_OOM, "tkf_field_create: host allocation failed");
+    for (size_t i = 0; i < cnt; ++i) host[i] = make_float2(d->br[i], d->bz[i]);
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaMalloc(&dev, cnt * sizeof(float2));
+    if (e != cudaSuccess) {
+      delete[] host;
+      return cuda_fail(ctx, e, "tkf_field_create: cudaMalloc");
+    }
+    e = cudaMemcpy(dev, host, cnt * sizeof(float2), cudaMemcpyHostToDevice);
+    delete[] host;
+    if (e != cudaSuccess) {
+      cudaFree(dev);
+      return cuda_fail(ctx, e, "tkf_field_create: cudaMemcpy");
+    }
+    f.nr = int(d->nr);
+    f.nz = int(d->nz);
+    f.r0 = d->r0;
+    f.dr = d->dr;
+    f.z0 = d->z0;
+    f.dz = d->dz;
+    f.inv_dr = 1.0 / d->dr;
+    f.inv_dz = 1.0 / d->dz;
+    f.grid = dev;
+  } else {
+    return fail(ctx, TKF_ERR_INVALID_ARG, "tkf_field_create: unknown field kind");
+  }
+  tkf_field h = new (std::nothrow) tkf_field_s();
+  if (!h) {
+    if (dev) cudaFree(dev);
+    return fail(ctx, TKF_ERR_OOM, "tkf_field_create: host allocation failed");
+  }
+  h->ctx = ctx;
+  h->device = ctx->device;
+  h->f = f;
+  h->d_grid = dev;
+  *out = h;
+  return TKF_OK;
+}
+
+void tkf_field_destroy(tkf_field field) {
+  if (!field) return;
+  if (field->d_grid) {
+    DeviceGuard g(field->device);
+    cudaFree(field->d_grid);
+  }
+  delete field;
+}
+
+void tkf_fit_options_default(tkf_fit_options* o) {
+  if (!o) return;
+  o->precision = TKF_FP64;
+  o->step_mode = TKF_STEP_ADAPTIVE;
+  o->tol = 1e-4;
+  o->h_max = 1000.0;
+  o->h_min = 1e-4;
+  o->surf_tol = 1e-9;
+  o->max_steps = 10000;
+  o->mass = 0.1056583755;
+  o->mlp = nullptr;
+}
+
+static tkf_status check_common(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf_fit_options* o,
+                               const tkf_fit_inputs* in, const tkf_fit_outputs* out, const char* fn) {
+  if (!ctx) return fail(nullptr, TKF_ERR_BAD_HANDLE, std::string(fn) + ": NULL context");
+  if (!geo || !field || geo->ctx != ctx || field->ctx != ctx)
+    return fail(ctx, TKF_ERR_BAD_HANDLE, std::string(fn) + ": geometry or field handle NULL or from another context");
+  if (!o || !in || !out) return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": NULL options, inputs or outputs");
+  if (!(o->precision == TKF_FP64 || o->precision == TKF_MIXED))
+    return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": unknown precision");
+  if (!(o->step_mode == TKF_STEP_ADAPTIVE || o->step_mode == TKF_STEP_LEARNED))
+    return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": unknown step mode");
+  if (o->step_mode == TKF_STEP_LEARNED && !o->mlp)
+    return fail(ctx, TKF_ERR_UNSUPPORTED, std::string(fn) + ": TKF_STEP_LEARNED needs an mlp handle");
+  if (!(o->tol > 0) || !(o->h_max > 0) || !(o->h_min > 0) || !(o->h_min <= o->h_max) || !(o->surf_tol > 0) ||
+      o->max_steps == 0 || !(o->mass > 0) || !isfinite(o->h_max))
+    return fail(ctx, TKF_ERR_INVALID_ARG,
+                std::string(fn) + ": options need tol, h_max, h_min, surf_tol, mass > 0, h_min <= h_max, max_steps > 0");
+  if (in->n_meas > 0xffffffffull)
+    return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": n_meas exceeds 32-bit offsets");
+  if (in->n_tracks == 0) return TKF_OK;
+  if (!in->offsets || !in->seed_par || !in->seed_cov || !out->par || !out->cov || !out->chi2 || !out->ndf ||
+      !out->status)
+    return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": NULL required pointer");
+  if (in->n_meas > 0 && (!in->loc0 || !in->loc1 || !in->v00 || !in->v01 || !in->v11 || !in->sid))
+    return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": NULL measurement pointer");
+  const void* ptrs[] = {in->loc0, in->loc1, in->v00, in->v01, in->v11, in->seed_par, in->seed_cov,
+                        out->par, out->cov, out->chi2};
+  for (const void* p : ptrs)
+    if (!aligned8(p)) return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": pointer not 8-byte aligned");
+  return TKF_OK;
+}
+
+static tkf::FitArgs make_args(tkf_geometry geo, const tkf_fit_options* o, const tkf_fit_inputs* in,
+                              const tkf_fit_outputs* out) {
+  tkf::FitArgs a{};
+  a.n_tracks = in->n_tracks;
+  a.n_meas = in->n_meas;
+  a.offsets = in->offsets;
+  a.loc0 = in->loc0;
+  a.loc1 = in->loc1;
+  a.v00 = in->v00;
+  a.v01 = in->v01;
+  a.v11 = in->v11;
+  a.sid = in->sid;
+  a.seed_par = in->seed_par;
+  a.seed_cov = in->seed_cov;
+  a.par = out->par;
+  a.cov = out->cov;
+  a.chi2 = out->chi2;
+  a.ndf = out->ndf;
+  a.status = out->status;
+  a.steps = out->steps;
+  a.surf = geo->d_surf;
+  a.n_surf = geo->n;
+  a.mat = geo->mat;
+  a.opt.tol = o->tol;
+  a.opt.h_max = o->h_max;
+  a.opt.h_min = o->h_min;
+  a.opt.surf_tol = o->surf_tol;
+  a.opt.mass = o->mass;
+  a.opt.max_steps = o->max_steps;
+  return a;
+}
+
+tkf_status tkf_fit(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf_fit_options* o,
+                   const tkf_fit_inputs* in, const tkf_fit_outputs* out, void* stream) {
+  tkf_status s = check_common(ctx, geo, field, o, in, out, "tkf_fit");
+  if (s != TKF_OK || in->n_tracks == 0) return s;
+  if (o->step_mode == TKF_STEP_LEARNED)
+    return fail(ctx, TKF_ERR_UNSUPPORTED, "tkf_fit: learned step proposals are not available in this build");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(ctx, TKF_ERR_DEVICE, "tkf_fit: cudaSetDevice failed");
+  tkf::FitArgs a = make_args(geo, o, in, out);
+  cudaError_t e = tkf::launch_fit(a, field->f, o->precision, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit: launch");
+  return TKF_OK;
+}
+
+tkf_status tkf_fit_host(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf_fit_options* o,
+                        const tkf_fit_inputs* hin, const tkf_fit_outputs* hout, void* stream) {
+  tkf_status s = check_common(ctx, geo, field, o, hin, hout, "tkf_fit_host");
+  if (s != TKF_OK || hin->n_tracks == 0) return s;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(ctx, TKF_ERR_DEVICE, "tkf_fit_host: cudaSetDevice failed");
+  const size_t n = hin->n_tracks, m = hin->n_meas;
+  auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t b_off = up((n + 1) * 4), b_meas = up(m * 8), b_sid = up(m * 4), b_seedp = up(5 * n * 8),
+               b_seedc = up(15 * n * 8), b_par = up(5 * n * 8), b_cov = up(15 * n * 8), b_n8 = up(n * 8),
+               b_n4 = up(n * 4), b_steps = hout->steps ? up(2 * n * 4) : 0;
+  const size_t total = b_off + 5 * b_meas + b_sid + b_seedp + b_seedc + b_par + b_cov + b_n8 + 2 * b_n4 + b_steps;
+  if (total > ctx->stage_bytes) {
+    if (ctx->stage) cudaFree(ctx->stage);
+    ctx->stage = nullptr;
+    ctx->stage_bytes = 0;
+    cudaError_t e = cudaMalloc(&ctx->stage, total);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_host: staging cudaMalloc");
+    ctx->stage_bytes = total;
+  }
+  char* p = static_cast<char*>(ctx->stage);
+  auto take = [&p](size_t b) {
+    char* q = p;
+    p += b;
+    return q;
+  };
+  tkf_fit_inputs din = *hin;
+  tkf_fit_outputs dout{};
+  din.offsets = reinterpret_cast<uint32_t*>(take(b_off));
+  din.loc0 = reinterpret_cast<double*>(take(b_meas));
+  din.loc1 = reinterpret_cast<double*>(take(b_meas));
+  din.v00 = reinterpret_cast<double*>(take(b_meas));
+  din.v01 = reinterpret_cast<double*>(take(b_meas));
+  din.v11 = reinterpret_cast<double*>(take(b_meas));
+  din.sid = reinterpret_cast<uint32_t*>(take(b_sid));
+  din.seed_par = reinterpret_cast<double*>(take(b_seedp));
+  din.seed_cov = reinterpret_cast<double*>(take(b_seedc));
+  dout.par = reinterpret_cast<double*>(take(b_par));
+  dout.cov = reinterpret_cast<double*>(take(b_cov));
+  dout.chi2 = reinterpret_cast<double*>(take(b_n8));
+  dout.ndf = reinterpret_cast<int32_t*>(take(b_n4));
+  dout.status = reinterpret_cast<uint32_t*>(take(b_n4));
+  dout.steps = hout->steps ? reinterpret_cast<uint32_t*>(take(b_steps)) : nullptr;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  struct Cp {
+    void* dst;
+    const void* src;
+    size_t bytes;
+  };
+  const Cp h2d[] = {{(void*)din.offsets, hin->offsets, (n + 1) * 4}, {(void*)din.loc0, hin->loc0, m * 8},
+                    {(void*)din.loc1, hin->loc1, m * 8},           {(void*)din.v00, hin->v00, m * 8},
+                    {(void*)din.v01, hin->v01, m * 8},             {(void*)din.v11, hin->v11, m * 8},
+                    {(void*)din.sid, hin->sid, m * 4},             {(void*)din.seed_par, hin->seed_par, 5 * n * 8},
+                    {(void*)din.seed_cov, hin->seed_cov, 15 * n * 8}};
+  for (const Cp& c : h2d) {
+    if (c.bytes == 0) continue;
+    cudaError_t e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_host: host-to-device copy");
+  }
+  s = tkf_fit(ctx, geo, field, o, &din, &dout, stream);
+  if (s != TKF_OK) return s;
+  const Cp d2h[] = {{hout->par, dout.par, 5 * n * 8},   {hout->cov, dout.cov, 15 * n * 8},
+                    {hout->chi2, dout.chi2, n * 8},     {hout->ndf, dout.ndf, n * 4},
+                    {hout->status, dout.status, n * 4}, {hout->steps, dout.steps, hout->steps ? 2 * n * 4 : 0}};
+  for (const Cp& c : d2h) {
+    if (c.bytes == 0) continue;
+    cudaError_t e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_host: device-to-host copy");
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_host: stream synchronize");
+  return TKF_OK;
+}
+
+}  // extern "C"

@@ -362,7 +362,10 @@ def barrel_workload(n_events: int = 50, lo: int = 2000, hi: int = 20000, seed: i
     g = geom or barrel_endcap_geometry()
     f = fld or uniform_field(2.0)
     counts = event_counts(seed, n_events, lo, hi)
-    t = simulate(g, f, barrel_params(**kw), seed, counts)
+    p = barrel_params(**kw)
+    if f.kind == 0 and "step" not in kw:
+        p.step = 40.0  # exact helix segments: the step only bounds the crossing search
+    t = simulate(g, f, p, seed, counts)
     return Workload(f"barrel_endcap_{n_events}ev", g, f, t)
 
 

@@ -376,15 +376,15 @@ double sdist(const Surf& s, const double x[3]) {
   return s.n[0] * (x[0] - s.c[0]) + s.n[1] * (x[1] - s.c[1]) + s.n[2] * (x[2] - s.c[2]);
 }
 
-void candidates(const Geometry& g, const double a[3], const double b[3], std::vector<uint32_t>& out) {
+void candidates(const Geometry& g, const double a[3], const double b[3], double margin, std::vector<uint32_t>& out) {
   out.clear();
   if (g.kind == 0) {
     for (uint32_t i = 0; i < g.s.size(); ++i) out.push_back(i);
     return;
   }
   double ra = std::hypot(a[0], a[1]), rb = std::hypot(b[0], b[1]);
-  double rlo = std::min(ra, rb) - 0.2, rhi = std::max(ra, rb) + 0.2;
-  double zlo = std::min(a[2], b[2]) - 0.2, zhi = std::max(a[2], b[2]) + 0.2;
+  double rlo = std::min(ra, rb) - margin, rhi = std::max(ra, rb) + margin;
+  double zlo = std::min(a[2], b[2]) - margin, zhi = std::max(a[2], b[2]) + margin;
   double xm[3] = {0.5 * (a[0] + b[0]), 0.5 * (a[1] + b[1]), 0.5 * (a[2] + b[2])};
   double phim = std::atan2(xm[1], xm[0]);
   if (phim < 0) phim += 2.0 * kPi;
@@ -408,7 +408,10 @@ void candidates(const Geometry& g, const double a[3], const double b[3], std::ve
     if (zhi < zl || zlo > zh) continue;
     for (size_t k = 0; k < D.rings.size(); ++k) {
       const DiskRing& R = D.rings[k];
-      if (rm < R.rc - 40.0 || rm > std::sqrt((R.rc + 35.0) * (R.rc + 35.0) + 225.0) + 1.0) continue;
+      double half_len = 0.5 * std::sqrt((b[0] - a[0]) * (b[0] - a[0]) + (b[1] - a[1]) * (b[1] - a[1]));
+      if (rm < R.rc - 36.0 - half_len - margin ||
+          rm > std::sqrt((R.rc + 35.0) * (R.rc + 35.0) + 225.0) + half_len + margin)
+        continue;
       int ip0 = int(std::floor(phim / (2.0 * kPi / R.nphi) + 0.5));
       for (int dip = -2; dip <= 2; ++dip) {
         int ip = ((ip0 + dip) % R.nphi + R.nphi) % R.nphi;
@@ -473,7 +476,9 @@ bool simulate(const Geometry& g, const FieldDesc& f, const Params& P, Rng& rng, 
       double xm[3] = {x[0] + 0.5 * h * T[0], x[1] + 0.5 * h * T[1], x[2] + 0.5 * h * T[2]};
       field_value(f, xm, B);
       helix(x, T, qop, B, h, xb, Tb);
-      candidates(g, x, xb, cand);
+      double bmag = std::sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+      double margin = 0.2 + 0.125 * h * h * kC * std::fabs(qop) * bmag;  // + sagitta of the step
+      candidates(g, x, xb, margin, cand);
       double best = h + 1.0;
       for (uint32_t id : cand) {
         const Surf& s = g.s[id];
@@ -481,16 +486,23 @@ bool simulate(const Geometry& g, const FieldDesc& f, const Params& P, Rng& rng, 
         if (id == last && std::fabs(da) < 1e-7) continue;
         if ((da > 0) == (db > 0) && da != 0.0) continue;
         if (da == 0.0) continue;
+        // root of n.(x(s) - c) in the bracket [0, h]: Newton from the secant, bisection
+        // whenever an iterate leaves the bracket
         double lo = 0.0, hi = h, xm2[3], Tm2[3];
-        for (int b = 0; b < 100; ++b) {
-          double mid = 0.5 * (lo + hi);
-          helix(x, T, qop, B, mid, xm2, Tm2);
-          if ((sdist(s, xm2) > 0) == (da > 0))
-            lo = mid;
+        double sc = h * da / (da - db);
+        for (int it = 0; it < 60; ++it) {
+          helix(x, T, qop, B, sc, xm2, Tm2);
+          double fs = sdist(s, xm2);
+          if (std::fabs(fs) < 1e-12) break;
+          if ((fs > 0) == (da > 0))
+            lo = sc;
           else
-            hi = mid;
+            hi = sc;
+          double dfs = s.n[0] * Tm2[0] + s.n[1] * Tm2[1] + s.n[2] * Tm2[2];
+          double nx = sc - fs / dfs;
+          sc = (nx > lo && nx < hi && std::isfinite(nx)) ? nx : 0.5 * (lo + hi);
+          if (hi - lo < 1e-13) break;
         }
-        double sc = 0.5 * (lo + hi);
         if (sc >= best) continue;
         helix(x, T, qop, B, sc, xm2, Tm2);
         double l0, l1;

@@ -1,0 +1,76 @@
+"""Element-wise comparison of a GPU fit with the CPU oracle (test infrastructure).
+
+Metric (the first-surface smoothed state is a difference of terms of the size of the
+filtered covariance C_0|0, so that is the scale of rounding differences between two correct
+FP64 evaluations):
+  parameters   |dp_i|   <= tol * max(|p_i|, sigma_i)      (phi difference wrapped)
+  covariance   |dC_ij|  <= tol * sqrt(C0_ii C0_jj)         (C0 = filtered cov at surface 0)
+  chi2         |dchi2|  <= tol * max(chi2, 1)
+  status, ndf  identical
+"""
+
+import numpy as np
+
+import oracle
+
+
+def gpu_to_track_major(res):
+    """paper_2505_22822_gb300.Result (torch or numpy, SoA) -> dict of numpy track-major arrays."""
+    def host(x):
+        if x is None:
+            return None
+        if hasattr(x, "detach"):
+            x = x.detach().cpu().numpy()
+        return np.asarray(x)
+    out = {"par": host(res.par).T.copy(), "cov": host(res.cov).T.copy(), "chi2": host(res.chi2),
+           "ndf": host(res.ndf).astype(np.int64), "status": host(res.status).astype(np.uint32)}
+    st = host(res.steps)
+    out["steps"] = st.T.astype(np.uint32) if st is not None else None
+    return out
+
+
+def compare(g: dict, o: "oracle.FitResult", tol: float, idx=None):
+    """Returns (ok_mask over compared tracks, stats dict)."""
+    if idx is None:
+        idx = np.arange(o.par.shape[0])
+    gp, gc, gx = g["par"][idx], g["cov"][idx], g["chi2"][idx]
+    op, oc, ox = o.par, o.cov, o.chi2
+    if op.shape[0] != len(idx):
+        op, oc, ox = op[idx], oc[idx], ox[idx]
+        ocf, ost, ondf = o.cov_filt0[idx], o.status[idx], o.ndf[idx]
+        osteps = o.steps[idx]
+    else:
+        ocf, ost, ondf, osteps = o.cov_filt0, o.status, o.ndf, o.steps
+    status_eq = g["status"][idx] == ost
+    ndf_eq = g["ndf"][idx] == ondf
+    good = status_eq & ((ost & 0x39F) == 0)  # fatal bits clear on both
+    C = oracle.unpack(oc)
+    sig = np.sqrt(np.abs(np.einsum("nii->ni", C)))
+    dp = gp - op
+    dp[:, 2] = (dp[:, 2] + np.pi) % (2 * np.pi) - np.pi
+    rel_p = np.abs(dp) / np.maximum(np.abs(op), sig)
+    C0 = oracle.unpack(ocf)
+    C0 = np.where(np.isfinite(C0), C0, C)  # no filtered state (N = 0): the seed covariance
+    d0 = np.sqrt(np.abs(np.einsum("nii->ni", C0)))
+    scale = np.einsum("ni,nj->nij", d0, d0)
+    rel_c = np.abs(oracle.unpack(gc) - C) / scale
+    rel_x = np.abs(gx - ox) / np.maximum(np.abs(ox), 1.0)
+    rp = np.where(good[:, None], rel_p, 0).max(1)
+    rc = np.where(good[:, None, None], rel_c, 0).reshape(len(idx), -1).max(1)
+    rx = np.where(good, rel_x, 0)
+    # a track that failed on both sides must be NaN on the GPU too
+    nan_ok = good | ~status_eq | ((ost & 0x39F) == 0) | np.all(np.isnan(gp), axis=1)
+    ok = status_eq & ndf_eq & (rp <= tol) & (rc <= tol) & (rx <= tol) & nan_ok
+    same_steps = None
+    if g.get("steps") is not None:
+        same_steps = np.all(g["steps"][idx] == osteps, axis=1)
+    stats = {
+        "n": int(len(idx)), "ok": int(ok.sum()), "status_mismatch": int((~status_eq).sum()),
+        "max_rel_par": float(rp.max()) if len(rp) else 0.0,
+        "max_rel_cov": float(rc.max()) if len(rc) else 0.0,
+        "max_rel_chi2": float(rx.max()) if len(rx) else 0.0,
+        "same_steps": int(same_steps.sum()) if same_steps is not None else None,
+        "dp_over_sigma_max": float(np.where(good[:, None], np.abs(dp) / np.maximum(sig, 1e-300), 0).max())
+        if len(idx) else 0.0,
+    }
+    return ok, same_steps, stats
