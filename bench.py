@@ -131,6 +131,23 @@ def fp64_peak_tflops(sm_mhz: float | None):
     return 152 * 4 * mhz * 1e6 / 1e12
 
 
+def pull_stats(out, t):
+    """Pulls of the fitted first-surface parameters against the simulated truth, and chi2/ndf."""
+    par = out.par.cpu().numpy().T
+    cov = out.cov.cpu().numpy().T
+    status = out.status.cpu().numpy().view(np.uint32)
+    ok = status == 0
+    iu = np.triu_indices(5)
+    diag = [int(np.where((iu[0] == k) & (iu[1] == k))[0][0]) for k in range(5)]
+    sig = np.sqrt(cov[ok][:, diag])
+    d = par[ok] - t.truth[ok]
+    d[:, 2] = (d[:, 2] + np.pi) % (2 * np.pi) - np.pi
+    pull = d / sig
+    chi2 = out.chi2.cpu().numpy()[ok] / out.ndf.cpu().numpy()[ok]
+    return {"sigma": [round(float(x), 4) for x in pull.std(0)], "mean": [round(float(x), 4) for x in pull.mean(0)],
+            "chi2_ndf": round(float(chi2.mean()), 4)}
+
+
 def cpu_baseline(w, max_seconds: float = 20.0):
     """The CPU oracle as it stands on this host's cores, on a bounded sample of the workload."""
     import oracle
@@ -217,39 +234,47 @@ def main():
     fld = tkf.Field.from_desc(ctx, w.field)
     host = tkf.Batch.from_arrays(t.offsets, t.meas, t.sid, t.seed_par, t.seed_cov)
     dev = host.to(f"cuda:{local}")
-    variant = "fp64" if args.variant == "auto" else args.variant
-    opts = tkf.Options(precision=tkf.MIXED if variant == "mixed" else tkf.FP64, mass=w.mass)
-    out = tkf.alloc_outputs(n_tracks, dev.offsets.device, steps=True)
+    variants = ["fp64", "mixed"] if args.variant == "auto" else [args.variant]
     stream = torch.cuda.current_stream()
-
-    for _ in range(args.warmup):
-        tkf.fit(ctx, geo, fld, dev, opts, out=out, stream=stream)
-    torch.cuda.synchronize()
-    # work counted from this batch's step counters (identical every step)
-    st = out.steps.cpu().numpy().astype(np.int64)
-    attempts, rejected = int(st[0].sum()), int(st[1].sum())
-    status = out.status.cpu().numpy().view(np.uint32)
     hits_k1 = int((np.diff(t.offsets.astype(np.int64)) - 1).clip(min=0).sum())
-    flops = (FLOP_STEP_ACCEPTED * (attempts - rejected) + FLOP_STEP_REJECTED * rejected +
-             FLOP_HIT * hits_k1 + FLOP_TRACK * n_tracks)
-
-    barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        ev0.record(stream)
-        for _ in range(args.steps):
+    results = {}
+    for variant in variants:
+        opts = tkf.Options(precision=tkf.MIXED if variant == "mixed" else tkf.FP64, mass=w.mass)
+        out = tkf.alloc_outputs(n_tracks, dev.offsets.device, steps=True)
+        for _ in range(args.warmup):
             tkf.fit(ctx, geo, fld, dev, opts, out=out, stream=stream)
-        ev1.record(stream)
         torch.cuda.synchronize()
-    barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    ms_max = ms
-    if dist is not None:
-        tt = torch.tensor([ms], device=f"cuda:{local}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_max = float(tt.item())
-    clocks = clk.summary()
+        # work counted from this batch's step counters (identical every step)
+        st = out.steps.cpu().numpy().astype(np.int64)
+        attempts, rejected = int(st[0].sum()), int(st[1].sum())
+        status = out.status.cpu().numpy().view(np.uint32)
+        barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            ev0.record(stream)
+            for _ in range(args.steps):
+                tkf.fit(ctx, geo, fld, dev, opts, out=out, stream=stream)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        barrier()
+        ms = ev0.elapsed_time(ev1) / args.steps
+        ms_max = ms
+        if dist is not None:
+            tt = torch.tensor([ms], device=f"cuda:{local}")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms_max = float(tt.item())
+        results[variant] = {"ms": ms, "ms_max": ms_max, "clocks": clk.summary(), "opts": opts,
+                            "attempts": attempts, "rejected": rejected, "status_ok": float(np.mean(status == 0)),
+                            "pulls": pull_stats(out, t)}
+    head = "mixed" if "mixed" in results else variants[0]
+    opts = results[head]["opts"]
+    ms, ms_max, clocks = results[head]["ms"], results[head]["ms_max"], results[head]["clocks"]
+    flops = None
+    if "fp64" in results:
+        r64 = results["fp64"]
+        flops = (FLOP_STEP_ACCEPTED * (r64["attempts"] - r64["rejected"]) + FLOP_STEP_REJECTED * r64["rejected"] +
+                 FLOP_HIT * hits_k1 + FLOP_TRACK * n_tracks)
 
     # end to end through the host entry point: pinned host inputs -> fit -> host outputs
     e2e = None
@@ -276,7 +301,7 @@ def main():
         h2d = host.nbytes()
         d2h = n_tracks * (5 * 8 + 15 * 8 + 8 + 4 + 4)
         e2e = {"value": ws * n_tracks / e2e_s, "unit": "tracks/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h}
+               "d2h_bytes_per_step": d2h, "variant": head}
 
     if rank != 0:
         if dist is not None:
@@ -284,7 +309,13 @@ def main():
         return
 
     peak = fp64_peak_tflops(None)
-    achieved = flops / (ms * 1e-3) / 1e12
+    roof = None
+    if flops is not None:
+        ms64 = results["fp64"]["ms"]
+        achieved = flops / (ms64 * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "fit_persistent_kernel<fp64>", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "note": "FP64 CUDA-core pipe of the plain-FP64 fit; peak derived from 152 SMs x 4 flop/clk x 2070 MHz"}
     line = {
         "metric": METRIC,
         "value": ws * n_tracks / (ms_max * 1e-3),
@@ -296,20 +327,23 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if variant == "fp64" else "f32+f64",
+        "dtype": "f64" if head == "fp64" else "f32+f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "variant": variant, "tracks_per_gpu": n_tracks,
+        "config": {"workload": WORKLOAD, "variant": head, "tracks_per_gpu": n_tracks,
                    "measurements_per_gpu": n_meas, "events_per_gpu": args.events,
                    "field": "uniform 2 T along z", "l2": "inputs 0.41 GB > L2, no flush",
-                   "fit_status_ok": float(np.mean(status == 0))},
-        "gpu_launches": args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "note": "FP64 CUDA-core pipe; peak derived from 152 SMs x 4 flop/clk x 2070 MHz"},
+                   "step_mode": "adaptive (learned proposer not in this build)"},
+        "gpu_launches": 4 * args.steps,
+        "roofline": roof,
         "clocks": clocks,
-        "work": {"step_attempts": attempts, "rejected": rejected, "hits_propagated": hits_k1,
-                 "fp64_flop_per_launch": flops},
+        "variants": {k: {"tracks_per_s": ws * n_tracks / (v["ms_max"] * 1e-3), "ms_per_step": v["ms_max"],
+                         "step_attempts": v["attempts"], "rejected": v["rejected"],
+                         "fit_status_ok": v["status_ok"], "pull_sigma": v["pulls"]["sigma"],
+                         "pull_mean": v["pulls"]["mean"], "chi2_ndf_mean": v["pulls"]["chi2_ndf"]}
+                     for k, v in results.items()},
     }
+    if "fp64" in results and "mixed" in results:
+        line["speedup_vs_fp64"] = results["fp64"]["ms_max"] / results["mixed"]["ms_max"]
     if e2e:
         line["e2e"] = e2e
     if not args.no_cpu_baseline:

@@ -25,8 +25,10 @@
  *   tracks never fail a call: they are reported in that track's status word.
  *
  * Threading
- *   A context is used by one host thread at a time. Handles are freed by the matching
- *   *_destroy call, after all work that uses them has completed.
+ *   A context is used by one host thread at a time, and its fits must not overlap on the
+ *   device: they share the context's workspace, so give each concurrent stream its own
+ *   context. Handles are freed by the matching *_destroy call, after all work that uses them
+ *   has completed.
  */
 #ifndef TKF_H_
 #define TKF_H_
@@ -154,7 +156,7 @@ typedef struct tkf_fit_options {
   double tol;          /* RKN local error tolerance, mm (default 1e-4) */
   double h_max;        /* largest step, mm (default 1000) */
   double h_min;        /* smallest step-size control value, mm (default 1e-4) */
-  double surf_tol;     /* propagation stops within this distance of the target plane, mm (1e-9) */
+  double surf_tol;     /* within this distance of the target plane a Taylor step lands on it, mm (1e-2) */
   uint32_t max_steps;  /* step attempts per surface (default 10000) */
   double mass;         /* particle hypothesis, GeV (default: muon, 0.1056583755) */
   tkf_mlp mlp;         /* step proposer for TKF_STEP_LEARNED, else NULL */

@@ -61,7 +61,7 @@ class Options:
     tol: float = 1e-4        # RKN local error tolerance, mm
     h_max: float = 1000.0    # mm
     h_min: float = 1e-4      # mm
-    surf_tol: float = 1e-9   # mm
+    surf_tol: float = 1e-2   # mm
     mass: float = MUON_MASS  # GeV
     max_steps: int = 10000   # step attempts per surface
     material: tuple = SI

@@ -275,7 +275,7 @@ class Options:
     tol: float = 1e-4
     h_max: float = 1000.0
     h_min: float = 1e-4
-    surf_tol: float = 1e-9
+    surf_tol: float = 1e-2
     max_steps: int = 10000
     mass: float = 0.1056583755
 

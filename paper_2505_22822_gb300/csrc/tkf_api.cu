@@ -71,15 +71,17 @@ tkf_status tkf_context_create(int device, tkf_context* out) {
   tkf_context c = new (std::nothrow) tkf_context_s();
   if (!c) return fail(nullptr, TKF_ERR_OOM, "tkf_context_create: host allocation failed");
   c->device = device;
+  c->sm_count = prop.multiProcessorCount;
   *out = c;
   return TKF_OK;
 }
 
 void tkf_context_destroy(tkf_context ctx) {
   if (!ctx) return;
-  if (ctx->stage) {
+  if (ctx->stage || ctx->ws) {
     DeviceGuard g(ctx->device);
-    cudaFree(ctx->stage);
+    if (ctx->stage) cudaFree(ctx->stage);
+    if (ctx->ws) cudaFree(ctx->ws);
   }
   delete ctx;
 }
@@ -176,6 +178,7 @@ tkf_status tkf_geometry_create(tkf_context ctx, const tkf_surface_desc* s, uint3
   h->mat.rho = m.rho_g_cm3;
   h->mat.hwp_ev = m.hbar_omega_p_ev;
   h->mat.log_hwp_over_i = log(m.hbar_omega_p_ev / m.i_ev);
+  h->mat.bg2_density = exp(1.0 - 2.0 * h->mat.log_hwp_over_i);
   *out = h;
   return TKF_OK;
 }
@@ -262,7 +265,7 @@ void tkf_fit_options_default(tkf_fit_options* o) {
   o->tol = 1e-4;
   o->h_max = 1000.0;
   o->h_min = 1e-4;
-  o->surf_tol = 1e-9;
+  o->surf_tol = 1e-2;
   o->max_steps = 10000;
   o->mass = 0.1056583755;
   o->mlp = nullptr;
@@ -340,7 +343,20 @@ tkf_status tkf_fit(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(ctx, TKF_ERR_DEVICE, "tkf_fit: cudaSetDevice failed");
   tkf::FitArgs a = make_args(geo, o, in, out);
-  cudaError_t e = tkf::launch_fit(a, field->f, o->precision, static_cast<cudaStream_t>(stream));
+  const size_t need = tkf::workspace_bytes(in->n_tracks);
+  if (need > ctx->ws_bytes) {
+    // the old workspace may still be in use by earlier work on this context's stream
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit: stream synchronize");
+    if (ctx->ws) cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+    e = cudaMalloc(&ctx->ws, need);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit: workspace cudaMalloc");
+    ctx->ws_bytes = need;
+  }
+  tkf::Workspace ws = tkf::carve_workspace(ctx->ws, in->n_tracks);
+  cudaError_t e = tkf::launch_fit(a, field->f, o->precision, ws, ctx->sm_count, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit: launch");
   return TKF_OK;
 }

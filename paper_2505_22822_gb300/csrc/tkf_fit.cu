@@ -61,6 +61,9 @@ struct FieldUniformZ {
   __device__ __forceinline__ void at(const double*, double B[3], bool&) const {
     B[0] = 0.0; B[1] = 0.0; B[2] = bz;
   }
+  __device__ __forceinline__ void atf(const float*, float B[3], bool&) const {
+    B[0] = 0.0f; B[1] = 0.0f; B[2] = float(bz);
+  }
 };
 
 struct FieldUniform {
@@ -68,6 +71,9 @@ struct FieldUniform {
   static constexpr bool kUniform = true;
   __device__ __forceinline__ void at(const double*, double B[3], bool&) const {
     B[0] = b[0]; B[1] = b[1]; B[2] = b[2];
+  }
+  __device__ __forceinline__ void atf(const float*, float B[3], bool&) const {
+    B[0] = float(b[0]); B[1] = float(b[1]); B[2] = float(b[2]);
   }
 };
 
@@ -104,7 +110,40 @@ struct FieldGrid {
     }
     B[2] = bz;
   }
+  // the same interpolation in FP32 (mixed precision)
+  __device__ __forceinline__ void atf(const float* x, float B[3], bool& oof) const {
+    const float r = sqrtf(x[0] * x[0] + x[1] * x[1]);
+    const float fr = (r - float(r0)) * float(inv_dr);
+    const float fz = (x[2] - float(z0)) * float(inv_dz);
+    if (!(fr >= 0.0f && fr <= float(nr - 1) && fz >= 0.0f && fz <= float(nz - 1))) {
+      B[0] = B[1] = B[2] = 0.0f;
+      oof = true;
+      return;
+    }
+    const int ir = min(int(fr), nr - 2);
+    const int iz = min(int(fz), nz - 2);
+    const float a = fr - ir, b = fz - iz;
+    const float2* g = grid + size_t(iz) * nr + ir;
+    const float2 g00 = __ldg(g), g01 = __ldg(g + 1), g10 = __ldg(g + nr), g11 = __ldg(g + nr + 1);
+    const float br = (1.0f - b) * ((1.0f - a) * g00.x + a * g01.x) + b * ((1.0f - a) * g10.x + a * g11.x);
+    const float bz = (1.0f - b) * ((1.0f - a) * g00.y + a * g01.y) + b * ((1.0f - a) * g10.y + a * g11.y);
+    const float q = r > 0.0f ? br / r : 0.0f;
+    B[0] = q * x[0];
+    B[1] = q * x[1];
+    B[2] = bz;
+  }
 };
+
+template <class R>
+__device__ __forceinline__ R dotr(const R a[3], const R b[3]) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+__device__ __forceinline__ void cross(const float a[3], const float b[3], float o[3]) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
 
 __device__ __forceinline__ void cross(const double a[3], const double b[3], double o[3]) {
   o[0] = a[1] * b[2] - a[2] * b[1];
@@ -112,18 +151,32 @@ __device__ __forceinline__ void cross(const double a[3], const double b[3], doub
   o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-// clamp((q)^(1/4), lo, hi) with the quarter root as two square roots
-__device__ __forceinline__ double qroot(double q, double lo, double hi) {
-  double f = sqrt(sqrt(q));
+// clamp(0.9 q^(1/4), lo, hi) with the quarter root as two square roots
+__device__ __forceinline__ double step_factor(double q, double lo, double hi) {
+  double f = 0.9 * sqrt(sqrt(q));
   return fmin(fmax(f, lo), hi);
+}
+
+// Path length to the plane along the parabola r + s T + s^2/2 k (a = n.T, b = n.k, d = n.(c - r)),
+// the straight-line d / a when the parabola misses the plane.
+__device__ __forceinline__ double parabolic_path(double d, double a, double b) {
+  double s = d / a;
+  const double disc = a * a + 2.0 * b * d;
+  if (disc >= 0.0) {
+    const double q = 2.0 * d / (a + copysign(sqrt(disc), a));
+    if (isfinite(q)) s = q;
+  }
+  return s;
 }
 
 // ------------------------------------------------------------------ propagation
 // Adaptive RKN4 stepping of (r, T, lam) to the plane of `s`, transporting the derivative
-// columns of (phi, theta, q/p): dr[c], dT[c] (c = 0, 1, 2). Step control (Lund 2009a):
-// eps = h^2 |k1 - k2 - k3 + k4|_1; eps > tol rejects and sets h_ctrl = |h| max(1/4, (tol/eps)^1/4);
-// an accepted step limited by h_ctrl sets h_ctrl = min(h_max, h_ctrl min(4, (tol/eps)^1/4)).
-// Each step aims at the straight-line intersection; within surf_tol a straight step lands on the plane.
+// columns of (phi, theta, q/p): dr[c], dT[c] (c = 0, 1, 2). Step control (Lund 2009a, safety
+// factor 0.9): eps = h^2 |k1 - k2 - k3 + k4|_1; eps > tol rejects and sets
+// h_ctrl = |h| clamp(0.9 (tol/eps)^1/4, 1/4, 4); an accepted step limited by h_ctrl sets
+// h_ctrl = min(h_max, h_ctrl clamp(0.9 (tol/eps)^1/4, 1/4, 4)). Each step aims at the plane's
+// intersection with the parabola r + s T + s^2/2 k1; within surf_tol a second-order Taylor
+// step (state and columns) lands on the plane.
 template <class F>
 __device__ uint32_t propagate(const F& fld, const OptionsDev& o, const Surf& s, double r[3], double T[3],
                               double lam, double dr[3][3], double dT[3][3], double& h_ctrl,
@@ -133,28 +186,49 @@ __device__ uint32_t propagate(const F& fld, const OptionsDev& o, const Surf& s, 
   uint32_t n_here = 0;
   const double lk = lam * kKappa;
   for (;;) {
-    double dist = s.n[0] * (s.c[0] - r[0]) + s.n[1] * (s.c[1] - r[1]) + s.n[2] * (s.c[2] - r[2]);
+    const double dist = s.n[0] * (s.c[0] - r[0]) + s.n[1] * (s.c[1] - r[1]) + s.n[2] * (s.c[2] - r[2]);
+    const double a = dot3(s.n, T);
+    bool oof = false;
+    double B1[3], Bt1[3], k1[3];
+    fld.at(r, B1, oof);
+    for (int i = 0; i < 3; ++i) Bt1[i] = lk * B1[i];
+    cross(T, Bt1, k1);
     if (fabs(dist) <= o.surf_tol) {
-      // close the last (<= surf_tol) distance with a straight step onto the plane
-      const double sl = dist / dot3(s.n, T);
-      for (int i = 0; i < 3; ++i) r[i] += sl * T[i];
+      // second-order Taylor step onto the plane, with the derivative columns
+      if (oof) st |= TKF_TRACK_OUT_OF_FIELD;
+      const double sp = parabolic_path(dist, a, dot3(s.n, k1)), sp2 = 0.5 * sp * sp;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        double q[3];
+        cross(dT[c], Bt1, q);
+        if (c == 2) {
+          double e[3], Bk[3] = {kKappa * B1[0], kKappa * B1[1], kKappa * B1[2]};
+          cross(T, Bk, e);
+          for (int i = 0; i < 3; ++i) q[i] += e[i];
+        }
+        for (int i = 0; i < 3; ++i) {
+          dr[c][i] += sp * dT[c][i] + sp2 * q[i];
+          dT[c][i] += sp * q[i];
+        }
+      }
+      for (int i = 0; i < 3; ++i) {
+        r[i] += sp * T[i] + sp2 * k1[i];
+        T[i] += sp * k1[i];
+      }
       break;
     }
-    double sl = dist / dot3(s.n, T);
+    const double sl = dist / a;
     if (first && !(sl > -1.0 && isfinite(sl))) return st | TKF_TRACK_SURFACE_MISSED;
     first = false;
     if (n_here >= o.max_steps) return st | TKF_TRACK_MAX_STEPS;
     ++n_here;
     ++attempts;
-    const bool limited = !(fabs(sl) < h_ctrl);
-    const double h = limited ? copysign(h_ctrl, sl) : sl;
+    const double sp = parabolic_path(dist, a, dot3(s.n, k1));
+    const bool limited = !(fabs(sp) < h_ctrl);
+    const double h = limited ? copysign(h_ctrl, sp) : sp;
     const double h2 = 0.5 * h, h6 = h * (1.0 / 6.0);
-    bool oof = false;
-    double B1[3], B2[3], B4[3], Bt1[3], Bt2[3], Bt4[3];
-    fld.at(r, B1, oof);
-    for (int i = 0; i < 3; ++i) Bt1[i] = lk * B1[i];
-    double k1[3], k2[3], k3[3], k4[3], T2[3], T3[3], T4[3];
-    cross(T, Bt1, k1);
+    double B2[3], B4[3], Bt2[3], Bt4[3];
+    double k2[3], k3[3], k4[3], T2[3], T3[3], T4[3];
     if (F::kUniform) {
       for (int i = 0; i < 3; ++i) { B2[i] = B1[i]; Bt2[i] = Bt1[i]; }
     } else {
@@ -182,7 +256,7 @@ __device__ uint32_t propagate(const F& fld, const OptionsDev& o, const Surf& s, 
     eps *= h * h;
     if (eps > o.tol) {
       ++rejected;
-      h_ctrl = fabs(h) * qroot(o.tol / eps, 0.25, 4.0);
+      h_ctrl = fabs(h) * step_factor(o.tol / eps, 0.25, 4.0);
       if (h_ctrl < o.h_min) return st | TKF_TRACK_STEP_UNDERFLOW;
       continue;
     }
@@ -232,7 +306,7 @@ __device__ uint32_t propagate(const F& fld, const OptionsDev& o, const Surf& s, 
       T[i] += h6 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
     }
     if (limited) {
-      double fac = (eps > 0.0) ? qroot(o.tol / eps, 0.25, 4.0) : 4.0;
+      const double fac = (eps > 0.0) ? step_factor(o.tol / eps, 0.25, 4.0) : 4.0;
       h_ctrl = fmin(o.h_max, h_ctrl * fac);
     }
   }
@@ -245,37 +319,272 @@ __device__ uint32_t propagate(const F& fld, const OptionsDev& o, const Surf& s, 
   return st;
 }
 
+// ------------------------------------------------------------------ propagation, mixed precision
+// The same stepping, step control and targeting with the stage derivatives, the error estimate,
+// the step control and the derivative columns in FP32; the position and direction are FP64
+// anchors that accumulate each accepted step's FP32 increments, and the distance to the plane
+// is taken in FP64 (sub-micron landing at metre-scale coordinates).
+__device__ __forceinline__ float step_factor_f(float q) {
+  return fminf(fmaxf(0.9f * sqrtf(sqrtf(q)), 0.25f), 4.0f);
+}
+
+__device__ __forceinline__ float parabolic_path_f(float d, float a, float b) {
+  float s = d / a;
+  const float disc = a * a + 2.0f * b * d;
+  if (disc >= 0.0f) {
+    const float q = 2.0f * d / (a + copysignf(sqrtf(disc), a));
+    if (isfinite(q)) s = q;
+  }
+  return s;
+}
+
+template <class F>
+__device__ uint32_t propagate_mixed(const F& fld, const OptionsDev& o, const Surf& s, const float nf[3], double r[3],
+                                    double T[3], double lam, float dr[3][3], float dT[3][3], float& h_ctrl,
+                                    uint32_t& attempts, uint32_t& rejected, float kend[3]) {
+  uint32_t st = 0;
+  bool first = true;
+  uint32_t n_here = 0;
+  const float lk = float(lam * kKappa);
+  const float tol = float(o.tol), h_min = float(o.h_min), h_max = float(o.h_max);
+  for (;;) {
+    const double dist = s.n[0] * (s.c[0] - r[0]) + s.n[1] * (s.c[1] - r[1]) + s.n[2] * (s.c[2] - r[2]);
+    const float Tf[3] = {float(T[0]), float(T[1]), float(T[2])};
+    const float rf[3] = {float(r[0]), float(r[1]), float(r[2])};
+    const float a = dotr(nf, Tf), df = float(dist);
+    bool oof = false;
+    float B1[3], Bt1[3], k1[3];
+    fld.atf(rf, B1, oof);
+    for (int i = 0; i < 3; ++i) Bt1[i] = lk * B1[i];
+    cross(Tf, Bt1, k1);
+    if (fabs(dist) <= o.surf_tol) {
+      if (oof) st |= TKF_TRACK_OUT_OF_FIELD;
+      const float sp = parabolic_path_f(df, a, dotr(nf, k1)), sp2 = 0.5f * sp * sp;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float q[3];
+        cross(dT[c], Bt1, q);
+        if (c == 2) {
+          float e[3], Bk[3] = {float(kKappa) * B1[0], float(kKappa) * B1[1], float(kKappa) * B1[2]};
+          cross(Tf, Bk, e);
+          for (int i = 0; i < 3; ++i) q[i] += e[i];
+        }
+        for (int i = 0; i < 3; ++i) {
+          dr[c][i] += sp * dT[c][i] + sp2 * q[i];
+          dT[c][i] += sp * q[i];
+        }
+      }
+      const double spd = sp;
+      for (int i = 0; i < 3; ++i) {
+        r[i] += spd * T[i] + double(sp2 * k1[i]);
+        T[i] += double(sp * k1[i]);
+      }
+      break;
+    }
+    const float sl = df / a;
+    if (first && !(sl > -1.0f && isfinite(sl))) return st | TKF_TRACK_SURFACE_MISSED;
+    first = false;
+    if (n_here >= o.max_steps) return st | TKF_TRACK_MAX_STEPS;
+    ++n_here;
+    ++attempts;
+    const float sp = parabolic_path_f(df, a, dotr(nf, k1));
+    const bool limited = !(fabsf(sp) < h_ctrl);
+    const float h = limited ? copysignf(h_ctrl, sp) : sp;
+    const float h2 = 0.5f * h, h6 = h * (1.0f / 6.0f);
+    float B2[3], B4[3], Bt2[3], Bt4[3], k2[3], k3[3], k4[3], T2[3], T3[3], T4[3];
+    if (F::kUniform) {
+      for (int i = 0; i < 3; ++i) { B2[i] = B1[i]; Bt2[i] = Bt1[i]; }
+    } else {
+      float r2[3];
+      for (int i = 0; i < 3; ++i) r2[i] = rf[i] + h2 * Tf[i] + 0.125f * h * h * k1[i];
+      fld.atf(r2, B2, oof);
+      for (int i = 0; i < 3; ++i) Bt2[i] = lk * B2[i];
+    }
+    for (int i = 0; i < 3; ++i) T2[i] = Tf[i] + h2 * k1[i];
+    cross(T2, Bt2, k2);
+    for (int i = 0; i < 3; ++i) T3[i] = Tf[i] + h2 * k2[i];
+    cross(T3, Bt2, k3);
+    if (F::kUniform) {
+      for (int i = 0; i < 3; ++i) { B4[i] = B1[i]; Bt4[i] = Bt1[i]; }
+    } else {
+      float r4[3];
+      for (int i = 0; i < 3; ++i) r4[i] = rf[i] + h * Tf[i] + 0.5f * h * h * k3[i];
+      fld.atf(r4, B4, oof);
+      for (int i = 0; i < 3; ++i) Bt4[i] = lk * B4[i];
+    }
+    for (int i = 0; i < 3; ++i) T4[i] = Tf[i] + h * k3[i];
+    cross(T4, Bt4, k4);
+    float eps = 0.0f;
+    for (int i = 0; i < 3; ++i) eps += fabsf(k1[i] - k2[i] - k3[i] + k4[i]);
+    eps *= h * h;
+    if (eps > tol) {
+      ++rejected;
+      h_ctrl = fabsf(h) * step_factor_f(tol / eps);
+      if (h_ctrl < h_min) return st | TKF_TRACK_STEP_UNDERFLOW;
+      continue;
+    }
+    if (oof) st |= TKF_TRACK_OUT_OF_FIELD;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float q1[3], q2[3], q3[3], q4[3], u2[3], u3[3], u4[3];
+      cross(dT[c], Bt1, q1);
+      if (c == 2) {
+        float e[3], Bk[3] = {float(kKappa) * B1[0], float(kKappa) * B1[1], float(kKappa) * B1[2]};
+        cross(Tf, Bk, e);
+        for (int i = 0; i < 3; ++i) q1[i] += e[i];
+      }
+      for (int i = 0; i < 3; ++i) u2[i] = dT[c][i] + h2 * q1[i];
+      cross(u2, Bt2, q2);
+      if (c == 2) {
+        float e[3], Bk[3] = {float(kKappa) * B2[0], float(kKappa) * B2[1], float(kKappa) * B2[2]};
+        cross(T2, Bk, e);
+        for (int i = 0; i < 3; ++i) q2[i] += e[i];
+      }
+      for (int i = 0; i < 3; ++i) u3[i] = dT[c][i] + h2 * q2[i];
+      cross(u3, Bt2, q3);
+      if (c == 2) {
+        float e[3], Bk[3] = {float(kKappa) * B2[0], float(kKappa) * B2[1], float(kKappa) * B2[2]};
+        cross(T3, Bk, e);
+        for (int i = 0; i < 3; ++i) q3[i] += e[i];
+      }
+      for (int i = 0; i < 3; ++i) u4[i] = dT[c][i] + h * q3[i];
+      cross(u4, Bt4, q4);
+      if (c == 2) {
+        float e[3], Bk[3] = {float(kKappa) * B4[0], float(kKappa) * B4[1], float(kKappa) * B4[2]};
+        cross(T4, Bk, e);
+        for (int i = 0; i < 3; ++i) q4[i] += e[i];
+      }
+      for (int i = 0; i < 3; ++i) {
+        dr[c][i] += h * dT[c][i] + h * h6 * (q1[i] + q2[i] + q3[i]);
+        dT[c][i] += h6 * (q1[i] + 2.0f * q2[i] + 2.0f * q3[i] + q4[i]);
+      }
+    }
+    const double hd = h;
+    for (int i = 0; i < 3; ++i) {
+      r[i] += hd * T[i] + double(h * h6 * (k1[i] + k2[i] + k3[i]));
+      T[i] += double(h6 * (k1[i] + 2.0f * k2[i] + 2.0f * k3[i] + k4[i]));
+    }
+    if (limited) {
+      const float fac = (eps > 0.0f) ? step_factor_f(tol / eps) : 4.0f;
+      h_ctrl = fminf(h_max, h_ctrl * fac);
+    }
+  }
+  float B[3], Bt[3];
+  bool oof = false;
+  const float rf[3] = {float(r[0]), float(r[1]), float(r[2])};
+  const float Tf[3] = {float(T[0]), float(T[1]), float(T[2])};
+  fld.atf(rf, B, oof);
+  if (oof) st |= TKF_TRACK_OUT_OF_FIELD;
+  for (int i = 0; i < 3; ++i) Bt[i] = lk * B[i];
+  cross(Tf, Bt, kend);
+  return st;
+}
+
 // ------------------------------------------------------------------ material
-// Thin layer at surface s crossed with unit direction T: returns theta0^2 (Highland) and
-// lowers |q/p| by the Bethe mean loss (density effect: high-energy asymptote).
+// Thin layer at surface s crossed with unit direction T: returns theta0^2 (Highland) and lowers
+// |q/p| by the Bethe mean loss (density effect: high-energy asymptote). With p^2 = 1/lam^2:
+//   1/(beta p) = E lam^2,  1/beta^2 = 1 + m^2 lam^2,  beta^2 gamma^2 = p^2 / m^2.
+// Above beta gamma = exp(1/2 - ln(hbar omega_p / I)) the density term cancels ln(beta gamma) and
+// the Bethe bracket needs one logarithm: 1/2 ln(2 m_e W_max / I^2) - ln(hbar omega_p / I) + 1/2 - beta^2.
 __device__ __forceinline__ uint32_t material(const Surf& s, const MaterialDev& m, double mass, const double T[3],
                                              double& lam, double& th0sq) {
   th0sq = 0.0;
   if (!(s.t > 0.0)) return 0;
-  double x = s.t / fabs(dot3(s.n, T));
-  double mom = 1.0 / fabs(lam);
-  double E = sqrt(mom * mom + mass * mass);
-  double beta = mom / E;
-  double xx0 = x / s.x0;
-  double th0 = 0.0136 / (beta * mom) * sqrt(xx0) * (1.0 + 0.038 * log(xx0 / (beta * beta)));
-  th0sq = th0 * th0;
-  double beta2 = beta * beta;
-  double bg = mom / mass, bg2 = bg * bg;
-  double gamma = E / mass;
-  double me_m = kMe / mass;
-  double wmax = 2.0 * kMe * bg2 / (1.0 + 2.0 * gamma * me_m + me_m * me_m);
-  double I = m.i_ev * 1e-9;
-  double half_delta = fmax(0.0, m.log_hwp_over_i + log(bg) - 0.5);
-  double dedx = kBetheK * m.z_over_a / beta2 * (0.5 * log(2.0 * kMe * bg2 * wmax / (I * I)) - beta2 - half_delta);
-  double dE = dedx * m.rho * (x * 0.1) * 1e-3;
-  double E2 = E - dE;
-  if (!(E2 > mass)) return TKF_TRACK_PARTICLE_STOPPED;
-  lam = copysign(1.0 / sqrt(E2 * E2 - mass * mass), lam);
+  const double inv_cos = 1.0 / fabs(dot3(s.n, T));
+  const double x = s.t * inv_cos, xx0 = s.t_x0 * inv_cos;
+  const double l2 = lam * lam;
+  const double p2 = 1.0 / l2;
+  const double m2 = mass * mass;
+  const double E2 = p2 + m2, E = sqrt(E2);
+  const double inv_beta2 = 1.0 + m2 * l2;
+  const double beta2 = 1.0 / inv_beta2;
+  const double hl = 1.0 + 0.038 * log(xx0 * inv_beta2);
+  const double a = 0.0136 * E * l2;
+  th0sq = a * a * xx0 * hl * hl;
+  const double bg2 = p2 / m2;
+  const double me_m = kMe / mass;
+  const double wmax = 2.0 * kMe * bg2 / (1.0 + 2.0 * (E / mass) * me_m + me_m * me_m);
+  const double I = m.i_ev * 1e-9;
+  double bracket;
+  if (bg2 > m.bg2_density)  // density term active: ln(beta gamma) cancels
+    bracket = 0.5 * log(2.0 * kMe * wmax / (I * I)) - m.log_hwp_over_i + 0.5 - beta2;
+  else
+    bracket = 0.5 * log(2.0 * kMe * bg2 * wmax / (I * I)) - beta2;
+  const double dedx = kBetheK * m.z_over_a * inv_beta2 * bracket;
+  const double dE = dedx * m.rho * x * 1e-4;  // MeV cm^2/g * g/cm^3 * mm -> GeV
+  const double Ef = E - dE;
+  if (!(Ef > mass)) return TKF_TRACK_PARTICLE_STOPPED;
+  lam = copysign(1.0 / sqrt((Ef - mass) * (Ef + mass)), lam);
   return 0;
 }
 
+// Material in mixed precision: theta0^2 and the mean loss dE in FP32; the new q/p as
+// lam (1 - delta)^(-1/2) with delta = (2 E dE - dE^2) lam^2, i.e. lam + lam g in FP64 where
+// g = (1 - delta)^(-1/2) - 1 is formed in FP32 (series for small delta).
+__device__ __forceinline__ uint32_t material_mixed(const Surf& s, const MaterialDev& m, float mass, const float T[3],
+                                                   const float nf[3], double& lam, float& th0sq) {
+  th0sq = 0.0f;
+  if (!(s.t > 0.0)) return 0;
+  const float inv_cos = 1.0f / fabsf(dotr(nf, T));
+  const float x = float(s.t) * inv_cos, xx0 = float(s.t_x0) * inv_cos;
+  const float lf = float(lam), l2 = lf * lf;
+  const float p2 = 1.0f / l2, m2 = mass * mass;
+  const float E = sqrtf(p2 + m2);
+  const float inv_beta2 = 1.0f + m2 * l2, beta2 = 1.0f / inv_beta2;
+  const float hl = 1.0f + 0.038f * logf(xx0 * inv_beta2);
+  const float aa = 0.0136f * E * l2;
+  th0sq = aa * aa * xx0 * hl * hl;
+  const float bg2 = p2 / m2;
+  const float me_m = float(kMe) / mass;
+  const float wmax = 2.0f * float(kMe) * bg2 / (1.0f + 2.0f * (E / mass) * me_m + me_m * me_m);
+  const float I = float(m.i_ev * 1e-9);
+  float bracket;
+  if (bg2 > float(m.bg2_density))
+    bracket = 0.5f * logf(2.0f * float(kMe) * wmax / (I * I)) - float(m.log_hwp_over_i) + 0.5f - beta2;
+  else
+    bracket = 0.5f * logf(2.0f * float(kMe) * bg2 * wmax / (I * I)) - beta2;
+  const float dE = float(kBetheK * m.z_over_a) * inv_beta2 * bracket * float(m.rho) * x * 1e-4f;
+  if (!(dE < E - mass)) return TKF_TRACK_PARTICLE_STOPPED;
+  const float delta = (2.0f * E * dE - dE * dE) * l2;
+  const float g = delta < 0.01f
+                      ? delta * (0.5f + delta * (0.375f + delta * (0.3125f + delta * (0.2734375f + delta * 0.24609375f))))
+                      : rsqrtf(1.0f - delta) - 1.0f;
+  lam += lam * double(g);
+  return 0;
+}
+
+// sin and cos of a small angle: Taylor polynomials through x^9 / x^8 (truncation below
+// 1e-19 for |x| < 1/16), else the library sincos.
+__device__ __forceinline__ void small_sincos(double x, double& s, double& c) {
+  if (fabs(x) < 0.0625) {
+    const double x2 = x * x;
+    s = x * (1.0 + x2 * (-1.0 / 6 + x2 * (1.0 / 120 + x2 * (-1.0 / 5040 + x2 * (1.0 / 362880)))));
+    c = 1.0 + x2 * (-0.5 + x2 * (1.0 / 24 + x2 * (-1.0 / 720 + x2 * (1.0 / 40320 - x2 * (1.0 / 3628800)))));
+  } else {
+    sincos(x, &s, &c);
+  }
+}
+
+// sin x and cos x - 1 of a small angle in FP32 (absolute errors ~1e-8 |x| and ~1e-8 x^2),
+// FP64 sincos above 1/16.
+__device__ __forceinline__ void small_sincos_m1(double x, double& s, double& cm1) {
+  if (fabs(x) < 0.0625) {
+    const float xf = float(x);
+    const float h = sinf(0.5f * xf);
+    s = double(sinf(xf));
+    cm1 = double(-2.0f * h * h);
+  } else {
+    double c;
+    sincos(x, &s, &c);
+    cm1 = c - 1.0;
+  }
+}
+
 // ------------------------------------------------------------------ fit of one track
-template <class F>
+// For k >= 1 the absolute angles are never output, so the filtered direction is carried as
+// (sin phi, cos phi, sin theta, cos theta): the predicted values come from the propagated
+// direction and the update's increments are applied by the angle-addition identities.
+template <bool kMixed, class F>
 __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
   const uint32_t n = a.n_tracks;
   const uint32_t b0 = a.offsets[i], b1 = a.offsets[i + 1];
@@ -312,21 +621,21 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
     if (!fin) status = TKF_TRACK_NON_FINITE;
   }
 
-  double P[5][5];  // G_k C_k|k (smoother recursion)
-  Surf sp;         // surface of the previous measurement
+  double P[5][5];                // G_k C_k|k (smoother recursion)
+  Surf sp;                       // surface of the previous measurement
+  double sph = 0.0, cph = 1.0, sth = 1.0, cth = 0.0;  // filtered direction at sp
   double h_ctrl = a.opt.h_max;
+  float h_ctrl_f = float(a.opt.h_max);
 
   for (int k = 0; k < N && !(status & kFatal); ++k) {
     const uint32_t m = b0 + k;
-    const uint32_t id = a.sid[m];
     Surf s;
-    load_surf(a.surf, id, s);
+    load_surf(a.surf, a.sid[m], s);
     double J[5][5];
+    double sp2 = 0.0, cp2 = 1.0, st2 = 1.0, ct2 = 0.0;  // predicted direction at s (k >= 1)
     if (k > 0) {
-      // ---- material of the previous surface, then propagation (paper Sec. 3: muon hypothesis)
-      double sph, cph, sth, cth;
-      sincos(p[2], &sph, &cph);
-      sincos(p[3], &sth, &cth);
+      if constexpr (!kMixed) {
+      // ---- material of the previous surface (muon hypothesis), then propagation
       double T[3] = {sth * cph, sth * sph, cth};
       double lam = p[4], th0sq;
       status |= material(sp, a.mat, a.opt.mass, T, lam, th0sq);
@@ -339,11 +648,14 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
       status |= propagate(fld, a.opt, s, r, T, lam, dr, dT, h_ctrl, attempts, rejected, kend);
       if (status & kFatal) break;
       // ---- bound parameters at the target and the transport Jacobian (path correction)
-      double tnorm = sqrt(dot3(T, T));
-      double tn[3] = {T[0] / tnorm, T[1] / tnorm, T[2] / tnorm};
-      double st2 = sqrt(tn[0] * tn[0] + tn[1] * tn[1]);
-      double ct2 = tn[2], cp2 = tn[0] / st2, sp2 = tn[1] / st2;
-      double inv_nT = 1.0 / dot3(s.n, T);
+      const double inv_norm = 1.0 / sqrt(dot3(T, T));
+      const double tn[3] = {T[0] * inv_norm, T[1] * inv_norm, T[2] * inv_norm};
+      st2 = sqrt(tn[0] * tn[0] + tn[1] * tn[1]);
+      const double inv_st = 1.0 / st2;
+      ct2 = tn[2];
+      cp2 = tn[0] * inv_st;
+      sp2 = tn[1] * inv_st;
+      const double inv_nT = 1.0 / dot3(s.n, T);
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
         double x[3], t[3];
@@ -351,22 +663,22 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
           x[j] = (c == 0) ? sp.u[j] : (c == 1) ? sp.v[j] : dr[c - 2][j];
           t[j] = (c < 2) ? 0.0 : dT[c - 2][j];
         }
-        double ds = -dot3(s.n, x) * inv_nT;
+        const double ds = -dot3(s.n, x) * inv_nT;
         for (int j = 0; j < 3; ++j) {
           x[j] += T[j] * ds;
           t[j] += kend[j] * ds;
         }
         J[0][c] = dot3(s.u, x);
         J[1][c] = dot3(s.v, x);
-        J[2][c] = (-sp2 * t[0] + cp2 * t[1]) / st2;
+        J[2][c] = (-sp2 * t[0] + cp2 * t[1]) * inv_st;
         J[3][c] = ct2 * cp2 * t[0] + ct2 * sp2 * t[1] - st2 * t[2];
         J[4][c] = (c == 4) ? 1.0 : 0.0;
       }
-      double d[3] = {r[0] - s.c[0], r[1] - s.c[1], r[2] - s.c[2]};
+      const double d[3] = {r[0] - s.c[0], r[1] - s.c[1], r[2] - s.c[2]};
       p[0] = dot3(s.u, d);
       p[1] = dot3(s.v, d);
-      p[2] = atan2(tn[1], tn[0]);
-      p[3] = acos(tn[2]);
+      p[2] = 0.0;  // angles are carried as sines and cosines from here on
+      p[3] = 0.0;
       p[4] = lam;
       // ---- C_pred = J (C + Q) J^T, Q = diag(0, 0, th0^2/sin^2(theta), th0^2, 0)
       C[S(2, 2)] += th0sq / (sth * sth);
@@ -397,6 +709,113 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
           }
           C[S(r0, c0)] = acc;
         }
+      } else {
+      // ---- mixed precision: material, propagation, Jacobian and covariance transport in FP32
+      const float nprev[3] = {float(sp.n[0]), float(sp.n[1]), float(sp.n[2])};
+      const float Tm[3] = {float(sth * cph), float(sth * sph), float(cth)};
+      double lam = p[4];
+      float th0sq;
+      status |= material_mixed(sp, a.mat, float(a.opt.mass), Tm, nprev, lam, th0sq);
+      if (status & kFatal) break;
+      double T[3] = {sth * cph, sth * sph, cth};
+      double r[3];
+      for (int j = 0; j < 3; ++j) r[j] = sp.c[j] + p[0] * sp.u[j] + p[1] * sp.v[j];
+      const float fsth = float(sth), fcth = float(cth), fsph = float(sph), fcph = float(cph);
+      float dr[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+      float dT[3][3] = {{-fsth * fsph, fsth * fcph, 0.0f}, {fcth * fcph, fcth * fsph, -fsth}, {0, 0, 0}};
+      const float nf[3] = {float(s.n[0]), float(s.n[1]), float(s.n[2])};
+      float kend[3];
+      status |= propagate_mixed(fld, a.opt, s, nf, r, T, lam, dr, dT, h_ctrl_f, attempts, rejected, kend);
+      if (status & kFatal) break;
+      // direction at the target in FP64 from FP32-seeded Newton steps (relative error ~1e-14)
+      const double t2 = dot3(T, T), e2 = t2 - 1.0;
+      const double inv_norm = fabs(e2) < 1e-4 ? 1.0 - e2 * (0.5 - 0.375 * e2) : 1.0 / sqrt(t2);
+      const double tn[3] = {T[0] * inv_norm, T[1] * inv_norm, T[2] * inv_norm};
+      const double v = tn[0] * tn[0] + tn[1] * tn[1];
+      double inv_st;
+      if (v > 1e-12) {
+        const float yf = sqrtf(float(v));
+        double y = yf;
+        y = fma(fma(-y, y, v), double(0.5f / yf), y);
+        const float zf = 1.0f / float(y);
+        double z = zf;
+        z = z * fma(-y, z, 2.0);
+        st2 = y;
+        inv_st = z;
+      } else {
+        st2 = sqrt(v);
+        inv_st = 1.0 / st2;
+      }
+      ct2 = tn[2];
+      cp2 = tn[0] * inv_st;
+      sp2 = tn[1] * inv_st;
+      const float Tf[3] = {float(T[0]), float(T[1]), float(T[2])};
+      const float uf[3] = {float(s.u[0]), float(s.u[1]), float(s.u[2])};
+      const float vf[3] = {float(s.v[0]), float(s.v[1]), float(s.v[2])};
+      const float inv_nT = 1.0f / dotr(nf, Tf);
+      const float fst = float(st2), fct = float(ct2), fcp = float(cp2), fsp = float(sp2), finv_st = float(inv_st);
+      float Jf[5][5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        float x[3], t[3];
+        for (int j = 0; j < 3; ++j) {
+          x[j] = (c == 0) ? float(sp.u[j]) : (c == 1) ? float(sp.v[j]) : dr[c - 2][j];
+          t[j] = (c < 2) ? 0.0f : dT[c - 2][j];
+        }
+        const float ds = -dotr(nf, x) * inv_nT;
+        for (int j = 0; j < 3; ++j) {
+          x[j] += Tf[j] * ds;
+          t[j] += kend[j] * ds;
+        }
+        Jf[0][c] = dotr(uf, x);
+        Jf[1][c] = dotr(vf, x);
+        Jf[2][c] = (-fsp * t[0] + fcp * t[1]) * finv_st;
+        Jf[3][c] = fct * fcp * t[0] + fct * fsp * t[1] - fst * t[2];
+        Jf[4][c] = (c == 4) ? 1.0f : 0.0f;
+      }
+      const double d[3] = {r[0] - s.c[0], r[1] - s.c[1], r[2] - s.c[2]};
+      p[0] = dot3(s.u, d);
+      p[1] = dot3(s.v, d);
+      p[2] = 0.0;
+      p[3] = 0.0;
+      p[4] = lam;
+      // C_pred = J (C + Q) J^T in FP32
+      float Cf[15];
+#pragma unroll
+      for (int j = 0; j < 15; ++j) Cf[j] = float(C[j]);
+      Cf[S(2, 2)] += th0sq / (fsth * fsth);
+      Cf[S(3, 3)] += th0sq;
+      float M[5][5];
+#pragma unroll
+      for (int r0 = 0; r0 < 4; ++r0)
+#pragma unroll
+        for (int c0 = 0; c0 < 5; ++c0) {
+          float acc = 0.0f;
+#pragma unroll
+          for (int q = 0; q < 5; ++q) acc += Jf[r0][q] * Cf[S(q, c0)];
+          M[r0][c0] = acc;
+        }
+#pragma unroll
+      for (int c0 = 0; c0 < 5; ++c0) M[4][c0] = Cf[S(4, c0)];
+#pragma unroll
+      for (int r0 = 0; r0 < 5; ++r0)
+#pragma unroll
+        for (int c0 = r0; c0 < 5; ++c0) {
+          float acc;
+          if (c0 == 4) {
+            acc = M[r0][4];
+          } else {
+            acc = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) acc += M[r0][q] * Jf[c0][q];
+          }
+          C[S(r0, c0)] = double(acc);
+        }
+#pragma unroll
+      for (int r0 = 0; r0 < 5; ++r0)
+#pragma unroll
+        for (int c0 = 0; c0 < 5; ++c0) J[r0][c0] = double(Jf[r0][c0]);
+      }
       // ---- smoother: R = P J^T (in place; J row 4 is e_4)
 #pragma unroll
       for (int r0 = 0; r0 < 5; ++r0) {
@@ -453,13 +872,15 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
 #pragma unroll
         for (int c_ = r_; c_ < 5; ++c_) C[S(r_, c_)] = X[r_][c_] - Y[r_][0] * K[c_][0] - Y[r_][1] * K[c_][1];
     }
-    if (p[2] > kPi) p[2] -= 2.0 * kPi;
-    if (p[2] <= -kPi) p[2] += 2.0 * kPi;
-    if (!(p[3] > 0.0 && p[3] < kPi)) {
-      status |= TKF_TRACK_NON_FINITE;
-      break;
-    }
     if (k == 0) {
+      if (p[2] > kPi) p[2] -= 2.0 * kPi;
+      if (p[2] <= -kPi) p[2] += 2.0 * kPi;
+      if (!(p[3] > 0.0 && p[3] < kPi)) {
+        status |= TKF_TRACK_NON_FINITE;
+        break;
+      }
+      sincos(p[2], &sph, &cph);
+      sincos(p[3], &sth, &cth);
       // p_0|0 and C_0|0 start the smoothed sums; P_0 = C_0|0
 #pragma unroll
       for (int j = 0; j < 5; ++j) dl[j] = p[j];
@@ -470,6 +891,29 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
 #pragma unroll
         for (int c_ = 0; c_ < 5; ++c_) P[r_][c_] = C[S(r_, c_)];
     } else {
+      // filtered direction: predicted angles plus the update's increments p[2], p[3]
+      if constexpr (!kMixed) {
+        double sd, cd, se, ce;
+        small_sincos(p[2], sd, cd);
+        small_sincos(p[3], se, ce);
+        sph = sp2 * cd + cp2 * sd;
+        cph = cp2 * cd - sp2 * sd;
+        sth = st2 * ce + ct2 * se;
+        cth = ct2 * ce - st2 * se;
+      } else {
+        // sin and (cos - 1) of the small increments in FP32, applied to the FP64 anchors
+        double sd, cd1, se, ce1;
+        small_sincos_m1(p[2], sd, cd1);
+        small_sincos_m1(p[3], se, ce1);
+        sph = sp2 + (sp2 * cd1 + cp2 * sd);
+        cph = cp2 + (cp2 * cd1 - sp2 * sd);
+        sth = st2 + (st2 * ce1 + ct2 * se);
+        cth = ct2 + (ct2 * ce1 - st2 * se);
+      }
+      if (!(sth > 0.0)) {  // theta left (0, pi)
+        status |= TKF_TRACK_NON_FINITE;
+        break;
+      }
       // W = R H^T S^-1; p_0|N += W r; C_0|N -= W (R H^T)^T; P = R - R H^T K^T
       double W[5][2];
 #pragma unroll
@@ -502,12 +946,12 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
     bool spd = true;
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
-      double d = L[S(j, j)];
+      const double d = L[S(j, j)];
       spd = spd && (d > 0.0);
-      double inv = 1.0 / d;
+      const double inv = 1.0 / d;
 #pragma unroll
       for (int r_ = j + 1; r_ < 5; ++r_) {
-        double f = L[S(j, r_)] * inv;
+        const double f = L[S(j, r_)] * inv;
 #pragma unroll
         for (int c_ = r_; c_ < 5; ++c_) L[S(r_, c_)] -= f * L[S(j, c_)];
       }
@@ -541,33 +985,117 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
   }
 }
 
-template <class F>
-__global__ void __launch_bounds__(128) fit_kernel(FitArgs a, F fld) {
+// ------------------------------------------------------------------ track ordering
+// Counting sort of the tracks by key = (most measurements first, then lowest seed pT first):
+// warps then hold tracks with the same number of measurements and similar step counts, and
+// the work queue hands out the longest tracks first.
+constexpr int kPtBins = 16;
+constexpr int kNBins = 64;
+constexpr int kKeyBins = kPtBins * kNBins;
+
+__global__ void __launch_bounds__(256) order_keys_kernel(const uint32_t* __restrict__ offsets,
+                                                         const double* __restrict__ seed_par, uint32_t n,
+                                                         uint32_t* __restrict__ keys, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[kKeyBins];
+  for (int b = threadIdx.x; b < kKeyBins; b += blockDim.x) h[b] = 0;
+  __syncthreads();
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n_tracks) return;
-  fit_track(a, fld, i);
+  if (i < n) {
+    const uint32_t b0 = offsets[i], b1 = offsets[i + 1];
+    const uint32_t nh = b1 >= b0 ? min(b1 - b0, uint32_t(kNBins - 1)) : 0u;
+    const float qop = float(seed_par[size_t(4) * n + i]);
+    const float sth = fabsf(sinf(float(seed_par[size_t(3) * n + i])));
+    const float pt = (qop != 0.0f) ? sth / fabsf(qop) : 1e30f;
+    int pb = (pt > 0.0f) ? int(floorf(log2f(pt))) + 4 : 0;  // octaves from 1/16 GeV
+    pb = pb < 0 ? 0 : (pb >= kPtBins ? kPtBins - 1 : pb);
+    const uint32_t key = (uint32_t(kNBins - 1) - nh) * kPtBins + uint32_t(pb);
+    keys[i] = key;
+    atomicAdd(&h[key], 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < kKeyBins; b += blockDim.x)
+    if (h[b]) atomicAdd(&hist[b], h[b]);
+}
+
+// exclusive scan of the kKeyBins histogram in place (one block of kKeyBins threads)
+__global__ void __launch_bounds__(kKeyBins) order_scan_kernel(uint32_t* __restrict__ hist) {
+  __shared__ uint32_t v[kKeyBins];
+  const int t = threadIdx.x;
+  v[t] = hist[t];
+  __syncthreads();
+  for (int off = 1; off < kKeyBins; off <<= 1) {
+    const uint32_t x = t >= off ? v[t - off] : 0u;
+    __syncthreads();
+    v[t] += x;
+    __syncthreads();
+  }
+  hist[t] = v[t] - hist[t];
+}
+
+__global__ void __launch_bounds__(256) order_scatter_kernel(const uint32_t* __restrict__ keys, uint32_t n,
+                                                            uint32_t* __restrict__ base, uint32_t* __restrict__ perm) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) perm[atomicAdd(&base[keys[i]], 1u)] = i;
+}
+
+// Persistent fit: each warp takes the next 32 tracks of the ordered list from a global counter.
+template <bool kMixed, class F>
+__global__ void __launch_bounds__(128) fit_persistent_kernel(FitArgs a, F fld, const uint32_t* __restrict__ perm,
+                                                             uint32_t* __restrict__ counter) {
+  const uint32_t lane = threadIdx.x & 31u;
+  for (;;) {
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(counter, 32u);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= a.n_tracks) break;
+    const uint32_t j = base + lane;
+    if (j < a.n_tracks) fit_track<kMixed>(a, fld, perm[j]);
+  }
+}
+
+template <class F>
+cudaError_t launch_with(const FitArgs& a, const F& fld, bool mixed, const Workspace& ws, int blocks,
+                        cudaStream_t stream) {
+  const uint32_t n = a.n_tracks;
+  cudaError_t e = cudaMemsetAsync(ws.counter, 0, sizeof(uint32_t) * (1 + kKeyBins), stream);
+  if (e != cudaSuccess) return e;
+  const unsigned g256 = (n + 255) / 256;
+  order_keys_kernel<<<g256, 256, 0, stream>>>(a.offsets, a.seed_par, n, ws.keys, ws.hist);
+  order_scan_kernel<<<1, kKeyBins, 0, stream>>>(ws.hist);
+  order_scatter_kernel<<<g256, 256, 0, stream>>>(ws.keys, n, ws.hist, ws.perm);
+  if (mixed)
+    fit_persistent_kernel<true><<<blocks, 128, 0, stream>>>(a, fld, ws.perm, ws.counter);
+  else
+    fit_persistent_kernel<false><<<blocks, 128, 0, stream>>>(a, fld, ws.perm, ws.counter);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_fit(const FitArgs& a, const FieldDev& f, int precision, cudaStream_t stream) {
-  (void)precision;
+size_t workspace_bytes(uint32_t n_tracks) {
+  return 256 + sizeof(uint32_t) * (kKeyBins + 2 * size_t(n_tracks)) + 256;
+}
+
+Workspace carve_workspace(void* base, uint32_t n_tracks) {
+  Workspace w;
+  uint32_t* p = static_cast<uint32_t*>(base);
+  w.counter = p;          // 1 word, followed directly by the histogram (one memset clears both)
+  w.hist = p + 1;
+  w.keys = p + 1 + kKeyBins;
+  w.perm = w.keys + n_tracks;
+  return w;
+}
+
+cudaError_t launch_fit(const FitArgs& a, const FieldDev& f, int precision, const Workspace& ws, int sm_count,
+                       cudaStream_t stream) {
   if (a.n_tracks == 0) return cudaSuccess;
-  const int block = 128;
-  const unsigned grid = (a.n_tracks + block - 1) / block;
+  const bool mixed = precision == TKF_MIXED;
+  const int blocks = 2 * sm_count;  // 255 registers x 128 threads: two blocks per SM
   if (f.kind == TKF_FIELD_UNIFORM) {
-    if (f.b[0] == 0.0 && f.b[1] == 0.0) {
-      FieldUniformZ u{f.b[2]};
-      fit_kernel<<<grid, block, 0, stream>>>(a, u);
-    } else {
-      FieldUniform u{{f.b[0], f.b[1], f.b[2]}};
-      fit_kernel<<<grid, block, 0, stream>>>(a, u);
-    }
-  } else {
-    FieldGrid g{f.grid, f.nr, f.nz, f.r0, f.z0, f.inv_dr, f.inv_dz};
-    fit_kernel<<<grid, block, 0, stream>>>(a, g);
+    if (f.b[0] == 0.0 && f.b[1] == 0.0) return launch_with(a, FieldUniformZ{f.b[2]}, mixed, ws, blocks, stream);
+    return launch_with(a, FieldUniform{{f.b[0], f.b[1], f.b[2]}}, mixed, ws, blocks, stream);
   }
-  return cudaGetLastError();
+  return launch_with(a, FieldGrid{f.grid, f.nr, f.nz, f.r0, f.z0, f.inv_dr, f.inv_dz}, mixed, ws, blocks, stream);
 }
 
 }  // namespace tkf

@@ -18,6 +18,7 @@ constexpr int kSurfStride = 16;
 struct MaterialDev {
   double z_over_a, i_ev, rho, hwp_ev;
   double log_hwp_over_i;  // ln(hbar omega_p / I)
+  double bg2_density;     // (beta gamma)^2 above which the density-effect term is positive
 };
 
 struct FieldDev {
@@ -58,14 +59,29 @@ struct FitArgs {
   OptionsDev opt;
 };
 
-// Launches the fit of every track in `a` on `stream` with `field`.
-cudaError_t launch_fit(const FitArgs& a, const FieldDev& field, int precision, cudaStream_t stream);
+// Scratch of one fit launch: work counter, key histogram, sort keys, track permutation.
+struct Workspace {
+  uint32_t* counter = nullptr;
+  uint32_t* hist = nullptr;
+  uint32_t* keys = nullptr;
+  uint32_t* perm = nullptr;
+};
+size_t workspace_bytes(uint32_t n_tracks);
+Workspace carve_workspace(void* base, uint32_t n_tracks);
+
+// Enqueues the fit of every track in `a` on `stream`: track ordering, then the persistent fit.
+cudaError_t launch_fit(const FitArgs& a, const FieldDev& field, int precision, const Workspace& ws, int sm_count,
+                       cudaStream_t stream);
 
 }  // namespace tkf
 
 struct tkf_context_s {
   int device = 0;
+  int sm_count = 0;
   std::string last_error;
+  // fit workspace (ordering scratch), grown on demand and reused by later calls
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
   // staging for tkf_fit_host
   void* stage = nullptr;
   size_t stage_bytes = 0;

@@ -32,7 +32,7 @@ def test_option_defaults():
     o = tkf.FitOptions()
     tkf.lib().tkf_fit_options_default(ctypes.byref(o))
     assert (o.precision, o.step_mode, o.tol, o.h_max, o.h_min, o.surf_tol, o.max_steps) == \
-        (0, 0, 1e-4, 1000.0, 1e-4, 1e-9, 10000)
+        (0, 0, 1e-4, 1000.0, 1e-4, 1e-2, 10000)
     assert abs(o.mass - 0.1056583755) < 1e-12
 
 

@@ -206,3 +206,51 @@ def test_invalid_arguments_enqueue_nothing(ctx):
     bad[1, 0] = 2.0
     with pytest.raises(tkf.TkfError):
         tkf.Geometry(ctx, bad, np.zeros((2, 3)), 0.3, 93.7)
+
+
+# ---------------------------------------------------------------- mixed precision
+MIXED_TOL_SIGMA = 1e-3   # |dp_i| <= 1e-3 sigma_i
+MIXED_TOL_CHI2 = 1e-3    # relative
+
+
+def check_mixed(g, o, max_bad_frac=1e-3):
+    """Mixed path vs the FP64 oracle: parameters within 1e-3 sigma, chi2 within 1e-3 relative."""
+    ok64 = (o.status & 0x39F) == 0
+    assert np.array_equal(g["status"], o.status) or np.mean(g["status"] != o.status) < 1e-3
+    good = ok64 & (g["status"] == o.status)
+    C = oracle.unpack(o.cov[good])
+    sig = np.sqrt(np.einsum("nii->ni", C))
+    dp = g["par"][good] - o.par[good]
+    dp[:, 2] = (dp[:, 2] + np.pi) % (2 * np.pi) - np.pi
+    ds = np.abs(dp) / sig
+    dchi = np.abs(g["chi2"][good] - o.chi2[good]) / np.maximum(o.chi2[good], 1.0)
+    bad = (ds.max(1) > MIXED_TOL_SIGMA) | (dchi > MIXED_TOL_CHI2)
+    stats = {"n": int(good.sum()), "max_dp_over_sigma": float(ds.max()), "p99_dp_over_sigma": float(np.quantile(ds.max(1), 0.99)),
+             "max_rel_chi2": float(dchi.max()), "bad": int(bad.sum())}
+    print(stats)
+    assert bad.sum() <= max_bad_frac * good.sum(), stats
+    return stats
+
+
+MIXED = tkf.Options(precision=tkf.MIXED)
+
+
+@pytest.mark.parametrize("name", ["telescope", "barrel", "solenoid_map"])
+def test_mixed_precision_within_1e3_sigma(ctx, name):
+    if name == "telescope":
+        w = synth.telescope_workload(2000, seed=0)
+    elif name == "barrel":
+        w = synth.barrel_workload(n_events=2, lo=1500, hi=2500, seed=2)
+    else:
+        w = synth.solenoid_muon_workload(3000, seed=3)
+    g = run_gpu(ctx, w, opts=tkf.Options(precision=tkf.MIXED, mass=w.mass))
+    o = run_oracle(w)
+    check_mixed(g, o)
+
+
+def test_mixed_edge_cases_status(ctx):
+    w, tr = _edge_tracks()
+    g = run_gpu(ctx, w, tr, opts=MIXED)
+    o = run_oracle(w, tr)
+    np.testing.assert_array_equal(g["status"], o.status)
+    np.testing.assert_array_equal(g["ndf"], o.ndf)
