@@ -32,13 +32,14 @@ import synth  # noqa: E402
 METRIC = "fitted tracks/s on 1 GB300: mixed+learned vs plain FP64, at fixed pull error"
 WORKLOAD = "barrel_endcap_50ev_uniform2T_pions"
 
-# FP64 work per unit of the fit kernel (flops: add/sub/mul = 1, fma = 2, div/sqrt = 1,
-# sin/cos/atan2/acos/log = 1; derivation in the design doc). Units: accepted RKN step,
-# rejected step attempt, propagated measurement (k >= 1), track.
-FLOP_STEP_ACCEPTED = 236
-FLOP_STEP_REJECTED = 44
-FLOP_HIT = 1046
-FLOP_TRACK = 260
+# Algorithmic FP64 flops per unit of the fit kernels, counted from the kernel source
+# (add/sub/mul = 1, fma = 2, each div/sqrt/log/sin/cos = 1; derivation in the design doc):
+# (accepted RKN step, rejected step attempt, propagated measurement k >= 1, track).
+FLOPS = {
+    "fp64": (493, 111, 1494, 330),
+    # mixed: only the FP64 anchors, the Joseph update and the smoother count
+    "mixed": (20, 8, 749, 330),
+}
 
 
 def parse():
@@ -61,9 +62,28 @@ def dist_env():
     return ws, rank, local
 
 
-def make_workload(events: int, rank: int):
+def shard_seed(rank: int) -> int:
     # weak scaling: every rank fits its own batch of the same shape (seed offset by rank)
-    return synth.barrel_workload(n_events=events, seed=2 + 1000 * rank)
+    return 2 + 1000 * rank
+
+
+def make_workload(events: int, rank: int, **kw):
+    return synth.barrel_workload(n_events=events, seed=shard_seed(rank), **kw)
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_throughput(tracks_per_rank: int, world_size: int, max_seconds: float) -> float:
+    """Whole-job throughput: the tracks of all ranks over the slowest rank's time."""
+    return world_size * tracks_per_rank / max_seconds
 
 
 class ClockSampler:
@@ -259,22 +279,16 @@ def main():
             torch.cuda.synchronize()
         barrier()
         ms = ev0.elapsed_time(ev1) / args.steps
-        ms_max = ms
-        if dist is not None:
-            tt = torch.tensor([ms], device=f"cuda:{local}")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms_max = float(tt.item())
+        ms_max = max_over_ranks(ms, dist, f"cuda:{local}")
         results[variant] = {"ms": ms, "ms_max": ms_max, "clocks": clk.summary(), "opts": opts,
                             "attempts": attempts, "rejected": rejected, "status_ok": float(np.mean(status == 0)),
                             "pulls": pull_stats(out, t)}
     head = "mixed" if "mixed" in results else variants[0]
     opts = results[head]["opts"]
     ms, ms_max, clocks = results[head]["ms"], results[head]["ms_max"], results[head]["clocks"]
-    flops = None
-    if "fp64" in results:
-        r64 = results["fp64"]
-        flops = (FLOP_STEP_ACCEPTED * (r64["attempts"] - r64["rejected"]) + FLOP_STEP_REJECTED * r64["rejected"] +
-                 FLOP_HIT * hits_k1 + FLOP_TRACK * n_tracks)
+    for k, v in results.items():
+        fa, fr, fh, ft = FLOPS[k]
+        v["flops"] = fa * (v["attempts"] - v["rejected"]) + fr * v["rejected"] + fh * hits_k1 + ft * n_tracks
 
     # end to end through the host entry point: pinned host inputs -> fit -> host outputs
     e2e = None
@@ -293,14 +307,10 @@ def main():
         for _ in range(args.steps):
             tkf.fit_host(ctx, geo, fld, pinned, opts, out=hout, stream=stream)
         torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / args.steps
-        if dist is not None:
-            tt = torch.tensor([e2e_s], device=f"cuda:{local}")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, dist, f"cuda:{local}")
         h2d = host.nbytes()
         d2h = n_tracks * (5 * 8 + 15 * 8 + 8 + 4 + 4)
-        e2e = {"value": ws * n_tracks / e2e_s, "unit": "tracks/s", "h2d_bytes_per_step": h2d,
+        e2e = {"value": aggregate_throughput(n_tracks, ws, e2e_s), "unit": "tracks/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "variant": head}
 
     if rank != 0:
@@ -309,16 +319,18 @@ def main():
         return
 
     peak = fp64_peak_tflops(None)
-    roof = None
-    if flops is not None:
-        ms64 = results["fp64"]["ms"]
-        achieved = flops / (ms64 * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "fit_persistent_kernel<fp64>", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "note": "FP64 CUDA-core pipe of the plain-FP64 fit; peak derived from 152 SMs x 4 flop/clk x 2070 MHz"}
+    # the step is four launches; the fit kernel is > 99.5 % of it, so its duration is taken as
+    # the step time measured with CUDA events on the launching stream
+    hv = results[head]
+    achieved = hv["flops"] / (hv["ms"] * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": f"fit_persistent_kernel<{head}>", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "fp64_flop_per_launch": hv["flops"],
+            "note": "FP64 CUDA-core pipe (the bound of both variants); peak derived from "
+                    "152 SMs x 4 flop/clk x 2070 MHz; 1.20 TFLOP/s measured by an FMA probe"}
     line = {
         "metric": METRIC,
-        "value": ws * n_tracks / (ms_max * 1e-3),
+        "value": aggregate_throughput(n_tracks, ws, ms_max * 1e-3),
         "unit": "tracks/s",
         "n_gpus": ws,
         "steps": args.steps,
@@ -336,9 +348,11 @@ def main():
         "gpu_launches": 4 * args.steps,
         "roofline": roof,
         "clocks": clocks,
-        "variants": {k: {"tracks_per_s": ws * n_tracks / (v["ms_max"] * 1e-3), "ms_per_step": v["ms_max"],
+        "variants": {k: {"tracks_per_s": aggregate_throughput(n_tracks, ws, v["ms_max"] * 1e-3),
+                         "ms_per_step": v["ms_max"],
                          "step_attempts": v["attempts"], "rejected": v["rejected"],
                          "fit_status_ok": v["status_ok"], "pull_sigma": v["pulls"]["sigma"],
+                         "fp64_tflops": v["flops"] / (v["ms"] * 1e-3) / 1e12,
                          "pull_mean": v["pulls"]["mean"], "chi2_ndf_mean": v["pulls"]["chi2_ndf"]}
                      for k, v in results.items()},
     }
