@@ -216,6 +216,27 @@ tkf_status tkf_fit_host(tkf_context ctx, tkf_geometry geo, tkf_field field,
                         const tkf_fit_options* opts, const tkf_fit_inputs* host_in,
                         const tkf_fit_outputs* host_out, void* stream);
 
+/* ---------------------------------------------------------------------------- allocation-free fit */
+
+/* The paper has no counterpart to this entry point. It is the fit of tkf_fit for callers that
+ * may not allocate device memory while running: for example an online trigger or
+ * reconstruction process that reserves all of its GPU memory at start-up and forbids later
+ * allocations, or a host framework whose own memory pool owns the device. It calls no
+ * cudaMalloc, cudaFree or other allocating routine: its scratch (work counter, sort keys and
+ * track permutation, 16 MB) is a static device array of the library, held on every GPU that
+ * loads the library until the process exits.
+ *   - Batches are limited to TKF_NOALLOC_MAX_TRACKS tracks; a larger n_tracks returns
+ *     TKF_ERR_INVALID_ARG with a message, and nothing is enqueued.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *     once for that device; make that first call before any stream capture.
+ *   - Every call on a device shares the one array: calls whose work overlaps on the GPU
+ *     (different streams, or different contexts, without ordering) race and give wrong
+ *     results. Serialize them.
+ * Arguments, outputs and the other errors are those of tkf_fit. */
+#define TKF_NOALLOC_MAX_TRACKS 2097152u
+tkf_status tkf_fit_noalloc(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf_fit_options* opts,
+                           const tkf_fit_inputs* in, const tkf_fit_outputs* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -139,7 +139,11 @@ _SIGNATURES = {
                                ctypes.POINTER(FitOutputs), _VP]),
     "tkf_fit_host": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(FitOptions),
                                     ctypes.POINTER(FitInputs), ctypes.POINTER(FitOutputs), _VP]),
+    "tkf_fit_noalloc": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(FitOptions),
+                                       ctypes.POINTER(FitInputs), ctypes.POINTER(FitOutputs), _VP]),
 }
+
+NOALLOC_MAX_TRACKS = 2097152
 
 
 def lib(build_if_missing: bool = True):
@@ -422,6 +426,21 @@ def fit_host(ctx: Context, geo: Geometry, field: Field, batch: Batch, opts: Opti
     _check(lib().tkf_fit_host(ctx.handle, geo.handle, field.handle, ctypes.byref(o),
                               ctypes.byref(_inputs_struct(batch)), ctypes.byref(_outputs_struct(out)),
                               _VP(s) if s else None), ctx.handle, "tkf_fit_host")
+    return out
+
+
+def fit_noalloc(ctx: Context, geo: Geometry, field: Field, batch: Batch, out: Result,
+                opts: Options | None = None, stream=None) -> Result:
+    """tkf_fit_noalloc: the fit of ``fit`` for callers that may not allocate device memory while
+    running; its scratch is a static array of the library (at most NOALLOC_MAX_TRACKS tracks per
+    call). ``out`` must be preallocated CUDA tensors. Calls that overlap on the GPU race."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(batch.offsets.device)
+    o = (opts or Options()).c()
+    _check(lib().tkf_fit_noalloc(ctx.handle, geo.handle, field.handle, ctypes.byref(o),
+                                 ctypes.byref(_inputs_struct(batch)), ctypes.byref(_outputs_struct(out)),
+                                 _VP(stream.cuda_stream)), ctx.handle, "tkf_fit_noalloc")
     return out
 
 

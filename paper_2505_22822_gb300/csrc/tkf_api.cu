@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -436,3 +437,62 @@ tkf_status tkf_fit_host(tkf_context ctx, tkf_geometry geo, tkf_field field, cons
 }
 
 }  // extern "C"
+
+// ============================================================================ allocation-free fit
+// Some callers cannot allocate device memory once they are running: an online trigger or
+// reconstruction process that reserves all of its GPU memory at start-up and forbids later
+// allocations (their latency and fragmentation are not allowed on the event path), or a host
+// framework whose own pool allocator owns the whole device. tkf_fit_noalloc serves them: its
+// scratch (work counter, key histogram, sort keys, track permutation) is this file-scope
+// array, which every GPU that loads the library holds until the process exits.
+
+namespace {
+
+constexpr uint32_t kNoallocMaxTracks = TKF_NOALLOC_MAX_TRACKS;
+constexpr size_t kNoallocWords = 1 + 1024 + 2 * size_t(kNoallocMaxTracks) + 64;
+
+static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoallocWords];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on `device` (which must be current); looked up once per
+// device. Host code cannot use the array's name as a device address.
+cudaError_t noalloc_scratch(int device, void** out) {
+  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[device]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[device] = ptr;
+  }
+  *out = g_noalloc_ptr[device];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" tkf_status tkf_fit_noalloc(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf_fit_options* o,
+                                      const tkf_fit_inputs* in, const tkf_fit_outputs* out, void* stream) {
+  tkf_status s = check_common(ctx, geo, field, o, in, out, "tkf_fit_noalloc");
+  if (s != TKF_OK || in->n_tracks == 0) return s;
+  if (in->n_tracks > kNoallocMaxTracks)
+    return fail(ctx, TKF_ERR_INVALID_ARG,
+                "tkf_fit_noalloc: n_tracks " + std::to_string(in->n_tracks) + " exceeds the maximum " +
+                    std::to_string(kNoallocMaxTracks) + " of the static scratch; use tkf_fit or split the batch");
+  if (o->step_mode == TKF_STEP_LEARNED)
+    return fail(ctx, TKF_ERR_UNSUPPORTED, "tkf_fit_noalloc: learned step proposals are not available in this build");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(ctx, TKF_ERR_DEVICE, "tkf_fit_noalloc: cudaSetDevice failed");
+  void* scratch = nullptr;
+  cudaError_t e = noalloc_scratch(ctx->device, &scratch);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_noalloc: cudaGetSymbolAddress");
+  tkf::FitArgs a = make_args(geo, o, in, out);
+  // the launch clears the counter and histogram before use (the array keeps the last call's data)
+  tkf::Workspace ws = tkf::carve_workspace(scratch, in->n_tracks);
+  e = tkf::launch_fit(a, field->f, o->precision, ws, ctx->sm_count, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_noalloc: launch");
+  return TKF_OK;
+}
