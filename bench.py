@@ -39,6 +39,7 @@ FLOPS = {
     "fp64": (493, 111, 1494, 330),
     # mixed: only the FP64 anchors, the Joseph update and the smoother count
     "mixed": (20, 8, 749, 330),
+    "mixed_learned": (20, 8, 749, 330),
 }
 
 
@@ -48,7 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--variant", default="auto", choices=["auto", "fp64", "mixed"])
+    ap.add_argument("--variant", default="auto", choices=["auto", "fp64", "mixed", "mixed_learned"])
     ap.add_argument("--events", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -254,12 +255,26 @@ def main():
     fld = tkf.Field.from_desc(ctx, w.field)
     host = tkf.Batch.from_arrays(t.offsets, t.meas, t.sid, t.seed_par, t.seed_cov)
     dev = host.to(f"cuda:{local}")
-    variants = ["fp64", "mixed"] if args.variant == "auto" else [args.variant]
+    variants = ["fp64", "mixed", "mixed_learned"] if args.variant == "auto" else [args.variant]
     stream = torch.cuda.current_stream()
     hits_k1 = int((np.diff(t.offsets.astype(np.int64)) - 1).clip(min=0).sum())
+    proposer, learn_info = None, None
+    if any(v.endswith("learned") for v in variants):
+        # the step proposer is trained before timing, on records of seed-disjoint tracks
+        from paper_2505_22822_gb300 import learn
+        tw = synth.barrel_workload(n_events=5, seed=10_000 + shard_seed(rank))
+        tt = tw.tracks
+        tb = tkf.Batch.from_arrays(tt.offsets, tt.meas, tt.sid, tt.seed_par, tt.seed_cov).to(f"cuda:{local}")
+        t0 = time.perf_counter()
+        proposer, info = learn.build_proposer(ctx, geo, fld, tb, tkf.MIXED, mass=w.mass)
+        learn_info = {"records": info["records"], "final_loss": round(info["epoch_loss"][-1], 4),
+                      "bias_shift": round(info["bias_shift"], 4), "train_s": round(time.perf_counter() - t0, 2),
+                      "tracks": tt.n_tracks}
     results = {}
     for variant in variants:
-        opts = tkf.Options(precision=tkf.MIXED if variant == "mixed" else tkf.FP64, mass=w.mass)
+        opts = tkf.Options(precision=tkf.FP64 if variant == "fp64" else tkf.MIXED, mass=w.mass)
+        if variant.endswith("learned"):
+            opts.step_mode, opts.mlp = tkf.STEP_LEARNED, proposer
         out = tkf.alloc_outputs(n_tracks, dev.offsets.device, steps=True)
         for _ in range(args.warmup):
             tkf.fit(ctx, geo, fld, dev, opts, out=out, stream=stream)
@@ -283,7 +298,7 @@ def main():
         results[variant] = {"ms": ms, "ms_max": ms_max, "clocks": clk.summary(), "opts": opts,
                             "attempts": attempts, "rejected": rejected, "status_ok": float(np.mean(status == 0)),
                             "pulls": pull_stats(out, t)}
-    head = "mixed" if "mixed" in results else variants[0]
+    head = variants[-1]
     opts = results[head]["opts"]
     ms, ms_max, clocks = results[head]["ms"], results[head]["ms_max"], results[head]["clocks"]
     for k, v in results.items():
@@ -339,12 +354,12 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if head == "fp64" else "f32+f64",
+        "dtype": "f64" if head == "fp64" else "f32+f64 (+bf16 weights)",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "variant": head, "tracks_per_gpu": n_tracks,
                    "measurements_per_gpu": n_meas, "events_per_gpu": args.events,
                    "field": "uniform 2 T along z", "l2": "inputs 0.41 GB > L2, no flush",
-                   "step_mode": "adaptive (learned proposer not in this build)"},
+                   "step_mode": "learned starting step + adaptive" if head.endswith("learned") else "adaptive"},
         "gpu_launches": 4 * args.steps,
         "roofline": roof,
         "clocks": clocks,
@@ -356,8 +371,11 @@ def main():
                          "pull_mean": v["pulls"]["mean"], "chi2_ndf_mean": v["pulls"]["chi2_ndf"]}
                      for k, v in results.items()},
     }
-    if "fp64" in results and "mixed" in results:
-        line["speedup_vs_fp64"] = results["fp64"]["ms_max"] / results["mixed"]["ms_max"]
+    if "fp64" in results:
+        line["speedup_vs_fp64"] = {k: results["fp64"]["ms_max"] / v["ms_max"] for k, v in results.items()
+                                   if k != "fp64"}
+    if learn_info:
+        line["learned_proposer"] = learn_info
     if e2e:
         line["e2e"] = e2e
     if not args.no_cpu_baseline:

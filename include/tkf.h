@@ -147,7 +147,7 @@ typedef enum tkf_precision {
 
 typedef enum tkf_step_mode {
   TKF_STEP_ADAPTIVE = 0, /* RKN step-size control from the local error estimate */
-  TKF_STEP_LEARNED = 1   /* a small MLP proposes each step; the error estimate still judges */
+  TKF_STEP_LEARNED = 1   /* a small MLP proposes the starting step; the error estimate judges */
 } tkf_step_mode;
 
 typedef struct tkf_fit_options {
@@ -160,6 +160,15 @@ typedef struct tkf_fit_options {
   uint32_t max_steps;  /* step attempts per surface (default 10000) */
   double mass;         /* particle hypothesis, GeV (default: muon, 0.1056583755) */
   tkf_mlp mlp;         /* step proposer for TKF_STEP_LEARNED, else NULL */
+  /* Optional training-record capture (TKF_STEP_ADAPTIVE only): for every accepted RKN step
+   * that the step-size control limited (the steps a proposer is asked about) and that has a
+   * nonzero error estimate, TKF_MLP_RECORD floats are appended to `records` (DEVICE,
+   * record_capacity records): the TKF_MLP_INPUTS network inputs at the step start and the
+   * label ln(|h| (tol/eps)^(1/4) / mm), the largest step within tolerance. *record_count
+   * (DEVICE, zeroed by the caller) counts every record, also those beyond the capacity. */
+  float* records;
+  uint32_t record_capacity;
+  uint32_t* record_count;
 } tkf_fit_options;
 
 void tkf_fit_options_default(tkf_fit_options* opts);
@@ -215,6 +224,63 @@ tkf_status tkf_fit(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf
 tkf_status tkf_fit_host(tkf_context ctx, tkf_geometry geo, tkf_field field,
                         const tkf_fit_options* opts, const tkf_fit_inputs* host_in,
                         const tkf_fit_outputs* host_out, void* stream);
+
+/* ---------------------------------------------------------------------------- learned step proposer */
+
+/* The benchmark spec's learned part (the paper has no learned component): before a track's first
+ * RKN step, where the step-size control has no error estimate yet, a network proposes the
+ * control's starting value from the seed state and the field at the first surface, toward the
+ * second (the plain control starts from h_max and sheds it by rejected steps). From then on the
+ * plain control adapts the value from the error estimates, and every step is accepted only if
+ * the RKN error estimate passes, so proposals never loosen the tolerance. (Proposing every
+ * control-limited step was measured to take more steps: once it exists, the control's own
+ * estimate from the last step's error is the better predictor.) The proposals run in a
+ * separate pre-pass kernel over all tracks.
+ *
+ * Network: TKF_MLP_INPUTS inputs -> 64 SiLU -> 64 SiLU -> 1 output, the natural log of the
+ * largest step within tolerance in mm (proposal = 0.9 exp(output), clamped to [h_min, h_max]).
+ * Inputs, at the step start: u, v, n components of (r - c_target) / 1000 mm; u, v, n components
+ * of the direction; q/p (e/GeV); B / 2 T (global x, y, z); ln(last accepted step / mm) / 5; the
+ * straight-line path to the target plane / 1000 mm, clamped to [-2, 2].
+ * Parameter layout (TKF_MLP_PARAMS values): W1 [64][12] row-major, b1 [64], W2 [64][64],
+ * b2 [64], w3 [64], b3 [1]. Inference uses BF16 weights and FP32 arithmetic.
+ * For the starting proposal the inputs are taken at the seed state on the first surface, with
+ * the second surface as the target and h_max as the last step. */
+#define TKF_MLP_INPUTS 12
+#define TKF_MLP_RECORD 13
+#define TKF_MLP_PARAMS 5057
+
+/* Uploads BF16 weights (host, TKF_MLP_PARAMS 16-bit patterns) into a handle for
+ * tkf_fit_options.mlp. Errors: TKF_ERR_INVALID_ARG, TKF_ERR_OOM, TKF_ERR_DEVICE. */
+tkf_status tkf_mlp_load(tkf_context ctx, const uint16_t* bf16_weights, tkf_mlp* out);
+void tkf_mlp_destroy(tkf_mlp mlp);
+
+typedef struct tkf_mlp_train_options {
+  uint32_t batch;   /* records per Adam step (1..8192); the last partial batch is dropped */
+  uint32_t epochs;  /* passes over the records, in their given order */
+  float lr, beta1, beta2, eps;  /* Adam (Kingma & Ba 2015); e.g. 1e-3, 0.9, 0.999, 1e-8 */
+} tkf_mlp_train_options;
+
+/* Trains FP32 parameters in place with mean-squared-error loss and Adam, with the library's
+ * own forward, backward and update kernels, on `stream`. All pointers are DEVICE memory:
+ * records [n][TKF_MLP_RECORD] (inputs, label), params [TKF_MLP_PARAMS], adam_moments
+ * [2][TKF_MLP_PARAMS] (first and second moments; zero them before the first call),
+ * epoch_loss [epochs] (mean loss of each epoch). *adam_t (HOST) counts the Adam steps taken so
+ * far (0 before the first call) and is advanced. Scratch comes from the context workspace.
+ * Errors: TKF_ERR_INVALID_ARG (NULL, batch out of range or larger than n), TKF_ERR_OOM,
+ * TKF_ERR_DEVICE. */
+tkf_status tkf_mlp_train(tkf_context ctx, const float* records, uint32_t n, const tkf_mlp_train_options* opts,
+                         float* params, float* adam_moments, uint32_t* adam_t, float* epoch_loss, void* stream);
+
+/* Mean squared error of the network on n samples (x [n][TKF_MLP_INPUTS], y [n], DEVICE) and
+ * its gradient grad [TKF_MLP_PARAMS] (DEVICE); loss is one DEVICE float. For checks of the
+ * training kernels. Errors as tkf_mlp_train. */
+tkf_status tkf_mlp_loss_grad(tkf_context ctx, const float* params, const float* x, const float* y, uint32_t n,
+                             float* grad, float* loss, void* stream);
+
+/* Raw outputs out [n] (DEVICE) of the network with FP32 params for x [n][TKF_MLP_INPUTS]. */
+tkf_status tkf_mlp_forward(tkf_context ctx, const float* params, const float* x, uint32_t n, float* out,
+                           void* stream);
 
 /* ---------------------------------------------------------------------------- allocation-free fit */
 

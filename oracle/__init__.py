@@ -53,7 +53,7 @@ class OOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("h_max", ctypes.c_double), ("h_min", ctypes.c_double),
                 ("surf_tol", ctypes.c_double), ("mass", ctypes.c_double),
                 ("max_steps", ctypes.c_uint32), ("ZA", ctypes.c_double), ("I_eV", ctypes.c_double),
-                ("rho", ctypes.c_double), ("hwp_eV", ctypes.c_double)]
+                ("rho", ctypes.c_double), ("hwp_eV", ctypes.c_double), ("mlp_bf16", ctypes.c_void_p)]
 
 
 @dataclass
@@ -65,6 +65,7 @@ class Options:
     mass: float = MUON_MASS  # GeV
     max_steps: int = 10000   # step attempts per surface
     material: tuple = SI
+    mlp: object = None       # 5057 BF16 weights (uint16) of the step proposer, or None
 
     def _c(self) -> OOpts:
         o = OOpts()
@@ -72,6 +73,10 @@ class Options:
             self.surf_tol, self.mass
         o.max_steps = self.max_steps
         o.ZA, o.I_eV, o.rho, o.hwp_eV = self.material
+        if self.mlp is not None:
+            w = np.ascontiguousarray(self.mlp, dtype=np.uint16)
+            o._keep = w
+            o.mlp_bf16 = w.ctypes.data
         return o
 
 
@@ -98,6 +103,7 @@ def lib():
         L.orc_fit_states.restype = u32
         L.orc_fit_states.argtypes = [vp, u32, ctypes.POINTER(OField), ctypes.POINTER(OOpts), u32, vp, vp,
                                      vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.orc_mlp_forward.argtypes = [vp, vp, u32, vp]
         L.orc_update.restype = u32
         L.orc_update.argtypes = [vp, vp, vp, vp, vp]
         _lib = L
@@ -249,6 +255,15 @@ def fit_states(surfaces, fld: OField, opts: Options, meas, sid, seed_par, seed_c
                               _p(out["Cs"]), _p(chi2))
     out["chi2"] = float(chi2[0])
     out["status"] = int(st)
+    return out
+
+
+def mlp_forward(w_bf16, x):
+    """Raw outputs of the step-proposer network (FP32 arithmetic, BF16 weights) for x [n, 12]."""
+    w = np.ascontiguousarray(w_bf16, dtype=np.uint16)
+    x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 12)
+    out = np.zeros(x.shape[0], np.float32)
+    lib().orc_mlp_forward(_p(w), _p(x), x.shape[0], _p(out))
     return out
 
 

@@ -66,7 +66,14 @@ struct Field {
   const float* Bz;  // [nz][nr]
 };
 
+// Learned step proposer (the benchmark spec, not in the paper): an MLP 12 -> 64 -> 64 -> 1 with SiLU
+// activations whose weights are BF16 values; the forward pass is FP32 arithmetic.
+struct Mlp {
+  float W1[64][12], b1[64], W2[64][64], b2[64], w3[64], b3;
+};
+
 struct Opts {
+  const Mlp* mlp;   // learned step proposals when not null
   double tol;       // RKN local error tolerance, mm
   double h_max;     // largest step, mm
   double h_min;     // smallest step-size control value, mm
@@ -312,7 +319,61 @@ struct PropState {
   double h_ctrl;
   uint32_t attempts;  // all step attempts, this track
   uint32_t rejected;  // rejected attempts, this track
+  double h_last;      // last accepted step length (an MLP input)
+  bool use_mlp;       // unused by the oracle's propagation (the proposal is made per track)
 };
+
+// MLP inputs at the start of a step, FP32: position (u, v, n components of r - c) / 1000 mm,
+// direction (u, v, n components of T), q/p, B / 2 T, ln(last step / mm) / 5, and the
+// straight-line path to the plane / 1000 mm clamped to [-2, 2].
+void mlp_features(const Surface& s, const double r[3], const double T[3], double lam, const double B[3],
+                  double h_last, double sl, float x[12]) {
+  float d[3], t[3], u[3], v[3], n[3];
+  for (int i = 0; i < 3; ++i) {
+    d[i] = float(r[i] - s.c[i]);
+    t[i] = float(T[i]);
+    u[i] = float(s.u[i]);
+    v[i] = float(s.v[i]);
+    n[i] = float(s.n[i]);
+  }
+  x[0] = (u[0] * d[0] + u[1] * d[1] + u[2] * d[2]) * 1e-3f;
+  x[1] = (v[0] * d[0] + v[1] * d[1] + v[2] * d[2]) * 1e-3f;
+  x[2] = (n[0] * d[0] + n[1] * d[1] + n[2] * d[2]) * 1e-3f;
+  x[3] = u[0] * t[0] + u[1] * t[1] + u[2] * t[2];
+  x[4] = v[0] * t[0] + v[1] * t[1] + v[2] * t[2];
+  x[5] = n[0] * t[0] + n[1] * t[1] + n[2] * t[2];
+  x[6] = float(lam);
+  x[7] = float(B[0]) * 0.5f;
+  x[8] = float(B[1]) * 0.5f;
+  x[9] = float(B[2]) * 0.5f;
+  x[10] = std::log(float(h_last)) * 0.2f;
+  float q = float(sl) * 1e-3f;
+  x[11] = q < -2.0f ? -2.0f : (q > 2.0f ? 2.0f : q);
+}
+
+float silu(float z) { return z / (1.0f + std::exp(-z)); }
+
+// The network's output is ln(h / mm) of the largest step within tolerance; the proposal is
+// 0.9 exp(output), clamped to [h_min, h_max].
+double mlp_propose(const Mlp& m, const float x[12], double h_min, double h_max) {
+  float a1[64], a2[64];
+  for (int j = 0; j < 64; ++j) {
+    float z = m.b1[j];
+    for (int i = 0; i < 12; ++i) z += m.W1[j][i] * x[i];
+    a1[j] = silu(z);
+  }
+  for (int j = 0; j < 64; ++j) {
+    float z = m.b2[j];
+    for (int i = 0; i < 64; ++i) z += m.W2[j][i] * a1[i];
+    a2[j] = silu(z);
+  }
+  float out = m.b3;
+  for (int i = 0; i < 64; ++i) out += m.w3[i] * a2[i];
+  double h = 0.9 * double(std::exp(out));
+  if (!(h >= h_min)) h = h_min;
+  if (h > h_max) h = h_max;
+  return h;
+}
 
 double step_factor(double q, double lo, double hi) {
   // clamp(0.9 q^(1/4), lo, hi) with q^(1/4) taken as sqrt(sqrt(q)).
@@ -328,6 +389,7 @@ uint32_t propagate(const Field& f, const Opts& o, const Surface& s, double r[3],
   for (int i = 0; i < 49; ++i) Dtot[i] = (i % 8 == 0) ? 1.0 : 0.0;
   bool first = true;
   uint32_t n_here = 0;
+
   for (;;) {
     double diff[3] = {s.c[0] - r[0], s.c[1] - r[1], s.c[2] - r[2]};
     double dist = dot3(s.n, diff);
@@ -385,8 +447,9 @@ uint32_t propagate(const Field& f, const Opts& o, const Surface& s, double r[3],
       sp = 2.0 * dist / (a + std::copysign(std::sqrt(disc), a));
       if (!std::isfinite(sp)) sp = sl;
     }
-    bool limited = !(std::fabs(sp) < ps.h_ctrl);
-    double h = limited ? std::copysign(ps.h_ctrl, sp) : sp;
+    double limit = ps.h_ctrl;
+    bool limited = !(std::fabs(sp) < limit);
+    double h = limited ? std::copysign(limit, sp) : sp;
     Step st;
     bool oof = false;
     rkn_step(f, r, T, lam, h, st, &oof);
@@ -404,8 +467,9 @@ uint32_t propagate(const Field& f, const Opts& o, const Surface& s, double r[3],
     matmul(st.D, Dtot, Dtot, 7, 7, 7);
     if (limited) {
       double fac = (st.eps > 0.0) ? step_factor(o.tol / st.eps, 0.25, 4.0) : 4.0;
-      ps.h_ctrl = std::min(o.h_max, ps.h_ctrl * fac);
+      ps.h_ctrl = std::min(o.h_max, std::fabs(h) * fac);
     }
+    ps.h_last = std::fabs(h);
   }
   // dx/ds at the end point: (T, kappa*lam*T x B(r), 0).
   double B[3], c[3];
@@ -692,7 +756,23 @@ void fit_track(const Surface* surf, uint32_t n_surf, const Field& f, const Opts&
   std::vector<double> pp(N * 5), Cp(N * 25), pf(N * 5), Cf(N * 25), J(N * 25, 0.0), ps(N * 5), Cs(N * 25);
   std::memcpy(&pp[0], in.seed_par, sizeof(double) * 5);
   unpack_cov(in.seed_cov, &Cp[0]);
-  PropState prop{o.h_max, 0, 0};
+  PropState prop{o.h_max, 0, 0, o.h_max, true};
+  if (o.mlp && N >= 2) {
+    // Reading (learned mode): the step-size control has no error estimate before the first step,
+    // so the network proposes its starting value (instead of h_max) from the seed state at the
+    // first surface, toward the second surface; from then on the plain control adapts it from
+    // the error estimates, and the error estimate judges every step.
+    const Surface& s0 = surf[in.sid[0]];
+    const Surface& s1 = surf[in.sid[1]];
+    double r[3], T[3], B[3], diff[3];
+    bound_to_free(s0, in.seed_par, r, T);
+    bool oofm = false;
+    field_at(f, r, B, &oofm);
+    for (int i = 0; i < 3; ++i) diff[i] = s1.c[i] - r[i];
+    float x[12];
+    mlp_features(s1, r, T, in.seed_par[4], B, o.h_max, dot3(s1.n, diff) / dot3(s1.n, T), x);
+    prop.h_ctrl = mlp_propose(*o.mlp, x, o.h_min, o.h_max);
+  }
   double chi2 = 0.0;
   uint32_t status = 0;
   for (int k = 0; k < N; ++k) {
@@ -776,7 +856,27 @@ struct orc_opts {
   double tol, h_max, h_min, surf_tol, mass;
   uint32_t max_steps;
   double ZA, I_eV, rho, hwp_eV;
+  const uint16_t* mlp_bf16;  // 5057 BF16 weights (W1, b1, W2, b2, w3, b3) or null
 };
+
+static float bf16_to_float(uint16_t b) {
+  uint32_t u = uint32_t(b) << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+static void unpack_mlp(const uint16_t* w, Mlp& m) {
+  size_t k = 0;
+  for (int j = 0; j < 64; ++j)
+    for (int i = 0; i < 12; ++i) m.W1[j][i] = bf16_to_float(w[k++]);
+  for (int j = 0; j < 64; ++j) m.b1[j] = bf16_to_float(w[k++]);
+  for (int j = 0; j < 64; ++j)
+    for (int i = 0; i < 64; ++i) m.W2[j][i] = bf16_to_float(w[k++]);
+  for (int j = 0; j < 64; ++j) m.b2[j] = bf16_to_float(w[k++]);
+  for (int i = 0; i < 64; ++i) m.w3[i] = bf16_to_float(w[k++]);
+  m.b3 = bf16_to_float(w[k++]);
+}
 
 static Field to_field(const orc_field* f) {
   Field F;
@@ -788,8 +888,13 @@ static Field to_field(const orc_field* f) {
   return F;
 }
 
-static Opts to_opts(const orc_opts* o) {
+static Opts to_opts(const orc_opts* o, Mlp* storage) {
   Opts O;
+  O.mlp = nullptr;
+  if (o->mlp_bf16 && storage) {
+    unpack_mlp(o->mlp_bf16, *storage);
+    O.mlp = storage;
+  }
   O.tol = o->tol; O.h_max = o->h_max; O.h_min = o->h_min; O.surf_tol = o->surf_tol; O.mass = o->mass;
   O.max_steps = o->max_steps;
   O.ZA = o->ZA; O.I_eV = o->I_eV; O.rho = o->rho; O.hwp_eV = o->hwp_eV;
@@ -823,7 +928,8 @@ int orc_fit(const double* surfaces, uint32_t n_surf, const orc_field* field, con
             int32_t* ndf, uint32_t* status, uint32_t* steps, double* cov_filt0, int n_threads) {
   std::vector<Surface> surf = to_surfaces(surfaces, n_surf);
   Field F = to_field(field);
-  Opts O = to_opts(opts);
+  Mlp mlp_store;
+  Opts O = to_opts(opts, &mlp_store);
   auto work = [&](uint32_t lo, uint32_t hi) {
     for (uint32_t i = lo; i < hi; ++i) {
       TrackIn in;
@@ -921,11 +1027,12 @@ uint32_t orc_transport(const double* surfaces, uint32_t a, uint32_t b, const orc
                        uint32_t* attempts) {
   std::vector<Surface> surf = to_surfaces(surfaces, std::max(a, b) + 1);
   Field F = to_field(field);
-  Opts O = to_opts(opts);
+  Mlp mlp_store;
+  Opts O = to_opts(opts, &mlp_store);
   double r[3], T[3], Dtot[49], dxds[7], Jb2f[35], Jf2b[35], P[49], tmp[49], t75[35];
   bound_to_free(surf[a], par_in, r, T);
   jac_bound_to_free(surf[a], par_in, Jb2f);
-  PropState ps{O.h_max, 0, 0};
+  PropState ps{O.h_max, 0, 0, O.h_max, true};
   uint32_t st = propagate(F, O, surf[b], r, T, par_in[4], Dtot, dxds, ps);
   if (attempts) *attempts = ps.attempts;
   if (st & kFatal) return st;
@@ -942,7 +1049,8 @@ uint32_t orc_transport(const double* surfaces, uint32_t a, uint32_t b, const orc
 uint32_t orc_material(const double* surface14, const orc_opts* opts, const double* par, double* theta0,
                       double* qop_after, double* dedx_mev_cm2_g) {
   std::vector<Surface> s = to_surfaces(surface14, 1);
-  Opts O = to_opts(opts);
+  Mlp mlp_store;
+  Opts O = to_opts(opts, &mlp_store);
   double p[5], Q[25];
   std::memcpy(p, par, sizeof(p));
   uint32_t st = material(s[0], O, p, Q);
@@ -998,7 +1106,8 @@ uint32_t orc_fit_states(const double* surfaces, uint32_t n_surf, const orc_field
                         double* ps, double* Cs, double* chi2) {
   std::vector<Surface> surf = to_surfaces(surfaces, n_surf);
   Field F = to_field(field);
-  Opts O = to_opts(opts);
+  Mlp mlp_store;
+  Opts O = to_opts(opts, &mlp_store);
   TrackIn in{N, meas, sid, seed_par, seed_cov};
   TrackOut out;
   States st;
@@ -1014,6 +1123,30 @@ uint32_t orc_fit_states(const double* surfaces, uint32_t n_surf, const orc_field
   }
   *chi2 = out.chi2;
   return out.status;
+}
+
+// Raw network output (ln of the proposed step before the 0.9 factor and clamping) for n inputs
+// x [n][12], with BF16 weights w (5057).
+void orc_mlp_forward(const uint16_t* w, const float* x, uint32_t n, float* out) {
+  Mlp m;
+  unpack_mlp(w, m);
+  for (uint32_t s = 0; s < n; ++s) {
+    const float* xi = x + 12 * size_t(s);
+    float a1[64], a2[64];
+    for (int j = 0; j < 64; ++j) {
+      float z = m.b1[j];
+      for (int i = 0; i < 12; ++i) z += m.W1[j][i] * xi[i];
+      a1[j] = silu(z);
+    }
+    for (int j = 0; j < 64; ++j) {
+      float z = m.b2[j];
+      for (int i = 0; i < 64; ++i) z += m.W2[j][i] * a1[i];
+      a2[j] = silu(z);
+    }
+    float o = m.b3;
+    for (int i = 0; i < 64; ++i) o += m.w3[i] * a2[i];
+    out[s] = o;
+  }
 }
 
 // One gain-matrix update (for the chi2 identity pin).

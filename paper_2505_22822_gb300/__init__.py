@@ -24,7 +24,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _ROOT = os.path.dirname(_HERE)
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "libtkf.so")
-_SOURCES = ["tkf_api.cu", "tkf_fit.cu"]
+_SOURCES = ["tkf_api.cu", "tkf_order.cu", "tkf_fit_fp64.cu", "tkf_fit_mixed.cu", "tkf_mlp.cu"]
 _lib = None
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
@@ -106,7 +106,13 @@ class FitOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("step_mode", ctypes.c_int), ("tol", ctypes.c_double),
                 ("h_max", ctypes.c_double), ("h_min", ctypes.c_double),
                 ("surf_tol", ctypes.c_double), ("max_steps", ctypes.c_uint32),
-                ("mass", ctypes.c_double), ("mlp", ctypes.c_void_p)]
+                ("mass", ctypes.c_double), ("mlp", ctypes.c_void_p), ("records", ctypes.c_void_p),
+                ("record_capacity", ctypes.c_uint32), ("record_count", ctypes.c_void_p)]
+
+
+class MlpTrainOptions(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_uint32), ("epochs", ctypes.c_uint32), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float)]
 
 
 class FitInputs(ctypes.Structure):
@@ -141,7 +147,15 @@ _SIGNATURES = {
                                     ctypes.POINTER(FitInputs), ctypes.POINTER(FitOutputs), _VP]),
     "tkf_fit_noalloc": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(FitOptions),
                                        ctypes.POINTER(FitInputs), ctypes.POINTER(FitOutputs), _VP]),
+    "tkf_mlp_load": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(_VP)]),
+    "tkf_mlp_destroy": (None, [_VP]),
+    "tkf_mlp_train": (ctypes.c_int, [_VP, _VP, ctypes.c_uint32, ctypes.POINTER(MlpTrainOptions), _VP, _VP,
+                                     ctypes.POINTER(ctypes.c_uint32), _VP, _VP]),
+    "tkf_mlp_loss_grad": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_uint32, _VP, _VP, _VP]),
+    "tkf_mlp_forward": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_uint32, _VP, _VP]),
 }
+
+MLP_PARAMS, MLP_INPUTS, MLP_RECORD = 5057, 12, 13
 
 NOALLOC_MAX_TRACKS = 2097152
 
@@ -272,6 +286,26 @@ class Field:
             pass
 
 
+class Mlp:
+    """Step-proposer network handle (BF16 weights uploaded to the device)."""
+
+    def __init__(self, ctx: Context, bf16_weights):
+        w = np.ascontiguousarray(bf16_weights, dtype=np.uint16)
+        if w.size != MLP_PARAMS:
+            raise TkfError(f"expected {MLP_PARAMS} BF16 weights, got {w.size}")
+        h = _VP()
+        _check(lib().tkf_mlp_load(ctx.handle, w.ctypes.data_as(_VP), ctypes.byref(h)), ctx.handle, "tkf_mlp_load")
+        self.handle, self.ctx = h, ctx
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None):
+                lib().tkf_mlp_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
 @dataclass
 class Options:
     precision: int = FP64
@@ -282,6 +316,9 @@ class Options:
     surf_tol: float = 1e-2
     max_steps: int = 10000
     mass: float = 0.1056583755
+    mlp: object = None            # Mlp for STEP_LEARNED
+    records: object = None        # CUDA float tensor [capacity, 13] for record capture
+    record_count: object = None   # CUDA int32 tensor [1], zeroed by the caller
 
     def c(self) -> FitOptions:
         o = FitOptions()
@@ -289,6 +326,12 @@ class Options:
         o.precision, o.step_mode = self.precision, self.step_mode
         o.tol, o.h_max, o.h_min, o.surf_tol = self.tol, self.h_max, self.h_min, self.surf_tol
         o.max_steps, o.mass = self.max_steps, self.mass
+        if self.mlp is not None:
+            o.mlp = self.mlp.handle
+        if self.records is not None:
+            o.records = self.records.data_ptr()
+            o.record_capacity = int(self.records.shape[0])
+            o.record_count = self.record_count.data_ptr()
         return o
 
 
@@ -441,6 +484,44 @@ def fit_noalloc(ctx: Context, geo: Geometry, field: Field, batch: Batch, out: Re
     _check(lib().tkf_fit_noalloc(ctx.handle, geo.handle, field.handle, ctypes.byref(o),
                                  ctypes.byref(_inputs_struct(batch)), ctypes.byref(_outputs_struct(out)),
                                  _VP(stream.cuda_stream)), ctx.handle, "tkf_fit_noalloc")
+    return out
+
+
+def mlp_train(ctx: Context, records, params, moments, adam_t: int, batch: int, epochs: int, lr=1e-3,
+              beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """Trains FP32 params (CUDA tensor [5057]) in place on records (CUDA [n, 13]) with the library's
+    kernels; moments is a CUDA tensor [2, 5057]. Returns (per-epoch mean loss tensor, new adam_t)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(records.device)
+    loss = torch.zeros(epochs, dtype=torch.float32, device=records.device)
+    t = ctypes.c_uint32(adam_t)
+    o = MlpTrainOptions(batch, epochs, lr, beta1, beta2, eps)
+    _check(lib().tkf_mlp_train(ctx.handle, _VP(records.data_ptr()), records.shape[0], ctypes.byref(o),
+                               _VP(params.data_ptr()), _VP(moments.data_ptr()), ctypes.byref(t),
+                               _VP(loss.data_ptr()), _VP(stream.cuda_stream)), ctx.handle, "tkf_mlp_train")
+    return loss, t.value
+
+
+def mlp_loss_grad(ctx: Context, params, x, y, stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(x.device)
+    grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device=x.device)
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    _check(lib().tkf_mlp_loss_grad(ctx.handle, _VP(params.data_ptr()), _VP(x.data_ptr()), _VP(y.data_ptr()),
+                                   x.shape[0], _VP(grad.data_ptr()), _VP(loss.data_ptr()),
+                                   _VP(stream.cuda_stream)), ctx.handle, "tkf_mlp_loss_grad")
+    return loss, grad
+
+
+def mlp_forward(ctx: Context, params, x, stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(x.device)
+    out = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+    _check(lib().tkf_mlp_forward(ctx.handle, _VP(params.data_ptr()), _VP(x.data_ptr()), x.shape[0],
+                                 _VP(out.data_ptr()), _VP(stream.cuda_stream)), ctx.handle, "tkf_mlp_forward")
     return out
 
 

@@ -79,10 +79,11 @@ tkf_status tkf_context_create(int device, tkf_context* out) {
 
 void tkf_context_destroy(tkf_context ctx) {
   if (!ctx) return;
-  if (ctx->stage || ctx->ws) {
+  if (ctx->stage || ctx->ws || ctx->train_ws) {
     DeviceGuard g(ctx->device);
     if (ctx->stage) cudaFree(ctx->stage);
     if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->train_ws) cudaFree(ctx->train_ws);
   }
   delete ctx;
 }
@@ -270,6 +271,9 @@ void tkf_fit_options_default(tkf_fit_options* o) {
   o->max_steps = 10000;
   o->mass = 0.1056583755;
   o->mlp = nullptr;
+  o->records = nullptr;
+  o->record_capacity = 0;
+  o->record_count = nullptr;
 }
 
 static tkf_status check_common(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf_fit_options* o,
@@ -284,6 +288,11 @@ static tkf_status check_common(tkf_context ctx, tkf_geometry geo, tkf_field fiel
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": unknown step mode");
   if (o->step_mode == TKF_STEP_LEARNED && !o->mlp)
     return fail(ctx, TKF_ERR_UNSUPPORTED, std::string(fn) + ": TKF_STEP_LEARNED needs an mlp handle");
+  if (o->step_mode == TKF_STEP_LEARNED && o->mlp->ctx != ctx)
+    return fail(ctx, TKF_ERR_BAD_HANDLE, std::string(fn) + ": mlp handle from another context");
+  if (o->records && (!o->record_count || o->record_capacity == 0 || o->step_mode != TKF_STEP_ADAPTIVE))
+    return fail(ctx, TKF_ERR_INVALID_ARG,
+                std::string(fn) + ": record capture needs record_count, a capacity and TKF_STEP_ADAPTIVE");
   if (!(o->tol > 0) || !(o->h_max > 0) || !(o->h_min > 0) || !(o->h_min <= o->h_max) || !(o->surf_tol > 0) ||
       o->max_steps == 0 || !(o->mass > 0) || !isfinite(o->h_max))
     return fail(ctx, TKF_ERR_INVALID_ARG,
@@ -332,6 +341,10 @@ static tkf::FitArgs make_args(tkf_geometry geo, const tkf_fit_options* o, const 
   a.opt.surf_tol = o->surf_tol;
   a.opt.mass = o->mass;
   a.opt.max_steps = o->max_steps;
+  a.mlp = (o->step_mode == TKF_STEP_LEARNED && o->mlp) ? o->mlp->d_weights : nullptr;
+  a.records = (o->step_mode == TKF_STEP_ADAPTIVE) ? o->records : nullptr;
+  a.record_capacity = o->record_capacity;
+  a.record_count = o->record_count;
   return a;
 }
 
@@ -339,12 +352,11 @@ tkf_status tkf_fit(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf
                    const tkf_fit_inputs* in, const tkf_fit_outputs* out, void* stream) {
   tkf_status s = check_common(ctx, geo, field, o, in, out, "tkf_fit");
   if (s != TKF_OK || in->n_tracks == 0) return s;
-  if (o->step_mode == TKF_STEP_LEARNED)
-    return fail(ctx, TKF_ERR_UNSUPPORTED, "tkf_fit: learned step proposals are not available in this build");
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(ctx, TKF_ERR_DEVICE, "tkf_fit: cudaSetDevice failed");
   tkf::FitArgs a = make_args(geo, o, in, out);
-  const size_t need = tkf::workspace_bytes(in->n_tracks);
+  const bool learned = o->step_mode == TKF_STEP_LEARNED;
+  const size_t need = tkf::workspace_bytes(in->n_tracks, learned);
   if (need > ctx->ws_bytes) {
     // the old workspace may still be in use by earlier work on this context's stream
     cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
@@ -356,7 +368,7 @@ tkf_status tkf_fit(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit: workspace cudaMalloc");
     ctx->ws_bytes = need;
   }
-  tkf::Workspace ws = tkf::carve_workspace(ctx->ws, in->n_tracks);
+  tkf::Workspace ws = tkf::carve_workspace(ctx->ws, in->n_tracks, learned);
   cudaError_t e = tkf::launch_fit(a, field->f, o->precision, ws, ctx->sm_count, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit: launch");
   return TKF_OK;
@@ -438,6 +450,113 @@ tkf_status tkf_fit_host(tkf_context ctx, tkf_geometry geo, tkf_field field, cons
 
 }  // extern "C"
 
+// ============================================================================ learned step proposer
+extern "C" {
+
+tkf_status tkf_mlp_load(tkf_context ctx, const uint16_t* w, tkf_mlp* out) {
+  if (!ctx) return fail(nullptr, TKF_ERR_BAD_HANDLE, "tkf_mlp_load: NULL context");
+  if (!w || !out) return fail(ctx, TKF_ERR_INVALID_ARG, "tkf_mlp_load: NULL pointer");
+  *out = nullptr;
+  float host[TKF_MLP_PARAMS];
+  for (int k = 0; k < TKF_MLP_PARAMS; ++k) {
+    const uint32_t u = uint32_t(w[k]) << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    if (!isfinite(f)) return fail(ctx, TKF_ERR_INVALID_ARG, "tkf_mlp_load: non-finite weight " + std::to_string(k));
+    host[k] = f;
+  }
+  DeviceGuard g(ctx->device);
+  float* dev = nullptr;
+  cudaError_t e = cudaMalloc(&dev, sizeof(host));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_mlp_load: cudaMalloc");
+  e = cudaMemcpy(dev, host, sizeof(host), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(dev);
+    return cuda_fail(ctx, e, "tkf_mlp_load: cudaMemcpy");
+  }
+  tkf_mlp h = new (std::nothrow) tkf_mlp_s();
+  if (!h) {
+    cudaFree(dev);
+    return fail(ctx, TKF_ERR_OOM, "tkf_mlp_load: host allocation failed");
+  }
+  h->ctx = ctx;
+  h->device = ctx->device;
+  h->d_weights = dev;
+  *out = h;
+  return TKF_OK;
+}
+
+void tkf_mlp_destroy(tkf_mlp m) {
+  if (!m) return;
+  DeviceGuard g(m->device);
+  cudaFree(m->d_weights);
+  delete m;
+}
+
+static tkf_status train_scratch(tkf_context ctx, uint32_t batch, void** out, cudaStream_t stream, const char* fn) {
+  const size_t need = tkf::mlp_train_scratch_bytes(batch);
+  if (need > ctx->train_bytes) {
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, fn);
+    if (ctx->train_ws) cudaFree(ctx->train_ws);
+    ctx->train_ws = nullptr;
+    ctx->train_bytes = 0;
+    e = cudaMalloc(&ctx->train_ws, need);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, fn);
+    ctx->train_bytes = need;
+  }
+  *out = ctx->train_ws;
+  return TKF_OK;
+}
+
+tkf_status tkf_mlp_train(tkf_context ctx, const float* records, uint32_t n, const tkf_mlp_train_options* o,
+                         float* params, float* moments, uint32_t* adam_t, float* epoch_loss, void* stream) {
+  if (!ctx) return fail(nullptr, TKF_ERR_BAD_HANDLE, "tkf_mlp_train: NULL context");
+  if (!records || !o || !params || !moments || !adam_t || !epoch_loss)
+    return fail(ctx, TKF_ERR_INVALID_ARG, "tkf_mlp_train: NULL pointer");
+  if (o->batch == 0 || o->batch > 8192 || o->batch > n || o->epochs == 0 || !(o->lr > 0) || !(o->beta1 >= 0) ||
+      !(o->beta1 < 1) || !(o->beta2 >= 0) || !(o->beta2 < 1) || !(o->eps > 0))
+    return fail(ctx, TKF_ERR_INVALID_ARG,
+                "tkf_mlp_train: need 1 <= batch <= min(8192, n), epochs > 0, lr > 0, 0 <= beta < 1, eps > 0");
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void* scratch = nullptr;
+  tkf_status s = train_scratch(ctx, o->batch, &scratch, st, "tkf_mlp_train: scratch");
+  if (s != TKF_OK) return s;
+  cudaError_t e = tkf::mlp_train(records, n, o->batch, o->epochs, o->lr, o->beta1, o->beta2, o->eps, params, moments,
+                                 adam_t, epoch_loss, scratch, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_mlp_train: launch");
+  return TKF_OK;
+}
+
+tkf_status tkf_mlp_loss_grad(tkf_context ctx, const float* params, const float* x, const float* y, uint32_t n,
+                             float* grad, float* loss, void* stream) {
+  if (!ctx) return fail(nullptr, TKF_ERR_BAD_HANDLE, "tkf_mlp_loss_grad: NULL context");
+  if (!params || !x || !y || !grad || !loss || n == 0 || n > 65536)
+    return fail(ctx, TKF_ERR_INVALID_ARG, "tkf_mlp_loss_grad: NULL pointer, or n not in 1..65536");
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void* scratch = nullptr;
+  tkf_status s = train_scratch(ctx, n, &scratch, st, "tkf_mlp_loss_grad: scratch");
+  if (s != TKF_OK) return s;
+  cudaError_t e = tkf::mlp_loss_grad(params, x, TKF_MLP_INPUTS, y, 1, n, grad, loss, scratch, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_mlp_loss_grad: launch");
+  return TKF_OK;
+}
+
+tkf_status tkf_mlp_forward(tkf_context ctx, const float* params, const float* x, uint32_t n, float* out,
+                           void* stream) {
+  if (!ctx) return fail(nullptr, TKF_ERR_BAD_HANDLE, "tkf_mlp_forward: NULL context");
+  if (!params || !x || !out) return fail(ctx, TKF_ERR_INVALID_ARG, "tkf_mlp_forward: NULL pointer");
+  if (n == 0) return TKF_OK;
+  DeviceGuard g(ctx->device);
+  cudaError_t e = tkf::mlp_forward(params, x, n, out, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_mlp_forward: launch");
+  return TKF_OK;
+}
+
+}  // extern "C"
+
 // ============================================================================ allocation-free fit
 // Some callers cannot allocate device memory once they are running: an online trigger or
 // reconstruction process that reserves all of its GPU memory at start-up and forbids later
@@ -491,7 +610,7 @@ extern "C" tkf_status tkf_fit_noalloc(tkf_context ctx, tkf_geometry geo, tkf_fie
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_noalloc: cudaGetSymbolAddress");
   tkf::FitArgs a = make_args(geo, o, in, out);
   // the launch clears the counter and histogram before use (the array keeps the last call's data)
-  tkf::Workspace ws = tkf::carve_workspace(scratch, in->n_tracks);
+  tkf::Workspace ws = tkf::carve_workspace(scratch, in->n_tracks, false);
   e = tkf::launch_fit(a, field->f, o->precision, ws, ctx->sm_count, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_noalloc: launch");
   return TKF_OK;

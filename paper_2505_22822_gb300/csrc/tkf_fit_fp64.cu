@@ -1,0 +1,11 @@
+// tkf_fit_fp64.cu -- instantiation of the persistent fit kernels, FP64.
+#include "tkf_fit_impl.cuh"
+
+namespace tkf {
+
+cudaError_t launch_fit_fp64(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm, uint32_t* counter,
+                            int blocks, cudaStream_t stream) {
+  return launch_fields<false>(a, f, mode, perm, counter, blocks, stream);
+}
+
+}  // namespace tkf

@@ -1,4 +1,6 @@
-// tkf_fit.cu -- Kalman-filter fit kernels for GB300 (sm_103a).
+#pragma once
+// tkf_fit_impl.cuh -- Kalman-filter fit kernels for GB300 (sm_103a), included by the per-precision
+// translation units tkf_fit_fp64.cu and tkf_fit_mixed.cu.
 //
 // One thread fits one track end to end with every per-track quantity in registers:
 //   seed -> [update at k = 0] -> for k = 1..N-1: material at k-1 (Highland + Bethe mean
@@ -169,6 +171,88 @@ __device__ __forceinline__ double parabolic_path(double d, double a, double b) {
   return s;
 }
 
+// ------------------------------------------------------------------ learned step proposer
+// Network inputs at the start of a step (FP32): u, v, n components of (r - c) / 1000 mm, of the
+// direction, q/p, B / 2 T, ln(last step / mm) / 5, straight-line path / 1000 mm in [-2, 2].
+__device__ __forceinline__ void mlp_features(const Surf& s, const double r[3], const float Tf[3], double lam,
+                                             const float B[3], float h_last, float sl, float x[12]) {
+  const float d[3] = {float(r[0] - s.c[0]), float(r[1] - s.c[1]), float(r[2] - s.c[2])};
+  const float u[3] = {float(s.u[0]), float(s.u[1]), float(s.u[2])};
+  const float v[3] = {float(s.v[0]), float(s.v[1]), float(s.v[2])};
+  const float n[3] = {float(s.n[0]), float(s.n[1]), float(s.n[2])};
+  x[0] = (u[0] * d[0] + u[1] * d[1] + u[2] * d[2]) * 1e-3f;
+  x[1] = (v[0] * d[0] + v[1] * d[1] + v[2] * d[2]) * 1e-3f;
+  x[2] = (n[0] * d[0] + n[1] * d[1] + n[2] * d[2]) * 1e-3f;
+  x[3] = u[0] * Tf[0] + u[1] * Tf[1] + u[2] * Tf[2];
+  x[4] = v[0] * Tf[0] + v[1] * Tf[1] + v[2] * Tf[2];
+  x[5] = n[0] * Tf[0] + n[1] * Tf[1] + n[2] * Tf[2];
+  x[6] = float(lam);
+  x[7] = B[0] * 0.5f;
+  x[8] = B[1] * 0.5f;
+  x[9] = B[2] * 0.5f;
+  x[10] = logf(h_last) * 0.2f;
+  x[11] = fminf(fmaxf(sl * 1e-3f, -2.0f), 2.0f);
+}
+
+__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + expf(-z)); }
+
+// Raw network output for inputs x; w = W1 [64][12], b1, W2 [64][64], b2, w3, b3 (global memory,
+// read through the read-only cache: every lane reads the same weight, once per track).
+__device__ __forceinline__ float mlp_eval(const float* __restrict__ w, const float x[12]) {
+  const float* W1 = w;
+  const float* b1 = w + 768;
+  const float* W2 = w + 832;
+  const float* b2 = w + 4928;
+  const float* w3 = w + 4992;
+  float a1[64];
+#pragma unroll
+  for (int j = 0; j < 64; ++j) {
+    float z = __ldg(b1 + j);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) z = fmaf(__ldg(W1 + j * 12 + i), x[i], z);
+    a1[j] = silu_f(z);
+  }
+  float out = __ldg(w + 5056);
+#pragma unroll 4
+  for (int j = 0; j < 64; ++j) {
+    const float4* row = reinterpret_cast<const float4*>(W2 + j * 64);
+    float z = __ldg(b2 + j);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const float4 c = __ldg(row + q);
+      z = fmaf(c.x, a1[4 * q], z);
+      z = fmaf(c.y, a1[4 * q + 1], z);
+      z = fmaf(c.z, a1[4 * q + 2], z);
+      z = fmaf(c.w, a1[4 * q + 3], z);
+    }
+    out = fmaf(__ldg(w3 + j), silu_f(z), out);
+  }
+  return out;
+}
+
+// Step modes: plain adaptive control, learned proposals, or plain control with record capture.
+constexpr int kPlain = 0, kLearned = 1, kRecord = 2;
+
+// Where learned proposals and training records go during one track's propagation.
+struct StepLearn {
+  const float* w;         // network weights (global memory), or null
+  float* rec;             // record buffer, or null
+  uint32_t rec_cap;
+  uint32_t* rec_count;
+  float h_last;           // last accepted step (network input), per track
+  bool use_mlp;           // the network has not proposed yet (true until the track's first step)
+};
+
+__device__ __forceinline__ void put_record(StepLearn& L, const float x[12], float label) {
+  const uint32_t k = atomicAdd(L.rec_count, 1u);
+  if (k < L.rec_cap) {
+    float* o = L.rec + size_t(k) * kMlpRecord;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) o[i] = x[i];
+    o[12] = label;
+  }
+}
+
 // ------------------------------------------------------------------ propagation
 // Adaptive RKN4 stepping of (r, T, lam) to the plane of `s`, transporting the derivative
 // columns of (phi, theta, q/p): dr[c], dT[c] (c = 0, 1, 2). Step control (Lund 2009a, safety
@@ -177,10 +261,10 @@ __device__ __forceinline__ double parabolic_path(double d, double a, double b) {
 // h_ctrl = min(h_max, h_ctrl clamp(0.9 (tol/eps)^1/4, 1/4, 4)). Each step aims at the plane's
 // intersection with the parabola r + s T + s^2/2 k1; within surf_tol a second-order Taylor
 // step (state and columns) lands on the plane.
-template <class F>
+template <int kMode, class F>
 __device__ uint32_t propagate(const F& fld, const OptionsDev& o, const Surf& s, double r[3], double T[3],
                               double lam, double dr[3][3], double dT[3][3], double& h_ctrl,
-                              uint32_t& attempts, uint32_t& rejected, double kend[3]) {
+                              uint32_t& attempts, uint32_t& rejected, double kend[3], StepLearn& L) {
   uint32_t st = 0;
   bool first = true;
   uint32_t n_here = 0;
@@ -224,8 +308,15 @@ __device__ uint32_t propagate(const F& fld, const OptionsDev& o, const Surf& s, 
     ++n_here;
     ++attempts;
     const double sp = parabolic_path(dist, a, dot3(s.n, k1));
-    const bool limited = !(fabs(sp) < h_ctrl);
-    const double h = limited ? copysign(h_ctrl, sp) : sp;
+    float x[kMode == kRecord ? 12 : 1];
+    if constexpr (kMode == kRecord) {
+      const float Tf[3] = {float(T[0]), float(T[1]), float(T[2])};
+      const float Bf[3] = {float(B1[0]), float(B1[1]), float(B1[2])};
+      mlp_features(s, r, Tf, lam, Bf, L.h_last, float(sl), x);
+    }
+    const double limit = h_ctrl;
+    const bool limited = !(fabs(sp) < limit);
+    const double h = limited ? copysign(limit, sp) : sp;
     const double h2 = 0.5 * h, h6 = h * (1.0 / 6.0);
     double B2[3], B4[3], Bt2[3], Bt4[3];
     double k2[3], k3[3], k4[3], T2[3], T3[3], T4[3];
@@ -261,6 +352,8 @@ __device__ uint32_t propagate(const F& fld, const OptionsDev& o, const Surf& s, 
       continue;
     }
     if (oof) st |= TKF_TRACK_OUT_OF_FIELD;
+    if constexpr (kMode == kRecord)  // steps the control limited: the proposals' domain
+      if (limited && eps > 0.0) put_record(L, x, float(log(fabs(h) * sqrt(sqrt(o.tol / eps)))));
     // derivative columns through the accepted step (dB/dr neglected)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -307,8 +400,9 @@ __device__ uint32_t propagate(const F& fld, const OptionsDev& o, const Surf& s, 
     }
     if (limited) {
       const double fac = (eps > 0.0) ? step_factor(o.tol / eps, 0.25, 4.0) : 4.0;
-      h_ctrl = fmin(o.h_max, h_ctrl * fac);
+      h_ctrl = fmin(o.h_max, fabs(h) * fac);
     }
+    if constexpr (kMode == kRecord) L.h_last = float(fabs(h));
   }
   double B[3], Bt[3];
   bool oof = false;
@@ -338,10 +432,10 @@ __device__ __forceinline__ float parabolic_path_f(float d, float a, float b) {
   return s;
 }
 
-template <class F>
+template <int kMode, class F>
 __device__ uint32_t propagate_mixed(const F& fld, const OptionsDev& o, const Surf& s, const float nf[3], double r[3],
                                     double T[3], double lam, float dr[3][3], float dT[3][3], float& h_ctrl,
-                                    uint32_t& attempts, uint32_t& rejected, float kend[3]) {
+                                    uint32_t& attempts, uint32_t& rejected, float kend[3], StepLearn& L) {
   uint32_t st = 0;
   bool first = true;
   uint32_t n_here = 0;
@@ -388,8 +482,11 @@ __device__ uint32_t propagate_mixed(const F& fld, const OptionsDev& o, const Sur
     ++n_here;
     ++attempts;
     const float sp = parabolic_path_f(df, a, dotr(nf, k1));
-    const bool limited = !(fabsf(sp) < h_ctrl);
-    const float h = limited ? copysignf(h_ctrl, sp) : sp;
+    float x[kMode == kRecord ? 12 : 1];
+    if constexpr (kMode == kRecord) mlp_features(s, r, Tf, lam, B1, L.h_last, sl, x);
+    const float limit = h_ctrl;
+    const bool limited = !(fabsf(sp) < limit);
+    const float h = limited ? copysignf(limit, sp) : sp;
     const float h2 = 0.5f * h, h6 = h * (1.0f / 6.0f);
     float B2[3], B4[3], Bt2[3], Bt4[3], k2[3], k3[3], k4[3], T2[3], T3[3], T4[3];
     if (F::kUniform) {
@@ -424,6 +521,8 @@ __device__ uint32_t propagate_mixed(const F& fld, const OptionsDev& o, const Sur
       continue;
     }
     if (oof) st |= TKF_TRACK_OUT_OF_FIELD;
+    if constexpr (kMode == kRecord)  // steps the control limited: the proposals' domain
+      if (limited && eps > 0.0f) put_record(L, x, logf(fabsf(h) * sqrtf(sqrtf(tol / eps))));
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       float q1[3], q2[3], q3[3], q4[3], u2[3], u3[3], u4[3];
@@ -466,8 +565,9 @@ __device__ uint32_t propagate_mixed(const F& fld, const OptionsDev& o, const Sur
     }
     if (limited) {
       const float fac = (eps > 0.0f) ? step_factor_f(tol / eps) : 4.0f;
-      h_ctrl = fminf(h_max, h_ctrl * fac);
+      h_ctrl = fminf(h_max, fabsf(h) * fac);
     }
+    if constexpr (kMode == kRecord) L.h_last = fabsf(h);
   }
   float B[3], Bt[3];
   bool oof = false;
@@ -584,8 +684,8 @@ __device__ __forceinline__ void small_sincos_m1(double x, double& s, double& cm1
 // For k >= 1 the absolute angles are never output, so the filtered direction is carried as
 // (sin phi, cos phi, sin theta, cos theta): the predicted values come from the propagated
 // direction and the update's increments are applied by the angle-addition identities.
-template <bool kMixed, class F>
-__device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
+template <bool kMixed, int kMode, class F>
+__device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i, const float* mlp_w) {
   const uint32_t n = a.n_tracks;
   const uint32_t b0 = a.offsets[i], b1 = a.offsets[i + 1];
   double p[5], C[15];
@@ -624,8 +724,10 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
   double P[5][5];                // G_k C_k|k (smoother recursion)
   Surf sp;                       // surface of the previous measurement
   double sph = 0.0, cph = 1.0, sth = 1.0, cth = 0.0;  // filtered direction at sp
-  double h_ctrl = a.opt.h_max;
-  float h_ctrl_f = float(a.opt.h_max);
+  // learned mode: the step-size control starts from the network's proposal for this track
+  double h_ctrl = kMode == kLearned ? double(a.h0[i]) : a.opt.h_max;
+  float h_ctrl_f = kMode == kLearned ? a.h0[i] : float(a.opt.h_max);
+  StepLearn learn{mlp_w, a.records, a.record_capacity, a.record_count, float(a.opt.h_max), true};
 
   for (int k = 0; k < N && !(status & kFatal); ++k) {
     const uint32_t m = b0 + k;
@@ -645,7 +747,8 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
       double dr[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
       double dT[3][3] = {{-sth * sph, sth * cph, 0.0}, {cth * cph, cth * sph, -sth}, {0, 0, 0}};
       double kend[3];
-      status |= propagate(fld, a.opt, s, r, T, lam, dr, dT, h_ctrl, attempts, rejected, kend);
+      status |= propagate<kMode == kRecord ? kRecord : kPlain>(fld, a.opt, s, r, T, lam, dr, dT, h_ctrl, attempts,
+                                                              rejected, kend, learn);
       if (status & kFatal) break;
       // ---- bound parameters at the target and the transport Jacobian (path correction)
       const double inv_norm = 1.0 / sqrt(dot3(T, T));
@@ -725,7 +828,8 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
       float dT[3][3] = {{-fsth * fsph, fsth * fcph, 0.0f}, {fcth * fcph, fcth * fsph, -fsth}, {0, 0, 0}};
       const float nf[3] = {float(s.n[0]), float(s.n[1]), float(s.n[2])};
       float kend[3];
-      status |= propagate_mixed(fld, a.opt, s, nf, r, T, lam, dr, dT, h_ctrl_f, attempts, rejected, kend);
+      status |= propagate_mixed<kMode == kRecord ? kRecord : kPlain>(fld, a.opt, s, nf, r, T, lam, dr, dT, h_ctrl_f,
+                                                                    attempts, rejected, kend, learn);
       if (status & kFatal) break;
       // direction at the target in FP64 from FP32-seeded Newton steps (relative error ~1e-14)
       const double t2 = dot3(T, T), e2 = t2 - 1.0;
@@ -985,63 +1089,11 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
   }
 }
 
-// ------------------------------------------------------------------ track ordering
-// Counting sort of the tracks by key = (most measurements first, then lowest seed pT first):
-// warps then hold tracks with the same number of measurements and similar step counts, and
-// the work queue hands out the longest tracks first.
-constexpr int kPtBins = 16;
-constexpr int kNBins = 64;
-constexpr int kKeyBins = kPtBins * kNBins;
-
-__global__ void __launch_bounds__(256) order_keys_kernel(const uint32_t* __restrict__ offsets,
-                                                         const double* __restrict__ seed_par, uint32_t n,
-                                                         uint32_t* __restrict__ keys, uint32_t* __restrict__ hist) {
-  __shared__ uint32_t h[kKeyBins];
-  for (int b = threadIdx.x; b < kKeyBins; b += blockDim.x) h[b] = 0;
-  __syncthreads();
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) {
-    const uint32_t b0 = offsets[i], b1 = offsets[i + 1];
-    const uint32_t nh = b1 >= b0 ? min(b1 - b0, uint32_t(kNBins - 1)) : 0u;
-    const float qop = float(seed_par[size_t(4) * n + i]);
-    const float sth = fabsf(sinf(float(seed_par[size_t(3) * n + i])));
-    const float pt = (qop != 0.0f) ? sth / fabsf(qop) : 1e30f;
-    int pb = (pt > 0.0f) ? int(floorf(log2f(pt))) + 4 : 0;  // octaves from 1/16 GeV
-    pb = pb < 0 ? 0 : (pb >= kPtBins ? kPtBins - 1 : pb);
-    const uint32_t key = (uint32_t(kNBins - 1) - nh) * kPtBins + uint32_t(pb);
-    keys[i] = key;
-    atomicAdd(&h[key], 1u);
-  }
-  __syncthreads();
-  for (int b = threadIdx.x; b < kKeyBins; b += blockDim.x)
-    if (h[b]) atomicAdd(&hist[b], h[b]);
-}
-
-// exclusive scan of the kKeyBins histogram in place (one block of kKeyBins threads)
-__global__ void __launch_bounds__(kKeyBins) order_scan_kernel(uint32_t* __restrict__ hist) {
-  __shared__ uint32_t v[kKeyBins];
-  const int t = threadIdx.x;
-  v[t] = hist[t];
-  __syncthreads();
-  for (int off = 1; off < kKeyBins; off <<= 1) {
-    const uint32_t x = t >= off ? v[t - off] : 0u;
-    __syncthreads();
-    v[t] += x;
-    __syncthreads();
-  }
-  hist[t] = v[t] - hist[t];
-}
-
-__global__ void __launch_bounds__(256) order_scatter_kernel(const uint32_t* __restrict__ keys, uint32_t n,
-                                                            uint32_t* __restrict__ base, uint32_t* __restrict__ perm) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) perm[atomicAdd(&base[keys[i]], 1u)] = i;
-}
-
 // Persistent fit: each warp takes the next 32 tracks of the ordered list from a global counter.
-template <bool kMixed, class F>
+template <bool kMixed, int kMode, class F>
 __global__ void __launch_bounds__(128) fit_persistent_kernel(FitArgs a, F fld, const uint32_t* __restrict__ perm,
                                                              uint32_t* __restrict__ counter) {
+  const float* mlp_w = nullptr;
   const uint32_t lane = threadIdx.x & 31u;
   for (;;) {
     uint32_t base = 0;
@@ -1049,53 +1101,92 @@ __global__ void __launch_bounds__(128) fit_persistent_kernel(FitArgs a, F fld, c
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= a.n_tracks) break;
     const uint32_t j = base + lane;
-    if (j < a.n_tracks) fit_track<kMixed>(a, fld, perm[j]);
+    if (j < a.n_tracks) fit_track<kMixed, kMode>(a, fld, perm[j], mlp_w);
   }
+}
+
+// Learned mode pre-pass: one thread per track evaluates the network on the seed state at the
+// first surface, toward the second surface, and writes the step-size control's starting value
+// 0.9 exp(output), clamped to [h_min, h_max] (h_max where there is nothing to propagate).
+// Tracks in a warp are evaluated together, so the network runs convergent.
+template <class F>
+__global__ void __launch_bounds__(128) propose_start_kernel(FitArgs a, F fld, float* __restrict__ h0) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n_tracks) return;
+  const uint32_t n = a.n_tracks;
+  const uint32_t b0 = a.offsets[i], b1 = a.offsets[i + 1];
+  float h = float(a.opt.h_max);
+  const bool ok = b1 >= b0 && b1 - b0 >= 2 && b1 <= a.n_meas && a.sid[b0] < a.n_surf && a.sid[b0 + 1] < a.n_surf;
+  if (ok) {
+    Surf s0, s1;
+    load_surf(a.surf, a.sid[b0], s0);
+    load_surf(a.surf, a.sid[b0 + 1], s1);
+    double p[5];
+    for (int j = 0; j < 5; ++j) p[j] = a.seed_par[size_t(j) * n + i];
+    double sph, cph, sth, cth;
+    sincos(p[2], &sph, &cph);
+    sincos(p[3], &sth, &cth);
+    const double T[3] = {sth * cph, sth * sph, cth};
+    double r[3];
+    for (int j = 0; j < 3; ++j) r[j] = s0.c[j] + p[0] * s0.u[j] + p[1] * s0.v[j];
+    const float rf[3] = {float(r[0]), float(r[1]), float(r[2])};
+    const float Tf[3] = {float(T[0]), float(T[1]), float(T[2])};
+    float B[3];
+    bool oof = false;
+    fld.atf(rf, B, oof);
+    const double dist = s1.n[0] * (s1.c[0] - r[0]) + s1.n[1] * (s1.c[1] - r[1]) + s1.n[2] * (s1.c[2] - r[2]);
+    const double sl = dist / (s1.n[0] * T[0] + s1.n[1] * T[1] + s1.n[2] * T[2]);
+    float x[12];
+    mlp_features(s1, r, Tf, p[4], B, float(a.opt.h_max), float(sl), x);
+    const float q = 0.9f * expf(mlp_eval(a.mlp, x));
+    h = fminf(fmaxf(q, float(a.opt.h_min)), float(a.opt.h_max));
+    if (!isfinite(q)) h = float(a.opt.h_max);
+  }
+  h0[i] = h;
 }
 
 template <class F>
-cudaError_t launch_with(const FitArgs& a, const F& fld, bool mixed, const Workspace& ws, int blocks,
-                        cudaStream_t stream) {
-  const uint32_t n = a.n_tracks;
-  cudaError_t e = cudaMemsetAsync(ws.counter, 0, sizeof(uint32_t) * (1 + kKeyBins), stream);
-  if (e != cudaSuccess) return e;
-  const unsigned g256 = (n + 255) / 256;
-  order_keys_kernel<<<g256, 256, 0, stream>>>(a.offsets, a.seed_par, n, ws.keys, ws.hist);
-  order_scan_kernel<<<1, kKeyBins, 0, stream>>>(ws.hist);
-  order_scatter_kernel<<<g256, 256, 0, stream>>>(ws.keys, n, ws.hist, ws.perm);
-  if (mixed)
-    fit_persistent_kernel<true><<<blocks, 128, 0, stream>>>(a, fld, ws.perm, ws.counter);
-  else
-    fit_persistent_kernel<false><<<blocks, 128, 0, stream>>>(a, fld, ws.perm, ws.counter);
+cudaError_t launch_propose(const FitArgs& a, const F& fld, float* h0, cudaStream_t stream) {
+  propose_start_kernel<<<(a.n_tracks + 127) / 128, 128, 0, stream>>>(a, fld, h0);
   return cudaGetLastError();
 }
 
-}  // namespace
-
-size_t workspace_bytes(uint32_t n_tracks) {
-  return 256 + sizeof(uint32_t) * (kKeyBins + 2 * size_t(n_tracks)) + 256;
-}
-
-Workspace carve_workspace(void* base, uint32_t n_tracks) {
-  Workspace w;
-  uint32_t* p = static_cast<uint32_t*>(base);
-  w.counter = p;          // 1 word, followed directly by the histogram (one memset clears both)
-  w.hist = p + 1;
-  w.keys = p + 1 + kKeyBins;
-  w.perm = w.keys + n_tracks;
-  return w;
-}
-
-cudaError_t launch_fit(const FitArgs& a, const FieldDev& f, int precision, const Workspace& ws, int sm_count,
-                       cudaStream_t stream) {
-  if (a.n_tracks == 0) return cudaSuccess;
-  const bool mixed = precision == TKF_MIXED;
-  const int blocks = 2 * sm_count;  // 255 registers x 128 threads: two blocks per SM
+template <class R>
+cudaError_t propose_fields(const FitArgs& a, const FieldDev& f, float* h0, cudaStream_t stream) {
   if (f.kind == TKF_FIELD_UNIFORM) {
-    if (f.b[0] == 0.0 && f.b[1] == 0.0) return launch_with(a, FieldUniformZ{f.b[2]}, mixed, ws, blocks, stream);
-    return launch_with(a, FieldUniform{{f.b[0], f.b[1], f.b[2]}}, mixed, ws, blocks, stream);
+    if (f.b[0] == 0.0 && f.b[1] == 0.0) return launch_propose(a, FieldUniformZ{f.b[2]}, h0, stream);
+    return launch_propose(a, FieldUniform{{f.b[0], f.b[1], f.b[2]}}, h0, stream);
   }
-  return launch_with(a, FieldGrid{f.grid, f.nr, f.nz, f.r0, f.z0, f.inv_dr, f.inv_dz}, mixed, ws, blocks, stream);
+  return launch_propose(a, FieldGrid{f.grid, f.nr, f.nz, f.r0, f.z0, f.inv_dr, f.inv_dz}, h0, stream);
 }
 
+// Launches the persistent fit for one precision, step mode and field.
+template <bool kMixed, int kMode, class F>
+cudaError_t launch_persistent(const FitArgs& a, const F& fld, const uint32_t* perm, uint32_t* counter, int blocks,
+                              cudaStream_t stream) {
+  fit_persistent_kernel<kMixed, kMode><<<blocks, 128, 0, stream>>>(a, fld, perm, counter);
+  return cudaGetLastError();
+}
+
+template <bool kMixed, class F>
+cudaError_t launch_mode(const FitArgs& a, const F& fld, int mode, const uint32_t* perm, uint32_t* counter, int blocks,
+                        cudaStream_t stream) {
+  if (mode == kLearned) return launch_persistent<kMixed, kLearned>(a, fld, perm, counter, blocks, stream);
+  if (mode == kRecord) return launch_persistent<kMixed, kRecord>(a, fld, perm, counter, blocks, stream);
+  return launch_persistent<kMixed, kPlain>(a, fld, perm, counter, blocks, stream);
+}
+
+template <bool kMixed>
+cudaError_t launch_fields(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm, uint32_t* counter,
+                          int blocks, cudaStream_t stream) {
+  if (f.kind == TKF_FIELD_UNIFORM) {
+    if (f.b[0] == 0.0 && f.b[1] == 0.0)
+      return launch_mode<kMixed>(a, FieldUniformZ{f.b[2]}, mode, perm, counter, blocks, stream);
+    return launch_mode<kMixed>(a, FieldUniform{{f.b[0], f.b[1], f.b[2]}}, mode, perm, counter, blocks, stream);
+  }
+  return launch_mode<kMixed>(a, FieldGrid{f.grid, f.nr, f.nz, f.r0, f.z0, f.inv_dr, f.inv_dz}, mode, perm, counter,
+                             blocks, stream);
+}
+
+}  // namespace
 }  // namespace tkf

@@ -57,7 +57,15 @@ struct FitArgs {
   uint32_t n_surf;
   MaterialDev mat;
   OptionsDev opt;
+  const float* __restrict__ mlp;     // FP32 (BF16-rounded) step-proposer weights, or null
+  const float* __restrict__ h0;      // learned mode: per-track starting step-size control
+  float* __restrict__ records;       // training-record capture, or null
+  uint32_t record_capacity;
+  uint32_t* __restrict__ record_count;
 };
+
+constexpr int kMlpParams = TKF_MLP_PARAMS;
+constexpr int kMlpRecord = TKF_MLP_RECORD;
 
 // Scratch of one fit launch: work counter, key histogram, sort keys, track permutation.
 struct Workspace {
@@ -65,9 +73,17 @@ struct Workspace {
   uint32_t* hist = nullptr;
   uint32_t* keys = nullptr;
   uint32_t* perm = nullptr;
+  float* h0 = nullptr;  // learned mode: per-track starting step size (only when space was reserved)
 };
-size_t workspace_bytes(uint32_t n_tracks);
-Workspace carve_workspace(void* base, uint32_t n_tracks);
+size_t workspace_bytes(uint32_t n_tracks, bool learned);
+Workspace carve_workspace(void* base, uint32_t n_tracks, bool learned);
+cudaError_t launch_propose_start(const FitArgs& a, const FieldDev& f, float* h0, cudaStream_t stream);
+
+// Persistent fit launches per precision; mode 0 plain, 1 learned proposals, 2 record capture.
+cudaError_t launch_fit_fp64(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm, uint32_t* counter,
+                            int blocks, cudaStream_t stream);
+cudaError_t launch_fit_mixed(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm, uint32_t* counter,
+                             int blocks, cudaStream_t stream);
 
 // Enqueues the fit of every track in `a` on `stream`: track ordering, then the persistent fit.
 cudaError_t launch_fit(const FitArgs& a, const FieldDev& field, int precision, const Workspace& ws, int sm_count,
@@ -82,6 +98,9 @@ struct tkf_context_s {
   // fit workspace (ordering scratch), grown on demand and reused by later calls
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  // scratch of the network's training kernels
+  void* train_ws = nullptr;
+  size_t train_bytes = 0;
   // staging for tkf_fit_host
   void* stage = nullptr;
   size_t stage_bytes = 0;
@@ -105,4 +124,16 @@ struct tkf_field_s {
 struct tkf_mlp_s {
   tkf_context ctx = nullptr;
   int device = 0;
+  float* d_weights = nullptr;  // TKF_MLP_PARAMS FP32 values, each a BF16 value
 };
+
+namespace tkf {
+// Training scratch size and launches (tkf_mlp.cu).
+size_t mlp_train_scratch_bytes(uint32_t batch);
+cudaError_t mlp_loss_grad(const float* params, const float* x, int x_stride, const float* y, int y_stride,
+                          uint32_t n, float* grad, float* loss, void* scratch, cudaStream_t stream);
+cudaError_t mlp_train(const float* records, uint32_t n, uint32_t batch, uint32_t epochs, float lr, float beta1,
+                      float beta2, float eps, float* params, float* moments, uint32_t* adam_t, float* epoch_loss,
+                      void* scratch, cudaStream_t stream);
+cudaError_t mlp_forward(const float* params, const float* x, uint32_t n, float* out, cudaStream_t stream);
+}  // namespace tkf

@@ -1,0 +1,104 @@
+// tkf_order.cu -- track ordering for the fit (counting sort into a permutation) and the launch
+// sequence: ordering kernels, then the persistent fit of the requested precision and mode.
+
+#include "tkf_internal.cuh"
+
+namespace tkf {
+namespace {
+
+// ------------------------------------------------------------------ track ordering
+// Counting sort of the tracks by key = (most measurements first, then lowest seed pT first):
+// warps then hold tracks with the same number of measurements and similar step counts, and
+// the work queue hands out the longest tracks first.
+constexpr int kPtBins = 16;
+constexpr int kNBins = 64;
+constexpr int kKeyBins = kPtBins * kNBins;
+
+__global__ void __launch_bounds__(256) order_keys_kernel(const uint32_t* __restrict__ offsets,
+                                                         const double* __restrict__ seed_par, uint32_t n,
+                                                         uint32_t* __restrict__ keys, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[kKeyBins];
+  for (int b = threadIdx.x; b < kKeyBins; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const uint32_t b0 = offsets[i], b1 = offsets[i + 1];
+    const uint32_t nh = b1 >= b0 ? min(b1 - b0, uint32_t(kNBins - 1)) : 0u;
+    const float qop = float(seed_par[size_t(4) * n + i]);
+    const float sth = fabsf(sinf(float(seed_par[size_t(3) * n + i])));
+    const float pt = (qop != 0.0f) ? sth / fabsf(qop) : 1e30f;
+    int pb = (pt > 0.0f) ? int(floorf(log2f(pt))) + 4 : 0;  // octaves from 1/16 GeV
+    pb = pb < 0 ? 0 : (pb >= kPtBins ? kPtBins - 1 : pb);
+    const uint32_t key = (uint32_t(kNBins - 1) - nh) * kPtBins + uint32_t(pb);
+    keys[i] = key;
+    atomicAdd(&h[key], 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < kKeyBins; b += blockDim.x)
+    if (h[b]) atomicAdd(&hist[b], h[b]);
+}
+
+// exclusive scan of the kKeyBins histogram in place (one block of kKeyBins threads)
+__global__ void __launch_bounds__(kKeyBins) order_scan_kernel(uint32_t* __restrict__ hist) {
+  __shared__ uint32_t v[kKeyBins];
+  const int t = threadIdx.x;
+  v[t] = hist[t];
+  __syncthreads();
+  for (int off = 1; off < kKeyBins; off <<= 1) {
+    const uint32_t x = t >= off ? v[t - off] : 0u;
+    __syncthreads();
+    v[t] += x;
+    __syncthreads();
+  }
+  hist[t] = v[t] - hist[t];
+}
+
+__global__ void __launch_bounds__(256) order_scatter_kernel(const uint32_t* __restrict__ keys, uint32_t n,
+                                                            uint32_t* __restrict__ base, uint32_t* __restrict__ perm) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) perm[atomicAdd(&base[keys[i]], 1u)] = i;
+}
+
+}  // namespace
+
+size_t workspace_bytes(uint32_t n_tracks, bool learned) {
+  return 256 + sizeof(uint32_t) * (kKeyBins + (learned ? 3 : 2) * size_t(n_tracks)) + 256;
+}
+
+Workspace carve_workspace(void* base, uint32_t n_tracks, bool learned) {
+  Workspace w;
+  uint32_t* p = static_cast<uint32_t*>(base);
+  w.counter = p;          // 1 word, followed directly by the histogram (one memset clears both)
+  w.hist = p + 1;
+  w.keys = p + 1 + kKeyBins;
+  w.perm = w.keys + n_tracks;
+  if (learned) w.h0 = reinterpret_cast<float*>(w.perm + n_tracks);
+  return w;
+}
+
+cudaError_t launch_fit(const FitArgs& a, const FieldDev& f, int precision, const Workspace& ws, int sm_count,
+                       cudaStream_t stream) {
+  if (a.n_tracks == 0) return cudaSuccess;
+  const uint32_t n = a.n_tracks;
+  cudaError_t e = cudaMemsetAsync(ws.counter, 0, sizeof(uint32_t) * (1 + kKeyBins), stream);
+  if (e != cudaSuccess) return e;
+  const unsigned g256 = (n + 255) / 256;
+  order_keys_kernel<<<g256, 256, 0, stream>>>(a.offsets, a.seed_par, n, ws.keys, ws.hist);
+  order_scan_kernel<<<1, kKeyBins, 0, stream>>>(ws.hist);
+  order_scatter_kernel<<<g256, 256, 0, stream>>>(ws.keys, n, ws.hist, ws.perm);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int mode = a.mlp ? 1 : (a.records ? 2 : 0);  // learned, record capture, or plain
+  FitArgs b = a;
+  if (mode == 1) {  // network proposals of each track's starting step size
+    if (!ws.h0) return cudaErrorInvalidValue;
+    e = launch_propose_start(a, f, ws.h0, stream);
+    if (e != cudaSuccess) return e;
+    b.h0 = ws.h0;
+  }
+  const int blocks = 2 * sm_count;  // 255 registers x 128 threads: two blocks per SM
+  if (precision == TKF_MIXED) return launch_fit_mixed(b, f, mode, ws.perm, ws.counter, blocks, stream);
+  return launch_fit_fp64(b, f, mode, ws.perm, ws.counter, blocks, stream);
+}
+
+}  // namespace tkf

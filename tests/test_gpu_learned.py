@@ -1,0 +1,153 @@
+"""GPU tests of the learned step proposer: the library's training kernels against the FP64
+numpy reference (gradients, a short training run), record capture, and fits with learned
+proposals against the oracle running the same proposals, plus the gain over plain control."""
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2505_22822_gb300 as tkf
+import synth
+from oracle import mlp
+from tests import parity
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return tkf.Context(0)
+
+
+def _cuda(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0", dtype)
+
+
+def test_loss_and_gradient_match_the_fp64_reference(ctx):
+    rng = np.random.default_rng(0)
+    theta = mlp.init(1) + 0.05 * rng.normal(size=mlp.N_PARAMS)
+    X = rng.normal(size=(777, 12))
+    y = rng.normal(size=777)
+    loss, g = tkf.mlp_loss_grad(ctx, _cuda(theta), _cuda(X), _cuda(y))
+    torch.cuda.synchronize()
+    ref_loss, ref_g = mlp.loss_and_grad(theta.astype(np.float32).astype(np.float64), X.astype(np.float32), y.astype(np.float32))
+    assert abs(loss.item() - ref_loss) <= 1e-5 * ref_loss
+    g = g.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(g, ref_g, rtol=1e-3, atol=1e-5 * np.abs(ref_g).max())
+
+
+def test_forward_matches_the_oracle(ctx):
+    rng = np.random.default_rng(2)
+    theta = mlp.init(3) + 0.1 * rng.normal(size=mlp.N_PARAMS)
+    w = mlp.to_bf16(theta)
+    X = rng.normal(size=(500, 12)).astype(np.float32)
+    out = tkf.mlp_forward(ctx, _cuda(mlp.from_bf16(w)), _cuda(X)).cpu().numpy()
+    np.testing.assert_allclose(out, oracle.mlp_forward(w, X), rtol=1e-5, atol=1e-5)
+
+
+def test_training_steps_follow_the_fp64_adam_reference(ctx):
+    rng = np.random.default_rng(4)
+    X = rng.normal(size=(2048, 12))
+    y = np.sin(X[:, 0]) + 0.5 * X[:, 6] ** 2 - 0.3 * X[:, 10]
+    theta0 = mlp.init(5)
+    rec = np.concatenate([X, y[:, None]], axis=1)
+    p = _cuda(theta0)
+    mom = torch.zeros((2, mlp.N_PARAMS), dtype=torch.float32, device="cuda:0")
+    loss, t = tkf.mlp_train(ctx, _cuda(rec), p, mom, 0, batch=256, epochs=2, lr=1e-3)
+    torch.cuda.synchronize()
+    ref, ref_losses = mlp.train(theta0.astype(np.float32).astype(np.float64), X.astype(np.float32).astype(np.float64),
+                                y.astype(np.float32).astype(np.float64), batch=256, epochs=2, lr=1e-3)
+    assert t == 16
+    got = p.cpu().numpy().astype(np.float64)
+    # 16 Adam steps of 1e-3: FP32 vs FP64 agree to a small fraction of the total move
+    assert np.max(np.abs(got - ref)) < 2e-4
+    np.testing.assert_allclose(loss.cpu().numpy(), ref_losses, rtol=1e-3)
+
+
+def _fit(ctx, w, opts, tracks=None):
+    t = tracks if tracks is not None else w.tracks
+    geo = tkf.Geometry.from_table(ctx, w.geometry.table)
+    fld = tkf.Field.from_desc(ctx, w.field)
+    b = tkf.Batch.from_arrays(t.offsets, t.meas, t.sid, t.seed_par, t.seed_cov).to("cuda:0")
+    res = tkf.fit(ctx, geo, fld, b, opts)
+    torch.cuda.synchronize()
+    return res
+
+
+def train_proposer(ctx, fld, n_tracks=20000, epochs=8, seed=1000):
+    """Records from the plain stepper on seed-disjoint tracks, training on the GPU, calibration."""
+    from paper_2505_22822_gb300 import learn
+    w = synth.solenoid_muon_workload(n_tracks, seed=seed, fld=fld)
+    t = w.tracks
+    geo = tkf.Geometry.from_table(ctx, w.geometry.table)
+    f = tkf.Field.from_desc(ctx, w.field)
+    b = tkf.Batch.from_arrays(t.offsets, t.meas, t.sid, t.seed_par, t.seed_cov).to("cuda:0")
+    rec = learn.record_steps(ctx, geo, f, b, tkf.MIXED)
+    assert rec.shape[0] > 5000
+    theta, losses = learn.train(ctx, rec, epochs=epochs)
+    cal, q = learn.calibrate(ctx, theta, rec)
+    print({"records": int(rec.shape[0]), "losses": [round(float(x), 4) for x in losses], "bias_shift": q})
+    return rec, cal, losses
+
+
+@pytest.fixture(scope="module")
+def trained(ctx):
+    fld = synth.solenoid_map()
+    rec, theta, losses = train_proposer(ctx, fld)
+    return fld, rec, theta, losses
+
+
+def test_records_are_sane_and_training_converges(trained):
+    fld, rec, theta, losses = trained
+    r = rec.cpu().numpy()
+    assert np.all(np.isfinite(r))
+    assert np.all(np.abs(r[:, 3:6]) <= 1.0 + 1e-3)           # direction components
+    assert np.all((r[:, 12] > np.log(1e-4)) & (r[:, 12] < 12))  # ln(step / mm)
+    assert losses[-1] < 0.3 * losses[0]
+
+
+@pytest.mark.parametrize("precision", [tkf.MIXED, tkf.FP64])
+def test_learned_fit_matches_the_oracle_with_the_same_proposals(ctx, trained, precision):
+    fld, _, theta, _ = trained
+    wbf = mlp.to_bf16(theta)
+    m = tkf.Mlp(ctx, wbf)
+    w = synth.solenoid_muon_workload(3000, seed=3, fld=fld)
+    res = _fit(ctx, w, tkf.Options(precision=precision, step_mode=tkf.STEP_LEARNED, mlp=m))
+    g = parity.gpu_to_track_major(res)
+    o = oracle.fit(w.geometry.table, oracle.field_from(w.field), oracle.Options(mlp=wbf), w.tracks.offsets,
+                   w.tracks.meas, w.tracks.sid, w.tracks.seed_par, w.tracks.seed_cov, n_threads=8)
+    assert np.mean(g["status"] == o.status) > 0.999
+    good = (o.status == 0) & (g["status"] == 0)
+    C = oracle.unpack(o.cov[good])
+    sig = np.sqrt(np.einsum("nii->ni", C))
+    dp = g["par"][good] - o.par[good]
+    dp[:, 2] = (dp[:, 2] + np.pi) % (2 * np.pi) - np.pi
+    ds = (np.abs(dp) / sig).max(1)
+    tol = 1e-3 if precision == tkf.MIXED else 1e-8
+    assert np.mean(ds > tol) < 2e-3, (np.quantile(ds, [0.5, 0.99, 1.0]))
+
+
+def test_learned_proposals_save_step_attempts_at_equal_tolerance(ctx, trained):
+    fld, _, theta, _ = trained
+    m = tkf.Mlp(ctx, mlp.to_bf16(theta))
+    w = synth.solenoid_muon_workload(20000, seed=3, fld=fld)
+    plain = _fit(ctx, w, tkf.Options(precision=tkf.MIXED))
+    learn = _fit(ctx, w, tkf.Options(precision=tkf.MIXED, step_mode=tkf.STEP_LEARNED, mlp=m))
+    sp = plain.steps.cpu().numpy().astype(np.int64).sum(1)
+    sl = learn.steps.cpu().numpy().astype(np.int64).sum(1)
+    print({"plain_attempts": int(sp[0]), "plain_rejected": int(sp[1]),
+           "learned_attempts": int(sl[0]), "learned_rejected": int(sl[1])})
+    # same physics: the fits agree to a small fraction of sigma (different, valid step sequences)
+    gp, gl = parity.gpu_to_track_major(plain), parity.gpu_to_track_major(learn)
+    ok = (gp["status"] == 0) & (gl["status"] == 0)
+    C = oracle.unpack(gp["cov"][ok])
+    sig = np.sqrt(np.einsum("nii->ni", C))
+    d = gl["par"][ok] - gp["par"][ok]
+    d[:, 2] = (d[:, 2] + np.pi) % (2 * np.pi) - np.pi
+    assert np.quantile(np.abs(d) / sig, 0.999) < 0.05
+    # the proposals avoid the plain control's rejected attempts without costing extra steps
+    assert sl[1] < sp[1]
+    assert sl[0] <= sp[0]
