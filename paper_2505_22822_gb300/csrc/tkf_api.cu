@@ -148,6 +148,15 @@ tkf_status tkf_geometry_create(tkf_context ctx, const tkf_surface_desc* s, uint3
     o[13] = d.x0;
     o[14] = d.thickness / d.x0;
     o[15] = 0.0;
+    float* f = reinterpret_cast<float*>(o + 16);
+    for (int r = 0; r < 3; ++r) {
+      f[r] = float(col[0][r]);
+      f[3 + r] = float(col[1][r]);
+      f[6 + r] = float(col[2][r]);
+    }
+    f[9] = float(d.thickness);
+    f[10] = float(d.thickness / d.x0);
+    for (int k = 11; k < 16; ++k) f[k] = 0.0f;
   }
   DeviceGuard g(ctx->device);
   if (!g.ok) {
@@ -181,6 +190,11 @@ tkf_status tkf_geometry_create(tkf_context ctx, const tkf_surface_desc* s, uint3
   h->mat.hwp_ev = m.hbar_omega_p_ev;
   h->mat.log_hwp_over_i = log(m.hbar_omega_p_ev / m.i_ev);
   h->mat.bg2_density = exp(1.0 - 2.0 * h->mat.log_hwp_over_i);
+  h->mat.log_hwp_over_i_f = float(h->mat.log_hwp_over_i);
+  h->mat.bg2_density_f = float(h->mat.bg2_density);
+  const double I = m.i_ev * 1e-9;
+  h->mat.two_me_over_i2_f = float(2.0 * 0.51099895e-3 / (I * I));
+  h->mat.dedx_scale_f = float(0.307075 * m.z_over_a * m.rho_g_cm3 * 1e-4);
   *out = h;
   return TKF_OK;
 }
@@ -341,6 +355,11 @@ static tkf::FitArgs make_args(tkf_geometry geo, const tkf_fit_options* o, const 
   a.opt.surf_tol = o->surf_tol;
   a.opt.mass = o->mass;
   a.opt.max_steps = o->max_steps;
+  a.opt.tol_f = float(o->tol);
+  a.opt.h_max_f = float(o->h_max);
+  a.opt.h_min_f = float(o->h_min);
+  a.opt.mass_f = float(o->mass);
+  a.opt.me_over_mass_f = float(0.51099895e-3 / o->mass);
   a.mlp = (o->step_mode == TKF_STEP_LEARNED && o->mlp) ? o->mlp->d_weights : nullptr;
   a.records = (o->step_mode == TKF_STEP_ADAPTIVE) ? o->records : nullptr;
   a.record_capacity = o->record_capacity;

@@ -38,6 +38,7 @@ __host__ __device__ constexpr int S(int i, int j) { return i <= j ? i * (9 - i) 
 
 struct Surf {
   double u[3], v[3], n[3], c[3], t, x0, t_x0;
+  float uf[3], vf[3], nf[3], tf, t_x0f;  // FP32 copies (mixed path)
 };
 
 __device__ __forceinline__ void load_surf(const double* __restrict__ g, uint32_t id, Surf& s) {
@@ -49,6 +50,12 @@ __device__ __forceinline__ void load_surf(const double* __restrict__ g, uint32_t
   s.n[0] = a3.x; s.n[1] = a3.y; s.n[2] = a4.x;
   s.c[0] = a4.y; s.c[1] = a5.x; s.c[2] = a5.y;
   s.t = a6.x; s.x0 = a6.y; s.t_x0 = a7.x;
+  const float4* q = reinterpret_cast<const float4*>(p + 8);
+  const float4 f0 = __ldg(q), f1 = __ldg(q + 1), f2 = __ldg(q + 2);
+  s.uf[0] = f0.x; s.uf[1] = f0.y; s.uf[2] = f0.z;
+  s.vf[0] = f0.w; s.vf[1] = f1.x; s.vf[2] = f1.y;
+  s.nf[0] = f1.z; s.nf[1] = f1.w; s.nf[2] = f2.x;
+  s.tf = f2.y; s.t_x0f = f2.z;
 }
 
 __device__ __forceinline__ double dot3(const double a[3], const double b[3]) {
@@ -59,23 +66,25 @@ __device__ __forceinline__ double dot3(const double a[3], const double b[3]) {
 // Uniform field along z (the solenoid axis): T x B has no z component.
 struct FieldUniformZ {
   double bz;
+  float bzf;
   static constexpr bool kUniform = true;
   __device__ __forceinline__ void at(const double*, double B[3], bool&) const {
     B[0] = 0.0; B[1] = 0.0; B[2] = bz;
   }
   __device__ __forceinline__ void atf(const float*, float B[3], bool&) const {
-    B[0] = 0.0f; B[1] = 0.0f; B[2] = float(bz);
+    B[0] = 0.0f; B[1] = 0.0f; B[2] = bzf;
   }
 };
 
 struct FieldUniform {
   double b[3];
+  float bf[3];
   static constexpr bool kUniform = true;
   __device__ __forceinline__ void at(const double*, double B[3], bool&) const {
     B[0] = b[0]; B[1] = b[1]; B[2] = b[2];
   }
   __device__ __forceinline__ void atf(const float*, float B[3], bool&) const {
-    B[0] = float(b[0]); B[1] = float(b[1]); B[2] = float(b[2]);
+    B[0] = bf[0]; B[1] = bf[1]; B[2] = bf[2];
   }
 };
 
@@ -84,6 +93,7 @@ struct FieldGrid {
   const float2* __restrict__ grid;
   int nr, nz;
   double r0, z0, inv_dr, inv_dz;
+  float r0f, z0f, inv_drf, inv_dzf, rmaxf, zmaxf;  // FP32 copies: origin, 1/spacing, nr-1, nz-1
   static constexpr bool kUniform = false;
   __device__ __forceinline__ void at(const double* x, double B[3], bool& oof) const {
     double r = sqrt(x[0] * x[0] + x[1] * x[1]);
@@ -115,9 +125,9 @@ struct FieldGrid {
   // the same interpolation in FP32 (mixed precision)
   __device__ __forceinline__ void atf(const float* x, float B[3], bool& oof) const {
     const float r = sqrtf(x[0] * x[0] + x[1] * x[1]);
-    const float fr = (r - float(r0)) * float(inv_dr);
-    const float fz = (x[2] - float(z0)) * float(inv_dz);
-    if (!(fr >= 0.0f && fr <= float(nr - 1) && fz >= 0.0f && fz <= float(nz - 1))) {
+    const float fr = (r - r0f) * inv_drf;
+    const float fz = (x[2] - z0f) * inv_dzf;
+    if (!(fr >= 0.0f && fr <= rmaxf && fz >= 0.0f && fz <= zmaxf)) {
       B[0] = B[1] = B[2] = 0.0f;
       oof = true;
       return;
@@ -177,9 +187,9 @@ __device__ __forceinline__ double parabolic_path(double d, double a, double b) {
 __device__ __forceinline__ void mlp_features(const Surf& s, const double r[3], const float Tf[3], double lam,
                                              const float B[3], float h_last, float sl, float x[12]) {
   const float d[3] = {float(r[0] - s.c[0]), float(r[1] - s.c[1]), float(r[2] - s.c[2])};
-  const float u[3] = {float(s.u[0]), float(s.u[1]), float(s.u[2])};
-  const float v[3] = {float(s.v[0]), float(s.v[1]), float(s.v[2])};
-  const float n[3] = {float(s.n[0]), float(s.n[1]), float(s.n[2])};
+  const float* u = s.uf;
+  const float* v = s.vf;
+  const float* n = s.nf;
   x[0] = (u[0] * d[0] + u[1] * d[1] + u[2] * d[2]) * 1e-3f;
   x[1] = (v[0] * d[0] + v[1] * d[1] + v[2] * d[2]) * 1e-3f;
   x[2] = (n[0] * d[0] + n[1] * d[1] + n[2] * d[2]) * 1e-3f;
@@ -196,8 +206,8 @@ __device__ __forceinline__ void mlp_features(const Surf& s, const double r[3], c
 
 __device__ __forceinline__ float silu_f(float z) { return z / (1.0f + expf(-z)); }
 
-// Raw network output for inputs x; w = W1 [64][12], b1, W2 [64][64], b2, w3, b3 (global memory,
-// read through the read-only cache: every lane reads the same weight, once per track).
+// Raw network output for inputs x; w = W1 [64][12], b1, W2 [64][64], b2, w3, b3 (shared memory:
+// every lane reads the same weight, a broadcast).
 __device__ __forceinline__ float mlp_eval(const float* __restrict__ w, const float x[12]) {
   const float* W1 = w;
   const float* b1 = w + 768;
@@ -207,25 +217,32 @@ __device__ __forceinline__ float mlp_eval(const float* __restrict__ w, const flo
   float a1[64];
 #pragma unroll
   for (int j = 0; j < 64; ++j) {
-    float z = __ldg(b1 + j);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) z = fmaf(__ldg(W1 + j * 12 + i), x[i], z);
+    const float4* row = reinterpret_cast<const float4*>(W1 + j * 12);
+    const float4 c0 = row[0], c1 = row[1], c2 = row[2];
+    float z = b1[j];
+    z = fmaf(c0.x, x[0], z); z = fmaf(c0.y, x[1], z); z = fmaf(c0.z, x[2], z); z = fmaf(c0.w, x[3], z);
+    z = fmaf(c1.x, x[4], z); z = fmaf(c1.y, x[5], z); z = fmaf(c1.z, x[6], z); z = fmaf(c1.w, x[7], z);
+    z = fmaf(c2.x, x[8], z); z = fmaf(c2.y, x[9], z); z = fmaf(c2.z, x[10], z); z = fmaf(c2.w, x[11], z);
     a1[j] = silu_f(z);
   }
-  float out = __ldg(w + 5056);
-#pragma unroll 4
+  float out = w[5056];
+#pragma unroll 2
   for (int j = 0; j < 64; ++j) {
     const float4* row = reinterpret_cast<const float4*>(W2 + j * 64);
-    float z = __ldg(b2 + j);
+    float z0 = b2[j], z1 = 0.0f;
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const float4 c = __ldg(row + q);
-      z = fmaf(c.x, a1[4 * q], z);
-      z = fmaf(c.y, a1[4 * q + 1], z);
-      z = fmaf(c.z, a1[4 * q + 2], z);
-      z = fmaf(c.w, a1[4 * q + 3], z);
+    for (int q = 0; q < 16; q += 2) {
+      const float4 c = row[q], d = row[q + 1];
+      z0 = fmaf(c.x, a1[4 * q], z0);
+      z1 = fmaf(d.x, a1[4 * q + 4], z1);
+      z0 = fmaf(c.y, a1[4 * q + 1], z0);
+      z1 = fmaf(d.y, a1[4 * q + 5], z1);
+      z0 = fmaf(c.z, a1[4 * q + 2], z0);
+      z1 = fmaf(d.z, a1[4 * q + 6], z1);
+      z0 = fmaf(c.w, a1[4 * q + 3], z0);
+      z1 = fmaf(d.w, a1[4 * q + 7], z1);
     }
-    out = fmaf(__ldg(w3 + j), silu_f(z), out);
+    out = fmaf(w3[j], silu_f(z0 + z1), out);
   }
   return out;
 }
@@ -440,11 +457,13 @@ __device__ uint32_t propagate_mixed(const F& fld, const OptionsDev& o, const Sur
   bool first = true;
   uint32_t n_here = 0;
   const float lk = float(lam * kKappa);
-  const float tol = float(o.tol), h_min = float(o.h_min), h_max = float(o.h_max);
+  const float tol = o.tol_f, h_min = o.h_min_f, h_max = o.h_max_f;
   for (;;) {
     const double dist = s.n[0] * (s.c[0] - r[0]) + s.n[1] * (s.c[1] - r[1]) + s.n[2] * (s.c[2] - r[2]);
     const float Tf[3] = {float(T[0]), float(T[1]), float(T[2])};
-    const float rf[3] = {float(r[0]), float(r[1]), float(r[2])};
+    float rf[3] = {0.0f, 0.0f, 0.0f};
+    if (!F::kUniform || kMode == kRecord)
+      for (int i = 0; i < 3; ++i) rf[i] = float(r[i]);
     const float a = dotr(nf, Tf), df = float(dist);
     bool oof = false;
     float B1[3], Bt1[3], k1[3];
@@ -571,7 +590,9 @@ __device__ uint32_t propagate_mixed(const F& fld, const OptionsDev& o, const Sur
   }
   float B[3], Bt[3];
   bool oof = false;
-  const float rf[3] = {float(r[0]), float(r[1]), float(r[2])};
+  float rf[3] = {0.0f, 0.0f, 0.0f};
+  if (!F::kUniform)
+    for (int i = 0; i < 3; ++i) rf[i] = float(r[i]);
   const float Tf[3] = {float(T[0]), float(T[1]), float(T[2])};
   fld.atf(rf, B, oof);
   if (oof) st |= TKF_TRACK_OUT_OF_FIELD;
@@ -621,12 +642,13 @@ __device__ __forceinline__ uint32_t material(const Surf& s, const MaterialDev& m
 // Material in mixed precision: theta0^2 and the mean loss dE in FP32; the new q/p as
 // lam (1 - delta)^(-1/2) with delta = (2 E dE - dE^2) lam^2, i.e. lam + lam g in FP64 where
 // g = (1 - delta)^(-1/2) - 1 is formed in FP32 (series for small delta).
-__device__ __forceinline__ uint32_t material_mixed(const Surf& s, const MaterialDev& m, float mass, const float T[3],
-                                                   const float nf[3], double& lam, float& th0sq) {
+__device__ __forceinline__ uint32_t material_mixed(const Surf& s, const MaterialDev& m, const OptionsDev& o,
+                                                   const float T[3], double& lam, float& th0sq) {
   th0sq = 0.0f;
-  if (!(s.t > 0.0)) return 0;
-  const float inv_cos = 1.0f / fabsf(dotr(nf, T));
-  const float x = float(s.t) * inv_cos, xx0 = float(s.t_x0) * inv_cos;
+  if (!(s.tf > 0.0f)) return 0;
+  const float mass = o.mass_f;
+  const float inv_cos = 1.0f / fabsf(dotr(s.nf, T));
+  const float x = s.tf * inv_cos, xx0 = s.t_x0f * inv_cos;
   const float lf = float(lam), l2 = lf * lf;
   const float p2 = 1.0f / l2, m2 = mass * mass;
   const float E = sqrtf(p2 + m2);
@@ -635,15 +657,14 @@ __device__ __forceinline__ uint32_t material_mixed(const Surf& s, const Material
   const float aa = 0.0136f * E * l2;
   th0sq = aa * aa * xx0 * hl * hl;
   const float bg2 = p2 / m2;
-  const float me_m = float(kMe) / mass;
+  const float me_m = o.me_over_mass_f;
   const float wmax = 2.0f * float(kMe) * bg2 / (1.0f + 2.0f * (E / mass) * me_m + me_m * me_m);
-  const float I = float(m.i_ev * 1e-9);
   float bracket;
-  if (bg2 > float(m.bg2_density))
-    bracket = 0.5f * logf(2.0f * float(kMe) * wmax / (I * I)) - float(m.log_hwp_over_i) + 0.5f - beta2;
+  if (bg2 > m.bg2_density_f)
+    bracket = 0.5f * logf(m.two_me_over_i2_f * wmax) - m.log_hwp_over_i_f + 0.5f - beta2;
   else
-    bracket = 0.5f * logf(2.0f * float(kMe) * bg2 * wmax / (I * I)) - beta2;
-  const float dE = float(kBetheK * m.z_over_a) * inv_beta2 * bracket * float(m.rho) * x * 1e-4f;
+    bracket = 0.5f * logf(m.two_me_over_i2_f * bg2 * wmax) - beta2;
+  const float dE = m.dedx_scale_f * inv_beta2 * bracket * x;
   if (!(dE < E - mass)) return TKF_TRACK_PARTICLE_STOPPED;
   const float delta = (2.0f * E * dE - dE * dE) * l2;
   const float g = delta < 0.01f
@@ -726,8 +747,8 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i, const floa
   double sph = 0.0, cph = 1.0, sth = 1.0, cth = 0.0;  // filtered direction at sp
   // learned mode: the step-size control starts from the network's proposal for this track
   double h_ctrl = kMode == kLearned ? double(a.h0[i]) : a.opt.h_max;
-  float h_ctrl_f = kMode == kLearned ? a.h0[i] : float(a.opt.h_max);
-  StepLearn learn{mlp_w, a.records, a.record_capacity, a.record_count, float(a.opt.h_max), true};
+  float h_ctrl_f = kMode == kLearned ? a.h0[i] : a.opt.h_max_f;
+  StepLearn learn{mlp_w, a.records, a.record_capacity, a.record_count, a.opt.h_max_f, true};
 
   for (int k = 0; k < N && !(status & kFatal); ++k) {
     const uint32_t m = b0 + k;
@@ -814,11 +835,10 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i, const floa
         }
       } else {
       // ---- mixed precision: material, propagation, Jacobian and covariance transport in FP32
-      const float nprev[3] = {float(sp.n[0]), float(sp.n[1]), float(sp.n[2])};
       const float Tm[3] = {float(sth * cph), float(sth * sph), float(cth)};
       double lam = p[4];
       float th0sq;
-      status |= material_mixed(sp, a.mat, float(a.opt.mass), Tm, nprev, lam, th0sq);
+      status |= material_mixed(sp, a.mat, a.opt, Tm, lam, th0sq);
       if (status & kFatal) break;
       double T[3] = {sth * cph, sth * sph, cth};
       double r[3];
@@ -826,7 +846,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i, const floa
       const float fsth = float(sth), fcth = float(cth), fsph = float(sph), fcph = float(cph);
       float dr[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
       float dT[3][3] = {{-fsth * fsph, fsth * fcph, 0.0f}, {fcth * fcph, fcth * fsph, -fsth}, {0, 0, 0}};
-      const float nf[3] = {float(s.n[0]), float(s.n[1]), float(s.n[2])};
+      const float* nf = s.nf;
       float kend[3];
       status |= propagate_mixed<kMode == kRecord ? kRecord : kPlain>(fld, a.opt, s, nf, r, T, lam, dr, dT, h_ctrl_f,
                                                                     attempts, rejected, kend, learn);
@@ -854,8 +874,8 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i, const floa
       cp2 = tn[0] * inv_st;
       sp2 = tn[1] * inv_st;
       const float Tf[3] = {float(T[0]), float(T[1]), float(T[2])};
-      const float uf[3] = {float(s.u[0]), float(s.u[1]), float(s.u[2])};
-      const float vf[3] = {float(s.v[0]), float(s.v[1]), float(s.v[2])};
+      const float* uf = s.uf;
+      const float* vf = s.vf;
       const float inv_nT = 1.0f / dotr(nf, Tf);
       const float fst = float(st2), fct = float(ct2), fcp = float(cp2), fsp = float(sp2), finv_st = float(inv_st);
       float Jf[5][5];
@@ -863,7 +883,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i, const floa
       for (int c = 0; c < 5; ++c) {
         float x[3], t[3];
         for (int j = 0; j < 3; ++j) {
-          x[j] = (c == 0) ? float(sp.u[j]) : (c == 1) ? float(sp.v[j]) : dr[c - 2][j];
+          x[j] = (c == 0) ? sp.uf[j] : (c == 1) ? sp.vf[j] : dr[c - 2][j];
           t[j] = (c < 2) ? 0.0f : dT[c - 2][j];
         }
         const float ds = -dotr(nf, x) * inv_nT;
@@ -1105,17 +1125,25 @@ __global__ void __launch_bounds__(128) fit_persistent_kernel(FitArgs a, F fld, c
   }
 }
 
+inline FieldGrid grid_policy(const FieldDev& f) {
+  return FieldGrid{f.grid, f.nr, f.nz, f.r0, f.z0, f.inv_dr, f.inv_dz, float(f.r0), float(f.z0), float(f.inv_dr),
+                   float(f.inv_dz), float(f.nr - 1), float(f.nz - 1)};
+}
+
 // Learned mode pre-pass: one thread per track evaluates the network on the seed state at the
 // first surface, toward the second surface, and writes the step-size control's starting value
 // 0.9 exp(output), clamped to [h_min, h_max] (h_max where there is nothing to propagate).
 // Tracks in a warp are evaluated together, so the network runs convergent.
 template <class F>
-__global__ void __launch_bounds__(128) propose_start_kernel(FitArgs a, F fld, float* __restrict__ h0) {
+__global__ void __launch_bounds__(256) propose_start_kernel(FitArgs a, F fld, float* __restrict__ h0) {
+  __shared__ __align__(16) float w[(kMlpParams + 3) / 4 * 4];
+  for (int k = threadIdx.x; k < kMlpParams; k += blockDim.x) w[k] = a.mlp[k];
+  __syncthreads();
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n_tracks) return;
   const uint32_t n = a.n_tracks;
   const uint32_t b0 = a.offsets[i], b1 = a.offsets[i + 1];
-  float h = float(a.opt.h_max);
+  float h = a.opt.h_max_f;
   const bool ok = b1 >= b0 && b1 - b0 >= 2 && b1 <= a.n_meas && a.sid[b0] < a.n_surf && a.sid[b0 + 1] < a.n_surf;
   if (ok) {
     Surf s0, s1;
@@ -1137,27 +1165,28 @@ __global__ void __launch_bounds__(128) propose_start_kernel(FitArgs a, F fld, fl
     const double dist = s1.n[0] * (s1.c[0] - r[0]) + s1.n[1] * (s1.c[1] - r[1]) + s1.n[2] * (s1.c[2] - r[2]);
     const double sl = dist / (s1.n[0] * T[0] + s1.n[1] * T[1] + s1.n[2] * T[2]);
     float x[12];
-    mlp_features(s1, r, Tf, p[4], B, float(a.opt.h_max), float(sl), x);
-    const float q = 0.9f * expf(mlp_eval(a.mlp, x));
-    h = fminf(fmaxf(q, float(a.opt.h_min)), float(a.opt.h_max));
-    if (!isfinite(q)) h = float(a.opt.h_max);
+    mlp_features(s1, r, Tf, p[4], B, a.opt.h_max_f, float(sl), x);
+    const float q = 0.9f * expf(mlp_eval(w, x));
+    h = fminf(fmaxf(q, a.opt.h_min_f), a.opt.h_max_f);
+    if (!isfinite(q)) h = a.opt.h_max_f;
   }
   h0[i] = h;
 }
 
 template <class F>
 cudaError_t launch_propose(const FitArgs& a, const F& fld, float* h0, cudaStream_t stream) {
-  propose_start_kernel<<<(a.n_tracks + 127) / 128, 128, 0, stream>>>(a, fld, h0);
+  propose_start_kernel<<<(a.n_tracks + 255) / 256, 256, 0, stream>>>(a, fld, h0);
   return cudaGetLastError();
 }
 
 template <class R>
 cudaError_t propose_fields(const FitArgs& a, const FieldDev& f, float* h0, cudaStream_t stream) {
   if (f.kind == TKF_FIELD_UNIFORM) {
-    if (f.b[0] == 0.0 && f.b[1] == 0.0) return launch_propose(a, FieldUniformZ{f.b[2]}, h0, stream);
-    return launch_propose(a, FieldUniform{{f.b[0], f.b[1], f.b[2]}}, h0, stream);
+    if (f.b[0] == 0.0 && f.b[1] == 0.0) return launch_propose(a, FieldUniformZ{f.b[2], float(f.b[2])}, h0, stream);
+    return launch_propose(a, FieldUniform{{f.b[0], f.b[1], f.b[2]}, {float(f.b[0]), float(f.b[1]), float(f.b[2])}}, h0,
+                          stream);
   }
-  return launch_propose(a, FieldGrid{f.grid, f.nr, f.nz, f.r0, f.z0, f.inv_dr, f.inv_dz}, h0, stream);
+  return launch_propose(a, grid_policy(f), h0, stream);
 }
 
 // Launches the persistent fit for one precision, step mode and field.
@@ -1181,11 +1210,11 @@ cudaError_t launch_fields(const FitArgs& a, const FieldDev& f, int mode, const u
                           int blocks, cudaStream_t stream) {
   if (f.kind == TKF_FIELD_UNIFORM) {
     if (f.b[0] == 0.0 && f.b[1] == 0.0)
-      return launch_mode<kMixed>(a, FieldUniformZ{f.b[2]}, mode, perm, counter, blocks, stream);
-    return launch_mode<kMixed>(a, FieldUniform{{f.b[0], f.b[1], f.b[2]}}, mode, perm, counter, blocks, stream);
+      return launch_mode<kMixed>(a, FieldUniformZ{f.b[2], float(f.b[2])}, mode, perm, counter, blocks, stream);
+    return launch_mode<kMixed>(a, FieldUniform{{f.b[0], f.b[1], f.b[2]}, {float(f.b[0]), float(f.b[1]), float(f.b[2])}},
+                               mode, perm, counter, blocks, stream);
   }
-  return launch_mode<kMixed>(a, FieldGrid{f.grid, f.nr, f.nz, f.r0, f.z0, f.inv_dr, f.inv_dz}, mode, perm, counter,
-                             blocks, stream);
+  return launch_mode<kMixed>(a, grid_policy(f), mode, perm, counter, blocks, stream);
 }
 
 }  // namespace

@@ -10,15 +10,20 @@
 
 namespace tkf {
 
-// Device surface record: 16 doubles (128 B, one aligned L2 line pair) per surface:
-//   [0..2] u, [3..5] v, [6..8] n, [9..11] c, [12] thickness, [13] x0, [14] t / x0, [15] 0.
-constexpr int kSurfStride = 16;
+// Device surface record: 24 doubles (192 B) per surface:
+//   [0..2] u, [3..5] v, [6..8] n, [9..11] c, [12] thickness, [13] x0, [14] t / x0, [15] 0,
+//   then 16 floats: u, v, n, thickness, t / x0 (FP32 copies for the mixed path), 5 x 0.
+constexpr int kSurfStride = 24;
 
 // Material constants folded for the kernels.
 struct MaterialDev {
   double z_over_a, i_ev, rho, hwp_ev;
   double log_hwp_over_i;  // ln(hbar omega_p / I)
   double bg2_density;     // (beta gamma)^2 above which the density-effect term is positive
+  // FP32 copies for the mixed path
+  float log_hwp_over_i_f, bg2_density_f;
+  float two_me_over_i2_f;  // 2 m_e / I^2, 1/GeV
+  float dedx_scale_f;      // K Z/A rho 1e-4: MeV cm^2/g -> GeV per mm of path
 };
 
 struct FieldDev {
@@ -33,6 +38,8 @@ struct FieldDev {
 struct OptionsDev {
   double tol, h_max, h_min, surf_tol, mass;
   uint32_t max_steps;
+  // FP32 copies for the mixed path
+  float tol_f, h_max_f, h_min_f, mass_f, me_over_mass_f;
 };
 
 struct FitArgs {
