@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--events", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="launch directly instead of replaying a CUDA graph")
+    ap.add_argument("--no-autotune", action="store_true", help="fixed 128 x 2 block shape instead of the tuned one")
+    ap.add_argument("--sweep", action="store_true",
+                    help="throughput sweep 1e3..1e7 tracks per launch in the solenoid map (one JSON line per point)")
     return ap.parse_args()
 
 
@@ -226,6 +230,115 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def setup_tune_cache() -> str:
+    """Autotuner cache file (TKF_AUTOTUNE_CACHE, else a fresh temporary file); read back to
+    report the tuned block shapes. Set before the first context is created."""
+    path = os.environ.get("TKF_AUTOTUNE_CACHE")
+    if not path:
+        fd, path = tempfile.mkstemp(prefix="tkf_tune_", suffix=".json")
+        os.close(fd)
+        os.unlink(path)
+        os.environ["TKF_AUTOTUNE_CACHE"] = path
+    return path
+
+
+def tuned_shape(path: str, variant: str, n_tracks: int, field: str, disabled: bool):
+    """[threads, blocks per SM] the autotuner chose for this launch class."""
+    if disabled:
+        return [128, 2]
+    prec = "fp64" if variant == "fp64" else "mixed"
+    mode = "learned" if variant.endswith("learned") else "adaptive"
+    prefix = f"{prec}.{mode}.{field}.n{int(n_tracks).bit_length() - 1}."
+    try:
+        with open(path) as fh:
+            table = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    return next((v for k, v in table.items() if k.startswith(prefix)), None)
+
+
+def _prefix_batch(b, n: int):
+    """The first n tracks of a device batch (measurement arrays shared)."""
+    import paper_2505_22822_gb300 as tkf
+    return tkf.Batch(b.offsets[:n + 1].clone(), b.loc0, b.loc1, b.v00, b.v01, b.v11, b.sid,
+                     b.seed_par[:, :n].contiguous(), b.seed_cov[:, :n].contiguous())
+
+
+def _tile_batch(b, k: int):
+    """k copies of a device batch back to back (offsets shifted)."""
+    import torch
+    import paper_2505_22822_gb300 as tkf
+    m = b.n_meas
+    off = b.offsets.to(torch.int64)
+    offs = torch.cat([off[:-1] + j * m for j in range(k)] + [off[-1:] + (k - 1) * m]).to(torch.int32)
+    rep = [getattr(b, f).repeat(k) for f in ("loc0", "loc1", "v00", "v01", "v11", "sid")]
+    return tkf.Batch(offs, *rep, b.seed_par.repeat(1, k), b.seed_cov.repeat(1, k))
+
+
+def run_sweep(args, local: int, rank: int, tune_file: str):
+    """Tracks/s against tracks per launch (1e3..1e7) in the barrel + endcap detector and the
+    solenoid field map, events of log-uniform 1e3..1e5 pions batched per launch, for plain
+    FP64, mixed and mixed + learned, each replayed from a CUDA graph with the autotuned block
+    shape (and, up to 1e5 tracks, also launched directly). 1e6 distinct tracks are simulated;
+    the 1e7 point fits ten copies of them. One JSON line per point."""
+    import torch
+    import paper_2505_22822_gb300 as tkf
+    from paper_2505_22822_gb300 import learn
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    g, f = synth.barrel_endcap_geometry(), synth.solenoid_map()
+    pp = synth.barrel_params(step=5.0)
+    t0 = time.perf_counter()
+    counts = synth.event_counts_loguniform(500 + shard_seed(rank), 10 ** 6)
+    t = synth.simulate(g, f, pp, 500 + shard_seed(rank), counts)
+    tw = synth.simulate(g, f, pp, 20_000 + shard_seed(rank), synth.event_counts_loguniform(20_000, 200_000))
+    gen_s = time.perf_counter() - t0
+    ctx = tkf.Context(local)
+    geo, fld = tkf.Geometry.from_table(ctx, g.table), tkf.Field.from_desc(ctx, f)
+    full = tkf.Batch.from_arrays(t.offsets, t.meas, t.sid, t.seed_par, t.seed_cov).to(dev)
+    tb = tkf.Batch.from_arrays(tw.offsets, tw.meas, tw.sid, tw.seed_par, tw.seed_cov).to(dev)
+    proposer, info = learn.build_proposer(ctx, geo, fld, tb, tkf.MIXED, mass=synth.MUON_MASS)
+    del tb
+    print(json.dumps({"sweep": "setup", "workload": "barrel_endcap_solenoid_map_pions_loguniform_events",
+                      "events": int(len(counts)), "tracks": int(t.n_tracks), "measurements": int(t.n_hits),
+                      "generate_s": round(gen_s, 1), "proposer_records": info["records"]}), flush=True)
+    sizes = [10 ** 3, 10 ** 4, 10 ** 5, 10 ** 6, 10 ** 7]
+    for n in sizes:
+        k = -(-n // full.n_tracks)
+        b = _prefix_batch(_tile_batch(full, k) if k > 1 else full, n)
+        out = tkf.alloc_outputs(n, dev, steps=True)
+        for variant in ("fp64", "mixed", "mixed_learned"):
+            for graph in ((True, False) if n <= 10 ** 5 else (True,)):
+                opts = tkf.Options(precision=tkf.FP64 if variant == "fp64" else tkf.MIXED, mass=synth.MUON_MASS,
+                                   graph=graph, autotune=True)
+                if variant.endswith("learned"):
+                    opts.step_mode, opts.mlp = tkf.STEP_LEARNED, proposer
+                for _ in range(max(3, args.warmup)):
+                    tkf.fit(ctx, geo, fld, b, opts, out=out, stream=stream)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                tkf.fit(ctx, geo, fld, b, opts, out=out, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                reps = int(min(500, max(5, 0.5e3 / max(e0.elapsed_time(e1), 1e-3))))
+                with ClockSampler(local) as clk:
+                    e0.record(stream)
+                    for _ in range(reps):
+                        tkf.fit(ctx, geo, fld, b, opts, out=out, stream=stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                status = out.status.cpu().numpy().view(np.uint32)
+                print(json.dumps({"sweep": "point", "tracks_per_launch": n, "variant": variant, "cuda_graph": graph,
+                                  "tracks_per_s": n / (ms * 1e-3), "ms_per_launch": ms, "reps": reps,
+                                  "block_shape": tuned_shape(tune_file, variant, n, "grid", False),
+                                  "fit_status_ok": float(np.mean(status == 0)),
+                                  "clocks": clk.summary()}), flush=True)
+        del b, out
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -247,6 +360,10 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    tune_file = setup_tune_cache()
+    if args.sweep:
+        run_sweep(args, local, rank, tune_file)
+        return
     w = make_workload(args.events, rank)
     t = w.tracks
     n_tracks, n_meas = t.n_tracks, t.n_hits
@@ -256,7 +373,9 @@ def main():
     host = tkf.Batch.from_arrays(t.offsets, t.meas, t.sid, t.seed_par, t.seed_cov)
     dev = host.to(f"cuda:{local}")
     variants = ["fp64", "mixed", "mixed_learned"] if args.variant == "auto" else [args.variant]
-    stream = torch.cuda.current_stream()
+    # a side stream: CUDA graphs cannot be captured on the legacy default stream
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     hits_k1 = int((np.diff(t.offsets.astype(np.int64)) - 1).clip(min=0).sum())
     proposer, learn_info = None, None
     if any(v.endswith("learned") for v in variants):
@@ -272,10 +391,12 @@ def main():
                       "tracks": tt.n_tracks}
     results = {}
     for variant in variants:
-        opts = tkf.Options(precision=tkf.FP64 if variant == "fp64" else tkf.MIXED, mass=w.mass)
+        opts = tkf.Options(precision=tkf.FP64 if variant == "fp64" else tkf.MIXED, mass=w.mass,
+                           graph=not args.no_graph, autotune=not args.no_autotune)
         if variant.endswith("learned"):
             opts.step_mode, opts.mlp = tkf.STEP_LEARNED, proposer
         out = tkf.alloc_outputs(n_tracks, dev.offsets.device, steps=True)
+        # warm-up: the first call tunes the block shape, the second captures the graph
         for _ in range(args.warmup):
             tkf.fit(ctx, geo, fld, dev, opts, out=out, stream=stream)
         torch.cuda.synchronize()
@@ -296,6 +417,7 @@ def main():
         ms = ev0.elapsed_time(ev1) / args.steps
         ms_max = max_over_ranks(ms, dist, f"cuda:{local}")
         results[variant] = {"ms": ms, "ms_max": ms_max, "clocks": clk.summary(), "opts": opts,
+                            "shape": tuned_shape(tune_file, variant, n_tracks, "uz", args.no_autotune),
                             "attempts": attempts, "rejected": rejected, "status_ok": float(np.mean(status == 0)),
                             "pulls": pull_stats(out, t)}
     head = variants[-1]
@@ -360,7 +482,11 @@ def main():
                    "measurements_per_gpu": n_meas, "events_per_gpu": args.events,
                    "field": "uniform 2 T along z", "l2": "inputs 0.41 GB > L2, no flush",
                    "step_mode": "learned starting step + adaptive" if head.endswith("learned") else "adaptive"},
-        "gpu_launches": 4 * args.steps,
+        # per step: key, scan and scatter kernels of the ordering, the proposal pre-pass
+        # (learned), the persistent fit (plus one memset node)
+        "gpu_launches": (5 if head.endswith("learned") else 4) * args.steps,
+        "launch_policy": {"cuda_graph": not args.no_graph, "autotune": not args.no_autotune,
+                          "block_shape": {k: v["shape"] for k, v in results.items()}},
         "roofline": roof,
         "clocks": clocks,
         "variants": {k: {"tracks_per_s": aggregate_throughput(n_tracks, ws, v["ms_max"] * 1e-3),

@@ -169,7 +169,31 @@ typedef struct tkf_fit_options {
   float* records;
   uint32_t record_capacity;
   uint32_t* record_count;
+  /* Launch policy (no effect on the results: every track's arithmetic is the same under any
+   * block shape). flags: TKF_FIT_AUTOTUNE and/or TKF_FIT_GRAPH, default 0. block_threads
+   * (32, 64, 128 or 256) and blocks_per_sm (1..32) fix the persistent kernel's block shape
+   * when both are nonzero; 0, 0 takes the tuned shape of this launch class when
+   * TKF_FIT_AUTOTUNE is set, else 128 threads x 2 blocks per SM. */
+  uint32_t flags;
+  uint32_t block_threads;
+  uint32_t blocks_per_sm;
 } tkf_fit_options;
+
+/* Autotuning: the first call of a launch class (precision, step mode, field kind, batch size
+ * rounded down to a power of two, SM count) times every candidate block shape on the call's
+ * own inputs (each candidate runs the whole fit into the call's outputs, then the call runs
+ * with the fastest shape) and keeps the winner in the context. The call synchronizes its
+ * stream while tuning. If the environment variable TKF_AUTOTUNE_CACHE names a file when the
+ * context is created, tuned shapes are read from it and every new one is written back (JSON
+ * object: class -> [threads, blocks per SM]); an unreadable or unwritable file is ignored.
+ * Skipped (defaults used) while the stream is capturing and in record-capture mode. */
+#define TKF_FIT_AUTOTUNE 1u
+/* Graph replay: the ordering and fit launches of a call are captured into a CUDA graph on the
+ * second consecutive call with identical arguments (every pointer, size, option, handle and
+ * the block shape) and replayed as one graph launch by every further identical call; any
+ * change of argument launches directly again. Needs a stream other than the legacy default
+ * stream (ignored there and while the caller is itself capturing the stream). */
+#define TKF_FIT_GRAPH 2u
 
 void tkf_fit_options_default(tkf_fit_options* opts);
 
@@ -210,9 +234,11 @@ typedef struct tkf_fit_outputs {
  * legacy default stream). Nothing is copied between host and device. Device pointers must
  * be 8-byte aligned and stay valid until the stream reaches this work.
  * Errors (nothing enqueued): TKF_ERR_INVALID_ARG (NULL required pointers, n_meas too large
- * for 32-bit offsets, bad options, misaligned pointers), TKF_ERR_BAD_HANDLE,
- * TKF_ERR_UNSUPPORTED (TKF_STEP_LEARNED without an mlp), TKF_ERR_DEVICE (launch failure).
- * Offsets are read on the device: a decreasing pair flags TKF_TRACK_BAD_INPUT. */
+ * for 32-bit offsets, bad options or block shape, misaligned pointers), TKF_ERR_BAD_HANDLE,
+ * TKF_ERR_UNSUPPORTED (TKF_STEP_LEARNED without an mlp), TKF_ERR_DEVICE (launch, capture or
+ * graph failure). Offsets are read on the device: a decreasing pair flags
+ * TKF_TRACK_BAD_INPUT. The call blocks on the stream only when the context's workspace must
+ * grow and while autotuning (TKF_FIT_AUTOTUNE, first call of a launch class). */
 tkf_status tkf_fit(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf_fit_options* opts,
                    const tkf_fit_inputs* in, const tkf_fit_outputs* out, void* stream);
 
@@ -298,6 +324,8 @@ tkf_status tkf_mlp_forward(tkf_context ctx, const float* params, const float* x,
  *   - Every call on a device shares the one array: calls whose work overlaps on the GPU
  *     (different streams, or different contexts, without ordering) race and give wrong
  *     results. Serialize them.
+ *   - It ignores the flags TKF_FIT_AUTOTUNE and TKF_FIT_GRAPH (both allocate); an explicit
+ *     block shape is used.
  * Arguments, outputs and the other errors are those of tkf_fit. */
 #define TKF_NOALLOC_MAX_TRACKS 2097152u
 tkf_status tkf_fit_noalloc(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf_fit_options* opts,

@@ -24,7 +24,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _ROOT = os.path.dirname(_HERE)
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "libtkf.so")
-_SOURCES = ["tkf_api.cu", "tkf_order.cu", "tkf_fit_fp64.cu", "tkf_fit_mixed.cu", "tkf_mlp.cu"]
+_SOURCES = ["tkf_api.cu", "tkf_order.cu", "tkf_policy.cu", "tkf_fit_fp64.cu", "tkf_fit_mixed.cu", "tkf_mlp.cu"]
 _lib = None
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
@@ -32,6 +32,7 @@ NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", 
 
 FP64, MIXED = 0, 1
 STEP_ADAPTIVE, STEP_LEARNED = 0, 1
+FIT_AUTOTUNE, FIT_GRAPH = 1, 2
 FIELD_UNIFORM, FIELD_RZ_GRID = 0, 1
 
 TRACK_STATUS = {
@@ -107,7 +108,9 @@ class FitOptions(ctypes.Structure):
                 ("h_max", ctypes.c_double), ("h_min", ctypes.c_double),
                 ("surf_tol", ctypes.c_double), ("max_steps", ctypes.c_uint32),
                 ("mass", ctypes.c_double), ("mlp", ctypes.c_void_p), ("records", ctypes.c_void_p),
-                ("record_capacity", ctypes.c_uint32), ("record_count", ctypes.c_void_p)]
+                ("record_capacity", ctypes.c_uint32), ("record_count", ctypes.c_void_p),
+                ("flags", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
+                ("blocks_per_sm", ctypes.c_uint32)]
 
 
 class MlpTrainOptions(ctypes.Structure):
@@ -319,6 +322,10 @@ class Options:
     mlp: object = None            # Mlp for STEP_LEARNED
     records: object = None        # CUDA float tensor [capacity, 13] for record capture
     record_count: object = None   # CUDA int32 tensor [1], zeroed by the caller
+    autotune: bool = False        # time the candidate block shapes on the first call of a class
+    graph: bool = False           # capture repeated identical calls into a CUDA graph
+    block_threads: int = 0        # explicit block shape (both nonzero), else default or tuned
+    blocks_per_sm: int = 0
 
     def c(self) -> FitOptions:
         o = FitOptions()
@@ -332,6 +339,8 @@ class Options:
             o.records = self.records.data_ptr()
             o.record_capacity = int(self.records.shape[0])
             o.record_count = self.record_count.data_ptr()
+        o.flags = (FIT_AUTOTUNE if self.autotune else 0) | (FIT_GRAPH if self.graph else 0)
+        o.block_threads, o.blocks_per_sm = self.block_threads, self.blocks_per_sm
         return o
 
 

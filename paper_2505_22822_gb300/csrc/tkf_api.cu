@@ -73,14 +73,16 @@ tkf_status tkf_context_create(int device, tkf_context* out) {
   if (!c) return fail(nullptr, TKF_ERR_OOM, "tkf_context_create: host allocation failed");
   c->device = device;
   c->sm_count = prop.multiProcessorCount;
+  tkf::load_tune_cache(c);
   *out = c;
   return TKF_OK;
 }
 
 void tkf_context_destroy(tkf_context ctx) {
   if (!ctx) return;
-  if (ctx->stage || ctx->ws || ctx->train_ws) {
+  if (ctx->stage || ctx->ws || ctx->train_ws || ctx->graph_exec) {
     DeviceGuard g(ctx->device);
+    tkf::release_graph(ctx);
     if (ctx->stage) cudaFree(ctx->stage);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->train_ws) cudaFree(ctx->train_ws);
@@ -288,6 +290,9 @@ void tkf_fit_options_default(tkf_fit_options* o) {
   o->records = nullptr;
   o->record_capacity = 0;
   o->record_count = nullptr;
+  o->flags = 0;
+  o->block_threads = 0;
+  o->blocks_per_sm = 0;
 }
 
 static tkf_status check_common(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf_fit_options* o,
@@ -311,6 +316,11 @@ static tkf_status check_common(tkf_context ctx, tkf_geometry geo, tkf_field fiel
       o->max_steps == 0 || !(o->mass > 0) || !isfinite(o->h_max))
     return fail(ctx, TKF_ERR_INVALID_ARG,
                 std::string(fn) + ": options need tol, h_max, h_min, surf_tol, mass > 0, h_min <= h_max, max_steps > 0");
+  if ((o->flags & ~(TKF_FIT_AUTOTUNE | TKF_FIT_GRAPH)) != 0)
+    return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": unknown flag");
+  if (!tkf::valid_block_shape(o->block_threads, o->blocks_per_sm))
+    return fail(ctx, TKF_ERR_INVALID_ARG,
+                std::string(fn) + ": block shape needs threads 32, 64, 128 or 256 and 1..32 blocks per SM (or 0, 0)");
   if (in->n_meas > 0xffffffffull)
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": n_meas exceeds 32-bit offsets");
   if (in->n_tracks == 0) return TKF_OK;
@@ -388,7 +398,11 @@ tkf_status tkf_fit(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf
     ctx->ws_bytes = need;
   }
   tkf::Workspace ws = tkf::carve_workspace(ctx->ws, in->n_tracks, learned);
-  cudaError_t e = tkf::launch_fit(a, field->f, o->precision, ws, ctx->sm_count, static_cast<cudaStream_t>(stream));
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  tkf::LaunchShape shape;
+  cudaError_t e = tkf::resolve_shape(ctx, a, field->f, o->precision, ws, o, st, &shape);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit: autotune");
+  e = tkf::launch_with_policy(ctx, a, field->f, o->precision, ws, shape, (o->flags & TKF_FIT_GRAPH) != 0, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit: launch");
   return TKF_OK;
 }
@@ -630,7 +644,13 @@ extern "C" tkf_status tkf_fit_noalloc(tkf_context ctx, tkf_geometry geo, tkf_fie
   tkf::FitArgs a = make_args(geo, o, in, out);
   // the launch clears the counter and histogram before use (the array keeps the last call's data)
   tkf::Workspace ws = tkf::carve_workspace(scratch, in->n_tracks, false);
-  e = tkf::launch_fit(a, field->f, o->precision, ws, ctx->sm_count, static_cast<cudaStream_t>(stream));
+  tkf::LaunchShape shape;
+  shape.blocks = 2 * ctx->sm_count;
+  if (o->block_threads && o->blocks_per_sm) {
+    shape.threads = int(o->block_threads);
+    shape.blocks = int(o->blocks_per_sm) * ctx->sm_count;
+  }
+  e = tkf::launch_fit(a, field->f, o->precision, ws, shape, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_noalloc: launch");
   return TKF_OK;
 }

@@ -1111,7 +1111,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i, const floa
 
 // Persistent fit: each warp takes the next 32 tracks of the ordered list from a global counter.
 template <bool kMixed, int kMode, class F>
-__global__ void __launch_bounds__(128) fit_persistent_kernel(FitArgs a, F fld, const uint32_t* __restrict__ perm,
+__global__ void __launch_bounds__(256) fit_persistent_kernel(FitArgs a, F fld, const uint32_t* __restrict__ perm,
                                                              uint32_t* __restrict__ counter) {
   const float* mlp_w = nullptr;
   const uint32_t lane = threadIdx.x & 31u;
@@ -1191,30 +1191,30 @@ cudaError_t propose_fields(const FitArgs& a, const FieldDev& f, float* h0, cudaS
 
 // Launches the persistent fit for one precision, step mode and field.
 template <bool kMixed, int kMode, class F>
-cudaError_t launch_persistent(const FitArgs& a, const F& fld, const uint32_t* perm, uint32_t* counter, int blocks,
-                              cudaStream_t stream) {
-  fit_persistent_kernel<kMixed, kMode><<<blocks, 128, 0, stream>>>(a, fld, perm, counter);
+cudaError_t launch_persistent(const FitArgs& a, const F& fld, const uint32_t* perm, uint32_t* counter,
+                              LaunchShape shape, cudaStream_t stream) {
+  fit_persistent_kernel<kMixed, kMode><<<shape.blocks, shape.threads, 0, stream>>>(a, fld, perm, counter);
   return cudaGetLastError();
 }
 
 template <bool kMixed, class F>
-cudaError_t launch_mode(const FitArgs& a, const F& fld, int mode, const uint32_t* perm, uint32_t* counter, int blocks,
-                        cudaStream_t stream) {
-  if (mode == kLearned) return launch_persistent<kMixed, kLearned>(a, fld, perm, counter, blocks, stream);
-  if (mode == kRecord) return launch_persistent<kMixed, kRecord>(a, fld, perm, counter, blocks, stream);
-  return launch_persistent<kMixed, kPlain>(a, fld, perm, counter, blocks, stream);
+cudaError_t launch_mode(const FitArgs& a, const F& fld, int mode, const uint32_t* perm, uint32_t* counter,
+                        LaunchShape shape, cudaStream_t stream) {
+  if (mode == kLearned) return launch_persistent<kMixed, kLearned>(a, fld, perm, counter, shape, stream);
+  if (mode == kRecord) return launch_persistent<kMixed, kRecord>(a, fld, perm, counter, shape, stream);
+  return launch_persistent<kMixed, kPlain>(a, fld, perm, counter, shape, stream);
 }
 
 template <bool kMixed>
 cudaError_t launch_fields(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm, uint32_t* counter,
-                          int blocks, cudaStream_t stream) {
+                          LaunchShape shape, cudaStream_t stream) {
   if (f.kind == TKF_FIELD_UNIFORM) {
     if (f.b[0] == 0.0 && f.b[1] == 0.0)
-      return launch_mode<kMixed>(a, FieldUniformZ{f.b[2], float(f.b[2])}, mode, perm, counter, blocks, stream);
+      return launch_mode<kMixed>(a, FieldUniformZ{f.b[2], float(f.b[2])}, mode, perm, counter, shape, stream);
     return launch_mode<kMixed>(a, FieldUniform{{f.b[0], f.b[1], f.b[2]}, {float(f.b[0]), float(f.b[1]), float(f.b[2])}},
-                               mode, perm, counter, blocks, stream);
+                               mode, perm, counter, shape, stream);
   }
-  return launch_mode<kMixed>(a, grid_policy(f), mode, perm, counter, blocks, stream);
+  return launch_mode<kMixed>(a, grid_policy(f), mode, perm, counter, shape, stream);
 }
 
 }  // namespace

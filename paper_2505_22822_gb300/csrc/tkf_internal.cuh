@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
+#include <utility>
 
 #include "tkf.h"
 
@@ -86,15 +88,40 @@ size_t workspace_bytes(uint32_t n_tracks, bool learned);
 Workspace carve_workspace(void* base, uint32_t n_tracks, bool learned);
 cudaError_t launch_propose_start(const FitArgs& a, const FieldDev& f, float* h0, cudaStream_t stream);
 
+// Block shape of the persistent fit: threads per block and blocks in the grid.
+struct LaunchShape {
+  int threads = 128;
+  int blocks = 0;
+};
+
 // Persistent fit launches per precision; mode 0 plain, 1 learned proposals, 2 record capture.
 cudaError_t launch_fit_fp64(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm, uint32_t* counter,
-                            int blocks, cudaStream_t stream);
+                            LaunchShape shape, cudaStream_t stream);
 cudaError_t launch_fit_mixed(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm, uint32_t* counter,
-                             int blocks, cudaStream_t stream);
+                             LaunchShape shape, cudaStream_t stream);
 
 // Enqueues the fit of every track in `a` on `stream`: track ordering, then the persistent fit.
-cudaError_t launch_fit(const FitArgs& a, const FieldDev& field, int precision, const Workspace& ws, int sm_count,
+cudaError_t launch_fit(const FitArgs& a, const FieldDev& field, int precision, const Workspace& ws, LaunchShape shape,
                        cudaStream_t stream);
+
+}  // namespace tkf
+
+struct tkf_context_s;
+
+namespace tkf {
+
+// Launch policy (tkf_policy.cu). The block shape of a call: the explicit one of the options,
+// the context's tuned one for the launch class (timing the candidates on the first call when
+// TKF_FIT_AUTOTUNE is set), else the default.
+bool valid_block_shape(uint32_t threads, uint32_t blocks_per_sm);
+cudaError_t resolve_shape(tkf_context_s* ctx, const FitArgs& a, const FieldDev& f, int precision, const Workspace& ws,
+                          const tkf_fit_options* o, cudaStream_t stream, LaunchShape* out);
+// Direct launch, or through the context's CUDA graph when `use_graph` (captured on the second
+// consecutive call with identical arguments, replayed after that).
+cudaError_t launch_with_policy(tkf_context_s* ctx, const FitArgs& a, const FieldDev& f, int precision,
+                               const Workspace& ws, LaunchShape shape, bool use_graph, cudaStream_t stream);
+void load_tune_cache(tkf_context_s* ctx);
+void release_graph(tkf_context_s* ctx);
 
 }  // namespace tkf
 
@@ -102,6 +129,12 @@ struct tkf_context_s {
   int device = 0;
   int sm_count = 0;
   std::string last_error;
+  // autotuner: best block shape (threads, blocks per SM) per launch key; optional cache file
+  std::map<std::string, std::pair<int, int>> tuned;
+  std::string tune_cache_path;
+  // CUDA graph of the last repeated launch sequence
+  cudaGraphExec_t graph_exec = nullptr;
+  std::string graph_key, pending_key;
   // fit workspace (ordering scratch), grown on demand and reused by later calls
   void* ws = nullptr;
   size_t ws_bytes = 0;

@@ -76,7 +76,7 @@ Workspace carve_workspace(void* base, uint32_t n_tracks, bool learned) {
   return w;
 }
 
-cudaError_t launch_fit(const FitArgs& a, const FieldDev& f, int precision, const Workspace& ws, int sm_count,
+cudaError_t launch_fit(const FitArgs& a, const FieldDev& f, int precision, const Workspace& ws, LaunchShape shape,
                        cudaStream_t stream) {
   if (a.n_tracks == 0) return cudaSuccess;
   const uint32_t n = a.n_tracks;
@@ -96,9 +96,8 @@ cudaError_t launch_fit(const FitArgs& a, const FieldDev& f, int precision, const
     if (e != cudaSuccess) return e;
     b.h0 = ws.h0;
   }
-  const int blocks = 2 * sm_count;  // 255 registers x 128 threads: two blocks per SM
-  if (precision == TKF_MIXED) return launch_fit_mixed(b, f, mode, ws.perm, ws.counter, blocks, stream);
-  return launch_fit_fp64(b, f, mode, ws.perm, ws.counter, blocks, stream);
+  if (precision == TKF_MIXED) return launch_fit_mixed(b, f, mode, ws.perm, ws.counter, shape, stream);
+  return launch_fit_fp64(b, f, mode, ws.perm, ws.counter, shape, stream);
 }
 
 }  // namespace tkf

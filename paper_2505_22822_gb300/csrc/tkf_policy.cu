@@ -1,0 +1,253 @@
+// tkf_policy.cu -- launch policy of the fit: block-shape autotuning and CUDA-graph replay.
+//
+// Neither changes what a track computes: every thread fits its own tracks with the same
+// arithmetic whatever the block shape, and a graph replays exactly the launches that a direct
+// call makes. The paper launches one fit kernel per batch with a fixed shape (Sec. 3); these
+// are the batching refinements of the persistent design on GB300.
+
+#include <errno.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+
+#include "tkf_internal.cuh"
+
+namespace tkf {
+namespace {
+
+// Candidate (threads per block, blocks per SM). The fit kernel takes 255 registers a thread,
+// so an SM holds 8 warps of it: the first four fill it, the last two use half of it (less
+// contention for the FP64 pipe and the L1 per warp).
+constexpr int kCandidates[][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {64, 2}, {128, 1}};
+constexpr int kDefaultThreads = 128, kDefaultBlocksPerSm = 2;
+
+int field_class(const FieldDev& f) {
+  if (f.kind != TKF_FIELD_UNIFORM) return 2;
+  return (f.b[0] == 0.0 && f.b[1] == 0.0) ? 0 : 1;
+}
+
+int fit_mode(const FitArgs& a) { return a.mlp ? 1 : (a.records ? 2 : 0); }
+
+std::string tune_key(const FitArgs& a, const FieldDev& f, int precision, int sm_count) {
+  static const char* kField[] = {"uz", "u", "grid"};
+  int lg = 0;
+  while ((2u << lg) <= a.n_tracks && lg < 31) ++lg;
+  char buf[96];
+  snprintf(buf, sizeof(buf), "%s.%s.%s.n%d.sm%d", precision == TKF_MIXED ? "mixed" : "fp64",
+           fit_mode(a) == 1 ? "learned" : (fit_mode(a) == 2 ? "record" : "adaptive"), kField[field_class(f)], lg,
+           sm_count);
+  return buf;
+}
+
+LaunchShape make_shape(int threads, int blocks_per_sm, int sm_count) {
+  LaunchShape s;
+  s.threads = threads;
+  s.blocks = blocks_per_sm * sm_count;
+  return s;
+}
+
+// Cache file: one JSON object, "class": [threads, blocks_per_sm] per entry.
+void save_cache(const tkf_context ctx) {
+  if (ctx->tune_cache_path.empty()) return;
+  const std::string tmp = ctx->tune_cache_path + ".tmp";
+  FILE* fp = fopen(tmp.c_str(), "w");
+  if (!fp) return;
+  fprintf(fp, "{\n");
+  size_t k = 0;
+  for (const auto& kv : ctx->tuned)
+    fprintf(fp, "  \"%s\": [%d, %d]%s\n", kv.first.c_str(), kv.second.first, kv.second.second,
+            ++k < ctx->tuned.size() ? "," : "");
+  fprintf(fp, "}\n");
+  const bool ok = fclose(fp) == 0;
+  if (ok) rename(tmp.c_str(), ctx->tune_cache_path.c_str());
+}
+
+bool valid_shape(int threads, int bps) {
+  return (threads == 32 || threads == 64 || threads == 128 || threads == 256) && bps >= 1 && bps <= 32;
+}
+
+// Times every candidate on the call's inputs: one warm-up fit, then the best of two fits each.
+cudaError_t tune(tkf_context ctx, const FitArgs& a, const FieldDev& f, int precision, const Workspace& ws,
+                 cudaStream_t stream, std::pair<int, int>* best) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best_ms = INFINITY;
+  *best = {kDefaultThreads, kDefaultBlocksPerSm};
+  if (e == cudaSuccess)
+    e = launch_fit(a, f, precision, ws, make_shape(kDefaultThreads, kDefaultBlocksPerSm, ctx->sm_count), stream);
+  for (const auto& c : kCandidates) {
+    if (e != cudaSuccess) break;
+    const LaunchShape s = make_shape(c[0], c[1], ctx->sm_count);
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+      e = cudaEventRecord(e0, stream);
+      if (e == cudaSuccess) e = launch_fit(a, f, precision, ws, s, stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        *best = {c[0], c[1]};
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return e;
+}
+
+// Byte string of every launch argument: equal strings mean identical launches.
+struct KeyWriter {
+  std::string s;
+  template <class T>
+  void put(const T& v) {
+    s.append(reinterpret_cast<const char*>(&v), sizeof(T));
+  }
+};
+
+std::string graph_key(const FitArgs& a, const FieldDev& f, int precision, const Workspace& ws, LaunchShape shape) {
+  KeyWriter k;
+  k.put(precision);
+  k.put(shape.threads);
+  k.put(shape.blocks);
+  k.put(a.n_tracks);
+  k.put(a.n_meas);
+  const void* ptrs[] = {a.offsets, a.loc0,   a.loc1,  a.v00,      a.v01,     a.v11,
+                        a.sid,     a.seed_par, a.seed_cov, a.par,   a.cov,     a.chi2,
+                        a.ndf,     a.status, a.steps, a.surf,     a.mlp,     a.records,
+                        a.record_count, ws.counter, ws.hist, ws.keys, ws.perm, ws.h0, f.grid};
+  for (const void* p : ptrs) k.put(p);
+  k.put(a.n_surf);
+  k.put(a.record_capacity);
+  const double dm[] = {a.mat.z_over_a, a.mat.i_ev, a.mat.rho, a.mat.hwp_ev, a.mat.log_hwp_over_i, a.mat.bg2_density,
+                       a.opt.tol, a.opt.h_max, a.opt.h_min, a.opt.surf_tol, a.opt.mass, f.b[0], f.b[1], f.b[2],
+                       f.r0, f.dr, f.z0, f.dz, f.inv_dr, f.inv_dz};
+  for (double d : dm) k.put(d);
+  const float fm[] = {a.mat.log_hwp_over_i_f, a.mat.bg2_density_f, a.mat.two_me_over_i2_f, a.mat.dedx_scale_f,
+                      a.opt.tol_f, a.opt.h_max_f, a.opt.h_min_f, a.opt.mass_f, a.opt.me_over_mass_f};
+  for (float x : fm) k.put(x);
+  k.put(a.opt.max_steps);
+  k.put(f.kind);
+  k.put(f.nr);
+  k.put(f.nz);
+  return k.s;
+}
+
+}  // namespace
+
+void load_tune_cache(tkf_context ctx) {
+  const char* path = getenv("TKF_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  ctx->tune_cache_path = path;
+  FILE* fp = fopen(path, "r");
+  if (!fp) return;
+  std::string text;
+  char buf[4096];
+  size_t n;
+  while ((n = fread(buf, 1, sizeof(buf), fp)) > 0) text.append(buf, n);
+  fclose(fp);
+  // entries "class": [threads, blocks_per_sm]; anything else is skipped
+  size_t pos = 0;
+  while ((pos = text.find('"', pos)) != std::string::npos) {
+    const size_t end = text.find('"', pos + 1);
+    if (end == std::string::npos) break;
+    const std::string key = text.substr(pos + 1, end - pos - 1);
+    const size_t lb = text.find('[', end);
+    const size_t next = text.find('"', end + 1);
+    pos = end + 1;
+    if (lb == std::string::npos || (next != std::string::npos && next < lb)) continue;
+    int t = 0, b = 0;
+    if (sscanf(text.c_str() + lb, "[ %d , %d ]", &t, &b) == 2 && valid_shape(t, b)) ctx->tuned[key] = {t, b};
+  }
+}
+
+void release_graph(tkf_context ctx) {
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  ctx->graph_exec = nullptr;
+  ctx->graph_key.clear();
+  ctx->pending_key.clear();
+}
+
+bool valid_block_shape(uint32_t threads, uint32_t blocks_per_sm) {
+  if (threads == 0 && blocks_per_sm == 0) return true;
+  return valid_shape(int(threads), int(blocks_per_sm));
+}
+
+cudaError_t resolve_shape(tkf_context ctx, const FitArgs& a, const FieldDev& f, int precision, const Workspace& ws,
+                          const tkf_fit_options* o, cudaStream_t stream, LaunchShape* out) {
+  if (o->block_threads && o->blocks_per_sm) {
+    *out = make_shape(int(o->block_threads), int(o->blocks_per_sm), ctx->sm_count);
+    return cudaSuccess;
+  }
+  *out = make_shape(kDefaultThreads, kDefaultBlocksPerSm, ctx->sm_count);
+  if (!(o->flags & TKF_FIT_AUTOTUNE) || a.records) return cudaSuccess;
+  const std::string key = tune_key(a, f, precision, ctx->sm_count);
+  auto it = ctx->tuned.find(key);
+  if (it != ctx->tuned.end()) {
+    *out = make_shape(it->second.first, it->second.second, ctx->sm_count);
+    return cudaSuccess;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(stream, &cs);
+  if (e != cudaSuccess || cs != cudaStreamCaptureStatusNone) return e;
+  std::pair<int, int> best;
+  e = tune(ctx, a, f, precision, ws, stream, &best);
+  if (e != cudaSuccess) return e;
+  ctx->tuned[key] = best;
+  save_cache(ctx);
+  *out = make_shape(best.first, best.second, ctx->sm_count);
+  return cudaSuccess;
+}
+
+cudaError_t launch_with_policy(tkf_context ctx, const FitArgs& a, const FieldDev& f, int precision,
+                               const Workspace& ws, LaunchShape shape, bool use_graph, cudaStream_t stream) {
+  if (!use_graph || stream == nullptr || stream == cudaStreamLegacy) return launch_fit(a, f, precision, ws, shape, stream);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(stream, &cs);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusNone) return launch_fit(a, f, precision, ws, shape, stream);
+  std::string key = graph_key(a, f, precision, ws, shape);
+  if (ctx->graph_exec && key == ctx->graph_key) return cudaGraphLaunch(ctx->graph_exec, stream);
+  if (key != ctx->pending_key) {
+    // first call with these arguments: launch directly and remember them
+    ctx->pending_key = std::move(key);
+    return launch_fit(a, f, precision, ws, shape, stream);
+  }
+  // second consecutive call with these arguments: capture, instantiate (or update), launch
+  cudaGraph_t g = nullptr;
+  e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  const cudaError_t le = launch_fit(a, f, precision, ws, shape, stream);
+  e = cudaStreamEndCapture(stream, &g);
+  if (le != cudaSuccess || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return le != cudaSuccess ? le : e;
+  }
+  if (ctx->graph_exec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(ctx->graph_exec, g, &info) != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(ctx->graph_exec);
+      ctx->graph_exec = nullptr;
+    }
+  }
+  if (!ctx->graph_exec) {
+    e = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      ctx->graph_exec = nullptr;
+      ctx->graph_key.clear();
+      return e;
+    }
+  }
+  cudaGraphDestroy(g);
+  ctx->graph_key = std::move(key);
+  ctx->pending_key.clear();
+  return cudaGraphLaunch(ctx->graph_exec, stream);
+}
+
+}  // namespace tkf

@@ -299,6 +299,19 @@ def event_counts(seed: int, n_events: int, lo: int, hi: int) -> np.ndarray:
     return out
 
 
+def event_counts_loguniform(seed: int, total: int, lo: int = 1000, hi: int = 100000) -> np.ndarray:
+    """Track counts of events drawn log-uniform in [lo, hi] until they add up to ``total``
+    (the last event is cut to land on it exactly)."""
+    rng = np.random.default_rng(seed)
+    counts, acc = [], 0
+    while acc < total:
+        c = int(round(float(np.exp(rng.uniform(np.log(lo), np.log(hi))))))
+        c = min(c, total - acc)
+        counts.append(c)
+        acc += c
+    return np.asarray(counts, dtype=np.uint32)
+
+
 def simulate(geom: Geometry, fld: Field, params: SimParams, seed: int, tracks_per_event,
              n_threads: int | None = None) -> Tracks:
     L = lib()
