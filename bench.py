@@ -243,9 +243,9 @@ def setup_tune_cache() -> str:
 
 
 def tuned_shape(path: str, variant: str, n_tracks: int, field: str, disabled: bool):
-    """[threads, blocks per SM] the autotuner chose for this launch class."""
+    """[threads, blocks per SM, tracks per warp] the autotuner chose for this launch class."""
     if disabled:
-        return [128, 2]
+        return [128, 2, 32]
     prec = "fp64" if variant == "fp64" else "mixed"
     mode = "learned" if variant.endswith("learned") else "adaptive"
     prefix = f"{prec}.{mode}.{field}.n{int(n_tracks).bit_length() - 1}."
@@ -310,9 +310,10 @@ def run_sweep(args, local: int, rank: int, tune_file: str):
         b = _prefix_batch(_tile_batch(full, k) if k > 1 else full, n)
         out = tkf.alloc_outputs(n, dev, steps=True)
         for variant in ("fp64", "mixed", "mixed_learned"):
-            for graph in ((True, False) if n <= 10 ** 5 else (True,)):
+            policies = [(True, True), (False, True), (True, False)] if n <= 10 ** 5 else [(True, True)]
+            for graph, autotune in policies:
                 opts = tkf.Options(precision=tkf.FP64 if variant == "fp64" else tkf.MIXED, mass=synth.MUON_MASS,
-                                   graph=graph, autotune=True)
+                                   graph=graph, autotune=autotune)
                 if variant.endswith("learned"):
                     opts.step_mode, opts.mlp = tkf.STEP_LEARNED, proposer
                 for _ in range(max(3, args.warmup)):
@@ -332,8 +333,8 @@ def run_sweep(args, local: int, rank: int, tune_file: str):
                 ms = e0.elapsed_time(e1) / reps
                 status = out.status.cpu().numpy().view(np.uint32)
                 print(json.dumps({"sweep": "point", "tracks_per_launch": n, "variant": variant, "cuda_graph": graph,
-                                  "tracks_per_s": n / (ms * 1e-3), "ms_per_launch": ms, "reps": reps,
-                                  "block_shape": tuned_shape(tune_file, variant, n, "grid", False),
+                                  "autotune": autotune, "tracks_per_s": n / (ms * 1e-3), "ms_per_launch": ms,
+                                  "reps": reps, "launch_shape": tuned_shape(tune_file, variant, n, "grid", not autotune),
                                   "fit_status_ok": float(np.mean(status == 0)),
                                   "clocks": clk.summary()}), flush=True)
         del b, out
@@ -486,7 +487,7 @@ def main():
         # (learned), the persistent fit (plus one memset node)
         "gpu_launches": (5 if head.endswith("learned") else 4) * args.steps,
         "launch_policy": {"cuda_graph": not args.no_graph, "autotune": not args.no_autotune,
-                          "block_shape": {k: v["shape"] for k, v in results.items()}},
+                          "launch_shape": {k: v["shape"] for k, v in results.items()}},
         "roofline": roof,
         "clocks": clocks,
         "variants": {k: {"tracks_per_s": aggregate_throughput(n_tracks, ws, v["ms_max"] * 1e-3),

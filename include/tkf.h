@@ -170,23 +170,28 @@ typedef struct tkf_fit_options {
   uint32_t record_capacity;
   uint32_t* record_count;
   /* Launch policy (no effect on the results: every track's arithmetic is the same under any
-   * block shape). flags: TKF_FIT_AUTOTUNE and/or TKF_FIT_GRAPH, default 0. block_threads
+   * launch shape). flags: TKF_FIT_AUTOTUNE and/or TKF_FIT_GRAPH, default 0. block_threads
    * (32, 64, 128 or 256) and blocks_per_sm (1..32) fix the persistent kernel's block shape
-   * when both are nonzero; 0, 0 takes the tuned shape of this launch class when
-   * TKF_FIT_AUTOTUNE is set, else 128 threads x 2 blocks per SM. */
+   * when both are nonzero; tracks_per_warp (1..32) fixes how many tracks a warp takes at a
+   * time, one per lane, when nonzero. With all three 0 the shape is the tuned one of this
+   * launch class when TKF_FIT_AUTOTUNE is set, else 128 threads x 2 blocks per SM x 32
+   * tracks per warp; an explicit part disables tuning and the other parts take defaults. */
   uint32_t flags;
   uint32_t block_threads;
   uint32_t blocks_per_sm;
+  uint32_t tracks_per_warp;
 } tkf_fit_options;
 
 /* Autotuning: the first call of a launch class (precision, step mode, field kind, batch size
- * rounded down to a power of two, SM count) times every candidate block shape on the call's
- * own inputs (each candidate runs the whole fit into the call's outputs, then the call runs
- * with the fastest shape) and keeps the winner in the context. The call synchronizes its
- * stream while tuning. If the environment variable TKF_AUTOTUNE_CACHE names a file when the
- * context is created, tuned shapes are read from it and every new one is written back (JSON
- * object: class -> [threads, blocks per SM]); an unreadable or unwritable file is ignored.
- * Skipped (defaults used) while the stream is capturing and in record-capture mode. */
+ * rounded down to a power of two, SM count) times every candidate launch shape on the call's
+ * own inputs (six block shapes; below one track per lane of every resident warp also 16, 8
+ * and 4 tracks per warp; each candidate runs the whole fit into the call's outputs, then the
+ * call runs with the fastest shape) and keeps the winner in the context. The call
+ * synchronizes its stream while tuning. If the environment variable TKF_AUTOTUNE_CACHE names
+ * a file when the context is created, tuned shapes are read from it and every new one is
+ * written back (JSON object: class -> [threads, blocks per SM, tracks per warp]); an
+ * unreadable or unwritable file is ignored. Skipped (defaults used) while the stream is
+ * capturing and in record-capture mode. */
 #define TKF_FIT_AUTOTUNE 1u
 /* Graph replay: the ordering and fit launches of a call are captured into a CUDA graph on the
  * second consecutive call with identical arguments (every pointer, size, option, handle and
@@ -325,7 +330,7 @@ tkf_status tkf_mlp_forward(tkf_context ctx, const float* params, const float* x,
  *     (different streams, or different contexts, without ordering) race and give wrong
  *     results. Serialize them.
  *   - It ignores the flags TKF_FIT_AUTOTUNE and TKF_FIT_GRAPH (both allocate); an explicit
- *     block shape is used.
+ *     launch shape is used.
  * Arguments, outputs and the other errors are those of tkf_fit. */
 #define TKF_NOALLOC_MAX_TRACKS 2097152u
 tkf_status tkf_fit_noalloc(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf_fit_options* opts,

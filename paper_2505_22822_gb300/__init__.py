@@ -110,7 +110,7 @@ class FitOptions(ctypes.Structure):
                 ("mass", ctypes.c_double), ("mlp", ctypes.c_void_p), ("records", ctypes.c_void_p),
                 ("record_capacity", ctypes.c_uint32), ("record_count", ctypes.c_void_p),
                 ("flags", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
-                ("blocks_per_sm", ctypes.c_uint32)]
+                ("blocks_per_sm", ctypes.c_uint32), ("tracks_per_warp", ctypes.c_uint32)]
 
 
 class MlpTrainOptions(ctypes.Structure):
@@ -326,6 +326,7 @@ class Options:
     graph: bool = False           # capture repeated identical calls into a CUDA graph
     block_threads: int = 0        # explicit block shape (both nonzero), else default or tuned
     blocks_per_sm: int = 0
+    tracks_per_warp: int = 0      # explicit tracks a warp takes at a time (1..32), else 32 or tuned
 
     def c(self) -> FitOptions:
         o = FitOptions()
@@ -341,6 +342,7 @@ class Options:
             o.record_count = self.record_count.data_ptr()
         o.flags = (FIT_AUTOTUNE if self.autotune else 0) | (FIT_GRAPH if self.graph else 0)
         o.block_threads, o.blocks_per_sm = self.block_threads, self.blocks_per_sm
+        o.tracks_per_warp = self.tracks_per_warp
         return o
 
 

@@ -293,6 +293,7 @@ void tkf_fit_options_default(tkf_fit_options* o) {
   o->flags = 0;
   o->block_threads = 0;
   o->blocks_per_sm = 0;
+  o->tracks_per_warp = 0;
 }
 
 static tkf_status check_common(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf_fit_options* o,
@@ -318,9 +319,10 @@ static tkf_status check_common(tkf_context ctx, tkf_geometry geo, tkf_field fiel
                 std::string(fn) + ": options need tol, h_max, h_min, surf_tol, mass > 0, h_min <= h_max, max_steps > 0");
   if ((o->flags & ~(TKF_FIT_AUTOTUNE | TKF_FIT_GRAPH)) != 0)
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": unknown flag");
-  if (!tkf::valid_block_shape(o->block_threads, o->blocks_per_sm))
+  if (!tkf::valid_block_shape(o->block_threads, o->blocks_per_sm, o->tracks_per_warp))
     return fail(ctx, TKF_ERR_INVALID_ARG,
-                std::string(fn) + ": block shape needs threads 32, 64, 128 or 256 and 1..32 blocks per SM (or 0, 0)");
+                std::string(fn) + ": block shape needs threads 32, 64, 128 or 256 and 1..32 blocks per SM (or 0, 0), "
+                                  "and 0..32 tracks per warp");
   if (in->n_meas > 0xffffffffull)
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": n_meas exceeds 32-bit offsets");
   if (in->n_tracks == 0) return TKF_OK;
@@ -650,6 +652,7 @@ extern "C" tkf_status tkf_fit_noalloc(tkf_context ctx, tkf_geometry geo, tkf_fie
     shape.threads = int(o->block_threads);
     shape.blocks = int(o->blocks_per_sm) * ctx->sm_count;
   }
+  if (o->tracks_per_warp) shape.tracks_per_warp = int(o->tracks_per_warp);
   e = tkf::launch_fit(a, field->f, o->precision, ws, shape, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_noalloc: launch");
   return TKF_OK;

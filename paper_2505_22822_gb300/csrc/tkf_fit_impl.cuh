@@ -1109,19 +1109,21 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i, const floa
   }
 }
 
-// Persistent fit: each warp takes the next 32 tracks of the ordered list from a global counter.
+// Persistent fit: each warp takes the next `tpw` (1..32) tracks of the ordered list from a
+// global counter, one per lane; lanes tpw..31 idle. Fewer tracks per warp spread a small batch
+// over more warps and schedulers.
 template <bool kMixed, int kMode, class F>
 __global__ void __launch_bounds__(256) fit_persistent_kernel(FitArgs a, F fld, const uint32_t* __restrict__ perm,
-                                                             uint32_t* __restrict__ counter) {
+                                                             uint32_t* __restrict__ counter, uint32_t tpw) {
   const float* mlp_w = nullptr;
   const uint32_t lane = threadIdx.x & 31u;
   for (;;) {
     uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(counter, 32u);
+    if (lane == 0) base = atomicAdd(counter, tpw);
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= a.n_tracks) break;
     const uint32_t j = base + lane;
-    if (j < a.n_tracks) fit_track<kMixed, kMode>(a, fld, perm[j], mlp_w);
+    if (lane < tpw && j < a.n_tracks) fit_track<kMixed, kMode>(a, fld, perm[j], mlp_w);
   }
 }
 
@@ -1193,7 +1195,8 @@ cudaError_t propose_fields(const FitArgs& a, const FieldDev& f, float* h0, cudaS
 template <bool kMixed, int kMode, class F>
 cudaError_t launch_persistent(const FitArgs& a, const F& fld, const uint32_t* perm, uint32_t* counter,
                               LaunchShape shape, cudaStream_t stream) {
-  fit_persistent_kernel<kMixed, kMode><<<shape.blocks, shape.threads, 0, stream>>>(a, fld, perm, counter);
+  fit_persistent_kernel<kMixed, kMode>
+      <<<shape.blocks, shape.threads, 0, stream>>>(a, fld, perm, counter, uint32_t(shape.tracks_per_warp));
   return cudaGetLastError();
 }
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
 #include <map>
 #include <string>
 #include <utility>
@@ -88,10 +89,12 @@ size_t workspace_bytes(uint32_t n_tracks, bool learned);
 Workspace carve_workspace(void* base, uint32_t n_tracks, bool learned);
 cudaError_t launch_propose_start(const FitArgs& a, const FieldDev& f, float* h0, cudaStream_t stream);
 
-// Block shape of the persistent fit: threads per block and blocks in the grid.
+// Launch shape of the persistent fit: threads per block, blocks in the grid, tracks a warp
+// takes at a time (1..32, one per lane).
 struct LaunchShape {
   int threads = 128;
   int blocks = 0;
+  int tracks_per_warp = 32;
 };
 
 // Persistent fit launches per precision; mode 0 plain, 1 learned proposals, 2 record capture.
@@ -113,7 +116,7 @@ namespace tkf {
 // Launch policy (tkf_policy.cu). The block shape of a call: the explicit one of the options,
 // the context's tuned one for the launch class (timing the candidates on the first call when
 // TKF_FIT_AUTOTUNE is set), else the default.
-bool valid_block_shape(uint32_t threads, uint32_t blocks_per_sm);
+bool valid_block_shape(uint32_t threads, uint32_t blocks_per_sm, uint32_t tracks_per_warp);
 cudaError_t resolve_shape(tkf_context_s* ctx, const FitArgs& a, const FieldDev& f, int precision, const Workspace& ws,
                           const tkf_fit_options* o, cudaStream_t stream, LaunchShape* out);
 // Direct launch, or through the context's CUDA graph when `use_graph` (captured on the second
@@ -129,8 +132,8 @@ struct tkf_context_s {
   int device = 0;
   int sm_count = 0;
   std::string last_error;
-  // autotuner: best block shape (threads, blocks per SM) per launch key; optional cache file
-  std::map<std::string, std::pair<int, int>> tuned;
+  // autotuner: best (threads, blocks per SM, tracks per warp) per launch class; optional cache file
+  std::map<std::string, std::array<int, 3>> tuned;
   std::string tune_cache_path;
   // CUDA graph of the last repeated launch sequence
   cudaGraphExec_t graph_exec = nullptr;

@@ -1,9 +1,8 @@
-// tkf_policy.cu -- launch policy of the fit: block-shape autotuning and CUDA-graph replay.
+// tkf_policy.cu -- launch policy of the fit: launch-shape autotuning and CUDA-graph replay.
 //
 // Neither changes what a track computes: every thread fits its own tracks with the same
-// arithmetic whatever the block shape, and a graph replays exactly the launches that a direct
-// call makes. The paper launches one fit kernel per batch with a fixed shape (Sec. 3); these
-// are the batching refinements of the persistent design on GB300.
+// arithmetic whatever the launch shape, and a graph replays exactly the launches that a
+// direct call makes.
 
 #include <errno.h>
 #include <math.h>
@@ -11,6 +10,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <array>
 #include <string>
 
 #include "tkf_internal.cuh"
@@ -22,7 +22,11 @@ namespace {
 // so an SM holds 8 warps of it: the first four fill it, the last two use half of it (less
 // contention for the FP64 pipe and the L1 per warp).
 constexpr int kCandidates[][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {64, 2}, {128, 1}};
-constexpr int kDefaultThreads = 128, kDefaultBlocksPerSm = 2;
+// Tracks per warp: below one track per lane of every resident warp, fewer tracks per warp
+// spread the batch over more schedulers.
+constexpr int kTracksPerWarp[] = {32, 16, 8, 4};
+constexpr int kDefaultThreads = 128, kDefaultBlocksPerSm = 2, kDefaultTracksPerWarp = 32;
+constexpr int kResidentWarpsPerSm = 8;
 
 int field_class(const FieldDev& f) {
   if (f.kind != TKF_FIELD_UNIFORM) return 2;
@@ -42,14 +46,17 @@ std::string tune_key(const FitArgs& a, const FieldDev& f, int precision, int sm_
   return buf;
 }
 
-LaunchShape make_shape(int threads, int blocks_per_sm, int sm_count) {
+LaunchShape make_shape(int threads, int blocks_per_sm, int tracks_per_warp, int sm_count) {
   LaunchShape s;
   s.threads = threads;
   s.blocks = blocks_per_sm * sm_count;
+  s.tracks_per_warp = tracks_per_warp;
   return s;
 }
 
-// Cache file: one JSON object, "class": [threads, blocks_per_sm] per entry.
+LaunchShape make_shape(const std::array<int, 3>& c, int sm_count) { return make_shape(c[0], c[1], c[2], sm_count); }
+
+// Cache file: one JSON object, "class": [threads, blocks_per_sm, tracks_per_warp] per entry.
 void save_cache(const tkf_context ctx) {
   if (ctx->tune_cache_path.empty()) return;
   const std::string tmp = ctx->tune_cache_path + ".tmp";
@@ -58,7 +65,7 @@ void save_cache(const tkf_context ctx) {
   fprintf(fp, "{\n");
   size_t k = 0;
   for (const auto& kv : ctx->tuned)
-    fprintf(fp, "  \"%s\": [%d, %d]%s\n", kv.first.c_str(), kv.second.first, kv.second.second,
+    fprintf(fp, "  \"%s\": [%d, %d, %d]%s\n", kv.first.c_str(), kv.second[0], kv.second[1], kv.second[2],
             ++k < ctx->tuned.size() ? "," : "");
   fprintf(fp, "}\n");
   const bool ok = fclose(fp) == 0;
@@ -71,27 +78,31 @@ bool valid_shape(int threads, int bps) {
 
 // Times every candidate on the call's inputs: one warm-up fit, then the best of two fits each.
 cudaError_t tune(tkf_context ctx, const FitArgs& a, const FieldDev& f, int precision, const Workspace& ws,
-                 cudaStream_t stream, std::pair<int, int>* best) {
+                 cudaStream_t stream, std::array<int, 3>* best) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   float best_ms = INFINITY;
-  *best = {kDefaultThreads, kDefaultBlocksPerSm};
-  if (e == cudaSuccess)
-    e = launch_fit(a, f, precision, ws, make_shape(kDefaultThreads, kDefaultBlocksPerSm, ctx->sm_count), stream);
-  for (const auto& c : kCandidates) {
-    if (e != cudaSuccess) break;
-    const LaunchShape s = make_shape(c[0], c[1], ctx->sm_count);
-    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
-      e = cudaEventRecord(e0, stream);
-      if (e == cudaSuccess) e = launch_fit(a, f, precision, ws, s, stream);
-      if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      float ms = 0.0f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-      if (e == cudaSuccess && ms < best_ms) {
-        best_ms = ms;
-        *best = {c[0], c[1]};
+  *best = {kDefaultThreads, kDefaultBlocksPerSm, kDefaultTracksPerWarp};
+  if (e == cudaSuccess) e = launch_fit(a, f, precision, ws, make_shape(*best, ctx->sm_count), stream);
+  const bool small = a.n_tracks < uint32_t(32 * kResidentWarpsPerSm * ctx->sm_count);
+  for (const int tpw : kTracksPerWarp) {
+    if (tpw != 32 && !small) break;
+    for (const auto& c : kCandidates) {
+      if (e != cudaSuccess) break;
+      const std::array<int, 3> cand = {c[0], c[1], tpw};
+      const LaunchShape s = make_shape(cand, ctx->sm_count);
+      for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+        e = cudaEventRecord(e0, stream);
+        if (e == cudaSuccess) e = launch_fit(a, f, precision, ws, s, stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best_ms) {
+          best_ms = ms;
+          *best = cand;
+        }
       }
     }
   }
@@ -114,6 +125,7 @@ std::string graph_key(const FitArgs& a, const FieldDev& f, int precision, const 
   k.put(precision);
   k.put(shape.threads);
   k.put(shape.blocks);
+  k.put(shape.tracks_per_warp);
   k.put(a.n_tracks);
   k.put(a.n_meas);
   const void* ptrs[] = {a.offsets, a.loc0,   a.loc1,  a.v00,      a.v01,     a.v11,
@@ -150,7 +162,7 @@ void load_tune_cache(tkf_context ctx) {
   size_t n;
   while ((n = fread(buf, 1, sizeof(buf), fp)) > 0) text.append(buf, n);
   fclose(fp);
-  // entries "class": [threads, blocks_per_sm]; anything else is skipped
+  // entries "class": [threads, blocks_per_sm, tracks_per_warp]; anything else is skipped
   size_t pos = 0;
   while ((pos = text.find('"', pos)) != std::string::npos) {
     const size_t end = text.find('"', pos + 1);
@@ -160,8 +172,9 @@ void load_tune_cache(tkf_context ctx) {
     const size_t next = text.find('"', end + 1);
     pos = end + 1;
     if (lb == std::string::npos || (next != std::string::npos && next < lb)) continue;
-    int t = 0, b = 0;
-    if (sscanf(text.c_str() + lb, "[ %d , %d ]", &t, &b) == 2 && valid_shape(t, b)) ctx->tuned[key] = {t, b};
+    int t = 0, b = 0, w = 0;
+    if (sscanf(text.c_str() + lb, "[ %d , %d , %d ]", &t, &b, &w) == 3 && valid_shape(t, b) && w >= 1 && w <= 32)
+      ctx->tuned[key] = {t, b, w};
   }
 }
 
@@ -172,34 +185,34 @@ void release_graph(tkf_context ctx) {
   ctx->pending_key.clear();
 }
 
-bool valid_block_shape(uint32_t threads, uint32_t blocks_per_sm) {
+bool valid_block_shape(uint32_t threads, uint32_t blocks_per_sm, uint32_t tracks_per_warp) {
+  if (tracks_per_warp > 32) return false;
   if (threads == 0 && blocks_per_sm == 0) return true;
   return valid_shape(int(threads), int(blocks_per_sm));
 }
 
 cudaError_t resolve_shape(tkf_context ctx, const FitArgs& a, const FieldDev& f, int precision, const Workspace& ws,
                           const tkf_fit_options* o, cudaStream_t stream, LaunchShape* out) {
-  if (o->block_threads && o->blocks_per_sm) {
-    *out = make_shape(int(o->block_threads), int(o->blocks_per_sm), ctx->sm_count);
-    return cudaSuccess;
-  }
-  *out = make_shape(kDefaultThreads, kDefaultBlocksPerSm, ctx->sm_count);
-  if (!(o->flags & TKF_FIT_AUTOTUNE) || a.records) return cudaSuccess;
+  const bool explicit_block = o->block_threads && o->blocks_per_sm;
+  *out = make_shape(explicit_block ? int(o->block_threads) : kDefaultThreads,
+                    explicit_block ? int(o->blocks_per_sm) : kDefaultBlocksPerSm,
+                    o->tracks_per_warp ? int(o->tracks_per_warp) : kDefaultTracksPerWarp, ctx->sm_count);
+  if (explicit_block || o->tracks_per_warp || !(o->flags & TKF_FIT_AUTOTUNE) || a.records) return cudaSuccess;
   const std::string key = tune_key(a, f, precision, ctx->sm_count);
   auto it = ctx->tuned.find(key);
   if (it != ctx->tuned.end()) {
-    *out = make_shape(it->second.first, it->second.second, ctx->sm_count);
+    *out = make_shape(it->second, ctx->sm_count);
     return cudaSuccess;
   }
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaError_t e = cudaStreamIsCapturing(stream, &cs);
   if (e != cudaSuccess || cs != cudaStreamCaptureStatusNone) return e;
-  std::pair<int, int> best;
+  std::array<int, 3> best;
   e = tune(ctx, a, f, precision, ws, stream, &best);
   if (e != cudaSuccess) return e;
   ctx->tuned[key] = best;
   save_cache(ctx);
-  *out = make_shape(best.first, best.second, ctx->sm_count);
+  *out = make_shape(best, ctx->sm_count);
   return cudaSuccess;
 }
 

@@ -14,7 +14,9 @@ import synth
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(32, 8), (64, 4), (128, 2), (256, 1), (64, 2), (128, 1), (256, 3)]
+SHAPES = [(32, 8, 0), (64, 4, 0), (128, 2, 0), (256, 1, 0), (64, 2, 0), (128, 1, 0), (256, 3, 0),
+          (128, 2, 16), (64, 4, 8), (32, 8, 4), (0, 0, 1), (0, 0, 7)]
+CANDIDATES = {(t, b, w) for t, b in [(32, 8), (64, 4), (128, 2), (256, 1), (64, 2), (128, 1)] for w in (32, 16, 8, 4)}
 
 
 @pytest.fixture(scope="module")
@@ -53,8 +55,9 @@ def _run(ctx, geo, fld, b, stream=None, **kw):
 def test_every_block_shape_gives_identical_results(setup, precision):
     ctx, geo, fld, b, _ = setup
     ref = _run(ctx, geo, fld, b, precision=precision)
-    for t, bps in SHAPES:
-        _same(_run(ctx, geo, fld, b, precision=precision, block_threads=t, blocks_per_sm=bps), ref)
+    for t, bps, tpw in SHAPES:
+        _same(_run(ctx, geo, fld, b, precision=precision, block_threads=t, blocks_per_sm=bps, tracks_per_warp=tpw),
+              ref)
 
 
 def test_autotune_picks_a_candidate_and_writes_the_cache(setup, tmp_path, monkeypatch):
@@ -69,13 +72,13 @@ def test_autotune_picks_a_candidate_and_writes_the_cache(setup, tmp_path, monkey
     assert len(entries) == 1
     (key, shape), = entries.items()
     assert key.startswith("mixed.adaptive.uz.n11.")
-    assert tuple(shape) in {(32, 8), (64, 4), (128, 2), (256, 1), (64, 2), (128, 1)}
+    assert tuple(shape) in CANDIDATES
     # a second call of the same class takes the tuned shape without timing again
     before = cache.stat().st_mtime_ns
     _same(_run(ctx, geo, fld, b, precision=tkf.MIXED, autotune=True), ref)
     assert cache.stat().st_mtime_ns == before
     # a new context reads the file: with a planted entry it tunes nothing for that class
-    cache.write_text(json.dumps({key: [64, 4]}))
+    cache.write_text(json.dumps({key: [64, 4, 8]}))
     before = cache.stat().st_mtime_ns
     ctx2 = tkf.Context(0)
     geo2, fld2 = _handles(ctx2, w)
@@ -85,7 +88,7 @@ def test_autotune_picks_a_candidate_and_writes_the_cache(setup, tmp_path, monkey
     _run(ctx2, geo2, fld2, b, precision=tkf.FP64, autotune=True)
     entries = json.loads(cache.read_text())
     assert set(entries) == {key, key.replace("mixed.", "fp64.", 1)}
-    assert entries[key] == [64, 4]
+    assert entries[key] == [64, 4, 8]
 
 
 def test_graph_replay_matches_direct_launches_and_reads_current_inputs(setup):
@@ -147,7 +150,7 @@ def test_graph_and_autotune_with_learned_proposals(setup):
 
 @pytest.mark.parametrize("kw", [dict(block_threads=96, blocks_per_sm=1), dict(block_threads=128, blocks_per_sm=0),
                                 dict(block_threads=0, blocks_per_sm=2), dict(block_threads=512, blocks_per_sm=1),
-                                dict(block_threads=64, blocks_per_sm=33)])
+                                dict(block_threads=64, blocks_per_sm=33), dict(tracks_per_warp=33)])
 def test_bad_block_shapes_are_rejected(setup, kw):
     ctx, geo, fld, b, _ = setup
     with pytest.raises(tkf.TkfError, match="block shape"):
