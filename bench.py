@@ -13,6 +13,7 @@ Lines printed (rank 0): one JSON object. ``--impl reference`` times the CPU orac
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -31,6 +32,7 @@ import synth  # noqa: E402
 
 METRIC = "fitted tracks/s on 1 GB300: mixed+learned vs plain FP64, at fixed pull error"
 WORKLOAD = "barrel_endcap_50ev_uniform2T_pions"
+WORKLOAD_MAP = "solenoid_map_100k_muons"
 
 # Algorithmic FP64 flops per unit of the fit kernels, counted from the kernel source
 # (add/sub/mul = 1, fma = 2, each div/sqrt/log/sin/cos = 1; derivation in the design doc):
@@ -41,6 +43,20 @@ FLOPS = {
     "mixed": (20, 8, 749, 330),
     "mixed_learned": (20, 8, 749, 330),
 }
+# r-z field map: every attempt adds two stage positions and three bilinear lookups (FP64 in
+# the plain path: 32 flops each incl. one square root and one division), every propagated
+# measurement two more lookups; the mixed path looks up in FP32.
+FLOPS_MAP = {
+    "fp64": (619, 237, 1558, 330),
+    "mixed": (20, 8, 749, 330),
+    "mixed_learned": (20, 8, 749, 330),
+}
+
+
+# DRAM bytes per track of the fit kernel (dram__bytes_read.sum + dram__bytes_write.sum of one
+# ncu capture of a 5-event batch, 81,077 tracks, divided by its tracks; traffic grows with the
+# tracks of a launch). Keyed by (workload, variant); a kernel change voids the entry.
+TRAFFIC_PER_TRACK = {("barrel", "mixed_learned"): (77.133568e6 + 9.316864e6) / 81077}
 
 
 def parse():
@@ -51,6 +67,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--variant", default="auto", choices=["auto", "fp64", "mixed", "mixed_learned"])
     ap.add_argument("--events", type=int, default=50)
+    ap.add_argument("--workload", default="barrel", choices=["barrel", "map"],
+                    help="barrel: events in the barrel + endcap detector, uniform 2 T; map: 1e5 muons "
+                         "in the solenoid field map")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch directly instead of replaying a CUDA graph")
@@ -72,8 +91,18 @@ def shard_seed(rank: int) -> int:
     return 2 + 1000 * rank
 
 
-def make_workload(events: int, rank: int, **kw):
+def make_workload(workload: str, events: int, rank: int, **kw):
+    """The timed batch: the barrel + endcap events in 2 T, or 1e5 muons in the solenoid map."""
+    if workload == "map":
+        return synth.solenoid_muon_workload(100_000, seed=3 + shard_seed(rank), **kw)
     return synth.barrel_workload(n_events=events, seed=shard_seed(rank), **kw)
+
+
+def make_training_batch(args, rank: int):
+    """Seed-disjoint tracks of the same kind for the step proposer's training records."""
+    if args.workload == "map":
+        return synth.solenoid_muon_workload(100_000, seed=10_003 + shard_seed(rank)).tracks
+    return synth.barrel_workload(n_events=5, seed=10_000 + shard_seed(rank)).tracks
 
 
 def max_over_ranks(x: float, dist, device) -> float:
@@ -198,7 +227,7 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return
     import oracle  # noqa: F401
-    w = make_workload(args.events, 0)
+    w = make_workload(args.workload, args.events, 0)
     t = w.tracks
     cores = os.cpu_count() or 1
     # each step fits a bounded sample sized to keep the whole run within minutes
@@ -220,7 +249,8 @@ def run_reference(args, ws, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "tracks/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "tracks_per_step": per_step,
+        "data": "synthetic", "config": {"workload": WORKLOAD_MAP if args.workload == "map" else WORKLOAD,
+                                        "tracks_per_step": per_step,
                                         "sample": "bounded sample of the batch per step",
                                         "l2": "inputs on the host"},
         "cpu_baseline": {"value": value, "unit": "tracks/s", "cores": cores, "kind": "oracle",
@@ -365,7 +395,7 @@ def main():
     if args.sweep:
         run_sweep(args, local, rank, tune_file)
         return
-    w = make_workload(args.events, rank)
+    w = make_workload(args.workload, args.events, rank)
     t = w.tracks
     n_tracks, n_meas = t.n_tracks, t.n_hits
     ctx = tkf.Context(local)
@@ -382,8 +412,7 @@ def main():
     if any(v.endswith("learned") for v in variants):
         # the step proposer is trained before timing, on records of seed-disjoint tracks
         from paper_2505_22822_gb300 import learn
-        tw = synth.barrel_workload(n_events=5, seed=10_000 + shard_seed(rank))
-        tt = tw.tracks
+        tt = make_training_batch(args, rank)
         tb = tkf.Batch.from_arrays(tt.offsets, tt.meas, tt.sid, tt.seed_par, tt.seed_cov).to(f"cuda:{local}")
         t0 = time.perf_counter()
         proposer, info = learn.build_proposer(ctx, geo, fld, tb, tkf.MIXED, mass=w.mass)
@@ -391,6 +420,9 @@ def main():
                       "bias_shift": round(info["bias_shift"], 4), "train_s": round(time.perf_counter() - t0, 2),
                       "tracks": tt.n_tracks}
     results = {}
+    L2_BYTES = 129e6
+    flush = (torch.zeros(int(2 * L2_BYTES) // 4, dtype=torch.float32, device=f"cuda:{local}")
+             if host.nbytes() < 2 * L2_BYTES else None)
     for variant in variants:
         opts = tkf.Options(precision=tkf.FP64 if variant == "fp64" else tkf.MIXED, mass=w.mass,
                            graph=not args.no_graph, autotune=not args.no_autotune)
@@ -407,25 +439,54 @@ def main():
         status = out.status.cpu().numpy().view(np.uint32)
         barrier()
         torch.cuda.synchronize()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with ClockSampler(local) as clk:
-            ev0.record(stream)
-            for _ in range(args.steps):
-                tkf.fit(ctx, geo, fld, dev, opts, out=out, stream=stream)
-            ev1.record(stream)
-            torch.cuda.synchronize()
+        if flush is None:
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with ClockSampler(local) as clk:
+                ev0.record(stream)
+                for _ in range(args.steps):
+                    tkf.fit(ctx, geo, fld, dev, opts, out=out, stream=stream)
+                ev1.record(stream)
+                torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1) / args.steps
+        else:
+            # inputs smaller than L2: overwrite a buffer larger than L2 before every step, and
+            # time each step alone
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+            with ClockSampler(local) as clk:
+                for e0, e1 in evs:
+                    flush.add_(1.0)
+                    e0.record(stream)
+                    tkf.fit(ctx, geo, fld, dev, opts, out=out, stream=stream)
+                    e1.record(stream)
+                torch.cuda.synchronize()
+            ms = sum(e0.elapsed_time(e1) for e0, e1 in evs) / args.steps
         barrier()
-        ms = ev0.elapsed_time(ev1) / args.steps
+        # the fit kernel alone: the library records a pair of events around it (steps timed one
+        # by one, after the timed region)
+        kev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        for ev in kev:
+            ev.record(stream)  # creates the events
+        kopts = dataclasses.replace(opts, kernel_events=kev)
+        kms = []
+        for _ in range(args.steps):
+            if flush is not None:
+                flush.add_(1.0)
+            tkf.fit(ctx, geo, fld, dev, kopts, out=out, stream=stream)
+            kev[1].synchronize()
+            kms.append(kev[0].elapsed_time(kev[1]))
+        kernel_ms = statistics.mean(kms)
         ms_max = max_over_ranks(ms, dist, f"cuda:{local}")
-        results[variant] = {"ms": ms, "ms_max": ms_max, "clocks": clk.summary(), "opts": opts,
-                            "shape": tuned_shape(tune_file, variant, n_tracks, "uz", args.no_autotune),
+        results[variant] = {"ms": ms, "ms_max": ms_max, "kernel_ms": kernel_ms, "clocks": clk.summary(), "opts": opts,
+                            "shape": tuned_shape(tune_file, variant, n_tracks, "grid" if args.workload == "map" else "uz",
+                                                 args.no_autotune),
                             "attempts": attempts, "rejected": rejected, "status_ok": float(np.mean(status == 0)),
                             "pulls": pull_stats(out, t)}
     head = variants[-1]
     opts = results[head]["opts"]
     ms, ms_max, clocks = results[head]["ms"], results[head]["ms_max"], results[head]["clocks"]
     for k, v in results.items():
-        fa, fr, fh, ft = FLOPS[k]
+        fa, fr, fh, ft = (FLOPS_MAP if args.workload == "map" else FLOPS)[k]
         v["flops"] = fa * (v["attempts"] - v["rejected"]) + fr * v["rejected"] + fh * hits_k1 + ft * n_tracks
 
     # end to end through the host entry point: pinned host inputs -> fit -> host outputs
@@ -457,12 +518,16 @@ def main():
         return
 
     peak = fp64_peak_tflops(None)
-    # the step is four launches; the fit kernel is > 99.5 % of it, so its duration is taken as
-    # the step time measured with CUDA events on the launching stream
+    # the fit kernel's own duration, from the events the library records around it
     hv = results[head]
-    achieved = hv["flops"] / (hv["ms"] * 1e-3) / 1e12
+    achieved = hv["flops"] / (hv["kernel_ms"] * 1e-3) / 1e12
     roof = {"bound": "alu", "kernel": f"fit_persistent_kernel<{head}>", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": (TRAFFIC_PER_TRACK[(args.workload, head)] * n_tracks
+                        if (args.workload, head) in TRAFFIC_PER_TRACK else None),
+            "traffic_note": "DRAM bytes per launch, scaled by tracks from an ncu capture of 81,077 tracks; "
+                            "algorithmic bytes (inputs + outputs) per launch: "
+                            f"{host.nbytes() + n_tracks * (5 * 8 + 15 * 8 + 8 + 4 + 4 + 8)}",
             "fp64_flop_per_launch": hv["flops"],
             "note": "FP64 CUDA-core pipe (the bound of both variants); peak derived from "
                     "152 SMs x 4 flop/clk x 2070 MHz; 1.20 TFLOP/s measured by an FMA probe"}
@@ -479,9 +544,14 @@ def main():
         "vs_baseline": None,
         "dtype": "f64" if head == "fp64" else "f32+f64 (+bf16 weights)",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "variant": head, "tracks_per_gpu": n_tracks,
-                   "measurements_per_gpu": n_meas, "events_per_gpu": args.events,
-                   "field": "uniform 2 T along z", "l2": "inputs 0.41 GB > L2, no flush",
+        "config": {"workload": WORKLOAD_MAP if args.workload == "map" else WORKLOAD, "variant": head,
+                   "tracks_per_gpu": n_tracks, "measurements_per_gpu": n_meas,
+                   "events_per_gpu": None if args.workload == "map" else args.events,
+                   "field": ("solenoid r-z map, 241 x 1401 nodes, FP32" if args.workload == "map"
+                             else "uniform 2 T along z"),
+                   "l2": (f"inputs {host.nbytes() / 1e9:.2f} GB > L2, no flush" if flush is None else
+                          f"inputs {host.nbytes() / 1e9:.3f} GB: L2 flushed (258 MB write) before every step, "
+                          "steps timed one by one"),
                    "step_mode": "learned starting step + adaptive" if head.endswith("learned") else "adaptive"},
         # per step: key, scan and scatter kernels of the ordering, the proposal pre-pass
         # (learned), the persistent fit (plus one memset node)
@@ -494,7 +564,8 @@ def main():
                          "ms_per_step": v["ms_max"],
                          "step_attempts": v["attempts"], "rejected": v["rejected"],
                          "fit_status_ok": v["status_ok"], "pull_sigma": v["pulls"]["sigma"],
-                         "fp64_tflops": v["flops"] / (v["ms"] * 1e-3) / 1e12,
+                         "fit_kernel_ms": v["kernel_ms"], "fit_kernel_share": v["kernel_ms"] / v["ms"],
+                         "fp64_tflops": v["flops"] / (v["kernel_ms"] * 1e-3) / 1e12,
                          "pull_mean": v["pulls"]["mean"], "chi2_ndf_mean": v["pulls"]["chi2_ndf"]}
                      for k, v in results.items()},
     }

@@ -50,8 +50,8 @@ typedef enum tkf_status {
 } tkf_status;
 
 /* Per-track status bits written to tkf_fit_outputs.status. A track with any bit other than
- * TKF_TRACK_TOO_FEW_HITS or TKF_TRACK_OUT_OF_FIELD set has NaN parameters, covariance and
- * chi2. */
+ * TKF_TRACK_TOO_FEW_HITS, TKF_TRACK_OUT_OF_FIELD or TKF_TRACK_PROPOSAL_FALLBACK set has NaN
+ * parameters, covariance and chi2. */
 #define TKF_TRACK_MAX_STEPS (1u << 0)        /* more than max_steps step attempts to one surface */
 #define TKF_TRACK_SURFACE_MISSED (1u << 1)   /* next surface more than 1 mm behind, or parallel */
 #define TKF_TRACK_PARTICLE_STOPPED (1u << 2) /* mean energy loss left E <= mass */
@@ -62,6 +62,8 @@ typedef enum tkf_status {
 #define TKF_TRACK_BAD_INPUT (1u << 7)        /* surface id out of range, or offsets decreasing */
 #define TKF_TRACK_STEP_UNDERFLOW (1u << 8)   /* step size control fell below h_min */
 #define TKF_TRACK_NON_FINITE (1u << 9)       /* NaN/Inf in the seed or the result, theta left (0, pi) */
+#define TKF_TRACK_PROPOSAL_FALLBACK (1u << 10) /* learned mode: no proposal (the tensor-core pre-pass
+                                                  timed out), the control started from h_max */
 
 typedef struct tkf_context_s* tkf_context;
 typedef struct tkf_geometry_s* tkf_geometry;
@@ -180,6 +182,11 @@ typedef struct tkf_fit_options {
   uint32_t block_threads;
   uint32_t blocks_per_sm;
   uint32_t tracks_per_warp;
+  /* Optional kernel timing: NULL, or two cudaEvent_t (begin, end; created by the caller)
+   * that tkf_fit records on its stream right before and right after the persistent fit
+   * kernel, so that cudaEventElapsedTime gives that kernel's duration alone (without the
+   * ordering and proposal launches). A call with events launches directly (no graph). */
+  void* const* kernel_events;
 } tkf_fit_options;
 
 /* Autotuning: the first call of a launch class (precision, step mode, field kind, batch size
@@ -312,6 +319,18 @@ tkf_status tkf_mlp_loss_grad(tkf_context ctx, const float* params, const float* 
 /* Raw outputs out [n] (DEVICE) of the network with FP32 params for x [n][TKF_MLP_INPUTS]. */
 tkf_status tkf_mlp_forward(tkf_context ctx, const float* params, const float* x, uint32_t n, float* out,
                            void* stream);
+
+/* Learned mode, the proposal pre-pass alone: h0[i] (DEVICE, n_tracks floats) receives the
+ * starting step-size control that tkf_fit uses for track i with these options (opts->mlp
+ * required, step_mode TKF_STEP_LEARNED): the network, its two dense layers on the tensor cores
+ * (BF16 operands, FP32 accumulation), evaluated on the seed state at the first surface toward
+ * the second; 0.9 exp(output rounded to a 1/32 grid), clamped to [h_min, h_max]; h_max for
+ * tracks with fewer than two measurements or a bad surface id; -1 if the pre-pass timed out
+ * waiting for its tensor-core work. For inspection and tests; asynchronous on `stream`.
+ * Errors: as tkf_fit, TKF_ERR_INVALID_ARG for a NULL h0. The benchmark spec's learned step
+ * proposer has no counterpart in the paper. */
+tkf_status tkf_propose_start(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf_fit_options* opts,
+                             const tkf_fit_inputs* in, float* h0, void* stream);
 
 /* ---------------------------------------------------------------------------- allocation-free fit */
 

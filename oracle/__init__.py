@@ -104,6 +104,8 @@ def lib():
         L.orc_fit_states.argtypes = [vp, u32, ctypes.POINTER(OField), ctypes.POINTER(OOpts), u32, vp, vp,
                                      vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.orc_mlp_forward.argtypes = [vp, vp, u32, vp]
+        L.orc_propose_start.argtypes = [vp, u32, ctypes.POINTER(OField), ctypes.POINTER(OOpts), u32,
+                                        ctypes.c_uint64, vp, vp, vp, vp]
         L.orc_update.restype = u32
         L.orc_update.argtypes = [vp, vp, vp, vp, vp]
         _lib = L
@@ -265,6 +267,21 @@ def mlp_forward(w_bf16, x):
     out = np.zeros(x.shape[0], np.float32)
     lib().orc_mlp_forward(_p(w), _p(x), x.shape[0], _p(out))
     return out
+
+
+def propose_start(surfaces: np.ndarray, fld: OField, opts: Options, offsets, sid, seed_par, n_meas: int):
+    """Learned mode: every track's proposed starting step-size control (mm), from the network of
+    ``opts.mlp`` on the seed state at its first surface toward its second."""
+    s = surfaces14(surfaces)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint32)
+    n = offsets.shape[0] - 1
+    sid = np.ascontiguousarray(sid, dtype=np.uint32)
+    seed_par = _f64(seed_par)
+    h0 = np.zeros(n)
+    o = opts._c()
+    lib().orc_propose_start(_p(s), s.shape[0], ctypes.byref(fld), ctypes.byref(o), n, int(n_meas), _p(offsets),
+                            _p(sid), _p(seed_par), _p(h0))
+    return h0
 
 
 def update(m, V, p, C):

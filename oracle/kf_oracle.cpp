@@ -353,26 +353,63 @@ void mlp_features(const Surface& s, const double r[3], const double T[3], double
 
 float silu(float z) { return z / (1.0f + std::exp(-z)); }
 
-// The network's output is ln(h / mm) of the largest step within tolerance; the proposal is
-// 0.9 exp(output), clamped to [h_min, h_max].
+// BF16 rounding of an FP32 value (nearest, ties to even), returned as FP32.
+float bf16_round(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+  float y;
+  std::memcpy(&y, &u, 4);
+  return y;
+}
+
+// The network's output is ln(h / mm) of the largest step within tolerance. Reading of "BF16
+// weights, FP32 accumulate, dense layers on tensor cores": the operands of both dense layers
+// are BF16 (the inputs and the first hidden layer's activations are rounded to BF16), each
+// layer's products are exact and summed in FP32 (here: summed exactly, rounded once), and the
+// bias is added in FP32; the 64 -> 1 output layer is FP32. Reading (proposal): the output is
+// rounded to a 1/32 grid of ln h, and the proposal is 0.9 exp(k / 32), clamped to
+// [h_min, h_max]; non-finite inputs propose h_max.
 double mlp_propose(const Mlp& m, const float x[12], double h_min, double h_max) {
+  float xb[12];
+  for (int i = 0; i < 12; ++i) {
+    if (!std::isfinite(x[i])) return h_max;
+    xb[i] = bf16_round(x[i]);
+  }
   float a1[64], a2[64];
   for (int j = 0; j < 64; ++j) {
-    float z = m.b1[j];
-    for (int i = 0; i < 12; ++i) z += m.W1[j][i] * x[i];
-    a1[j] = silu(z);
+    double acc = 0.0;
+    for (int i = 0; i < 12; ++i) acc += double(m.W1[j][i]) * double(xb[i]);
+    a1[j] = bf16_round(silu(float(acc) + m.b1[j]));
   }
   for (int j = 0; j < 64; ++j) {
-    float z = m.b2[j];
-    for (int i = 0; i < 64; ++i) z += m.W2[j][i] * a1[i];
-    a2[j] = silu(z);
+    double acc = 0.0;
+    for (int i = 0; i < 64; ++i) acc += double(m.W2[j][i]) * double(a1[i]);
+    a2[j] = silu(float(acc) + m.b2[j]);
   }
   float out = m.b3;
   for (int i = 0; i < 64; ++i) out += m.w3[i] * a2[i];
-  double h = 0.9 * double(std::exp(out));
-  if (!(h >= h_min)) h = h_min;
+  const float q = 0.9f * std::exp(std::nearbyint(out * 32.0f) / 32.0f);
+  if (!std::isfinite(q)) return h_max;
+  double h = q;
+  if (h < h_min) h = h_min;
   if (h > h_max) h = h_max;
   return h;
+}
+
+void bound_to_free(const Surface& s, const double p[5], double r[3], double T[3]);
+
+// Learned mode: the starting step-size control of a track, proposed from the seed state at the
+// first surface s0, toward the second surface s1.
+double propose_start(const Surface& s0, const Surface& s1, const Field& f, const Opts& o, const double* seed_par) {
+  double r[3], T[3], B[3], diff[3];
+  bound_to_free(s0, seed_par, r, T);
+  bool oofm = false;
+  field_at(f, r, B, &oofm);
+  for (int i = 0; i < 3; ++i) diff[i] = s1.c[i] - r[i];
+  float x[12];
+  mlp_features(s1, r, T, seed_par[4], B, o.h_max, dot3(s1.n, diff) / dot3(s1.n, T), x);
+  return mlp_propose(*o.mlp, x, o.h_min, o.h_max);
 }
 
 double step_factor(double q, double lo, double hi) {
@@ -762,16 +799,7 @@ void fit_track(const Surface* surf, uint32_t n_surf, const Field& f, const Opts&
     // so the network proposes its starting value (instead of h_max) from the seed state at the
     // first surface, toward the second surface; from then on the plain control adapts it from
     // the error estimates, and the error estimate judges every step.
-    const Surface& s0 = surf[in.sid[0]];
-    const Surface& s1 = surf[in.sid[1]];
-    double r[3], T[3], B[3], diff[3];
-    bound_to_free(s0, in.seed_par, r, T);
-    bool oofm = false;
-    field_at(f, r, B, &oofm);
-    for (int i = 0; i < 3; ++i) diff[i] = s1.c[i] - r[i];
-    float x[12];
-    mlp_features(s1, r, T, in.seed_par[4], B, o.h_max, dot3(s1.n, diff) / dot3(s1.n, T), x);
-    prop.h_ctrl = mlp_propose(*o.mlp, x, o.h_min, o.h_max);
+    prop.h_ctrl = propose_start(surf[in.sid[0]], surf[in.sid[1]], f, o, in.seed_par);
   }
   double chi2 = 0.0;
   uint32_t status = 0;
@@ -1146,6 +1174,23 @@ void orc_mlp_forward(const uint16_t* w, const float* x, uint32_t n, float* out) 
     float o = m.b3;
     for (int i = 0; i < 64; ++i) o += m.w3[i] * a2[i];
     out[s] = o;
+  }
+}
+
+// Learned mode: each track's proposed starting step-size control (h_max where there are fewer
+// than two measurements or a surface id is out of range).
+void orc_propose_start(const double* surfaces, uint32_t n_surf, const orc_field* field, const orc_opts* opts,
+                       uint32_t n_tracks, uint64_t n_meas, const uint32_t* offsets, const uint32_t* sid,
+                       const double* seed_par, double* h0) {
+  std::vector<Surface> surf = to_surfaces(surfaces, n_surf);
+  Field F = to_field(field);
+  Mlp mlp_store;
+  Opts O = to_opts(opts, &mlp_store);
+  for (uint32_t i = 0; i < n_tracks; ++i) {
+    const uint32_t a = offsets[i], b = offsets[i + 1];
+    h0[i] = O.h_max;
+    if (!O.mlp || b < a || b - a < 2 || b > n_meas || sid[a] >= n_surf || sid[a + 1] >= n_surf) continue;
+    h0[i] = propose_start(surf[sid[a]], surf[sid[a + 1]], F, O, seed_par + 5 * size_t(i));
   }
 }
 

@@ -39,8 +39,10 @@ TRACK_STATUS = {
     "MAX_STEPS": 1 << 0, "SURFACE_MISSED": 1 << 1, "PARTICLE_STOPPED": 1 << 2,
     "UPDATE_NOT_SPD": 1 << 3, "SMOOTHER_NOT_SPD": 1 << 4, "TOO_FEW_HITS": 1 << 5,
     "OUT_OF_FIELD": 1 << 6, "BAD_INPUT": 1 << 7, "STEP_UNDERFLOW": 1 << 8, "NON_FINITE": 1 << 9,
+    "PROPOSAL_FALLBACK": 1 << 10,
 }
-FATAL_MASK = ~(TRACK_STATUS["TOO_FEW_HITS"] | TRACK_STATUS["OUT_OF_FIELD"]) & 0xFFFFFFFF
+FATAL_MASK = ~(TRACK_STATUS["TOO_FEW_HITS"] | TRACK_STATUS["OUT_OF_FIELD"]
+               | TRACK_STATUS["PROPOSAL_FALLBACK"]) & 0xFFFFFFFF
 
 
 class TkfError(RuntimeError):
@@ -110,7 +112,8 @@ class FitOptions(ctypes.Structure):
                 ("mass", ctypes.c_double), ("mlp", ctypes.c_void_p), ("records", ctypes.c_void_p),
                 ("record_capacity", ctypes.c_uint32), ("record_count", ctypes.c_void_p),
                 ("flags", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
-                ("blocks_per_sm", ctypes.c_uint32), ("tracks_per_warp", ctypes.c_uint32)]
+                ("blocks_per_sm", ctypes.c_uint32), ("tracks_per_warp", ctypes.c_uint32),
+                ("kernel_events", ctypes.c_void_p)]
 
 
 class MlpTrainOptions(ctypes.Structure):
@@ -150,6 +153,8 @@ _SIGNATURES = {
                                     ctypes.POINTER(FitInputs), ctypes.POINTER(FitOutputs), _VP]),
     "tkf_fit_noalloc": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(FitOptions),
                                        ctypes.POINTER(FitInputs), ctypes.POINTER(FitOutputs), _VP]),
+    "tkf_propose_start": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(FitOptions), ctypes.POINTER(FitInputs),
+                                         _VP, _VP]),
     "tkf_mlp_load": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(_VP)]),
     "tkf_mlp_destroy": (None, [_VP]),
     "tkf_mlp_train": (ctypes.c_int, [_VP, _VP, ctypes.c_uint32, ctypes.POINTER(MlpTrainOptions), _VP, _VP,
@@ -327,6 +332,7 @@ class Options:
     block_threads: int = 0        # explicit block shape (both nonzero), else default or tuned
     blocks_per_sm: int = 0
     tracks_per_warp: int = 0      # explicit tracks a warp takes at a time (1..32), else 32 or tuned
+    kernel_events: object = None  # (begin, end) torch.cuda.Event pair around the fit kernel
 
     def c(self) -> FitOptions:
         o = FitOptions()
@@ -343,6 +349,10 @@ class Options:
         o.flags = (FIT_AUTOTUNE if self.autotune else 0) | (FIT_GRAPH if self.graph else 0)
         o.block_threads, o.blocks_per_sm = self.block_threads, self.blocks_per_sm
         o.tracks_per_warp = self.tracks_per_warp
+        if self.kernel_events is not None:
+            # the C array must outlive the call: kept on the options struct
+            o._events = (ctypes.c_void_p * 2)(*(ev.cuda_event for ev in self.kernel_events))
+            o.kernel_events = ctypes.cast(o._events, ctypes.c_void_p)
         return o
 
 
@@ -481,6 +491,21 @@ def fit_host(ctx: Context, geo: Geometry, field: Field, batch: Batch, opts: Opti
                               ctypes.byref(_inputs_struct(batch)), ctypes.byref(_outputs_struct(out)),
                               _VP(s) if s else None), ctx.handle, "tkf_fit_host")
     return out
+
+
+def propose_start(ctx: Context, geo: Geometry, field: Field, batch: Batch, opts: Options, stream=None):
+    """tkf_propose_start: the learned mode's starting step-size control of every track (CUDA
+    float32 tensor [n]), as the fit computes it with ``opts`` (STEP_LEARNED, ``opts.mlp``)."""
+    import torch
+    dev = batch.offsets.device
+    h0 = torch.empty(batch.n_tracks, dtype=torch.float32, device=dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    o = opts.c()
+    _check(lib().tkf_propose_start(ctx.handle, geo.handle, field.handle, ctypes.byref(o),
+                                   ctypes.byref(_inputs_struct(batch)), _VP(h0.data_ptr()),
+                                   _VP(stream.cuda_stream)), ctx.handle, "tkf_propose_start")
+    return h0
 
 
 def fit_noalloc(ctx: Context, geo: Geometry, field: Field, batch: Batch, out: Result,

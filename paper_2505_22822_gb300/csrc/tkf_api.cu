@@ -294,14 +294,18 @@ void tkf_fit_options_default(tkf_fit_options* o) {
   o->block_threads = 0;
   o->blocks_per_sm = 0;
   o->tracks_per_warp = 0;
+  o->kernel_events = nullptr;
 }
 
+// Validation shared by the fit entry points; `out` may be NULL only when `need_out` is false.
 static tkf_status check_common(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf_fit_options* o,
-                               const tkf_fit_inputs* in, const tkf_fit_outputs* out, const char* fn) {
+                               const tkf_fit_inputs* in, const tkf_fit_outputs* out, const char* fn,
+                               bool need_out = true) {
   if (!ctx) return fail(nullptr, TKF_ERR_BAD_HANDLE, std::string(fn) + ": NULL context");
   if (!geo || !field || geo->ctx != ctx || field->ctx != ctx)
     return fail(ctx, TKF_ERR_BAD_HANDLE, std::string(fn) + ": geometry or field handle NULL or from another context");
-  if (!o || !in || !out) return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": NULL options, inputs or outputs");
+  if (!o || !in || (need_out && !out))
+    return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": NULL options, inputs or outputs");
   if (!(o->precision == TKF_FP64 || o->precision == TKF_MIXED))
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": unknown precision");
   if (!(o->step_mode == TKF_STEP_ADAPTIVE || o->step_mode == TKF_STEP_LEARNED))
@@ -326,13 +330,14 @@ static tkf_status check_common(tkf_context ctx, tkf_geometry geo, tkf_field fiel
   if (in->n_meas > 0xffffffffull)
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": n_meas exceeds 32-bit offsets");
   if (in->n_tracks == 0) return TKF_OK;
-  if (!in->offsets || !in->seed_par || !in->seed_cov || !out->par || !out->cov || !out->chi2 || !out->ndf ||
-      !out->status)
+  if (!in->offsets || !in->seed_par || !in->seed_cov)
+    return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": NULL required pointer");
+  if (out && (!out->par || !out->cov || !out->chi2 || !out->ndf || !out->status))
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": NULL required pointer");
   if (in->n_meas > 0 && (!in->loc0 || !in->loc1 || !in->v00 || !in->v01 || !in->v11 || !in->sid))
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": NULL measurement pointer");
   const void* ptrs[] = {in->loc0, in->loc1, in->v00, in->v01, in->v11, in->seed_par, in->seed_cov,
-                        out->par, out->cov, out->chi2};
+                        out ? out->par : nullptr, out ? out->cov : nullptr, out ? out->chi2 : nullptr};
   for (const void* p : ptrs)
     if (!aligned8(p)) return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": pointer not 8-byte aligned");
   return TKF_OK;
@@ -352,12 +357,14 @@ static tkf::FitArgs make_args(tkf_geometry geo, const tkf_fit_options* o, const 
   a.sid = in->sid;
   a.seed_par = in->seed_par;
   a.seed_cov = in->seed_cov;
-  a.par = out->par;
-  a.cov = out->cov;
-  a.chi2 = out->chi2;
-  a.ndf = out->ndf;
-  a.status = out->status;
-  a.steps = out->steps;
+  if (out) {
+    a.par = out->par;
+    a.cov = out->cov;
+    a.chi2 = out->chi2;
+    a.ndf = out->ndf;
+    a.status = out->status;
+    a.steps = out->steps;
+  }
   a.surf = geo->d_surf;
   a.n_surf = geo->n;
   a.mat = geo->mat;
@@ -404,8 +411,26 @@ tkf_status tkf_fit(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf
   tkf::LaunchShape shape;
   cudaError_t e = tkf::resolve_shape(ctx, a, field->f, o->precision, ws, o, st, &shape);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit: autotune");
-  e = tkf::launch_with_policy(ctx, a, field->f, o->precision, ws, shape, (o->flags & TKF_FIT_GRAPH) != 0, st);
+  const cudaEvent_t* timing = reinterpret_cast<const cudaEvent_t*>(o->kernel_events);
+  e = tkf::launch_with_policy(ctx, a, field->f, o->precision, ws, shape, (o->flags & TKF_FIT_GRAPH) != 0, st,
+                              timing);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit: launch");
+  return TKF_OK;
+}
+
+tkf_status tkf_propose_start(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf_fit_options* o,
+                             const tkf_fit_inputs* in, float* h0, void* stream) {
+  tkf_status s = check_common(ctx, geo, field, o, in, nullptr, "tkf_propose_start", false);
+  if (s != TKF_OK) return s;
+  if (o->step_mode != TKF_STEP_LEARNED)
+    return fail(ctx, TKF_ERR_INVALID_ARG, "tkf_propose_start: needs TKF_STEP_LEARNED and an mlp handle");
+  if (in->n_tracks == 0) return TKF_OK;
+  if (!h0) return fail(ctx, TKF_ERR_INVALID_ARG, "tkf_propose_start: NULL h0");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(ctx, TKF_ERR_DEVICE, "tkf_propose_start: cudaSetDevice failed");
+  tkf::FitArgs a = make_args(geo, o, in, nullptr);
+  cudaError_t e = tkf::launch_propose_start(a, field->f, h0, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_propose_start: launch");
   return TKF_OK;
 }
 

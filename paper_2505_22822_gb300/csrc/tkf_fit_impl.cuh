@@ -31,7 +31,7 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kMe = 0.51099895e-3;  // GeV
 constexpr double kBetheK = 0.307075;   // MeV cm^2 / mol
 
-constexpr uint32_t kFatal = ~(TKF_TRACK_TOO_FEW_HITS | TKF_TRACK_OUT_OF_FIELD);
+constexpr uint32_t kFatal = ~(TKF_TRACK_TOO_FEW_HITS | TKF_TRACK_OUT_OF_FIELD | TKF_TRACK_PROPOSAL_FALLBACK);
 
 // index of (i, j) in the packed row-major upper triangle of a symmetric 5x5 matrix
 __host__ __device__ constexpr int S(int i, int j) { return i <= j ? i * (9 - i) / 2 + j : j * (9 - j) / 2 + i; }
@@ -746,8 +746,17 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i, const floa
   Surf sp;                       // surface of the previous measurement
   double sph = 0.0, cph = 1.0, sth = 1.0, cth = 0.0;  // filtered direction at sp
   // learned mode: the step-size control starts from the network's proposal for this track
-  double h_ctrl = kMode == kLearned ? double(a.h0[i]) : a.opt.h_max;
-  float h_ctrl_f = kMode == kLearned ? a.h0[i] : a.opt.h_max_f;
+  // (a negative value: the proposal pre-pass gave up; start from h_max and flag the track)
+  float h_start = a.opt.h_max_f;
+  if constexpr (kMode == kLearned) {
+    h_start = a.h0[i];
+    if (!(h_start > 0.0f)) {
+      h_start = a.opt.h_max_f;
+      status |= TKF_TRACK_PROPOSAL_FALLBACK;
+    }
+  }
+  double h_ctrl = kMode == kLearned ? double(h_start) : a.opt.h_max;
+  float h_ctrl_f = h_start;
   StepLearn learn{mlp_w, a.records, a.record_capacity, a.record_count, a.opt.h_max_f, true};
 
   for (int k = 0; k < N && !(status & kFatal); ++k) {
@@ -1132,52 +1141,293 @@ inline FieldGrid grid_policy(const FieldDev& f) {
                    float(f.inv_dz), float(f.nr - 1), float(f.nz - 1)};
 }
 
-// Learned mode pre-pass: one thread per track evaluates the network on the seed state at the
-// first surface, toward the second surface, and writes the step-size control's starting value
-// 0.9 exp(output), clamped to [h_min, h_max] (h_max where there is nothing to propagate).
-// Tracks in a warp are evaluated together, so the network runs convergent.
-template <class F>
-__global__ void __launch_bounds__(256) propose_start_kernel(FitArgs a, F fld, float* __restrict__ h0) {
-  __shared__ __align__(16) float w[(kMlpParams + 3) / 4 * 4];
-  for (int k = threadIdx.x; k < kMlpParams; k += blockDim.x) w[k] = a.mlp[k];
-  __syncthreads();
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n_tracks) return;
-  const uint32_t n = a.n_tracks;
-  const uint32_t b0 = a.offsets[i], b1 = a.offsets[i + 1];
-  float h = a.opt.h_max_f;
-  const bool ok = b1 >= b0 && b1 - b0 >= 2 && b1 <= a.n_meas && a.sid[b0] < a.n_surf && a.sid[b0 + 1] < a.n_surf;
-  if (ok) {
-    Surf s0, s1;
-    load_surf(a.surf, a.sid[b0], s0);
-    load_surf(a.surf, a.sid[b0 + 1], s1);
-    double p[5];
-    for (int j = 0; j < 5; ++j) p[j] = a.seed_par[size_t(j) * n + i];
-    double sph, cph, sth, cth;
-    sincos(p[2], &sph, &cph);
-    sincos(p[3], &sth, &cth);
-    const double T[3] = {sth * cph, sth * sph, cth};
-    double r[3];
-    for (int j = 0; j < 3; ++j) r[j] = s0.c[j] + p[0] * s0.u[j] + p[1] * s0.v[j];
-    const float rf[3] = {float(r[0]), float(r[1]), float(r[2])};
-    const float Tf[3] = {float(T[0]), float(T[1]), float(T[2])};
-    float B[3];
-    bool oof = false;
-    fld.atf(rf, B, oof);
-    const double dist = s1.n[0] * (s1.c[0] - r[0]) + s1.n[1] * (s1.c[1] - r[1]) + s1.n[2] * (s1.c[2] - r[2]);
-    const double sl = dist / (s1.n[0] * T[0] + s1.n[1] * T[1] + s1.n[2] * T[2]);
-    float x[12];
-    mlp_features(s1, r, Tf, p[4], B, a.opt.h_max_f, float(sl), x);
-    const float q = 0.9f * expf(mlp_eval(w, x));
-    h = fminf(fmaxf(q, a.opt.h_min_f), a.opt.h_max_f);
-    if (!isfinite(q)) h = a.opt.h_max_f;
+// ------------------------------------------------------------------ learned pre-pass on tensor cores
+// Each track's starting step-size control comes from the network, evaluated on the seed state
+// at the first surface toward the second. The two dense layers run on the fifth-generation
+// tensor cores (tcgen05.mma, BF16 operands from shared memory, FP32 accumulators in tensor
+// memory); bias, SiLU and the 64 -> 1 output layer run on the CUDA cores. A CTA of 128 threads
+// takes tiles of 128 tracks (one track per thread and per accumulator row):
+//   features (FP32, rounded to BF16) -> A1 [128 x 16]      layer 1: D = A1 W1^T   (M128 N64 K16)
+//   SiLU(D + b1) rounded to BF16    -> A2 [128 x 64]       layer 2: D = A2 W2^T   (4 x K16)
+//   out = b3 + w3 . SiLU(D + b2);  h0 = 0.9 exp(round(32 out) / 32), clamped to [h_min, h_max].
+// The proposal is rounded to a 1/32 grid in ln h: the control only needs a rough start, and
+// the grid makes the proposal insensitive to the accumulation order of the tensor cores.
+// Operand layout: K-major, no swizzle, 8 x 16-byte core matrices; the core matrix (row group g,
+// K group q) of a [rows x K] operand sits at (g * K/8 + q) * 128 bytes, so consecutive K
+// groups are 128 bytes apart (leading byte offset) and row groups K/8 * 128 bytes (stride byte
+// offset).
+constexpr int kPropTile = 128;
+constexpr uint32_t kPropWaitLimit = 1u << 20;  // mbarrier polls before a tile gives up
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint32_t bf16_rne(float x) {
+  uint32_t u = __float_as_uint(x);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return u >> 16;
+}
+
+__device__ __forceinline__ float bf16_value(uint32_t b) { return __uint_as_float(b << 16); }
+
+// Shared-memory matrix descriptor: start address, leading and stride byte offsets (all >> 4),
+// the fixed version field 0b001 at bit 46, no swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return uint64_t((saddr >> 4) & 0x3FFFu) | (uint64_t((lbo >> 4) & 0x3FFFu) << 16) |
+         (uint64_t((sbo >> 4) & 0x3FFFu) << 32) | (uint64_t(1) << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bit 4), BF16 A (bit 7) and B (bit 10),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t kIdescM128N64 = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(kIdescM128N64), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(mbar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+  for (uint32_t it = 0; it < kPropWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(smem_addr(mbar)), "r"(parity)
+        : "memory");
+    if (done) return true;
   }
-  h0[i] = h;
+  return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 32 consecutive FP32 accumulator columns of this thread's row (lane) of tensor memory.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// Byte offset of element (row, k) in a K-major no-swizzle operand with `kgroups` groups of 8 along K.
+__device__ __forceinline__ uint32_t core_offset(int row, int k, int kgroups) {
+  return uint32_t(((row >> 3) * kgroups + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+struct __align__(1024) PropSmem {
+  uint8_t a2[kPropTile * 64 * 2];  // layer-2 activations, 16 KB
+  uint8_t a1[kPropTile * 16 * 2];  // features, 4 KB
+  uint8_t w2[64 * 64 * 2];         // W2 (N = 64 outputs x K = 64), 8 KB
+  uint8_t w1[64 * 16 * 2];         // W1 (N = 64 x K = 16, inputs 12..15 zero), 2 KB
+  float b1[64], b2[64], w3[64], b3;
+  uint64_t mbar;
+  uint32_t tmem_base;
+};
+
+template <class F>
+__global__ void __launch_bounds__(kPropTile) propose_start_tc_kernel(FitArgs a, F fld, float* __restrict__ h0) {
+  __shared__ PropSmem sm;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // weights: BF16-representable FP32 values, converted exactly
+  for (int e = tid; e < 64 * 16; e += kPropTile) {
+    const int j = e >> 4, i = e & 15;
+    const uint32_t b = i < 12 ? (__float_as_uint(a.mlp[j * 12 + i]) >> 16) : 0u;
+    *reinterpret_cast<uint16_t*>(sm.w1 + core_offset(j, i, 2)) = uint16_t(b);
+  }
+  for (int e = tid; e < 64 * 64; e += kPropTile) {
+    const int j = e >> 6, i = e & 63;
+    *reinterpret_cast<uint16_t*>(sm.w2 + core_offset(j, i, 8)) = uint16_t(__float_as_uint(a.mlp[832 + e]) >> 16);
+  }
+  if (tid < 64) {
+    sm.b1[tid] = a.mlp[768 + tid];
+    sm.b2[tid] = a.mlp[4928 + tid];
+    sm.w3[tid] = a.mlp[4992 + tid];
+  }
+  if (tid == 0) {
+    sm.b3 = a.mlp[5056];
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sm.mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {  // 64 accumulator columns, reused by both layers
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_addr(&sm.tmem_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sm.tmem_base;
+  const uint32_t t_row = tmem + (uint32_t(warp * 32) << 16);  // this warp's 32 lanes
+  const uint64_t d_a1 = umma_desc(smem_addr(sm.a1), 128, 256), d_w1 = umma_desc(smem_addr(sm.w1), 128, 256);
+  uint32_t phase = 0;
+  bool failed = false;
+  const uint32_t n = a.n_tracks, n_tiles = (n + kPropTile - 1) / kPropTile;
+
+  uint32_t tile = blockIdx.x;
+  for (; tile < n_tiles && !failed; tile += gridDim.x) {
+    const uint32_t i = tile * kPropTile + tid;
+    bool ok = false;
+    float x[12] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    if (i < n) {
+      const uint32_t b0 = a.offsets[i], b1 = a.offsets[i + 1];
+      ok = b1 >= b0 && b1 - b0 >= 2 && b1 <= a.n_meas && a.sid[b0] < a.n_surf && a.sid[b0 + 1] < a.n_surf;
+      if (ok) {
+        Surf s0, s1;
+        load_surf(a.surf, a.sid[b0], s0);
+        load_surf(a.surf, a.sid[b0 + 1], s1);
+        float p[5];
+        for (int j = 0; j < 5; ++j) p[j] = float(a.seed_par[size_t(j) * n + i]);
+        float sph, cph, sth, cth;
+        sincosf(p[2], &sph, &cph);
+        sincosf(p[3], &sth, &cth);
+        const float Tf[3] = {sth * cph, sth * sph, cth};
+        // position relative to the target surface's origin, FP32 (features are BF16 anyway)
+        float d[3], rf[3];
+        for (int j = 0; j < 3; ++j) {
+          rf[j] = float(s0.c[j]) + p[0] * s0.uf[j] + p[1] * s0.vf[j];
+          d[j] = float(s0.c[j] - s1.c[j]) + p[0] * s0.uf[j] + p[1] * s0.vf[j];
+        }
+        float B[3];
+        bool oof = false;
+        fld.atf(rf, B, oof);
+        const float sl = -(s1.nf[0] * d[0] + s1.nf[1] * d[1] + s1.nf[2] * d[2]) /
+                         (s1.nf[0] * Tf[0] + s1.nf[1] * Tf[1] + s1.nf[2] * Tf[2]);
+        x[0] = (s1.uf[0] * d[0] + s1.uf[1] * d[1] + s1.uf[2] * d[2]) * 1e-3f;
+        x[1] = (s1.vf[0] * d[0] + s1.vf[1] * d[1] + s1.vf[2] * d[2]) * 1e-3f;
+        x[2] = (s1.nf[0] * d[0] + s1.nf[1] * d[1] + s1.nf[2] * d[2]) * 1e-3f;
+        x[3] = s1.uf[0] * Tf[0] + s1.uf[1] * Tf[1] + s1.uf[2] * Tf[2];
+        x[4] = s1.vf[0] * Tf[0] + s1.vf[1] * Tf[1] + s1.vf[2] * Tf[2];
+        x[5] = s1.nf[0] * Tf[0] + s1.nf[1] * Tf[1] + s1.nf[2] * Tf[2];
+        x[6] = p[4];
+        x[7] = B[0] * 0.5f;
+        x[8] = B[1] * 0.5f;
+        x[9] = B[2] * 0.5f;
+        x[10] = logf(a.opt.h_max_f) * 0.2f;
+        x[11] = fminf(fmaxf(sl * 1e-3f, -2.0f), 2.0f);
+        for (int j = 0; j < 12; ++j) ok = ok && isfinite(x[j]);
+        if (!ok)
+          for (int j = 0; j < 12; ++j) x[j] = 0.0f;
+      }
+    }
+    {  // row tid of A1: two 16-byte chunks (K 0..7, 8..15)
+      uint4 c0, c1;
+      c0.x = bf16_rne(x[0]) | (bf16_rne(x[1]) << 16);
+      c0.y = bf16_rne(x[2]) | (bf16_rne(x[3]) << 16);
+      c0.z = bf16_rne(x[4]) | (bf16_rne(x[5]) << 16);
+      c0.w = bf16_rne(x[6]) | (bf16_rne(x[7]) << 16);
+      c1.x = bf16_rne(x[8]) | (bf16_rne(x[9]) << 16);
+      c1.y = bf16_rne(x[10]) | (bf16_rne(x[11]) << 16);
+      c1.z = 0u;
+      c1.w = 0u;
+      *reinterpret_cast<uint4*>(sm.a1 + core_offset(tid, 0, 2)) = c0;
+      *reinterpret_cast<uint4*>(sm.a1 + core_offset(tid, 8, 2)) = c1;
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      tc_mma(tmem, d_a1, d_w1, 0u);
+      tc_commit(&sm.mbar);
+    }
+    bool done = mbar_wait(&sm.mbar, phase);
+    phase ^= 1u;
+    __syncwarp();  // the tensor-memory loads are warp-collective
+    tc_fence_after();
+    float v[32];
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      tmem_ld32(t_row + uint32_t(half * 32), v);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {  // K groups 4 half + q of A2's row tid
+        uint32_t w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int j0 = half * 32 + q * 8 + 2 * e;
+          const float z0 = v[q * 8 + 2 * e] + sm.b1[j0], z1 = v[q * 8 + 2 * e + 1] + sm.b1[j0 + 1];
+          w[e] = bf16_rne(silu_f(z0)) | (bf16_rne(silu_f(z1)) << 16);
+        }
+        *reinterpret_cast<uint4*>(sm.a2 + core_offset(tid, half * 32 + q * 8, 8)) = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        tc_mma(tmem, umma_desc(smem_addr(sm.a2) + k * 256, 128, 1024), umma_desc(smem_addr(sm.w2) + k * 256, 128, 1024),
+               k > 0 ? 1u : 0u);
+      tc_commit(&sm.mbar);
+    }
+    done = mbar_wait(&sm.mbar, phase) && done;
+    phase ^= 1u;
+    __syncwarp();
+    tc_fence_after();
+    float out = sm.b3;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      tmem_ld32(t_row + uint32_t(half * 32), v);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) out = fmaf(sm.w3[half * 32 + k], silu_f(v[k] + sm.b2[half * 32 + k]), out);
+    }
+    tc_fence_before();
+    failed = __syncthreads_or(!done) != 0;
+    if (i < n) {
+      float h = a.opt.h_max_f;
+      if (ok) {
+        const float q = 0.9f * expf(rintf(out * 32.0f) * (1.0f / 32.0f));
+        h = isfinite(q) ? fminf(fmaxf(q, a.opt.h_min_f), a.opt.h_max_f) : a.opt.h_max_f;
+      }
+      h0[i] = failed ? -1.0f : h;  // -1: no proposal (the fit starts from h_max and flags it)
+    }
+  }
+  if (failed) {  // the tiles this CTA did not reach get no proposal either
+    for (; tile < n_tiles; tile += gridDim.x) {
+      const uint32_t i = tile * kPropTile + tid;
+      if (i < n) h0[i] = -1.0f;
+    }
+    mbar_wait(&sm.mbar, phase ^ 1u);  // give an MMA still in flight a bounded time to finish
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
+  }
 }
 
 template <class F>
 cudaError_t launch_propose(const FitArgs& a, const F& fld, float* h0, cudaStream_t stream) {
-  propose_start_kernel<<<(a.n_tracks + 255) / 256, 256, 0, stream>>>(a, fld, h0);
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const uint32_t tiles = (a.n_tracks + kPropTile - 1) / kPropTile;
+  const uint32_t grid = tiles < uint32_t(4 * sms) ? tiles : uint32_t(4 * sms);
+  propose_start_tc_kernel<<<grid, kPropTile, 0, stream>>>(a, fld, h0);
   return cudaGetLastError();
 }
 

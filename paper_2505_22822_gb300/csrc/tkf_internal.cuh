@@ -104,8 +104,10 @@ cudaError_t launch_fit_mixed(const FitArgs& a, const FieldDev& f, int mode, cons
                              LaunchShape shape, cudaStream_t stream);
 
 // Enqueues the fit of every track in `a` on `stream`: track ordering, then the persistent fit.
+// With `timing`, events timing[0] and timing[1] are recorded right before and after the
+// persistent fit kernel.
 cudaError_t launch_fit(const FitArgs& a, const FieldDev& field, int precision, const Workspace& ws, LaunchShape shape,
-                       cudaStream_t stream);
+                       cudaStream_t stream, const cudaEvent_t* timing = nullptr);
 
 }  // namespace tkf
 
@@ -122,7 +124,8 @@ cudaError_t resolve_shape(tkf_context_s* ctx, const FitArgs& a, const FieldDev& 
 // Direct launch, or through the context's CUDA graph when `use_graph` (captured on the second
 // consecutive call with identical arguments, replayed after that).
 cudaError_t launch_with_policy(tkf_context_s* ctx, const FitArgs& a, const FieldDev& f, int precision,
-                               const Workspace& ws, LaunchShape shape, bool use_graph, cudaStream_t stream);
+                               const Workspace& ws, LaunchShape shape, bool use_graph, cudaStream_t stream,
+                               const cudaEvent_t* timing);
 void load_tune_cache(tkf_context_s* ctx);
 void release_graph(tkf_context_s* ctx);
 

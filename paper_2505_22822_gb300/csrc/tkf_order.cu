@@ -77,7 +77,7 @@ Workspace carve_workspace(void* base, uint32_t n_tracks, bool learned) {
 }
 
 cudaError_t launch_fit(const FitArgs& a, const FieldDev& f, int precision, const Workspace& ws, LaunchShape shape,
-                       cudaStream_t stream) {
+                       cudaStream_t stream, const cudaEvent_t* timing) {
   if (a.n_tracks == 0) return cudaSuccess;
   const uint32_t n = a.n_tracks;
   cudaError_t e = cudaMemsetAsync(ws.counter, 0, sizeof(uint32_t) * (1 + kKeyBins), stream);
@@ -96,8 +96,12 @@ cudaError_t launch_fit(const FitArgs& a, const FieldDev& f, int precision, const
     if (e != cudaSuccess) return e;
     b.h0 = ws.h0;
   }
-  if (precision == TKF_MIXED) return launch_fit_mixed(b, f, mode, ws.perm, ws.counter, shape, stream);
-  return launch_fit_fp64(b, f, mode, ws.perm, ws.counter, shape, stream);
+  if (timing && (e = cudaEventRecord(timing[0], stream)) != cudaSuccess) return e;
+  e = precision == TKF_MIXED ? launch_fit_mixed(b, f, mode, ws.perm, ws.counter, shape, stream)
+                             : launch_fit_fp64(b, f, mode, ws.perm, ws.counter, shape, stream);
+  if (e != cudaSuccess) return e;
+  if (timing) e = cudaEventRecord(timing[1], stream);
+  return e;
 }
 
 }  // namespace tkf

@@ -217,8 +217,10 @@ cudaError_t resolve_shape(tkf_context ctx, const FitArgs& a, const FieldDev& f, 
 }
 
 cudaError_t launch_with_policy(tkf_context ctx, const FitArgs& a, const FieldDev& f, int precision,
-                               const Workspace& ws, LaunchShape shape, bool use_graph, cudaStream_t stream) {
-  if (!use_graph || stream == nullptr || stream == cudaStreamLegacy) return launch_fit(a, f, precision, ws, shape, stream);
+                               const Workspace& ws, LaunchShape shape, bool use_graph, cudaStream_t stream,
+                               const cudaEvent_t* timing) {
+  if (!use_graph || timing || stream == nullptr || stream == cudaStreamLegacy)
+    return launch_fit(a, f, precision, ws, shape, stream, timing);
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaError_t e = cudaStreamIsCapturing(stream, &cs);
   if (e != cudaSuccess) return e;

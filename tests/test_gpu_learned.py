@@ -151,3 +151,32 @@ def test_learned_proposals_save_step_attempts_at_equal_tolerance(ctx, trained):
     # the proposals avoid the plain control's rejected attempts without costing extra steps
     assert sl[1] < sp[1]
     assert sl[0] <= sp[0]
+
+
+def test_tensor_core_proposals_match_the_oracle(ctx, trained):
+    """The pre-pass's two dense layers run on the tensor cores (BF16 operands, FP32 accumulate);
+    its proposals sit on a 1/32 grid of ln h, so they equal the oracle's except where an
+    accumulation-order difference flips a rounding (then by one grid step)."""
+    fld, _, theta, _ = trained
+    wbf = mlp.to_bf16(theta)
+    m = tkf.Mlp(ctx, wbf)
+    w = synth.solenoid_muon_workload(20000, seed=33, fld=fld)
+    t = w.tracks
+    geo = tkf.Geometry.from_table(ctx, w.geometry.table)
+    f = tkf.Field.from_desc(ctx, w.field)
+    b = tkf.Batch.from_arrays(t.offsets, t.meas, t.sid, t.seed_par, t.seed_cov).to("cuda:0")
+    opts = tkf.Options(precision=tkf.MIXED, step_mode=tkf.STEP_LEARNED, mlp=m)
+    h_gpu = tkf.propose_start(ctx, geo, f, b, opts).cpu().numpy().astype(np.float64)
+    o = oracle.Options(mlp=wbf)
+    h_orc = oracle.propose_start(w.geometry.table, oracle.field_from(w.field), o, t.offsets, t.sid, t.seed_par,
+                                 t.n_hits)
+    assert np.all(h_gpu > 0)
+    ratio = np.log(h_gpu / h_orc) * 32.0
+    same = np.abs(ratio) < 1e-3
+    assert np.mean(same) > 0.999, np.mean(same)
+    # the rest differ by exactly one grid step (or meet a clamp)
+    k = np.abs(ratio[~same])
+    assert np.all((np.abs(k - 1.0) < 1e-3) | (h_gpu[~same] == np.float32(o.h_max)) |
+                  (h_gpu[~same] == np.float32(o.h_min)))
+    # a spread of proposals, not a constant
+    assert np.unique(np.round(np.log(h_gpu[same]) * 32)).size > 10

@@ -168,3 +168,24 @@ def test_unknown_flags_are_rejected(setup):
                        ctypes.byref(_outputs_struct(out)), None)
     assert st != 0
     assert "unknown flag" in lib().tkf_last_error(ctx.handle).decode()
+
+
+def test_kernel_events_time_the_fit_kernel_alone(setup):
+    ctx, geo, fld, b, _ = setup
+    ref = _run(ctx, geo, fld, b, precision=tkf.MIXED)
+    s = torch.cuda.Stream()
+    kev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    outer = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    for ev in kev:
+        ev.record(s)
+    out = tkf.alloc_outputs(b.n_tracks, "cuda:0")
+    for _ in range(3):
+        with torch.cuda.stream(s):
+            outer[0].record(s)
+            tkf.fit(ctx, geo, fld, b, tkf.Options(precision=tkf.MIXED, graph=True, kernel_events=kev), out=out,
+                    stream=s)
+            outer[1].record(s)
+        s.synchronize()
+        _same(_host(out), ref)
+        k, o = kev[0].elapsed_time(kev[1]), outer[0].elapsed_time(outer[1])
+        assert 0.0 < k <= o

@@ -88,3 +88,27 @@ def test_learned_control_in_the_oracle_keeps_the_fit(n_threads):
     d[:, 2] = (d[:, 2] + np.pi) % (2 * np.pi) - np.pi
     assert np.max(np.abs(d) / sig) < 0.05
     assert not np.array_equal(plain.steps, learned.steps)
+
+
+def test_proposal_grid_ties_and_clamps_in_closed_form():
+    """With every weight zero the hidden layers are silu(0) = 0, so the output is b3 and the
+    proposal is 0.9 exp(k / 32), k = b3 * 32 rounded to nearest (ties to even), clamped to
+    [h_min, h_max]; a track with fewer than two measurements gets h_max."""
+    w = synth.telescope_workload(4, seed=5)
+    t = w.tracks
+    offsets = t.offsets.astype(np.uint32).copy()
+    offsets[1] = offsets[0] + 1  # track 0: one measurement
+    for b3, k in ((2.265625, 72), (2.28125, 73), (-1.015625, -32), (10.0, None), (-12.0, None)):
+        theta = np.zeros(mlp.N_PARAMS)
+        theta[-1] = b3
+        wbf = mlp.to_bf16(theta)
+        assert float(mlp.from_bf16(wbf)[-1]) == b3  # exactly representable in BF16
+        o = oracle.Options(mlp=wbf)
+        h = oracle.propose_start(w.geometry.table, oracle.field_from(w.field), o, offsets, t.sid, t.seed_par,
+                                 t.n_hits)
+        assert h[0] == o.h_max
+        if k is None:
+            expect = o.h_max if b3 > 0 else o.h_min
+        else:
+            expect = float(np.float32(0.9) * np.exp(np.float32(k / 32.0), dtype=np.float32))
+        np.testing.assert_allclose(h[1:], expect, rtol=2e-7)

@@ -29,7 +29,7 @@ def _rank_main(rank, world, port, q):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        w = bench.make_workload(1, rank, lo=200, hi=200)
+        w = bench.make_workload("barrel", 1, rank, lo=200, hi=200)
         first = w.tracks.truth[0].tolist()
         firsts = [None] * world
         dist.all_gather_object(firsts, first)
