@@ -204,60 +204,19 @@ __device__ __forceinline__ void mlp_features(const Surf& s, const double r[3], c
   x[11] = fminf(fmaxf(sl * 1e-3f, -2.0f), 2.0f);
 }
 
-__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + expf(-z)); }
-
-// Raw network output for inputs x; w = W1 [64][12], b1, W2 [64][64], b2, w3, b3 (shared memory:
-// every lane reads the same weight, a broadcast).
-__device__ __forceinline__ float mlp_eval(const float* __restrict__ w, const float x[12]) {
-  const float* W1 = w;
-  const float* b1 = w + 768;
-  const float* W2 = w + 832;
-  const float* b2 = w + 4928;
-  const float* w3 = w + 4992;
-  float a1[64];
-#pragma unroll
-  for (int j = 0; j < 64; ++j) {
-    const float4* row = reinterpret_cast<const float4*>(W1 + j * 12);
-    const float4 c0 = row[0], c1 = row[1], c2 = row[2];
-    float z = b1[j];
-    z = fmaf(c0.x, x[0], z); z = fmaf(c0.y, x[1], z); z = fmaf(c0.z, x[2], z); z = fmaf(c0.w, x[3], z);
-    z = fmaf(c1.x, x[4], z); z = fmaf(c1.y, x[5], z); z = fmaf(c1.z, x[6], z); z = fmaf(c1.w, x[7], z);
-    z = fmaf(c2.x, x[8], z); z = fmaf(c2.y, x[9], z); z = fmaf(c2.z, x[10], z); z = fmaf(c2.w, x[11], z);
-    a1[j] = silu_f(z);
-  }
-  float out = w[5056];
-#pragma unroll 2
-  for (int j = 0; j < 64; ++j) {
-    const float4* row = reinterpret_cast<const float4*>(W2 + j * 64);
-    float z0 = b2[j], z1 = 0.0f;
-#pragma unroll
-    for (int q = 0; q < 16; q += 2) {
-      const float4 c = row[q], d = row[q + 1];
-      z0 = fmaf(c.x, a1[4 * q], z0);
-      z1 = fmaf(d.x, a1[4 * q + 4], z1);
-      z0 = fmaf(c.y, a1[4 * q + 1], z0);
-      z1 = fmaf(d.y, a1[4 * q + 5], z1);
-      z0 = fmaf(c.z, a1[4 * q + 2], z0);
-      z1 = fmaf(d.z, a1[4 * q + 6], z1);
-      z0 = fmaf(c.w, a1[4 * q + 3], z0);
-      z1 = fmaf(d.w, a1[4 * q + 7], z1);
-    }
-    out = fmaf(w3[j], silu_f(z0 + z1), out);
-  }
-  return out;
-}
+// SiLU z sigmoid(z) with the fast exponential and division (a few ulp; the proposal grid
+// absorbs the difference from the exactly rounded form)
+__device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 
 // Step modes: plain adaptive control, learned proposals, or plain control with record capture.
 constexpr int kPlain = 0, kLearned = 1, kRecord = 2;
 
 // Where learned proposals and training records go during one track's propagation.
 struct StepLearn {
-  const float* w;         // network weights (global memory), or null
   float* rec;             // record buffer, or null
   uint32_t rec_cap;
   uint32_t* rec_count;
   float h_last;           // last accepted step (network input), per track
-  bool use_mlp;           // the network has not proposed yet (true until the track's first step)
 };
 
 __device__ __forceinline__ void put_record(StepLearn& L, const float x[12], float label) {
@@ -706,7 +665,7 @@ __device__ __forceinline__ void small_sincos_m1(double x, double& s, double& cm1
 // (sin phi, cos phi, sin theta, cos theta): the predicted values come from the propagated
 // direction and the update's increments are applied by the angle-addition identities.
 template <bool kMixed, int kMode, class F>
-__device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i, const float* mlp_w) {
+__device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
   const uint32_t n = a.n_tracks;
   const uint32_t b0 = a.offsets[i], b1 = a.offsets[i + 1];
   double p[5], C[15];
@@ -757,7 +716,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i, const floa
   }
   double h_ctrl = kMode == kLearned ? double(h_start) : a.opt.h_max;
   float h_ctrl_f = h_start;
-  StepLearn learn{mlp_w, a.records, a.record_capacity, a.record_count, a.opt.h_max_f, true};
+  StepLearn learn{a.records, a.record_capacity, a.record_count, a.opt.h_max_f};
 
   for (int k = 0; k < N && !(status & kFatal); ++k) {
     const uint32_t m = b0 + k;
@@ -1124,7 +1083,6 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i, const floa
 template <bool kMixed, int kMode, class F>
 __global__ void __launch_bounds__(256) fit_persistent_kernel(FitArgs a, F fld, const uint32_t* __restrict__ perm,
                                                              uint32_t* __restrict__ counter, uint32_t tpw) {
-  const float* mlp_w = nullptr;
   const uint32_t lane = threadIdx.x & 31u;
   for (;;) {
     uint32_t base = 0;
@@ -1132,7 +1090,7 @@ __global__ void __launch_bounds__(256) fit_persistent_kernel(FitArgs a, F fld, c
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= a.n_tracks) break;
     const uint32_t j = base + lane;
-    if (lane < tpw && j < a.n_tracks) fit_track<kMixed, kMode>(a, fld, perm[j], mlp_w);
+    if (lane < tpw && j < a.n_tracks) fit_track<kMixed, kMode>(a, fld, perm[j]);
   }
 }
 
