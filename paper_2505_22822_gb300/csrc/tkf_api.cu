@@ -379,6 +379,7 @@ static tkf::FitArgs make_args(tkf_geometry geo, const tkf_fit_options* o, const 
   a.opt.h_min_f = float(o->h_min);
   a.opt.mass_f = float(o->mass);
   a.opt.me_over_mass_f = float(0.51099895e-3 / o->mass);
+  a.opt.surf_tol_f = float(o->surf_tol);
   a.mlp = (o->step_mode == TKF_STEP_LEARNED && o->mlp) ? o->mlp->d_weights : nullptr;
   a.records = (o->step_mode == TKF_STEP_ADAPTIVE) ? o->records : nullptr;
   a.record_capacity = o->record_capacity;

@@ -33,6 +33,30 @@ constexpr double kBetheK = 0.307075;   // MeV cm^2 / mol
 
 constexpr uint32_t kFatal = ~(TKF_TRACK_TOO_FEW_HITS | TKF_TRACK_OUT_OF_FIELD | TKF_TRACK_PROPOSAL_FALLBACK);
 
+// Exact FP32 <-> FP64 conversions on the integer pipes. On GB300 the hardware conversion runs
+// on the FP64 pipe (a warp instruction occupies it for 16 SM cycles), and the FP64 pipe bounds
+// the mixed path; these give the IEEE results (round to nearest even) for every normal number,
+// zero, infinity and NaN with a few integer operations. Denormals (|x| < 2^-126 in FP32) are
+// flushed to signed zero.
+__device__ __forceinline__ double f2d(float x) {
+  const uint32_t u = __float_as_uint(x), a = u & 0x7FFFFFFFu;
+  uint32_t hi = (a >> 3) + (896u << 20);                 // exponent bias 127 -> 1023
+  hi = a >= 0x7F800000u ? ((a >> 3) | 0x7FF00000u) : hi;  // infinity, NaN
+  const bool tiny = a < 0x00800000u;
+  return __hiloint2double(int((u & 0x80000000u) | (tiny ? 0u : hi)), int(tiny ? 0u : (u << 29)));
+}
+
+__device__ __forceinline__ float d2f(double x) {
+  const uint32_t hi = uint32_t(__double2hiint(x)), lo = uint32_t(__double2loint(x)), a = hi & 0x7FFFFFFFu;
+  uint32_t m = ((a - 0x38000000u) << 3) | (lo >> 29);  // exponent bias 1023 -> 127, top 23 mantissa bits
+  const uint32_t rest = lo & 0x1FFFFFFFu;              // the 29 dropped bits: round to nearest even
+  m += uint32_t(rest > 0x10000000u) | (uint32_t(rest == 0x10000000u) & m & 1u);
+  const bool nan = a > 0x7FF00000u || (a == 0x7FF00000u && lo != 0u);
+  m = a >= 0x47F00000u ? (nan ? 0x7FC00000u : 0x7F800000u) : m;  // beyond FP32: infinity or NaN
+  m = a < 0x38100000u ? 0u : m;                                  // below the FP32 normals
+  return __uint_as_float((hi & 0x80000000u) | m);
+}
+
 // index of (i, j) in the packed row-major upper triangle of a symmetric 5x5 matrix
 __host__ __device__ constexpr int S(int i, int j) { return i <= j ? i * (9 - i) / 2 + j : j * (9 - j) / 2 + i; }
 
@@ -415,21 +439,21 @@ __device__ uint32_t propagate_mixed(const F& fld, const OptionsDev& o, const Sur
   uint32_t st = 0;
   bool first = true;
   uint32_t n_here = 0;
-  const float lk = float(lam * kKappa);
-  const float tol = o.tol_f, h_min = o.h_min_f, h_max = o.h_max_f;
+  const float lk = d2f(lam * kKappa);
+  const float tol = o.tol_f, h_min = o.h_min_f, h_max = o.h_max_f, surf_tol = o.surf_tol_f;
   for (;;) {
     const double dist = s.n[0] * (s.c[0] - r[0]) + s.n[1] * (s.c[1] - r[1]) + s.n[2] * (s.c[2] - r[2]);
-    const float Tf[3] = {float(T[0]), float(T[1]), float(T[2])};
+    const float Tf[3] = {d2f(T[0]), d2f(T[1]), d2f(T[2])};
     float rf[3] = {0.0f, 0.0f, 0.0f};
     if (!F::kUniform || kMode == kRecord)
-      for (int i = 0; i < 3; ++i) rf[i] = float(r[i]);
-    const float a = dotr(nf, Tf), df = float(dist);
+      for (int i = 0; i < 3; ++i) rf[i] = d2f(r[i]);
+    const float a = dotr(nf, Tf), df = d2f(dist);
     bool oof = false;
     float B1[3], Bt1[3], k1[3];
     fld.atf(rf, B1, oof);
     for (int i = 0; i < 3; ++i) Bt1[i] = lk * B1[i];
     cross(Tf, Bt1, k1);
-    if (fabs(dist) <= o.surf_tol) {
+    if (fabsf(df) <= surf_tol) {
       if (oof) st |= TKF_TRACK_OUT_OF_FIELD;
       const float sp = parabolic_path_f(df, a, dotr(nf, k1)), sp2 = 0.5f * sp * sp;
 #pragma unroll
@@ -446,10 +470,10 @@ __device__ uint32_t propagate_mixed(const F& fld, const OptionsDev& o, const Sur
           dT[c][i] += sp * q[i];
         }
       }
-      const double spd = sp;
+      const double spd = f2d(sp);
       for (int i = 0; i < 3; ++i) {
-        r[i] += spd * T[i] + double(sp2 * k1[i]);
-        T[i] += double(sp * k1[i]);
+        r[i] += spd * T[i] + f2d(sp2 * k1[i]);
+        T[i] += f2d(sp * k1[i]);
       }
       break;
     }
@@ -536,10 +560,10 @@ __device__ uint32_t propagate_mixed(const F& fld, const OptionsDev& o, const Sur
         dT[c][i] += h6 * (q1[i] + 2.0f * q2[i] + 2.0f * q3[i] + q4[i]);
       }
     }
-    const double hd = h;
+    const double hd = f2d(h);
     for (int i = 0; i < 3; ++i) {
-      r[i] += hd * T[i] + double(h * h6 * (k1[i] + k2[i] + k3[i]));
-      T[i] += double(h6 * (k1[i] + 2.0f * k2[i] + 2.0f * k3[i] + k4[i]));
+      r[i] += hd * T[i] + f2d(h * h6 * (k1[i] + k2[i] + k3[i]));
+      T[i] += f2d(h6 * (k1[i] + 2.0f * k2[i] + 2.0f * k3[i] + k4[i]));
     }
     if (limited) {
       const float fac = (eps > 0.0f) ? step_factor_f(tol / eps) : 4.0f;
@@ -551,8 +575,8 @@ __device__ uint32_t propagate_mixed(const F& fld, const OptionsDev& o, const Sur
   bool oof = false;
   float rf[3] = {0.0f, 0.0f, 0.0f};
   if (!F::kUniform)
-    for (int i = 0; i < 3; ++i) rf[i] = float(r[i]);
-  const float Tf[3] = {float(T[0]), float(T[1]), float(T[2])};
+    for (int i = 0; i < 3; ++i) rf[i] = d2f(r[i]);
+  const float Tf[3] = {d2f(T[0]), d2f(T[1]), d2f(T[2])};
   fld.atf(rf, B, oof);
   if (oof) st |= TKF_TRACK_OUT_OF_FIELD;
   for (int i = 0; i < 3; ++i) Bt[i] = lk * B[i];
@@ -608,7 +632,7 @@ __device__ __forceinline__ uint32_t material_mixed(const Surf& s, const Material
   const float mass = o.mass_f;
   const float inv_cos = 1.0f / fabsf(dotr(s.nf, T));
   const float x = s.tf * inv_cos, xx0 = s.t_x0f * inv_cos;
-  const float lf = float(lam), l2 = lf * lf;
+  const float lf = d2f(lam), l2 = lf * lf;
   const float p2 = 1.0f / l2, m2 = mass * mass;
   const float E = sqrtf(p2 + m2);
   const float inv_beta2 = 1.0f + m2 * l2, beta2 = 1.0f / inv_beta2;
@@ -629,7 +653,7 @@ __device__ __forceinline__ uint32_t material_mixed(const Surf& s, const Material
   const float g = delta < 0.01f
                       ? delta * (0.5f + delta * (0.375f + delta * (0.3125f + delta * (0.2734375f + delta * 0.24609375f))))
                       : rsqrtf(1.0f - delta) - 1.0f;
-  lam += lam * double(g);
+  lam += lam * f2d(g);
   return 0;
 }
 
@@ -648,11 +672,11 @@ __device__ __forceinline__ void small_sincos(double x, double& s, double& c) {
 // sin x and cos x - 1 of a small angle in FP32 (absolute errors ~1e-8 |x| and ~1e-8 x^2),
 // FP64 sincos above 1/16.
 __device__ __forceinline__ void small_sincos_m1(double x, double& s, double& cm1) {
-  if (fabs(x) < 0.0625) {
-    const float xf = float(x);
+  const float xf = d2f(x);
+  if (fabsf(xf) < 0.0625f) {
     const float h = sinf(0.5f * xf);
-    s = double(sinf(xf));
-    cm1 = double(-2.0f * h * h);
+    s = f2d(sinf(xf));
+    cm1 = f2d(-2.0f * h * h);
   } else {
     double c;
     sincos(x, &s, &c);
@@ -803,7 +827,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
         }
       } else {
       // ---- mixed precision: material, propagation, Jacobian and covariance transport in FP32
-      const float Tm[3] = {float(sth * cph), float(sth * sph), float(cth)};
+      const float Tm[3] = {d2f(sth * cph), d2f(sth * sph), d2f(cth)};
       double lam = p[4];
       float th0sq;
       status |= material_mixed(sp, a.mat, a.opt, Tm, lam, th0sq);
@@ -811,7 +835,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
       double T[3] = {sth * cph, sth * sph, cth};
       double r[3];
       for (int j = 0; j < 3; ++j) r[j] = sp.c[j] + p[0] * sp.u[j] + p[1] * sp.v[j];
-      const float fsth = float(sth), fcth = float(cth), fsph = float(sph), fcph = float(cph);
+      const float fsth = d2f(sth), fcth = d2f(cth), fsph = d2f(sph), fcph = d2f(cph);
       float dr[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
       float dT[3][3] = {{-fsth * fsph, fsth * fcph, 0.0f}, {fcth * fcph, fcth * fsph, -fsth}, {0, 0, 0}};
       const float* nf = s.nf;
@@ -826,11 +850,11 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
       const double v = tn[0] * tn[0] + tn[1] * tn[1];
       double inv_st;
       if (v > 1e-12) {
-        const float yf = sqrtf(float(v));
-        double y = yf;
-        y = fma(fma(-y, y, v), double(0.5f / yf), y);
-        const float zf = 1.0f / float(y);
-        double z = zf;
+        const float yf = sqrtf(d2f(v));
+        double y = f2d(yf);
+        y = fma(fma(-y, y, v), f2d(0.5f / yf), y);
+        const float zf = 1.0f / d2f(y);
+        double z = f2d(zf);
         z = z * fma(-y, z, 2.0);
         st2 = y;
         inv_st = z;
@@ -841,11 +865,11 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
       ct2 = tn[2];
       cp2 = tn[0] * inv_st;
       sp2 = tn[1] * inv_st;
-      const float Tf[3] = {float(T[0]), float(T[1]), float(T[2])};
+      const float Tf[3] = {d2f(T[0]), d2f(T[1]), d2f(T[2])};
       const float* uf = s.uf;
       const float* vf = s.vf;
       const float inv_nT = 1.0f / dotr(nf, Tf);
-      const float fst = float(st2), fct = float(ct2), fcp = float(cp2), fsp = float(sp2), finv_st = float(inv_st);
+      const float fst = d2f(st2), fct = d2f(ct2), fcp = d2f(cp2), fsp = d2f(sp2), finv_st = d2f(inv_st);
       float Jf[5][5];
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
@@ -874,7 +898,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
       // C_pred = J (C + Q) J^T in FP32
       float Cf[15];
 #pragma unroll
-      for (int j = 0; j < 15; ++j) Cf[j] = float(C[j]);
+      for (int j = 0; j < 15; ++j) Cf[j] = d2f(C[j]);
       Cf[S(2, 2)] += th0sq / (fsth * fsth);
       Cf[S(3, 3)] += th0sq;
       float M[5][5];
@@ -901,12 +925,12 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
 #pragma unroll
             for (int q = 0; q < 5; ++q) acc += M[r0][q] * Jf[c0][q];
           }
-          C[S(r0, c0)] = double(acc);
+          C[S(r0, c0)] = f2d(acc);
         }
 #pragma unroll
       for (int r0 = 0; r0 < 5; ++r0)
 #pragma unroll
-        for (int c0 = 0; c0 < 5; ++c0) J[r0][c0] = double(Jf[r0][c0]);
+        for (int c0 = 0; c0 < 5; ++c0) J[r0][c0] = f2d(Jf[r0][c0]);
       }
       // ---- smoother: R = P J^T (in place; J row 4 is e_4)
 #pragma unroll

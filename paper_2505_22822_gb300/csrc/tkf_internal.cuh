@@ -42,7 +42,7 @@ struct OptionsDev {
   double tol, h_max, h_min, surf_tol, mass;
   uint32_t max_steps;
   // FP32 copies for the mixed path
-  float tol_f, h_max_f, h_min_f, mass_f, me_over_mass_f;
+  float tol_f, h_max_f, h_min_f, mass_f, me_over_mass_f, surf_tol_f;
 };
 
 struct FitArgs {

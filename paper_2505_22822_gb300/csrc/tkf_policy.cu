@@ -140,7 +140,8 @@ std::string graph_key(const FitArgs& a, const FieldDev& f, int precision, const 
                        f.r0, f.dr, f.z0, f.dz, f.inv_dr, f.inv_dz};
   for (double d : dm) k.put(d);
   const float fm[] = {a.mat.log_hwp_over_i_f, a.mat.bg2_density_f, a.mat.two_me_over_i2_f, a.mat.dedx_scale_f,
-                      a.opt.tol_f, a.opt.h_max_f, a.opt.h_min_f, a.opt.mass_f, a.opt.me_over_mass_f};
+                      a.opt.tol_f, a.opt.h_max_f, a.opt.h_min_f, a.opt.mass_f, a.opt.me_over_mass_f,
+                      a.opt.surf_tol_f};
   for (float x : fm) k.put(x);
   k.put(a.opt.max_steps);
   k.put(f.kind);
