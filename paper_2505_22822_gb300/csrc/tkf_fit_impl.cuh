@@ -35,25 +35,23 @@ constexpr uint32_t kFatal = ~(TKF_TRACK_TOO_FEW_HITS | TKF_TRACK_OUT_OF_FIELD | 
 
 // Exact FP32 <-> FP64 conversions on the integer pipes. On GB300 the hardware conversion runs
 // on the FP64 pipe (a warp instruction occupies it for 16 SM cycles), and the FP64 pipe bounds
-// the mixed path; these give the IEEE results (round to nearest even) for every normal number,
-// zero, infinity and NaN with a few integer operations. Denormals (|x| < 2^-126 in FP32) are
-// flushed to signed zero.
+// the mixed path; these give the IEEE results (round to nearest even) for every normal number
+// and zero with a few integer operations. FP32 denormals become signed zero; out of range
+// FP64 values (beyond the FP32 normals, infinities, NaN) become NaN, and FP32 infinities and
+// NaN become FP64 NaN, so a non-finite value stays non-finite.
 __device__ __forceinline__ double f2d(float x) {
   const uint32_t u = __float_as_uint(x), a = u & 0x7FFFFFFFu;
-  uint32_t hi = (a >> 3) + (896u << 20);                 // exponent bias 127 -> 1023
-  hi = a >= 0x7F800000u ? ((a >> 3) | 0x7FF00000u) : hi;  // infinity, NaN
-  const bool tiny = a < 0x00800000u;
-  return __hiloint2double(int((u & 0x80000000u) | (tiny ? 0u : hi)), int(tiny ? 0u : (u << 29)));
+  const bool tiny = a < 0x00800000u, special = a >= 0x7F800000u;
+  const uint32_t hi = tiny ? 0u : (special ? 0x7FF80000u : (a >> 3) + (896u << 20));  // bias 127 -> 1023
+  return __hiloint2double(int((u & 0x80000000u) | hi), int(tiny ? 0u : (u << 29)));
 }
 
 __device__ __forceinline__ float d2f(double x) {
   const uint32_t hi = uint32_t(__double2hiint(x)), lo = uint32_t(__double2loint(x)), a = hi & 0x7FFFFFFFu;
-  uint32_t m = ((a - 0x38000000u) << 3) | (lo >> 29);  // exponent bias 1023 -> 127, top 23 mantissa bits
-  const uint32_t rest = lo & 0x1FFFFFFFu;              // the 29 dropped bits: round to nearest even
-  m += uint32_t(rest > 0x10000000u) | (uint32_t(rest == 0x10000000u) & m & 1u);
-  const bool nan = a > 0x7FF00000u || (a == 0x7FF00000u && lo != 0u);
-  m = a >= 0x47F00000u ? (nan ? 0x7FC00000u : 0x7F800000u) : m;  // beyond FP32: infinity or NaN
-  m = a < 0x38100000u ? 0u : m;                                  // below the FP32 normals
+  uint32_t m = ((a - 0x38000000u) << 3) | (lo >> 29);  // bias 1023 -> 127, top 23 mantissa bits
+  // round to nearest even on the 29 dropped bits: up if above half, or at half with m odd
+  m += (lo >> 28) & ((lo & 0x0FFFFFFFu ? 1u : 0u) | m) & 1u;
+  m = a < 0x38100000u ? 0u : (a >= 0x47F00000u ? 0x7FC00000u : m);
   return __uint_as_float((hi & 0x80000000u) | m);
 }
 
