@@ -30,7 +30,8 @@ def gpu_to_track_major(res):
 
 
 def compare(g: dict, o: "oracle.FitResult", tol: float, idx=None):
-    """Returns (ok_mask over compared tracks, stats dict)."""
+    """Returns (ok mask over compared tracks, same-step-sequence mask, stats dict); stats["dev"]
+    is each track's largest deviation in the metric above."""
     if idx is None:
         idx = np.arange(o.par.shape[0])
     gp, gc, gx = g["par"][idx], g["cov"][idx], g["chi2"][idx]
@@ -61,11 +62,13 @@ def compare(g: dict, o: "oracle.FitResult", tol: float, idx=None):
     # a track that failed on both sides must be NaN on the GPU too
     nan_ok = good | ~status_eq | ((ost & 0x39F) == 0) | np.all(np.isnan(gp), axis=1)
     ok = status_eq & ndf_eq & (rp <= tol) & (rc <= tol) & (rx <= tol) & nan_ok
+    dev = np.maximum(np.maximum(rp, rc), rx)
     same_steps = None
     if g.get("steps") is not None:
         same_steps = np.all(g["steps"][idx] == osteps, axis=1)
     stats = {
         "n": int(len(idx)), "ok": int(ok.sum()), "status_mismatch": int((~status_eq).sum()),
+        "dev": dev,
         "max_rel_par": float(rp.max()) if len(rp) else 0.0,
         "max_rel_cov": float(rc.max()) if len(rc) else 0.0,
         "max_rel_chi2": float(rx.max()) if len(rx) else 0.0,
@@ -74,3 +77,29 @@ def compare(g: dict, o: "oracle.FitResult", tol: float, idx=None):
         if len(idx) else 0.0,
     }
     return ok, same_steps, stats
+
+
+def self_sensitivity(w, track: int, trials: int = 8, seed: int = 0) -> float:
+    """How far the oracle's own result for one track moves, in the metric above, when its seed
+    parameters and measured positions change by one unit in the last place (random signs): the
+    resolution to which the track's FP64 result is determined at all. Two correct FP64
+    evaluations in different orders cannot be expected to agree more closely than this."""
+    t = w.tracks
+    sub = t.subset(np.array([track]))
+    fo = oracle.field_from(w.field)
+    opts = oracle.Options(mass=w.mass)
+    base = oracle.fit(w.geometry.table, fo, opts, sub.offsets, sub.meas, sub.sid, sub.seed_par, sub.seed_cov)
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    for _ in range(trials):
+        sp = sub.seed_par * (1 + rng.choice([-1.0, 1.0], size=sub.seed_par.shape) * 2.0 ** -52)
+        m = sub.meas.copy()
+        m[:, :2] *= 1 + rng.choice([-1.0, 1.0], size=m[:, :2].shape) * 2.0 ** -52
+        o = oracle.fit(w.geometry.table, fo, opts, sub.offsets, m, sub.sid, sp, sub.seed_cov)
+        g = {"par": o.par, "cov": o.cov, "chi2": o.chi2, "ndf": o.ndf.astype(np.int64), "status": o.status,
+             "steps": o.steps}
+        if not np.array_equal(o.steps, base.steps):
+            continue  # a different step sequence is another comparison
+        _, _, st = compare(g, base, np.inf)
+        worst = max(worst, float(st["dev"][0]))
+    return worst

@@ -1,0 +1,23 @@
+"""How precisely the FP64 fit result of a track is determined: the oracle's own output under
+one-ulp changes of its inputs. Most tracks move by ~1e-12 in the parity metric; a few
+(long, low-momentum tracks whose smoother shrinks the q/p variance many times over) move by
+more than the 1e-10 parity tolerance, so no correct FP64 evaluation in another order can be
+held to it there. The full-size GPU parity tests accept such a track only within 3x this
+movement (tests/test_gpu_parity.check)."""
+
+import numpy as np
+
+import synth
+from tests import parity
+
+
+def test_sensitivity_is_tiny_for_ordinary_tracks_and_large_for_ill_conditioned_ones():
+    w = synth.solenoid_muon_workload(100_000, seed=3)
+    ordinary = [parity.self_sensitivity(w, i) for i in (0, 1, 2, 3)]
+    assert max(ordinary) < 2e-11, ordinary
+    # a 1 GeV muon at theta 172 degrees, 14 measurements, 77 step attempts through the end of
+    # the solenoid: the smoother reduces var(q/p) 59-fold from the prior
+    ill = parity.self_sensitivity(w, 56715)
+    assert ill > 1e-10, ill
+    t = w.tracks
+    assert np.diff(t.offsets.astype(np.int64))[56715] == 14
