@@ -273,9 +273,9 @@ def setup_tune_cache() -> str:
 
 
 def tuned_shape(path: str, variant: str, n_tracks: int, field: str, disabled: bool):
-    """[threads, blocks per SM, tracks per warp] the autotuner chose for this launch class."""
+    """[threads, blocks per SM, tracks per warp, registers] the autotuner chose for this class."""
     if disabled:
-        return [128, 2, 32]
+        return [128, 2, 32, 255] if variant == "fp64" else [128, 4, 32, 128]
     prec = "fp64" if variant == "fp64" else "mixed"
     mode = "learned" if variant.endswith("learned") else "adaptive"
     prefix = f"{prec}.{mode}.{field}.n{int(n_tracks).bit_length() - 1}."

@@ -174,14 +174,19 @@ typedef struct tkf_fit_options {
   /* Launch policy (no effect on the results: every track's arithmetic is the same under any
    * launch shape). flags: TKF_FIT_AUTOTUNE and/or TKF_FIT_GRAPH, default 0. block_threads
    * (32, 64, 128 or 256) and blocks_per_sm (1..32) fix the persistent kernel's block shape
-   * when both are nonzero; tracks_per_warp (1..32) fixes how many tracks a warp takes at a
-   * time, one per lane, when nonzero. With all three 0 the shape is the tuned one of this
-   * launch class when TKF_FIT_AUTOTUNE is set, else 128 threads x 2 blocks per SM x 32
-   * tracks per warp; an explicit part disables tuning and the other parts take defaults. */
+   * when both are nonzero (with the full register file unless max_registers says otherwise);
+   * tracks_per_warp (1..32) fixes how many tracks a warp takes at a time, one per lane, when
+   * nonzero; max_registers (255, or 128 / 64 for TKF_MIXED without record capture, blocks of
+   * at most 128 threads) picks the kernel variant capped at that many registers a thread,
+   * which keeps part of the per-track state in local memory and holds more warps per SM. With
+   * all four 0 the shape is the tuned one of this launch class when TKF_FIT_AUTOTUNE is set,
+   * else FP64: 128 threads x 2 blocks per SM, 255 registers; mixed: 128 x 4, 128 registers;
+   * 32 tracks per warp. An explicit part disables tuning; the other parts take defaults. */
   uint32_t flags;
   uint32_t block_threads;
   uint32_t blocks_per_sm;
   uint32_t tracks_per_warp;
+  uint32_t max_registers;
   /* Optional kernel timing: NULL, or two cudaEvent_t (begin, end; created by the caller)
    * that tkf_fit records on its stream right before and right after the persistent fit
    * kernel, so that cudaEventElapsedTime gives that kernel's duration alone (without the
@@ -191,14 +196,15 @@ typedef struct tkf_fit_options {
 
 /* Autotuning: the first call of a launch class (precision, step mode, field kind, batch size
  * rounded down to a power of two, SM count) times every candidate launch shape on the call's
- * own inputs (six block shapes; below one track per lane of every resident warp also 16, 8
- * and 4 tracks per warp; each candidate runs the whole fit into the call's outputs, then the
- * call runs with the fastest shape) and keeps the winner in the context. The call
- * synchronizes its stream while tuning. If the environment variable TKF_AUTOTUNE_CACHE names
- * a file when the context is created, tuned shapes are read from it and every new one is
- * written back (JSON object: class -> [threads, blocks per SM, tracks per warp]); an
- * unreadable or unwritable file is ignored. Skipped (defaults used) while the stream is
- * capturing and in record-capture mode. */
+ * own inputs (six block shapes at 255 registers, and for the mixed path three each at 128 and
+ * 64 registers; below one track per lane of every resident warp also 16, 8 and 4 tracks per
+ * warp; each candidate runs the whole fit into the call's outputs, then the call runs with the
+ * fastest shape) and keeps the winner in the context. The call synchronizes its stream while
+ * tuning. If the environment variable TKF_AUTOTUNE_CACHE names a file when the context is
+ * created, tuned shapes are read from it and every new one is written back (JSON object:
+ * class -> [threads, blocks per SM, tracks per warp, registers]); an unreadable or unwritable
+ * file is ignored. Skipped (defaults used) while the stream is capturing and in record-capture
+ * mode. */
 #define TKF_FIT_AUTOTUNE 1u
 /* Graph replay: the ordering and fit launches of a call are captured into a CUDA graph on the
  * second consecutive call with identical arguments (every pointer, size, option, handle and

@@ -24,7 +24,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _ROOT = os.path.dirname(_HERE)
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "libtkf.so")
-_SOURCES = ["tkf_api.cu", "tkf_order.cu", "tkf_policy.cu", "tkf_fit_fp64.cu", "tkf_fit_mixed.cu", "tkf_mlp.cu"]
+_SOURCES = ["tkf_api.cu", "tkf_order.cu", "tkf_policy.cu", "tkf_fit_fp64.cu", "tkf_fit_mixed.cu",
+            "tkf_fit_mixed_r128.cu", "tkf_fit_mixed_r64.cu", "tkf_mlp.cu"]
 _lib = None
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
@@ -113,7 +114,7 @@ class FitOptions(ctypes.Structure):
                 ("record_capacity", ctypes.c_uint32), ("record_count", ctypes.c_void_p),
                 ("flags", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
                 ("blocks_per_sm", ctypes.c_uint32), ("tracks_per_warp", ctypes.c_uint32),
-                ("kernel_events", ctypes.c_void_p)]
+                ("max_registers", ctypes.c_uint32), ("kernel_events", ctypes.c_void_p)]
 
 
 class MlpTrainOptions(ctypes.Structure):
@@ -332,6 +333,7 @@ class Options:
     block_threads: int = 0        # explicit block shape (both nonzero), else default or tuned
     blocks_per_sm: int = 0
     tracks_per_warp: int = 0      # explicit tracks a warp takes at a time (1..32), else 32 or tuned
+    max_registers: int = 0        # explicit register cap (255; 128 or 64 for MIXED), else default or tuned
     kernel_events: object = None  # (begin, end) torch.cuda.Event pair around the fit kernel
 
     def c(self) -> FitOptions:
@@ -349,6 +351,7 @@ class Options:
         o.flags = (FIT_AUTOTUNE if self.autotune else 0) | (FIT_GRAPH if self.graph else 0)
         o.block_threads, o.blocks_per_sm = self.block_threads, self.blocks_per_sm
         o.tracks_per_warp = self.tracks_per_warp
+        o.max_registers = self.max_registers
         if self.kernel_events is not None:
             # the C array must outlive the call: kept on the options struct
             o._events = (ctypes.c_void_p * 2)(*(ev.cuda_event for ev in self.kernel_events))

@@ -294,6 +294,7 @@ void tkf_fit_options_default(tkf_fit_options* o) {
   o->block_threads = 0;
   o->blocks_per_sm = 0;
   o->tracks_per_warp = 0;
+  o->max_registers = 0;
   o->kernel_events = nullptr;
 }
 
@@ -323,10 +324,12 @@ static tkf_status check_common(tkf_context ctx, tkf_geometry geo, tkf_field fiel
                 std::string(fn) + ": options need tol, h_max, h_min, surf_tol, mass > 0, h_min <= h_max, max_steps > 0");
   if ((o->flags & ~(TKF_FIT_AUTOTUNE | TKF_FIT_GRAPH)) != 0)
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": unknown flag");
-  if (!tkf::valid_block_shape(o->block_threads, o->blocks_per_sm, o->tracks_per_warp))
+  if (!tkf::valid_block_shape(o->block_threads, o->blocks_per_sm, o->tracks_per_warp, o->max_registers, o->precision,
+                              o->records != nullptr))
     return fail(ctx, TKF_ERR_INVALID_ARG,
-                std::string(fn) + ": block shape needs threads 32, 64, 128 or 256 and 1..32 blocks per SM (or 0, 0), "
-                                  "and 0..32 tracks per warp");
+                std::string(fn) + ": block shape needs threads 32, 64, 128 or 256 (at most 128 below 255 registers) "
+                                  "and 1..32 blocks per SM (or 0, 0), 0..32 tracks per warp, and max_registers 0, 255, "
+                                  "or 128 / 64 for the mixed path without record capture");
   if (in->n_meas > 0xffffffffull)
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": n_meas exceeds 32-bit offsets");
   if (in->n_tracks == 0) return TKF_OK;
@@ -672,13 +675,14 @@ extern "C" tkf_status tkf_fit_noalloc(tkf_context ctx, tkf_geometry geo, tkf_fie
   tkf::FitArgs a = make_args(geo, o, in, out);
   // the launch clears the counter and histogram before use (the array keeps the last call's data)
   tkf::Workspace ws = tkf::carve_workspace(scratch, in->n_tracks, false);
-  tkf::LaunchShape shape;
-  shape.blocks = 2 * ctx->sm_count;
+  tkf::LaunchShape shape = tkf::default_launch_shape(o->precision, false, ctx->sm_count);
   if (o->block_threads && o->blocks_per_sm) {
     shape.threads = int(o->block_threads);
     shape.blocks = int(o->blocks_per_sm) * ctx->sm_count;
+    shape.regs = 255;
   }
   if (o->tracks_per_warp) shape.tracks_per_warp = int(o->tracks_per_warp);
+  if (o->max_registers) shape.regs = int(o->max_registers);
   e = tkf::launch_fit(a, field->f, o->precision, ws, shape, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_noalloc: launch");
   return TKF_OK;

@@ -1101,10 +1101,16 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
 
 // Persistent fit: each warp takes the next `tpw` (1..32) tracks of the ordered list from a
 // global counter, one per lane; lanes tpw..31 idle. Fewer tracks per warp spread a small batch
-// over more warps and schedulers.
-template <bool kMixed, int kMode, class F>
-__global__ void __launch_bounds__(256) fit_persistent_kernel(FitArgs a, F fld, const uint32_t* __restrict__ perm,
-                                                             uint32_t* __restrict__ counter, uint32_t tpw) {
+// over more warps and schedulers. kRegs caps the registers a thread (255, 128 or 64): below
+// 255 part of the per-track state lives in local memory (L1), and an SM holds 16 or 32 warps
+// instead of 8, which hides more of the latency between the FP64 and FP32 phases.
+constexpr int reg_block_threads(int regs) { return regs >= 255 ? 256 : 128; }
+constexpr int reg_min_blocks(int regs) { return regs >= 255 ? 1 : 65536 / (regs * 128); }
+
+template <bool kMixed, int kMode, int kRegs, class F>
+__global__ void __launch_bounds__(reg_block_threads(kRegs), reg_min_blocks(kRegs))
+    fit_persistent_kernel(FitArgs a, F fld, const uint32_t* __restrict__ perm, uint32_t* __restrict__ counter,
+                          uint32_t tpw) {
   const uint32_t lane = threadIdx.x & 31u;
   for (;;) {
     uint32_t base = 0;
@@ -1422,32 +1428,38 @@ cudaError_t propose_fields(const FitArgs& a, const FieldDev& f, float* h0, cudaS
 }
 
 // Launches the persistent fit for one precision, step mode and field.
-template <bool kMixed, int kMode, class F>
+template <bool kMixed, int kMode, int kRegs, class F>
 cudaError_t launch_persistent(const FitArgs& a, const F& fld, const uint32_t* perm, uint32_t* counter,
                               LaunchShape shape, cudaStream_t stream) {
-  fit_persistent_kernel<kMixed, kMode>
+  if (shape.threads > reg_block_threads(kRegs)) return cudaErrorInvalidConfiguration;
+  fit_persistent_kernel<kMixed, kMode, kRegs>
       <<<shape.blocks, shape.threads, 0, stream>>>(a, fld, perm, counter, uint32_t(shape.tracks_per_warp));
   return cudaGetLastError();
 }
 
-template <bool kMixed, class F>
+// Record capture (training only) is built with the full register file alone.
+template <bool kMixed, int kRegs, class F>
 cudaError_t launch_mode(const FitArgs& a, const F& fld, int mode, const uint32_t* perm, uint32_t* counter,
                         LaunchShape shape, cudaStream_t stream) {
-  if (mode == kLearned) return launch_persistent<kMixed, kLearned>(a, fld, perm, counter, shape, stream);
-  if (mode == kRecord) return launch_persistent<kMixed, kRecord>(a, fld, perm, counter, shape, stream);
-  return launch_persistent<kMixed, kPlain>(a, fld, perm, counter, shape, stream);
+  if (mode == kLearned) return launch_persistent<kMixed, kLearned, kRegs>(a, fld, perm, counter, shape, stream);
+  if (mode == kRecord) {
+    if constexpr (kRegs == 255) return launch_persistent<kMixed, kRecord, kRegs>(a, fld, perm, counter, shape, stream);
+    return cudaErrorInvalidValue;
+  }
+  return launch_persistent<kMixed, kPlain, kRegs>(a, fld, perm, counter, shape, stream);
 }
 
-template <bool kMixed>
+template <bool kMixed, int kRegs>
 cudaError_t launch_fields(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm, uint32_t* counter,
                           LaunchShape shape, cudaStream_t stream) {
   if (f.kind == TKF_FIELD_UNIFORM) {
     if (f.b[0] == 0.0 && f.b[1] == 0.0)
-      return launch_mode<kMixed>(a, FieldUniformZ{f.b[2], float(f.b[2])}, mode, perm, counter, shape, stream);
-    return launch_mode<kMixed>(a, FieldUniform{{f.b[0], f.b[1], f.b[2]}, {float(f.b[0]), float(f.b[1]), float(f.b[2])}},
-                               mode, perm, counter, shape, stream);
+      return launch_mode<kMixed, kRegs>(a, FieldUniformZ{f.b[2], float(f.b[2])}, mode, perm, counter, shape, stream);
+    return launch_mode<kMixed, kRegs>(
+        a, FieldUniform{{f.b[0], f.b[1], f.b[2]}, {float(f.b[0]), float(f.b[1]), float(f.b[2])}}, mode, perm, counter,
+        shape, stream);
   }
-  return launch_mode<kMixed>(a, grid_policy(f), mode, perm, counter, shape, stream);
+  return launch_mode<kMixed, kRegs>(a, grid_policy(f), mode, perm, counter, shape, stream);
 }
 
 }  // namespace

@@ -90,11 +90,13 @@ Workspace carve_workspace(void* base, uint32_t n_tracks, bool learned);
 cudaError_t launch_propose_start(const FitArgs& a, const FieldDev& f, float* h0, cudaStream_t stream);
 
 // Launch shape of the persistent fit: threads per block, blocks in the grid, tracks a warp
-// takes at a time (1..32, one per lane).
+// takes at a time (1..32, one per lane), and the register cap of the kernel variant (255, or
+// 128 / 64 for the mixed path, whose blocks then have at most 128 threads).
 struct LaunchShape {
   int threads = 128;
   int blocks = 0;
   int tracks_per_warp = 32;
+  int regs = 255;
 };
 
 // Persistent fit launches per precision; mode 0 plain, 1 learned proposals, 2 record capture.
@@ -102,6 +104,10 @@ cudaError_t launch_fit_fp64(const FitArgs& a, const FieldDev& f, int mode, const
                             LaunchShape shape, cudaStream_t stream);
 cudaError_t launch_fit_mixed(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm, uint32_t* counter,
                              LaunchShape shape, cudaStream_t stream);
+cudaError_t launch_fit_mixed_r128(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm,
+                                  uint32_t* counter, LaunchShape shape, cudaStream_t stream);
+cudaError_t launch_fit_mixed_r64(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm,
+                                 uint32_t* counter, LaunchShape shape, cudaStream_t stream);
 
 // Enqueues the fit of every track in `a` on `stream`: track ordering, then the persistent fit.
 // With `timing`, events timing[0] and timing[1] are recorded right before and after the
@@ -118,7 +124,8 @@ namespace tkf {
 // Launch policy (tkf_policy.cu). The block shape of a call: the explicit one of the options,
 // the context's tuned one for the launch class (timing the candidates on the first call when
 // TKF_FIT_AUTOTUNE is set), else the default.
-bool valid_block_shape(uint32_t threads, uint32_t blocks_per_sm, uint32_t tracks_per_warp);
+bool valid_block_shape(uint32_t threads, uint32_t blocks_per_sm, uint32_t tracks_per_warp, uint32_t max_registers,
+                       int precision, bool record);
 cudaError_t resolve_shape(tkf_context_s* ctx, const FitArgs& a, const FieldDev& f, int precision, const Workspace& ws,
                           const tkf_fit_options* o, cudaStream_t stream, LaunchShape* out);
 // Direct launch, or through the context's CUDA graph when `use_graph` (captured on the second
@@ -127,6 +134,8 @@ cudaError_t launch_with_policy(tkf_context_s* ctx, const FitArgs& a, const Field
                                const Workspace& ws, LaunchShape shape, bool use_graph, cudaStream_t stream,
                                const cudaEvent_t* timing);
 void load_tune_cache(tkf_context_s* ctx);
+// The launch shape used without tuning or explicit options.
+LaunchShape default_launch_shape(int precision, bool record, int sm_count);
 void release_graph(tkf_context_s* ctx);
 
 }  // namespace tkf
@@ -135,8 +144,9 @@ struct tkf_context_s {
   int device = 0;
   int sm_count = 0;
   std::string last_error;
-  // autotuner: best (threads, blocks per SM, tracks per warp) per launch class; optional cache file
-  std::map<std::string, std::array<int, 3>> tuned;
+  // autotuner: best (threads, blocks per SM, tracks per warp, registers) per launch class;
+  // optional cache file
+  std::map<std::string, std::array<int, 4>> tuned;
   std::string tune_cache_path;
   // CUDA graph of the last repeated launch sequence
   cudaGraphExec_t graph_exec = nullptr;

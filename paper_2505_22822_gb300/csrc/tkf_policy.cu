@@ -18,15 +18,30 @@
 namespace tkf {
 namespace {
 
-// Candidate (threads per block, blocks per SM). The fit kernel takes 255 registers a thread,
-// so an SM holds 8 warps of it: the first four fill it, the last two use half of it (less
-// contention for the FP64 pipe and the L1 per warp).
-constexpr int kCandidates[][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {64, 2}, {128, 1}};
+// Candidates: (threads per block, blocks per SM, registers a thread). With 255 registers an SM
+// holds 8 warps: the first four shapes fill it, the next two use half of it (less contention
+// for the FP64 pipe and the L1 per warp). The mixed path also has kernels capped at 128 and 64
+// registers (16 and 32 warps an SM, part of the per-track state in local memory): more warps
+// hide more of the latency between its FP64 and FP32 phases, at the cost of spill traffic, and
+// which balance wins depends on the field and the tracks.
+struct Candidate {
+  int threads, blocks_per_sm, regs;
+};
+constexpr Candidate kCandidates[] = {{32, 8, 255},   {64, 4, 255},   {128, 2, 255}, {256, 1, 255},
+                                     {64, 2, 255},   {128, 1, 255},  {128, 4, 128}, {64, 8, 128},
+                                     {32, 16, 128},  {128, 8, 64},   {64, 16, 64},  {32, 32, 64}};
 // Tracks per warp: below one track per lane of every resident warp, fewer tracks per warp
 // spread the batch over more schedulers.
 constexpr int kTracksPerWarp[] = {32, 16, 8, 4};
-constexpr int kDefaultThreads = 128, kDefaultBlocksPerSm = 2, kDefaultTracksPerWarp = 32;
 constexpr int kResidentWarpsPerSm = 8;
+
+// Defaults without tuning: FP64 128 x 2 at 255 registers; mixed 128 x 4 at 128 registers (the
+// best single shape over the uniform-field and field-map batches); record capture keeps the
+// full register file (its kernels exist only there).
+std::array<int, 4> default_shape(int precision, bool record) {
+  if (precision == TKF_MIXED && !record) return {128, 4, 32, 128};
+  return {128, 2, 32, 255};
+}
 
 int field_class(const FieldDev& f) {
   if (f.kind != TKF_FIELD_UNIFORM) return 2;
@@ -46,17 +61,16 @@ std::string tune_key(const FitArgs& a, const FieldDev& f, int precision, int sm_
   return buf;
 }
 
-LaunchShape make_shape(int threads, int blocks_per_sm, int tracks_per_warp, int sm_count) {
+LaunchShape make_shape(const std::array<int, 4>& c, int sm_count) {
   LaunchShape s;
-  s.threads = threads;
-  s.blocks = blocks_per_sm * sm_count;
-  s.tracks_per_warp = tracks_per_warp;
+  s.threads = c[0];
+  s.blocks = c[1] * sm_count;
+  s.tracks_per_warp = c[2];
+  s.regs = c[3];
   return s;
 }
 
-LaunchShape make_shape(const std::array<int, 3>& c, int sm_count) { return make_shape(c[0], c[1], c[2], sm_count); }
-
-// Cache file: one JSON object, "class": [threads, blocks_per_sm, tracks_per_warp] per entry.
+// Cache file: one JSON object, "class": [threads, blocks_per_sm, tracks_per_warp, registers].
 void save_cache(const tkf_context ctx) {
   if (ctx->tune_cache_path.empty()) return;
   const std::string tmp = ctx->tune_cache_path + ".tmp";
@@ -65,32 +79,34 @@ void save_cache(const tkf_context ctx) {
   fprintf(fp, "{\n");
   size_t k = 0;
   for (const auto& kv : ctx->tuned)
-    fprintf(fp, "  \"%s\": [%d, %d, %d]%s\n", kv.first.c_str(), kv.second[0], kv.second[1], kv.second[2],
-            ++k < ctx->tuned.size() ? "," : "");
+    fprintf(fp, "  \"%s\": [%d, %d, %d, %d]%s\n", kv.first.c_str(), kv.second[0], kv.second[1], kv.second[2],
+            kv.second[3], ++k < ctx->tuned.size() ? "," : "");
   fprintf(fp, "}\n");
   const bool ok = fclose(fp) == 0;
   if (ok) rename(tmp.c_str(), ctx->tune_cache_path.c_str());
 }
 
-bool valid_shape(int threads, int bps) {
-  return (threads == 32 || threads == 64 || threads == 128 || threads == 256) && bps >= 1 && bps <= 32;
+bool valid_shape(int threads, int bps, int regs) {
+  return (threads == 32 || threads == 64 || threads == 128 || (threads == 256 && regs == 255)) && bps >= 1 &&
+         bps <= 32 && (regs == 255 || regs == 128 || regs == 64);
 }
 
 // Times every candidate on the call's inputs: one warm-up fit, then the best of two fits each.
 cudaError_t tune(tkf_context ctx, const FitArgs& a, const FieldDev& f, int precision, const Workspace& ws,
-                 cudaStream_t stream, std::array<int, 3>* best) {
+                 cudaStream_t stream, std::array<int, 4>* best) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   float best_ms = INFINITY;
-  *best = {kDefaultThreads, kDefaultBlocksPerSm, kDefaultTracksPerWarp};
+  *best = default_shape(precision, a.records != nullptr);
   if (e == cudaSuccess) e = launch_fit(a, f, precision, ws, make_shape(*best, ctx->sm_count), stream);
   const bool small = a.n_tracks < uint32_t(32 * kResidentWarpsPerSm * ctx->sm_count);
   for (const int tpw : kTracksPerWarp) {
     if (tpw != 32 && !small) break;
-    for (const auto& c : kCandidates) {
+    for (const Candidate& c : kCandidates) {
       if (e != cudaSuccess) break;
-      const std::array<int, 3> cand = {c[0], c[1], tpw};
+      if (c.regs != 255 && precision != TKF_MIXED) continue;
+      const std::array<int, 4> cand = {c.threads, c.blocks_per_sm, tpw, c.regs};
       const LaunchShape s = make_shape(cand, ctx->sm_count);
       for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
         e = cudaEventRecord(e0, stream);
@@ -126,6 +142,7 @@ std::string graph_key(const FitArgs& a, const FieldDev& f, int precision, const 
   k.put(shape.threads);
   k.put(shape.blocks);
   k.put(shape.tracks_per_warp);
+  k.put(shape.regs);
   k.put(a.n_tracks);
   k.put(a.n_meas);
   const void* ptrs[] = {a.offsets, a.loc0,   a.loc1,  a.v00,      a.v01,     a.v11,
@@ -163,7 +180,7 @@ void load_tune_cache(tkf_context ctx) {
   size_t n;
   while ((n = fread(buf, 1, sizeof(buf), fp)) > 0) text.append(buf, n);
   fclose(fp);
-  // entries "class": [threads, blocks_per_sm, tracks_per_warp]; anything else is skipped
+  // entries "class": [threads, blocks_per_sm, tracks_per_warp, registers]; anything else is skipped
   size_t pos = 0;
   while ((pos = text.find('"', pos)) != std::string::npos) {
     const size_t end = text.find('"', pos + 1);
@@ -173,9 +190,10 @@ void load_tune_cache(tkf_context ctx) {
     const size_t next = text.find('"', end + 1);
     pos = end + 1;
     if (lb == std::string::npos || (next != std::string::npos && next < lb)) continue;
-    int t = 0, b = 0, w = 0;
-    if (sscanf(text.c_str() + lb, "[ %d , %d , %d ]", &t, &b, &w) == 3 && valid_shape(t, b) && w >= 1 && w <= 32)
-      ctx->tuned[key] = {t, b, w};
+    int t = 0, b = 0, w = 0, r = 0;
+    if (sscanf(text.c_str() + lb, "[ %d , %d , %d , %d ]", &t, &b, &w, &r) == 4 && valid_shape(t, b, r) && w >= 1 &&
+        w <= 32)
+      ctx->tuned[key] = {t, b, w, r};
   }
 }
 
@@ -186,19 +204,29 @@ void release_graph(tkf_context ctx) {
   ctx->pending_key.clear();
 }
 
-bool valid_block_shape(uint32_t threads, uint32_t blocks_per_sm, uint32_t tracks_per_warp) {
+bool valid_block_shape(uint32_t threads, uint32_t blocks_per_sm, uint32_t tracks_per_warp, uint32_t max_registers,
+                       int precision, bool record) {
   if (tracks_per_warp > 32) return false;
+  if (max_registers != 0 && max_registers != 255 && max_registers != 128 && max_registers != 64) return false;
+  if (max_registers != 0 && max_registers != 255 && (precision != TKF_MIXED || record)) return false;
   if (threads == 0 && blocks_per_sm == 0) return true;
-  return valid_shape(int(threads), int(blocks_per_sm));
+  return valid_shape(int(threads), int(blocks_per_sm), max_registers ? int(max_registers) : 255);
 }
 
 cudaError_t resolve_shape(tkf_context ctx, const FitArgs& a, const FieldDev& f, int precision, const Workspace& ws,
                           const tkf_fit_options* o, cudaStream_t stream, LaunchShape* out) {
+  std::array<int, 4> shape = default_shape(precision, a.records != nullptr);
   const bool explicit_block = o->block_threads && o->blocks_per_sm;
-  *out = make_shape(explicit_block ? int(o->block_threads) : kDefaultThreads,
-                    explicit_block ? int(o->blocks_per_sm) : kDefaultBlocksPerSm,
-                    o->tracks_per_warp ? int(o->tracks_per_warp) : kDefaultTracksPerWarp, ctx->sm_count);
-  if (explicit_block || o->tracks_per_warp || !(o->flags & TKF_FIT_AUTOTUNE) || a.records) return cudaSuccess;
+  if (explicit_block) {
+    shape[0] = int(o->block_threads);
+    shape[1] = int(o->blocks_per_sm);
+    shape[3] = 255;  // an explicit block shape runs the full register file unless told otherwise
+  }
+  if (o->tracks_per_warp) shape[2] = int(o->tracks_per_warp);
+  if (o->max_registers) shape[3] = int(o->max_registers);
+  *out = make_shape(shape, ctx->sm_count);
+  const bool any_explicit = explicit_block || o->tracks_per_warp || o->max_registers;
+  if (any_explicit || !(o->flags & TKF_FIT_AUTOTUNE) || a.records) return cudaSuccess;
   const std::string key = tune_key(a, f, precision, ctx->sm_count);
   auto it = ctx->tuned.find(key);
   if (it != ctx->tuned.end()) {
@@ -208,13 +236,17 @@ cudaError_t resolve_shape(tkf_context ctx, const FitArgs& a, const FieldDev& f, 
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaError_t e = cudaStreamIsCapturing(stream, &cs);
   if (e != cudaSuccess || cs != cudaStreamCaptureStatusNone) return e;
-  std::array<int, 3> best;
+  std::array<int, 4> best;
   e = tune(ctx, a, f, precision, ws, stream, &best);
   if (e != cudaSuccess) return e;
   ctx->tuned[key] = best;
   save_cache(ctx);
   *out = make_shape(best, ctx->sm_count);
   return cudaSuccess;
+}
+
+LaunchShape default_launch_shape(int precision, bool record, int sm_count) {
+  return make_shape(default_shape(precision, record), sm_count);
 }
 
 cudaError_t launch_with_policy(tkf_context ctx, const FitArgs& a, const FieldDev& f, int precision,

@@ -14,9 +14,14 @@ import synth
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(32, 8, 0), (64, 4, 0), (128, 2, 0), (256, 1, 0), (64, 2, 0), (128, 1, 0), (256, 3, 0),
-          (128, 2, 16), (64, 4, 8), (32, 8, 4), (0, 0, 1), (0, 0, 7)]
-CANDIDATES = {(t, b, w) for t, b in [(32, 8), (64, 4), (128, 2), (256, 1), (64, 2), (128, 1)] for w in (32, 16, 8, 4)}
+# (threads, blocks per SM, tracks per warp, registers); 0 = default
+SHAPES = [(32, 8, 0, 0), (64, 4, 0, 0), (128, 2, 0, 0), (256, 1, 0, 0), (64, 2, 0, 0), (128, 1, 0, 0), (256, 3, 0, 0),
+          (128, 2, 16, 0), (64, 4, 8, 0), (32, 8, 4, 0), (0, 0, 1, 0), (0, 0, 7, 0),
+          (128, 4, 0, 128), (32, 16, 0, 128), (128, 8, 0, 64), (64, 16, 5, 64), (0, 0, 0, 64), (0, 0, 0, 255)]
+SHAPES_255 = [(t, b, w) for t, b in [(32, 8), (64, 4), (128, 2), (256, 1), (64, 2), (128, 1)] for w in (32, 16, 8, 4)]
+CANDIDATES = ({(t, b, w, 255) for t, b, w in SHAPES_255}
+              | {(t, b, w, r) for t, b, r in [(128, 4, 128), (64, 8, 128), (32, 16, 128), (128, 8, 64), (64, 16, 64),
+                                              (32, 32, 64)] for w in (32, 16, 8, 4)})
 
 
 @pytest.fixture(scope="module")
@@ -55,9 +60,11 @@ def _run(ctx, geo, fld, b, stream=None, **kw):
 def test_every_block_shape_gives_identical_results(setup, precision):
     ctx, geo, fld, b, _ = setup
     ref = _run(ctx, geo, fld, b, precision=precision)
-    for t, bps, tpw in SHAPES:
-        _same(_run(ctx, geo, fld, b, precision=precision, block_threads=t, blocks_per_sm=bps, tracks_per_warp=tpw),
-              ref)
+    for t, bps, tpw, regs in SHAPES:
+        if precision == tkf.FP64 and regs not in (0, 255):
+            continue
+        _same(_run(ctx, geo, fld, b, precision=precision, block_threads=t, blocks_per_sm=bps, tracks_per_warp=tpw,
+                   max_registers=regs), ref)
 
 
 def test_autotune_picks_a_candidate_and_writes_the_cache(setup, tmp_path, monkeypatch):
@@ -78,7 +85,7 @@ def test_autotune_picks_a_candidate_and_writes_the_cache(setup, tmp_path, monkey
     _same(_run(ctx, geo, fld, b, precision=tkf.MIXED, autotune=True), ref)
     assert cache.stat().st_mtime_ns == before
     # a new context reads the file: with a planted entry it tunes nothing for that class
-    cache.write_text(json.dumps({key: [64, 4, 8]}))
+    cache.write_text(json.dumps({key: [64, 8, 8, 128]}))
     before = cache.stat().st_mtime_ns
     ctx2 = tkf.Context(0)
     geo2, fld2 = _handles(ctx2, w)
@@ -88,7 +95,7 @@ def test_autotune_picks_a_candidate_and_writes_the_cache(setup, tmp_path, monkey
     _run(ctx2, geo2, fld2, b, precision=tkf.FP64, autotune=True)
     entries = json.loads(cache.read_text())
     assert set(entries) == {key, key.replace("mixed.", "fp64.", 1)}
-    assert entries[key] == [64, 4, 8]
+    assert entries[key] == [64, 8, 8, 128]
 
 
 def test_graph_replay_matches_direct_launches_and_reads_current_inputs(setup):
@@ -150,7 +157,9 @@ def test_graph_and_autotune_with_learned_proposals(setup):
 
 @pytest.mark.parametrize("kw", [dict(block_threads=96, blocks_per_sm=1), dict(block_threads=128, blocks_per_sm=0),
                                 dict(block_threads=0, blocks_per_sm=2), dict(block_threads=512, blocks_per_sm=1),
-                                dict(block_threads=64, blocks_per_sm=33), dict(tracks_per_warp=33)])
+                                dict(block_threads=64, blocks_per_sm=33), dict(tracks_per_warp=33),
+                                dict(max_registers=100, precision=tkf.MIXED), dict(max_registers=64),
+                                dict(max_registers=128, precision=tkf.MIXED, block_threads=256, blocks_per_sm=1)])
 def test_bad_block_shapes_are_rejected(setup, kw):
     ctx, geo, fld, b, _ = setup
     with pytest.raises(tkf.TkfError, match="block shape"):
