@@ -54,9 +54,11 @@ FLOPS_MAP = {
 
 
 # DRAM bytes per track of the fit kernel (dram__bytes_read.sum + dram__bytes_write.sum of one
-# ncu capture of a 5-event batch, 81,077 tracks, divided by its tracks; traffic grows with the
-# tracks of a launch). Keyed by (workload, variant); a kernel change voids the entry.
-TRAFFIC_PER_TRACK = {("barrel", "mixed_learned"): (77.133568e6 + 9.316864e6) / 81077}
+# ncu capture, divided by the capture's tracks; traffic grows with the tracks of a launch).
+# Keyed by (workload, variant, register cap of the launched kernel); a kernel change voids the
+# entry. Barrel, learned start, 64 registers: 20-event batch, 279,450 tracks, 128 x 8 blocks.
+TRAFFIC_PER_TRACK = {("barrel", "mixed_learned", 64): (5.721680e9 + 5.006209e9) / 279450}
+TRAFFIC_CAPTURE = {("barrel", "mixed_learned", 64): "ncu capture of 279,450 tracks (20 events), scaled by tracks"}
 
 
 def parse():
@@ -73,7 +75,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch directly instead of replaying a CUDA graph")
-    ap.add_argument("--no-autotune", action="store_true", help="fixed 128 x 2 block shape instead of the tuned one")
+    ap.add_argument("--no-autotune", action="store_true", help="the default launch shape instead of the tuned one")
+    ap.add_argument("--shape", default=None,
+                    help="fixed launch shape 'threads,blocks_per_sm,tracks_per_warp,registers' for every variant "
+                         "(registers 128 or 64 apply to the mixed variants; FP64 keeps 255)")
     ap.add_argument("--sweep", action="store_true",
                     help="throughput sweep 1e3..1e7 tracks per launch in the solenoid map (one JSON line per point)")
     return ap.parse_args()
@@ -425,7 +430,11 @@ def main():
              if host.nbytes() < 2 * L2_BYTES else None)
     for variant in variants:
         opts = tkf.Options(precision=tkf.FP64 if variant == "fp64" else tkf.MIXED, mass=w.mass,
-                           graph=not args.no_graph, autotune=not args.no_autotune)
+                           graph=not args.no_graph, autotune=not args.no_autotune and args.shape is None)
+        if args.shape:
+            th, bps, tpw, regs = (int(x) for x in args.shape.split(","))
+            opts.block_threads, opts.blocks_per_sm, opts.tracks_per_warp = th, bps, tpw
+            opts.max_registers = 255 if variant == "fp64" else regs
         if variant.endswith("learned"):
             opts.step_mode, opts.mlp = tkf.STEP_LEARNED, proposer
         out = tkf.alloc_outputs(n_tracks, dev.offsets.device, steps=True)
@@ -478,8 +487,10 @@ def main():
         kernel_ms = statistics.mean(kms)
         ms_max = max_over_ranks(ms, dist, f"cuda:{local}")
         results[variant] = {"ms": ms, "ms_max": ms_max, "kernel_ms": kernel_ms, "clocks": clk.summary(), "opts": opts,
-                            "shape": tuned_shape(tune_file, variant, n_tracks, "grid" if args.workload == "map" else "uz",
-                                                 args.no_autotune),
+                            "shape": ([opts.block_threads, opts.blocks_per_sm, opts.tracks_per_warp, opts.max_registers]
+                                      if args.shape else
+                                      tuned_shape(tune_file, variant, n_tracks, "grid" if args.workload == "map" else "uz",
+                                                  args.no_autotune)),
                             "attempts": attempts, "rejected": rejected, "status_ok": float(np.mean(status == 0)),
                             "pulls": pull_stats(out, t)}
     head = variants[-1]
@@ -520,14 +531,16 @@ def main():
     peak = fp64_peak_tflops(None)
     # the fit kernel's own duration, from the events the library records around it
     hv = results[head]
+    head_shape = hv["shape"] or [None] * 4
+    traffic_key = (args.workload, head, head_shape[3])
     achieved = hv["flops"] / (hv["kernel_ms"] * 1e-3) / 1e12
     roof = {"bound": "alu", "kernel": f"fit_persistent_kernel<{head}>", "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": (TRAFFIC_PER_TRACK[(args.workload, head)] * n_tracks
-                        if (args.workload, head) in TRAFFIC_PER_TRACK else None),
-            "traffic_note": "DRAM bytes per launch, scaled by tracks from an ncu capture of 81,077 tracks; "
-                            "algorithmic bytes (inputs + outputs) per launch: "
-                            f"{host.nbytes() + n_tracks * (5 * 8 + 15 * 8 + 8 + 4 + 4 + 8)}",
+            "traffic": (TRAFFIC_PER_TRACK[traffic_key] * n_tracks if traffic_key in TRAFFIC_PER_TRACK else None),
+            "traffic_note": (TRAFFIC_CAPTURE.get(traffic_key, "no capture for this kernel variant") +
+                             "; algorithmic bytes (inputs + outputs) per launch: "
+                             f"{host.nbytes() + n_tracks * (5 * 8 + 15 * 8 + 8 + 4 + 4 + 8)}; above them: local-memory "
+                             "spill traffic of the register-capped kernel"),
             "fp64_flop_per_launch": hv["flops"],
             "note": "FP64 CUDA-core pipe (the bound of both variants); peak derived from "
                     "152 SMs x 4 flop/clk x 2070 MHz; 1.20 TFLOP/s measured by an FMA probe"}
@@ -556,7 +569,7 @@ def main():
         # per step: key, scan and scatter kernels of the ordering, the proposal pre-pass
         # (learned), the persistent fit (plus one memset node)
         "gpu_launches": (5 if head.endswith("learned") else 4) * args.steps,
-        "launch_policy": {"cuda_graph": not args.no_graph, "autotune": not args.no_autotune,
+        "launch_policy": {"cuda_graph": not args.no_graph, "autotune": not args.no_autotune and args.shape is None,
                           "launch_shape": {k: v["shape"] for k, v in results.items()}},
         "roofline": roof,
         "clocks": clocks,

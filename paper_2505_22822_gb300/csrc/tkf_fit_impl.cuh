@@ -686,8 +686,37 @@ __device__ __forceinline__ void small_sincos_m1(double x, double& s, double& cm1
 // For k >= 1 the absolute angles are never output, so the filtered direction is carried as
 // (sin phi, cos phi, sin theta, cos theta): the predicted values come from the propagated
 // direction and the update's increments are applied by the angle-addition identities.
-template <bool kMixed, int kMode, class F>
-__device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
+// Smoother state of one track (P = G_k C_k|k, the smoothed sums E and dl): 45 doubles that
+// are read and written once per measurement. kPlace 0 keeps them in registers (spilled to
+// local memory when the register cap is low); 1 puts P, and 2 all of them, in this thread's
+// slot of shared memory (an odd number of doubles a slot, so a warp's accesses hit distinct
+// bank pairs), which frees registers for a register-capped kernel.
+template <int kPlace>
+struct SmootherStore {
+  double P_[25], E_[15], dl_[5];
+  __device__ __forceinline__ double& P(int r, int c) { return P_[r * 5 + c]; }
+  __device__ __forceinline__ double& E(int j) { return E_[j]; }
+  __device__ __forceinline__ double& dl(int j) { return dl_[j]; }
+};
+template <>
+struct SmootherStore<1> {
+  double* s;  // 25 doubles
+  double E_[15], dl_[5];
+  __device__ __forceinline__ double& P(int r, int c) { return s[r * 5 + c]; }
+  __device__ __forceinline__ double& E(int j) { return E_[j]; }
+  __device__ __forceinline__ double& dl(int j) { return dl_[j]; }
+};
+template <>
+struct SmootherStore<2> {
+  double* s;  // 45 doubles
+  __device__ __forceinline__ double& P(int r, int c) { return s[r * 5 + c]; }
+  __device__ __forceinline__ double& E(int j) { return s[25 + j]; }
+  __device__ __forceinline__ double& dl(int j) { return s[40 + j]; }
+};
+__host__ __device__ constexpr int state_doubles(int place) { return place == 0 ? 0 : (place == 1 ? 25 : 45); }
+
+template <bool kMixed, int kMode, int kPlace, class F>
+__device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i, SmootherStore<kPlace> st) {
   const uint32_t n = a.n_tracks;
   const uint32_t b0 = a.offsets[i], b1 = a.offsets[i + 1];
   double p[5], C[15];
@@ -696,7 +725,6 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
   uint32_t status = 0, attempts = 0, rejected = 0;
   double chi2 = 0.0;
   int N = 0;
-  double dl[5], E[15];
   const double nan = __longlong_as_double(0x7ff8000000000000LL);
 
   const bool bad_offsets = b1 < b0 || b1 > a.n_meas;
@@ -723,7 +751,6 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
     if (!fin) status = TKF_TRACK_NON_FINITE;
   }
 
-  double P[5][5];                // G_k C_k|k (smoother recursion)
   Surf sp;                       // surface of the previous measurement
   double sph = 0.0, cph = 1.0, sth = 1.0, cth = 0.0;  // filtered direction at sp
   // learned mode: the step-size control starts from the network's proposal for this track
@@ -938,12 +965,12 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
         for (int c0 = 0; c0 < 4; ++c0) {
           double acc = 0.0;
 #pragma unroll
-          for (int q = 0; q < 5; ++q) acc += P[r0][q] * J[c0][q];
+          for (int q = 0; q < 5; ++q) acc += st.P(r0, q) * J[c0][q];
           row[c0] = acc;
         }
-        row[4] = P[r0][4];
+        row[4] = st.P(r0, 4);
 #pragma unroll
-        for (int c0 = 0; c0 < 5; ++c0) P[r0][c0] = row[c0];
+        for (int c0 = 0; c0 < 5; ++c0) st.P(r0, c0) = row[c0];
       }
     }
     // ---- gain-matrix update with H = [I2 0]; Joseph form (paper Sec. 2; Fruhwirth 1987)
@@ -997,13 +1024,13 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
       sincos(p[3], &sth, &cth);
       // p_0|0 and C_0|0 start the smoothed sums; P_0 = C_0|0
 #pragma unroll
-      for (int j = 0; j < 5; ++j) dl[j] = p[j];
+      for (int j = 0; j < 5; ++j) st.dl(j) = p[j];
 #pragma unroll
-      for (int j = 0; j < 15; ++j) E[j] = C[j];
+      for (int j = 0; j < 15; ++j) st.E(j) = C[j];
 #pragma unroll
       for (int r_ = 0; r_ < 5; ++r_)
 #pragma unroll
-        for (int c_ = 0; c_ < 5; ++c_) P[r_][c_] = C[S(r_, c_)];
+        for (int c_ = 0; c_ < 5; ++c_) st.P(r_, c_) = C[S(r_, c_)];
     } else {
       // filtered direction: predicted angles plus the update's increments p[2], p[3]
       if constexpr (!kMixed) {
@@ -1032,31 +1059,31 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
       double W[5][2];
 #pragma unroll
       for (int j = 0; j < 5; ++j) {
-        W[j][0] = P[j][0] * Si00 + P[j][1] * Si01;
-        W[j][1] = P[j][0] * Si01 + P[j][1] * Si11;
-        dl[j] += W[j][0] * r0 + W[j][1] * r1;
+        W[j][0] = st.P(j, 0) * Si00 + st.P(j, 1) * Si01;
+        W[j][1] = st.P(j, 0) * Si01 + st.P(j, 1) * Si11;
+        st.dl(j) += W[j][0] * r0 + W[j][1] * r1;
       }
 #pragma unroll
       for (int r_ = 0; r_ < 5; ++r_)
 #pragma unroll
-        for (int c_ = r_; c_ < 5; ++c_) E[S(r_, c_)] -= W[r_][0] * P[c_][0] + W[r_][1] * P[c_][1];
+        for (int c_ = r_; c_ < 5; ++c_) st.E(S(r_, c_)) -= W[r_][0] * st.P(c_, 0) + W[r_][1] * st.P(c_, 1);
 #pragma unroll
       for (int r_ = 0; r_ < 5; ++r_) {
-        const double R0 = P[r_][0], R1 = P[r_][1];
+        const double R0 = st.P(r_, 0), R1 = st.P(r_, 1);
 #pragma unroll
-        for (int c_ = 0; c_ < 5; ++c_) P[r_][c_] -= R0 * K[c_][0] + R1 * K[c_][1];
+        for (int c_ = 0; c_ < 5; ++c_) st.P(r_, c_) -= R0 * K[c_][0] + R1 * K[c_][1];
       }
     }
     sp = s;
   }
 
   if (!(status & kFatal)) {
-    if (dl[2] > kPi) dl[2] -= 2.0 * kPi;
-    if (dl[2] <= -kPi) dl[2] += 2.0 * kPi;
+    if (st.dl(2) > kPi) st.dl(2) -= 2.0 * kPi;
+    if (st.dl(2) <= -kPi) st.dl(2) += 2.0 * kPi;
     // positive definiteness of the smoothed covariance: all LDL^T pivots > 0
     double L[15];
 #pragma unroll
-    for (int j = 0; j < 15; ++j) L[j] = E[j];
+    for (int j = 0; j < 15; ++j) L[j] = st.E(j);
     bool spd = true;
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
@@ -1073,23 +1100,23 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
     if (!spd) status |= TKF_TRACK_SMOOTHER_NOT_SPD;
     bool fin = isfinite(chi2);
 #pragma unroll
-    for (int j = 0; j < 5; ++j) fin = fin && isfinite(dl[j]);
+    for (int j = 0; j < 5; ++j) fin = fin && isfinite(st.dl(j));
 #pragma unroll
-    for (int j = 0; j < 15; ++j) fin = fin && isfinite(E[j]);
+    for (int j = 0; j < 15; ++j) fin = fin && isfinite(st.E(j));
     if (!fin) status |= TKF_TRACK_NON_FINITE;
   }
   if (status & kFatal) {
 #pragma unroll
-    for (int j = 0; j < 5; ++j) dl[j] = nan;
+    for (int j = 0; j < 5; ++j) st.dl(j) = nan;
 #pragma unroll
-    for (int j = 0; j < 15; ++j) E[j] = nan;
+    for (int j = 0; j < 15; ++j) st.E(j) = nan;
     chi2 = nan;
   }
   if (N < 3 && !bad_offsets) status |= TKF_TRACK_TOO_FEW_HITS;
 #pragma unroll
-  for (int j = 0; j < 5; ++j) a.par[size_t(j) * n + i] = dl[j];
+  for (int j = 0; j < 5; ++j) a.par[size_t(j) * n + i] = st.dl(j);
 #pragma unroll
-  for (int j = 0; j < 15; ++j) a.cov[size_t(j) * n + i] = E[j];
+  for (int j = 0; j < 15; ++j) a.cov[size_t(j) * n + i] = st.E(j);
   a.chi2[i] = chi2;
   a.ndf[i] = 2 * N;
   a.status[i] = status;
@@ -1104,13 +1131,23 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i) {
 // over more warps and schedulers. kRegs caps the registers a thread (255, 128 or 64): below
 // 255 part of the per-track state lives in local memory (L1), and an SM holds 16 or 32 warps
 // instead of 8, which hides more of the latency between the FP64 and FP32 phases.
-constexpr int reg_block_threads(int regs) { return regs >= 255 ? 256 : 128; }
-constexpr int reg_min_blocks(int regs) { return regs >= 255 ? 1 : 65536 / (regs * 128); }
+__host__ __device__ constexpr int reg_block_threads(int regs) { return regs >= 255 ? 256 : 128; }
+__host__ __device__ constexpr int reg_min_blocks(int regs) { return regs >= 255 ? 1 : 65536 / (regs * 128); }
+
+// Where the smoother state lives per register cap (measured): 255 registers hold it; at 128 the
+// whole state goes to shared memory (184 KB an SM at 16 warps; spills fall from 1.2 to 0.4 KB a
+// thread, launch -3 %); at 64 registers it stays with the spilled state (shared memory for 32
+// warps would take the L1 capacity those spills need: launch +6 %).
+__host__ __device__ constexpr int reg_state_place(int regs) { return regs == 128 ? 2 : 0; }
 
 template <bool kMixed, int kMode, int kRegs, class F>
 __global__ void __launch_bounds__(reg_block_threads(kRegs), reg_min_blocks(kRegs))
     fit_persistent_kernel(FitArgs a, F fld, const uint32_t* __restrict__ perm, uint32_t* __restrict__ counter,
                           uint32_t tpw) {
+  constexpr int kPlace = reg_state_place(kRegs);
+  extern __shared__ double smem_state[];
+  SmootherStore<kPlace> st{};
+  if constexpr (kPlace != 0) st.s = smem_state + threadIdx.x * state_doubles(kPlace);
   const uint32_t lane = threadIdx.x & 31u;
   for (;;) {
     uint32_t base = 0;
@@ -1118,7 +1155,7 @@ __global__ void __launch_bounds__(reg_block_threads(kRegs), reg_min_blocks(kRegs
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= a.n_tracks) break;
     const uint32_t j = base + lane;
-    if (lane < tpw && j < a.n_tracks) fit_track<kMixed, kMode>(a, fld, perm[j]);
+    if (lane < tpw && j < a.n_tracks) fit_track<kMixed, kMode>(a, fld, perm[j], st);
   }
 }
 
@@ -1432,8 +1469,9 @@ template <bool kMixed, int kMode, int kRegs, class F>
 cudaError_t launch_persistent(const FitArgs& a, const F& fld, const uint32_t* perm, uint32_t* counter,
                               LaunchShape shape, cudaStream_t stream) {
   if (shape.threads > reg_block_threads(kRegs)) return cudaErrorInvalidConfiguration;
+  const size_t smem = size_t(shape.threads) * state_doubles(reg_state_place(kRegs)) * sizeof(double);
   fit_persistent_kernel<kMixed, kMode, kRegs>
-      <<<shape.blocks, shape.threads, 0, stream>>>(a, fld, perm, counter, uint32_t(shape.tracks_per_warp));
+      <<<shape.blocks, shape.threads, smem, stream>>>(a, fld, perm, counter, uint32_t(shape.tracks_per_warp));
   return cudaGetLastError();
 }
 
