@@ -482,8 +482,8 @@ def fit(ctx: Context, geo: Geometry, field: Field, batch: Batch, opts: Options |
 def fit_host(ctx: Context, geo: Geometry, field: Field, batch: Batch, opts: Options | None = None,
              out: Result | None = None, stream=None, steps: bool = True) -> Result:
     """Fits a batch of host arrays (numpy or pinned CPU tensors) through tkf_fit_host:
-    host-to-device copies, the fit and device-to-host copies on one stream; returns when the
-    results are in the host buffers."""
+    host-to-device copies, the fit and device-to-host copies, pipelined in chunks for large
+    batches (the copies overlap the fits); returns when the results are in the host buffers."""
     n = batch.n_tracks
     if out is None:
         out = Result(np.empty((5, n)), np.empty((15, n)), np.empty(n), np.empty(n, np.int32),

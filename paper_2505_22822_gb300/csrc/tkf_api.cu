@@ -44,6 +44,11 @@ struct DeviceGuard {
 
 bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
 
+// Host-buffer entry point: the batch is cut into at most kHostChunksMax chunks of at least
+// kHostChunkMinTracks tracks, whose copies overlap the fits of their neighbours.
+constexpr int kHostChunksMax = 6;
+constexpr size_t kHostChunkMinTracks = 65536;
+
 }  // namespace
 
 extern "C" {
@@ -80,9 +85,16 @@ tkf_status tkf_context_create(int device, tkf_context* out) {
 
 void tkf_context_destroy(tkf_context ctx) {
   if (!ctx) return;
-  if (ctx->stage || ctx->ws || ctx->train_ws || ctx->graph_exec) {
+  if (ctx->stage || ctx->ws || ctx->train_ws || ctx->graph_exec || ctx->h2d_stream) {
     DeviceGuard g(ctx->device);
     tkf::release_graph(ctx);
+    for (int c = 0; c < 8; ++c) {
+      if (ctx->chunk_in[c]) cudaEventDestroy(ctx->chunk_in[c]);
+      if (ctx->chunk_fit[c]) cudaEventDestroy(ctx->chunk_fit[c]);
+    }
+    if (ctx->h2d_stream) cudaStreamDestroy(ctx->h2d_stream);
+    if (ctx->d2h_stream) cudaStreamDestroy(ctx->d2h_stream);
+    if (ctx->fit2_stream) cudaStreamDestroy(ctx->fit2_stream);
     if (ctx->stage) cudaFree(ctx->stage);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->train_ws) cudaFree(ctx->train_ws);
@@ -350,6 +362,7 @@ static tkf::FitArgs make_args(tkf_geometry geo, const tkf_fit_options* o, const 
                               const tkf_fit_outputs* out) {
   tkf::FitArgs a{};
   a.n_tracks = in->n_tracks;
+  a.stride = in->n_tracks;
   a.n_meas = in->n_meas;
   a.offsets = in->offsets;
   a.loc0 = in->loc0;
@@ -390,36 +403,41 @@ static tkf::FitArgs make_args(tkf_geometry geo, const tkf_fit_options* o, const 
   return a;
 }
 
+// Enqueues the fit of `a` (device pointers) on `stream`: grows the workspace if needed, picks
+// the launch shape, launches directly or through the graph cache.
+static tkf_status fit_enqueue(tkf_context ctx, tkf_field field, const tkf_fit_options* o, const tkf::FitArgs& a,
+                              cudaStream_t st, bool allow_graph, const char* fn) {
+  const bool learned = o->step_mode == TKF_STEP_LEARNED;
+  const size_t need = tkf::workspace_bytes(a.n_tracks, learned);
+  if (need > ctx->ws_bytes) {
+    // the old workspace may still be in use by earlier work on this context's stream
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, (std::string(fn) + ": stream synchronize").c_str());
+    if (ctx->ws) cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+    e = cudaMalloc(&ctx->ws, need);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, (std::string(fn) + ": workspace cudaMalloc").c_str());
+    ctx->ws_bytes = need;
+  }
+  tkf::Workspace ws = tkf::carve_workspace(ctx->ws, a.n_tracks, learned);
+  tkf::LaunchShape shape;
+  cudaError_t e = tkf::resolve_shape(ctx, a, field->f, o->precision, ws, o, st, &shape);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, (std::string(fn) + ": autotune").c_str());
+  const cudaEvent_t* timing = reinterpret_cast<const cudaEvent_t*>(o->kernel_events);
+  e = tkf::launch_with_policy(ctx, a, field->f, o->precision, ws, shape,
+                              allow_graph && (o->flags & TKF_FIT_GRAPH) != 0, st, timing);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, (std::string(fn) + ": launch").c_str());
+  return TKF_OK;
+}
+
 tkf_status tkf_fit(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf_fit_options* o,
                    const tkf_fit_inputs* in, const tkf_fit_outputs* out, void* stream) {
   tkf_status s = check_common(ctx, geo, field, o, in, out, "tkf_fit");
   if (s != TKF_OK || in->n_tracks == 0) return s;
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(ctx, TKF_ERR_DEVICE, "tkf_fit: cudaSetDevice failed");
-  tkf::FitArgs a = make_args(geo, o, in, out);
-  const bool learned = o->step_mode == TKF_STEP_LEARNED;
-  const size_t need = tkf::workspace_bytes(in->n_tracks, learned);
-  if (need > ctx->ws_bytes) {
-    // the old workspace may still be in use by earlier work on this context's stream
-    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit: stream synchronize");
-    if (ctx->ws) cudaFree(ctx->ws);
-    ctx->ws = nullptr;
-    ctx->ws_bytes = 0;
-    e = cudaMalloc(&ctx->ws, need);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit: workspace cudaMalloc");
-    ctx->ws_bytes = need;
-  }
-  tkf::Workspace ws = tkf::carve_workspace(ctx->ws, in->n_tracks, learned);
-  const cudaStream_t st = static_cast<cudaStream_t>(stream);
-  tkf::LaunchShape shape;
-  cudaError_t e = tkf::resolve_shape(ctx, a, field->f, o->precision, ws, o, st, &shape);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit: autotune");
-  const cudaEvent_t* timing = reinterpret_cast<const cudaEvent_t*>(o->kernel_events);
-  e = tkf::launch_with_policy(ctx, a, field->f, o->precision, ws, shape, (o->flags & TKF_FIT_GRAPH) != 0, st,
-                              timing);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit: launch");
-  return TKF_OK;
+  return fit_enqueue(ctx, field, o, make_args(geo, o, in, out), static_cast<cudaStream_t>(stream), true, "tkf_fit");
 }
 
 tkf_status tkf_propose_start(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf_fit_options* o,
@@ -481,33 +499,124 @@ tkf_status tkf_fit_host(tkf_context ctx, tkf_geometry geo, tkf_field field, cons
   dout.ndf = reinterpret_cast<int32_t*>(take(b_n4));
   dout.status = reinterpret_cast<uint32_t*>(take(b_n4));
   dout.steps = hout->steps ? reinterpret_cast<uint32_t*>(take(b_steps)) : nullptr;
+  // Pipeline over chunks of tracks: the copy-in of chunk c + 1 (h2d stream) and the copy-out of
+  // chunk c - 1 (d2h stream) overlap the fit of chunk c (the caller's stream). Each chunk is the
+  // tracks [t0, t1) with their measurements [offsets[t0], offsets[t1]), copied to the same
+  // positions of full-size staging arrays, so offsets stay absolute; seeds and outputs are SoA
+  // rows of the full batch, so a chunk's fit runs with the batch's row stride.
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  struct Cp {
-    void* dst;
-    const void* src;
-    size_t bytes;
-  };
-  const Cp h2d[] = {{(void*)din.offsets, hin->offsets, (n + 1) * 4}, {(void*)din.loc0, hin->loc0, m * 8},
-                    {(void*)din.loc1, hin->loc1, m * 8},           {(void*)din.v00, hin->v00, m * 8},
-                    {(void*)din.v01, hin->v01, m * 8},             {(void*)din.v11, hin->v11, m * 8},
-                    {(void*)din.sid, hin->sid, m * 4},             {(void*)din.seed_par, hin->seed_par, 5 * n * 8},
-                    {(void*)din.seed_cov, hin->seed_cov, 15 * n * 8}};
-  for (const Cp& c : h2d) {
-    if (c.bytes == 0) continue;
-    cudaError_t e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_host: host-to-device copy");
+  cudaError_t e = cudaSuccess;
+  if (!ctx->h2d_stream) {
+    e = cudaStreamCreateWithFlags(&ctx->h2d_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->d2h_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->fit2_stream, cudaStreamNonBlocking);
+    for (int c = 0; c < kHostChunksMax && e == cudaSuccess; ++c) {
+      e = cudaEventCreateWithFlags(&ctx->chunk_in[c], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->chunk_fit[c], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_host: stream or event creation");
   }
-  s = tkf_fit(ctx, geo, field, o, &din, &dout, stream);
-  if (s != TKF_OK) return s;
-  const Cp d2h[] = {{hout->par, dout.par, 5 * n * 8},   {hout->cov, dout.cov, 15 * n * 8},
-                    {hout->chi2, dout.chi2, n * 8},     {hout->ndf, dout.ndf, n * 4},
-                    {hout->status, dout.status, n * 4}, {hout->steps, dout.steps, hout->steps ? 2 * n * 4 : 0}};
-  for (const Cp& c : d2h) {
-    if (c.bytes == 0) continue;
-    cudaError_t e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost, st);
+  uint32_t chunks = n >= size_t(kHostChunkMinTracks) * 2
+                        ? uint32_t(kHostChunksMax < n / kHostChunkMinTracks ? kHostChunksMax : n / kHostChunkMinTracks)
+                        : 1u;
+  if (chunks > 1) {
+    // a chunk carries the measurements between its first and last offset: only when the offsets
+    // never decrease does that hold every measurement its tracks can reference
+    bool monotone = true;
+    for (size_t i = 0; i < n; ++i) monotone &= hin->offsets[i + 1] >= hin->offsets[i];
+    if (!monotone) chunks = 1;
+  }
+  tkf::FitArgs full = make_args(geo, o, &din, &dout);
+  const bool learned = o->step_mode == TKF_STEP_LEARNED;
+  // one workspace per chunk (a chunk has at most n / chunks + 1 tracks)
+  const size_t chunk_ws = (tkf::workspace_bytes(uint32_t(n / chunks + 1), learned) + 255) & ~size_t(255);
+  tkf::LaunchShape chunk_shape;
+  if (chunks > 1 && chunks * chunk_ws > ctx->ws_bytes) {
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_host: stream synchronize");
+    if (ctx->ws) cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+    e = cudaMalloc(&ctx->ws, chunks * chunk_ws);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_host: workspace cudaMalloc");
+    ctx->ws_bytes = chunks * chunk_ws;
+  }
+  // the staging buffers may still be read by an earlier call's work on the caller's stream
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_host: stream synchronize");
+  auto h2d = [&](void* dst, const void* src, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->h2d_stream);
+  };
+  auto d2h = [&](void* dst, const void* src, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->d2h_stream);
+  };
+  // `cols` consecutive doubles of each of `rows` rows of a [rows][n] matrix
+  auto h2d_rows = [&](double* dst, const double* src, size_t cols, size_t rows) {
+    if (e == cudaSuccess && cols)
+      e = cudaMemcpy2DAsync(dst, n * 8, src, n * 8, cols * 8, rows, cudaMemcpyHostToDevice, ctx->h2d_stream);
+  };
+  auto d2h_rows = [&](double* dst, const double* src, size_t cols, size_t rows) {
+    if (e == cudaSuccess && cols)
+      e = cudaMemcpy2DAsync(dst, n * 8, src, n * 8, cols * 8, rows, cudaMemcpyDeviceToHost, ctx->d2h_stream);
+  };
+  for (uint32_t c = 0; c < chunks; ++c) {
+    const size_t t0 = n * c / chunks, t1 = n * (c + 1) / chunks, nt = t1 - t0;
+    // one chunk: every measurement; offsets beyond n_meas are the kernel's to flag
+    const size_t m0 = chunks == 1 ? 0 : hin->offsets[t0];
+    const size_t m1 = chunks == 1 ? m : (hin->offsets[t1] <= m ? hin->offsets[t1] : m);
+    const size_t mc = m1 > m0 ? m1 - m0 : 0;
+    h2d(const_cast<uint32_t*>(din.offsets) + t0, hin->offsets + t0, (nt + 1) * 4);
+    h2d(const_cast<double*>(din.loc0) + m0, hin->loc0 + m0, mc * 8);
+    h2d(const_cast<double*>(din.loc1) + m0, hin->loc1 + m0, mc * 8);
+    h2d(const_cast<double*>(din.v00) + m0, hin->v00 + m0, mc * 8);
+    h2d(const_cast<double*>(din.v01) + m0, hin->v01 + m0, mc * 8);
+    h2d(const_cast<double*>(din.v11) + m0, hin->v11 + m0, mc * 8);
+    h2d(const_cast<uint32_t*>(din.sid) + m0, hin->sid + m0, mc * 4);
+    // the chunk's columns of the SoA seed matrices: one strided copy each
+    h2d_rows(const_cast<double*>(din.seed_par) + t0, hin->seed_par + t0, nt, 5);
+    h2d_rows(const_cast<double*>(din.seed_cov) + t0, hin->seed_cov + t0, nt, 15);
+    // chunks alternate between the caller's stream and a second compute stream, each with a
+    // workspace of its own, so that a chunk's fit fills the SMs its predecessor's tail leaves
+    const cudaStream_t cs = (chunks > 1 && (c & 1u)) ? ctx->fit2_stream : st;
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->chunk_in[c], ctx->h2d_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->chunk_in[c], 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_host: host-to-device copy");
+    tkf::FitArgs a = full;
+    a.n_tracks = uint32_t(nt);
+    a.offsets += t0;
+    a.seed_par += t0;
+    a.seed_cov += t0;
+    a.par += t0;
+    a.cov += t0;
+    a.chi2 += t0;
+    a.ndf += t0;
+    a.status += t0;
+    if (a.steps) a.steps += t0;
+    if (chunks == 1) {
+      s = fit_enqueue(ctx, field, o, a, st, true, "tkf_fit_host");
+      if (s != TKF_OK) return s;
+    } else {
+      const tkf::Workspace wsc = tkf::carve_workspace(static_cast<char*>(ctx->ws) + c * chunk_ws, nt, learned);
+      if (c == 0 && (e = tkf::resolve_shape(ctx, a, field->f, o->precision, wsc, o, st, &chunk_shape)) != cudaSuccess)
+        return cuda_fail(ctx, e, "tkf_fit_host: autotune");
+      if ((e = tkf::launch_fit(a, field->f, o->precision, wsc, chunk_shape, cs)) != cudaSuccess)
+        return cuda_fail(ctx, e, "tkf_fit_host: launch");
+    }
+    e = cudaEventRecord(ctx->chunk_fit[c], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->d2h_stream, ctx->chunk_fit[c], 0);
+    d2h_rows(hout->par + t0, dout.par + t0, nt, 5);
+    d2h_rows(hout->cov + t0, dout.cov + t0, nt, 15);
+    d2h(hout->chi2 + t0, dout.chi2 + t0, nt * 8);
+    d2h(hout->ndf + t0, dout.ndf + t0, nt * 4);
+    d2h(hout->status + t0, dout.status + t0, nt * 4);
+    if (hout->steps && e == cudaSuccess && nt)
+      e = cudaMemcpy2DAsync(hout->steps + t0, n * 4, dout.steps + t0, n * 4, nt * 4, 2, cudaMemcpyDeviceToHost,
+                            ctx->d2h_stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_host: device-to-host copy");
   }
-  cudaError_t e = cudaStreamSynchronize(st);
+  e = cudaStreamSynchronize(ctx->d2h_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->fit2_stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_host: stream synchronize");
   return TKF_OK;
 }

@@ -717,7 +717,7 @@ __host__ __device__ constexpr int state_doubles(int place) { return place == 0 ?
 
 template <bool kMixed, int kMode, int kPlace, class F>
 __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i, SmootherStore<kPlace> st) {
-  const uint32_t n = a.n_tracks;
+  const uint32_t n = a.stride;  // SoA row stride of seeds and outputs
   const uint32_t b0 = a.offsets[i], b1 = a.offsets[i + 1];
   double p[5], C[15];
   for (int j = 0; j < 5; ++j) p[j] = a.seed_par[size_t(j) * n + i];
@@ -1321,7 +1321,7 @@ __global__ void __launch_bounds__(kPropTile) propose_start_tc_kernel(FitArgs a, 
         load_surf(a.surf, a.sid[b0], s0);
         load_surf(a.surf, a.sid[b0 + 1], s1);
         float p[5];
-        for (int j = 0; j < 5; ++j) p[j] = float(a.seed_par[size_t(j) * n + i]);
+        for (int j = 0; j < 5; ++j) p[j] = float(a.seed_par[size_t(j) * a.stride + i]);
         float sph, cph, sth, cth;
         sincosf(p[2], &sph, &cph);
         sincosf(p[3], &sth, &cth);

@@ -47,6 +47,7 @@ struct OptionsDev {
 
 struct FitArgs {
   uint32_t n_tracks;
+  uint32_t stride;  // row stride of the SoA seed and output arrays: n_tracks, or a whole batch's for a chunk of it
   uint64_t n_meas;
   const uint32_t* __restrict__ offsets;
   const double* __restrict__ loc0;
@@ -151,6 +152,9 @@ struct tkf_context_s {
   // CUDA graph of the last repeated launch sequence
   cudaGraphExec_t graph_exec = nullptr;
   std::string graph_key, pending_key;
+  // host-buffer entry point: copy streams and events of its chunk pipeline (created on first use)
+  cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr, fit2_stream = nullptr;
+  cudaEvent_t chunk_in[8] = {}, chunk_fit[8] = {};
   // fit workspace (ordering scratch), grown on demand and reused by later calls
   void* ws = nullptr;
   size_t ws_bytes = 0;

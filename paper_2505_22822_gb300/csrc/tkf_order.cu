@@ -16,7 +16,8 @@ constexpr int kKeyBins = kPtBins * kNBins;
 
 __global__ void __launch_bounds__(256) order_keys_kernel(const uint32_t* __restrict__ offsets,
                                                          const double* __restrict__ seed_par, uint32_t n,
-                                                         uint32_t* __restrict__ keys, uint32_t* __restrict__ hist) {
+                                                         uint32_t stride, uint32_t* __restrict__ keys,
+                                                         uint32_t* __restrict__ hist) {
   __shared__ uint32_t h[kKeyBins];
   for (int b = threadIdx.x; b < kKeyBins; b += blockDim.x) h[b] = 0;
   __syncthreads();
@@ -24,8 +25,8 @@ __global__ void __launch_bounds__(256) order_keys_kernel(const uint32_t* __restr
   if (i < n) {
     const uint32_t b0 = offsets[i], b1 = offsets[i + 1];
     const uint32_t nh = b1 >= b0 ? min(b1 - b0, uint32_t(kNBins - 1)) : 0u;
-    const float qop = float(seed_par[size_t(4) * n + i]);
-    const float sth = fabsf(sinf(float(seed_par[size_t(3) * n + i])));
+    const float qop = float(seed_par[size_t(4) * stride + i]);
+    const float sth = fabsf(sinf(float(seed_par[size_t(3) * stride + i])));
     const float pt = (qop != 0.0f) ? sth / fabsf(qop) : 1e30f;
     int pb = (pt > 0.0f) ? int(floorf(log2f(pt))) + 4 : 0;  // octaves from 1/16 GeV
     pb = pb < 0 ? 0 : (pb >= kPtBins ? kPtBins - 1 : pb);
@@ -83,7 +84,7 @@ cudaError_t launch_fit(const FitArgs& a, const FieldDev& f, int precision, const
   cudaError_t e = cudaMemsetAsync(ws.counter, 0, sizeof(uint32_t) * (1 + kKeyBins), stream);
   if (e != cudaSuccess) return e;
   const unsigned g256 = (n + 255) / 256;
-  order_keys_kernel<<<g256, 256, 0, stream>>>(a.offsets, a.seed_par, n, ws.keys, ws.hist);
+  order_keys_kernel<<<g256, 256, 0, stream>>>(a.offsets, a.seed_par, n, a.stride, ws.keys, ws.hist);
   order_scan_kernel<<<1, kKeyBins, 0, stream>>>(ws.hist);
   order_scatter_kernel<<<g256, 256, 0, stream>>>(ws.keys, n, ws.hist, ws.perm);
   e = cudaGetLastError();

@@ -144,6 +144,7 @@ std::string graph_key(const FitArgs& a, const FieldDev& f, int precision, const 
   k.put(shape.tracks_per_warp);
   k.put(shape.regs);
   k.put(a.n_tracks);
+  k.put(a.stride);
   k.put(a.n_meas);
   const void* ptrs[] = {a.offsets, a.loc0,   a.loc1,  a.v00,      a.v01,     a.v11,
                         a.sid,     a.seed_par, a.seed_cov, a.par,   a.cov,     a.chi2,

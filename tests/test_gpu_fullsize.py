@@ -121,3 +121,37 @@ def test_solenoid_map_full_batch(precision):
     pulls = d / sig
     assert np.all(np.abs(pulls.std(0) - 1.0) < 0.02), pulls.std(0)
     assert np.all(np.abs(pulls.mean(0)) < 0.02), pulls.mean(0)
+
+
+def _host_vs_device(ctx, geo, fld, hb, opts):
+    h = tkf.fit_host(ctx, geo, fld, hb, opts)
+    d = tkf.fit(ctx, geo, fld, hb.to("cuda:0"), opts)
+    torch.cuda.synchronize()
+    for k in ("par", "cov", "chi2"):
+        np.testing.assert_array_equal(getattr(h, k), getattr(d, k).cpu().numpy(), err_msg=k)
+    np.testing.assert_array_equal(h.ndf, d.ndf.cpu().numpy())
+    np.testing.assert_array_equal(h.status, d.status.cpu().numpy().view(np.uint32))
+    np.testing.assert_array_equal(h.steps, d.steps.cpu().numpy().view(np.uint32))
+    return h
+
+
+@pytest.mark.parametrize("precision", [tkf.FP64, tkf.MIXED])
+def test_host_entry_point_pipelines_chunks_with_identical_results(barrel, precision):
+    """605,172 tracks through tkf_fit_host: four chunks whose copies overlap the fits, results
+    bit for bit those of the device entry point."""
+    ctx, w, geo, fld, _, _ = barrel
+    t = w.tracks
+    hb = tkf.Batch.from_arrays(t.offsets, t.meas, t.sid, t.seed_par, t.seed_cov)
+    _host_vs_device(ctx, geo, fld, hb, tkf.Options(precision=precision, mass=w.mass))
+
+
+def test_host_entry_point_with_decreasing_offsets_fits_in_one_piece(barrel):
+    """Offsets that decrease somewhere cannot be chunked by measurement ranges: the call copies
+    everything and still matches the device entry point (the decreasing pair flags BAD_INPUT)."""
+    ctx, w, geo, fld, _, _ = barrel
+    sub = w.tracks.subset(np.arange(140_000))
+    offsets = sub.offsets.astype(np.uint32).copy()
+    offsets[70_000] = offsets[70_001] + 3  # track 69,999 ends after track 70,000 starts
+    hb = tkf.Batch.from_arrays(offsets, sub.meas, sub.sid, sub.seed_par, sub.seed_cov)
+    h = _host_vs_device(ctx, geo, fld, hb, tkf.Options(precision=tkf.MIXED, mass=w.mass))
+    assert h.status[70_000] & tkf.TRACK_STATUS["BAD_INPUT"]
