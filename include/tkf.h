@@ -212,6 +212,10 @@ typedef struct tkf_fit_options {
  * change of argument launches directly again. Needs a stream other than the legacy default
  * stream (ignored there and while the caller is itself capturing the stream). */
 #define TKF_FIT_GRAPH 2u
+/* For tests of the failure path of the learned mode's tensor-core pre-pass: the pre-pass
+ * issues no tensor-core work, so its bounded waits for it run out (about 0.1 s); every track
+ * then gets no proposal, starts from h_max and carries TKF_TRACK_PROPOSAL_FALLBACK. */
+#define TKF_FIT_TEST_PROPOSAL_TIMEOUT (1u << 31)
 
 void tkf_fit_options_default(tkf_fit_options* opts);
 

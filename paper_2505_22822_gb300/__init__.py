@@ -33,7 +33,7 @@ NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", 
 
 FP64, MIXED = 0, 1
 STEP_ADAPTIVE, STEP_LEARNED = 0, 1
-FIT_AUTOTUNE, FIT_GRAPH = 1, 2
+FIT_AUTOTUNE, FIT_GRAPH, FIT_TEST_PROPOSAL_TIMEOUT = 1, 2, 1 << 31
 FIELD_UNIFORM, FIELD_RZ_GRID = 0, 1
 
 TRACK_STATUS = {
@@ -330,6 +330,7 @@ class Options:
     record_count: object = None   # CUDA int32 tensor [1], zeroed by the caller
     autotune: bool = False        # time the candidate block shapes on the first call of a class
     graph: bool = False           # capture repeated identical calls into a CUDA graph
+    test_proposal_timeout: bool = False  # test hook: the pre-pass issues no tensor-core work
     block_threads: int = 0        # explicit block shape (both nonzero), else default or tuned
     blocks_per_sm: int = 0
     tracks_per_warp: int = 0      # explicit tracks a warp takes at a time (1..32), else 32 or tuned
@@ -348,7 +349,8 @@ class Options:
             o.records = self.records.data_ptr()
             o.record_capacity = int(self.records.shape[0])
             o.record_count = self.record_count.data_ptr()
-        o.flags = (FIT_AUTOTUNE if self.autotune else 0) | (FIT_GRAPH if self.graph else 0)
+        o.flags = ((FIT_AUTOTUNE if self.autotune else 0) | (FIT_GRAPH if self.graph else 0)
+                   | (FIT_TEST_PROPOSAL_TIMEOUT if self.test_proposal_timeout else 0))
         o.block_threads, o.blocks_per_sm = self.block_threads, self.blocks_per_sm
         o.tracks_per_warp = self.tracks_per_warp
         o.max_registers = self.max_registers

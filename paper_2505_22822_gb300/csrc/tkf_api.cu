@@ -334,7 +334,7 @@ static tkf_status check_common(tkf_context ctx, tkf_geometry geo, tkf_field fiel
       o->max_steps == 0 || !(o->mass > 0) || !isfinite(o->h_max))
     return fail(ctx, TKF_ERR_INVALID_ARG,
                 std::string(fn) + ": options need tol, h_max, h_min, surf_tol, mass > 0, h_min <= h_max, max_steps > 0");
-  if ((o->flags & ~(TKF_FIT_AUTOTUNE | TKF_FIT_GRAPH)) != 0)
+  if ((o->flags & ~(TKF_FIT_AUTOTUNE | TKF_FIT_GRAPH | TKF_FIT_TEST_PROPOSAL_TIMEOUT)) != 0)
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": unknown flag");
   if (!tkf::valid_block_shape(o->block_threads, o->blocks_per_sm, o->tracks_per_warp, o->max_registers, o->precision,
                               o->records != nullptr))
@@ -400,6 +400,7 @@ static tkf::FitArgs make_args(tkf_geometry geo, const tkf_fit_options* o, const 
   a.records = (o->step_mode == TKF_STEP_ADAPTIVE) ? o->records : nullptr;
   a.record_capacity = o->record_capacity;
   a.record_count = o->record_count;
+  a.test_stall_proposals = (o->flags & TKF_FIT_TEST_PROPOSAL_TIMEOUT) != 0;
   return a;
 }
 

@@ -1180,7 +1180,7 @@ inline FieldGrid grid_policy(const FieldDev& f) {
 // groups are 128 bytes apart (leading byte offset) and row groups K/8 * 128 bytes (stride byte
 // offset).
 constexpr int kPropTile = 128;
-constexpr uint32_t kPropWaitLimit = 1u << 20;  // mbarrier polls before a tile gives up
+constexpr uint32_t kPropWaitLimit = 1u << 20;  // mbarrier polls (100 ns apart) before a tile gives up
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -1218,16 +1218,19 @@ __device__ __forceinline__ void tc_commit(uint64_t* mbar) {
                : "memory");
 }
 
+// Waits for the mbarrier phase of the given parity to complete: a non-blocking test every
+// 100 ns, at most kPropWaitLimit times (about 0.1 s); false if it never completed.
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
   for (uint32_t it = 0; it < kPropWaitLimit; ++it) {
     uint32_t done;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done)
         : "r"(smem_addr(mbar)), "r"(parity)
         : "memory");
     if (done) return true;
+    __nanosleep(100);
   }
   return false;
 }
@@ -1370,7 +1373,7 @@ __global__ void __launch_bounds__(kPropTile) propose_start_tc_kernel(FitArgs a, 
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && !a.test_stall_proposals) {
       tc_fence_after();
       tc_mma(tmem, d_a1, d_w1, 0u);
       tc_commit(&sm.mbar);
@@ -1398,7 +1401,7 @@ __global__ void __launch_bounds__(kPropTile) propose_start_tc_kernel(FitArgs a, 
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && !a.test_stall_proposals) {
       tc_fence_after();
 #pragma unroll
       for (int k = 0; k < 4; ++k)

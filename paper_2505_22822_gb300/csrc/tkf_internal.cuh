@@ -73,6 +73,7 @@ struct FitArgs {
   float* __restrict__ records;       // training-record capture, or null
   uint32_t record_capacity;
   uint32_t* __restrict__ record_count;
+  bool test_stall_proposals;  // test of the timeout path: the pre-pass issues no tensor-core work
 };
 
 constexpr int kMlpParams = TKF_MLP_PARAMS;

@@ -153,6 +153,7 @@ std::string graph_key(const FitArgs& a, const FieldDev& f, int precision, const 
   for (const void* p : ptrs) k.put(p);
   k.put(a.n_surf);
   k.put(a.record_capacity);
+  k.put(a.test_stall_proposals);
   const double dm[] = {a.mat.z_over_a, a.mat.i_ev, a.mat.rho, a.mat.hwp_ev, a.mat.log_hwp_over_i, a.mat.bg2_density,
                        a.opt.tol, a.opt.h_max, a.opt.h_min, a.opt.surf_tol, a.opt.mass, f.b[0], f.b[1], f.b[2],
                        f.r0, f.dr, f.z0, f.dz, f.inv_dr, f.inv_dz};

@@ -180,3 +180,25 @@ def test_tensor_core_proposals_match_the_oracle(ctx, trained):
                   (h_gpu[~same] == np.float32(o.h_min)))
     # a spread of proposals, not a constant
     assert np.unique(np.round(np.log(h_gpu[same]) * 32)).size > 10
+
+
+def test_pre_pass_timeout_falls_back_to_the_plain_start(ctx, trained):
+    """Failure path without a GPU fault: with the test flag the pre-pass issues no tensor-core
+    work, so nothing ever arrives on its mbarrier; its bounded waits run out, it frees its tensor
+    memory and returns, and the fit starts every track from h_max with PROPOSAL_FALLBACK, which
+    gives the plain adaptive fit's results. The context stays usable."""
+    fld, _, theta, _ = trained
+    m = tkf.Mlp(ctx, mlp.to_bf16(theta))
+    w = synth.solenoid_muon_workload(2000, seed=34, fld=fld)
+    stalled = _fit(ctx, w, tkf.Options(precision=tkf.MIXED, step_mode=tkf.STEP_LEARNED, mlp=m,
+                                       test_proposal_timeout=True))
+    plain = _fit(ctx, w, tkf.Options(precision=tkf.MIXED))
+    fb = tkf.TRACK_STATUS["PROPOSAL_FALLBACK"]
+    st = stalled.status.cpu().numpy().view(np.uint32)
+    assert np.all(st & fb)
+    np.testing.assert_array_equal(st & ~np.uint32(fb), plain.status.cpu().numpy().view(np.uint32))
+    for k in ("par", "cov", "chi2", "steps"):
+        np.testing.assert_array_equal(getattr(stalled, k).cpu().numpy(), getattr(plain, k).cpu().numpy(), err_msg=k)
+    # the context still works: a normal learned fit afterwards has no fallback
+    again = _fit(ctx, w, tkf.Options(precision=tkf.MIXED, step_mode=tkf.STEP_LEARNED, mlp=m))
+    assert not np.any(again.status.cpu().numpy().view(np.uint32) & fb)
