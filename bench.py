@@ -42,6 +42,8 @@ FLOPS = {
     # mixed: only the FP64 anchors, the Joseph update and the smoother count
     "mixed": (20, 8, 749, 330),
     "mixed_learned": (20, 8, 749, 330),
+    # experimental FP32 covariance algebra: only the anchors and the smoothed sums stay FP64
+    "mixed_fp32": (20, 8, 45, 30),
 }
 # r-z field map: every attempt adds two stage positions and three bilinear lookups (FP64 in
 # the plain path: 32 flops each incl. one square root and one division), every propagated
@@ -50,6 +52,7 @@ FLOPS_MAP = {
     "fp64": (619, 237, 1558, 330),
     "mixed": (20, 8, 749, 330),
     "mixed_learned": (20, 8, 749, 330),
+    "mixed_fp32": (20, 8, 45, 30),
 }
 
 
@@ -67,7 +70,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--variant", default="auto", choices=["auto", "fp64", "mixed", "mixed_learned"])
+    ap.add_argument("--variant", default="auto", choices=["auto", "fp64", "mixed_fp32", "mixed", "mixed_learned"])
     ap.add_argument("--events", type=int, default=50)
     ap.add_argument("--workload", default="barrel", choices=["barrel", "map"],
                     help="barrel: events in the barrel + endcap detector, uniform 2 T; map: 1e5 muons "
@@ -280,8 +283,8 @@ def setup_tune_cache() -> str:
 def tuned_shape(path: str, variant: str, n_tracks: int, field: str, disabled: bool):
     """[threads, blocks per SM, tracks per warp, registers] the autotuner chose for this class."""
     if disabled:
-        return [128, 2, 32, 255] if variant == "fp64" else [128, 4, 32, 128]
-    prec = "fp64" if variant == "fp64" else "mixed"
+        return [128, 2, 32, 255] if variant in ("fp64", "mixed_fp32") else [128, 4, 32, 128]
+    prec = variant if variant in ("fp64", "mixed_fp32") else "mixed"
     mode = "learned" if variant.endswith("learned") else "adaptive"
     prefix = f"{prec}.{mode}.{field}.n{int(n_tracks).bit_length() - 1}."
     try:
@@ -408,7 +411,8 @@ def main():
     fld = tkf.Field.from_desc(ctx, w.field)
     host = tkf.Batch.from_arrays(t.offsets, t.meas, t.sid, t.seed_par, t.seed_cov)
     dev = host.to(f"cuda:{local}")
-    variants = ["fp64", "mixed", "mixed_learned"] if args.variant == "auto" else [args.variant]
+    # the headline is the last: mixed + learned; mixed_fp32 is the experimental FP32 covariance algebra
+    variants = ["fp64", "mixed_fp32", "mixed", "mixed_learned"] if args.variant == "auto" else [args.variant]
     # a side stream: CUDA graphs cannot be captured on the legacy default stream
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -429,12 +433,13 @@ def main():
     flush = (torch.zeros(int(2 * L2_BYTES) // 4, dtype=torch.float32, device=f"cuda:{local}")
              if host.nbytes() < 2 * L2_BYTES else None)
     for variant in variants:
-        opts = tkf.Options(precision=tkf.FP64 if variant == "fp64" else tkf.MIXED, mass=w.mass,
+        opts = tkf.Options(precision={"fp64": tkf.FP64, "mixed_fp32": tkf.MIXED_FP32}.get(variant, tkf.MIXED),
+                           mass=w.mass,
                            graph=not args.no_graph, autotune=not args.no_autotune and args.shape is None)
         if args.shape:
             th, bps, tpw, regs = (int(x) for x in args.shape.split(","))
             opts.block_threads, opts.blocks_per_sm, opts.tracks_per_warp = th, bps, tpw
-            opts.max_registers = 255 if variant == "fp64" else regs
+            opts.max_registers = 255 if variant == "fp64" or (variant == "mixed_fp32" and regs == 64) else regs
         if variant.endswith("learned"):
             opts.step_mode, opts.mlp = tkf.STEP_LEARNED, proposer
         out = tkf.alloc_outputs(n_tracks, dev.offsets.device, steps=True)

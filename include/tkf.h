@@ -143,8 +143,12 @@ void tkf_field_destroy(tkf_field field);
 
 typedef enum tkf_precision {
   TKF_FP64 = 0,  /* every step in FP64 */
-  TKF_MIXED = 1  /* propagation and transport in FP32 around FP64 anchors; update and
+  TKF_MIXED = 1, /* propagation and transport in FP32 around FP64 anchors; update and
                     smoother in FP64 */
+  TKF_MIXED_FP32 = 2 /* experimental, outside the FP64-update policy of TKF_MIXED: the mixed
+                        path with the covariance algebra (Joseph update, smoother, covariance
+                        transport results) in FP32 as well; FP64 is left only for the position
+                        and direction anchors and the smoothed parameters. No record capture. */
 } tkf_precision;
 
 typedef enum tkf_step_mode {

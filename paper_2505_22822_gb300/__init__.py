@@ -25,13 +25,13 @@ _ROOT = os.path.dirname(_HERE)
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "libtkf.so")
 _SOURCES = ["tkf_api.cu", "tkf_order.cu", "tkf_policy.cu", "tkf_fit_fp64.cu", "tkf_fit_mixed.cu",
-            "tkf_fit_mixed_r128.cu", "tkf_fit_mixed_r64.cu", "tkf_mlp.cu"]
+            "tkf_fit_mixed_r128.cu", "tkf_fit_mixed_r64.cu", "tkf_fit_mixed32.cu", "tkf_mlp.cu"]
 _lib = None
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-Xcompiler", "-fPIC"]
 
-FP64, MIXED = 0, 1
+FP64, MIXED, MIXED_FP32 = 0, 1, 2
 STEP_ADAPTIVE, STEP_LEARNED = 0, 1
 FIT_AUTOTUNE, FIT_GRAPH, FIT_TEST_PROPOSAL_TIMEOUT = 1, 2, 1 << 31
 FIELD_UNIFORM, FIELD_RZ_GRID = 0, 1

@@ -319,8 +319,10 @@ static tkf_status check_common(tkf_context ctx, tkf_geometry geo, tkf_field fiel
     return fail(ctx, TKF_ERR_BAD_HANDLE, std::string(fn) + ": geometry or field handle NULL or from another context");
   if (!o || !in || (need_out && !out))
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": NULL options, inputs or outputs");
-  if (!(o->precision == TKF_FP64 || o->precision == TKF_MIXED))
+  if (!(o->precision == TKF_FP64 || o->precision == TKF_MIXED || o->precision == TKF_MIXED_FP32))
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": unknown precision");
+  if (o->precision == TKF_MIXED_FP32 && o->records)
+    return fail(ctx, TKF_ERR_UNSUPPORTED, std::string(fn) + ": record capture runs in TKF_FP64 or TKF_MIXED");
   if (!(o->step_mode == TKF_STEP_ADAPTIVE || o->step_mode == TKF_STEP_LEARNED))
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": unknown step mode");
   if (o->step_mode == TKF_STEP_LEARNED && !o->mlp)

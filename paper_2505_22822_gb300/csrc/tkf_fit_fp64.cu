@@ -5,7 +5,7 @@ namespace tkf {
 
 cudaError_t launch_fit_fp64(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm, uint32_t* counter,
                             LaunchShape shape, cudaStream_t stream) {
-  return launch_fields<false, 255>(a, f, mode, perm, counter, shape, stream);
+  return launch_fields<0, 255>(a, f, mode, perm, counter, shape, stream);
 }
 
 }  // namespace tkf

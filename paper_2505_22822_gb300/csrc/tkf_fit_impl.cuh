@@ -691,15 +691,16 @@ __device__ __forceinline__ void small_sincos_m1(double x, double& s, double& cm1
 // local memory when the register cap is low); 1 puts P, and 2 all of them, in this thread's
 // slot of shared memory (an odd number of doubles a slot, so a warp's accesses hit distinct
 // bank pairs), which frees registers for a register-capped kernel.
-template <int kPlace>
+template <int kPlace, class U>
 struct SmootherStore {
-  double P_[25], E_[15], dl_[5];
-  __device__ __forceinline__ double& P(int r, int c) { return P_[r * 5 + c]; }
-  __device__ __forceinline__ double& E(int j) { return E_[j]; }
+  U P_[25], E_[15];
+  double dl_[5];
+  __device__ __forceinline__ U& P(int r, int c) { return P_[r * 5 + c]; }
+  __device__ __forceinline__ U& E(int j) { return E_[j]; }
   __device__ __forceinline__ double& dl(int j) { return dl_[j]; }
 };
 template <>
-struct SmootherStore<1> {
+struct SmootherStore<1, double> {
   double* s;  // 25 doubles
   double E_[15], dl_[5];
   __device__ __forceinline__ double& P(int r, int c) { return s[r * 5 + c]; }
@@ -707,21 +708,53 @@ struct SmootherStore<1> {
   __device__ __forceinline__ double& dl(int j) { return dl_[j]; }
 };
 template <>
-struct SmootherStore<2> {
+struct SmootherStore<2, double> {
   double* s;  // 45 doubles
   __device__ __forceinline__ double& P(int r, int c) { return s[r * 5 + c]; }
   __device__ __forceinline__ double& E(int j) { return s[25 + j]; }
   __device__ __forceinline__ double& dl(int j) { return s[40 + j]; }
 };
+
+// Precision of the covariance algebra (Joseph update, smoother, covariance transport results):
+// FP64 in the FP64 (kPrec 0) and mixed (kPrec 1) paths, FP32 in the experimental kPrec 2.
+template <int kPrec>
+struct CovType {
+  using type = double;
+};
+template <>
+struct CovType<2> {
+  using type = float;
+};
+template <class U>
+__device__ __forceinline__ U cov_from_d(double x);
+template <>
+__device__ __forceinline__ double cov_from_d<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float cov_from_d<float>(double x) { return d2f(x); }
+template <class U>
+__device__ __forceinline__ U cov_from_f(float x);
+template <>
+__device__ __forceinline__ double cov_from_f<double>(float x) { return f2d(x); }
+template <>
+__device__ __forceinline__ float cov_from_f<float>(float x) { return x; }
+__device__ __forceinline__ double cov_to_d(double x) { return x; }
+__device__ __forceinline__ double cov_to_d(float x) { return f2d(x); }
+__device__ __forceinline__ float cov_to_f(double x) { return d2f(x); }
+__device__ __forceinline__ float cov_to_f(float x) { return x; }
+
 __host__ __device__ constexpr int state_doubles(int place) { return place == 0 ? 0 : (place == 1 ? 25 : 45); }
 
-template <bool kMixed, int kMode, int kPlace, class F>
-__device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i, SmootherStore<kPlace> st) {
+template <int kPrec, int kMode, int kPlace, class F>
+__device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
+                          SmootherStore<kPlace, typename CovType<kPrec>::type> st) {
+  constexpr bool kMixed = kPrec != 0;
+  using U = typename CovType<kPrec>::type;
   const uint32_t n = a.stride;  // SoA row stride of seeds and outputs
   const uint32_t b0 = a.offsets[i], b1 = a.offsets[i + 1];
-  double p[5], C[15];
+  double p[5];
+  U C[15];
   for (int j = 0; j < 5; ++j) p[j] = a.seed_par[size_t(j) * n + i];
-  for (int j = 0; j < 15; ++j) C[j] = a.seed_cov[size_t(j) * n + i];
+  for (int j = 0; j < 15; ++j) C[j] = cov_from_d<U>(a.seed_cov[size_t(j) * n + i]);
   uint32_t status = 0, attempts = 0, rejected = 0;
   double chi2 = 0.0;
   int N = 0;
@@ -737,7 +770,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i, SmootherSt
   }
   if (N == 0 && status == 0) {
     for (int j = 0; j < 5; ++j) a.par[size_t(j) * n + i] = p[j];
-    for (int j = 0; j < 15; ++j) a.cov[size_t(j) * n + i] = C[j];
+    for (int j = 0; j < 15; ++j) a.cov[size_t(j) * n + i] = cov_to_d(C[j]);
     a.chi2[i] = 0.0;
     a.ndf[i] = 0;
     a.status[i] = TKF_TRACK_TOO_FEW_HITS;
@@ -771,7 +804,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i, SmootherSt
     const uint32_t m = b0 + k;
     Surf s;
     load_surf(a.surf, a.sid[m], s);
-    double J[5][5];
+    U J[5][5];
     double sp2 = 0.0, cp2 = 1.0, st2 = 1.0, ct2 = 0.0;  // predicted direction at s (k >= 1)
     if (k > 0) {
       if constexpr (!kMixed) {
@@ -923,7 +956,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i, SmootherSt
       // C_pred = J (C + Q) J^T in FP32
       float Cf[15];
 #pragma unroll
-      for (int j = 0; j < 15; ++j) Cf[j] = d2f(C[j]);
+      for (int j = 0; j < 15; ++j) Cf[j] = cov_to_f(C[j]);
       Cf[S(2, 2)] += th0sq / (fsth * fsth);
       Cf[S(3, 3)] += th0sq;
       float M[5][5];
@@ -950,20 +983,20 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i, SmootherSt
 #pragma unroll
             for (int q = 0; q < 5; ++q) acc += M[r0][q] * Jf[c0][q];
           }
-          C[S(r0, c0)] = f2d(acc);
+          C[S(r0, c0)] = cov_from_f<U>(acc);
         }
 #pragma unroll
       for (int r0 = 0; r0 < 5; ++r0)
 #pragma unroll
-        for (int c0 = 0; c0 < 5; ++c0) J[r0][c0] = f2d(Jf[r0][c0]);
+        for (int c0 = 0; c0 < 5; ++c0) J[r0][c0] = cov_from_f<U>(Jf[r0][c0]);
       }
       // ---- smoother: R = P J^T (in place; J row 4 is e_4)
 #pragma unroll
       for (int r0 = 0; r0 < 5; ++r0) {
-        double row[5];
+        U row[5];
 #pragma unroll
         for (int c0 = 0; c0 < 4; ++c0) {
-          double acc = 0.0;
+          U acc = 0;
 #pragma unroll
           for (int q = 0; q < 5; ++q) acc += st.P(r0, q) * J[c0][q];
           row[c0] = acc;
@@ -975,34 +1008,34 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i, SmootherSt
     }
     // ---- gain-matrix update with H = [I2 0]; Joseph form (paper Sec. 2; Fruhwirth 1987)
     const double m0 = a.loc0[m], m1 = a.loc1[m];
-    const double V00 = a.v00[m], V01 = a.v01[m], V11 = a.v11[m];
-    const double S00 = C[S(0, 0)] + V00, S01 = C[S(0, 1)] + V01, S11 = C[S(1, 1)] + V11;
-    const double det = S00 * S11 - S01 * S01;
-    if (!(S00 > 0.0 && det > 0.0)) {
+    const U V00 = cov_from_d<U>(a.v00[m]), V01 = cov_from_d<U>(a.v01[m]), V11 = cov_from_d<U>(a.v11[m]);
+    const U S00 = C[S(0, 0)] + V00, S01 = C[S(0, 1)] + V01, S11 = C[S(1, 1)] + V11;
+    const U det = S00 * S11 - S01 * S01;
+    if (!(S00 > U(0) && det > U(0))) {
       status |= TKF_TRACK_UPDATE_NOT_SPD;
       break;
     }
-    const double idet = 1.0 / det;
-    const double Si00 = S11 * idet, Si01 = -S01 * idet, Si11 = S00 * idet;
-    const double r0 = m0 - p[0], r1 = m1 - p[1];
-    chi2 += r0 * (Si00 * r0 + Si01 * r1) + r1 * (Si01 * r0 + Si11 * r1);
-    double K[5][2];
+    const U idet = U(1) / det;
+    const U Si00 = S11 * idet, Si01 = -S01 * idet, Si11 = S00 * idet;
+    const U r0 = cov_from_d<U>(m0 - p[0]), r1 = cov_from_d<U>(m1 - p[1]);
+    chi2 += cov_to_d(r0 * (Si00 * r0 + Si01 * r1) + r1 * (Si01 * r0 + Si11 * r1));
+    U K[5][2];
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
-      const double U0 = C[S(j, 0)], U1 = C[S(j, 1)];
+      const U U0 = C[S(j, 0)], U1 = C[S(j, 1)];
       K[j][0] = U0 * Si00 + U1 * Si01;
       K[j][1] = U0 * Si01 + U1 * Si11;
     }
 #pragma unroll
-    for (int j = 0; j < 5; ++j) p[j] += K[j][0] * r0 + K[j][1] * r1;
+    for (int j = 0; j < 5; ++j) p[j] += cov_to_d(K[j][0] * r0 + K[j][1] * r1);
     {
       // X = (I - K H) C ; C' = X - (X H^T - K V) K^T
-      double X[5][5];
+      U X[5][5];
 #pragma unroll
       for (int r_ = 0; r_ < 5; ++r_)
 #pragma unroll
         for (int c_ = 0; c_ < 5; ++c_) X[r_][c_] = C[S(r_, c_)] - K[r_][0] * C[S(0, c_)] - K[r_][1] * C[S(1, c_)];
-      double Y[5][2];
+      U Y[5][2];
 #pragma unroll
       for (int r_ = 0; r_ < 5; ++r_) {
         Y[r_][0] = X[r_][0] - (K[r_][0] * V00 + K[r_][1] * V01);
@@ -1056,12 +1089,12 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i, SmootherSt
         break;
       }
       // W = R H^T S^-1; p_0|N += W r; C_0|N -= W (R H^T)^T; P = R - R H^T K^T
-      double W[5][2];
+      U W[5][2];
 #pragma unroll
       for (int j = 0; j < 5; ++j) {
         W[j][0] = st.P(j, 0) * Si00 + st.P(j, 1) * Si01;
         W[j][1] = st.P(j, 0) * Si01 + st.P(j, 1) * Si11;
-        st.dl(j) += W[j][0] * r0 + W[j][1] * r1;
+        st.dl(j) += cov_to_d(W[j][0] * r0 + W[j][1] * r1);
       }
 #pragma unroll
       for (int r_ = 0; r_ < 5; ++r_)
@@ -1069,7 +1102,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i, SmootherSt
         for (int c_ = r_; c_ < 5; ++c_) st.E(S(r_, c_)) -= W[r_][0] * st.P(c_, 0) + W[r_][1] * st.P(c_, 1);
 #pragma unroll
       for (int r_ = 0; r_ < 5; ++r_) {
-        const double R0 = st.P(r_, 0), R1 = st.P(r_, 1);
+        const U R0 = st.P(r_, 0), R1 = st.P(r_, 1);
 #pragma unroll
         for (int c_ = 0; c_ < 5; ++c_) st.P(r_, c_) -= R0 * K[c_][0] + R1 * K[c_][1];
       }
@@ -1081,18 +1114,18 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i, SmootherSt
     if (st.dl(2) > kPi) st.dl(2) -= 2.0 * kPi;
     if (st.dl(2) <= -kPi) st.dl(2) += 2.0 * kPi;
     // positive definiteness of the smoothed covariance: all LDL^T pivots > 0
-    double L[15];
+    U L[15];
 #pragma unroll
     for (int j = 0; j < 15; ++j) L[j] = st.E(j);
     bool spd = true;
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
-      const double d = L[S(j, j)];
-      spd = spd && (d > 0.0);
-      const double inv = 1.0 / d;
+      const U d = L[S(j, j)];
+      spd = spd && (d > U(0));
+      const U inv = U(1) / d;
 #pragma unroll
       for (int r_ = j + 1; r_ < 5; ++r_) {
-        const double f = L[S(j, r_)] * inv;
+        const U f = L[S(j, r_)] * inv;
 #pragma unroll
         for (int c_ = r_; c_ < 5; ++c_) L[S(r_, c_)] -= f * L[S(j, c_)];
       }
@@ -1109,14 +1142,14 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i, SmootherSt
 #pragma unroll
     for (int j = 0; j < 5; ++j) st.dl(j) = nan;
 #pragma unroll
-    for (int j = 0; j < 15; ++j) st.E(j) = nan;
+    for (int j = 0; j < 15; ++j) st.E(j) = U(nan);
     chi2 = nan;
   }
   if (N < 3 && !bad_offsets) status |= TKF_TRACK_TOO_FEW_HITS;
 #pragma unroll
   for (int j = 0; j < 5; ++j) a.par[size_t(j) * n + i] = st.dl(j);
 #pragma unroll
-  for (int j = 0; j < 15; ++j) a.cov[size_t(j) * n + i] = st.E(j);
+  for (int j = 0; j < 15; ++j) a.cov[size_t(j) * n + i] = cov_to_d(st.E(j));
   a.chi2[i] = chi2;
   a.ndf[i] = 2 * N;
   a.status[i] = status;
@@ -1140,13 +1173,13 @@ __host__ __device__ constexpr int reg_min_blocks(int regs) { return regs >= 255 
 // warps would take the L1 capacity those spills need: launch +6 %).
 __host__ __device__ constexpr int reg_state_place(int regs) { return regs == 128 ? 2 : 0; }
 
-template <bool kMixed, int kMode, int kRegs, class F>
+template <int kPrec, int kMode, int kRegs, class F>
 __global__ void __launch_bounds__(reg_block_threads(kRegs), reg_min_blocks(kRegs))
     fit_persistent_kernel(FitArgs a, F fld, const uint32_t* __restrict__ perm, uint32_t* __restrict__ counter,
                           uint32_t tpw) {
-  constexpr int kPlace = reg_state_place(kRegs);
+  constexpr int kPlace = kPrec == 2 ? 0 : reg_state_place(kRegs);
   extern __shared__ double smem_state[];
-  SmootherStore<kPlace> st{};
+  SmootherStore<kPlace, typename CovType<kPrec>::type> st{};
   if constexpr (kPlace != 0) st.s = smem_state + threadIdx.x * state_doubles(kPlace);
   const uint32_t lane = threadIdx.x & 31u;
   for (;;) {
@@ -1155,7 +1188,7 @@ __global__ void __launch_bounds__(reg_block_threads(kRegs), reg_min_blocks(kRegs
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= a.n_tracks) break;
     const uint32_t j = base + lane;
-    if (lane < tpw && j < a.n_tracks) fit_track<kMixed, kMode>(a, fld, perm[j], st);
+    if (lane < tpw && j < a.n_tracks) fit_track<kPrec, kMode>(a, fld, perm[j], st);
   }
 }
 
@@ -1468,39 +1501,41 @@ cudaError_t propose_fields(const FitArgs& a, const FieldDev& f, float* h0, cudaS
 }
 
 // Launches the persistent fit for one precision, step mode and field.
-template <bool kMixed, int kMode, int kRegs, class F>
+template <int kPrec, int kMode, int kRegs, class F>
 cudaError_t launch_persistent(const FitArgs& a, const F& fld, const uint32_t* perm, uint32_t* counter,
                               LaunchShape shape, cudaStream_t stream) {
   if (shape.threads > reg_block_threads(kRegs)) return cudaErrorInvalidConfiguration;
-  const size_t smem = size_t(shape.threads) * state_doubles(reg_state_place(kRegs)) * sizeof(double);
-  fit_persistent_kernel<kMixed, kMode, kRegs>
+  const int place = kPrec == 2 ? 0 : reg_state_place(kRegs);
+  const size_t smem = size_t(shape.threads) * state_doubles(place) * sizeof(double);
+  fit_persistent_kernel<kPrec, kMode, kRegs>
       <<<shape.blocks, shape.threads, smem, stream>>>(a, fld, perm, counter, uint32_t(shape.tracks_per_warp));
   return cudaGetLastError();
 }
 
 // Record capture (training only) is built with the full register file alone.
-template <bool kMixed, int kRegs, class F>
+template <int kPrec, int kRegs, class F>
 cudaError_t launch_mode(const FitArgs& a, const F& fld, int mode, const uint32_t* perm, uint32_t* counter,
                         LaunchShape shape, cudaStream_t stream) {
-  if (mode == kLearned) return launch_persistent<kMixed, kLearned, kRegs>(a, fld, perm, counter, shape, stream);
+  if (mode == kLearned) return launch_persistent<kPrec, kLearned, kRegs>(a, fld, perm, counter, shape, stream);
   if (mode == kRecord) {
-    if constexpr (kRegs == 255) return launch_persistent<kMixed, kRecord, kRegs>(a, fld, perm, counter, shape, stream);
+    if constexpr (kRegs == 255 && kPrec != 2)
+      return launch_persistent<kPrec, kRecord, kRegs>(a, fld, perm, counter, shape, stream);
     return cudaErrorInvalidValue;
   }
-  return launch_persistent<kMixed, kPlain, kRegs>(a, fld, perm, counter, shape, stream);
+  return launch_persistent<kPrec, kPlain, kRegs>(a, fld, perm, counter, shape, stream);
 }
 
-template <bool kMixed, int kRegs>
+template <int kPrec, int kRegs>
 cudaError_t launch_fields(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm, uint32_t* counter,
                           LaunchShape shape, cudaStream_t stream) {
   if (f.kind == TKF_FIELD_UNIFORM) {
     if (f.b[0] == 0.0 && f.b[1] == 0.0)
-      return launch_mode<kMixed, kRegs>(a, FieldUniformZ{f.b[2], float(f.b[2])}, mode, perm, counter, shape, stream);
-    return launch_mode<kMixed, kRegs>(
+      return launch_mode<kPrec, kRegs>(a, FieldUniformZ{f.b[2], float(f.b[2])}, mode, perm, counter, shape, stream);
+    return launch_mode<kPrec, kRegs>(
         a, FieldUniform{{f.b[0], f.b[1], f.b[2]}, {float(f.b[0]), float(f.b[1]), float(f.b[2])}}, mode, perm, counter,
         shape, stream);
   }
-  return launch_mode<kMixed, kRegs>(a, grid_policy(f), mode, perm, counter, shape, stream);
+  return launch_mode<kPrec, kRegs>(a, grid_policy(f), mode, perm, counter, shape, stream);
 }
 
 }  // namespace

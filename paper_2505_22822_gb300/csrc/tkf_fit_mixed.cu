@@ -8,7 +8,7 @@ cudaError_t launch_fit_mixed(const FitArgs& a, const FieldDev& f, int mode, cons
                              LaunchShape shape, cudaStream_t stream) {
   if (shape.regs == 128) return launch_fit_mixed_r128(a, f, mode, perm, counter, shape, stream);
   if (shape.regs == 64) return launch_fit_mixed_r64(a, f, mode, perm, counter, shape, stream);
-  return launch_fields<true, 255>(a, f, mode, perm, counter, shape, stream);
+  return launch_fields<1, 255>(a, f, mode, perm, counter, shape, stream);
 }
 
 cudaError_t launch_propose_start(const FitArgs& a, const FieldDev& f, float* h0, cudaStream_t stream) {

@@ -6,7 +6,7 @@ namespace tkf {
 
 cudaError_t launch_fit_mixed_r64(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm,
                                    uint32_t* counter, LaunchShape shape, cudaStream_t stream) {
-  return launch_fields<true, 64>(a, f, mode, perm, counter, shape, stream);
+  return launch_fields<1, 64>(a, f, mode, perm, counter, shape, stream);
 }
 
 }  // namespace tkf

@@ -110,6 +110,8 @@ cudaError_t launch_fit_mixed_r128(const FitArgs& a, const FieldDev& f, int mode,
                                   uint32_t* counter, LaunchShape shape, cudaStream_t stream);
 cudaError_t launch_fit_mixed_r64(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm,
                                  uint32_t* counter, LaunchShape shape, cudaStream_t stream);
+cudaError_t launch_fit_mixed32(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm, uint32_t* counter,
+                               LaunchShape shape, cudaStream_t stream);
 
 // Enqueues the fit of every track in `a` on `stream`: track ordering, then the persistent fit.
 // With `timing`, events timing[0] and timing[1] are recorded right before and after the

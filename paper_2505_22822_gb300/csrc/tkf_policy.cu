@@ -43,6 +43,14 @@ std::array<int, 4> default_shape(int precision, bool record) {
   return {128, 2, 32, 255};
 }
 
+// Register caps the kernels of a precision exist at.
+bool has_regs(int precision, int regs) {
+  if (regs == 255) return true;
+  if (precision == TKF_MIXED) return regs == 128 || regs == 64;
+  if (precision == TKF_MIXED_FP32) return regs == 128;
+  return false;
+}
+
 int field_class(const FieldDev& f) {
   if (f.kind != TKF_FIELD_UNIFORM) return 2;
   return (f.b[0] == 0.0 && f.b[1] == 0.0) ? 0 : 1;
@@ -55,7 +63,8 @@ std::string tune_key(const FitArgs& a, const FieldDev& f, int precision, int sm_
   int lg = 0;
   while ((2u << lg) <= a.n_tracks && lg < 31) ++lg;
   char buf[96];
-  snprintf(buf, sizeof(buf), "%s.%s.%s.n%d.sm%d", precision == TKF_MIXED ? "mixed" : "fp64",
+  snprintf(buf, sizeof(buf), "%s.%s.%s.n%d.sm%d",
+           precision == TKF_MIXED ? "mixed" : (precision == TKF_MIXED_FP32 ? "mixed_fp32" : "fp64"),
            fit_mode(a) == 1 ? "learned" : (fit_mode(a) == 2 ? "record" : "adaptive"), kField[field_class(f)], lg,
            sm_count);
   return buf;
@@ -105,7 +114,7 @@ cudaError_t tune(tkf_context ctx, const FitArgs& a, const FieldDev& f, int preci
     if (tpw != 32 && !small) break;
     for (const Candidate& c : kCandidates) {
       if (e != cudaSuccess) break;
-      if (c.regs != 255 && precision != TKF_MIXED) continue;
+      if (!has_regs(precision, c.regs)) continue;
       const std::array<int, 4> cand = {c.threads, c.blocks_per_sm, tpw, c.regs};
       const LaunchShape s = make_shape(cand, ctx->sm_count);
       for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
@@ -210,7 +219,8 @@ bool valid_block_shape(uint32_t threads, uint32_t blocks_per_sm, uint32_t tracks
                        int precision, bool record) {
   if (tracks_per_warp > 32) return false;
   if (max_registers != 0 && max_registers != 255 && max_registers != 128 && max_registers != 64) return false;
-  if (max_registers != 0 && max_registers != 255 && (precision != TKF_MIXED || record)) return false;
+  if (max_registers != 0 && (!has_regs(precision, int(max_registers)) || (max_registers != 255 && record)))
+    return false;
   if (threads == 0 && blocks_per_sm == 0) return true;
   return valid_shape(int(threads), int(blocks_per_sm), max_registers ? int(max_registers) : 255);
 }

@@ -263,3 +263,44 @@ def test_mixed_edge_cases_status(ctx):
     o = run_oracle(w, tr)
     np.testing.assert_array_equal(g["status"], o.status)
     np.testing.assert_array_equal(g["ndf"], o.ndf)
+
+
+# ---------------------------------------------------------------- FP32 covariance algebra
+def _dp_over_sigma(g, o):
+    good = ((o.status & 0x39F) == 0) & (g["status"] == o.status)
+    C = oracle.unpack(o.cov[good])
+    sig = np.sqrt(np.einsum("nii->ni", C))
+    dp = g["par"][good] - o.par[good]
+    dp[:, 2] = (dp[:, 2] + np.pi) % (2 * np.pi) - np.pi
+    dchi = np.abs(g["chi2"][good] - o.chi2[good]) / np.maximum(o.chi2[good], 1.0)
+    return (np.abs(dp) / sig).max(1), dchi
+
+
+@pytest.mark.parametrize("name", ["barrel", "solenoid_map"])
+def test_fp32_covariance_algebra_meets_the_mixed_tolerance(ctx, name):
+    """The experimental TKF_MIXED_FP32 (Joseph update and smoother in FP32 too, no C^-1 in the
+    forward-accumulated smoother): on the barrel and field-map workloads every track stays
+    within 1e-3 sigma of the FP64 oracle and chi2 within 1e-3 relative."""
+    w = (synth.barrel_workload(n_events=2, lo=1500, hi=2500, seed=2) if name == "barrel"
+         else synth.solenoid_muon_workload(5000, seed=3))
+    g = run_gpu(ctx, w, opts=tkf.Options(precision=tkf.MIXED_FP32, mass=w.mass))
+    o = run_oracle(w)
+    assert np.array_equal(g["status"], o.status)
+    ds, dchi = _dp_over_sigma(g, o)
+    print({"max_dp_over_sigma": float(ds.max()), "max_rel_chi2": float(dchi.max())})
+    assert ds.max() <= MIXED_TOL_SIGMA and dchi.max() <= MIXED_TOL_CHI2
+
+
+def test_fp32_covariance_algebra_misses_on_wide_priors(ctx):
+    """Where the seed prior is wide (telescope: 1 mm, 10 mrad, 10 % in q/p) the smoother cancels
+    more of the prior covariance, and FP32 covariance algebra loses part of the tolerance: a
+    fraction of a percent of tracks land between 1e-3 and 3e-3 sigma (the mixed path, with its
+    FP64 update and smoother, stays below 1e-3 sigma on the same tracks)."""
+    w = synth.telescope_workload(2000, seed=0)
+    o = run_oracle(w)
+    ds32, _ = _dp_over_sigma(run_gpu(ctx, w, opts=tkf.Options(precision=tkf.MIXED_FP32)), o)
+    ds, _ = _dp_over_sigma(run_gpu(ctx, w, opts=tkf.Options(precision=tkf.MIXED)), o)
+    print({"fp32_frac_within": float(np.mean(ds32 <= 1e-3)), "fp32_max": float(ds32.max()), "mixed_max": float(ds.max())})
+    assert ds.max() <= MIXED_TOL_SIGMA
+    assert 0.98 < np.mean(ds32 <= MIXED_TOL_SIGMA) < 1.0
+    assert ds32.max() < 3e-3
