@@ -544,8 +544,12 @@ tkf_status tkf_fit_host(tkf_context ctx, tkf_geometry geo, tkf_field field, cons
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_host: workspace cudaMalloc");
     ctx->ws_bytes = chunks * chunk_ws;
   }
-  // the staging buffers may still be read by an earlier call's work on the caller's stream
+  // the staging buffers may still be in use by an earlier call's work (also one that stopped on
+  // an error with copies in flight)
   e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->h2d_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->d2h_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->fit2_stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_host: stream synchronize");
   auto h2d = [&](void* dst, const void* src, size_t bytes) {
     if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->h2d_stream);

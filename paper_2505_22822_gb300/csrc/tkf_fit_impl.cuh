@@ -1490,8 +1490,7 @@ cudaError_t launch_propose(const FitArgs& a, const F& fld, float* h0, cudaStream
   return cudaGetLastError();
 }
 
-template <class R>
-cudaError_t propose_fields(const FitArgs& a, const FieldDev& f, float* h0, cudaStream_t stream) {
+inline cudaError_t propose_fields(const FitArgs& a, const FieldDev& f, float* h0, cudaStream_t stream) {
   if (f.kind == TKF_FIELD_UNIFORM) {
     if (f.b[0] == 0.0 && f.b[1] == 0.0) return launch_propose(a, FieldUniformZ{f.b[2], float(f.b[2])}, h0, stream);
     return launch_propose(a, FieldUniform{{f.b[0], f.b[1], f.b[2]}, {float(f.b[0]), float(f.b[1]), float(f.b[2])}}, h0,

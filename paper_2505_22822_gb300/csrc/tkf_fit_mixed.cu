@@ -12,7 +12,7 @@ cudaError_t launch_fit_mixed(const FitArgs& a, const FieldDev& f, int mode, cons
 }
 
 cudaError_t launch_propose_start(const FitArgs& a, const FieldDev& f, float* h0, cudaStream_t stream) {
-  return propose_fields<float>(a, f, h0, stream);
+  return propose_fields(a, f, h0, stream);
 }
 
 }  // namespace tkf
