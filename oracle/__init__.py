@@ -106,6 +106,10 @@ def lib():
         L.orc_mlp_forward.argtypes = [vp, vp, u32, vp]
         L.orc_propose_start.argtypes = [vp, u32, ctypes.POINTER(OField), ctypes.POINTER(OOpts), u32,
                                         ctypes.c_uint64, vp, vp, vp, vp]
+        L.orc_estimate_seeds.argtypes = [vp, u32, ctypes.POINTER(OField), u32, ctypes.c_uint64, vp, vp, vp,
+                                         ctypes.c_int, vp, vp, vp]
+        L.orc_helix_seed.restype = u32
+        L.orc_helix_seed.argtypes = [vp, vp, vp, d, vp]
         L.orc_update.restype = u32
         L.orc_update.argtypes = [vp, vp, vp, vp, vp]
         _lib = L
@@ -282,6 +286,29 @@ def propose_start(surfaces: np.ndarray, fld: OField, opts: Options, offsets, sid
     lib().orc_propose_start(_p(s), s.shape[0], ctypes.byref(fld), ctypes.byref(o), n, int(n_meas), _p(offsets),
                             _p(sid), _p(seed_par), _p(h0))
     return h0
+
+
+def estimate_seeds(surfaces: np.ndarray, fld: OField, offsets, meas, sid, first_three: bool = False):
+    """Seed parameters [n, 5], packed covariances [n, 15] and status [n] of every track from the
+    helix through three of its measurements: the first, middle and last, or the first three
+    (status 1: fewer than 3, 2: no curvature, q/p = 0, 4: bad offsets or surface ids)."""
+    s = surfaces14(surfaces)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint32)
+    n = offsets.shape[0] - 1
+    meas = _f64(meas)
+    sid = np.ascontiguousarray(sid, dtype=np.uint32)
+    par, cov, st = np.zeros((n, 5)), np.zeros((n, 15)), np.zeros(n, dtype=np.uint32)
+    lib().orc_estimate_seeds(_p(s), s.shape[0], ctypes.byref(fld), n, int(sid.shape[0]), _p(offsets), _p(meas),
+                             _p(sid), int(bool(first_three)), _p(par), _p(cov), _p(st))
+    return par, cov, st
+
+
+def helix_seed(r1, r2, r3, bz: float):
+    """(phi, theta, q/p) at r1 of the helix through three points in an axial field B_z, and the
+    status (2: no curvature)."""
+    out = np.zeros(3)
+    st = lib().orc_helix_seed(_p(_f64(r1)), _p(_f64(r2)), _p(_f64(r3)), float(bz), _p(out))
+    return out, int(st)
 
 
 def update(m, V, p, C):

@@ -1194,6 +1194,157 @@ void orc_propose_start(const double* surfaces, uint32_t n_surf, const orc_field*
   }
 }
 
+// ---------------------------------------------------------------- seed estimation (helix through 3 hits)
+// Reading (the paper lists track parameter estimation from a seed as a step of the chain,
+// Sec. 2, and prints no method): three measurements of a track give three space points; the
+// helix axis is z. In the transverse plane the circle through the points gives the radius R,
+// the turning sense (hence the charge) and the direction at the first point; along a helix z is
+// linear in the transverse arc length, which gives cot(theta) from points 1 and 3;
+// p_T = kappa |B_z| R. The parameters are expressed on the surface of the first measurement (its
+// measured local position, the direction angles, q/p). Exact for noise-free hits of a track in
+// a uniform axial field without material.
+// Status: 1 fewer than 3 measurements; 2 no curvature (collinear points in the transverse plane,
+// or B_z = 0: a straight line, q/p = 0); 4 bad input (offsets or surface ids).
+static uint32_t helix_seed(const double r1[3], const double r2[3], const double r3[3], double bz, double par[3]) {
+  // par: phi, theta, q/p at r1
+  const double ax = r2[0] - r1[0], ay = r2[1] - r1[1], bx = r3[0] - r1[0], by = r3[1] - r1[1];
+  const double a2 = ax * ax + ay * ay, b2 = bx * bx + by * by;
+  // twice the signed area of the triangle: > 0 when 1 -> 2 -> 3 runs counterclockwise seen from +z
+  const double D = 2.0 * (ax * by - ay * bx);
+  uint32_t st = 0;
+  double tx, ty, s13;
+  if (!(std::fabs(D) > 1e-12 * (a2 + b2)) || bz == 0.0) {
+    st = 2;  // the straight line from point 1 to point 3
+    const double c13 = std::sqrt(b2);
+    tx = bx / c13;
+    ty = by / c13;
+    s13 = c13;
+    par[2] = 0.0;
+  } else {
+    // centre of the circle, relative to point 1
+    const double cx = (by * a2 - ay * b2) / D, cy = (ax * b2 - bx * a2) / D;
+    const double R = std::sqrt(cx * cx + cy * cy);
+    // unit tangent at point 1 in the sense of travel: the radius vector (-cx, -cy) turned by
+    // +90 degrees when counterclockwise, -90 when clockwise
+    const double sg = D > 0.0 ? 1.0 : -1.0;
+    tx = sg * cy / R;
+    ty = -sg * cx / R;
+    // transverse arc from point 1 to point 3 in the sense of travel (up to one full turn)
+    const double u1x = -cx, u1y = -cy, u3x = bx - cx, u3y = by - cy;
+    double ang = std::atan2(sg * (u1x * u3y - u1y * u3x), u1x * u3x + u1y * u3y);
+    if (ang < 0.0) ang += 2.0 * kPi;
+    s13 = R * ang;
+    // F = q v x B: for B_z > 0 a positive charge turns clockwise seen from +z
+    const double q = (D > 0.0) == (bz > 0.0) ? -1.0 : 1.0;
+    const double pt = kKappa * std::fabs(bz) * R;
+    const double cot = (r3[2] - r1[2]) / s13;
+    par[2] = q / (pt * std::sqrt(1.0 + cot * cot));
+  }
+  par[0] = std::atan2(ty, tx);
+  par[1] = std::atan2(s13, r3[2] - r1[2]);
+  return st;
+}
+
+static void seed_track(const Surface* surf, uint32_t n_surf, const Field& F, const double* meas, const uint32_t* sid,
+                       uint32_t N, int first_three, double par[5], double cov[15], uint32_t* status) {
+  for (int j = 0; j < 5; ++j) par[j] = std::nan("");
+  for (int j = 0; j < 15; ++j) cov[j] = 0.0;
+  if (N < 3) {
+    *status = 1;
+    return;
+  }
+  // Reading (which three): the first, middle and last measurements of the candidate by default
+  // (the longest lever arm the candidate offers); the first three on request, as for a seed
+  // made of three inner space points.
+  const uint32_t k[3] = {0, first_three ? 1u : (N - 1) / 2, first_three ? 2u : N - 1};
+  double r[3][3], bz[3];
+  for (int j = 0; j < 3; ++j) {
+    if (sid[k[j]] >= n_surf) {
+      *status = 4;
+      return;
+    }
+    const Surface& s = surf[sid[k[j]]];
+    const double* m = meas + 5 * size_t(k[j]);
+    for (int i = 0; i < 3; ++i) r[j][i] = s.c[i] + m[0] * s.u[i] + m[1] * s.v[i];
+    double B[3];
+    bool oof = false;
+    field_at(F, r[j], B, &oof);
+    bz[j] = B[2];
+  }
+  // Reading (field): the mean of B_z at the three points
+  const double bmean = (bz[0] + bz[1] + bz[2]) / 3.0;
+  double ang[3];
+  *status = helix_seed(r[0], r[1], r[2], bmean, ang);
+  par[0] = meas[0];
+  par[1] = meas[1];
+  par[2] = ang[0];
+  par[3] = ang[1];
+  par[4] = ang[2];
+
+  // Reading (covariance: a prior for the fit, meant to be wide rather than narrow). The local
+  // position is the first measurement's. sh2 is the mean per-coordinate hit variance. Multiple
+  // scattering: the Highland angle theta0 of the first surface at normal incidence, at the
+  // estimated momentum (1 GeV without curvature) and beta = 1, once per surface spanned. Angles:
+  // the hit errors over the lever arm L (transverse L_T for phi) plus twice the scattering, and for
+  // phi the bending angle L_T / 2R times the relative curvature error. Relative q/p error: hit
+  // errors and scattering over the sagitta, the spread of B_z over the points, and a 1 % floor.
+  // Without curvature var(q/p) = 1 GeV^-2. Angle variances are at most pi^2.
+  double sh2 = 0.0;
+  for (int j = 0; j < 3; ++j) sh2 += (meas[5 * k[j] + 2] + meas[5 * k[j] + 4]) / 6.0;
+  const double dx = r[2][0] - r[0][0], dy = r[2][1] - r[0][1], dz = r[2][2] - r[0][2];
+  const double LT2 = dx * dx + dy * dy, L2 = LT2 + dz * dz;
+  const double p_est = *status == 0 ? std::fabs(1.0 / ang[2]) : 1.0;
+  const Surface& s0 = surf[sid[0]];
+  const double th0 = (s0.t > 0.0 && s0.X0 > 0.0) ? highland(p_est, 1.0, s0.t, s0.X0) : 0.0;
+  const double ms2 = double(k[2] - k[0]) * th0 * th0;
+  const double sth = std::sin(ang[1]);
+  double var_phi = 64.0 * sh2 / LT2 + 2.0 * ms2 / (sth * sth);
+  double var_qop = 1.0;
+  if (*status == 0) {
+    const double R = p_est * sth / (kKappa * std::fabs(bmean));
+    const double sag = LT2 / (8.0 * R);
+    const double bmax = std::fmax(bz[0], std::fmax(bz[1], bz[2]));
+    const double bmin = std::fmin(bz[0], std::fmin(bz[1], bz[2]));
+    const double db = (bmax - bmin) / bmean;
+    const double rel2 = 4.0 * sh2 / (sag * sag) + ms2 * LT2 / (16.0 * sag * sag) + db * db + 1e-4;
+    var_qop = rel2 * ang[2] * ang[2];
+    var_phi += LT2 / (4.0 * R * R) * rel2;
+  }
+  const double pi2 = kPi * kPi;
+  cov[0] = meas[2];                                                 // (l0, l0)
+  cov[1] = meas[3];                                                 // (l0, l1)
+  cov[5] = meas[4];                                                 // (l1, l1)
+  cov[9] = std::fmin(var_phi, pi2);                                 // (phi, phi)
+  cov[12] = std::fmin(16.0 * sh2 / L2 + 2.0 * ms2, pi2);            // (theta, theta)
+  cov[14] = var_qop;                                                // (q/p, q/p)
+}
+
+// Seed parameters [n][5] and packed covariances [n][15] of every track from three of its
+// measurements (first_three = 0: first, middle, last; 1: the first three); status [n] as in
+// seed_track.
+void orc_estimate_seeds(const double* surfaces, uint32_t n_surf, const orc_field* field, uint32_t n_tracks,
+                        uint64_t n_meas, const uint32_t* offsets, const double* meas, const uint32_t* sid,
+                        int first_three, double* seed_par, double* seed_cov, uint32_t* status) {
+  std::vector<Surface> surf = to_surfaces(surfaces, n_surf);
+  Field F = to_field(field);
+  for (uint32_t i = 0; i < n_tracks; ++i) {
+    const uint32_t a = offsets[i], b = offsets[i + 1];
+    if (b < a || b > n_meas) {
+      for (int j = 0; j < 5; ++j) seed_par[5 * size_t(i) + j] = std::nan("");
+      for (int j = 0; j < 15; ++j) seed_cov[15 * size_t(i) + j] = 0.0;
+      status[i] = 4;
+      continue;
+    }
+    seed_track(surf.data(), n_surf, F, meas + 5 * size_t(a), sid + a, b - a, first_three, seed_par + 5 * size_t(i),
+               seed_cov + 15 * size_t(i), status + i);
+  }
+}
+
+// The helix-through-three-points step alone (for the pins): phi, theta, q/p and the status.
+uint32_t orc_helix_seed(const double* r1, const double* r2, const double* r3, double bz, double* out) {
+  return helix_seed(r1, r2, r3, bz, out);
+}
+
 // One gain-matrix update (for the chi2 identity pin).
 uint32_t orc_update(const double* m, const double* V, double* p, double* C, double* chi2) {
   return kf_update(m, V, p, C, chi2);
