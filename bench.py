@@ -82,6 +82,11 @@ def parse():
     ap.add_argument("--shape", default=None,
                     help="fixed launch shape 'threads,blocks_per_sm,tracks_per_warp,registers' for every variant "
                          "(registers 128 or 64 apply to the mixed variants; FP64 keeps 255)")
+    ap.add_argument("--no-seeds", action="store_true",
+                    help="skip the seed-estimation kernel and the chain from estimated seeds")
+    ap.add_argument("--streams", action="store_true",
+                    help="event-level concurrency: one launch per event on 1..16 CUDA streams against one "
+                         "batched launch (one JSON line per configuration)")
     ap.add_argument("--sweep", action="store_true",
                     help="throughput sweep 1e3..1e7 tracks per launch in the solenoid map (one JSON line per point)")
     return ap.parse_args()
@@ -208,6 +213,86 @@ def pull_stats(out, t):
     chi2 = out.chi2.cpu().numpy()[ok] / out.ndf.cpu().numpy()[ok]
     return {"sigma": [round(float(x), 4) for x in pull.std(0)], "mean": [round(float(x), 4) for x in pull.mean(0)],
             "chi2_ndf": round(float(chi2.mean()), 4)}
+
+
+# Seed estimation, algorithmic bytes per track: its two offsets (4 bytes amortized), three
+# measurements (loc0, loc1, v00, v01, v11, sid: 44 bytes each), 20 output doubles and a status.
+SEED_BYTES_PER_TRACK = 4 + 3 * 44 + 20 * 8 + 4
+
+
+def hbm_peak_gbs() -> tuple[float, str]:
+    """The measured copy bandwidth of MEASURED_PEAKS.json, else the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "of fallback"
+
+
+def seed_stage(ctx, geo, fld, dev, t, opts, stream, steps: int, warmup: int, flush):
+    """The seed-estimation kernel alone on the batch (HBM roofline), and the chain that starts
+    from its seeds: estimated seeds -> fit -> refit with the fit's covariance inflated 100-fold,
+    with the pulls of the refit against the truth."""
+    import torch
+    import paper_2505_22822_gb300 as tkf
+    n = t.n_tracks
+    device = dev.offsets.device
+    out = tkf.SeedResult(torch.empty((5, n), dtype=torch.float64, device=device),
+                         torch.empty((15, n), dtype=torch.float64, device=device),
+                         torch.empty(n, dtype=torch.int32, device=device))
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for e0, e1 in evs:
+            if flush is not None:
+                flush.add_(1.0)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
+
+    ms = timed(lambda: tkf.estimate_seeds(ctx, geo, fld, dev, out=out, stream=stream))
+    status = out.status.cpu().numpy().view(np.uint32)
+    par, cov = out.par.cpu().numpy().T, out.cov.cpu().numpy().T
+    d = par - t.truth
+    d[:, 2] = (d[:, 2] + np.pi) % (2 * np.pi) - np.pi
+    iu = np.triu_indices(5)
+    diag = [int(np.where((iu[0] == k) & (iu[1] == k))[0][0]) for k in range(5)]
+    ok = status == 0
+    seed_pulls = (d[ok] / np.sqrt(cov[ok][:, diag])).std(0)
+    peak, peak_src = hbm_peak_gbs()
+    achieved = SEED_BYTES_PER_TRACK * n / (ms * 1e-3) / 1e9
+    seeds = {"kernel": "estimate_seeds_kernel", "ms": ms, "tracks_per_s": n / (ms * 1e-3),
+             "status_ok": float(np.mean(ok)), "prior_pull_sigma": [round(float(x), 3) for x in seed_pulls],
+             "median_rel_qop_error": float(np.median(np.abs(par[ok, 4] / t.truth[ok, 4] - 1.0))),
+             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                          "frac": achieved / peak, "peak_source": peak_src,
+                          "algorithmic_bytes_per_track": SEED_BYTES_PER_TRACK}}
+    # the chain, timed as one unit per step: estimate, fit, refit (direct launches)
+    s1 = tkf.alloc_outputs(n, device, steps=False)
+    s2 = tkf.alloc_outputs(n, device, steps=False)
+    b1 = tkf.with_seeds(dev, out.par, out.cov)
+    b2 = tkf.with_seeds(dev, s1.par, s1.cov)
+    o1 = dataclasses.replace(opts, graph=False, kernel_events=None, step_mode=tkf.STEP_ADAPTIVE, mlp=None)
+    o2 = dataclasses.replace(o1, seed_cov_scale=100.0)
+
+    def chain():
+        tkf.estimate_seeds(ctx, geo, fld, dev, out=out, stream=stream)
+        tkf.fit(ctx, geo, fld, b1, o1, out=s1, stream=stream, steps=False)
+        tkf.fit(ctx, geo, fld, b2, o2, out=s2, stream=stream, steps=False)
+
+    cms = timed(chain)
+    pulls = pull_stats(s2, t)
+    chain_line = {"stages": "estimate_seeds -> fit -> refit (seed_cov_scale 100)",
+                  "precision": {0: "fp64", 1: "mixed", 2: "mixed_fp32"}[opts.precision],
+                  "ms_per_step": cms, "tracks_per_s": n / (cms * 1e-3),
+                  "fit_status_ok": float(np.mean(s2.status.cpu().numpy() == 0)),
+                  "pull_sigma": pulls["sigma"], "pull_mean": pulls["mean"], "chi2_ndf_mean": pulls["chi2_ndf"]}
+    return seeds, chain_line
 
 
 def cpu_baseline(w, max_seconds: float = 20.0):
@@ -378,6 +463,94 @@ def run_sweep(args, local: int, rank: int, tune_file: str):
         del b, out
 
 
+def run_streams(args, local: int, rank: int):
+    """Event-level concurrency against one batched launch: the bench batch's events fitted one
+    launch per event on S CUDA streams (S = 1, 2, 4, 8, 16; one library context per stream,
+    since a context's scratch serves one launch at a time; events dealt round-robin), and the
+    whole batch in one launch. Mixed precision, autotuned shapes, direct launches. One JSON line
+    per configuration."""
+    import torch
+    import paper_2505_22822_gb300 as tkf
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    w = make_workload("barrel", args.events, rank)
+    t = w.tracks
+    host = tkf.Batch.from_arrays(t.offsets, t.meas, t.sid, t.seed_par, t.seed_cov)
+    full = host.to(dev)
+    ev = t.event.astype(np.int64)
+    starts = np.flatnonzero(np.r_[True, ev[1:] != ev[:-1]])
+    bounds = list(zip(starts, np.r_[starts[1:], t.n_tracks]))
+    opts = tkf.Options(precision=tkf.MIXED, mass=w.mass, autotune=True)
+
+    def event_batch(t0, t1):
+        return tkf.Batch(full.offsets[t0:t1 + 1].clone(), full.loc0, full.loc1, full.v00, full.v01, full.v11,
+                         full.sid, full.seed_par[:, t0:t1].contiguous(), full.seed_cov[:, t0:t1].contiguous())
+
+    events = [event_batch(t0, t1) for t0, t1 in bounds]
+    outs = [tkf.alloc_outputs(t1 - t0, dev, steps=False) for t0, t1 in bounds]
+    L2_BYTES = 129e6
+    flush = torch.zeros(int(2 * L2_BYTES) // 4, dtype=torch.float32, device=dev)
+    results = []
+    for S in (1, 2, 4, 8, 16):
+        ctxs = [tkf.Context(local) for _ in range(S)]
+        hs = [(tkf.Geometry.from_table(c, w.geometry.table), tkf.Field.from_desc(c, w.field)) for c in ctxs]
+        streams = [torch.cuda.Stream() for _ in range(S)]
+
+        def step():
+            for e, (b, o) in enumerate(zip(events, outs)):
+                j = e % S
+                tkf.fit(ctxs[j], hs[j][0], hs[j][1], b, opts, out=o, stream=streams[j])
+
+        for _ in range(max(3, args.warmup)):  # the first tunes every size class per context
+            step()
+        torch.cuda.synchronize()
+        main_s = torch.cuda.current_stream()
+        times = []
+        for _ in range(args.steps):
+            flush.add_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(main_s)
+            for s in streams:
+                s.wait_event(e0)
+            step()
+            for s in streams:
+                done = torch.cuda.Event()
+                done.record(s)
+                main_s.wait_event(done)
+            e1.record(main_s)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = statistics.mean(times)
+        line = {"streams_experiment": "per-event launches", "streams": S, "events": len(bounds),
+                "tracks": int(t.n_tracks), "ms_per_step": ms, "tracks_per_s": t.n_tracks / (ms * 1e-3),
+                "launches_per_step": 3 * len(bounds)}
+        results.append(line)
+        print(json.dumps(line), flush=True)
+        del ctxs, hs
+    # the whole batch in one launch (replayed from a CUDA graph, as the main bench)
+    ctx = tkf.Context(local)
+    geo, fld = tkf.Geometry.from_table(ctx, w.geometry.table), tkf.Field.from_desc(ctx, w.field)
+    s = torch.cuda.Stream()
+    out = tkf.alloc_outputs(t.n_tracks, dev, steps=False)
+    gopts = dataclasses.replace(opts, graph=True)
+    for _ in range(max(3, args.warmup)):
+        tkf.fit(ctx, geo, fld, full, gopts, out=out, stream=s)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        flush.add_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        tkf.fit(ctx, geo, fld, full, gopts, out=out, stream=s)
+        e1.record(s)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.mean(times)
+    print(json.dumps({"streams_experiment": "one batched launch", "streams": 1, "events": len(bounds),
+                      "tracks": int(t.n_tracks), "ms_per_step": ms, "tracks_per_s": t.n_tracks / (ms * 1e-3),
+                      "launches_per_step": 3}), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -402,6 +575,9 @@ def main():
     tune_file = setup_tune_cache()
     if args.sweep:
         run_sweep(args, local, rank, tune_file)
+        return
+    if args.streams:
+        run_streams(args, local, rank)
         return
     w = make_workload(args.workload, args.events, rank)
     t = w.tracks
@@ -500,6 +676,10 @@ def main():
                             "pulls": pull_stats(out, t)}
     head = variants[-1]
     opts = results[head]["opts"]
+    seeds = chain = None
+    if not args.no_seeds:
+        copts = results["mixed"]["opts"] if "mixed" in results else opts
+        seeds, chain = seed_stage(ctx, geo, fld, dev, t, copts, stream, args.steps, args.warmup, flush)
     ms, ms_max, clocks = results[head]["ms"], results[head]["ms_max"], results[head]["clocks"]
     for k, v in results.items():
         fa, fr, fh, ft = (FLOPS_MAP if args.workload == "map" else FLOPS)[k]
@@ -592,6 +772,9 @@ def main():
                                    if k != "fp64"}
     if learn_info:
         line["learned_proposer"] = learn_info
+    if seeds:
+        line["seed_estimation"] = seeds
+        line["chain_from_estimated_seeds"] = chain
     if e2e:
         line["e2e"] = e2e
     if not args.no_cpu_baseline:

@@ -196,6 +196,11 @@ typedef struct tkf_fit_options {
    * kernel, so that cudaEventElapsedTime gives that kernel's duration alone (without the
    * ordering and proposal launches). A call with events launches directly (no graph). */
   void* const* kernel_events;
+  /* Factor applied to every seed covariance element before the fit (default 1; must be > 0
+   * and finite). A refit from an earlier pass's result (whose covariance already holds the
+   * information of these measurements) inflates it, for example by 100, so that the
+   * measurements are not counted twice. */
+  double seed_cov_scale;
 } tkf_fit_options;
 
 /* Autotuning: the first call of a launch class (precision, step mode, field kind, batch size
@@ -223,11 +228,19 @@ typedef struct tkf_fit_options {
 
 void tkf_fit_options_default(tkf_fit_options* opts);
 
+/* Surface-id flag of a track entry without a measurement (Sec. 2: the navigation passes every
+ * surface a track crosses): a hole in a sensitive module, or a passive surface. The fit
+ * propagates to the surface (sid & ~TKF_SID_NO_MEASUREMENT) and applies its material on
+ * leaving it, and makes no update there; loc0, loc1, v00, v01, v11 of the entry are not read.
+ * ndf counts measurements only. */
+#define TKF_SID_NO_MEASUREMENT 0x80000000u
+
 /* Inputs of one batch, all DEVICE pointers owned by the caller (read only).
- * Track i has the measurements offsets[i] .. offsets[i+1]-1, ordered along the track.
- * Measurement m: local position (loc0[m], loc1[m]) on surface sid[m] and its covariance
- * [[v00, v01], [v01, v11]] (mm^2). The seed of track i is given on the surface of its
- * first measurement: seed_par (5 x n_tracks) and seed_cov (15 x n_tracks, packed). */
+ * Track i has the entries offsets[i] .. offsets[i+1]-1, ordered along the track.
+ * Entry m: local position (loc0[m], loc1[m]) on surface sid[m] and its covariance
+ * [[v00, v01], [v01, v11]] (mm^2), or a surface crossed without a measurement (sid[m] with
+ * TKF_SID_NO_MEASUREMENT). The seed of track i is given on the surface of its first entry:
+ * seed_par (5 x n_tracks) and seed_cov (15 x n_tracks, packed). */
 typedef struct tkf_fit_inputs {
   uint32_t n_tracks;
   uint64_t n_meas;
@@ -281,6 +294,66 @@ tkf_status tkf_fit(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf
 tkf_status tkf_fit_host(tkf_context ctx, tkf_geometry geo, tkf_field field,
                         const tkf_fit_options* opts, const tkf_fit_inputs* host_in,
                         const tkf_fit_outputs* host_out, void* stream);
+
+/* ---------------------------------------------------------------------------- seed parameter estimation */
+
+/* Track parameter estimation (Sec. 2 places it between seeding and track finding and prints no
+ * method; this is the helix through three space points). For each track, three of its
+ * measurements become space points r = c + loc0 u + loc1 v on their surfaces. In the plane
+ * transverse to z the circle through them gives the radius R, the sense of turning (hence the
+ * charge: F = q v x B) and the direction at the first point; z is linear in the transverse arc
+ * length along a helix, which gives theta from points 1 and 3 (the arc followed in the sense
+ * of travel, up to one full turn); p_T = 2.99792458e-4 |B_z| R (GeV, T, mm) with B_z the mean
+ * of the field's z component at the three points. The result is expressed on the surface of
+ * the track's first measurement: (loc0, loc1) = that measurement, phi, theta, q/p. It is exact
+ * for noise-free hits of a track in a uniform axial field without material.
+ *
+ * Covariance (a prior for the fit, meant to be wide rather than narrow; all off-diagonal
+ * elements 0 but (loc0, loc1)): the first measurement's 2x2 covariance; with sh2 the mean
+ * per-coordinate hit variance of the three, L and L_T the 3D and transverse distances of points
+ * 1 and 3, theta0 the Highland angle of the first surface (t / X0, normal incidence, beta = 1)
+ * at the estimated momentum (1 GeV without curvature) and ms2 = (k3 - k1) theta0^2 for the
+ * measurement indices k1 < k3 of points 1 and 3:
+ *   var(theta) = 16 sh2 / L^2 + 2 ms2,
+ *   rel2 = 4 sh2 / s^2 + ms2 L_T^2 / (16 s^2) + (dB / B_z)^2 + 1e-4   (s = L_T^2 / 8R, the
+ *          sagitta; dB the spread of B_z over the three points),
+ *   var(phi) = 64 sh2 / L_T^2 + 2 ms2 / sin^2(theta) + L_T^2 / (4 R^2) rel2,
+ *   var(q/p) = rel2 (q/p)^2;
+ * without curvature the last term of var(phi) is left out and var(q/p) = 1 GeV^-2; the angle
+ * variances are capped at pi^2.
+ *
+ * `which` selects the measurements: TKF_SEED_FIRST_MIDDLE_LAST (the first, the one at index
+ * (N - 1) / 2 and the last of the N; the longest lever arm of a candidate) or
+ * TKF_SEED_FIRST_THREE (as for a seed of three inner space points). */
+#define TKF_SEED_FIRST_MIDDLE_LAST 0u
+#define TKF_SEED_FIRST_THREE 1u
+
+/* Seed status bits: fewer than 3 measurements (parameters NaN, covariance 0); no curvature
+ * (collinear points in the transverse plane, or B_z = 0: a straight line, q/p = 0); offsets
+ * decreasing or beyond n_meas, or a surface id out of range (parameters NaN, covariance 0). */
+#define TKF_SEED_TOO_FEW_HITS 1u
+#define TKF_SEED_NO_CURVATURE 2u
+#define TKF_SEED_BAD_INPUT 4u
+
+/* Outputs, DEVICE pointers owned by the caller (written), in the layout of the fit's seed
+ * inputs, so that they can be passed to tkf_fit as tkf_fit_inputs.seed_par / seed_cov. */
+typedef struct tkf_seed_outputs {
+  double* par;      /* 5 x n_tracks: loc0, loc1, phi, theta, q/p */
+  double* cov;      /* 15 x n_tracks, packed upper triangle */
+  uint32_t* status; /* n_tracks */
+} tkf_seed_outputs;
+
+/* Estimates the starting parameters of every track of the batch from its measurements,
+ * asynchronously on `stream` (a cudaStream_t; NULL is the legacy default stream). Reads
+ * offsets, loc0, loc1, v00, v01, v11 and sid of `in` (DEVICE pointers; seed_par and seed_cov
+ * are not read and may be NULL). Device pointers must be 8-byte aligned and stay valid until
+ * the stream reaches this work. One kernel launch, no allocation.
+ * Errors (nothing enqueued): TKF_ERR_BAD_HANDLE (NULL context, geometry or field from another
+ * context), TKF_ERR_INVALID_ARG (unknown `which`, NULL required pointers, misaligned pointers,
+ * n_meas too large for 32-bit offsets), TKF_ERR_DEVICE (launch failure). Bad offsets or surface
+ * ids are reported per track in `status`. */
+tkf_status tkf_estimate_seeds(tkf_context ctx, tkf_geometry geo, tkf_field field, uint32_t which,
+                              const tkf_fit_inputs* in, const tkf_seed_outputs* out, void* stream);
 
 /* ---------------------------------------------------------------------------- learned step proposer */
 

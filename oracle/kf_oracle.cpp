@@ -50,6 +50,14 @@ const uint32_t kStepUnderflow = 1u << 8;
 const uint32_t kNonFinite = 1u << 9;
 const uint32_t kFatal = ~(kTooFewHits | kOutOfField);
 
+// Reading (navigation through surfaces without a measurement, Sec. 2): a track-state entry
+// whose surface id carries this bit is a surface the track crosses without a measurement (a
+// hole in a sensitive module, or a passive surface): the fit propagates to it and applies its
+// material on leaving it, and makes no update there.
+const uint32_t kNoMeasurement = 0x80000000u;
+inline uint32_t surface_of(uint32_t sid) { return sid & ~kNoMeasurement; }
+inline bool measured(uint32_t sid) { return (sid & kNoMeasurement) == 0; }
+
 struct Surface {
   double u[3], v[3], n[3];  // local axes and normal (global frame); n = u x v
   double c[3];              // centre
@@ -770,21 +778,27 @@ void fit_track(const Surface* surf, uint32_t n_surf, const Field& f, const Opts&
   const int N = int(in.N);
   out.status = 0;
   out.attempts = out.rejected = 0;
-  out.ndf = 2 * N;
+  out.ndf = 0;
   for (int i = 0; i < 15; ++i) out.cov_filt0[i] = std::nan("");
-  if (N == 0) {
+  int M = 0;  // entries with a measurement
+  bool bad = false;
+  for (int k = 0; k < N; ++k) {
+    bad = bad || surface_of(in.sid[k]) >= n_surf;
+    M += measured(in.sid[k]) ? 1 : 0;
+  }
+  out.ndf = 2 * M;
+  if (bad) {
+    fill_nan(out);
+    out.status = kBadInput;
+    return;
+  }
+  if (M == 0) {  // nothing to fit: the seed is the result
     std::memcpy(out.par, in.seed_par, sizeof(double) * 5);
     std::memcpy(out.cov, in.seed_cov, sizeof(double) * 15);
     out.chi2 = 0.0;
     out.status = kTooFewHits;
     return;
   }
-  for (int k = 0; k < N; ++k)
-    if (in.sid[k] >= n_surf) {
-      fill_nan(out);
-      out.status = kBadInput;
-      return;
-    }
   if (!all_finite(in.seed_par, 5) || !all_finite(in.seed_cov, 15)) {
     fill_nan(out);
     out.status = kNonFinite;
@@ -799,14 +813,14 @@ void fit_track(const Surface* surf, uint32_t n_surf, const Field& f, const Opts&
     // so the network proposes its starting value (instead of h_max) from the seed state at the
     // first surface, toward the second surface; from then on the plain control adapts it from
     // the error estimates, and the error estimate judges every step.
-    prop.h_ctrl = propose_start(surf[in.sid[0]], surf[in.sid[1]], f, o, in.seed_par);
+    prop.h_ctrl = propose_start(surf[surface_of(in.sid[0])], surf[surface_of(in.sid[1])], f, o, in.seed_par);
   }
   double chi2 = 0.0;
   uint32_t status = 0;
   for (int k = 0; k < N; ++k) {
-    const Surface& sk = surf[in.sid[k]];
+    const Surface& sk = surf[surface_of(in.sid[k])];
     if (k > 0) {
-      const Surface& sprev = surf[in.sid[k - 1]];
+      const Surface& sprev = surf[surface_of(in.sid[k - 1])];
       double pm[5], Q[25];
       std::memcpy(pm, &pf[(k - 1) * 5], sizeof(pm));
       status |= material(sprev, o, pm, Q);
@@ -829,15 +843,17 @@ void fit_track(const Surface* surf, uint32_t n_surf, const Field& f, const Opts&
       matmul(t55, Jt, &Cp[k * 25], 5, 5, 5);
       symmetrize(&Cp[k * 25], 5);
     }
-    const double* mk = in.meas + 5 * k;
-    double m[2] = {mk[0], mk[1]};
-    double V[4] = {mk[2], mk[3], mk[3], mk[4]};
     std::memcpy(&pf[k * 5], &pp[k * 5], sizeof(double) * 5);
     std::memcpy(&Cf[k * 25], &Cp[k * 25], sizeof(double) * 25);
-    double c2 = 0.0;
-    status |= kf_update(m, V, &pf[k * 5], &Cf[k * 25], &c2);
-    if (status & kFatal) break;
-    chi2 += c2;
+    if (measured(in.sid[k])) {  // else the filtered state is the predicted one
+      const double* mk = in.meas + 5 * k;
+      double m[2] = {mk[0], mk[1]};
+      double V[4] = {mk[2], mk[3], mk[3], mk[4]};
+      double c2 = 0.0;
+      status |= kf_update(m, V, &pf[k * 5], &Cf[k * 25], &c2);
+      if (status & kFatal) break;
+      chi2 += c2;
+    }
     if (k == 0) pack_cov(&Cf[0], out.cov_filt0);
     pf[k * 5 + 2] = wrap_phi(pf[k * 5 + 2]);
     if (!(pf[k * 5 + 3] > 0.0 && pf[k * 5 + 3] < kPi)) {
@@ -859,7 +875,7 @@ void fit_track(const Surface* surf, uint32_t n_surf, const Field& f, const Opts&
     if (!all_finite(out.par, 5) || !all_finite(out.cov, 15) || !std::isfinite(chi2)) status |= kNonFinite;
   }
   if (status & kFatal) fill_nan(out);
-  if (N < 3) status |= kTooFewHits;
+  if (M < 3) status |= kTooFewHits;
   out.status = status;
   if (keep) {
     keep->pp = pp; keep->Cp = Cp; keep->pf = pf; keep->Cf = Cf; keep->J = J; keep->ps = ps; keep->Cs = Cs;
@@ -1092,7 +1108,8 @@ uint32_t orc_material(const double* surface14, const orc_opts* opts, const doubl
 // Linear-Gaussian chain through the oracle's own update and smoother: states x_k in R^5
 // with x_k = J_k (x_{k-1} + w_{k-1}), w ~ N(0, Q_{k-1}), measured by H = [I2 0] with
 // covariance V_k; prior x_0 ~ N(p0, C0). Writes the smoothed mean/cov of every state
-// (ps [N][5], Cs [N][25]) and the chi2 sum. Returns status bits.
+// (ps [N][5], Cs [N][25]) and the chi2 sum; a step whose measurement is NaN has none.
+// Returns status bits.
 uint32_t orc_linear_chain(int N, const double* J, const double* Q, const double* p0, const double* C0,
                           const double* m, const double* V, double* ps, double* Cs, double* chi2_out,
                           double* pf_out, double* Cf_out) {
@@ -1115,6 +1132,7 @@ uint32_t orc_linear_chain(int N, const double* J, const double* Q, const double*
     std::memcpy(&pf[k * 5], &pp[k * 5], sizeof(double) * 5);
     std::memcpy(&Cf[k * 25], &Cp[k * 25], sizeof(double) * 25);
     double c2 = 0.0, mm[2] = {m[2 * k], m[2 * k + 1]};
+    if (std::isnan(mm[0])) continue;  // a step without a measurement, as a hole in fit_track
     st |= kf_update(mm, V + 4 * k, &pf[k * 5], &Cf[k * 25], &c2);
     chi2 += c2;
   }
@@ -1189,8 +1207,10 @@ void orc_propose_start(const double* surfaces, uint32_t n_surf, const orc_field*
   for (uint32_t i = 0; i < n_tracks; ++i) {
     const uint32_t a = offsets[i], b = offsets[i + 1];
     h0[i] = O.h_max;
-    if (!O.mlp || b < a || b - a < 2 || b > n_meas || sid[a] >= n_surf || sid[a + 1] >= n_surf) continue;
-    h0[i] = propose_start(surf[sid[a]], surf[sid[a + 1]], F, O, seed_par + 5 * size_t(i));
+    if (!O.mlp || b < a || b - a < 2 || b > n_meas || surface_of(sid[a]) >= n_surf ||
+        surface_of(sid[a + 1]) >= n_surf)
+      continue;
+    h0[i] = propose_start(surf[surface_of(sid[a])], surf[surface_of(sid[a + 1])], F, O, seed_par + 5 * size_t(i));
   }
 }
 
@@ -1204,7 +1224,8 @@ void orc_propose_start(const double* surfaces, uint32_t n_surf, const orc_field*
 // measured local position, the direction angles, q/p). Exact for noise-free hits of a track in
 // a uniform axial field without material.
 // Status: 1 fewer than 3 measurements; 2 no curvature (collinear points in the transverse plane,
-// or B_z = 0: a straight line, q/p = 0); 4 bad input (offsets or surface ids).
+// or B_z = 0: a straight line, q/p = 0); 4 bad input (offsets or surface ids, or a first entry
+// without a measurement).
 static uint32_t helix_seed(const double r1[3], const double r2[3], const double r3[3], double bz, double par[3]) {
   // par: phi, theta, q/p at r1
   const double ax = r2[0] - r1[0], ay = r2[1] - r1[1], bx = r3[0] - r1[0], by = r3[1] - r1[1];
@@ -1249,20 +1270,31 @@ static void seed_track(const Surface* surf, uint32_t n_surf, const Field& F, con
                        uint32_t N, int first_three, double par[5], double cov[15], uint32_t* status) {
   for (int j = 0; j < 5; ++j) par[j] = std::nan("");
   for (int j = 0; j < 15; ++j) cov[j] = 0.0;
-  if (N < 3) {
+  // entries without a measurement (holes, passive surfaces) give no space point; the seed is
+  // expressed on the first entry's surface, which therefore needs its measurement
+  std::vector<uint32_t> mi;
+  for (uint32_t e = 0; e < N; ++e) {
+    if (surface_of(sid[e]) >= n_surf) {
+      *status = 4;
+      return;
+    }
+    if (measured(sid[e])) mi.push_back(e);
+  }
+  if (N > 0 && !measured(sid[0])) {
+    *status = 4;
+    return;
+  }
+  const uint32_t M = uint32_t(mi.size());
+  if (M < 3) {
     *status = 1;
     return;
   }
   // Reading (which three): the first, middle and last measurements of the candidate by default
   // (the longest lever arm the candidate offers); the first three on request, as for a seed
   // made of three inner space points.
-  const uint32_t k[3] = {0, first_three ? 1u : (N - 1) / 2, first_three ? 2u : N - 1};
+  const uint32_t k[3] = {mi[0], mi[first_three ? 1u : (M - 1) / 2], mi[first_three ? 2u : M - 1]};
   double r[3][3], bz[3];
   for (int j = 0; j < 3; ++j) {
-    if (sid[k[j]] >= n_surf) {
-      *status = 4;
-      return;
-    }
     const Surface& s = surf[sid[k[j]]];
     const double* m = meas + 5 * size_t(k[j]);
     for (int i = 0; i < 3; ++i) r[j][i] = s.c[i] + m[0] * s.u[i] + m[1] * s.v[i];
@@ -1294,7 +1326,7 @@ static void seed_track(const Surface* surf, uint32_t n_surf, const Field& F, con
   const double dx = r[2][0] - r[0][0], dy = r[2][1] - r[0][1], dz = r[2][2] - r[0][2];
   const double LT2 = dx * dx + dy * dy, L2 = LT2 + dz * dz;
   const double p_est = *status == 0 ? std::fabs(1.0 / ang[2]) : 1.0;
-  const Surface& s0 = surf[sid[0]];
+  const Surface& s0 = surf[sid[0]];  // measured, so no flag bit
   const double th0 = (s0.t > 0.0 && s0.X0 > 0.0) ? highland(p_est, 1.0, s0.t, s0.X0) : 0.0;
   const double ms2 = double(k[2] - k[0]) * th0 * th0;
   const double sth = std::sin(ang[1]);

@@ -25,7 +25,7 @@ _ROOT = os.path.dirname(_HERE)
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "libtkf.so")
 _SOURCES = ["tkf_api.cu", "tkf_order.cu", "tkf_policy.cu", "tkf_fit_fp64.cu", "tkf_fit_mixed.cu",
-            "tkf_fit_mixed_r128.cu", "tkf_fit_mixed_r64.cu", "tkf_fit_mixed32.cu", "tkf_mlp.cu"]
+            "tkf_fit_mixed_r128.cu", "tkf_fit_mixed_r64.cu", "tkf_fit_mixed32.cu", "tkf_mlp.cu", "tkf_seed.cu"]
 _lib = None
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
@@ -35,6 +35,9 @@ FP64, MIXED, MIXED_FP32 = 0, 1, 2
 STEP_ADAPTIVE, STEP_LEARNED = 0, 1
 FIT_AUTOTUNE, FIT_GRAPH, FIT_TEST_PROPOSAL_TIMEOUT = 1, 2, 1 << 31
 FIELD_UNIFORM, FIELD_RZ_GRID = 0, 1
+SEED_FIRST_MIDDLE_LAST, SEED_FIRST_THREE = 0, 1
+SID_NO_MEASUREMENT = 0x80000000  # surface-id flag: the track crosses the surface without a measurement
+SEED_STATUS = {"TOO_FEW_HITS": 1, "NO_CURVATURE": 2, "BAD_INPUT": 4}
 
 TRACK_STATUS = {
     "MAX_STEPS": 1 << 0, "SURFACE_MISSED": 1 << 1, "PARTICLE_STOPPED": 1 << 2,
@@ -114,7 +117,8 @@ class FitOptions(ctypes.Structure):
                 ("record_capacity", ctypes.c_uint32), ("record_count", ctypes.c_void_p),
                 ("flags", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
                 ("blocks_per_sm", ctypes.c_uint32), ("tracks_per_warp", ctypes.c_uint32),
-                ("max_registers", ctypes.c_uint32), ("kernel_events", ctypes.c_void_p)]
+                ("max_registers", ctypes.c_uint32), ("kernel_events", ctypes.c_void_p),
+                ("seed_cov_scale", ctypes.c_double)]
 
 
 class MlpTrainOptions(ctypes.Structure):
@@ -133,6 +137,10 @@ class FitInputs(ctypes.Structure):
 class FitOutputs(ctypes.Structure):
     _fields_ = [("par", ctypes.c_void_p), ("cov", ctypes.c_void_p), ("chi2", ctypes.c_void_p),
                 ("ndf", ctypes.c_void_p), ("status", ctypes.c_void_p), ("steps", ctypes.c_void_p)]
+
+
+class SeedOutputs(ctypes.Structure):
+    _fields_ = [("par", ctypes.c_void_p), ("cov", ctypes.c_void_p), ("status", ctypes.c_void_p)]
 
 
 # C entry points and their signatures (argument types), as declared in include/tkf.h.
@@ -154,6 +162,8 @@ _SIGNATURES = {
                                     ctypes.POINTER(FitInputs), ctypes.POINTER(FitOutputs), _VP]),
     "tkf_fit_noalloc": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(FitOptions),
                                        ctypes.POINTER(FitInputs), ctypes.POINTER(FitOutputs), _VP]),
+    "tkf_estimate_seeds": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_uint32, ctypes.POINTER(FitInputs),
+                                          ctypes.POINTER(SeedOutputs), _VP]),
     "tkf_propose_start": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(FitOptions), ctypes.POINTER(FitInputs),
                                          _VP, _VP]),
     "tkf_mlp_load": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(_VP)]),
@@ -336,6 +346,7 @@ class Options:
     tracks_per_warp: int = 0      # explicit tracks a warp takes at a time (1..32), else 32 or tuned
     max_registers: int = 0        # explicit register cap (255; 128 or 64 for MIXED), else default or tuned
     kernel_events: object = None  # (begin, end) torch.cuda.Event pair around the fit kernel
+    seed_cov_scale: float = 1.0   # factor on the seed covariance (a refit inflates it)
 
     def c(self) -> FitOptions:
         o = FitOptions()
@@ -354,6 +365,7 @@ class Options:
         o.block_threads, o.blocks_per_sm = self.block_threads, self.blocks_per_sm
         o.tracks_per_warp = self.tracks_per_warp
         o.max_registers = self.max_registers
+        o.seed_cov_scale = self.seed_cov_scale
         if self.kernel_events is not None:
             # the C array must outlive the call: kept on the options struct
             o._events = (ctypes.c_void_p * 2)(*(ev.cuda_event for ev in self.kernel_events))
@@ -511,6 +523,45 @@ def propose_start(ctx: Context, geo: Geometry, field: Field, batch: Batch, opts:
                                    ctypes.byref(_inputs_struct(batch)), _VP(h0.data_ptr()),
                                    _VP(stream.cuda_stream)), ctx.handle, "tkf_propose_start")
     return h0
+
+
+@dataclass
+class SeedResult:
+    par: object     # [5, n] f64: loc0, loc1, phi, theta, q/p on the first measurement's surface
+    cov: object     # [15, n] f64, packed upper triangle
+    status: object  # [n] (SEED_STATUS bits)
+
+
+def estimate_seeds(ctx: Context, geo: Geometry, field: Field, batch: Batch,
+                   which: int = SEED_FIRST_MIDDLE_LAST, out: SeedResult | None = None, stream=None) -> SeedResult:
+    """tkf_estimate_seeds: every track's starting parameters and prior covariance from the helix
+    through three of its measurements (the first, middle and last, or the first three), in the
+    layout of ``Batch.seed_par`` / ``seed_cov``; enqueued on ``stream`` (default: torch's current
+    stream). The batch's own seeds are not read."""
+    import torch
+    dev = batch.offsets.device
+    if dev.type != "cuda":
+        raise TkfError("estimate_seeds() needs CUDA tensors")
+    n = batch.n_tracks
+    if out is None:
+        out = SeedResult(torch.empty((5, n), dtype=torch.float64, device=dev),
+                         torch.empty((15, n), dtype=torch.float64, device=dev),
+                         torch.empty((n,), dtype=torch.int32, device=dev))
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    so = SeedOutputs()
+    so.par, so.cov, so.status = _ptr(out.par), _ptr(out.cov), _ptr(out.status)
+    _check(lib().tkf_estimate_seeds(ctx.handle, geo.handle, field.handle, int(which),
+                                    ctypes.byref(_inputs_struct(batch)), ctypes.byref(so),
+                                    _VP(stream.cuda_stream)), ctx.handle, "tkf_estimate_seeds")
+    return out
+
+
+def with_seeds(batch: Batch, seed_par, seed_cov) -> Batch:
+    """The batch with other seeds (for example those of estimate_seeds, or a fit's result for a
+    refit); the measurement arrays are shared, not copied."""
+    return Batch(batch.offsets, batch.loc0, batch.loc1, batch.v00, batch.v01, batch.v11, batch.sid,
+                 seed_par, seed_cov)
 
 
 def fit_noalloc(ctx: Context, geo: Geometry, field: Field, batch: Batch, out: Result,

@@ -161,7 +161,7 @@ tkf_status tkf_geometry_create(tkf_context ctx, const tkf_surface_desc* s, uint3
     o[12] = d.thickness;
     o[13] = d.x0;
     o[14] = d.thickness / d.x0;
-    o[15] = 0.0;
+    o[15] = (d.thickness > 0.0) ? sqrt(o[14]) * (1.0 + 0.038 * log(o[14])) : 0.0;
     float* f = reinterpret_cast<float*>(o + 16);
     for (int r = 0; r < 3; ++r) {
       f[r] = float(col[0][r]);
@@ -308,6 +308,7 @@ void tkf_fit_options_default(tkf_fit_options* o) {
   o->tracks_per_warp = 0;
   o->max_registers = 0;
   o->kernel_events = nullptr;
+  o->seed_cov_scale = 1.0;
 }
 
 // Validation shared by the fit entry points; `out` may be NULL only when `need_out` is false.
@@ -336,6 +337,8 @@ static tkf_status check_common(tkf_context ctx, tkf_geometry geo, tkf_field fiel
       o->max_steps == 0 || !(o->mass > 0) || !isfinite(o->h_max))
     return fail(ctx, TKF_ERR_INVALID_ARG,
                 std::string(fn) + ": options need tol, h_max, h_min, surf_tol, mass > 0, h_min <= h_max, max_steps > 0");
+  if (!(o->seed_cov_scale > 0) || !isfinite(o->seed_cov_scale))
+    return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": seed_cov_scale must be positive and finite");
   if ((o->flags & ~(TKF_FIT_AUTOTUNE | TKF_FIT_GRAPH | TKF_FIT_TEST_PROPOSAL_TIMEOUT)) != 0)
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": unknown flag");
   if (!tkf::valid_block_shape(o->block_threads, o->blocks_per_sm, o->tracks_per_warp, o->max_registers, o->precision,
@@ -375,6 +378,7 @@ static tkf::FitArgs make_args(tkf_geometry geo, const tkf_fit_options* o, const 
   a.sid = in->sid;
   a.seed_par = in->seed_par;
   a.seed_cov = in->seed_cov;
+  a.seed_cov_scale = o->seed_cov_scale;
   if (out) {
     a.par = out->par;
     a.cov = out->cov;
@@ -456,6 +460,48 @@ tkf_status tkf_propose_start(tkf_context ctx, tkf_geometry geo, tkf_field field,
   tkf::FitArgs a = make_args(geo, o, in, nullptr);
   cudaError_t e = tkf::launch_propose_start(a, field->f, h0, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_propose_start: launch");
+  return TKF_OK;
+}
+
+tkf_status tkf_estimate_seeds(tkf_context ctx, tkf_geometry geo, tkf_field field, uint32_t which,
+                              const tkf_fit_inputs* in, const tkf_seed_outputs* out, void* stream) {
+  const char* fn = "tkf_estimate_seeds";
+  if (!ctx) return fail(nullptr, TKF_ERR_BAD_HANDLE, std::string(fn) + ": NULL context");
+  if (!geo || !field || geo->ctx != ctx || field->ctx != ctx)
+    return fail(ctx, TKF_ERR_BAD_HANDLE, std::string(fn) + ": geometry or field handle NULL or from another context");
+  if (!in || !out) return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": NULL inputs or outputs");
+  if (which != TKF_SEED_FIRST_MIDDLE_LAST && which != TKF_SEED_FIRST_THREE)
+    return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": unknown measurement selection");
+  if (in->n_meas > 0xffffffffull)
+    return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": n_meas exceeds 32-bit offsets");
+  if (in->n_tracks == 0) return TKF_OK;
+  if (!in->offsets || !out->par || !out->cov || !out->status)
+    return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": NULL required pointer");
+  if (in->n_meas > 0 && (!in->loc0 || !in->loc1 || !in->v00 || !in->v01 || !in->v11 || !in->sid))
+    return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": NULL measurement pointer");
+  const void* ptrs[] = {in->loc0, in->loc1, in->v00, in->v01, in->v11, out->par, out->cov};
+  for (const void* p : ptrs)
+    if (!aligned8(p)) return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": pointer not 8-byte aligned");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(ctx, TKF_ERR_DEVICE, std::string(fn) + ": cudaSetDevice failed");
+  tkf::SeedArgs a{};
+  a.n_tracks = in->n_tracks;
+  a.n_meas = in->n_meas;
+  a.offsets = in->offsets;
+  a.loc0 = in->loc0;
+  a.loc1 = in->loc1;
+  a.v00 = in->v00;
+  a.v01 = in->v01;
+  a.v11 = in->v11;
+  a.sid = in->sid;
+  a.surf = geo->d_surf;
+  a.n_surf = geo->n;
+  a.first_three = which == TKF_SEED_FIRST_THREE ? 1u : 0u;
+  a.par = out->par;
+  a.cov = out->cov;
+  a.status = out->status;
+  cudaError_t e = tkf::launch_estimate_seeds(a, field->f, ctx->sm_count, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, (std::string(fn) + ": launch").c_str());
   return TKF_OK;
 }
 

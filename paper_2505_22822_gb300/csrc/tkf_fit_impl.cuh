@@ -754,10 +754,10 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
   double p[5];
   U C[15];
   for (int j = 0; j < 5; ++j) p[j] = a.seed_par[size_t(j) * n + i];
-  for (int j = 0; j < 15; ++j) C[j] = cov_from_d<U>(a.seed_cov[size_t(j) * n + i]);
+  for (int j = 0; j < 15; ++j) C[j] = cov_from_d<U>(a.seed_cov[size_t(j) * n + i] * a.seed_cov_scale);
   uint32_t status = 0, attempts = 0, rejected = 0;
   double chi2 = 0.0;
-  int N = 0;
+  int N = 0, M = 0;  // entries, and entries with a measurement
   const double nan = __longlong_as_double(0x7ff8000000000000LL);
 
   const bool bad_offsets = b1 < b0 || b1 > a.n_meas;
@@ -765,10 +765,13 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
     status = TKF_TRACK_BAD_INPUT;  // never read outside the measurement arrays
   } else {
     N = int(b1 - b0);
-    for (int k = 0; k < N; ++k)
-      if (a.sid[b0 + k] >= a.n_surf) status = TKF_TRACK_BAD_INPUT;
+    for (int k = 0; k < N; ++k) {
+      const uint32_t sid = a.sid[b0 + k];
+      if ((sid & ~TKF_SID_NO_MEASUREMENT) >= a.n_surf) status = TKF_TRACK_BAD_INPUT;
+      M += (sid & TKF_SID_NO_MEASUREMENT) ? 0 : 1;
+    }
   }
-  if (N == 0 && status == 0) {
+  if (M == 0 && status == 0) {  // nothing to fit (no entry, or no measurement): the seed
     for (int j = 0; j < 5; ++j) a.par[size_t(j) * n + i] = p[j];
     for (int j = 0; j < 15; ++j) a.cov[size_t(j) * n + i] = cov_to_d(C[j]);
     a.chi2[i] = 0.0;
@@ -803,7 +806,9 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
   for (int k = 0; k < N && !(status & kFatal); ++k) {
     const uint32_t m = b0 + k;
     Surf s;
-    load_surf(a.surf, a.sid[m], s);
+    const uint32_t sid_m = a.sid[m];
+    const bool measured = (sid_m & TKF_SID_NO_MEASUREMENT) == 0;
+    load_surf(a.surf, sid_m & ~TKF_SID_NO_MEASUREMENT, s);
     U J[5][5];
     double sp2 = 0.0, cp2 = 1.0, st2 = 1.0, ct2 = 0.0;  // predicted direction at s (k >= 1)
     if (k > 0) {
@@ -1006,7 +1011,15 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
         for (int c0 = 0; c0 < 5; ++c0) st.P(r0, c0) = row[c0];
       }
     }
-    // ---- gain-matrix update with H = [I2 0]; Joseph form (paper Sec. 2; Fruhwirth 1987)
+    // ---- gain-matrix update with H = [I2 0]; Joseph form (paper Sec. 2; Fruhwirth 1987).
+    // An entry without a measurement has none: the gain, the inverse residual covariance and
+    // the residual stay 0, so the filtered state is the predicted one and the smoother terms
+    // below add exact zeros.
+    U Si00 = U(0), Si01 = U(0), Si11 = U(0), r0 = U(0), r1 = U(0);
+    U K[5][2];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) K[j][0] = K[j][1] = U(0);
+    if (measured) {
     const double m0 = a.loc0[m], m1 = a.loc1[m];
     const U V00 = cov_from_d<U>(a.v00[m]), V01 = cov_from_d<U>(a.v01[m]), V11 = cov_from_d<U>(a.v11[m]);
     const U S00 = C[S(0, 0)] + V00, S01 = C[S(0, 1)] + V01, S11 = C[S(1, 1)] + V11;
@@ -1016,10 +1029,12 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
       break;
     }
     const U idet = U(1) / det;
-    const U Si00 = S11 * idet, Si01 = -S01 * idet, Si11 = S00 * idet;
-    const U r0 = cov_from_d<U>(m0 - p[0]), r1 = cov_from_d<U>(m1 - p[1]);
+    Si00 = S11 * idet;
+    Si01 = -S01 * idet;
+    Si11 = S00 * idet;
+    r0 = cov_from_d<U>(m0 - p[0]);
+    r1 = cov_from_d<U>(m1 - p[1]);
     chi2 += cov_to_d(r0 * (Si00 * r0 + Si01 * r1) + r1 * (Si01 * r0 + Si11 * r1));
-    U K[5][2];
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
       const U U0 = C[S(j, 0)], U1 = C[S(j, 1)];
@@ -1046,6 +1061,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
 #pragma unroll
         for (int c_ = r_; c_ < 5; ++c_) C[S(r_, c_)] = X[r_][c_] - Y[r_][0] * K[c_][0] - Y[r_][1] * K[c_][1];
     }
+    }  // measured
     if (k == 0) {
       if (p[2] > kPi) p[2] -= 2.0 * kPi;
       if (p[2] <= -kPi) p[2] += 2.0 * kPi;
@@ -1145,13 +1161,13 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
     for (int j = 0; j < 15; ++j) st.E(j) = U(nan);
     chi2 = nan;
   }
-  if (N < 3 && !bad_offsets) status |= TKF_TRACK_TOO_FEW_HITS;
+  if (M < 3 && !bad_offsets) status |= TKF_TRACK_TOO_FEW_HITS;
 #pragma unroll
   for (int j = 0; j < 5; ++j) a.par[size_t(j) * n + i] = st.dl(j);
 #pragma unroll
   for (int j = 0; j < 15; ++j) a.cov[size_t(j) * n + i] = cov_to_d(st.E(j));
   a.chi2[i] = chi2;
-  a.ndf[i] = 2 * N;
+  a.ndf[i] = 2 * M;
   a.status[i] = status;
   if (a.steps) {
     a.steps[i] = attempts;
@@ -1351,11 +1367,13 @@ __global__ void __launch_bounds__(kPropTile) propose_start_tc_kernel(FitArgs a, 
     float x[12] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     if (i < n) {
       const uint32_t b0 = a.offsets[i], b1 = a.offsets[i + 1];
-      ok = b1 >= b0 && b1 - b0 >= 2 && b1 <= a.n_meas && a.sid[b0] < a.n_surf && a.sid[b0 + 1] < a.n_surf;
+      const uint32_t id0 = b1 >= b0 + 2 && b1 <= a.n_meas ? a.sid[b0] & ~TKF_SID_NO_MEASUREMENT : a.n_surf;
+      const uint32_t id1 = b1 >= b0 + 2 && b1 <= a.n_meas ? a.sid[b0 + 1] & ~TKF_SID_NO_MEASUREMENT : a.n_surf;
+      ok = id0 < a.n_surf && id1 < a.n_surf;
       if (ok) {
         Surf s0, s1;
-        load_surf(a.surf, a.sid[b0], s0);
-        load_surf(a.surf, a.sid[b0 + 1], s1);
+        load_surf(a.surf, id0, s0);
+        load_surf(a.surf, id1, s1);
         float p[5];
         for (int j = 0; j < 5; ++j) p[j] = float(a.seed_par[size_t(j) * a.stride + i]);
         float sph, cph, sth, cth;

@@ -14,7 +14,9 @@
 namespace tkf {
 
 // Device surface record: 24 doubles (192 B) per surface:
-//   [0..2] u, [3..5] v, [6..8] n, [9..11] c, [12] thickness, [13] x0, [14] t / x0, [15] 0,
+//   [0..2] u, [3..5] v, [6..8] n, [9..11] c, [12] thickness, [13] x0, [14] t / x0,
+//   [15] sqrt(t / x0) (1 + 0.038 ln(t / x0)) (the Highland factor at normal incidence, beta = 1;
+//   0 without material),
 //   then 16 floats: u, v, n, thickness, t / x0 (FP32 copies for the mixed path), 5 x 0.
 constexpr int kSurfStride = 24;
 
@@ -58,6 +60,7 @@ struct FitArgs {
   const uint32_t* __restrict__ sid;
   const double* __restrict__ seed_par;
   const double* __restrict__ seed_cov;
+  double seed_cov_scale;  // factor on every seed covariance element (1: as given)
   double* __restrict__ par;
   double* __restrict__ cov;
   double* __restrict__ chi2;
@@ -90,6 +93,26 @@ struct Workspace {
 size_t workspace_bytes(uint32_t n_tracks, bool learned);
 Workspace carve_workspace(void* base, uint32_t n_tracks, bool learned);
 cudaError_t launch_propose_start(const FitArgs& a, const FieldDev& f, float* h0, cudaStream_t stream);
+
+// Seed parameter estimation (tkf_seed.cu): one thread per track, outputs in the fit's seed layout.
+struct SeedArgs {
+  uint32_t n_tracks;
+  uint64_t n_meas;
+  const uint32_t* __restrict__ offsets;
+  const double* __restrict__ loc0;
+  const double* __restrict__ loc1;
+  const double* __restrict__ v00;
+  const double* __restrict__ v01;
+  const double* __restrict__ v11;
+  const uint32_t* __restrict__ sid;
+  const double* __restrict__ surf;  // n_surf * kSurfStride
+  uint32_t n_surf;
+  uint32_t first_three;  // 0: first, middle, last measurement; 1: the first three
+  double* __restrict__ par;  // [5][n_tracks]
+  double* __restrict__ cov;  // [15][n_tracks]
+  uint32_t* __restrict__ status;
+};
+cudaError_t launch_estimate_seeds(const SeedArgs& a, const FieldDev& f, int sm_count, cudaStream_t stream);
 
 // Launch shape of the persistent fit: threads per block, blocks in the grid, tracks a warp
 // takes at a time (1..32, one per lane), and the register cap of the kernel variant (255, or

@@ -164,7 +164,7 @@ std::string graph_key(const FitArgs& a, const FieldDev& f, int precision, const 
   k.put(a.record_capacity);
   k.put(a.test_stall_proposals);
   const double dm[] = {a.mat.z_over_a, a.mat.i_ev, a.mat.rho, a.mat.hwp_ev, a.mat.log_hwp_over_i, a.mat.bg2_density,
-                       a.opt.tol, a.opt.h_max, a.opt.h_min, a.opt.surf_tol, a.opt.mass, f.b[0], f.b[1], f.b[2],
+                       a.opt.tol, a.opt.h_max, a.opt.h_min, a.opt.surf_tol, a.opt.mass, a.seed_cov_scale, f.b[0], f.b[1], f.b[2],
                        f.r0, f.dr, f.z0, f.dz, f.inv_dr, f.inv_dz};
   for (double d : dm) k.put(d);
   const float fm[] = {a.mat.log_hwp_over_i_f, a.mat.bg2_density_f, a.mat.two_me_over_i2_f, a.mat.dedx_scale_f,

@@ -62,7 +62,7 @@ class _Params(ctypes.Structure):
                 ("seed_cot", ctypes.c_int),
                 ("cov_inflate", ctypes.c_double), ("min_hits", ctypes.c_int),
                 ("max_hits", ctypes.c_int), ("step", ctypes.c_double),
-                ("r_max", ctypes.c_double), ("z_max", ctypes.c_double)]
+                ("r_max", ctypes.c_double), ("z_max", ctypes.c_double), ("p_hole", ctypes.c_double)]
 
 
 def lib():
@@ -240,6 +240,7 @@ class SimParams:
     step: float = 10.0
     r_max: float = 1050.0
     z_max: float = 3050.0
+    p_hole: float = 0.0       # probability that a crossing after the first is a hole (no measurement)
 
     def _c(self) -> _Params:
         p = _Params()

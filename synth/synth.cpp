@@ -351,11 +351,13 @@ struct Params {
   int min_hits, max_hits;
   double step;
   double r_max, z_max;
+  double p_hole;  // probability that a crossing after the first gives no measurement (a hole)
 };
 
 struct Hit {
   uint32_t sid;
   double l0, l1, t0, t1;  // smeared and true local position
+  bool hole;              // crossed without a measurement
 };
 
 struct TrackSim {
@@ -534,6 +536,9 @@ bool simulate(const Geometry& g, const FieldDesc& f, const Params& P, Rng& rng, 
       local_of(s, x, H.t0, H.t1);
       H.l0 = H.t0 + P.sigma_hit * rng.normal();
       H.l1 = H.t1 + P.sigma_hit * rng.normal();
+      // a hole: the module is crossed (its material acts) but gives no measurement; drawn only
+      // when holes are asked for, so that other workloads keep their random streams
+      H.hole = P.p_hole > 0.0 && !tr.hits.empty() && rng.uniform() < P.p_hole;
       if (tr.hits.empty()) bound_truth(s, x, T, qop, tr.truth);
       bound_truth(s, x, T, qop, tr.truth_last);
       tr.hits.push_back(H);
@@ -568,7 +573,9 @@ bool simulate(const Geometry& g, const FieldDesc& f, const Params& P, Rng& rng, 
     double rr = std::hypot(x[0], x[1]);
     if (rr > P.r_max || std::fabs(x[2]) > P.z_max || path > 20000.0) break;
   }
-  if (int(tr.hits.size()) < P.min_hits) return false;
+  int n_measured = 0;
+  for (const Hit& h : tr.hits) n_measured += h.hole ? 0 : 1;
+  if (n_measured < P.min_hits) return false;
   // seed: truth at the first measurement smeared by the nominal sigmas; covariance
   // diag(sigma^2) * cov_inflate (a diffuse prior).
   double sth = std::sin(tr.truth[3]);
@@ -620,6 +627,7 @@ struct syn_params {
   double cov_inflate;
   int min_hits, max_hits;
   double step, r_max, z_max;
+  double p_hole;
 };
 
 void* syn_geometry_telescope(int n_planes, double spacing, double t, double X0) {
@@ -720,9 +728,13 @@ void* syn_simulate(void* geom, const syn_field* field, const syn_params* params,
   for (size_t i = 0; i < sims.size(); ++i) {
     const TrackSim& s = sims[i];
     for (const Hit& h : s.hits) {
-      R->sid.push_back(h.sid);
+      // a hole: surface id with the no-measurement bit, its measurement fields NaN (unused)
+      R->sid.push_back(h.hole ? (h.sid | 0x80000000u) : h.sid);
       double v = P.sigma_v * P.sigma_v;
+      const double nan = std::nan("");
       double m[5] = {h.l0, h.l1, v, 0.0, v};
+      if (h.hole)
+        for (double& x : m) x = nan;
       R->meas.insert(R->meas.end(), m, m + 5);
       R->hit_truth.push_back(h.t0);
       R->hit_truth.push_back(h.t1);

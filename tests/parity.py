@@ -103,3 +103,42 @@ def self_sensitivity(w, track: int, trials: int = 8, seed: int = 0) -> float:
         _, _, st = compare(g, base, np.inf)
         worst = max(worst, float(st["dev"][0]))
     return worst
+
+
+def chain_self_sensitivity(w, tracks, scale: float = 100.0, trials: int = 32, seed: int = 0,
+                           n_threads: int = 8) -> np.ndarray:
+    """The same for the chain estimated seeds -> fit -> refit (covariance multiplied by
+    `scale`), for each of the `tracks` (indices into the workload): how far the oracle's chain
+    result moves when the measured positions, the estimated seeds and the first fit's result
+    each change by one unit in the last place (every hand-off between the stages is a place
+    where another correct FP64 evaluation order rounds differently). The tracks are perturbed
+    together, `trials` times; a trial that changes a track's step sequence does not count for
+    that track."""
+    t = w.tracks
+    sub = t.subset(np.asarray(tracks, dtype=np.int64))
+    fo = oracle.field_from(w.field)
+    opts = oracle.Options(mass=w.mass)
+    table = w.geometry.table
+
+    def ulp(x, rng):
+        return x * (1 + rng.choice([-1.0, 1.0], size=x.shape) * 2.0 ** -52) if rng is not None else x
+
+    def run(rng=None):
+        meas = sub.meas.copy()
+        meas[:, :2] = ulp(meas[:, :2], rng)
+        sp, sc, _ = oracle.estimate_seeds(table, fo, sub.offsets, meas, sub.sid)
+        r1 = oracle.fit(table, fo, opts, sub.offsets, meas, sub.sid, ulp(sp, rng), ulp(sc, rng), n_threads=n_threads)
+        return oracle.fit(table, fo, opts, sub.offsets, meas, sub.sid, ulp(r1.par, rng), ulp(r1.cov, rng) * scale,
+                          n_threads=n_threads)
+
+    base = run()
+    rng = np.random.default_rng(seed)
+    worst = np.zeros(sub.n_tracks)
+    for _ in range(trials):
+        o = run(rng)
+        same = np.all(o.steps == base.steps, axis=1)
+        g = {"par": o.par, "cov": o.cov, "chi2": o.chi2, "ndf": o.ndf.astype(np.int64), "status": o.status,
+             "steps": o.steps}
+        _, _, st = compare(g, base, np.inf)
+        worst = np.where(same, np.maximum(worst, st["dev"]), worst)
+    return worst

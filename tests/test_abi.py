@@ -34,6 +34,7 @@ def test_option_defaults():
     assert (o.precision, o.step_mode, o.tol, o.h_max, o.h_min, o.surf_tol, o.max_steps) == \
         (0, 0, 1e-4, 1000.0, 1e-4, 1e-2, 10000)
     assert abs(o.mass - 0.1056583755) < 1e-12
+    assert o.seed_cov_scale == 1.0 and o.kernel_events is None
 
 
 def test_null_and_handle_errors_need_no_device():
@@ -46,6 +47,7 @@ def test_null_and_handle_errors_need_no_device():
     L.tkf_fit_options_default(ctypes.byref(o))
     assert L.tkf_fit(None, None, None, ctypes.byref(o), None, None, None) == 2
     assert L.tkf_fit_host(None, None, None, ctypes.byref(o), None, None, None) == 2
+    assert L.tkf_estimate_seeds(None, None, None, 0, None, None, None) == 2
     L.tkf_context_destroy(None)
     L.tkf_geometry_destroy(None)
     L.tkf_field_destroy(None)

@@ -150,6 +150,8 @@ def _batch_posterior(J, L, p0, C0, m, V, upto=None):
     Lam[5:, 5:] += np.eye(nz - 5)
     last = N if upto is None else upto + 1
     for k in range(last):
+        if np.isnan(m[k][0]):
+            continue  # no measurement at this step
         HA = H @ A[k]
         Vi = np.linalg.inv(V[k])
         Lam += HA.T @ Vi @ HA
@@ -158,6 +160,8 @@ def _batch_posterior(J, L, p0, C0, m, V, upto=None):
     mu = S @ eta
     obj = (mu[:5] - p0) @ C0i @ (mu[:5] - p0) + mu[5:] @ mu[5:]
     for k in range(last):
+        if np.isnan(m[k][0]):
+            continue
         res = m[k] - H @ A[k] @ mu
         obj += res @ np.linalg.inv(V[k]) @ res
     means = np.array([A[k] @ mu for k in range(N)])
@@ -192,6 +196,30 @@ def test_update_and_rts_equal_batch_gaussian_posterior(seed, rank):
         mk, ck, _ = _batch_posterior(J, L, p0, C0, m, V, upto=k)
         np.testing.assert_allclose(pf[k], mk[k], atol=1e-11)
         np.testing.assert_allclose(Cf[k], ck[k], atol=1e-11 * np.abs(ck[k]).max())
+
+
+@pytest.mark.parametrize("holes", [(2, 5), (0, 3), (1, 2, 3, 4)])
+def test_rts_with_steps_without_measurement_equals_batch_posterior(holes):
+    """Steps without a measurement (holes, passive surfaces): the filtered state there is the
+    predicted one, and filter + RTS still give the batch posterior of the remaining
+    measurements, at every state."""
+    rng = np.random.default_rng(50 + len(holes))
+    N = 7
+    J = np.array([np.eye(5) + 0.2 * rng.normal(size=(5, 5)) for _ in range(N)])
+    L = 0.05 * rng.normal(size=(N, 5, 2))
+    Q = np.einsum("kij,klj->kil", L, L)
+    p0 = 0.1 * rng.normal(size=5)
+    X = rng.normal(size=(5, 5))
+    C0 = X @ X.T * 0.05 + 0.01 * np.eye(5)
+    m = 0.1 * rng.normal(size=(N, 2))
+    m[list(holes)] = np.nan
+    V = np.array([np.eye(2) * 0.004 + 0.001 for _ in range(N)])
+    ps, Cs, chi2, st, pf, Cf = oracle.linear_chain(J, Q, p0, C0, m, V)
+    assert st == 0
+    means, covs, obj = _batch_posterior(J, L, p0, C0, m, V)
+    np.testing.assert_allclose(ps, means, rtol=0, atol=1e-11 * (1 + np.abs(means).max()))
+    np.testing.assert_allclose(Cs, covs, rtol=0, atol=1e-11 * np.abs(covs).max())
+    assert abs(chi2 - obj) <= 1e-10 * max(1.0, obj)
 
 
 @pytest.mark.parametrize("seed", range(5))
