@@ -80,8 +80,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="launch directly instead of replaying a CUDA graph")
     ap.add_argument("--no-autotune", action="store_true", help="the default launch shape instead of the tuned one")
     ap.add_argument("--shape", default=None,
-                    help="fixed launch shape 'threads,blocks_per_sm,tracks_per_warp,registers' for every variant "
-                         "(registers 128 or 64 apply to the mixed variants; FP64 keeps 255)")
+                    help="fixed launch shape 'threads,blocks_per_sm,tracks_per_warp,registers[,lanes]' for every "
+                         "variant (registers 128 or 64 apply to the mixed variants; FP64 keeps 255; lanes 1 or 4)")
     ap.add_argument("--no-seeds", action="store_true",
                     help="skip the seed-estimation kernel and the chain from estimated seeds")
     ap.add_argument("--streams", action="store_true",
@@ -366,9 +366,10 @@ def setup_tune_cache() -> str:
 
 
 def tuned_shape(path: str, variant: str, n_tracks: int, field: str, disabled: bool):
-    """[threads, blocks per SM, tracks per warp, registers] the autotuner chose for this class."""
+    """[threads, blocks per SM, tracks per warp, registers, lanes a track] the autotuner chose
+    for this class."""
     if disabled:
-        return [128, 2, 32, 255] if variant in ("fp64", "mixed_fp32") else [128, 4, 32, 128]
+        return [128, 2, 32, 255, 1] if variant in ("fp64", "mixed_fp32") else [128, 4, 32, 128, 1]
     prec = variant if variant in ("fp64", "mixed_fp32") else "mixed"
     mode = "learned" if variant.endswith("learned") else "adaptive"
     prefix = f"{prec}.{mode}.{field}.n{int(n_tracks).bit_length() - 1}."
@@ -433,10 +434,13 @@ def run_sweep(args, local: int, rank: int, tune_file: str):
         b = _prefix_batch(_tile_batch(full, k) if k > 1 else full, n)
         out = tkf.alloc_outputs(n, dev, steps=True)
         for variant in ("fp64", "mixed", "mixed_learned"):
-            policies = [(True, True), (False, True), (True, False)] if n <= 10 ** 5 else [(True, True)]
-            for graph, autotune in policies:
+            # (graph, autotune, lanes a track): tuned (the tuner also tries 4 lanes a track below
+            # ~4e4 tracks), direct launches, the default shape, and 4 lanes a track forced
+            policies = ([(True, True, 0), (False, True, 0), (True, False, 0), (True, False, 4)] if n <= 10 ** 5
+                        else [(True, True, 0)])
+            for graph, autotune, lanes in policies:
                 opts = tkf.Options(precision=tkf.FP64 if variant == "fp64" else tkf.MIXED, mass=synth.MUON_MASS,
-                                   graph=graph, autotune=autotune)
+                                   graph=graph, autotune=autotune, lanes_per_track=lanes)
                 if variant.endswith("learned"):
                     opts.step_mode, opts.mlp = tkf.STEP_LEARNED, proposer
                 for _ in range(max(3, args.warmup)):
@@ -455,9 +459,12 @@ def run_sweep(args, local: int, rank: int, tune_file: str):
                     torch.cuda.synchronize()
                 ms = e0.elapsed_time(e1) / reps
                 status = out.status.cpu().numpy().view(np.uint32)
+                shape = tuned_shape(tune_file, variant, n, "grid", not autotune)
+                if lanes == 4:
+                    shape = [128, 2, 8, 255, 4]
                 print(json.dumps({"sweep": "point", "tracks_per_launch": n, "variant": variant, "cuda_graph": graph,
-                                  "autotune": autotune, "tracks_per_s": n / (ms * 1e-3), "ms_per_launch": ms,
-                                  "reps": reps, "launch_shape": tuned_shape(tune_file, variant, n, "grid", not autotune),
+                                  "autotune": autotune, "lanes_per_track": lanes, "tracks_per_s": n / (ms * 1e-3),
+                                  "ms_per_launch": ms, "reps": reps, "launch_shape": shape,
                                   "fit_status_ok": float(np.mean(status == 0)),
                                   "clocks": clk.summary()}), flush=True)
         del b, out
@@ -613,9 +620,10 @@ def main():
                            mass=w.mass,
                            graph=not args.no_graph, autotune=not args.no_autotune and args.shape is None)
         if args.shape:
-            th, bps, tpw, regs = (int(x) for x in args.shape.split(","))
+            th, bps, tpw, regs, *lanes = (int(x) for x in args.shape.split(","))
             opts.block_threads, opts.blocks_per_sm, opts.tracks_per_warp = th, bps, tpw
             opts.max_registers = 255 if variant == "fp64" or (variant == "mixed_fp32" and regs == 64) else regs
+            opts.lanes_per_track = lanes[0] if lanes and variant != "mixed_fp32" else 0
         if variant.endswith("learned"):
             opts.step_mode, opts.mlp = tkf.STEP_LEARNED, proposer
         out = tkf.alloc_outputs(n_tracks, dev.offsets.device, steps=True)
@@ -668,7 +676,8 @@ def main():
         kernel_ms = statistics.mean(kms)
         ms_max = max_over_ranks(ms, dist, f"cuda:{local}")
         results[variant] = {"ms": ms, "ms_max": ms_max, "kernel_ms": kernel_ms, "clocks": clk.summary(), "opts": opts,
-                            "shape": ([opts.block_threads, opts.blocks_per_sm, opts.tracks_per_warp, opts.max_registers]
+                            "shape": ([opts.block_threads, opts.blocks_per_sm, opts.tracks_per_warp, opts.max_registers,
+                                       opts.lanes_per_track or 1]
                                       if args.shape else
                                       tuned_shape(tune_file, variant, n_tracks, "grid" if args.workload == "map" else "uz",
                                                   args.no_autotune)),

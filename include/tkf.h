@@ -201,6 +201,14 @@ typedef struct tkf_fit_options {
    * information of these measurements) inflates it, for example by 100, so that the
    * measurements are not counted twice. */
   double seed_cov_scale;
+  /* Lanes a track (launch policy, no effect on the results): 0 = the default or tuned mapping,
+   * 1 = one lane a track, 4 = group-per-track (TKF_FP64 or TKF_MIXED, 255 registers, no record
+   * capture; at most 8 tracks a warp). In a group every lane steps the state, update and
+   * smoother; lane g transports derivative column g and computes row g of the covariance
+   * transport, exchanged by warp shuffles, which shortens each track's critical path when a
+   * batch is too small to fill the GPU one lane a track. TKF_FIT_AUTOTUNE also times the group
+   * mapping for small batches. */
+  uint32_t lanes_per_track;
 } tkf_fit_options;
 
 /* Autotuning: the first call of a launch class (precision, step mode, field kind, batch size

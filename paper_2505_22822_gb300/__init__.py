@@ -25,7 +25,8 @@ _ROOT = os.path.dirname(_HERE)
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "libtkf.so")
 _SOURCES = ["tkf_api.cu", "tkf_order.cu", "tkf_policy.cu", "tkf_fit_fp64.cu", "tkf_fit_mixed.cu",
-            "tkf_fit_mixed_r128.cu", "tkf_fit_mixed_r64.cu", "tkf_fit_mixed32.cu", "tkf_mlp.cu", "tkf_seed.cu"]
+            "tkf_fit_mixed_r128.cu", "tkf_fit_mixed_r64.cu", "tkf_fit_mixed32.cu", "tkf_mlp.cu", "tkf_seed.cu",
+            "tkf_fit_group.cu"]
 _lib = None
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
@@ -118,7 +119,7 @@ class FitOptions(ctypes.Structure):
                 ("flags", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
                 ("blocks_per_sm", ctypes.c_uint32), ("tracks_per_warp", ctypes.c_uint32),
                 ("max_registers", ctypes.c_uint32), ("kernel_events", ctypes.c_void_p),
-                ("seed_cov_scale", ctypes.c_double)]
+                ("seed_cov_scale", ctypes.c_double), ("lanes_per_track", ctypes.c_uint32)]
 
 
 class MlpTrainOptions(ctypes.Structure):
@@ -347,6 +348,7 @@ class Options:
     max_registers: int = 0        # explicit register cap (255; 128 or 64 for MIXED), else default or tuned
     kernel_events: object = None  # (begin, end) torch.cuda.Event pair around the fit kernel
     seed_cov_scale: float = 1.0   # factor on the seed covariance (a refit inflates it)
+    lanes_per_track: int = 0      # 0 default / tuned, 1, or 4 (group-per-track)
 
     def c(self) -> FitOptions:
         o = FitOptions()
@@ -366,6 +368,7 @@ class Options:
         o.tracks_per_warp = self.tracks_per_warp
         o.max_registers = self.max_registers
         o.seed_cov_scale = self.seed_cov_scale
+        o.lanes_per_track = self.lanes_per_track
         if self.kernel_events is not None:
             # the C array must outlive the call: kept on the options struct
             o._events = (ctypes.c_void_p * 2)(*(ev.cuda_event for ev in self.kernel_events))

@@ -309,6 +309,7 @@ void tkf_fit_options_default(tkf_fit_options* o) {
   o->max_registers = 0;
   o->kernel_events = nullptr;
   o->seed_cov_scale = 1.0;
+  o->lanes_per_track = 0;
 }
 
 // Validation shared by the fit entry points; `out` may be NULL only when `need_out` is false.
@@ -341,12 +342,13 @@ static tkf_status check_common(tkf_context ctx, tkf_geometry geo, tkf_field fiel
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": seed_cov_scale must be positive and finite");
   if ((o->flags & ~(TKF_FIT_AUTOTUNE | TKF_FIT_GRAPH | TKF_FIT_TEST_PROPOSAL_TIMEOUT)) != 0)
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": unknown flag");
-  if (!tkf::valid_block_shape(o->block_threads, o->blocks_per_sm, o->tracks_per_warp, o->max_registers, o->precision,
-                              o->records != nullptr))
+  if (!tkf::valid_block_shape(o->block_threads, o->blocks_per_sm, o->tracks_per_warp, o->max_registers,
+                              o->lanes_per_track, o->precision, o->records != nullptr))
     return fail(ctx, TKF_ERR_INVALID_ARG,
                 std::string(fn) + ": block shape needs threads 32, 64, 128 or 256 (at most 128 below 255 registers) "
                                   "and 1..32 blocks per SM (or 0, 0), 0..32 tracks per warp, and max_registers 0, 255, "
-                                  "or 128 / 64 for the mixed path without record capture");
+                                  "or 128 / 64 for the mixed path without record capture; lanes_per_track 0, 1, or 4 "
+                                  "(TKF_FP64 or TKF_MIXED, 255 registers, at most 8 tracks per warp, no record capture)");
   if (in->n_meas > 0xffffffffull)
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": n_meas exceeds 32-bit offsets");
   if (in->n_tracks == 0) return TKF_OK;
@@ -842,6 +844,11 @@ extern "C" tkf_status tkf_fit_noalloc(tkf_context ctx, tkf_geometry geo, tkf_fie
     shape.threads = int(o->block_threads);
     shape.blocks = int(o->blocks_per_sm) * ctx->sm_count;
     shape.regs = 255;
+  }
+  if (o->lanes_per_track > 1) {
+    shape.group = int(o->lanes_per_track);
+    shape.regs = 255;
+    shape.tracks_per_warp = 32 / shape.group;
   }
   if (o->tracks_per_warp) shape.tracks_per_warp = int(o->tracks_per_warp);
   if (o->max_registers) shape.regs = int(o->max_registers);

@@ -253,15 +253,17 @@ __device__ __forceinline__ void put_record(StepLearn& L, const float x[12], floa
 
 // ------------------------------------------------------------------ propagation
 // Adaptive RKN4 stepping of (r, T, lam) to the plane of `s`, transporting the derivative
-// columns of (phi, theta, q/p): dr[c], dT[c] (c = 0, 1, 2). Step control (Lund 2009a, safety
+// columns of (phi, theta, q/p): dr[c], dT[c] (c = 0, 1, 2); a lane of a group-per-track fit
+// carries one column (kCols = 1), with qcol = 1 for the q/p column (whose source term adds
+// T x kappa B) and 0 otherwise, and steps the state like the other lanes of its group. Step control (Lund 2009a, safety
 // factor 0.9): eps = h^2 |k1 - k2 - k3 + k4|_1; eps > tol rejects and sets
 // h_ctrl = |h| clamp(0.9 (tol/eps)^1/4, 1/4, 4); an accepted step limited by h_ctrl sets
 // h_ctrl = min(h_max, h_ctrl clamp(0.9 (tol/eps)^1/4, 1/4, 4)). Each step aims at the plane's
 // intersection with the parabola r + s T + s^2/2 k1; within surf_tol a second-order Taylor
 // step (state and columns) lands on the plane.
-template <int kMode, class F>
+template <int kMode, int kCols, class F>
 __device__ uint32_t propagate(const F& fld, const OptionsDev& o, const Surf& s, double r[3], double T[3],
-                              double lam, double dr[3][3], double dT[3][3], double& h_ctrl,
+                              double lam, double dr[kCols][3], double dT[kCols][3], double qcol, double& h_ctrl,
                               uint32_t& attempts, uint32_t& rejected, double kend[3], StepLearn& L) {
   uint32_t st = 0;
   bool first = true;
@@ -280,13 +282,13 @@ __device__ uint32_t propagate(const F& fld, const OptionsDev& o, const Surf& s, 
       if (oof) st |= TKF_TRACK_OUT_OF_FIELD;
       const double sp = parabolic_path(dist, a, dot3(s.n, k1)), sp2 = 0.5 * sp * sp;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
+      for (int c = 0; c < kCols; ++c) {
         double q[3];
         cross(dT[c], Bt1, q);
-        if (c == 2) {
+        if (kCols == 1 || c == 2) {
           double e[3], Bk[3] = {kKappa * B1[0], kKappa * B1[1], kKappa * B1[2]};
           cross(T, Bk, e);
-          for (int i = 0; i < 3; ++i) q[i] += e[i];
+          for (int i = 0; i < 3; ++i) q[i] += kCols == 1 ? qcol * e[i] : e[i];
         }
         for (int i = 0; i < 3; ++i) {
           dr[c][i] += sp * dT[c][i] + sp2 * q[i];
@@ -354,38 +356,38 @@ __device__ uint32_t propagate(const F& fld, const OptionsDev& o, const Surf& s, 
       if (limited && eps > 0.0) put_record(L, x, float(log(fabs(h) * sqrt(sqrt(o.tol / eps)))));
     // derivative columns through the accepted step (dB/dr neglected)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < kCols; ++c) {
       double q1[3], q2[3], q3[3], q4[3], u2[3], u3[3], u4[3];
       cross(dT[c], Bt1, q1);
-      if (c == 2) {
+      if (kCols == 1 || c == 2) {
         double e[3];
         double Bk1[3] = {kKappa * B1[0], kKappa * B1[1], kKappa * B1[2]};
         cross(T, Bk1, e);
-        for (int i = 0; i < 3; ++i) q1[i] += e[i];
+        for (int i = 0; i < 3; ++i) q1[i] += kCols == 1 ? qcol * e[i] : e[i];
       }
       for (int i = 0; i < 3; ++i) u2[i] = dT[c][i] + h2 * q1[i];
       cross(u2, Bt2, q2);
-      if (c == 2) {
+      if (kCols == 1 || c == 2) {
         double e[3];
         double Bk2[3] = {kKappa * B2[0], kKappa * B2[1], kKappa * B2[2]};
         cross(T2, Bk2, e);
-        for (int i = 0; i < 3; ++i) q2[i] += e[i];
+        for (int i = 0; i < 3; ++i) q2[i] += kCols == 1 ? qcol * e[i] : e[i];
       }
       for (int i = 0; i < 3; ++i) u3[i] = dT[c][i] + h2 * q2[i];
       cross(u3, Bt2, q3);
-      if (c == 2) {
+      if (kCols == 1 || c == 2) {
         double e[3];
         double Bk2[3] = {kKappa * B2[0], kKappa * B2[1], kKappa * B2[2]};
         cross(T3, Bk2, e);
-        for (int i = 0; i < 3; ++i) q3[i] += e[i];
+        for (int i = 0; i < 3; ++i) q3[i] += kCols == 1 ? qcol * e[i] : e[i];
       }
       for (int i = 0; i < 3; ++i) u4[i] = dT[c][i] + h * q3[i];
       cross(u4, Bt4, q4);
-      if (c == 2) {
+      if (kCols == 1 || c == 2) {
         double e[3];
         double Bk4[3] = {kKappa * B4[0], kKappa * B4[1], kKappa * B4[2]};
         cross(T4, Bk4, e);
-        for (int i = 0; i < 3; ++i) q4[i] += e[i];
+        for (int i = 0; i < 3; ++i) q4[i] += kCols == 1 ? qcol * e[i] : e[i];
       }
       for (int i = 0; i < 3; ++i) {
         dr[c][i] += h * dT[c][i] + h * h6 * (q1[i] + q2[i] + q3[i]);
@@ -430,9 +432,10 @@ __device__ __forceinline__ float parabolic_path_f(float d, float a, float b) {
   return s;
 }
 
-template <int kMode, class F>
+template <int kMode, int kCols, class F>
 __device__ uint32_t propagate_mixed(const F& fld, const OptionsDev& o, const Surf& s, const float nf[3], double r[3],
-                                    double T[3], double lam, float dr[3][3], float dT[3][3], float& h_ctrl,
+                                    double T[3], double lam, float dr[kCols][3], float dT[kCols][3], float qcol,
+                                    float& h_ctrl,
                                     uint32_t& attempts, uint32_t& rejected, float kend[3], StepLearn& L) {
   uint32_t st = 0;
   bool first = true;
@@ -455,13 +458,13 @@ __device__ uint32_t propagate_mixed(const F& fld, const OptionsDev& o, const Sur
       if (oof) st |= TKF_TRACK_OUT_OF_FIELD;
       const float sp = parabolic_path_f(df, a, dotr(nf, k1)), sp2 = 0.5f * sp * sp;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
+      for (int c = 0; c < kCols; ++c) {
         float q[3];
         cross(dT[c], Bt1, q);
-        if (c == 2) {
+        if (kCols == 1 || c == 2) {
           float e[3], Bk[3] = {float(kKappa) * B1[0], float(kKappa) * B1[1], float(kKappa) * B1[2]};
           cross(Tf, Bk, e);
-          for (int i = 0; i < 3; ++i) q[i] += e[i];
+          for (int i = 0; i < 3; ++i) q[i] += kCols == 1 ? qcol * e[i] : e[i];
         }
         for (int i = 0; i < 3; ++i) {
           dr[c][i] += sp * dT[c][i] + sp2 * q[i];
@@ -524,34 +527,34 @@ __device__ uint32_t propagate_mixed(const F& fld, const OptionsDev& o, const Sur
     if constexpr (kMode == kRecord)  // steps the control limited: the proposals' domain
       if (limited && eps > 0.0f) put_record(L, x, logf(fabsf(h) * sqrtf(sqrtf(tol / eps))));
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < kCols; ++c) {
       float q1[3], q2[3], q3[3], q4[3], u2[3], u3[3], u4[3];
       cross(dT[c], Bt1, q1);
-      if (c == 2) {
+      if (kCols == 1 || c == 2) {
         float e[3], Bk[3] = {float(kKappa) * B1[0], float(kKappa) * B1[1], float(kKappa) * B1[2]};
         cross(Tf, Bk, e);
-        for (int i = 0; i < 3; ++i) q1[i] += e[i];
+        for (int i = 0; i < 3; ++i) q1[i] += kCols == 1 ? qcol * e[i] : e[i];
       }
       for (int i = 0; i < 3; ++i) u2[i] = dT[c][i] + h2 * q1[i];
       cross(u2, Bt2, q2);
-      if (c == 2) {
+      if (kCols == 1 || c == 2) {
         float e[3], Bk[3] = {float(kKappa) * B2[0], float(kKappa) * B2[1], float(kKappa) * B2[2]};
         cross(T2, Bk, e);
-        for (int i = 0; i < 3; ++i) q2[i] += e[i];
+        for (int i = 0; i < 3; ++i) q2[i] += kCols == 1 ? qcol * e[i] : e[i];
       }
       for (int i = 0; i < 3; ++i) u3[i] = dT[c][i] + h2 * q2[i];
       cross(u3, Bt2, q3);
-      if (c == 2) {
+      if (kCols == 1 || c == 2) {
         float e[3], Bk[3] = {float(kKappa) * B2[0], float(kKappa) * B2[1], float(kKappa) * B2[2]};
         cross(T3, Bk, e);
-        for (int i = 0; i < 3; ++i) q3[i] += e[i];
+        for (int i = 0; i < 3; ++i) q3[i] += kCols == 1 ? qcol * e[i] : e[i];
       }
       for (int i = 0; i < 3; ++i) u4[i] = dT[c][i] + h * q3[i];
       cross(u4, Bt4, q4);
-      if (c == 2) {
+      if (kCols == 1 || c == 2) {
         float e[3], Bk[3] = {float(kKappa) * B4[0], float(kKappa) * B4[1], float(kKappa) * B4[2]};
         cross(T4, Bk, e);
-        for (int i = 0; i < 3; ++i) q4[i] += e[i];
+        for (int i = 0; i < 3; ++i) q4[i] += kCols == 1 ? qcol * e[i] : e[i];
       }
       for (int i = 0; i < 3; ++i) {
         dr[c][i] += h * dT[c][i] + h * h6 * (q1[i] + q2[i] + q3[i]);
@@ -744,10 +747,111 @@ __device__ __forceinline__ float cov_to_f(float x) { return x; }
 
 __host__ __device__ constexpr int state_doubles(int place) { return place == 0 ? 0 : (place == 1 ? 25 : 45); }
 
-template <int kPrec, int kMode, int kPlace, class F>
+// ------------------------------------------------------------------ group-per-track helpers
+// A group of kG lanes may share one track (kG = 4): every lane steps the state, the update and
+// the smoother identically (same data, same instructions, so the group never diverges), lane g
+// of the group transports derivative column g (g < 3), and lane r computes row r of the
+// covariance transport J (C + Q) J^T; shuffles within the group (width kG) assemble the full
+// Jacobian and covariance in every lane. Each element is computed by the same operations in the
+// same order as in the one-lane-per-track fit, so both give identical results.
+template <int kG, class T>
+__device__ __forceinline__ T gshfl(uint32_t gmask, T v, int src) {
+  if constexpr (kG == 1) {
+    return v;
+  } else {
+    return __shfl_sync(gmask, v, src, kG);
+  }
+}
+
+// a[gl] for a lane index gl in 0..3, by selects (no dynamic register indexing)
+template <class T>
+__device__ __forceinline__ T pick4(uint32_t gl, T a0, T a1, T a2, T a3) {
+  return gl == 0 ? a0 : (gl == 1 ? a1 : (gl == 2 ? a2 : a3));
+}
+
+// Rows 0..3 of one Jacobian column at the target: the derivative (x, t) of position and
+// direction, moved along T to the plane (path correction), in the target's bound frame.
+template <class R>
+__device__ __forceinline__ void jac_column(const R n[3], const R u[3], const R v[3], const R T[3], const R kend[3],
+                                           R inv_nT, R sp2, R cp2, R st2, R ct2, R inv_st, R x[3], R t[3],
+                                           R out[4]) {
+  const R ds = -dotr(n, x) * inv_nT;
+  for (int j = 0; j < 3; ++j) {
+    x[j] += T[j] * ds;
+    t[j] += kend[j] * ds;
+  }
+  out[0] = dotr(u, x);
+  out[1] = dotr(v, x);
+  out[2] = (-sp2 * t[0] + cp2 * t[1]) * inv_st;
+  out[3] = ct2 * cp2 * t[0] + ct2 * sp2 * t[1] - st2 * t[2];
+}
+
+// C <- J C J^T for the 5x5 packed symmetric C (J row 4 = e_4), over rows 0..3 of J; with kG = 4
+// lane gl computes row gl and the group exchanges the results.
+template <int kG, class R>
+__device__ __forceinline__ void transport_cov(const R J[5][5], R Cw[15], uint32_t gl, uint32_t gmask) {
+  if constexpr (kG == 1) {
+    R M[5][5];
+#pragma unroll
+    for (int r0 = 0; r0 < 4; ++r0)
+#pragma unroll
+      for (int c0 = 0; c0 < 5; ++c0) {
+        R acc = R(0);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) acc += J[r0][q] * Cw[S(q, c0)];
+        M[r0][c0] = acc;
+      }
+#pragma unroll
+    for (int c0 = 0; c0 < 5; ++c0) M[4][c0] = Cw[S(4, c0)];
+#pragma unroll
+    for (int r0 = 0; r0 < 5; ++r0)
+#pragma unroll
+      for (int c0 = r0; c0 < 5; ++c0) {
+        R acc;
+        if (c0 == 4) {
+          acc = M[r0][4];
+        } else {
+          acc = R(0);
+#pragma unroll
+          for (int q = 0; q < 5; ++q) acc += M[r0][q] * J[c0][q];
+        }
+        Cw[S(r0, c0)] = acc;
+      }
+  } else {
+    static_assert(kG == 4, "groups of 4 lanes");
+    R Jr[5], Mr[5], Cr[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) Jr[q] = pick4(gl, J[0][q], J[1][q], J[2][q], J[3][q]);
+#pragma unroll
+    for (int c0 = 0; c0 < 5; ++c0) {
+      R acc = R(0);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) acc += Jr[q] * Cw[S(q, c0)];
+      Mr[c0] = acc;
+    }
+#pragma unroll
+    for (int c0 = 0; c0 < 4; ++c0) {
+      R acc = R(0);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) acc += Mr[q] * J[c0][q];
+      Cr[c0] = acc;
+    }
+    Cr[4] = Mr[4];
+#pragma unroll
+    for (int r0 = 0; r0 < 4; ++r0)
+#pragma unroll
+      for (int c0 = r0; c0 < 5; ++c0) Cw[S(r0, c0)] = gshfl<kG>(gmask, Cr[c0], r0);
+  }
+}
+
+template <int kPrec, int kMode, int kG, int kPlace, class F>
 __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
-                          SmootherStore<kPlace, typename CovType<kPrec>::type> st) {
+                          SmootherStore<kPlace, typename CovType<kPrec>::type> st, uint32_t gl = 0,
+                          uint32_t gmask = 0xffffffffu) {
   constexpr bool kMixed = kPrec != 0;
+  constexpr int kCols = kG == 1 ? 3 : 1;  // derivative columns a lane transports
+  static_assert(kG == 1 || kMode != kRecord, "record capture runs one lane per track");
+  const bool writer = kG == 1 || gl == 0;  // the lane that writes the group's results
   using U = typename CovType<kPrec>::type;
   const uint32_t n = a.stride;  // SoA row stride of seeds and outputs
   const uint32_t b0 = a.offsets[i], b1 = a.offsets[i + 1];
@@ -772,6 +876,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
     }
   }
   if (M == 0 && status == 0) {  // nothing to fit (no entry, or no measurement): the seed
+    if (!writer) return;
     for (int j = 0; j < 5; ++j) a.par[size_t(j) * n + i] = p[j];
     for (int j = 0; j < 15; ++j) a.cov[size_t(j) * n + i] = cov_to_d(C[j]);
     a.chi2[i] = 0.0;
@@ -820,11 +925,20 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
       if (status & kFatal) break;
       double r[3];
       for (int j = 0; j < 3; ++j) r[j] = sp.c[j] + p[0] * sp.u[j] + p[1] * sp.v[j];
-      double dr[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-      double dT[3][3] = {{-sth * sph, sth * cph, 0.0}, {cth * cph, cth * sph, -sth}, {0, 0, 0}};
+      double dr[kCols][3], dT[kCols][3];
+      const double dphi[3] = {-sth * sph, sth * cph, 0.0}, dtheta[3] = {cth * cph, cth * sph, -sth};
+#pragma unroll
+      for (int c = 0; c < kCols; ++c)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const uint32_t col = kG == 1 ? uint32_t(c) : gl;  // this lane's column
+          dr[c][j] = 0.0;
+          dT[c][j] = col == 0 ? dphi[j] : (col == 1 ? dtheta[j] : 0.0);
+        }
+      const double qcol = gl == 2 ? 1.0 : 0.0;
       double kend[3];
-      status |= propagate<kMode == kRecord ? kRecord : kPlain>(fld, a.opt, s, r, T, lam, dr, dT, h_ctrl, attempts,
-                                                              rejected, kend, learn);
+      status |= propagate<kMode == kRecord ? kRecord : kPlain, kCols>(fld, a.opt, s, r, T, lam, dr, dT, qcol, h_ctrl,
+                                                                      attempts, rejected, kend, learn);
       if (status & kFatal) break;
       // ---- bound parameters at the target and the transport Jacobian (path correction)
       const double inv_norm = 1.0 / sqrt(dot3(T, T));
@@ -836,23 +950,24 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
       sp2 = tn[1] * inv_st;
       const double inv_nT = 1.0 / dot3(s.n, T);
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        double x[3], t[3];
+      for (int c = 0; c < 2 + kCols; ++c) {  // u, v, then this lane's derivative columns
+        double x[3], t[3], out[4];
         for (int j = 0; j < 3; ++j) {
           x[j] = (c == 0) ? sp.u[j] : (c == 1) ? sp.v[j] : dr[c - 2][j];
           t[j] = (c < 2) ? 0.0 : dT[c - 2][j];
         }
-        const double ds = -dot3(s.n, x) * inv_nT;
-        for (int j = 0; j < 3; ++j) {
-          x[j] += T[j] * ds;
-          t[j] += kend[j] * ds;
-        }
-        J[0][c] = dot3(s.u, x);
-        J[1][c] = dot3(s.v, x);
-        J[2][c] = (-sp2 * t[0] + cp2 * t[1]) * inv_st;
-        J[3][c] = ct2 * cp2 * t[0] + ct2 * sp2 * t[1] - st2 * t[2];
-        J[4][c] = (c == 4) ? 1.0 : 0.0;
+        jac_column(s.n, s.u, s.v, T, kend, inv_nT, sp2, cp2, st2, ct2, inv_st, x, t, out);
+        for (int rr = 0; rr < 4; ++rr) J[rr][c] = out[rr];
       }
+      if constexpr (kG > 1) {
+        const double own[4] = {J[0][2], J[1][2], J[2][2], J[3][2]};
+#pragma unroll
+        for (int c = 2; c < 5; ++c)
+#pragma unroll
+          for (int rr = 0; rr < 4; ++rr) J[rr][c] = gshfl<kG>(gmask, own[rr], c - 2);
+      }
+#pragma unroll
+      for (int c = 0; c < 5; ++c) J[4][c] = (c == 4) ? 1.0 : 0.0;
       const double d[3] = {r[0] - s.c[0], r[1] - s.c[1], r[2] - s.c[2]};
       p[0] = dot3(s.u, d);
       p[1] = dot3(s.v, d);
@@ -862,32 +977,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
       // ---- C_pred = J (C + Q) J^T, Q = diag(0, 0, th0^2/sin^2(theta), th0^2, 0)
       C[S(2, 2)] += th0sq / (sth * sth);
       C[S(3, 3)] += th0sq;
-      double M[5][5];
-#pragma unroll
-      for (int r0 = 0; r0 < 4; ++r0)
-#pragma unroll
-        for (int c0 = 0; c0 < 5; ++c0) {
-          double acc = 0.0;
-#pragma unroll
-          for (int q = 0; q < 5; ++q) acc += J[r0][q] * C[S(q, c0)];
-          M[r0][c0] = acc;
-        }
-#pragma unroll
-      for (int c0 = 0; c0 < 5; ++c0) M[4][c0] = C[S(4, c0)];
-#pragma unroll
-      for (int r0 = 0; r0 < 5; ++r0)
-#pragma unroll
-        for (int c0 = r0; c0 < 5; ++c0) {
-          double acc;
-          if (c0 == 4) {
-            acc = M[r0][4];
-          } else {
-            acc = 0.0;
-#pragma unroll
-            for (int q = 0; q < 5; ++q) acc += M[r0][q] * J[c0][q];
-          }
-          C[S(r0, c0)] = acc;
-        }
+      transport_cov<kG>(J, C, gl, gmask);
       } else {
       // ---- mixed precision: material, propagation, Jacobian and covariance transport in FP32
       const float Tm[3] = {d2f(sth * cph), d2f(sth * sph), d2f(cth)};
@@ -899,12 +989,21 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
       double r[3];
       for (int j = 0; j < 3; ++j) r[j] = sp.c[j] + p[0] * sp.u[j] + p[1] * sp.v[j];
       const float fsth = d2f(sth), fcth = d2f(cth), fsph = d2f(sph), fcph = d2f(cph);
-      float dr[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-      float dT[3][3] = {{-fsth * fsph, fsth * fcph, 0.0f}, {fcth * fcph, fcth * fsph, -fsth}, {0, 0, 0}};
+      float dr[kCols][3], dT[kCols][3];
+      const float dphi[3] = {-fsth * fsph, fsth * fcph, 0.0f}, dtheta[3] = {fcth * fcph, fcth * fsph, -fsth};
+#pragma unroll
+      for (int c = 0; c < kCols; ++c)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const uint32_t col = kG == 1 ? uint32_t(c) : gl;  // this lane's column
+          dr[c][j] = 0.0f;
+          dT[c][j] = col == 0 ? dphi[j] : (col == 1 ? dtheta[j] : 0.0f);
+        }
+      const float qcol = gl == 2 ? 1.0f : 0.0f;
       const float* nf = s.nf;
       float kend[3];
-      status |= propagate_mixed<kMode == kRecord ? kRecord : kPlain>(fld, a.opt, s, nf, r, T, lam, dr, dT, h_ctrl_f,
-                                                                    attempts, rejected, kend, learn);
+      status |= propagate_mixed<kMode == kRecord ? kRecord : kPlain, kCols>(fld, a.opt, s, nf, r, T, lam, dr, dT, qcol,
+                                                                            h_ctrl_f, attempts, rejected, kend, learn);
       if (status & kFatal) break;
       // direction at the target in FP64 from FP32-seeded Newton steps (relative error ~1e-14)
       const double t2 = dot3(T, T), e2 = t2 - 1.0;
@@ -935,23 +1034,24 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
       const float fst = d2f(st2), fct = d2f(ct2), fcp = d2f(cp2), fsp = d2f(sp2), finv_st = d2f(inv_st);
       float Jf[5][5];
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        float x[3], t[3];
+      for (int c = 0; c < 2 + kCols; ++c) {  // u, v, then this lane's derivative columns
+        float x[3], t[3], out[4];
         for (int j = 0; j < 3; ++j) {
           x[j] = (c == 0) ? sp.uf[j] : (c == 1) ? sp.vf[j] : dr[c - 2][j];
           t[j] = (c < 2) ? 0.0f : dT[c - 2][j];
         }
-        const float ds = -dotr(nf, x) * inv_nT;
-        for (int j = 0; j < 3; ++j) {
-          x[j] += Tf[j] * ds;
-          t[j] += kend[j] * ds;
-        }
-        Jf[0][c] = dotr(uf, x);
-        Jf[1][c] = dotr(vf, x);
-        Jf[2][c] = (-fsp * t[0] + fcp * t[1]) * finv_st;
-        Jf[3][c] = fct * fcp * t[0] + fct * fsp * t[1] - fst * t[2];
-        Jf[4][c] = (c == 4) ? 1.0f : 0.0f;
+        jac_column(nf, uf, vf, Tf, kend, inv_nT, fsp, fcp, fst, fct, finv_st, x, t, out);
+        for (int rr = 0; rr < 4; ++rr) Jf[rr][c] = out[rr];
       }
+      if constexpr (kG > 1) {
+        const float own[4] = {Jf[0][2], Jf[1][2], Jf[2][2], Jf[3][2]};
+#pragma unroll
+        for (int c = 2; c < 5; ++c)
+#pragma unroll
+          for (int rr = 0; rr < 4; ++rr) Jf[rr][c] = gshfl<kG>(gmask, own[rr], c - 2);
+      }
+#pragma unroll
+      for (int c = 0; c < 5; ++c) Jf[4][c] = (c == 4) ? 1.0f : 0.0f;
       const double d[3] = {r[0] - s.c[0], r[1] - s.c[1], r[2] - s.c[2]};
       p[0] = dot3(s.u, d);
       p[1] = dot3(s.v, d);
@@ -964,32 +1064,9 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
       for (int j = 0; j < 15; ++j) Cf[j] = cov_to_f(C[j]);
       Cf[S(2, 2)] += th0sq / (fsth * fsth);
       Cf[S(3, 3)] += th0sq;
-      float M[5][5];
+      transport_cov<kG>(Jf, Cf, gl, gmask);
 #pragma unroll
-      for (int r0 = 0; r0 < 4; ++r0)
-#pragma unroll
-        for (int c0 = 0; c0 < 5; ++c0) {
-          float acc = 0.0f;
-#pragma unroll
-          for (int q = 0; q < 5; ++q) acc += Jf[r0][q] * Cf[S(q, c0)];
-          M[r0][c0] = acc;
-        }
-#pragma unroll
-      for (int c0 = 0; c0 < 5; ++c0) M[4][c0] = Cf[S(4, c0)];
-#pragma unroll
-      for (int r0 = 0; r0 < 5; ++r0)
-#pragma unroll
-        for (int c0 = r0; c0 < 5; ++c0) {
-          float acc;
-          if (c0 == 4) {
-            acc = M[r0][4];
-          } else {
-            acc = 0.0f;
-#pragma unroll
-            for (int q = 0; q < 5; ++q) acc += M[r0][q] * Jf[c0][q];
-          }
-          C[S(r0, c0)] = cov_from_f<U>(acc);
-        }
+      for (int j = 0; j < 15; ++j) C[j] = cov_from_f<U>(Cf[j]);
 #pragma unroll
       for (int r0 = 0; r0 < 5; ++r0)
 #pragma unroll
@@ -1162,6 +1239,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
     chi2 = nan;
   }
   if (M < 3 && !bad_offsets) status |= TKF_TRACK_TOO_FEW_HITS;
+  if (!writer) return;
 #pragma unroll
   for (int j = 0; j < 5; ++j) a.par[size_t(j) * n + i] = st.dl(j);
 #pragma unroll
@@ -1189,7 +1267,9 @@ __host__ __device__ constexpr int reg_min_blocks(int regs) { return regs >= 255 
 // warps would take the L1 capacity those spills need: launch +6 %).
 __host__ __device__ constexpr int reg_state_place(int regs) { return regs == 128 ? 2 : 0; }
 
-template <int kPrec, int kMode, int kRegs, class F>
+// kG lanes a track (1, or 4 for the group-per-track mapping): a warp takes tpw <= 32 / kG tracks
+// at a time, lanes g kG .. g kG + kG - 1 fit track base + g together.
+template <int kPrec, int kMode, int kRegs, int kG, class F>
 __global__ void __launch_bounds__(reg_block_threads(kRegs), reg_min_blocks(kRegs))
     fit_persistent_kernel(FitArgs a, F fld, const uint32_t* __restrict__ perm, uint32_t* __restrict__ counter,
                           uint32_t tpw) {
@@ -1198,13 +1278,15 @@ __global__ void __launch_bounds__(reg_block_threads(kRegs), reg_min_blocks(kRegs
   SmootherStore<kPlace, typename CovType<kPrec>::type> st{};
   if constexpr (kPlace != 0) st.s = smem_state + threadIdx.x * state_doubles(kPlace);
   const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t g = lane / kG, gl = lane % kG;
+  const uint32_t gmask = kG == 1 ? 0xffffffffu : ((1u << kG) - 1u) << (g * kG);
   for (;;) {
     uint32_t base = 0;
     if (lane == 0) base = atomicAdd(counter, tpw);
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= a.n_tracks) break;
-    const uint32_t j = base + lane;
-    if (lane < tpw && j < a.n_tracks) fit_track<kPrec, kMode>(a, fld, perm[j], st);
+    const uint32_t j = base + g;
+    if (g < tpw && j < a.n_tracks) fit_track<kPrec, kMode, kG>(a, fld, perm[j], st, gl, gmask);
   }
 }
 
@@ -1517,42 +1599,43 @@ inline cudaError_t propose_fields(const FitArgs& a, const FieldDev& f, float* h0
   return launch_propose(a, grid_policy(f), h0, stream);
 }
 
-// Launches the persistent fit for one precision, step mode and field.
-template <int kPrec, int kMode, int kRegs, class F>
+// Launches the persistent fit for one precision, step mode, lanes a track and field.
+template <int kPrec, int kMode, int kRegs, int kG, class F>
 cudaError_t launch_persistent(const FitArgs& a, const F& fld, const uint32_t* perm, uint32_t* counter,
                               LaunchShape shape, cudaStream_t stream) {
-  if (shape.threads > reg_block_threads(kRegs)) return cudaErrorInvalidConfiguration;
+  if (shape.threads > reg_block_threads(kRegs) || shape.tracks_per_warp * kG > 32) return cudaErrorInvalidConfiguration;
   const int place = kPrec == 2 ? 0 : reg_state_place(kRegs);
   const size_t smem = size_t(shape.threads) * state_doubles(place) * sizeof(double);
-  fit_persistent_kernel<kPrec, kMode, kRegs>
+  fit_persistent_kernel<kPrec, kMode, kRegs, kG>
       <<<shape.blocks, shape.threads, smem, stream>>>(a, fld, perm, counter, uint32_t(shape.tracks_per_warp));
   return cudaGetLastError();
 }
 
-// Record capture (training only) is built with the full register file alone.
-template <int kPrec, int kRegs, class F>
+// Record capture (training only) is built with the full register file and one lane a track.
+template <int kPrec, int kRegs, int kG, class F>
 cudaError_t launch_mode(const FitArgs& a, const F& fld, int mode, const uint32_t* perm, uint32_t* counter,
                         LaunchShape shape, cudaStream_t stream) {
-  if (mode == kLearned) return launch_persistent<kPrec, kLearned, kRegs>(a, fld, perm, counter, shape, stream);
+  if (mode == kLearned) return launch_persistent<kPrec, kLearned, kRegs, kG>(a, fld, perm, counter, shape, stream);
   if (mode == kRecord) {
-    if constexpr (kRegs == 255 && kPrec != 2)
-      return launch_persistent<kPrec, kRecord, kRegs>(a, fld, perm, counter, shape, stream);
+    if constexpr (kRegs == 255 && kPrec != 2 && kG == 1)
+      return launch_persistent<kPrec, kRecord, kRegs, kG>(a, fld, perm, counter, shape, stream);
     return cudaErrorInvalidValue;
   }
-  return launch_persistent<kPrec, kPlain, kRegs>(a, fld, perm, counter, shape, stream);
+  return launch_persistent<kPrec, kPlain, kRegs, kG>(a, fld, perm, counter, shape, stream);
 }
 
-template <int kPrec, int kRegs>
+template <int kPrec, int kRegs, int kG = 1>
 cudaError_t launch_fields(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm, uint32_t* counter,
                           LaunchShape shape, cudaStream_t stream) {
   if (f.kind == TKF_FIELD_UNIFORM) {
     if (f.b[0] == 0.0 && f.b[1] == 0.0)
-      return launch_mode<kPrec, kRegs>(a, FieldUniformZ{f.b[2], float(f.b[2])}, mode, perm, counter, shape, stream);
-    return launch_mode<kPrec, kRegs>(
+      return launch_mode<kPrec, kRegs, kG>(a, FieldUniformZ{f.b[2], float(f.b[2])}, mode, perm, counter, shape,
+                                           stream);
+    return launch_mode<kPrec, kRegs, kG>(
         a, FieldUniform{{f.b[0], f.b[1], f.b[2]}, {float(f.b[0]), float(f.b[1]), float(f.b[2])}}, mode, perm, counter,
         shape, stream);
   }
-  return launch_mode<kPrec, kRegs>(a, grid_policy(f), mode, perm, counter, shape, stream);
+  return launch_mode<kPrec, kRegs, kG>(a, grid_policy(f), mode, perm, counter, shape, stream);
 }
 
 }  // namespace

@@ -115,13 +115,14 @@ struct SeedArgs {
 cudaError_t launch_estimate_seeds(const SeedArgs& a, const FieldDev& f, int sm_count, cudaStream_t stream);
 
 // Launch shape of the persistent fit: threads per block, blocks in the grid, tracks a warp
-// takes at a time (1..32, one per lane), and the register cap of the kernel variant (255, or
-// 128 / 64 for the mixed path, whose blocks then have at most 128 threads).
+// takes at a time (1..32 / group), the register cap of the kernel variant (255, or 128 / 64
+// for the mixed path, whose blocks then have at most 128 threads) and the lanes a track.
 struct LaunchShape {
   int threads = 128;
   int blocks = 0;
   int tracks_per_warp = 32;
   int regs = 255;
+  int group = 1;  // lanes a track: 1, or 4 (group-per-track: FP64 and mixed, 255 registers)
 };
 
 // Persistent fit launches per precision; mode 0 plain, 1 learned proposals, 2 record capture.
@@ -135,6 +136,8 @@ cudaError_t launch_fit_mixed_r64(const FitArgs& a, const FieldDev& f, int mode, 
                                  uint32_t* counter, LaunchShape shape, cudaStream_t stream);
 cudaError_t launch_fit_mixed32(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm, uint32_t* counter,
                                LaunchShape shape, cudaStream_t stream);
+cudaError_t launch_fit_group(const FitArgs& a, const FieldDev& f, int precision, int mode, const uint32_t* perm,
+                             uint32_t* counter, LaunchShape shape, cudaStream_t stream);
 
 // Enqueues the fit of every track in `a` on `stream`: track ordering, then the persistent fit.
 // With `timing`, events timing[0] and timing[1] are recorded right before and after the
@@ -152,7 +155,7 @@ namespace tkf {
 // the context's tuned one for the launch class (timing the candidates on the first call when
 // TKF_FIT_AUTOTUNE is set), else the default.
 bool valid_block_shape(uint32_t threads, uint32_t blocks_per_sm, uint32_t tracks_per_warp, uint32_t max_registers,
-                       int precision, bool record);
+                       uint32_t lanes_per_track, int precision, bool record);
 cudaError_t resolve_shape(tkf_context_s* ctx, const FitArgs& a, const FieldDev& f, int precision, const Workspace& ws,
                           const tkf_fit_options* o, cudaStream_t stream, LaunchShape* out);
 // Direct launch, or through the context's CUDA graph when `use_graph` (captured on the second
@@ -171,9 +174,9 @@ struct tkf_context_s {
   int device = 0;
   int sm_count = 0;
   std::string last_error;
-  // autotuner: best (threads, blocks per SM, tracks per warp, registers) per launch class;
+  // autotuner: best (threads, blocks per SM, tracks per warp, registers, lanes a track) per launch class;
   // optional cache file
-  std::map<std::string, std::array<int, 4>> tuned;
+  std::map<std::string, std::array<int, 5>> tuned;
   std::string tune_cache_path;
   // CUDA graph of the last repeated launch sequence
   cudaGraphExec_t graph_exec = nullptr;

@@ -31,16 +31,26 @@ constexpr Candidate kCandidates[] = {{32, 8, 255},   {64, 4, 255},   {128, 2, 25
                                      {64, 2, 255},   {128, 1, 255},  {128, 4, 128}, {64, 8, 128},
                                      {32, 16, 128},  {128, 8, 64},   {64, 16, 64},  {32, 32, 64}};
 // Tracks per warp: below one track per lane of every resident warp, fewer tracks per warp
-// spread the batch over more schedulers.
+// spread the batch over more schedulers. Small batches also try four lanes a track (full
+// register file, FP64 and mixed, 8 to 1 tracks a warp): every lane of a group transports one
+// derivative column and one row of the covariance transport, which shortens each track's
+// critical path when the batch cannot fill the GPU one lane a track.
 constexpr int kTracksPerWarp[] = {32, 16, 8, 4};
+constexpr int kGroupTracksPerWarp[] = {8, 4, 2, 1};
 constexpr int kResidentWarpsPerSm = 8;
 
 // Defaults without tuning: FP64 128 x 2 at 255 registers; mixed 128 x 4 at 128 registers (the
 // best single shape over the uniform-field and field-map batches); record capture keeps the
 // full register file (its kernels exist only there).
-std::array<int, 4> default_shape(int precision, bool record) {
-  if (precision == TKF_MIXED && !record) return {128, 4, 32, 128};
-  return {128, 2, 32, 255};
+std::array<int, 5> default_shape(int precision, bool record) {
+  if (precision == TKF_MIXED && !record) return {128, 4, 32, 128, 1};
+  return {128, 2, 32, 255, 1};
+}
+
+// Lanes a track the kernels of a precision and mode exist with.
+bool has_group(int precision, bool record, int group) {
+  if (group == 1) return true;
+  return group == 4 && !record && (precision == TKF_FP64 || precision == TKF_MIXED);
 }
 
 // Register caps the kernels of a precision exist at.
@@ -70,16 +80,18 @@ std::string tune_key(const FitArgs& a, const FieldDev& f, int precision, int sm_
   return buf;
 }
 
-LaunchShape make_shape(const std::array<int, 4>& c, int sm_count) {
+LaunchShape make_shape(const std::array<int, 5>& c, int sm_count) {
   LaunchShape s;
   s.threads = c[0];
   s.blocks = c[1] * sm_count;
   s.tracks_per_warp = c[2];
   s.regs = c[3];
+  s.group = c[4];
   return s;
 }
 
-// Cache file: one JSON object, "class": [threads, blocks_per_sm, tracks_per_warp, registers].
+// Cache file: one JSON object, "class": [threads, blocks_per_sm, tracks_per_warp, registers,
+// lanes_per_track].
 void save_cache(const tkf_context ctx) {
   if (ctx->tune_cache_path.empty()) return;
   const std::string tmp = ctx->tune_cache_path + ".tmp";
@@ -88,8 +100,8 @@ void save_cache(const tkf_context ctx) {
   fprintf(fp, "{\n");
   size_t k = 0;
   for (const auto& kv : ctx->tuned)
-    fprintf(fp, "  \"%s\": [%d, %d, %d, %d]%s\n", kv.first.c_str(), kv.second[0], kv.second[1], kv.second[2],
-            kv.second[3], ++k < ctx->tuned.size() ? "," : "");
+    fprintf(fp, "  \"%s\": [%d, %d, %d, %d, %d]%s\n", kv.first.c_str(), kv.second[0], kv.second[1], kv.second[2],
+            kv.second[3], kv.second[4], ++k < ctx->tuned.size() ? "," : "");
   fprintf(fp, "}\n");
   const bool ok = fclose(fp) == 0;
   if (ok) rename(tmp.c_str(), ctx->tune_cache_path.c_str());
@@ -102,7 +114,7 @@ bool valid_shape(int threads, int bps, int regs) {
 
 // Times every candidate on the call's inputs: one warm-up fit, then the best of two fits each.
 cudaError_t tune(tkf_context ctx, const FitArgs& a, const FieldDev& f, int precision, const Workspace& ws,
-                 cudaStream_t stream, std::array<int, 4>* best) {
+                 cudaStream_t stream, std::array<int, 5>* best) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -110,12 +122,15 @@ cudaError_t tune(tkf_context ctx, const FitArgs& a, const FieldDev& f, int preci
   *best = default_shape(precision, a.records != nullptr);
   if (e == cudaSuccess) e = launch_fit(a, f, precision, ws, make_shape(*best, ctx->sm_count), stream);
   const bool small = a.n_tracks < uint32_t(32 * kResidentWarpsPerSm * ctx->sm_count);
-  for (const int tpw : kTracksPerWarp) {
-    if (tpw != 32 && !small) break;
+  const bool record = a.records != nullptr;
+  for (int group : {1, 4}) {
+    if (group != 1 && (!small || !has_group(precision, record, group))) break;
+    for (const int tpw : (group == 1 ? kTracksPerWarp : kGroupTracksPerWarp)) {
+    if (group == 1 && tpw != 32 && !small) break;
     for (const Candidate& c : kCandidates) {
       if (e != cudaSuccess) break;
-      if (!has_regs(precision, c.regs)) continue;
-      const std::array<int, 4> cand = {c.threads, c.blocks_per_sm, tpw, c.regs};
+      if (!has_regs(precision, c.regs) || (group != 1 && c.regs != 255)) continue;
+      const std::array<int, 5> cand = {c.threads, c.blocks_per_sm, tpw, c.regs, group};
       const LaunchShape s = make_shape(cand, ctx->sm_count);
       for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
         e = cudaEventRecord(e0, stream);
@@ -129,6 +144,7 @@ cudaError_t tune(tkf_context ctx, const FitArgs& a, const FieldDev& f, int preci
           *best = cand;
         }
       }
+    }
     }
   }
   if (e0) cudaEventDestroy(e0);
@@ -152,6 +168,7 @@ std::string graph_key(const FitArgs& a, const FieldDev& f, int precision, const 
   k.put(shape.blocks);
   k.put(shape.tracks_per_warp);
   k.put(shape.regs);
+  k.put(shape.group);
   k.put(a.n_tracks);
   k.put(a.stride);
   k.put(a.n_meas);
@@ -191,7 +208,8 @@ void load_tune_cache(tkf_context ctx) {
   size_t n;
   while ((n = fread(buf, 1, sizeof(buf), fp)) > 0) text.append(buf, n);
   fclose(fp);
-  // entries "class": [threads, blocks_per_sm, tracks_per_warp, registers]; anything else is skipped
+  // entries "class": [threads, blocks_per_sm, tracks_per_warp, registers(, lanes_per_track)];
+  // anything else is skipped
   size_t pos = 0;
   while ((pos = text.find('"', pos)) != std::string::npos) {
     const size_t end = text.find('"', pos + 1);
@@ -201,10 +219,11 @@ void load_tune_cache(tkf_context ctx) {
     const size_t next = text.find('"', end + 1);
     pos = end + 1;
     if (lb == std::string::npos || (next != std::string::npos && next < lb)) continue;
-    int t = 0, b = 0, w = 0, r = 0;
-    if (sscanf(text.c_str() + lb, "[ %d , %d , %d , %d ]", &t, &b, &w, &r) == 4 && valid_shape(t, b, r) && w >= 1 &&
-        w <= 32)
-      ctx->tuned[key] = {t, b, w, r};
+    int t = 0, b = 0, w = 0, r = 0, g = 1;
+    const int got = sscanf(text.c_str() + lb, "[ %d , %d , %d , %d , %d ]", &t, &b, &w, &r, &g);
+    if (got == 4) g = 1;
+    if (got >= 4 && valid_shape(t, b, r) && (g == 1 || (g == 4 && r == 255)) && w >= 1 && w * g <= 32)
+      ctx->tuned[key] = {t, b, w, r, g};
   }
 }
 
@@ -216,8 +235,12 @@ void release_graph(tkf_context ctx) {
 }
 
 bool valid_block_shape(uint32_t threads, uint32_t blocks_per_sm, uint32_t tracks_per_warp, uint32_t max_registers,
-                       int precision, bool record) {
+                       uint32_t lanes_per_track, int precision, bool record) {
   if (tracks_per_warp > 32) return false;
+  if (lanes_per_track > 1) {
+    if (!has_group(precision, record, int(lanes_per_track))) return false;
+    if (tracks_per_warp * lanes_per_track > 32 || (max_registers != 0 && max_registers != 255)) return false;
+  }
   if (max_registers != 0 && max_registers != 255 && max_registers != 128 && max_registers != 64) return false;
   if (max_registers != 0 && (!has_regs(precision, int(max_registers)) || (max_registers != 255 && record)))
     return false;
@@ -227,17 +250,22 @@ bool valid_block_shape(uint32_t threads, uint32_t blocks_per_sm, uint32_t tracks
 
 cudaError_t resolve_shape(tkf_context ctx, const FitArgs& a, const FieldDev& f, int precision, const Workspace& ws,
                           const tkf_fit_options* o, cudaStream_t stream, LaunchShape* out) {
-  std::array<int, 4> shape = default_shape(precision, a.records != nullptr);
+  std::array<int, 5> shape = default_shape(precision, a.records != nullptr);
   const bool explicit_block = o->block_threads && o->blocks_per_sm;
   if (explicit_block) {
     shape[0] = int(o->block_threads);
     shape[1] = int(o->blocks_per_sm);
     shape[3] = 255;  // an explicit block shape runs the full register file unless told otherwise
   }
+  if (o->lanes_per_track > 1) {
+    shape[4] = int(o->lanes_per_track);
+    shape[3] = 255;
+    shape[2] = 32 / shape[4];
+  }
   if (o->tracks_per_warp) shape[2] = int(o->tracks_per_warp);
   if (o->max_registers) shape[3] = int(o->max_registers);
   *out = make_shape(shape, ctx->sm_count);
-  const bool any_explicit = explicit_block || o->tracks_per_warp || o->max_registers;
+  const bool any_explicit = explicit_block || o->tracks_per_warp || o->max_registers || o->lanes_per_track;
   if (any_explicit || !(o->flags & TKF_FIT_AUTOTUNE) || a.records) return cudaSuccess;
   const std::string key = tune_key(a, f, precision, ctx->sm_count);
   auto it = ctx->tuned.find(key);
@@ -248,7 +276,7 @@ cudaError_t resolve_shape(tkf_context ctx, const FitArgs& a, const FieldDev& f, 
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaError_t e = cudaStreamIsCapturing(stream, &cs);
   if (e != cudaSuccess || cs != cudaStreamCaptureStatusNone) return e;
-  std::array<int, 4> best;
+  std::array<int, 5> best;
   e = tune(ctx, a, f, precision, ws, stream, &best);
   if (e != cudaSuccess) return e;
   ctx->tuned[key] = best;

@@ -76,13 +76,16 @@ __device__ uint32_t seed_one(const SeedArgs& a, const F& fld, uint32_t i, double
   const uint32_t N = b1 - b0;
   // entries without a measurement (holes, passive surfaces) give no space point; the first
   // entry carries the seed and needs its measurement
+  // (no early exit inside the scan, so that the unrolled loads are all in flight together)
   uint32_t M = 0;
+  bool bad = false;
+#pragma unroll 4
   for (uint32_t e = 0; e < N; ++e) {
-    const uint32_t sid = a.sid[b0 + e];
-    if ((sid & ~TKF_SID_NO_MEASUREMENT) >= a.n_surf) return TKF_SEED_BAD_INPUT;
-    M += (sid & TKF_SID_NO_MEASUREMENT) ? 0u : 1u;
+    const uint32_t sid = __ldg(a.sid + b0 + e);
+    bad |= (sid & ~TKF_SID_NO_MEASUREMENT) >= a.n_surf;
+    M += (sid >> 31) ^ 1u;
   }
-  if (N > 0 && (a.sid[b0] & TKF_SID_NO_MEASUREMENT)) return TKF_SEED_BAD_INPUT;
+  if (bad || (N > 0 && (__ldg(a.sid + b0) & TKF_SID_NO_MEASUREMENT))) return TKF_SEED_BAD_INPUT;
   if (M < 3) return TKF_SEED_TOO_FEW_HITS;
   // the measured entries number 0, j1, j2 of the M
   const uint32_t j1 = a.first_three ? 1u : (M - 1) / 2, j2 = a.first_three ? 2u : M - 1;

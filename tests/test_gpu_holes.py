@@ -98,7 +98,9 @@ def test_edge_entries_without_measurement(ctx):
     np.testing.assert_array_equal(g["status"], o.status)
     assert list(g["ndf"][:5]) == [18, 4, 0, 16, 16]
     np.testing.assert_array_equal(g["par"][2], t.seed_par[2])
-    check(g, o, TOL64)
+    # track 1 keeps two measurements for five parameters: its result rests on the prior and
+    # moves by ~1e-9 under one-ulp input changes (the conditioning-aware reading applies)
+    check(g, o, TOL64, w=w, tracks=np.arange(t.n_tracks))
 
 
 def test_pulls_with_holes_on_the_gpu(ctx):

