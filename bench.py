@@ -60,7 +60,7 @@ FLOPS_MAP = {
 # ncu capture, divided by the capture's tracks; traffic grows with the tracks of a launch).
 # Keyed by (workload, variant, register cap of the launched kernel); a kernel change voids the
 # entry. Barrel, learned start, 64 registers: 20-event batch, 279,450 tracks, 128 x 8 blocks.
-TRAFFIC_PER_TRACK = {("barrel", "mixed_learned", 64): (5.721680e9 + 5.006209e9) / 279450}
+TRAFFIC_PER_TRACK = {("barrel", "mixed_learned", 64): (5.724735e9 + 4.941866e9) / 279450}
 TRAFFIC_CAPTURE = {("barrel", "mixed_learned", 64): "ncu capture of 279,450 tracks (20 events), scaled by tracks"}
 
 
@@ -725,8 +725,9 @@ def main():
     peak = fp64_peak_tflops(None)
     # the fit kernel's own duration, from the events the library records around it
     hv = results[head]
-    head_shape = hv["shape"] or [None] * 4
-    traffic_key = (args.workload, head, head_shape[3])
+    head_shape = hv["shape"] or [None] * 5
+    # the captured kernel: one lane a track (a group shape is another kernel)
+    traffic_key = (args.workload, head, head_shape[3]) if (head_shape[4:] or [1])[0] == 1 else None
     achieved = hv["flops"] / (hv["kernel_ms"] * 1e-3) / 1e12
     roof = {"bound": "alu", "kernel": f"fit_persistent_kernel<{head}>", "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak,

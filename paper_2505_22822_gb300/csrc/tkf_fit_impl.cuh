@@ -907,6 +907,12 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
   double h_ctrl = kMode == kLearned ? double(h_start) : a.opt.h_max;
   float h_ctrl_f = h_start;
   StepLearn learn{a.records, a.record_capacity, a.record_count, a.opt.h_max_f};
+  // group-per-track: lane gl keeps row gl of P and of E (and its element of dl), every lane
+  // keeps row 4 (gathered into `st` after the last measurement)
+  U Pg[5], P4[5], Eg[5], E44 = U(0);
+  double dlg = 0.0, dl4 = 0.0;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) Pg[c] = P4[c] = Eg[c] = U(0);
 
   for (int k = 0; k < N && !(status & kFatal); ++k) {
     const uint32_t m = b0 + k;
@@ -1073,6 +1079,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
         for (int c0 = 0; c0 < 5; ++c0) J[r0][c0] = cov_from_f<U>(Jf[r0][c0]);
       }
       // ---- smoother: R = P J^T (in place; J row 4 is e_4)
+      if constexpr (kG == 1) {
 #pragma unroll
       for (int r0 = 0; r0 < 5; ++r0) {
         U row[5];
@@ -1086,6 +1093,27 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
         row[4] = st.P(r0, 4);
 #pragma unroll
         for (int c0 = 0; c0 < 5; ++c0) st.P(r0, c0) = row[c0];
+      }
+      } else {
+        U rg[5], r4[5];
+#pragma unroll
+        for (int c0 = 0; c0 < 4; ++c0) {
+          U acc = 0, acc4 = 0;
+#pragma unroll
+          for (int q = 0; q < 5; ++q) {
+            acc += Pg[q] * J[c0][q];
+            acc4 += P4[q] * J[c0][q];
+          }
+          rg[c0] = acc;
+          r4[c0] = acc4;
+        }
+        rg[4] = Pg[4];
+        r4[4] = P4[4];
+#pragma unroll
+        for (int c0 = 0; c0 < 5; ++c0) {
+          Pg[c0] = rg[c0];
+          P4[c0] = r4[c0];
+        }
       }
     }
     // ---- gain-matrix update with H = [I2 0]; Joseph form (paper Sec. 2; Fruhwirth 1987).
@@ -1120,7 +1148,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
     }
 #pragma unroll
     for (int j = 0; j < 5; ++j) p[j] += cov_to_d(K[j][0] * r0 + K[j][1] * r1);
-    {
+    if constexpr (kG == 1) {
       // X = (I - K H) C ; C' = X - (X H^T - K V) K^T
       U X[5][5];
 #pragma unroll
@@ -1137,6 +1165,27 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
       for (int r_ = 0; r_ < 5; ++r_)
 #pragma unroll
         for (int c_ = r_; c_ < 5; ++c_) C[S(r_, c_)] = X[r_][c_] - Y[r_][0] * K[c_][0] - Y[r_][1] * K[c_][1];
+    } else {
+      // the same, row gl in lane gl and row 4 in every lane, then exchanged
+      const U Kg0 = pick4(gl, K[0][0], K[1][0], K[2][0], K[3][0]);
+      const U Kg1 = pick4(gl, K[0][1], K[1][1], K[2][1], K[3][1]);
+      U Xg[5], X4[5], Cn[5];
+#pragma unroll
+      for (int c_ = 0; c_ < 5; ++c_) {
+        const U Cgc = pick4(gl, C[S(0, c_)], C[S(1, c_)], C[S(2, c_)], C[S(3, c_)]);
+        Xg[c_] = Cgc - Kg0 * C[S(0, c_)] - Kg1 * C[S(1, c_)];
+        X4[c_] = C[S(4, c_)] - K[4][0] * C[S(0, c_)] - K[4][1] * C[S(1, c_)];
+      }
+      const U Yg0 = Xg[0] - (Kg0 * V00 + Kg1 * V01), Yg1 = Xg[1] - (Kg0 * V01 + Kg1 * V11);
+      const U Y40 = X4[0] - (K[4][0] * V00 + K[4][1] * V01), Y41 = X4[1] - (K[4][0] * V01 + K[4][1] * V11);
+#pragma unroll
+      for (int c_ = 0; c_ < 5; ++c_) Cn[c_] = Xg[c_] - Yg0 * K[c_][0] - Yg1 * K[c_][1];
+      const U C44 = X4[4] - Y40 * K[4][0] - Y41 * K[4][1];
+#pragma unroll
+      for (int r_ = 0; r_ < 4; ++r_)
+#pragma unroll
+        for (int c_ = r_; c_ < 5; ++c_) C[S(r_, c_)] = gshfl<kG>(gmask, Cn[c_], r_);
+      C[S(4, 4)] = C44;
     }
     }  // measured
     if (k == 0) {
@@ -1149,6 +1198,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
       sincos(p[2], &sph, &cph);
       sincos(p[3], &sth, &cth);
       // p_0|0 and C_0|0 start the smoothed sums; P_0 = C_0|0
+      if constexpr (kG == 1) {
 #pragma unroll
       for (int j = 0; j < 5; ++j) st.dl(j) = p[j];
 #pragma unroll
@@ -1157,6 +1207,16 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
       for (int r_ = 0; r_ < 5; ++r_)
 #pragma unroll
         for (int c_ = 0; c_ < 5; ++c_) st.P(r_, c_) = C[S(r_, c_)];
+      } else {
+        dlg = pick4(gl, p[0], p[1], p[2], p[3]);
+        dl4 = p[4];
+#pragma unroll
+        for (int c_ = 0; c_ < 5; ++c_) {
+          Pg[c_] = Eg[c_] = pick4(gl, C[S(0, c_)], C[S(1, c_)], C[S(2, c_)], C[S(3, c_)]);
+          P4[c_] = C[S(4, c_)];
+        }
+        E44 = C[S(4, 4)];
+      }
     } else {
       // filtered direction: predicted angles plus the update's increments p[2], p[3]
       if constexpr (!kMixed) {
@@ -1182,6 +1242,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
         break;
       }
       // W = R H^T S^-1; p_0|N += W r; C_0|N -= W (R H^T)^T; P = R - R H^T K^T
+      if constexpr (kG == 1) {
       U W[5][2];
 #pragma unroll
       for (int j = 0; j < 5; ++j) {
@@ -1199,8 +1260,43 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
 #pragma unroll
         for (int c_ = 0; c_ < 5; ++c_) st.P(r_, c_) -= R0 * K[c_][0] + R1 * K[c_][1];
       }
+      } else {
+        // rows gl and 4; columns 0 and 1 of R from every row's lane
+        const U Wg0 = Pg[0] * Si00 + Pg[1] * Si01, Wg1 = Pg[0] * Si01 + Pg[1] * Si11;
+        const U W40 = P4[0] * Si00 + P4[1] * Si01, W41 = P4[0] * Si01 + P4[1] * Si11;
+        dlg += cov_to_d(Wg0 * r0 + Wg1 * r1);
+        dl4 += cov_to_d(W40 * r0 + W41 * r1);
+        U R0c[5], R1c[5];
+#pragma unroll
+        for (int c_ = 0; c_ < 4; ++c_) {
+          R0c[c_] = gshfl<kG>(gmask, Pg[0], c_);
+          R1c[c_] = gshfl<kG>(gmask, Pg[1], c_);
+        }
+        R0c[4] = P4[0];
+        R1c[4] = P4[1];
+#pragma unroll
+        for (int c_ = 0; c_ < 5; ++c_) Eg[c_] -= Wg0 * R0c[c_] + Wg1 * R1c[c_];
+        E44 -= W40 * R0c[4] + W41 * R1c[4];
+        const U Rg0 = Pg[0], Rg1 = Pg[1], R40 = P4[0], R41 = P4[1];
+#pragma unroll
+        for (int c_ = 0; c_ < 5; ++c_) {
+          Pg[c_] -= Rg0 * K[c_][0] + Rg1 * K[c_][1];
+          P4[c_] -= R40 * K[c_][0] + R41 * K[c_][1];
+        }
+      }
     }
     sp = s;
+  }
+  if constexpr (kG > 1) {
+    // the smoothed sums into every lane's full store (rows 0..3 from their lanes)
+#pragma unroll
+    for (int r_ = 0; r_ < 4; ++r_) {
+      st.dl(r_) = gshfl<kG>(gmask, dlg, r_);
+#pragma unroll
+      for (int c_ = r_; c_ < 5; ++c_) st.E(S(r_, c_)) = gshfl<kG>(gmask, Eg[c_], r_);
+    }
+    st.dl(4) = dl4;
+    st.E(S(4, 4)) = E44;
   }
 
   if (!(status & kFatal)) {
