@@ -108,6 +108,8 @@ def lib():
                                         ctypes.c_uint64, vp, vp, vp, vp]
         L.orc_estimate_seeds.argtypes = [vp, u32, ctypes.POINTER(OField), u32, ctypes.c_uint64, vp, vp, vp,
                                          ctypes.c_int, vp, vp, vp]
+        L.orc_find_tracks.argtypes = [vp, u32, ctypes.POINTER(OField), ctypes.POINTER(OOpts), vp, u32, vp, u32,
+                                      vp, vp, u32, vp, vp, vp, d, u32, u32, u32, vp, vp, vp, vp, vp, ctypes.c_int]
         L.orc_helix_seed.restype = u32
         L.orc_helix_seed.argtypes = [vp, vp, vp, d, vp]
         L.orc_update.restype = u32
@@ -301,6 +303,28 @@ def estimate_seeds(surfaces: np.ndarray, fld: OField, offsets, meas, sid, first_
     lib().orc_estimate_seeds(_p(s), s.shape[0], ctypes.byref(fld), n, int(sid.shape[0]), _p(offsets), _p(meas),
                              _p(sid), int(bool(first_three)), _p(par), _p(cov), _p(st))
     return par, cov, st
+
+
+def find_tracks(surfaces: np.ndarray, fld: OField, opts: Options, layers, rings, meas_off, meas, seed_sid, seed_par,
+                seed_cov, chi2_max: float = 15.0, beam: int = 3, max_holes: int = 2, max_entries: int = 24,
+                n_threads: int = 8):
+    """Combinatorial Kalman filter track finding (see kf_oracle.cpp): for every seed the best
+    candidate's entries (surface ids, bit 31 for holes; measurement indices, -1 for holes)."""
+    s = surfaces14(surfaces)
+    layers, rings = _f64(layers), _f64(rings)
+    meas_off = np.ascontiguousarray(meas_off, dtype=np.uint32)
+    meas = _f64(meas)
+    seed_sid = np.ascontiguousarray(seed_sid, dtype=np.uint32)
+    seed_par, seed_cov = _f64(seed_par), _f64(seed_cov)
+    n = seed_sid.shape[0]
+    ne, nm, c2 = np.zeros(n, np.uint32), np.zeros(n, np.uint32), np.zeros(n)
+    es, em = np.zeros((n, max_entries), np.uint32), np.zeros((n, max_entries), np.int32)
+    o = opts._c()
+    lib().orc_find_tracks(_p(s), s.shape[0], ctypes.byref(fld), ctypes.byref(o), _p(layers), layers.shape[0],
+                          _p(rings), meas.shape[0], _p(meas_off), _p(meas), n, _p(seed_sid), _p(seed_par),
+                          _p(seed_cov), float(chi2_max), int(beam), int(max_holes), int(max_entries), _p(ne), _p(nm),
+                          _p(c2), _p(es), _p(em), int(n_threads))
+    return {"n_entries": ne, "n_meas": nm, "chi2": c2, "sid": es, "meas": em}
 
 
 def helix_seed(r1, r2, r3, bz: float):

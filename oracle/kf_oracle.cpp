@@ -882,6 +882,366 @@ void fit_track(const Surface* surf, uint32_t n_surf, const Field& f, const Opts&
   }
 }
 
+
+// ---------------------------------------------------------------- track finding (CKF)
+// Reading (Sec. 2, track finding; the paper describes the combinatorial Kalman filter as the
+// step that follows seeding and precedes fitting, and prints no algorithm): starting from a
+// seed (parameters and covariance on a sensitive surface), the filter navigates outward from
+// surface to surface; on every sensitive surface it crosses, each measurement whose predicted
+// chi2 passes a gate makes a branch (the best `kChildren` of them), and so does the
+// "no measurement here" hypothesis (a hole) while the branch has fewer than max_holes
+// consecutive holes. A beam of at most `beam` branches is kept after every step, ranked by
+// measurement count (more first), then consecutive holes (fewer first), then chi2 (lower
+// first), then the order the branches were made in. A branch ends when no surface lies ahead,
+// when it would exceed its holes, or when it has max_entries entries; the best ended branch (same
+// ranking) is the track candidate.
+//
+// Navigation (reading of the paper's navigator for a detector of layers): the modules are
+// planar and tile barrel cylinders and endcap disks. From a state on a module, the candidates
+// are the modules of the same layer around it (overlaps) and those of the layers whose outer
+// face the straight line from the state reaches ahead, in order of path length; the module
+// crossed first among them is taken (a layer is skipped once its face lies 20 mm beyond the
+// best crossing found: barrel and endcap overlap). In a layer, the modules next to the crossing point (phi bin and row or
+// ring, +-1 each; the point on the parabola x + s T + s^2/2 k at the straight-line path s, k the
+// path's curvature vector) are candidates; one is crossed if the parabola meets its plane ahead
+// within its half extents plus a margin for the helix's deviation from the parabola. The
+// nearest candidate is propagated to
+// with the RKN stepper; if the propagated point lies outside the module it is excluded and the
+// navigation repeats (at most 4 exclusions a step).
+
+constexpr int kChildren = 3;        // measurements a branch may take on one surface
+constexpr int kCkfMaxEntries = 32;  // entries (measurements and holes) a candidate may have
+
+struct CkfOpts {
+  double chi2_max;
+  uint32_t beam, max_holes, max_entries;
+};
+
+struct CkfLayers {
+  const double* layers;  // [n][8]
+  uint32_t n;
+  const double* rings;   // [m][4]
+  std::vector<int> layer_of;  // surface id -> layer
+};
+
+struct Branch {
+  double p[5], C[25];
+  double h_ctrl;
+  double chi2;
+  uint32_t n_meas, holes, n_entries, status;
+  uint32_t order;  // creation order (the last tie-break)
+  int32_t sid;     // current surface (-1: none yet)
+  bool done;
+  uint32_t e_sid[kCkfMaxEntries];
+  int32_t e_meas[kCkfMaxEntries];
+};
+
+bool branch_better(const Branch& a, const Branch& b) {
+  if (a.n_meas != b.n_meas) return a.n_meas > b.n_meas;
+  if (a.holes != b.holes) return a.holes < b.holes;
+  if (a.chi2 != b.chi2) return a.chi2 < b.chi2;
+  return a.order < b.order;
+}
+
+void build_layer_of(CkfLayers& L, uint32_t n_surf) {
+  L.layer_of.assign(n_surf, -1);
+  for (uint32_t li = 0; li < L.n; ++li) {
+    const double* l = L.layers + 8 * li;
+    if (l[0] == 0.0) {
+      const uint32_t first = uint32_t(l[5]), cnt = uint32_t(l[2]) * uint32_t(l[3]);
+      for (uint32_t k = 0; k < cnt && first + k < n_surf; ++k) L.layer_of[first + k] = int(li);
+    } else {
+      for (uint32_t k = 0; k < uint32_t(l[2]); ++k) {
+        const double* rg = L.rings + 4 * (uint32_t(l[3]) + k);
+        for (uint32_t ip = 0; ip < uint32_t(rg[1]) && uint32_t(rg[2]) + ip < n_surf; ++ip)
+          L.layer_of[uint32_t(rg[2]) + ip] = int(li);
+      }
+    }
+  }
+}
+
+// Modules of layer li next to the point q (phi bin and row or ring, +-1).
+void layer_candidates(const CkfLayers& L, uint32_t li, const double q[3], std::vector<uint32_t>& out) {
+  const double* l = L.layers + 8 * li;
+  double phi = std::atan2(q[1], q[0]);
+  if (phi < 0.0) phi += 2.0 * kPi;
+  if (l[0] == 0.0) {
+    const int nphi = int(l[2]), nrows = int(l[3]);
+    const int ip0 = int(std::floor(phi / (2.0 * kPi / nphi) + 0.5));
+    const int iz0 = int(std::floor(q[2] / l[4] + 0.5 * nrows));
+    for (int iz = iz0 - 1; iz <= iz0 + 1; ++iz) {
+      if (iz < 0 || iz >= nrows) continue;
+      for (int d = -1; d <= 1; ++d) out.push_back(uint32_t(l[5]) + uint32_t(iz * nphi + ((ip0 + d) % nphi + nphi) % nphi));
+    }
+  } else {
+    const int nr = int(l[2]);
+    const double r = std::hypot(q[0], q[1]);
+    const int k0 = int(std::floor((r - l[5]) / l[4]));
+    for (int k = k0 - 1; k <= k0 + 1; ++k) {
+      if (k < 0 || k >= nr) continue;
+      const double* rg = L.rings + 4 * (uint32_t(l[3]) + uint32_t(k));
+      const int nphi = int(rg[1]);
+      const int ip0 = int(std::floor(phi / (2.0 * kPi / nphi) + 0.5));
+      for (int d = -1; d <= 1; ++d) out.push_back(uint32_t(rg[2]) + uint32_t(((ip0 + d) % nphi + nphi) % nphi));
+    }
+  }
+}
+
+// Straight-line path from x along T to the outer face of layer li (the largest radius a flat
+// barrel module reaches, or the |z| of a disk's modules, which sit at the nominal value and
+// 1 mm beyond), if that lies ahead and its crossing point is within the layer's extent (margin
+// 10 mm); else -1.
+double layer_path(const CkfLayers& L, uint32_t li, const double x[3], const double T[3]) {
+  const double* l = L.layers + 8 * li;
+  double s;
+  if (l[0] == 0.0) {
+    const double a = T[0] * T[0] + T[1] * T[1], b = x[0] * T[0] + x[1] * T[1];
+    // the outer face: flat modules at r and r + 1 mm reach out to sqrt((r + 1)^2 + half_u^2)
+    const double rf = std::sqrt((l[1] + 1.0) * (l[1] + 1.0) + l[6] * l[6]);
+    const double c = x[0] * x[0] + x[1] * x[1] - rf * rf;
+    if (!(a > 0.0) || c >= 0.0) return -1.0;  // outward only: from inside the cylinder
+    s = (-b + std::sqrt(b * b - a * c)) / a;
+    if (std::fabs(x[2] + s * T[2]) > 0.5 * l[3] * l[4] + 10.0) return -1.0;
+  } else {
+    if (T[2] == 0.0) return -1.0;
+    s = (l[1] + (l[1] > 0.0 ? 1.0 : -1.0) - x[2]) / T[2];  // the outer face (modules at |z| and |z| + 1 mm)
+    if (!(s > 0.0)) return -1.0;
+    const double r = std::hypot(x[0] + s * T[0], x[1] + s * T[1]);
+    if (r < l[5] - 10.0 || r > l[5] + l[2] * l[4] + 10.0) return -1.0;
+  }
+  return s > 0.0 ? s : -1.0;
+}
+
+// Half extents (u, v) of a module: those of its layer.
+void module_half(const CkfLayers& L, uint32_t id, double& hu, double& hv) {
+  const int li = L.layer_of[id];
+  hu = li >= 0 ? L.layers[8 * li + 6] : 1e300;
+  hv = li >= 0 ? L.layers[8 * li + 7] : 1e300;
+}
+
+// The nearest module among `cand` (not in `skip`) crossed by the parabola x + s T + s^2/2 k (k the
+// path curvature vector at x), within its half extents plus a margin for the helix's deviation
+// from the parabola (1 mm + s^3 bend^2 / 6, bend = kappa |q/p| |B|); returns -1 if none.
+int nearest_crossed(const CkfLayers& L, const Surface* surf, const std::vector<uint32_t>& cand, const double x[3],
+                    const double T[3], const double k[3], double bend, const std::vector<uint32_t>& skip,
+                    uint32_t n_surf, double* s_out) {
+  int best = -1;
+  double best_s = 0.0;
+  for (uint32_t id : cand) {
+    if (id >= n_surf || std::find(skip.begin(), skip.end(), id) != skip.end()) continue;
+    const Surface& m = surf[id];
+    // the parabola x + s T + s^2/2 k meets the plane n.(r - c) = 0 (straight line if it misses)
+    double d[3] = {m.c[0] - x[0], m.c[1] - x[1], m.c[2] - x[2]};
+    const double dist = dot3(m.n, d), a = dot3(m.n, T), b = dot3(m.n, k);
+    if (a == 0.0) continue;
+    double s = dist / a;
+    const double disc = a * a + 2.0 * b * dist;
+    if (disc >= 0.0) {
+      const double q2 = 2.0 * dist / (a + std::copysign(std::sqrt(disc), a));
+      if (std::isfinite(q2)) s = q2;
+    }
+    if (!(s > 1e-3)) continue;
+    const double h = 0.5 * s * s;
+    double q[3] = {x[0] + s * T[0] + h * k[0] - m.c[0], x[1] + s * T[1] + h * k[1] - m.c[1],
+                   x[2] + s * T[2] + h * k[2] - m.c[2]};
+    const double margin = 1.0 + s * s * s * bend * bend / 6.0;
+    double hu, hv;
+    module_half(L, id, hu, hv);
+    if (std::fabs(dot3(m.u, q)) > hu + margin || std::fabs(dot3(m.v, q)) > hv + margin) continue;
+    if (best < 0 || s < best_s || (s == best_s && id < uint32_t(best))) {
+      best = int(id);
+      best_s = s;
+    }
+  }
+  if (s_out) *s_out = best_s;
+  return best;
+}
+
+// Next module from a state at position x, direction T on surface `cur` (-1: none): the nearest
+// crossing among the current layer's modules around x (overlaps) and the modules of the layers
+// ahead (a layer is skipped once its face lies 20 mm beyond the best crossing found: layers
+// overlap where barrel and endcap meet).
+int navigate(const CkfLayers& L, const Surface* surf, uint32_t n_surf, int cur, const double x[3], const double T[3],
+             const double k[3], double bend, const std::vector<uint32_t>& skip) {
+  std::vector<uint32_t> cand;
+  int best = -1;
+  double best_s = 0.0;
+  if (cur >= 0 && L.layer_of[uint32_t(cur)] >= 0) {  // overlaps in the same layer
+    layer_candidates(L, uint32_t(L.layer_of[uint32_t(cur)]), x, cand);
+    std::vector<uint32_t> sk = skip;
+    sk.push_back(uint32_t(cur));
+    best = nearest_crossed(L, surf, cand, x, T, k, bend, sk, n_surf, &best_s);
+  }
+  std::vector<std::pair<double, uint32_t>> order;
+  for (uint32_t li = 0; li < L.n; ++li) {
+    if (cur >= 0 && L.layer_of[uint32_t(cur)] == int(li)) continue;
+    const double s = layer_path(L, li, x, T);
+    if (s > 0.0) order.push_back({s, li});
+  }
+  std::sort(order.begin(), order.end());
+  for (const auto& sl : order) {
+    if (best >= 0 && sl.first > best_s + 20.0) break;
+    const double h = 0.5 * sl.first * sl.first;  // the parabola's point at the straight-line path
+    double q[3] = {x[0] + sl.first * T[0] + h * k[0], x[1] + sl.first * T[1] + h * k[1],
+                   x[2] + sl.first * T[2] + h * k[2]};
+    cand.clear();
+    layer_candidates(L, sl.second, q, cand);
+    double sm = 0.0;
+    const int m = nearest_crossed(L, surf, cand, x, T, k, bend, skip, n_surf, &sm);
+    if (m >= 0 && (best < 0 || sm < best_s)) {
+      best = m;
+      best_s = sm;
+    }
+  }
+  return best;
+}
+
+void find_track(const Surface* surf, uint32_t n_surf, const Field& f, const Opts& o, const CkfOpts& co,
+                const CkfLayers& L, const uint32_t* meas_off, const double* meas, uint32_t seed_sid,
+                const double* seed_par, const double* seed_cov, Branch& best, bool& have_best) {
+  std::vector<Branch> active(1), children, ended;
+  uint32_t order = 0;
+  Branch& b0 = active[0];
+  std::memcpy(b0.p, seed_par, sizeof(b0.p));
+  unpack_cov(seed_cov, b0.C);
+  b0.h_ctrl = o.h_max;
+  b0.chi2 = 0.0;
+  b0.n_meas = b0.holes = b0.n_entries = b0.status = 0;
+  b0.order = order++;
+  b0.sid = -1;
+  b0.done = false;
+  have_best = false;
+  bool first_step = true;
+  while (!active.empty()) {
+    children.clear();
+    for (Branch& br : active) {
+      // ---- the next surface and the predicted state on it
+      Branch nb = br;
+      int target = -1;
+      double pp[5], Cp[25];
+      if (first_step) {
+        target = int(seed_sid);
+        std::memcpy(pp, br.p, sizeof(pp));
+        std::memcpy(Cp, br.C, sizeof(Cp));
+      } else {
+        if (br.n_entries >= co.max_entries) {
+          ended.push_back(br);
+          continue;
+        }
+        const Surface& sc = surf[uint32_t(br.sid)];
+        double pm[5], Q[25];
+        std::memcpy(pm, br.p, sizeof(pm));
+        const uint32_t stm = material(sc, o, pm, Q);
+        if (stm & kFatal) {
+          ended.push_back(br);
+          continue;
+        }
+        double x[3], T[3], B[3];
+        bound_to_free(sc, pm, x, T);
+        bool oof = false;
+        field_at(f, x, B, &oof);
+        const double bend = kKappa * std::fabs(pm[4]) * std::sqrt(dot3(B, B));
+        double kc[3];  // curvature vector of the path: kappa (q/p) T x B
+        kc[0] = kKappa * pm[4] * (T[1] * B[2] - T[2] * B[1]);
+        kc[1] = kKappa * pm[4] * (T[2] * B[0] - T[0] * B[2]);
+        kc[2] = kKappa * pm[4] * (T[0] * B[1] - T[1] * B[0]);
+        std::vector<uint32_t> skip;
+        for (int tries = 0; tries < 4 && target < 0; ++tries) {
+          const int m = navigate(L, surf, n_surf, br.sid, x, T, kc, bend, skip);
+          if (m < 0) break;
+          const Surface& sk = surf[uint32_t(m)];
+          double r[3], Tt[3], Dtot[49], dxds[7], Jb2f[35], Jf2b[35], P[49], tmp[49], t75[35], J[25];
+          std::memcpy(r, x, sizeof(r));
+          std::memcpy(Tt, T, sizeof(Tt));
+          jac_bound_to_free(sc, pm, Jb2f);
+          PropState ps{br.h_ctrl, 0, 0, o.h_max, false};
+          const uint32_t stp = propagate(f, o, sk, r, Tt, pm[4], Dtot, dxds, ps);
+          if (stp & kFatal) {
+            skip.push_back(uint32_t(m));
+            continue;
+          }
+          double d[3] = {r[0] - sk.c[0], r[1] - sk.c[1], r[2] - sk.c[2]}, hu, hv;
+          module_half(L, uint32_t(m), hu, hv);
+          if (std::fabs(dot3(sk.u, d)) > hu || std::fabs(dot3(sk.v, d)) > hv) {
+            skip.push_back(uint32_t(m));
+            continue;
+          }
+          jac_free_to_bound(sk, Tt, Jf2b);
+          path_correction(sk, Tt, dxds, P);
+          matmul(P, Dtot, tmp, 7, 7, 7);
+          matmul(tmp, Jb2f, t75, 7, 7, 5);
+          matmul(Jf2b, t75, J, 5, 7, 5);
+          free_to_bound(sk, r, Tt, pm[4], pp);
+          double CQ[25], Jt[25], t55[25];
+          for (int i = 0; i < 25; ++i) CQ[i] = br.C[i] + Q[i];
+          transpose(J, Jt, 5, 5);
+          matmul(J, CQ, t55, 5, 5, 5);
+          matmul(t55, Jt, Cp, 5, 5, 5);
+          symmetrize(Cp, 5);
+          nb.h_ctrl = ps.h_ctrl;
+          target = m;
+        }
+        if (target < 0) {  // nothing ahead: the branch ends
+          ended.push_back(br);
+          continue;
+        }
+      }
+      // ---- branches on the target surface: compatible measurements, best kChildren by chi2
+      nb.sid = target;
+      std::vector<std::pair<double, uint32_t>> ok;
+      for (uint32_t mi = meas_off[uint32_t(target)]; mi < meas_off[uint32_t(target) + 1]; ++mi) {
+        const double* mk = meas + 5 * size_t(mi);
+        double pt[5], Ct[25], c2 = 0.0;
+        std::memcpy(pt, pp, sizeof(pt));
+        std::memcpy(Ct, Cp, sizeof(Ct));
+        const double m2[2] = {mk[0], mk[1]}, V[4] = {mk[2], mk[3], mk[3], mk[4]};
+        if (kf_update(m2, V, pt, Ct, &c2) != 0) continue;
+        if (c2 < co.chi2_max) ok.push_back({c2, mi});
+      }
+      std::sort(ok.begin(), ok.end());
+      for (size_t j = 0; j < ok.size() && j < size_t(kChildren); ++j) {
+        Branch ch = nb;
+        const double* mk = meas + 5 * size_t(ok[j].second);
+        const double m2[2] = {mk[0], mk[1]}, V[4] = {mk[2], mk[3], mk[3], mk[4]};
+        std::memcpy(ch.p, pp, sizeof(ch.p));
+        std::memcpy(ch.C, Cp, sizeof(ch.C));
+        double c2 = 0.0;
+        kf_update(m2, V, ch.p, ch.C, &c2);
+        ch.p[2] = wrap_phi(ch.p[2]);
+        ch.chi2 += c2;
+        ch.n_meas += 1;
+        ch.holes = 0;
+        ch.e_sid[ch.n_entries] = uint32_t(target);
+        ch.e_meas[ch.n_entries] = int32_t(ok[j].second);
+        ch.n_entries += 1;
+        ch.order = order++;
+        children.push_back(ch);
+      }
+      if (nb.holes < co.max_holes) {
+        Branch ch = nb;
+        std::memcpy(ch.p, pp, sizeof(ch.p));
+        std::memcpy(ch.C, Cp, sizeof(ch.C));
+        ch.holes += 1;
+        ch.e_sid[ch.n_entries] = uint32_t(target) | kNoMeasurement;
+        ch.e_meas[ch.n_entries] = -1;
+        ch.n_entries += 1;
+        ch.order = order++;
+        children.push_back(ch);
+      } else if (ok.empty()) {
+        ended.push_back(br);  // one hole too many: the branch ends before this surface
+      }
+    }
+    first_step = false;
+    std::stable_sort(children.begin(), children.end(), branch_better);
+    if (children.size() > co.beam) children.resize(co.beam);
+    active.swap(children);
+  }
+  for (const Branch& e : ended)
+    if (!have_best || branch_better(e, best)) {
+      best = e;
+      have_best = true;
+    }
+}
 }  // namespace
 
 // ================================================================ C interface
@@ -1370,6 +1730,57 @@ void orc_estimate_seeds(const double* surfaces, uint32_t n_surf, const orc_field
     seed_track(surf.data(), n_surf, F, meas + 5 * size_t(a), sid + a, b - a, first_three, seed_par + 5 * size_t(i),
                seed_cov + 15 * size_t(i), status + i);
   }
+}
+
+// Track finding: for every seed (surface id, parameters [5], packed covariance [15]) the best
+// candidate of the combinatorial Kalman filter. Measurements [n_meas][5] are grouped by surface:
+// those of surface s are meas_off[s] .. meas_off[s+1]-1. Outputs per seed: entries (surface ids,
+// with bit 31 for holes, and measurement indices or -1) [n_seeds][max_entries], the entry and
+// measurement counts and the chi2 sum; 0 entries when the seed surface is out of range.
+void orc_find_tracks(const double* surfaces, uint32_t n_surf, const orc_field* field, const orc_opts* opts,
+                     const double* layers, uint32_t n_layers, const double* rings, uint32_t n_meas,
+                     const uint32_t* meas_off, const double* meas, uint32_t n_seeds, const uint32_t* seed_sid,
+                     const double* seed_par, const double* seed_cov, double chi2_max, uint32_t beam,
+                     uint32_t max_holes, uint32_t max_entries, uint32_t* out_n_entries, uint32_t* out_n_meas,
+                     double* out_chi2, uint32_t* out_sid, int32_t* out_meas, int n_threads) {
+  (void)n_meas;
+  std::vector<Surface> surf = to_surfaces(surfaces, n_surf);
+  Field F = to_field(field);
+  Mlp mlp_store;
+  Opts O = to_opts(opts, &mlp_store);
+  CkfLayers L{layers, n_layers, rings, {}};
+  build_layer_of(L, n_surf);
+  CkfOpts co{chi2_max, beam < 1 ? 1u : beam, max_holes,
+             max_entries < 1 ? 1u : (max_entries > uint32_t(kCkfMaxEntries) ? uint32_t(kCkfMaxEntries) : max_entries)};
+  auto work = [&](uint32_t lo, uint32_t hi) {
+    for (uint32_t i = lo; i < hi; ++i) {
+      Branch best;
+      bool have = false;
+      uint32_t* es = out_sid + size_t(i) * max_entries;
+      int32_t* em = out_meas + size_t(i) * max_entries;
+      for (uint32_t j = 0; j < max_entries; ++j) {
+        es[j] = 0;
+        em[j] = -1;
+      }
+      out_n_entries[i] = out_n_meas[i] = 0;
+      out_chi2[i] = 0.0;
+      if (seed_sid[i] >= n_surf) continue;
+      find_track(surf.data(), n_surf, F, O, co, L, meas_off, meas, seed_sid[i], seed_par + 5 * size_t(i),
+                 seed_cov + 15 * size_t(i), best, have);
+      if (!have) continue;
+      out_n_entries[i] = best.n_entries;
+      out_n_meas[i] = best.n_meas;
+      out_chi2[i] = best.chi2;
+      for (uint32_t j = 0; j < best.n_entries && j < max_entries; ++j) {
+        es[j] = best.e_sid[j];
+        em[j] = best.e_meas[j];
+      }
+    }
+  };
+  int nt = std::max(1, n_threads);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t) th.emplace_back(work, uint32_t(uint64_t(n_seeds) * t / nt), uint32_t(uint64_t(n_seeds) * (t + 1) / nt));
+  for (auto& t : th) t.join();
 }
 
 // The helix-through-three-points step alone (for the pins): phi, theta, q/p and the status.

@@ -79,6 +79,8 @@ def lib():
         L.syn_geometry_size.argtypes = [vp]
         L.syn_geometry_export.argtypes = [vp, vp]
         L.syn_geometry_free.argtypes = [vp]
+        L.syn_geometry_layer_sizes.argtypes = [vp, vp, vp]
+        L.syn_geometry_layers.argtypes = [vp, vp, vp]
         L.syn_cel.restype = d
         L.syn_cel.argtypes = [d, d, d, d]
         L.syn_solenoid.argtypes = [d, d, d, d, ctypes.POINTER(d), ctypes.POINTER(d)]
@@ -101,9 +103,13 @@ def _ptr(a: np.ndarray):
 # ----------------------------------------------------------------------------- geometry
 @dataclass
 class Geometry:
-    """Planar surfaces; ``table`` is [n, 16] = u[3] v[3] n[3] c[3] thickness X0 half_u half_v."""
+    """Planar surfaces; ``table`` is [n, 16] = u[3] v[3] n[3] c[3] thickness X0 half_u half_v.
+    ``layers`` [n_layers, 8] and ``rings`` [n_rings, 4] describe the barrel cylinders and endcap
+    disks the modules tile (empty for a telescope); see syn_geometry_layers in synth.cpp."""
     table: np.ndarray
     _handle: int = 0
+    layers: np.ndarray = None
+    rings: np.ndarray = None
 
     @property
     def n(self) -> int:
@@ -149,7 +155,12 @@ def _export_geometry(h) -> Geometry:
     n = L.syn_geometry_size(h)
     t = np.zeros((n, 16), dtype=np.float64)
     L.syn_geometry_export(h, _ptr(t))
-    return Geometry(t, h)
+    nl, nr = ctypes.c_uint32(), ctypes.c_uint32()
+    L.syn_geometry_layer_sizes(ctypes.c_void_p(h), ctypes.byref(nl), ctypes.byref(nr))
+    layers, rings = np.zeros((nl.value, 8)), np.zeros((nr.value, 4))
+    if nl.value:
+        L.syn_geometry_layers(ctypes.c_void_p(h), _ptr(layers), _ptr(rings))
+    return Geometry(t, h, layers, rings)
 
 
 def telescope_geometry(n_planes: int = 9, spacing: float = 50.0, thickness: float = SI_THICKNESS,
@@ -393,3 +404,68 @@ def solenoid_muon_workload(n_tracks: int = 100000, seed: int = 3, fld: Field | N
         setattr(p, k, v)
     t = simulate(g, f, p, seed, [n_tracks])
     return Workload(f"solenoid_map_muons_{n_tracks}", g, f, t)
+
+
+@dataclass
+class MeasurementContainer:
+    """The measurements of a set of tracks grouped by surface, as a track finder sees them:
+    ``meas`` [m, 5] sorted by surface id (stable), surface s owning rows ``offsets[s]`` ..
+    ``offsets[s + 1] - 1``; ``track`` and ``hit`` give each row's simulated track and its index
+    in the tracks' own measurement arrays (for efficiency and purity)."""
+    offsets: np.ndarray
+    meas: np.ndarray
+    sid: np.ndarray
+    track: np.ndarray
+    hit: np.ndarray
+
+
+def measurement_container(tracks: Tracks, n_surfaces: int) -> MeasurementContainer:
+    """Groups the tracks' measured hits (holes left out) by surface."""
+    hole = (tracks.sid & np.uint32(0x80000000)) != 0
+    hit = np.flatnonzero(~hole)
+    track_of = np.repeat(np.arange(tracks.n_tracks), np.diff(tracks.offsets.astype(np.int64)))[hit]
+    sid = tracks.sid[hit].astype(np.int64)
+    order = np.argsort(sid, kind="stable")
+    counts = np.bincount(sid, minlength=n_surfaces)
+    offsets = np.zeros(n_surfaces + 1, np.uint32)
+    offsets[1:] = np.cumsum(counts)
+    return MeasurementContainer(offsets, np.ascontiguousarray(tracks.meas[hit][order]), sid[order].astype(np.uint32),
+                                track_of[order], hit[order])
+
+
+def layer_of_surfaces(geom: Geometry) -> np.ndarray:
+    """Layer index of every surface (-1 outside the layer structure)."""
+    out = np.full(geom.n, -1, dtype=np.int64)
+    if geom.layers is None:
+        return out
+    for li, l in enumerate(geom.layers):
+        if l[0] == 0:
+            first, cnt = int(l[5]), int(l[2]) * int(l[3])
+            out[first:first + cnt] = li
+        else:
+            for k in range(int(l[2])):
+                rg = geom.rings[int(l[3]) + k]
+                out[int(rg[2]):int(rg[2]) + int(rg[1])] = li
+    return out
+
+
+def triplet_seed_hits(tracks: Tracks, geom: Geometry):
+    """A stand-in for triplet seeding: every track's first measurements on three distinct layers
+    (offsets, measurements [m, 5], surface ids), for seed parameter estimation."""
+    layer_of = layer_of_surfaces(geom)
+    offs, pick = [0], []
+    for i in range(tracks.n_tracks):
+        seen = []
+        for j in range(int(tracks.offsets[i]), int(tracks.offsets[i + 1])):
+            if tracks.sid[j] & np.uint32(0x80000000):
+                continue
+            L = layer_of[tracks.sid[j]]
+            if L not in seen:
+                seen.append(L)
+                pick.append(j)
+            if len(seen) == 3:
+                break
+        offs.append(len(pick))
+    pick = np.array(pick, dtype=np.int64)
+    return np.array(offs, np.uint32), tracks.meas[pick], tracks.sid[pick]
+

@@ -655,6 +655,38 @@ void syn_geometry_export(void* g, double* out) {
 }
 void syn_geometry_free(void* g) { delete static_cast<Geometry*>(g); }
 
+// Layer structure of a barrel + endcap geometry, for navigation: n_layers (10 barrel + 14 disks)
+// rows of 8 doubles and n_rings rows of 4 doubles.
+//   barrel: [0, r (nominal), nphi, n_rows, row_pitch, first id, half_u, half_v]
+//           module (iz, ip) = first + iz nphi + ip, centre z = (iz - (n_rows - 1) / 2) row_pitch
+//   disk:   [1, z (signed nominal), n_rings, first ring row, ring_pitch, r_inner, half_u, half_v]
+//   ring:   [r_centre, nphi, first id, 0]; module ip = first + ip
+// A telescope has no layer structure (0 layers).
+void syn_geometry_layer_sizes(void* g, uint32_t* n_layers, uint32_t* n_rings) {
+  const Geometry* G = static_cast<Geometry*>(g);
+  *n_layers = uint32_t(G->layers.size() + G->disks.size());
+  uint32_t r = 0;
+  for (const Disk& D : G->disks) r += uint32_t(D.rings.size());
+  *n_rings = r;
+}
+void syn_geometry_layers(void* g, double* layers, double* rings) {
+  const Geometry* G = static_cast<Geometry*>(g);
+  size_t li = 0, ri = 0;
+  for (const BarrelLayer& L : G->layers) {
+    double* o = layers + 8 * li++;
+    o[0] = 0; o[1] = L.r; o[2] = L.nphi; o[3] = G->nrows; o[4] = G->row_pitch; o[5] = L.first; o[6] = 15.0; o[7] = 35.0;
+  }
+  for (const Disk& D : G->disks) {
+    double* o = layers + 8 * li++;
+    o[0] = 1; o[1] = D.z; o[2] = double(D.rings.size()); o[3] = double(ri); o[4] = G->ring_pitch; o[5] = 32.0;
+    o[6] = 35.0; o[7] = 15.0;
+    for (const DiskRing& R : D.rings) {
+      double* q = rings + 4 * ri++;
+      q[0] = R.rc; q[1] = R.nphi; q[2] = R.first; q[3] = 0;
+    }
+  }
+}
+
 double syn_cel(double kc, double p, double c, double s) { return cel(kc, p, c, s); }
 
 void syn_solenoid(double a, double b, double rho, double z, double* Brho, double* Bz) {
