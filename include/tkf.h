@@ -363,6 +363,98 @@ typedef struct tkf_seed_outputs {
 tkf_status tkf_estimate_seeds(tkf_context ctx, tkf_geometry geo, tkf_field field, uint32_t which,
                               const tkf_fit_inputs* in, const tkf_seed_outputs* out, void* stream);
 
+/* ---------------------------------------------------------------------------- track finding */
+
+/* Track finding with a combinatorial Kalman filter (Sec. 2 places it after seeding and before
+ * fitting, and prints no algorithm; this is the reading implemented). From a seed (parameters
+ * and covariance on a sensitive surface) the filter navigates outward module by module. On
+ * every module it crosses, each of the (at most 3) measurements with the lowest predicted chi2
+ * below chi2_max makes a branch, and so does a hole (no measurement) while the branch has fewer
+ * than max_holes consecutive holes. After every step a beam of the best `beam` branches is kept
+ * (ranked by measurement count, more first; then consecutive holes, fewer first; then chi2,
+ * lower first; then creation order). A branch ends when no module lies ahead, when a further
+ * hole would exceed max_holes with no compatible measurement, or at max_entries entries; the
+ * best ended branch is the seed's candidate. Propagation, material and the gain-matrix update
+ * are the fit's (FP64, TKF_STEP_ADAPTIVE).
+ *
+ * Navigation uses the layer structure of the geometry (tkf_geometry_set_layers): from a state
+ * on a module, the candidates are the modules of the same layer around the state (overlaps) and
+ * those of the layers whose outer face the straight line from the state reaches ahead, in order
+ * of path length; in a layer, the modules next to the crossing point (phi bin and row or ring,
+ * +-1 each; the point on the parabola x + s T + s^2/2 k at the straight-line path s, k the
+ * path's curvature vector kappa (q/p) T x B). A module is crossed if the parabola meets its plane
+ * ahead (s > 1e-3 mm) within its half extents plus 1 mm + s^3 (kappa |q/p| |B|)^2 / 6; the
+ * nearest is taken (a layer is skipped once its face lies 20 mm beyond the best crossing found).
+ * The RKN propagation to it must end within its half extents, else it is excluded and the
+ * navigation repeats (at most 4 exclusions). Surfaces outside the layer structure are never
+ * candidates. */
+#define TKF_CKF_MAX_ENTRIES 32u
+
+/* Layer structure for navigation, host arrays copied to the device (replacing an earlier one).
+ * layers [n_layers][8]:
+ *   barrel cylinder: {0, r, n_phi, n_rows, row_pitch, first, half_u, half_v}: module (row iz,
+ *     phi bin ip) has surface id first + iz n_phi + ip, its centre at phi 2 pi ip / n_phi and
+ *     z = (iz - (n_rows - 1) / 2) row_pitch; modules at radius r or r + 1 mm, normal radial;
+ *   endcap disk: {1, z, n_rings, first_ring, ring_pitch, r_inner, half_u, half_v}: rings
+ *     first_ring .. first_ring + n_rings - 1 of `rings`, ring k covering radii from
+ *     r_inner + k ring_pitch; modules at z or z + sign(z) 1 mm, normal along z;
+ * rings [n_rings][4]: {r_centre, n_phi, first, 0}: module ip has surface id first + ip.
+ * half_u, half_v: half extents of the layer's modules along their u and v axes (mm).
+ * At most 32 layers. Errors: TKF_ERR_BAD_HANDLE, TKF_ERR_INVALID_ARG (NULL pointers, more than
+ * 32 layers, surface ids or ring rows out of range), TKF_ERR_OOM / TKF_ERR_DEVICE. */
+tkf_status tkf_geometry_set_layers(tkf_geometry geo, const double* layers, uint32_t n_layers, const double* rings,
+                                   uint32_t n_rings);
+
+typedef struct tkf_ckf_options {
+  double chi2_max;      /* gate on the predicted chi2 of a measurement (2 dof; default 15) */
+  uint32_t beam;        /* branches kept after every step (1..8; default 3) */
+  uint32_t max_holes;   /* consecutive holes a branch may have (default 2) */
+  uint32_t max_entries; /* entries (measurements and holes) of a candidate, 1..TKF_CKF_MAX_ENTRIES (24) */
+} tkf_ckf_options;
+
+void tkf_ckf_options_default(tkf_ckf_options* o);
+
+/* Inputs, DEVICE pointers owned by the caller (read only): seeds (surface id, parameters 5 x n,
+ * packed covariance 15 x n, the fit's seed layout) and the measurements of the event grouped by
+ * surface: those of surface s are meas_offsets[s] .. meas_offsets[s+1]-1 (n_surfaces + 1
+ * offsets, non-decreasing). */
+typedef struct tkf_ckf_inputs {
+  uint32_t n_seeds;
+  const uint32_t* seed_sid;
+  const double* seed_par;
+  const double* seed_cov;
+  uint32_t n_meas;
+  const uint32_t* meas_offsets;
+  const double* loc0;
+  const double* loc1;
+  const double* v00;
+  const double* v01;
+  const double* v11;
+} tkf_ckf_inputs;
+
+/* Outputs, DEVICE pointers owned by the caller (written): per seed the candidate's entry count,
+ * measurement count and chi2 sum, and its entries in order, max_entries x n_seeds: entry_sid
+ * (surface id, TKF_SID_NO_MEASUREMENT for a hole) and entry_meas (measurement index, -1 for a
+ * hole); unused entries are 0 / -1. A seed whose surface is out of range gets 0 entries. The
+ * entries are a fit input as they stand (holes included). */
+typedef struct tkf_ckf_outputs {
+  uint32_t* n_entries;
+  uint32_t* n_meas;
+  double* chi2;
+  uint32_t* entry_sid;
+  int32_t* entry_meas;
+} tkf_ckf_outputs;
+
+/* Finds the candidate of every seed, asynchronously on `stream`. fit_opts gives the propagation
+ * and material options (precision TKF_FP64 and step mode TKF_STEP_ADAPTIVE required; launch
+ * policy fields ignored). The branch store (about 7.4 KB a seed at beam 3) is a workspace of the
+ * context, grown on demand (the call then synchronizes the stream). Errors: TKF_ERR_BAD_HANDLE,
+ * TKF_ERR_INVALID_ARG (NULL pointers, options out of range, no layer structure), TKF_ERR_OOM,
+ * TKF_ERR_DEVICE. */
+tkf_status tkf_find_tracks(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf_fit_options* fit_opts,
+                           const tkf_ckf_options* ckf_opts, const tkf_ckf_inputs* in, const tkf_ckf_outputs* out,
+                           void* stream);
+
 /* ---------------------------------------------------------------------------- learned step proposer */
 
 /* The benchmark spec's learned part (the paper has no learned component): before a track's first

@@ -26,7 +26,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "libtkf.so")
 _SOURCES = ["tkf_api.cu", "tkf_order.cu", "tkf_policy.cu", "tkf_fit_fp64.cu", "tkf_fit_mixed.cu",
             "tkf_fit_mixed_r128.cu", "tkf_fit_mixed_r64.cu", "tkf_fit_mixed32.cu", "tkf_mlp.cu", "tkf_seed.cu",
-            "tkf_fit_group.cu"]
+            "tkf_fit_group.cu", "tkf_ckf.cu"]
 _lib = None
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
@@ -144,6 +144,23 @@ class SeedOutputs(ctypes.Structure):
     _fields_ = [("par", ctypes.c_void_p), ("cov", ctypes.c_void_p), ("status", ctypes.c_void_p)]
 
 
+class CkfOptions(ctypes.Structure):
+    _fields_ = [("chi2_max", ctypes.c_double), ("beam", ctypes.c_uint32), ("max_holes", ctypes.c_uint32),
+                ("max_entries", ctypes.c_uint32)]
+
+
+class CkfInputs(ctypes.Structure):
+    _fields_ = [("n_seeds", ctypes.c_uint32), ("seed_sid", ctypes.c_void_p), ("seed_par", ctypes.c_void_p),
+                ("seed_cov", ctypes.c_void_p), ("n_meas", ctypes.c_uint32), ("meas_offsets", ctypes.c_void_p),
+                ("loc0", ctypes.c_void_p), ("loc1", ctypes.c_void_p), ("v00", ctypes.c_void_p),
+                ("v01", ctypes.c_void_p), ("v11", ctypes.c_void_p)]
+
+
+class CkfOutputs(ctypes.Structure):
+    _fields_ = [("n_entries", ctypes.c_void_p), ("n_meas", ctypes.c_void_p), ("chi2", ctypes.c_void_p),
+                ("entry_sid", ctypes.c_void_p), ("entry_meas", ctypes.c_void_p)]
+
+
 # C entry points and their signatures (argument types), as declared in include/tkf.h.
 _VP = ctypes.c_void_p
 _SIGNATURES = {
@@ -165,6 +182,10 @@ _SIGNATURES = {
                                        ctypes.POINTER(FitInputs), ctypes.POINTER(FitOutputs), _VP]),
     "tkf_estimate_seeds": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_uint32, ctypes.POINTER(FitInputs),
                                           ctypes.POINTER(SeedOutputs), _VP]),
+    "tkf_geometry_set_layers": (ctypes.c_int, [_VP, _VP, ctypes.c_uint32, _VP, ctypes.c_uint32]),
+    "tkf_ckf_options_default": (None, [ctypes.POINTER(CkfOptions)]),
+    "tkf_find_tracks": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(FitOptions), ctypes.POINTER(CkfOptions),
+                                       ctypes.POINTER(CkfInputs), ctypes.POINTER(CkfOutputs), _VP]),
     "tkf_propose_start": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(FitOptions), ctypes.POINTER(FitInputs),
                                          _VP, _VP]),
     "tkf_mlp_load": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(_VP)]),
@@ -246,6 +267,16 @@ class Geometry:
         _check(lib().tkf_geometry_create(ctx.handle, arr, n, ctypes.byref(mat) if mat else None,
                                          ctypes.byref(h)), ctx.handle, "tkf_geometry_create")
         self.handle, self.ctx, self.n = h, ctx, n
+
+    def set_layers(self, layers, rings):
+        """tkf_geometry_set_layers: the layer structure for track finding (host arrays [n, 8] and
+        [m, 4], as the geometry generator exports them)."""
+        layers = np.ascontiguousarray(layers, dtype=np.float64)
+        rings = np.ascontiguousarray(rings, dtype=np.float64)
+        _check(lib().tkf_geometry_set_layers(self.handle, _VP(layers.ctypes.data), layers.shape[0],
+                                             _VP(rings.ctypes.data) if rings.size else None, rings.shape[0]),
+               self.ctx.handle, "tkf_geometry_set_layers")
+        return self
 
     @classmethod
     def from_table(cls, ctx: Context, table: np.ndarray, material=None) -> "Geometry":
@@ -557,6 +588,48 @@ def estimate_seeds(ctx: Context, geo: Geometry, field: Field, batch: Batch,
     _check(lib().tkf_estimate_seeds(ctx.handle, geo.handle, field.handle, int(which),
                                     ctypes.byref(_inputs_struct(batch)), ctypes.byref(so),
                                     _VP(stream.cuda_stream)), ctx.handle, "tkf_estimate_seeds")
+    return out
+
+
+@dataclass
+class CkfResult:
+    n_entries: object   # [n] i32
+    n_meas: object      # [n] i32
+    chi2: object        # [n] f64
+    entry_sid: object   # [max_entries, n] i32 (bit 31: hole)
+    entry_meas: object  # [max_entries, n] i32 (-1: hole)
+
+
+def find_tracks(ctx: Context, geo: Geometry, field: Field, seed_sid, seed_par, seed_cov, meas_offsets, loc0, loc1, v00,
+                v01, v11, opts: Options | None = None, chi2_max: float = 15.0, beam: int = 3, max_holes: int = 2,
+                max_entries: int = 24, stream=None) -> CkfResult:
+    """tkf_find_tracks on CUDA tensors: seeds (surface ids [n], parameters [5, n], covariances
+    [15, n]) and the event's measurements grouped by surface (offsets [n_surfaces + 1] and the
+    SoA measurement arrays). Enqueued on ``stream`` (default: torch's current stream)."""
+    import torch
+    dev = seed_par.device
+    n = int(seed_sid.shape[0])
+    out = CkfResult(torch.empty(n, dtype=torch.int32, device=dev), torch.empty(n, dtype=torch.int32, device=dev),
+                    torch.empty(n, dtype=torch.float64, device=dev),
+                    torch.empty((max_entries, n), dtype=torch.int32, device=dev),
+                    torch.empty((max_entries, n), dtype=torch.int32, device=dev))
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    co = CkfOptions()
+    lib().tkf_ckf_options_default(ctypes.byref(co))
+    co.chi2_max, co.beam, co.max_holes, co.max_entries = chi2_max, beam, max_holes, max_entries
+    ci = CkfInputs()
+    ci.n_seeds, ci.n_meas = n, int(loc0.shape[0])
+    ci.seed_sid, ci.seed_par, ci.seed_cov = _ptr(seed_sid), _ptr(seed_par), _ptr(seed_cov)
+    ci.meas_offsets, ci.loc0, ci.loc1 = _ptr(meas_offsets), _ptr(loc0), _ptr(loc1)
+    ci.v00, ci.v01, ci.v11 = _ptr(v00), _ptr(v01), _ptr(v11)
+    cout = CkfOutputs()
+    cout.n_entries, cout.n_meas, cout.chi2 = _ptr(out.n_entries), _ptr(out.n_meas), _ptr(out.chi2)
+    cout.entry_sid, cout.entry_meas = _ptr(out.entry_sid), _ptr(out.entry_meas)
+    o = (opts or Options()).c()
+    _check(lib().tkf_find_tracks(ctx.handle, geo.handle, field.handle, ctypes.byref(o), ctypes.byref(co),
+                                 ctypes.byref(ci), ctypes.byref(cout), _VP(stream.cuda_stream)),
+           ctx.handle, "tkf_find_tracks")
     return out
 
 

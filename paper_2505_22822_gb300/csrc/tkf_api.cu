@@ -8,6 +8,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "tkf_internal.cuh"
 
@@ -85,7 +86,7 @@ tkf_status tkf_context_create(int device, tkf_context* out) {
 
 void tkf_context_destroy(tkf_context ctx) {
   if (!ctx) return;
-  if (ctx->stage || ctx->ws || ctx->train_ws || ctx->graph_exec || ctx->h2d_stream) {
+  if (ctx->stage || ctx->ws || ctx->train_ws || ctx->graph_exec || ctx->h2d_stream || ctx->ckf_ws) {
     DeviceGuard g(ctx->device);
     tkf::release_graph(ctx);
     for (int c = 0; c < 8; ++c) {
@@ -98,6 +99,7 @@ void tkf_context_destroy(tkf_context ctx) {
     if (ctx->stage) cudaFree(ctx->stage);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->train_ws) cudaFree(ctx->train_ws);
+    if (ctx->ckf_ws) cudaFree(ctx->ckf_ws);
   }
   delete ctx;
 }
@@ -217,7 +219,75 @@ void tkf_geometry_destroy(tkf_geometry geo) {
   if (!geo) return;
   DeviceGuard g(geo->device);
   cudaFree(geo->d_surf);
+  if (geo->d_layers) cudaFree(geo->d_layers);
+  if (geo->d_rings) cudaFree(geo->d_rings);
+  if (geo->d_layer_of) cudaFree(geo->d_layer_of);
   delete geo;
+}
+
+tkf_status tkf_geometry_set_layers(tkf_geometry geo, const double* layers, uint32_t n_layers, const double* rings,
+                                   uint32_t n_rings) {
+  if (!geo) return fail(nullptr, TKF_ERR_BAD_HANDLE, "tkf_geometry_set_layers: NULL geometry");
+  tkf_context ctx = geo->ctx;
+  if (!layers || n_layers == 0 || (n_rings && !rings))
+    return fail(ctx, TKF_ERR_INVALID_ARG, "tkf_geometry_set_layers: NULL or empty layer table");
+  if (n_layers > 32) return fail(ctx, TKF_ERR_INVALID_ARG, "tkf_geometry_set_layers: more than 32 layers");
+  // the layer of every surface; every module id and ring row must be in range
+  std::vector<int32_t> layer_of(geo->n, -1);
+  for (uint32_t li = 0; li < n_layers; ++li) {
+    const double* l = layers + 8 * size_t(li);
+    bool ok = (l[0] == 0.0 || l[0] == 1.0) && l[2] >= 1.0 && l[3] >= (l[0] == 0.0 ? 1.0 : 0.0) && l[4] > 0.0 &&
+              l[6] > 0.0 && l[7] > 0.0;
+    if (ok && l[0] == 0.0) {
+      const double cnt = l[2] * l[3];
+      ok = l[5] >= 0.0 && l[5] + cnt <= double(geo->n);
+      for (uint32_t k = 0; ok && k < uint32_t(cnt); ++k) layer_of[uint32_t(l[5]) + k] = int32_t(li);
+    } else if (ok) {
+      ok = l[3] >= 0.0 && l[3] + l[2] <= double(n_rings);
+      for (uint32_t k = 0; ok && k < uint32_t(l[2]); ++k) {
+        const double* rg = rings + 4 * (size_t(l[3]) + k);
+        ok = rg[1] >= 1.0 && rg[2] >= 0.0 && rg[2] + rg[1] <= double(geo->n);
+        for (uint32_t ip = 0; ok && ip < uint32_t(rg[1]); ++ip) layer_of[uint32_t(rg[2]) + ip] = int32_t(li);
+      }
+    }
+    if (!ok)
+      return fail(ctx, TKF_ERR_INVALID_ARG,
+                  "tkf_geometry_set_layers: layer " + std::to_string(li) + " malformed or out of range");
+  }
+  DeviceGuard g(geo->device);
+  if (!g.ok) return fail(ctx, TKF_ERR_DEVICE, "tkf_geometry_set_layers: cudaSetDevice failed");
+  double *dl = nullptr, *dr = nullptr;
+  int32_t* dlo = nullptr;
+  cudaError_t e = cudaMalloc(&dl, sizeof(double) * 8 * n_layers);
+  if (e == cudaSuccess) e = cudaMalloc(&dr, sizeof(double) * 4 * (n_rings ? n_rings : 1));
+  if (e == cudaSuccess) e = cudaMalloc(&dlo, sizeof(int32_t) * (geo->n ? geo->n : 1));
+  if (e == cudaSuccess) e = cudaMemcpy(dl, layers, sizeof(double) * 8 * n_layers, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && n_rings) e = cudaMemcpy(dr, rings, sizeof(double) * 4 * n_rings, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && geo->n)
+    e = cudaMemcpy(dlo, layer_of.data(), sizeof(int32_t) * geo->n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (dl) cudaFree(dl);
+    if (dr) cudaFree(dr);
+    if (dlo) cudaFree(dlo);
+    return cuda_fail(ctx, e, "tkf_geometry_set_layers: upload");
+  }
+  if (geo->d_layers) cudaFree(geo->d_layers);
+  if (geo->d_rings) cudaFree(geo->d_rings);
+  if (geo->d_layer_of) cudaFree(geo->d_layer_of);
+  geo->d_layers = dl;
+  geo->d_rings = dr;
+  geo->d_layer_of = dlo;
+  geo->n_layers = n_layers;
+  geo->n_rings = n_rings;
+  return TKF_OK;
+}
+
+void tkf_ckf_options_default(tkf_ckf_options* o) {
+  if (!o) return;
+  o->chi2_max = 15.0;
+  o->beam = 3;
+  o->max_holes = 2;
+  o->max_entries = 24;
 }
 
 tkf_status tkf_field_create(tkf_context ctx, const tkf_field_desc* d, tkf_field* out) {
@@ -503,6 +573,83 @@ tkf_status tkf_estimate_seeds(tkf_context ctx, tkf_geometry geo, tkf_field field
   a.cov = out->cov;
   a.status = out->status;
   cudaError_t e = tkf::launch_estimate_seeds(a, field->f, ctx->sm_count, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, (std::string(fn) + ": launch").c_str());
+  return TKF_OK;
+}
+
+tkf_status tkf_find_tracks(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf_fit_options* o,
+                           const tkf_ckf_options* co, const tkf_ckf_inputs* in, const tkf_ckf_outputs* out,
+                           void* stream) {
+  const char* fn = "tkf_find_tracks";
+  if (!ctx) return fail(nullptr, TKF_ERR_BAD_HANDLE, std::string(fn) + ": NULL context");
+  if (!geo || !field || geo->ctx != ctx || field->ctx != ctx)
+    return fail(ctx, TKF_ERR_BAD_HANDLE, std::string(fn) + ": geometry or field handle NULL or from another context");
+  if (!o || !co || !in || !out) return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": NULL argument");
+  if (o->precision != TKF_FP64 || o->step_mode != TKF_STEP_ADAPTIVE)
+    return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": needs TKF_FP64 and TKF_STEP_ADAPTIVE");
+  if (!(o->tol > 0) || !(o->h_max > 0) || !(o->h_min > 0) || !(o->h_min <= o->h_max) || !(o->surf_tol > 0) ||
+      o->max_steps == 0 || !(o->mass > 0) || !isfinite(o->h_max))
+    return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": fit options out of range");
+  if (!(co->chi2_max >= 0) || co->beam < 1 || co->beam > 8 || co->max_entries < 1 ||
+      co->max_entries > TKF_CKF_MAX_ENTRIES)
+    return fail(ctx, TKF_ERR_INVALID_ARG,
+                std::string(fn) + ": ckf options need chi2_max >= 0, beam 1..8, max_entries 1..TKF_CKF_MAX_ENTRIES");
+  if (!geo->d_layers) return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": geometry has no layer structure");
+  if (in->n_seeds == 0) return TKF_OK;
+  if (!in->seed_sid || !in->seed_par || !in->seed_cov || !in->meas_offsets || !out->n_entries || !out->n_meas ||
+      !out->chi2 || !out->entry_sid || !out->entry_meas)
+    return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": NULL required pointer");
+  if (in->n_meas > 0 && (!in->loc0 || !in->loc1 || !in->v00 || !in->v01 || !in->v11))
+    return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": NULL measurement pointer");
+  const void* ptrs[] = {in->seed_par, in->seed_cov, in->loc0, in->loc1, in->v00, in->v01, in->v11, out->chi2};
+  for (const void* p : ptrs)
+    if (!aligned8(p)) return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": pointer not 8-byte aligned");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(ctx, TKF_ERR_DEVICE, std::string(fn) + ": cudaSetDevice failed");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t need = tkf::ckf_workspace_bytes(in->n_seeds, co->beam);
+  if (need > ctx->ckf_ws_bytes) {
+    cudaError_t e = cudaStreamSynchronize(st);  // the old store may still be in use
+    if (e != cudaSuccess) return cuda_fail(ctx, e, (std::string(fn) + ": stream synchronize").c_str());
+    if (ctx->ckf_ws) cudaFree(ctx->ckf_ws);
+    ctx->ckf_ws = nullptr;
+    ctx->ckf_ws_bytes = 0;
+    e = cudaMalloc(&ctx->ckf_ws, need);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, (std::string(fn) + ": branch store cudaMalloc").c_str());
+    ctx->ckf_ws_bytes = need;
+  }
+  tkf_fit_inputs dummy_in{};
+  tkf::FitArgs fa = make_args(geo, o, &dummy_in, nullptr);
+  tkf::CkfArgs a{};
+  a.n_seeds = in->n_seeds;
+  a.seed_sid = in->seed_sid;
+  a.seed_par = in->seed_par;
+  a.seed_cov = in->seed_cov;
+  a.meas_off = in->meas_offsets;
+  a.loc0 = in->loc0;
+  a.loc1 = in->loc1;
+  a.v00 = in->v00;
+  a.v01 = in->v01;
+  a.v11 = in->v11;
+  a.surf = geo->d_surf;
+  a.n_surf = geo->n;
+  a.layers = geo->d_layers;
+  a.n_layers = geo->n_layers;
+  a.rings = geo->d_rings;
+  a.layer_of = geo->d_layer_of;
+  a.mat = fa.mat;
+  a.opt = fa.opt;
+  a.chi2_max = co->chi2_max;
+  a.beam = co->beam;
+  a.max_holes = co->max_holes;
+  a.max_entries = co->max_entries;
+  a.n_entries = out->n_entries;
+  a.n_meas_out = out->n_meas;
+  a.chi2 = out->chi2;
+  a.entry_sid = out->entry_sid;
+  a.entry_meas = out->entry_meas;
+  a.ws = ctx->ckf_ws;
+  cudaError_t e = tkf::launch_find_tracks(a, field->f, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, (std::string(fn) + ": launch").c_str());
   return TKF_OK;
 }

@@ -1,0 +1,460 @@
+// tkf_ckf.cu -- track finding with a combinatorial Kalman filter (the step of the chain of
+// Sec. 2 between seeding and fitting; the algorithm and the navigation read for this library
+// are stated in include/tkf.h at tkf_find_tracks).
+//
+// One thread per seed, FP64 throughout (the fit's RKN propagation, material and gain-matrix
+// update). Each thread keeps its beam of branches, their children and its best ended branch in
+// a workspace slot of global memory (a branch: state, covariance, counters and up to 32 entries,
+// 464 bytes); the branches are read and written once per step, the geometry, layer tables and
+// measurements are gathered through L1/L2.
+
+#include "tkf_fit_impl.cuh"
+
+namespace tkf {
+namespace {
+
+constexpr int kCkfChildren = 3;         // measurements a branch may take on one surface
+constexpr int kCkfMaxLayers = 32;
+constexpr int kCkfBlock = 128;
+
+struct CkfBranch {
+  double p[5];
+  double C[15];
+  double h_ctrl, chi2;
+  uint32_t n_meas, holes, n_entries, order;
+  int32_t sid;  // current surface, -1 before the seed surface
+  uint32_t pad;
+  uint32_t e_sid[TKF_CKF_MAX_ENTRIES];
+  int32_t e_meas[TKF_CKF_MAX_ENTRIES];
+};
+
+__device__ __forceinline__ uint32_t slots_per_seed(uint32_t beam) { return beam * (kCkfChildren + 2) + 1; }
+
+// ranking of branches: more measurements, fewer consecutive holes, lower chi2, created earlier
+__device__ __forceinline__ bool better(const CkfBranch& a, const CkfBranch& b) {
+  if (a.n_meas != b.n_meas) return a.n_meas > b.n_meas;
+  if (a.holes != b.holes) return a.holes < b.holes;
+  if (a.chi2 != b.chi2) return a.chi2 < b.chi2;
+  return a.order < b.order;
+}
+
+__device__ __forceinline__ void copy_branch(CkfBranch& d, const CkfBranch& s, uint32_t n_entries) {
+  for (int j = 0; j < 5; ++j) d.p[j] = s.p[j];
+  for (int j = 0; j < 15; ++j) d.C[j] = s.C[j];
+  d.h_ctrl = s.h_ctrl;
+  d.chi2 = s.chi2;
+  d.n_meas = s.n_meas;
+  d.holes = s.holes;
+  d.n_entries = s.n_entries;
+  d.order = s.order;
+  d.sid = s.sid;
+  for (uint32_t j = 0; j < n_entries; ++j) {
+    d.e_sid[j] = s.e_sid[j];
+    d.e_meas[j] = s.e_meas[j];
+  }
+}
+
+__device__ __forceinline__ void module_half(const CkfArgs& a, uint32_t id, double& hu, double& hv) {
+  const int li = a.layer_of[id];
+  hu = li >= 0 ? a.layers[8 * li + 6] : 1e300;
+  hv = li >= 0 ? a.layers[8 * li + 7] : 1e300;
+}
+
+// modules of layer li around the point q: phi bin and row (barrel) or ring (disk), +-1 each
+__device__ int layer_candidates(const CkfArgs& a, uint32_t li, const double q[3], uint32_t out[9]) {
+  const double* l = a.layers + 8 * li;
+  double phi = atan2(q[1], q[0]);
+  if (phi < 0.0) phi += 2.0 * kPi;
+  int n = 0;
+  if (l[0] == 0.0) {
+    const int nphi = int(l[2]), nrows = int(l[3]);
+    const int ip0 = int(floor(phi / (2.0 * kPi / nphi) + 0.5));
+    const int iz0 = int(floor(q[2] / l[4] + 0.5 * nrows));
+    for (int iz = iz0 - 1; iz <= iz0 + 1; ++iz) {
+      if (iz < 0 || iz >= nrows) continue;
+      for (int d = -1; d <= 1; ++d) out[n++] = uint32_t(l[5]) + uint32_t(iz * nphi + ((ip0 + d) % nphi + nphi) % nphi);
+    }
+  } else {
+    const int nr = int(l[2]);
+    const double r = hypot(q[0], q[1]);
+    const int k0 = int(floor((r - l[5]) / l[4]));
+    for (int k = k0 - 1; k <= k0 + 1; ++k) {
+      if (k < 0 || k >= nr) continue;
+      const double* rg = a.rings + 4 * (uint32_t(l[3]) + uint32_t(k));
+      const int nphi = int(rg[1]);
+      const int ip0 = int(floor(phi / (2.0 * kPi / nphi) + 0.5));
+      for (int d = -1; d <= 1; ++d) out[n++] = uint32_t(rg[2]) + uint32_t(((ip0 + d) % nphi + nphi) % nphi);
+    }
+  }
+  return n;
+}
+
+// straight-line path to the outer face of layer li if ahead and within its extent, else -1
+__device__ double layer_path(const CkfArgs& a, uint32_t li, const double x[3], const double T[3]) {
+  const double* l = a.layers + 8 * li;
+  double s;
+  if (l[0] == 0.0) {
+    const double aa = T[0] * T[0] + T[1] * T[1], b = x[0] * T[0] + x[1] * T[1];
+    const double rf = sqrt((l[1] + 1.0) * (l[1] + 1.0) + l[6] * l[6]);
+    const double c = x[0] * x[0] + x[1] * x[1] - rf * rf;
+    if (!(aa > 0.0) || c >= 0.0) return -1.0;
+    s = (-b + sqrt(b * b - aa * c)) / aa;
+    if (fabs(x[2] + s * T[2]) > 0.5 * l[3] * l[4] + 10.0) return -1.0;
+  } else {
+    if (T[2] == 0.0) return -1.0;
+    s = (l[1] + (l[1] > 0.0 ? 1.0 : -1.0) - x[2]) / T[2];
+    if (!(s > 0.0)) return -1.0;
+    const double r = hypot(x[0] + s * T[0], x[1] + s * T[1]);
+    if (r < l[5] - 10.0 || r > l[5] + l[2] * l[4] + 10.0) return -1.0;
+  }
+  return s > 0.0 ? s : -1.0;
+}
+
+__device__ __forceinline__ bool listed(const uint32_t* v, int n, uint32_t id) {
+  for (int j = 0; j < n; ++j)
+    if (v[j] == id) return true;
+  return false;
+}
+
+// nearest of `cand` crossed by the parabola x + s T + s^2/2 k within bounds and margin
+__device__ int nearest_crossed(const CkfArgs& a, const uint32_t* cand, int nc, const double x[3], const double T[3],
+                               const double k[3], double bend, const uint32_t* skip, int nskip, double& s_out) {
+  int best = -1;
+  double best_s = 0.0;
+  for (int j = 0; j < nc; ++j) {
+    const uint32_t id = cand[j];
+    if (id >= a.n_surf || listed(skip, nskip, id)) continue;
+    const double* rec = a.surf + size_t(id) * kSurfStride;
+    const double u[3] = {rec[0], rec[1], rec[2]}, v[3] = {rec[3], rec[4], rec[5]};
+    const double n[3] = {rec[6], rec[7], rec[8]}, c[3] = {rec[9], rec[10], rec[11]};
+    const double d[3] = {c[0] - x[0], c[1] - x[1], c[2] - x[2]};
+    const double dist = dot3(n, d), an = dot3(n, T), bn = dot3(n, k);
+    if (an == 0.0) continue;
+    double s = dist / an;
+    const double disc = an * an + 2.0 * bn * dist;
+    if (disc >= 0.0) {
+      const double q2 = 2.0 * dist / (an + copysign(sqrt(disc), an));
+      if (isfinite(q2)) s = q2;
+    }
+    if (!(s > 1e-3)) continue;
+    const double h = 0.5 * s * s;
+    const double q[3] = {x[0] + s * T[0] + h * k[0] - c[0], x[1] + s * T[1] + h * k[1] - c[1],
+                         x[2] + s * T[2] + h * k[2] - c[2]};
+    const double margin = 1.0 + s * s * s * bend * bend / 6.0;
+    double hu, hv;
+    module_half(a, id, hu, hv);
+    if (fabs(dot3(u, q)) > hu + margin || fabs(dot3(v, q)) > hv + margin) continue;
+    if (best < 0 || s < best_s || (s == best_s && id < uint32_t(best))) {
+      best = int(id);
+      best_s = s;
+    }
+  }
+  s_out = best_s;
+  return best;
+}
+
+// the next module from (x, T) on surface `cur`: the nearest crossing among the current layer's
+// modules around x and the modules of the layers ahead (in order of face path)
+__device__ int navigate(const CkfArgs& a, int cur, const double x[3], const double T[3], const double k[3],
+                        double bend, const uint32_t* skip, int nskip) {
+  uint32_t cand[9];
+  int best = -1;
+  double best_s = 0.0;
+  const int cur_layer = cur >= 0 ? a.layer_of[cur] : -1;
+  if (cur_layer >= 0) {
+    uint32_t sk[5];
+    for (int j = 0; j < nskip; ++j) sk[j] = skip[j];
+    sk[nskip] = uint32_t(cur);
+    const int nc = layer_candidates(a, uint32_t(cur_layer), x, cand);
+    best = nearest_crossed(a, cand, nc, x, T, k, bend, sk, nskip + 1, best_s);
+  }
+  double ls[kCkfMaxLayers];
+  for (uint32_t li = 0; li < a.n_layers; ++li) ls[li] = int(li) == cur_layer ? -1.0 : layer_path(a, li, x, T);
+  // layers in order of face path (ties: lower index first), as a repeated minimum search
+  double last_s = -1.0;
+  int last_li = -1;
+  for (uint32_t it = 0; it < a.n_layers; ++it) {
+    int pick = -1;
+    for (uint32_t li = 0; li < a.n_layers; ++li) {
+      const double s = ls[li];
+      if (!(s > 0.0)) continue;
+      const bool after = s > last_s || (s == last_s && int(li) > last_li);
+      if (!after) continue;
+      if (pick < 0 || s < ls[pick]) pick = int(li);
+    }
+    if (pick < 0) break;
+    const double sl = ls[pick];
+    last_s = sl;
+    last_li = pick;
+    if (best >= 0 && sl > best_s + 20.0) break;
+    const double h = 0.5 * sl * sl;
+    const double q[3] = {x[0] + sl * T[0] + h * k[0], x[1] + sl * T[1] + h * k[1], x[2] + sl * T[2] + h * k[2]};
+    const int nc = layer_candidates(a, uint32_t(pick), q, cand);
+    double sm = 0.0;
+    const int m = nearest_crossed(a, cand, nc, x, T, k, bend, skip, nskip, sm);
+    if (m >= 0 && (best < 0 || sm < best_s)) {
+      best = m;
+      best_s = sm;
+    }
+  }
+  return best;
+}
+
+// From a branch's filtered state on its surface: material, navigation, RKN propagation and
+// covariance transport to the next module; returns its id (-1: none ahead, or stopped).
+template <class F>
+__device__ int predict(const CkfArgs& a, const F& fld, const CkfBranch& br, double pp[5], double Cp[15],
+                       double& h_ctrl) {
+  Surf sc;
+  load_surf(a.surf, uint32_t(br.sid), sc);
+  double sph, cph, sth, cth;
+  sincos(br.p[2], &sph, &cph);
+  sincos(br.p[3], &sth, &cth);
+  const double T0[3] = {sth * cph, sth * sph, cth};
+  double lam = br.p[4], th0sq;
+  if (material(sc, a.mat, a.opt.mass, T0, lam, th0sq) & ~(TKF_TRACK_OUT_OF_FIELD)) return -1;
+  double x[3];
+  for (int j = 0; j < 3; ++j) x[j] = sc.c[j] + br.p[0] * sc.u[j] + br.p[1] * sc.v[j];
+  double B[3];
+  bool oof = false;
+  fld.at(x, B, oof);
+  const double bend = kKappa * fabs(lam) * sqrt(dot3(B, B));
+  const double kc[3] = {kKappa * lam * (T0[1] * B[2] - T0[2] * B[1]), kKappa * lam * (T0[2] * B[0] - T0[0] * B[2]),
+                        kKappa * lam * (T0[0] * B[1] - T0[1] * B[0])};
+  uint32_t skip[4];
+  int nskip = 0;
+  for (int tries = 0; tries < 4; ++tries) {
+    const int m = navigate(a, br.sid, x, T0, kc, bend, skip, nskip);
+    if (m < 0) return -1;
+    Surf s;
+    load_surf(a.surf, uint32_t(m), s);
+    double r[3] = {x[0], x[1], x[2]}, T[3] = {T0[0], T0[1], T0[2]};
+    double dr[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    double dT[3][3] = {{-sth * sph, sth * cph, 0.0}, {cth * cph, cth * sph, -sth}, {0, 0, 0}};
+    double kend[3], h = br.h_ctrl;
+    uint32_t att = 0, rej = 0;
+    StepLearn learn{nullptr, 0, nullptr, 0.0f};
+    const uint32_t st = propagate<kPlain, 3>(fld, a.opt, s, r, T, lam, dr, dT, 0.0, h, att, rej, kend, learn);
+    const double d[3] = {r[0] - s.c[0], r[1] - s.c[1], r[2] - s.c[2]};
+    double hu, hv;
+    module_half(a, uint32_t(m), hu, hv);
+    if ((st & ~TKF_TRACK_OUT_OF_FIELD) || fabs(dot3(s.u, d)) > hu || fabs(dot3(s.v, d)) > hv) {
+      skip[nskip++] = uint32_t(m);
+      continue;
+    }
+    // bound parameters and the transport Jacobian at the target (path correction)
+    const double inv_norm = 1.0 / sqrt(dot3(T, T));
+    const double tn[3] = {T[0] * inv_norm, T[1] * inv_norm, T[2] * inv_norm};
+    const double st2 = sqrt(tn[0] * tn[0] + tn[1] * tn[1]), inv_st = 1.0 / st2;
+    const double ct2 = tn[2], cp2 = tn[0] * inv_st, sp2 = tn[1] * inv_st;
+    const double inv_nT = 1.0 / dot3(s.n, T);
+    double J[5][5];
+    for (int c = 0; c < 5; ++c) {
+      double xx[3], tt[3], out[4];
+      for (int j = 0; j < 3; ++j) {
+        xx[j] = (c == 0) ? sc.u[j] : (c == 1) ? sc.v[j] : dr[c - 2][j];
+        tt[j] = (c < 2) ? 0.0 : dT[c - 2][j];
+      }
+      jac_column(s.n, s.u, s.v, T, kend, inv_nT, sp2, cp2, st2, ct2, inv_st, xx, tt, out);
+      for (int rr = 0; rr < 4; ++rr) J[rr][c] = out[rr];
+      J[4][c] = (c == 4) ? 1.0 : 0.0;
+    }
+    pp[0] = dot3(s.u, d);
+    pp[1] = dot3(s.v, d);
+    pp[2] = atan2(tn[1], tn[0]);
+    pp[3] = acos(tn[2]);
+    pp[4] = lam;
+    for (int j = 0; j < 15; ++j) Cp[j] = br.C[j];
+    Cp[S(2, 2)] += th0sq / (sth * sth);
+    Cp[S(3, 3)] += th0sq;
+    transport_cov<1>(J, Cp, 0u, 0xffffffffu);
+    h_ctrl = h;
+    return m;
+  }
+  return -1;
+}
+
+// predicted chi2 of a measurement (no update)
+__device__ __forceinline__ bool meas_chi2(const double pp[5], const double Cp[15], double m0, double m1, double V00,
+                                          double V01, double V11, double& chi2) {
+  const double S00 = Cp[S(0, 0)] + V00, S01 = Cp[S(0, 1)] + V01, S11 = Cp[S(1, 1)] + V11;
+  const double det = S00 * S11 - S01 * S01;
+  if (!(S00 > 0.0 && det > 0.0)) return false;
+  const double idet = 1.0 / det;
+  const double Si00 = S11 * idet, Si01 = -S01 * idet, Si11 = S00 * idet;
+  const double r0 = m0 - pp[0], r1 = m1 - pp[1];
+  chi2 = r0 * (Si00 * r0 + Si01 * r1) + r1 * (Si01 * r0 + Si11 * r1);
+  return true;
+}
+
+// gain-matrix update, Joseph form (as in the fit)
+__device__ void update(double p[5], double C[15], double m0, double m1, double V00, double V01, double V11,
+                       double& chi2) {
+  const double S00 = C[S(0, 0)] + V00, S01 = C[S(0, 1)] + V01, S11 = C[S(1, 1)] + V11;
+  const double idet = 1.0 / (S00 * S11 - S01 * S01);
+  const double Si00 = S11 * idet, Si01 = -S01 * idet, Si11 = S00 * idet;
+  const double r0 = m0 - p[0], r1 = m1 - p[1];
+  chi2 = r0 * (Si00 * r0 + Si01 * r1) + r1 * (Si01 * r0 + Si11 * r1);
+  double K[5][2];
+  for (int j = 0; j < 5; ++j) {
+    const double U0 = C[S(j, 0)], U1 = C[S(j, 1)];
+    K[j][0] = U0 * Si00 + U1 * Si01;
+    K[j][1] = U0 * Si01 + U1 * Si11;
+  }
+  for (int j = 0; j < 5; ++j) p[j] += K[j][0] * r0 + K[j][1] * r1;
+  double X[5][5];
+  for (int r_ = 0; r_ < 5; ++r_)
+    for (int c_ = 0; c_ < 5; ++c_) X[r_][c_] = C[S(r_, c_)] - K[r_][0] * C[S(0, c_)] - K[r_][1] * C[S(1, c_)];
+  double Y[5][2];
+  for (int r_ = 0; r_ < 5; ++r_) {
+    Y[r_][0] = X[r_][0] - (K[r_][0] * V00 + K[r_][1] * V01);
+    Y[r_][1] = X[r_][1] - (K[r_][0] * V01 + K[r_][1] * V11);
+  }
+  for (int r_ = 0; r_ < 5; ++r_)
+    for (int c_ = r_; c_ < 5; ++c_) C[S(r_, c_)] = X[r_][c_] - Y[r_][0] * K[c_][0] - Y[r_][1] * K[c_][1];
+  if (p[2] > kPi) p[2] -= 2.0 * kPi;
+  if (p[2] <= -kPi) p[2] += 2.0 * kPi;
+}
+
+template <class F>
+__global__ void __launch_bounds__(kCkfBlock) find_tracks_kernel(const CkfArgs a, const F fld) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n_seeds) return;
+  const uint32_t n = a.n_seeds, B = a.beam;
+  CkfBranch* act = static_cast<CkfBranch*>(a.ws) + size_t(i) * slots_per_seed(B);
+  CkfBranch* kids = act + B;
+  CkfBranch* best = kids + B * (kCkfChildren + 1);
+  bool have_best = false;
+  const uint32_t seed_sid = a.seed_sid[i];
+  if (seed_sid < a.n_surf) {
+    CkfBranch& b0 = act[0];
+    for (int j = 0; j < 5; ++j) b0.p[j] = a.seed_par[size_t(j) * n + i];
+    for (int j = 0; j < 15; ++j) b0.C[j] = a.seed_cov[size_t(j) * n + i];
+    b0.h_ctrl = a.opt.h_max;
+    b0.chi2 = 0.0;
+    b0.n_meas = b0.holes = b0.n_entries = 0;
+    b0.order = 0;
+    b0.sid = -1;
+    uint32_t n_act = 1, order = 1;
+    bool first = true;
+    // every step adds an entry to each surviving branch: at most max_entries + 1 steps
+    for (uint32_t step = 0; n_act > 0 && step <= a.max_entries + 1; ++step) {
+      uint32_t n_kids = 0;
+      for (uint32_t bi = 0; bi < n_act; ++bi) {
+        const CkfBranch& br = act[bi];
+        double pp[5], Cp[15], h = br.h_ctrl;
+        int target;
+        if (first) {
+          target = int(seed_sid);
+          for (int j = 0; j < 5; ++j) pp[j] = br.p[j];
+          for (int j = 0; j < 15; ++j) Cp[j] = br.C[j];
+        } else {
+          target = br.n_entries >= a.max_entries ? -1 : predict(a, fld, br, pp, Cp, h);
+        }
+        if (target < 0) {  // the branch ends
+          if (!have_best || better(br, *best)) {
+            copy_branch(*best, br, br.n_entries);
+            have_best = true;
+          }
+          continue;
+        }
+        // the (at most 3) compatible measurements with the lowest chi2 (ties: lower index)
+        double kc2[kCkfChildren];
+        uint32_t km[kCkfChildren];
+        int nk = 0;
+        for (uint32_t mi = a.meas_off[target]; mi < a.meas_off[target + 1]; ++mi) {
+          double c2;
+          if (!meas_chi2(pp, Cp, a.loc0[mi], a.loc1[mi], a.v00[mi], a.v01[mi], a.v11[mi], c2)) continue;
+          if (!(c2 < a.chi2_max)) continue;
+          int pos = nk;
+          while (pos > 0 && (c2 < kc2[pos - 1] || (c2 == kc2[pos - 1] && mi < km[pos - 1]))) --pos;
+          if (pos >= kCkfChildren) continue;
+          for (int q = (nk < kCkfChildren ? nk : kCkfChildren - 1); q > pos; --q) {
+            kc2[q] = kc2[q - 1];
+            km[q] = km[q - 1];
+          }
+          kc2[pos] = c2;
+          km[pos] = mi;
+          if (nk < kCkfChildren) ++nk;
+        }
+        for (int q = 0; q < nk; ++q) {
+          CkfBranch& ch = kids[n_kids++];
+          copy_branch(ch, br, br.n_entries);
+          for (int j = 0; j < 5; ++j) ch.p[j] = pp[j];
+          for (int j = 0; j < 15; ++j) ch.C[j] = Cp[j];
+          const uint32_t mi = km[q];
+          double c2;
+          update(ch.p, ch.C, a.loc0[mi], a.loc1[mi], a.v00[mi], a.v01[mi], a.v11[mi], c2);
+          ch.h_ctrl = h;
+          ch.chi2 += c2;
+          ch.n_meas += 1;
+          ch.holes = 0;
+          ch.sid = target;
+          ch.e_sid[ch.n_entries] = uint32_t(target);
+          ch.e_meas[ch.n_entries] = int32_t(mi);
+          ch.n_entries += 1;
+          ch.order = order++;
+        }
+        if (br.holes < a.max_holes) {
+          CkfBranch& ch = kids[n_kids++];
+          copy_branch(ch, br, br.n_entries);
+          for (int j = 0; j < 5; ++j) ch.p[j] = pp[j];
+          for (int j = 0; j < 15; ++j) ch.C[j] = Cp[j];
+          ch.h_ctrl = h;
+          ch.holes += 1;
+          ch.sid = target;
+          ch.e_sid[ch.n_entries] = uint32_t(target) | TKF_SID_NO_MEASUREMENT;
+          ch.e_meas[ch.n_entries] = -1;
+          ch.n_entries += 1;
+          ch.order = order++;
+        } else if (nk == 0 && (!have_best || better(br, *best))) {
+          copy_branch(*best, br, br.n_entries);  // one hole too many: ends before this surface
+          have_best = true;
+        }
+      }
+      first = false;
+      // the beam: the best B children, in rank order (at most 8 x 4 children: a bit mask of the taken)
+      n_act = n_kids < B ? n_kids : B;
+      uint32_t taken = 0;
+      for (uint32_t q = 0; q < n_act; ++q) {
+        int pick = -1;
+        for (uint32_t j = 0; j < n_kids; ++j)
+          if (!((taken >> j) & 1u) && (pick < 0 || better(kids[j], kids[pick]))) pick = int(j);
+        taken |= 1u << pick;
+        copy_branch(act[q], kids[pick], kids[pick].n_entries);
+      }
+    }
+  }
+  const uint32_t ne = have_best ? best->n_entries : 0;
+  a.n_entries[i] = ne;
+  a.n_meas_out[i] = have_best ? best->n_meas : 0;
+  a.chi2[i] = have_best ? best->chi2 : 0.0;
+  for (uint32_t j = 0; j < a.max_entries; ++j) {
+    a.entry_sid[size_t(j) * n + i] = j < ne ? best->e_sid[j] : 0u;
+    a.entry_meas[size_t(j) * n + i] = j < ne ? best->e_meas[j] : -1;
+  }
+}
+
+template <class F>
+cudaError_t launch_ckf(const CkfArgs& a, const F& fld, cudaStream_t stream) {
+  find_tracks_kernel<<<(a.n_seeds + kCkfBlock - 1) / kCkfBlock, kCkfBlock, 0, stream>>>(a, fld);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t ckf_workspace_bytes(uint32_t n_seeds, uint32_t beam) {
+  return size_t(n_seeds) * (beam * (kCkfChildren + 2) + 1) * sizeof(CkfBranch);
+}
+
+cudaError_t launch_find_tracks(const CkfArgs& a, const FieldDev& f, cudaStream_t stream) {
+  if (a.n_layers > uint32_t(kCkfMaxLayers)) return cudaErrorInvalidValue;
+  if (f.kind == TKF_FIELD_UNIFORM) {
+    if (f.b[0] == 0.0 && f.b[1] == 0.0) return launch_ckf(a, FieldUniformZ{f.b[2], float(f.b[2])}, stream);
+    return launch_ckf(a, FieldUniform{{f.b[0], f.b[1], f.b[2]}, {float(f.b[0]), float(f.b[1]), float(f.b[2])}},
+                      stream);
+  }
+  return launch_ckf(a, grid_policy(f), stream);
+}
+
+}  // namespace tkf

@@ -114,6 +114,38 @@ struct SeedArgs {
 };
 cudaError_t launch_estimate_seeds(const SeedArgs& a, const FieldDev& f, int sm_count, cudaStream_t stream);
 
+// Track finding (tkf_ckf.cu): one thread per seed, branch store in a workspace.
+struct CkfArgs {
+  uint32_t n_seeds;
+  const uint32_t* __restrict__ seed_sid;
+  const double* __restrict__ seed_par;  // [5][n_seeds]
+  const double* __restrict__ seed_cov;  // [15][n_seeds]
+  const uint32_t* __restrict__ meas_off;
+  const double* __restrict__ loc0;
+  const double* __restrict__ loc1;
+  const double* __restrict__ v00;
+  const double* __restrict__ v01;
+  const double* __restrict__ v11;
+  const double* __restrict__ surf;
+  uint32_t n_surf;
+  const double* __restrict__ layers;
+  uint32_t n_layers;
+  const double* __restrict__ rings;
+  const int32_t* __restrict__ layer_of;
+  MaterialDev mat;
+  OptionsDev opt;
+  double chi2_max;
+  uint32_t beam, max_holes, max_entries;
+  uint32_t* __restrict__ n_entries;
+  uint32_t* __restrict__ n_meas_out;
+  double* __restrict__ chi2;
+  uint32_t* __restrict__ entry_sid;   // [max_entries][n_seeds]
+  int32_t* __restrict__ entry_meas;   // [max_entries][n_seeds]
+  void* ws;                           // branch store
+};
+size_t ckf_workspace_bytes(uint32_t n_seeds, uint32_t beam);
+cudaError_t launch_find_tracks(const CkfArgs& a, const FieldDev& f, cudaStream_t stream);
+
 // Launch shape of the persistent fit: threads per block, blocks in the grid, tracks a warp
 // takes at a time (1..32 / group), the register cap of the kernel variant (255, or 128 / 64
 // for the mixed path, whose blocks then have at most 128 threads) and the lanes a track.
@@ -193,6 +225,9 @@ struct tkf_context_s {
   // staging for tkf_fit_host
   void* stage = nullptr;
   size_t stage_bytes = 0;
+  // branch store of track finding
+  void* ckf_ws = nullptr;
+  size_t ckf_ws_bytes = 0;
 };
 
 struct tkf_geometry_s {
@@ -201,6 +236,11 @@ struct tkf_geometry_s {
   double* d_surf = nullptr;
   uint32_t n = 0;
   tkf::MaterialDev mat{};
+  // navigation (track finding): layer rows, ring rows, layer of every surface (-1: none)
+  double* d_layers = nullptr;
+  double* d_rings = nullptr;
+  int32_t* d_layer_of = nullptr;
+  uint32_t n_layers = 0, n_rings = 0;
 };
 
 struct tkf_field_s {
