@@ -626,6 +626,7 @@ tkf_status tkf_find_tracks(tkf_context ctx, tkf_geometry geo, tkf_field field, c
   a.seed_par = in->seed_par;
   a.seed_cov = in->seed_cov;
   a.meas_off = in->meas_offsets;
+  a.n_meas = in->n_meas;
   a.loc0 = in->loc0;
   a.loc1 = in->loc1;
   a.v00 = in->v00;

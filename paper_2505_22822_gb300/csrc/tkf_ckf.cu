@@ -362,7 +362,8 @@ __global__ void __launch_bounds__(kCkfBlock) find_tracks_kernel(const CkfArgs a,
         double kc2[kCkfChildren];
         uint32_t km[kCkfChildren];
         int nk = 0;
-        for (uint32_t mi = a.meas_off[target]; mi < a.meas_off[target + 1]; ++mi) {
+        const uint32_t m_end = a.meas_off[target + 1] < a.n_meas ? a.meas_off[target + 1] : a.n_meas;
+        for (uint32_t mi = a.meas_off[target]; mi < m_end; ++mi) {
           double c2;
           if (!meas_chi2(pp, Cp, a.loc0[mi], a.loc1[mi], a.v00[mi], a.v01[mi], a.v11[mi], c2)) continue;
           if (!(c2 < a.chi2_max)) continue;

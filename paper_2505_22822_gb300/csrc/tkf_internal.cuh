@@ -121,6 +121,7 @@ struct CkfArgs {
   const double* __restrict__ seed_par;  // [5][n_seeds]
   const double* __restrict__ seed_cov;  // [15][n_seeds]
   const uint32_t* __restrict__ meas_off;
+  uint32_t n_meas;  // measurement rows: offsets beyond are clamped (never read past the arrays)
   const double* __restrict__ loc0;
   const double* __restrict__ loc1;
   const double* __restrict__ v00;
