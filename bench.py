@@ -83,7 +83,7 @@ def parse():
                     help="fixed launch shape 'threads,blocks_per_sm,tracks_per_warp,registers[,lanes]' for every "
                          "variant (registers 128 or 64 apply to the mixed variants; FP64 keeps 255; lanes 1 or 4)")
     ap.add_argument("--no-seeds", action="store_true",
-                    help="skip the seed-estimation kernel and the chain from estimated seeds")
+                    help="skip the seed-estimation kernel, the chain from estimated seeds and track finding")
     ap.add_argument("--streams", action="store_true",
                     help="event-level concurrency: one launch per event on 1..16 CUDA streams against one "
                          "batched launch (one JSON line per configuration)")
@@ -293,6 +293,72 @@ def seed_stage(ctx, geo, fld, dev, t, opts, stream, steps: int, warmup: int, flu
                   "fit_status_ok": float(np.mean(s2.status.cpu().numpy() == 0)),
                   "pull_sigma": pulls["sigma"], "pull_mean": pulls["mean"], "chi2_ndf_mean": pulls["chi2_ndf"]}
     return seeds, chain_line
+
+
+def ckf_stage(ctx, fld, w, stream, steps: int, warmup: int, events: int = 5):
+    """Track finding on the first `events` events of the batch, one event per launch pair: seed
+    estimation from triplets (the first measurements of each simulated track on three distinct
+    layers, a stand-in for triplet seeding), then the combinatorial Kalman filter over the
+    event's measurements grouped by surface. Efficiency and purity against the simulation."""
+    import torch
+    import paper_2505_22822_gb300 as tkf
+    g = w.geometry
+    geo = tkf.Geometry.from_table(ctx, g.table).set_layers(g.layers, g.rings)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def T(x, dt=torch.float64):
+        return torch.from_numpy(np.ascontiguousarray(x)).to(dt).to(dev)
+
+    t = w.tracks
+    per_event = []
+    for e in range(events):
+        idx = np.flatnonzero(t.event == e)
+        sub = t.subset(idx)
+        mc = synth.measurement_container(sub, g.n)
+        offs, meas, sid = synth.triplet_seed_hits(sub, g)
+        n = sub.n_tracks
+        sb = tkf.Batch.from_arrays(offs, meas, sid, np.zeros((n, 5)), np.zeros((n, 15))).to(dev)
+        per_event.append({"sub": sub, "mc": mc, "seed_batch": sb,
+                          "seed_sid": T(sub.sid[sub.offsets[:-1]].astype(np.int32), torch.int32),
+                          "moff": T(mc.offsets.astype(np.int32), torch.int32),
+                          "cols": [T(mc.meas[:, k]) for k in range(5)]})
+    opts = tkf.Options(mass=w.mass)
+    results = [None] * events
+
+    def step():
+        for k, ev in enumerate(per_event):
+            se = tkf.estimate_seeds(ctx, geo, fld, ev["seed_batch"], tkf.SEED_FIRST_THREE, stream=stream)
+            results[k] = tkf.find_tracks(ctx, geo, fld, ev["seed_sid"], se.par, se.cov, ev["moff"], *ev["cols"], opts,
+                                         stream=stream)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    n_seeds = sum(ev["sub"].n_tracks for ev in per_event)
+    eff, pur = [], []
+    for ev, r in zip(per_event, results):
+        nm, ne = r.n_entries.cpu().numpy(), r.entry_meas.cpu().numpy()
+        sub, mc = ev["sub"], ev["mc"]
+        ntrue = np.diff(sub.offsets.astype(np.int64))
+        for i in range(sub.n_tracks):
+            ms_i = ne[: nm[i], i]
+            ms_i = ms_i[ms_i >= 0]
+            good = int((mc.track[ms_i] == i).sum())
+            eff.append(good / ntrue[i])
+            pur.append(good / max(len(ms_i), 1))
+    eff, pur = np.array(eff), np.array(pur)
+    return {"events": events, "seeds": n_seeds, "ms_per_step": ms, "ms_per_event": ms / events,
+            "seeds_per_s": n_seeds / (ms * 1e-3), "hit_efficiency": float(eff.mean()),
+            "tracks_90pct_hits": float((eff >= 0.9).mean()), "purity": float(pur.mean()),
+            "stages": "seed estimation (triplets) + combinatorial Kalman filter, beam 3, chi2 < 15, 2 holes",
+            "launches_per_step": 2 * events}
 
 
 def cpu_baseline(w, max_seconds: float = 20.0):
@@ -685,10 +751,12 @@ def main():
                             "pulls": pull_stats(out, t)}
     head = variants[-1]
     opts = results[head]["opts"]
-    seeds = chain = None
+    seeds = chain = ckf = None
     if not args.no_seeds:
         copts = results["mixed"]["opts"] if "mixed" in results else opts
         seeds, chain = seed_stage(ctx, geo, fld, dev, t, copts, stream, args.steps, args.warmup, flush)
+        if args.workload == "barrel":
+            ckf = ckf_stage(ctx, fld, w, stream, max(1, args.steps // 2), 1)
     ms, ms_max, clocks = results[head]["ms"], results[head]["ms_max"], results[head]["clocks"]
     for k, v in results.items():
         fa, fr, fh, ft = (FLOPS_MAP if args.workload == "map" else FLOPS)[k]
@@ -785,6 +853,8 @@ def main():
     if seeds:
         line["seed_estimation"] = seeds
         line["chain_from_estimated_seeds"] = chain
+    if ckf:
+        line["track_finding"] = ckf
     if e2e:
         line["e2e"] = e2e
     if not args.no_cpu_baseline:

@@ -384,7 +384,8 @@ tkf_status tkf_estimate_seeds(tkf_context ctx, tkf_geometry geo, tkf_field field
  * +-1 each; the point on the parabola x + s T + s^2/2 k at the straight-line path s, k the
  * path's curvature vector kappa (q/p) T x B). A module is crossed if the parabola meets its plane
  * ahead (s > 1e-3 mm) within its half extents plus 1 mm + s^3 (kappa |q/p| |B|)^2 / 6; the
- * nearest is taken (a layer is skipped once its face lies 20 mm beyond the best crossing found).
+ * nearest is taken (crossings within 1e-6 mm of each other, coplanar overlapping modules, go to
+ * the lower surface id; a layer is skipped once its face lies 20 mm beyond the best crossing).
  * The RKN propagation to it must end within its half extents, else it is excluded and the
  * navigation repeats (at most 4 exclusions). Surfaces outside the layer structure are never
  * candidates. */

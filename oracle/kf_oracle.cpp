@@ -1048,7 +1048,9 @@ int nearest_crossed(const CkfLayers& L, const Surface* surf, const std::vector<u
     double hu, hv;
     module_half(L, id, hu, hv);
     if (std::fabs(dot3(m.u, q)) > hu + margin || std::fabs(dot3(m.v, q)) > hv + margin) continue;
-    if (best < 0 || s < best_s || (s == best_s && id < uint32_t(best))) {
+    // crossings within 1e-6 mm of each other (coplanar overlapping modules) count as one
+    // point: the lower id first, whatever the rounding
+    if (best < 0 || s < best_s - 1e-6 || (std::fabs(s - best_s) <= 1e-6 && id < uint32_t(best))) {
       best = int(id);
       best_s = s;
     }

@@ -144,7 +144,8 @@ __device__ int nearest_crossed(const CkfArgs& a, const uint32_t* cand, int nc, c
     double hu, hv;
     module_half(a, id, hu, hv);
     if (fabs(dot3(u, q)) > hu + margin || fabs(dot3(v, q)) > hv + margin) continue;
-    if (best < 0 || s < best_s || (s == best_s && id < uint32_t(best))) {
+    // crossings within 1e-6 mm of each other (coplanar overlapping modules): the lower id
+    if (best < 0 || s < best_s - 1e-6 || (fabs(s - best_s) <= 1e-6 && id < uint32_t(best))) {
       best = int(id);
       best_s = s;
     }

@@ -58,8 +58,8 @@ def test_noise_free_tracks_are_found_exactly():
 
 def test_pion_event_efficiency_and_purity():
     """2,000 pions in one event, seeds from triplets on three distinct layers (helix estimate):
-    mean hit efficiency above 97 %, at least 94 % of the tracks with 90 % of their hits, purity
-    above 99.5 %."""
+    mean hit efficiency above 99 %, at least 99 % of the tracks with 90 % of their hits, purity
+    above 99.9 % (measured: 99.5 %, 99.6 %, 100 %)."""
     w = synth.barrel_workload(n_events=1, lo=2000, hi=2000, seed=31)
     t, g = w.tracks, w.geometry
     mc = synth.measurement_container(t, g.n)
@@ -69,7 +69,7 @@ def test_pion_event_efficiency_and_purity():
     r = _find(w, mc, seed_sid[ok], par[ok], cov[ok])
     eff, pur = _eff_pur(r, mc, t, np.flatnonzero(ok))
     print(eff.mean(), (eff >= 0.9).mean(), pur.mean())
-    assert eff.mean() > 0.97 and (eff >= 0.9).mean() > 0.94 and pur.mean() > 0.995
+    assert eff.mean() > 0.99 and (eff >= 0.9).mean() > 0.99 and pur.mean() > 0.999
 
 
 def test_found_candidates_fit_like_the_true_tracks():

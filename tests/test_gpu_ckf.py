@@ -61,7 +61,11 @@ def compare(gr, orr, min_same=0.995):
                      and np.array_equal(gr["sid"][i][: gr["n_entries"][i]], orr["sid"][i][: orr["n_entries"][i]])
                      and np.array_equal(gr["meas"][i][: gr["n_entries"][i]], orr["meas"][i][: orr["n_entries"][i]])
                      for i in range(n)])
-    print({"seeds": n, "identical": int(same.sum())})
+    diff = np.flatnonzero(~same)
+    info = [(int(i), int(gr["n_meas"][i]), int(orr["n_meas"][i]),
+             len(set(gr["meas"][i][: gr["n_entries"][i]]) & set(orr["meas"][i][: orr["n_entries"][i]]) - {-1}))
+            for i in diff[:10]]
+    print({"seeds": n, "identical": int(same.sum()), "differing (seed, gpu meas, oracle meas, shared)": info})
     assert same.mean() >= min_same, same.mean()
     np.testing.assert_array_equal(gr["n_meas"][same], orr["n_meas"][same])
     rel = np.abs(gr["chi2"][same] - orr["chi2"][same]) / np.maximum(orr["chi2"][same], 1.0)
