@@ -386,9 +386,9 @@ tkf_status tkf_estimate_seeds(tkf_context ctx, tkf_geometry geo, tkf_field field
  * ahead (s > 1e-3 mm) within its half extents plus 1 mm + s^3 (kappa |q/p| |B|)^2 / 6; the
  * nearest is taken (crossings within 1e-6 mm of each other, coplanar overlapping modules, go to
  * the lower surface id; a layer is skipped once its face lies 20 mm beyond the best crossing).
- * The RKN propagation to it must end within its half extents, else it is excluded and the
- * navigation repeats (at most 4 exclusions). Surfaces outside the layer structure are never
- * candidates. */
+ * The RKN propagation to it must end within its half extents in at most min(max_steps, 100)
+ * attempts, else it is excluded and the navigation repeats (at most 4 exclusions). Surfaces
+ * outside the layer structure are never candidates. */
 #define TKF_CKF_MAX_ENTRIES 32u
 
 /* Layer structure for navigation, host arrays copied to the device (replacing an earlier one).

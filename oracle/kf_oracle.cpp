@@ -911,6 +911,10 @@ void fit_track(const Surface* surf, uint32_t n_surf, const Field& f, const Opts&
 
 constexpr int kChildren = 3;        // measurements a branch may take on one surface
 constexpr int kCkfMaxEntries = 32;  // entries (measurements and holes) a candidate may have
+// RKN attempts a propagation to the next module may take (the fit allows max_steps): a branch
+// whose state cannot reach the module in as many (a seed with far too low a momentum curls)
+// excludes it, as an out-of-bounds landing does
+constexpr uint32_t kCkfMaxSteps = 100;
 
 struct CkfOpts {
   double chi2_max;
@@ -1098,9 +1102,11 @@ int navigate(const CkfLayers& L, const Surface* surf, uint32_t n_surf, int cur, 
   return best;
 }
 
-void find_track(const Surface* surf, uint32_t n_surf, const Field& f, const Opts& o, const CkfOpts& co,
+void find_track(const Surface* surf, uint32_t n_surf, const Field& f, const Opts& o_fit, const CkfOpts& co,
                 const CkfLayers& L, const uint32_t* meas_off, const double* meas, uint32_t seed_sid,
                 const double* seed_par, const double* seed_cov, Branch& best, bool& have_best) {
+  Opts o = o_fit;
+  o.max_steps = std::min(o.max_steps, kCkfMaxSteps);
   std::vector<Branch> active(1), children, ended;
   uint32_t order = 0;
   Branch& b0 = active[0];

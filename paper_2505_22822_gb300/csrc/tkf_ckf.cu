@@ -16,6 +16,9 @@ namespace {
 constexpr int kCkfChildren = 3;         // measurements a branch may take on one surface
 constexpr int kCkfMaxLayers = 32;
 constexpr int kCkfBlock = 128;
+// RKN attempts a propagation to the next module may take: a branch whose state cannot reach
+// the module in as many (a seed with far too low a momentum curls) excludes it
+constexpr uint32_t kCkfMaxSteps = 100;
 
 struct CkfBranch {
   double p[5];
@@ -438,7 +441,9 @@ __global__ void __launch_bounds__(kCkfBlock) find_tracks_kernel(const CkfArgs a,
 }
 
 template <class F>
-cudaError_t launch_ckf(const CkfArgs& a, const F& fld, cudaStream_t stream) {
+cudaError_t launch_ckf(const CkfArgs& a_in, const F& fld, cudaStream_t stream) {
+  CkfArgs a = a_in;
+  if (a.opt.max_steps > kCkfMaxSteps) a.opt.max_steps = kCkfMaxSteps;
   find_tracks_kernel<<<(a.n_seeds + kCkfBlock - 1) / kCkfBlock, kCkfBlock, 0, stream>>>(a, fld);
   return cudaGetLastError();
 }
