@@ -53,7 +53,8 @@ class OOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("h_max", ctypes.c_double), ("h_min", ctypes.c_double),
                 ("surf_tol", ctypes.c_double), ("mass", ctypes.c_double),
                 ("max_steps", ctypes.c_uint32), ("ZA", ctypes.c_double), ("I_eV", ctypes.c_double),
-                ("rho", ctypes.c_double), ("hwp_eV", ctypes.c_double), ("mlp_bf16", ctypes.c_void_p)]
+                ("rho", ctypes.c_double), ("hwp_eV", ctypes.c_double), ("mlp_bf16", ctypes.c_void_p),
+                ("smoother", ctypes.c_int), ("inflation", ctypes.c_double)]
 
 
 @dataclass
@@ -66,6 +67,8 @@ class Options:
     max_steps: int = 10000   # step attempts per surface
     material: tuple = SI
     mlp: object = None       # 5057 BF16 weights (uint16) of the step proposer, or None
+    smoother: int = 0        # 0: RTS; 1: two-filter (backward filter + weighted mean with the seed)
+    inflation: float = 1e3   # two-filter: factor on the backward filter's starting covariance
 
     def _c(self) -> OOpts:
         o = OOpts()
@@ -73,6 +76,7 @@ class Options:
             self.surf_tol, self.mass
         o.max_steps = self.max_steps
         o.ZA, o.I_eV, o.rho, o.hwp_eV = self.material
+        o.smoother, o.inflation = int(self.smoother), float(self.inflation)
         if self.mlp is not None:
             w = np.ascontiguousarray(self.mlp, dtype=np.uint16)
             o._keep = w
@@ -100,6 +104,8 @@ def lib():
         L.orc_material.argtypes = [vp, ctypes.POINTER(OOpts), vp, vp, vp, vp]
         L.orc_linear_chain.restype = u32
         L.orc_linear_chain.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.orc_linear_chain_two_filter.restype = u32
+        L.orc_linear_chain_two_filter.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, vp, d, vp, vp]
         L.orc_fit_states.restype = u32
         L.orc_fit_states.argtypes = [vp, u32, ctypes.POINTER(OField), ctypes.POINTER(OOpts), u32, vp, vp,
                                      vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -245,6 +251,16 @@ def linear_chain(J, Q, p0, C0, m, V):
     st = lib().orc_linear_chain(N, _p(J), _p(Q), _p(p0), _p(C0), _p(m), _p(V), _p(ps), _p(Cs),
                                 _p(chi2), _p(pf), _p(Cf))
     return ps, Cs, float(chi2[0]), int(st), pf, Cf
+
+
+def linear_chain_two_filter(J, Q, p0, C0, m, V, inflation):
+    """Two-filter smoother of the linear chain: the smoothed state at step 0 and its status."""
+    N = m.shape[0]
+    J, Q, p0, C0, m, V = (_f64(x) for x in (J, Q, p0, C0, m, V))
+    ps, Cs = np.zeros(5), np.zeros((5, 5))
+    st = lib().orc_linear_chain_two_filter(N, _p(J), _p(Q), _p(p0), _p(C0), _p(m), _p(V), float(inflation), _p(ps),
+                                           _p(Cs))
+    return ps, Cs, st
 
 
 def fit_states(surfaces, fld: OField, opts: Options, meas, sid, seed_par, seed_cov):

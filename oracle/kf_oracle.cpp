@@ -89,6 +89,9 @@ struct Opts {
   double mass;      // particle hypothesis, GeV
   uint32_t max_steps;
   double ZA, I_eV, rho, hwp_eV;  // material: Z/A, mean excitation, density g/cm3, plasma energy
+  int smoother = 0;              // 0: RTS; 1: two-filter (forward filter, backward filter, weighted mean)
+  double inflation = 1e3;        // two-filter: the backward filter starts from the last filtered
+                                 // covariance times this factor
 };
 
 // ---------------------------------------------------------------- dense algebra
@@ -626,8 +629,12 @@ double bethe(double p, double m, const Opts& o) {
 // Thin-layer material at surface s, applied to the filtered state after the update.
 // Adds theta0^2 / sin^2(theta) to Var(phi) and theta0^2 to Var(theta) (Q, full 5x5), and
 // lowers |p| by the mean energy loss. Reading: no energy-loss variance; the material
-// Jacobian is the identity.
-uint32_t material(const Surface& s, const Opts& o, double p[5], double Q[25]) {
+// Jacobian is the identity. With `gain` (the backward filter's reversed particle, which crosses
+// the layer against the flight direction) |p| rises by the mean loss instead. Reading: theta0
+// and the loss are then evaluated at the reversed particle's momentum on arrival (the momentum
+// after the crossing in the flight direction), which differs from the forward evaluation at
+// second order in the loss.
+uint32_t material(const Surface& s, const Opts& o, double p[5], double Q[25], bool gain = false) {
   for (int i = 0; i < 25; ++i) Q[i] = 0.0;
   if (!(s.t > 0.0)) return 0;
   double r[3], T[3];
@@ -641,7 +648,7 @@ uint32_t material(const Surface& s, const Opts& o, double p[5], double Q[25]) {
   Q[2 * 5 + 2] = th0 * th0 / (sth * sth);
   Q[3 * 5 + 3] = th0 * th0;
   double dE = bethe(mom, o.mass, o) * o.rho * (x * 0.1) * 1e-3;  // GeV
-  double E2 = E - dE;
+  double E2 = gain ? E + dE : E - dE;
   if (!(E2 > o.mass)) return kParticleStopped;
   double mom2 = std::sqrt(E2 * E2 - o.mass * o.mass);
   p[4] = std::copysign(1.0 / mom2, p[4]);
@@ -773,6 +780,101 @@ struct States {
   std::vector<double> pp, Cp, pf, Cf, J, ps, Cs;
 };
 
+// ---------------------------------------------------------------- two-filter smoother
+// Reading of the optimal smoother (Sec. 4 ¶2: the smoothed parameters are the weighted mean of
+// a forward and a backward filter; Fraser-Potter form). For the first-surface result:
+//  * the forward filter runs as for RTS and gives the track's chi2;
+//  * the backward filter is a Kalman filter of the reversed particle (l0, l1, phi + pi,
+//    pi - theta, -q/p) -- the same trajectory traversed against the flight direction, so that
+//    the ordinary propagation applies -- over the entries from the last to the first. It starts
+//    from the forward filter's state at the last entry with that covariance times `inflation`
+//    (it then carries 1/inflation of the forward information) and updates with every
+//    measurement, the last one included. Before each earlier entry it propagates to it and then
+//    applies that surface's material (scattering variance; the mean loss given back), because
+//    the state on a surface is the one before its material in the flight direction;
+//  * the result is the weighted mean, at the first surface, of the backward filtered state
+//    (every measurement) and the seed (the prior there):
+//    K = C_b (C_b + C_0)^-1, p = p_b + K (p_0 - p_b), C = (I - K) C_b.
+// The reversal maps (phi, theta, q/p) to (phi + pi, pi - theta, -q/p): its Jacobian is
+// diag(1, 1, 1, -1, -1), applied to the covariance on both sides.
+void reverse_state(double p[5], double C[25]) {
+  p[2] = wrap_phi(p[2] + kPi);
+  p[3] = kPi - p[3];
+  p[4] = -p[4];
+  const double sgn[5] = {1, 1, 1, -1, -1};
+  for (int r = 0; r < 5; ++r)
+    for (int c = 0; c < 5; ++c) C[r * 5 + c] *= sgn[r] * sgn[c];
+}
+
+// Backward filter over entries N-1 .. 0 from (p_last, C_last), the forward filtered state at
+// the last entry. On return (pb, Cb) is the backward filtered state at the first entry in the
+// flight direction's parameters.
+uint32_t backward_filter(const Surface* surf, const Field& f, const Opts& o, const TrackIn& in,
+                         const double* p_last, const double* C_last, PropState& prop, double pb[5], double Cb[25]) {
+  const int N = int(in.N);
+  std::memcpy(pb, p_last, sizeof(double) * 5);
+  for (int i = 0; i < 25; ++i) Cb[i] = C_last[i] * o.inflation;
+  reverse_state(pb, Cb);
+  uint32_t status = 0;
+  for (int k = N - 1; k >= 0; --k) {
+    const Surface& sk = surf[surface_of(in.sid[k])];
+    if (k < N - 1) {
+      const Surface& snext = surf[surface_of(in.sid[k + 1])];
+      double r[3], T[3], Dtot[49], dxds[7], Jb2f[35], Jf2b[35], P[49], tmp[49], t75[35], J[25], Jt[25], t55[25];
+      bound_to_free(snext, pb, r, T);
+      jac_bound_to_free(snext, pb, Jb2f);
+      status |= propagate(f, o, sk, r, T, pb[4], Dtot, dxds, prop);
+      if (status & kFatal) return status;
+      jac_free_to_bound(sk, T, Jf2b);
+      path_correction(sk, T, dxds, P);
+      matmul(P, Dtot, tmp, 7, 7, 7);
+      matmul(tmp, Jb2f, t75, 7, 7, 5);
+      matmul(Jf2b, t75, J, 5, 7, 5);
+      const double lam = pb[4];
+      free_to_bound(sk, r, T, lam, pb);
+      transpose(J, Jt, 5, 5);
+      matmul(J, Cb, t55, 5, 5, 5);
+      matmul(t55, Jt, Cb, 5, 5, 5);
+      double Q[25];
+      status |= material(sk, o, pb, Q, true);
+      if (status & kFatal) return status;
+      for (int i = 0; i < 25; ++i) Cb[i] += Q[i];
+      symmetrize(Cb, 5);
+    }
+    if (measured(in.sid[k])) {
+      const double* mk = in.meas + 5 * k;
+      double m[2] = {mk[0], mk[1]};
+      double V[4] = {mk[2], mk[3], mk[3], mk[4]};
+      double c2 = 0.0;
+      status |= kf_update(m, V, pb, Cb, &c2);
+      if (status & kFatal) return status;
+    }
+    pb[2] = wrap_phi(pb[2]);
+    if (!(pb[3] > 0.0 && pb[3] < kPi)) return status | kNonFinite;
+  }
+  reverse_state(pb, Cb);
+  return status;
+}
+
+// Weighted mean of two estimates of the same parameters: (p0, C0) and (pb, Cb).
+uint32_t weighted_mean(const double p0[5], const double C0[25], const double pb[5], const double Cb[25], double ps[5],
+                       double Cs[25]) {
+  double S[25], Si[25], K[25], KCb[25];
+  for (int i = 0; i < 25; ++i) S[i] = Cb[i] + C0[i];
+  if (!spd_inverse(S, Si, 5)) return kSmootherNotSpd;
+  matmul(Cb, Si, K, 5, 5, 5);
+  double d[5], Kd[5];
+  for (int i = 0; i < 5; ++i) d[i] = p0[i] - pb[i];
+  d[2] = wrap_phi(d[2]);
+  matmul(K, d, Kd, 5, 5, 1);
+  for (int i = 0; i < 5; ++i) ps[i] = pb[i] + Kd[i];
+  ps[2] = wrap_phi(ps[2]);
+  matmul(K, Cb, KCb, 5, 5, 5);
+  for (int i = 0; i < 25; ++i) Cs[i] = Cb[i] - KCb[i];
+  symmetrize(Cs, 5);
+  return 0;
+}
+
 void fit_track(const Surface* surf, uint32_t n_surf, const Field& f, const Opts& o, const TrackIn& in,
                TrackOut& out, States* keep = nullptr) {
   const int N = int(in.N);
@@ -861,9 +963,16 @@ void fit_track(const Surface* surf, uint32_t n_surf, const Field& f, const Opts&
       break;
     }
   }
+  if (o.smoother == 1 && !(status & kFatal)) {
+    double pb[5], Cb[25], C0[25];
+    status |= backward_filter(surf, f, o, in, &pf[(N - 1) * 5], &Cf[(N - 1) * 25], prop, pb, Cb);
+    unpack_cov(in.seed_cov, C0);
+    if (!(status & kFatal)) status |= weighted_mean(in.seed_par, C0, pb, Cb, &ps[0], &Cs[0]);
+  }
   out.attempts = prop.attempts;
   out.rejected = prop.rejected;
-  if (!(status & kFatal)) status |= rts(N, &pf[0], &Cf[0], &pp[0], &Cp[0], &J[0], &ps[0], &Cs[0]);
+  if (o.smoother == 0 && !(status & kFatal))
+    status |= rts(N, &pf[0], &Cf[0], &pp[0], &Cp[0], &J[0], &ps[0], &Cs[0]);
   if (!(status & kFatal)) {
     double L[25];
     if (!cholesky(&Cs[0], L, 5)) status |= kSmootherNotSpd;
@@ -1269,6 +1378,8 @@ struct orc_opts {
   uint32_t max_steps;
   double ZA, I_eV, rho, hwp_eV;
   const uint16_t* mlp_bf16;  // 5057 BF16 weights (W1, b1, W2, b2, w3, b3) or null
+  int smoother;              // 0: RTS, 1: two-filter
+  double inflation;          // two-filter: backward filter's starting covariance factor
 };
 
 static float bf16_to_float(uint16_t b) {
@@ -1310,6 +1421,8 @@ static Opts to_opts(const orc_opts* o, Mlp* storage) {
   O.tol = o->tol; O.h_max = o->h_max; O.h_min = o->h_min; O.surf_tol = o->surf_tol; O.mass = o->mass;
   O.max_steps = o->max_steps;
   O.ZA = o->ZA; O.I_eV = o->I_eV; O.rho = o->rho; O.hwp_eV = o->hwp_eV;
+  O.smoother = o->smoother;
+  O.inflation = o->inflation;
   return O;
 }
 
@@ -1509,6 +1622,70 @@ uint32_t orc_linear_chain(int N, const double* J, const double* Q, const double*
   *chi2_out = chi2;
   if (pf_out) std::memcpy(pf_out, &pf[0], sizeof(double) * 5 * N);
   if (Cf_out) std::memcpy(Cf_out, &Cf[0], sizeof(double) * 25 * N);
+  return st;
+}
+
+// Inverse of a general n x n matrix by Gauss-Jordan elimination with partial pivoting.
+static bool general_inverse(const double* A, double* Ai, int n) {
+  std::vector<double> M(A, A + n * n);
+  for (int i = 0; i < n * n; ++i) Ai[i] = (i % (n + 1) == 0) ? 1.0 : 0.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(M[r * n + c]) > std::fabs(M[piv * n + c])) piv = r;
+    if (!(std::fabs(M[piv * n + c]) > 0.0)) return false;
+    for (int j = 0; j < n; ++j) {
+      std::swap(M[c * n + j], M[piv * n + j]);
+      std::swap(Ai[c * n + j], Ai[piv * n + j]);
+    }
+    const double d = M[c * n + c];
+    for (int j = 0; j < n; ++j) {
+      M[c * n + j] /= d;
+      Ai[c * n + j] /= d;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double f = M[r * n + c];
+      for (int j = 0; j < n; ++j) {
+        M[r * n + j] -= f * M[c * n + j];
+        Ai[r * n + j] -= f * Ai[c * n + j];
+      }
+    }
+  }
+  return true;
+}
+
+// The two-filter smoother on the linear chain of orc_linear_chain: the forward filter, then the
+// backward filter of x_k = J_{k+1}^-1 x_{k+1} - w_k (w_k ~ N(0, Q_k), the noise of step k seen
+// from its far end) from the last filtered state with the covariance times `inflation`, then the
+// weighted mean with the prior (p0, C0) at step 0. Returns the smoothed state at step 0.
+uint32_t orc_linear_chain_two_filter(int N, const double* J, const double* Q, const double* p0, const double* C0,
+                                     const double* m, const double* V, double inflation, double* ps0, double* Cs0) {
+  std::vector<double> pf(N * 5), Cf(N * 25);
+  double chi2 = 0.0;
+  std::vector<double> ps(N * 5), Cs(N * 25);
+  uint32_t st = orc_linear_chain(N, J, Q, p0, C0, m, V, &ps[0], &Cs[0], &chi2, &pf[0], &Cf[0]);
+  st &= ~kSmootherNotSpd;  // only the forward filter is used
+  double pb[5], Cb[25];
+  std::memcpy(pb, &pf[(N - 1) * 5], sizeof(pb));
+  for (int i = 0; i < 25; ++i) Cb[i] = Cf[(N - 1) * 25 + i] * inflation;
+  for (int k = N - 1; k >= 0; --k) {
+    if (k < N - 1) {
+      double Ji[25], Jit[25], t[25], pn[5];
+      if (!general_inverse(J + 25 * (k + 1), Ji, 5)) return st | kSmootherNotSpd;
+      matmul(Ji, pb, pn, 5, 5, 1);
+      std::memcpy(pb, pn, sizeof(pb));
+      transpose(Ji, Jit, 5, 5);
+      matmul(Ji, Cb, t, 5, 5, 5);
+      matmul(t, Jit, Cb, 5, 5, 5);
+      for (int i = 0; i < 25; ++i) Cb[i] += Q[k * 25 + i];
+      symmetrize(Cb, 5);
+    }
+    double mm[2] = {m[2 * k], m[2 * k + 1]}, c2 = 0.0;
+    if (std::isnan(mm[0])) continue;
+    st |= kf_update(mm, V + 4 * k, pb, Cb, &c2);
+  }
+  st |= weighted_mean(p0, C0, pb, Cb, ps0, Cs0);
   return st;
 }
 
