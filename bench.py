@@ -70,7 +70,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--variant", default="auto", choices=["auto", "fp64", "mixed_fp32", "mixed", "mixed_learned"])
+    ap.add_argument("--variant", default="auto", choices=["auto", "fp64", "mixed_fp32", "mixed", "mixed_learned",
+                                                          "fp64_two_filter", "mixed_two_filter",
+                                                          "mixed_fp32_two_filter"])
     ap.add_argument("--events", type=int, default=50)
     ap.add_argument("--workload", default="barrel", choices=["barrel", "map"],
                     help="barrel: events in the barrel + endcap detector, uniform 2 T; map: 1e5 muons "
@@ -434,6 +436,8 @@ def setup_tune_cache() -> str:
 def tuned_shape(path: str, variant: str, n_tracks: int, field: str, disabled: bool):
     """[threads, blocks per SM, tracks per warp, registers, lanes a track] the autotuner chose
     for this class."""
+    if variant.endswith("_two_filter"):  # one kernel variant, not tuned
+        return [128, 2, 32, 255, 1]
     if disabled:
         return [128, 2, 32, 255, 1] if variant in ("fp64", "mixed_fp32") else [128, 4, 32, 128, 1]
     prec = variant if variant in ("fp64", "mixed_fp32") else "mixed"
@@ -661,7 +665,9 @@ def main():
     host = tkf.Batch.from_arrays(t.offsets, t.meas, t.sid, t.seed_par, t.seed_cov)
     dev = host.to(f"cuda:{local}")
     # the headline is the last: mixed + learned; mixed_fp32 is the experimental FP32 covariance algebra
-    variants = ["fp64", "mixed_fp32", "mixed", "mixed_learned"] if args.variant == "auto" else [args.variant]
+    # *_two_filter: the optimal (two-filter) smoother instead of RTS
+    variants = (["fp64", "fp64_two_filter", "mixed_fp32", "mixed_two_filter", "mixed", "mixed_learned"]
+                if args.variant == "auto" else [args.variant])
     # a side stream: CUDA graphs cannot be captured on the legacy default stream
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -682,14 +688,17 @@ def main():
     flush = (torch.zeros(int(2 * L2_BYTES) // 4, dtype=torch.float32, device=f"cuda:{local}")
              if host.nbytes() < 2 * L2_BYTES else None)
     for variant in variants:
-        opts = tkf.Options(precision={"fp64": tkf.FP64, "mixed_fp32": tkf.MIXED_FP32}.get(variant, tkf.MIXED),
-                           mass=w.mass,
+        two_filter = variant.endswith("_two_filter")
+        base = variant.replace("_two_filter", "")
+        opts = tkf.Options(precision={"fp64": tkf.FP64, "mixed_fp32": tkf.MIXED_FP32}.get(base, tkf.MIXED),
+                           mass=w.mass, smoother=tkf.SMOOTHER_TWO_FILTER if two_filter else tkf.SMOOTHER_RTS,
                            graph=not args.no_graph, autotune=not args.no_autotune and args.shape is None)
         if args.shape:
             th, bps, tpw, regs, *lanes = (int(x) for x in args.shape.split(","))
             opts.block_threads, opts.blocks_per_sm, opts.tracks_per_warp = th, bps, tpw
-            opts.max_registers = 255 if variant == "fp64" or (variant == "mixed_fp32" and regs == 64) else regs
-            opts.lanes_per_track = lanes[0] if lanes and variant != "mixed_fp32" else 0
+            opts.max_registers = (255 if base == "fp64" or two_filter or (base == "mixed_fp32" and regs == 64)
+                                  else regs)
+            opts.lanes_per_track = lanes[0] if lanes and base != "mixed_fp32" and not two_filter else 0
         if variant.endswith("learned"):
             opts.step_mode, opts.mlp = tkf.STEP_LEARNED, proposer
         out = tkf.alloc_outputs(n_tracks, dev.offsets.device, steps=True)
@@ -759,7 +768,11 @@ def main():
             ckf = ckf_stage(ctx, fld, w, stream, max(1, args.steps // 2), 1)
     ms, ms_max, clocks = results[head]["ms"], results[head]["ms_max"], results[head]["clocks"]
     for k, v in results.items():
-        fa, fr, fh, ft = (FLOPS_MAP if args.workload == "map" else FLOPS)[k]
+        counts = (FLOPS_MAP if args.workload == "map" else FLOPS).get(k)  # no count for the two-filter form
+        if counts is None:
+            v["flops"] = None
+            continue
+        fa, fr, fh, ft = counts
         v["flops"] = fa * (v["attempts"] - v["rejected"]) + fr * v["rejected"] + fh * hits_k1 + ft * n_tracks
 
     # end to end through the host entry point: pinned host inputs -> fit -> host outputs
@@ -841,7 +854,8 @@ def main():
                          "step_attempts": v["attempts"], "rejected": v["rejected"],
                          "fit_status_ok": v["status_ok"], "pull_sigma": v["pulls"]["sigma"],
                          "fit_kernel_ms": v["kernel_ms"], "fit_kernel_share": v["kernel_ms"] / v["ms"],
-                         "fp64_tflops": v["flops"] / (v["kernel_ms"] * 1e-3) / 1e12,
+                         "fp64_tflops": (v["flops"] / (v["kernel_ms"] * 1e-3) / 1e12 if v["flops"] is not None
+                                         else None),
                          "pull_mean": v["pulls"]["mean"], "chi2_ndf_mean": v["pulls"]["chi2_ndf"]}
                      for k, v in results.items()},
     }

@@ -209,7 +209,28 @@ typedef struct tkf_fit_options {
    * batch is too small to fill the GPU one lane a track. TKF_FIT_AUTOTUNE also times the group
    * mapping for small batches. */
   uint32_t lanes_per_track;
+  /* Smoother that gives the first-surface result: TKF_SMOOTHER_RTS (default) or
+   * TKF_SMOOTHER_TWO_FILTER, the optimal smoother of Sec. 4 (weighted mean of a forward and a
+   * backward filter). The two-filter form runs, after the forward filter (whose chi2 is the
+   * track's), a backward Kalman filter of the reversed particle (phi + pi, pi - theta, -q/p)
+   * from the last entry to the first: it starts from the last filtered state with that
+   * covariance times backward_inflation, updates with every measurement, and before each
+   * earlier entry propagates to it and applies that surface's material (the scattering
+   * variance; the mean energy loss given back). The result is the weighted mean of the
+   * backward filtered state at the first surface and the seed. It propagates every track twice;
+   * no per-measurement state is kept. One lane a track at 255 registers (lanes_per_track 0 or 1,
+   * max_registers 0 or 255), no record capture; TKF_FIT_AUTOTUNE is ignored (the default block
+   * shape, 128 threads x 2 blocks per SM, unless one is given). */
+  int smoother;
+  /* TKF_SMOOTHER_TWO_FILTER: factor on the last filtered covariance that starts the backward
+   * filter (default 1e3; finite and >= 1). The start then holds 1/backward_inflation of the
+   * forward filter's information; larger factors let the first backward updates move the state
+   * (and its linearisation) further. */
+  double backward_inflation;
 } tkf_fit_options;
+
+#define TKF_SMOOTHER_RTS 0
+#define TKF_SMOOTHER_TWO_FILTER 1
 
 /* Autotuning: the first call of a launch class (precision, step mode, field kind, batch size
  * rounded down to a power of two, SM count) times every candidate launch shape on the call's

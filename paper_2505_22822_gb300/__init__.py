@@ -26,7 +26,8 @@ _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "libtkf.so")
 _SOURCES = ["tkf_api.cu", "tkf_order.cu", "tkf_policy.cu", "tkf_fit_fp64.cu", "tkf_fit_mixed.cu",
             "tkf_fit_mixed_r128.cu", "tkf_fit_mixed_r64.cu", "tkf_fit_mixed32.cu", "tkf_mlp.cu", "tkf_seed.cu",
-            "tkf_fit_group.cu", "tkf_ckf.cu"]
+            "tkf_fit_group.cu", "tkf_ckf.cu", "tkf_fit_two_filter.cu", "tkf_fit_two_filter_mixed.cu",
+            "tkf_fit_two_filter_mixed32.cu"]
 _lib = None
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
@@ -37,6 +38,7 @@ STEP_ADAPTIVE, STEP_LEARNED = 0, 1
 FIT_AUTOTUNE, FIT_GRAPH, FIT_TEST_PROPOSAL_TIMEOUT = 1, 2, 1 << 31
 FIELD_UNIFORM, FIELD_RZ_GRID = 0, 1
 SEED_FIRST_MIDDLE_LAST, SEED_FIRST_THREE = 0, 1
+SMOOTHER_RTS, SMOOTHER_TWO_FILTER = 0, 1
 SID_NO_MEASUREMENT = 0x80000000  # surface-id flag: the track crosses the surface without a measurement
 SEED_STATUS = {"TOO_FEW_HITS": 1, "NO_CURVATURE": 2, "BAD_INPUT": 4}
 
@@ -119,7 +121,8 @@ class FitOptions(ctypes.Structure):
                 ("flags", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
                 ("blocks_per_sm", ctypes.c_uint32), ("tracks_per_warp", ctypes.c_uint32),
                 ("max_registers", ctypes.c_uint32), ("kernel_events", ctypes.c_void_p),
-                ("seed_cov_scale", ctypes.c_double), ("lanes_per_track", ctypes.c_uint32)]
+                ("seed_cov_scale", ctypes.c_double), ("lanes_per_track", ctypes.c_uint32),
+                ("smoother", ctypes.c_int), ("backward_inflation", ctypes.c_double)]
 
 
 class MlpTrainOptions(ctypes.Structure):
@@ -380,6 +383,8 @@ class Options:
     kernel_events: object = None  # (begin, end) torch.cuda.Event pair around the fit kernel
     seed_cov_scale: float = 1.0   # factor on the seed covariance (a refit inflates it)
     lanes_per_track: int = 0      # 0 default / tuned, 1, or 4 (group-per-track)
+    smoother: int = 0             # SMOOTHER_RTS or SMOOTHER_TWO_FILTER
+    backward_inflation: float = 1e3  # two-filter: factor on the backward filter's starting covariance
 
     def c(self) -> FitOptions:
         o = FitOptions()
@@ -400,6 +405,7 @@ class Options:
         o.max_registers = self.max_registers
         o.seed_cov_scale = self.seed_cov_scale
         o.lanes_per_track = self.lanes_per_track
+        o.smoother, o.backward_inflation = self.smoother, self.backward_inflation
         if self.kernel_events is not None:
             # the C array must outlive the call: kept on the options struct
             o._events = (ctypes.c_void_p * 2)(*(ev.cuda_event for ev in self.kernel_events))

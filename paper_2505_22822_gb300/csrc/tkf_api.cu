@@ -380,6 +380,8 @@ void tkf_fit_options_default(tkf_fit_options* o) {
   o->kernel_events = nullptr;
   o->seed_cov_scale = 1.0;
   o->lanes_per_track = 0;
+  o->smoother = TKF_SMOOTHER_RTS;
+  o->backward_inflation = 1e3;
 }
 
 // Validation shared by the fit entry points; `out` may be NULL only when `need_out` is false.
@@ -410,6 +412,16 @@ static tkf_status check_common(tkf_context ctx, tkf_geometry geo, tkf_field fiel
                 std::string(fn) + ": options need tol, h_max, h_min, surf_tol, mass > 0, h_min <= h_max, max_steps > 0");
   if (!(o->seed_cov_scale > 0) || !isfinite(o->seed_cov_scale))
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": seed_cov_scale must be positive and finite");
+  if (!(o->smoother == TKF_SMOOTHER_RTS || o->smoother == TKF_SMOOTHER_TWO_FILTER))
+    return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": unknown smoother");
+  if (o->smoother == TKF_SMOOTHER_TWO_FILTER) {
+    if (!(o->backward_inflation >= 1.0) || !isfinite(o->backward_inflation))
+      return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": backward_inflation must be finite and >= 1");
+    if (o->records || o->lanes_per_track > 1 || (o->max_registers != 0 && o->max_registers != 255))
+      return fail(ctx, TKF_ERR_UNSUPPORTED,
+                  std::string(fn) + ": TKF_SMOOTHER_TWO_FILTER runs one lane a track at 255 registers, "
+                                    "without record capture");
+  }
   if ((o->flags & ~(TKF_FIT_AUTOTUNE | TKF_FIT_GRAPH | TKF_FIT_TEST_PROPOSAL_TIMEOUT)) != 0)
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": unknown flag");
   if (!tkf::valid_block_shape(o->block_threads, o->blocks_per_sm, o->tracks_per_warp, o->max_registers,
@@ -451,6 +463,8 @@ static tkf::FitArgs make_args(tkf_geometry geo, const tkf_fit_options* o, const 
   a.seed_par = in->seed_par;
   a.seed_cov = in->seed_cov;
   a.seed_cov_scale = o->seed_cov_scale;
+  a.smoother = o->smoother;
+  a.backward_inflation = o->backward_inflation;
   if (out) {
     a.par = out->par;
     a.cov = out->cov;
@@ -1000,6 +1014,11 @@ extern "C" tkf_status tkf_fit_noalloc(tkf_context ctx, tkf_geometry geo, tkf_fie
   }
   if (o->tracks_per_warp) shape.tracks_per_warp = int(o->tracks_per_warp);
   if (o->max_registers) shape.regs = int(o->max_registers);
+  if (o->smoother == TKF_SMOOTHER_TWO_FILTER && !(o->block_threads && o->blocks_per_sm)) {
+    shape.threads = 128;  // the two-filter kernels run at 255 registers: two 128-thread blocks an SM
+    shape.blocks = 2 * ctx->sm_count;
+    shape.regs = 255;
+  }
   e = tkf::launch_fit(a, field->f, o->precision, ws, shape, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_noalloc: launch");
   return TKF_OK;

@@ -591,6 +591,9 @@ __device__ uint32_t propagate_mixed(const F& fld, const OptionsDev& o, const Sur
 //   1/(beta p) = E lam^2,  1/beta^2 = 1 + m^2 lam^2,  beta^2 gamma^2 = p^2 / m^2.
 // Above beta gamma = exp(1/2 - ln(hbar omega_p / I)) the density term cancels ln(beta gamma) and
 // the Bethe bracket needs one logarithm: 1/2 ln(2 m_e W_max / I^2) - ln(hbar omega_p / I) + 1/2 - beta^2.
+// kGain: the reversed particle of the backward filter crosses the layer against the flight
+// direction and regains the mean loss (theta0 and the loss at its momentum on arrival).
+template <bool kGain = false>
 __device__ __forceinline__ uint32_t material(const Surf& s, const MaterialDev& m, double mass, const double T[3],
                                              double& lam, double& th0sq) {
   th0sq = 0.0;
@@ -617,7 +620,7 @@ __device__ __forceinline__ uint32_t material(const Surf& s, const MaterialDev& m
     bracket = 0.5 * log(2.0 * kMe * bg2 * wmax / (I * I)) - beta2;
   const double dedx = kBetheK * m.z_over_a * inv_beta2 * bracket;
   const double dE = dedx * m.rho * x * 1e-4;  // MeV cm^2/g * g/cm^3 * mm -> GeV
-  const double Ef = E - dE;
+  const double Ef = kGain ? E + dE : E - dE;
   if (!(Ef > mass)) return TKF_TRACK_PARTICLE_STOPPED;
   lam = copysign(1.0 / sqrt((Ef - mass) * (Ef + mass)), lam);
   return 0;
@@ -626,6 +629,8 @@ __device__ __forceinline__ uint32_t material(const Surf& s, const MaterialDev& m
 // Material in mixed precision: theta0^2 and the mean loss dE in FP32; the new q/p as
 // lam (1 - delta)^(-1/2) with delta = (2 E dE - dE^2) lam^2, i.e. lam + lam g in FP64 where
 // g = (1 - delta)^(-1/2) - 1 is formed in FP32 (series for small delta).
+// kGain as for `material`: delta = -(2 E dE + dE^2) lam^2 < 0.
+template <bool kGain = false>
 __device__ __forceinline__ uint32_t material_mixed(const Surf& s, const MaterialDev& m, const OptionsDev& o,
                                                    const float T[3], double& lam, float& th0sq) {
   th0sq = 0.0f;
@@ -649,9 +654,9 @@ __device__ __forceinline__ uint32_t material_mixed(const Surf& s, const Material
   else
     bracket = 0.5f * logf(m.two_me_over_i2_f * bg2 * wmax) - beta2;
   const float dE = m.dedx_scale_f * inv_beta2 * bracket * x;
-  if (!(dE < E - mass)) return TKF_TRACK_PARTICLE_STOPPED;
-  const float delta = (2.0f * E * dE - dE * dE) * l2;
-  const float g = delta < 0.01f
+  if (!kGain && !(dE < E - mass)) return TKF_TRACK_PARTICLE_STOPPED;
+  const float delta = kGain ? -(2.0f * E * dE + dE * dE) * l2 : (2.0f * E * dE - dE * dE) * l2;
+  const float g = (kGain ? fabsf(delta) < 0.01f : delta < 0.01f)
                       ? delta * (0.5f + delta * (0.375f + delta * (0.3125f + delta * (0.2734375f + delta * 0.24609375f))))
                       : rsqrtf(1.0f - delta) - 1.0f;
   lam += lam * f2d(g);
@@ -844,13 +849,262 @@ __device__ __forceinline__ void transport_cov(const R J[5][5], R Cw[15], uint32_
   }
 }
 
-template <int kPrec, int kMode, int kG, int kPlace, class F>
+// ---- gain-matrix update with H = [I2 0]; Joseph form (paper Sec. 2; Fruhwirth 1987), with the
+// measurement of entry m: sets the gain K, the inverse residual covariance Si and the residual r,
+// updates p and C and adds r^T Si r to chi2. Returns TKF_TRACK_UPDATE_NOT_SPD (state untouched)
+// when the residual covariance is not positive definite.
+template <int kG, class U>
+__device__ __forceinline__ uint32_t kalman_update(const FitArgs& a, uint32_t m, double p[5], U C[15], U K[5][2],
+                                                  U& Si00, U& Si01, U& Si11, U& r0, U& r1, double& chi2,
+                                                  uint32_t gl, uint32_t gmask) {
+  const double m0 = a.loc0[m], m1 = a.loc1[m];
+  const U V00 = cov_from_d<U>(a.v00[m]), V01 = cov_from_d<U>(a.v01[m]), V11 = cov_from_d<U>(a.v11[m]);
+  const U S00 = C[S(0, 0)] + V00, S01 = C[S(0, 1)] + V01, S11 = C[S(1, 1)] + V11;
+  const U det = S00 * S11 - S01 * S01;
+  if (!(S00 > U(0) && det > U(0))) return TKF_TRACK_UPDATE_NOT_SPD;
+  const U idet = U(1) / det;
+  Si00 = S11 * idet;
+  Si01 = -S01 * idet;
+  Si11 = S00 * idet;
+  r0 = cov_from_d<U>(m0 - p[0]);
+  r1 = cov_from_d<U>(m1 - p[1]);
+  chi2 += cov_to_d(r0 * (Si00 * r0 + Si01 * r1) + r1 * (Si01 * r0 + Si11 * r1));
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    const U U0 = C[S(j, 0)], U1 = C[S(j, 1)];
+    K[j][0] = U0 * Si00 + U1 * Si01;
+    K[j][1] = U0 * Si01 + U1 * Si11;
+  }
+#pragma unroll
+  for (int j = 0; j < 5; ++j) p[j] += cov_to_d(K[j][0] * r0 + K[j][1] * r1);
+  if constexpr (kG == 1) {
+    // X = (I - K H) C ; C' = X - (X H^T - K V) K^T
+    U X[5][5];
+#pragma unroll
+    for (int r_ = 0; r_ < 5; ++r_)
+#pragma unroll
+      for (int c_ = 0; c_ < 5; ++c_) X[r_][c_] = C[S(r_, c_)] - K[r_][0] * C[S(0, c_)] - K[r_][1] * C[S(1, c_)];
+    U Y[5][2];
+#pragma unroll
+    for (int r_ = 0; r_ < 5; ++r_) {
+      Y[r_][0] = X[r_][0] - (K[r_][0] * V00 + K[r_][1] * V01);
+      Y[r_][1] = X[r_][1] - (K[r_][0] * V01 + K[r_][1] * V11);
+    }
+#pragma unroll
+    for (int r_ = 0; r_ < 5; ++r_)
+#pragma unroll
+      for (int c_ = r_; c_ < 5; ++c_) C[S(r_, c_)] = X[r_][c_] - Y[r_][0] * K[c_][0] - Y[r_][1] * K[c_][1];
+  } else {
+    // the same, row gl in lane gl and row 4 in every lane, then exchanged
+    const U Kg0 = pick4(gl, K[0][0], K[1][0], K[2][0], K[3][0]);
+    const U Kg1 = pick4(gl, K[0][1], K[1][1], K[2][1], K[3][1]);
+    U Xg[5], X4[5], Cn[5];
+#pragma unroll
+    for (int c_ = 0; c_ < 5; ++c_) {
+      const U Cgc = pick4(gl, C[S(0, c_)], C[S(1, c_)], C[S(2, c_)], C[S(3, c_)]);
+      Xg[c_] = Cgc - Kg0 * C[S(0, c_)] - Kg1 * C[S(1, c_)];
+      X4[c_] = C[S(4, c_)] - K[4][0] * C[S(0, c_)] - K[4][1] * C[S(1, c_)];
+    }
+    const U Yg0 = Xg[0] - (Kg0 * V00 + Kg1 * V01), Yg1 = Xg[1] - (Kg0 * V01 + Kg1 * V11);
+    const U Y40 = X4[0] - (K[4][0] * V00 + K[4][1] * V01), Y41 = X4[1] - (K[4][0] * V01 + K[4][1] * V11);
+#pragma unroll
+    for (int c_ = 0; c_ < 5; ++c_) Cn[c_] = Xg[c_] - Yg0 * K[c_][0] - Yg1 * K[c_][1];
+    const U C44 = X4[4] - Y40 * K[4][0] - Y41 * K[4][1];
+#pragma unroll
+    for (int r_ = 0; r_ < 4; ++r_)
+#pragma unroll
+      for (int c_ = r_; c_ < 5; ++c_) C[S(r_, c_)] = gshfl<kG>(gmask, Cn[c_], r_);
+    C[S(4, 4)] = C44;
+  }
+  return 0;
+}
+
+// Filtered direction: the predicted one (sp2, cp2, st2, ct2) turned by the update's angle
+// increments p[2], p[3] (angle-addition identities). Returns false when theta leaves (0, pi).
+template <bool kMixed>
+__device__ __forceinline__ bool turn_direction(const double p[5], double sp2, double cp2, double st2, double ct2,
+                                               double& sph, double& cph, double& sth, double& cth) {
+  if constexpr (!kMixed) {
+    double sd, cd, se, ce;
+    small_sincos(p[2], sd, cd);
+    small_sincos(p[3], se, ce);
+    sph = sp2 * cd + cp2 * sd;
+    cph = cp2 * cd - sp2 * sd;
+    sth = st2 * ce + ct2 * se;
+    cth = ct2 * ce - st2 * se;
+  } else {
+    // sin and (cos - 1) of the small increments in FP32, applied to the FP64 anchors
+    double sd, cd1, se, ce1;
+    small_sincos_m1(p[2], sd, cd1);
+    small_sincos_m1(p[3], se, ce1);
+    sph = sp2 + (sp2 * cd1 + cp2 * sd);
+    cph = cp2 + (cp2 * cd1 - sp2 * sd);
+    sth = st2 + (st2 * ce1 + ct2 * se);
+    cth = ct2 + (ct2 * ce1 - st2 * se);
+  }
+  return sth > 0.0;
+}
+
+// ---- two-filter smoother (the optimal smoother of paper Sec. 4; Fraser-Potter form): after the
+// forward filter, a backward Kalman filter of the reversed particle -- (phi + pi, pi - theta,
+// -q/p): the same trajectory traversed against the flight direction, so that the ordinary
+// propagation applies -- runs from the last entry to the first. It starts from the last filtered
+// state with the covariance times the inflation factor, updates with every measurement, and
+// after each propagation applies the material of the surface reached (the state on a surface is
+// the one before its material in the flight direction). The result on the first surface is the
+// weighted mean of the backward filtered state and the seed.
+
+// The reversal's Jacobian is diag(1, 1, 1, -1, -1): the covariance elements that pair theta or
+// q/p with one of the other three change sign.
+__device__ __forceinline__ bool reversal_flips(int r, int c) { return (r >= 3) != (c >= 3); }
+
+// Backward start: the forward filter's last state reversed, its covariance times `infl`, angle
+// increments restarting at 0 (the direction is carried as sines and cosines).
+template <class U>
+__device__ __forceinline__ void reverse_for_backward(double p[5], U C[15], double& sph, double& cph, double& cth,
+                                                     U infl) {
+  sph = -sph;
+  cph = -cph;
+  cth = -cth;
+  p[2] = 0.0;
+  p[3] = 0.0;
+  p[4] = -p[4];
+#pragma unroll
+  for (int r = 0; r < 5; ++r)
+#pragma unroll
+    for (int c = r; c < 5; ++c) C[S(r, c)] = (reversal_flips(r, c) ? -infl : infl) * C[S(r, c)];
+}
+
+// The material of surface s for the reversed particle arriving with direction (sp2, cp2, st2,
+// ct2): the mean loss given back to q/p = p[4], the scattering variance added to C.
+template <int kPrec>
+__device__ __forceinline__ uint32_t arrival_material(const FitArgs& a, const Surf& s, double sp2, double cp2,
+                                                     double st2, double ct2, double p[5],
+                                                     typename CovType<kPrec>::type C[15]) {
+  using U = typename CovType<kPrec>::type;
+  double lam = p[4];
+  uint32_t status;
+  if constexpr (kPrec == 0) {
+    const double T[3] = {st2 * cp2, st2 * sp2, ct2};
+    double th0sq;
+    status = material<true>(s, a.mat, a.opt.mass, T, lam, th0sq);
+    C[S(2, 2)] += th0sq / (st2 * st2);
+    C[S(3, 3)] += th0sq;
+  } else {
+    const float T[3] = {d2f(st2 * cp2), d2f(st2 * sp2), d2f(ct2)};
+    float th0sq;
+    status = material_mixed<true>(s, a.mat, a.opt, T, lam, th0sq);
+    const float fst = d2f(st2);
+    C[S(2, 2)] += cov_from_f<U>(th0sq / (fst * fst));
+    C[S(3, 3)] += cov_from_f<U>(th0sq);
+  }
+  p[4] = lam;
+  return status;
+}
+
+// The backward filter's state on the first surface back in the flight direction's parameters,
+// and its weighted mean with the seed (p0, C0): K = Cb (Cb + C0)^-1, p = pb + K (p0 - pb),
+// C = (I - K) Cb (I - K)^T + K C0 K^T (the symmetric form of (I - K) Cb), into st.dl / st.E.
+template <int kPlace, class U>
+__device__ __forceinline__ uint32_t combine_with_seed(const FitArgs& a, uint32_t i, const double p[5], const U C[15],
+                                                      double sph, double cph, double sth, double cth,
+                                                      SmootherStore<kPlace, U>& st) {
+  const uint32_t n = a.stride;
+  double pb[5] = {p[0], p[1], atan2(-sph, -cph), atan2(sth, -cth), -p[4]};
+  U Cb[15], C0[15], L[15];
+  double d[5];
+#pragma unroll
+  for (int r = 0; r < 5; ++r)
+#pragma unroll
+    for (int c = r; c < 5; ++c) Cb[S(r, c)] = reversal_flips(r, c) ? -C[S(r, c)] : C[S(r, c)];
+#pragma unroll
+  for (int j = 0; j < 15; ++j) {
+    C0[j] = cov_from_d<U>(a.seed_cov[size_t(j) * n + i] * a.seed_cov_scale);
+    L[j] = Cb[j] + C0[j];
+  }
+#pragma unroll
+  for (int j = 0; j < 5; ++j) d[j] = a.seed_par[size_t(j) * n + i] - pb[j];
+  if (d[2] > kPi) d[2] -= 2.0 * kPi;
+  if (d[2] <= -kPi) d[2] += 2.0 * kPi;
+  // Cb + C0 = L D L^T in place (unit lower L below the diagonal, D on it)
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    if (!(L[S(j, j)] > U(0))) return TKF_TRACK_SMOOTHER_NOT_SPD;
+    const U inv = U(1) / L[S(j, j)];
+#pragma unroll
+    for (int r = j + 1; r < 5; ++r) {
+      const U f = L[S(j, r)] * inv;
+#pragma unroll
+      for (int c = r; c < 5; ++c) L[S(r, c)] -= f * L[S(j, c)];
+    }
+#pragma unroll
+    for (int r = j + 1; r < 5; ++r) L[S(j, r)] *= inv;
+  }
+  // K^T = (Cb + C0)^-1 Cb: column c of K^T (row c of K) from row c of Cb
+  U K[5][5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    U x[5];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      U acc = Cb[S(c, r)];
+#pragma unroll
+      for (int q = 0; q < r; ++q) acc -= L[S(q, r)] * x[q];
+      x[r] = acc;
+    }
+#pragma unroll
+    for (int r = 0; r < 5; ++r) x[r] /= L[S(r, r)];
+#pragma unroll
+    for (int r = 4; r >= 0; --r) {
+#pragma unroll
+      for (int q = r + 1; q < 5; ++q) x[r] -= L[S(r, q)] * x[q];
+    }
+#pragma unroll
+    for (int r = 0; r < 5; ++r) K[c][r] = x[r];
+  }
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    double acc = pb[r];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) acc += cov_to_d(K[r][c]) * d[c];
+    st.dl(r) = acc;
+  }
+  if (st.dl(2) > kPi) st.dl(2) -= 2.0 * kPi;
+  if (st.dl(2) <= -kPi) st.dl(2) += 2.0 * kPi;
+  // A = (I - K) Cb, B = K C0; C = A (I - K)^T + B K^T
+  U A[5][5], B[5][5];
+#pragma unroll
+  for (int r = 0; r < 5; ++r)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      U acc = Cb[S(r, c)], acc0 = U(0);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        acc -= K[r][q] * Cb[S(q, c)];
+        acc0 += K[r][q] * C0[S(q, c)];
+      }
+      A[r][c] = acc;
+      B[r][c] = acc0;
+    }
+#pragma unroll
+  for (int r = 0; r < 5; ++r)
+#pragma unroll
+    for (int c = r; c < 5; ++c) {
+      U acc = A[r][c];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) acc += B[r][q] * K[c][q] - A[r][q] * K[c][q];
+      st.E(S(r, c)) = acc;
+    }
+  return 0;
+}
+
+template <int kPrec, int kMode, int kG, int kPlace, int kSmooth, class F>
 __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
                           SmootherStore<kPlace, typename CovType<kPrec>::type> st, uint32_t gl = 0,
                           uint32_t gmask = 0xffffffffu) {
   constexpr bool kMixed = kPrec != 0;
-  constexpr int kCols = kG == 1 ? 3 : 1;  // derivative columns a lane transports
   static_assert(kG == 1 || kMode != kRecord, "record capture runs one lane per track");
+  static_assert(kSmooth == 0 || (kG == 1 && kMode != kRecord), "the two-filter smoother runs one lane a track");
   const bool writer = kG == 1 || gl == 0;  // the lane that writes the group's results
   using U = typename CovType<kPrec>::type;
   const uint32_t n = a.stride;  // SoA row stride of seeds and outputs
@@ -914,21 +1168,42 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
 #pragma unroll
   for (int c = 0; c < 5; ++c) Pg[c] = P4[c] = Eg[c] = U(0);
 
-  for (int k = 0; k < N && !(status & kFatal); ++k) {
+  // kSmooth 1 (two-filter): a second pass runs the backward filter over the entries in reverse
+  // (unrolled: each pass is compiled with its own direction)
+  constexpr int kPasses = kSmooth == 1 ? 2 : 1;
+  double chi2_bwd = 0.0;
+#pragma unroll
+  for (int pass = 0; pass < kPasses; ++pass) {
+  const bool bwd = pass == 1;
+  if (bwd) {
+    if (status & kFatal) break;
+    reverse_for_backward(p, C, sph, cph, cth, U(a.backward_inflation));
+  }
+  for (int ent = 0; ent < N && !(status & kFatal); ++ent) {
+    const int k = bwd ? N - 1 - ent : ent;
     const uint32_t m = b0 + k;
     Surf s;
     const uint32_t sid_m = a.sid[m];
     const bool measured = (sid_m & TKF_SID_NO_MEASUREMENT) == 0;
     load_surf(a.surf, sid_m & ~TKF_SID_NO_MEASUREMENT, s);
     U J[5][5];
-    double sp2 = 0.0, cp2 = 1.0, st2 = 1.0, ct2 = 0.0;  // predicted direction at s (k >= 1)
-    if (k > 0) {
+    double sp2 = 0.0, cp2 = 1.0, st2 = 1.0, ct2 = 0.0;  // predicted direction at s (ent >= 1)
+    if (bwd && ent == 0) {  // the backward filter starts on this surface: no prediction
+      sp2 = sph;
+      cp2 = cph;
+      st2 = sth;
+      ct2 = cth;
+    }
+    if (ent > 0) {
+      constexpr int kCols = kG == 1 ? 3 : 1;
       if constexpr (!kMixed) {
       // ---- material of the previous surface (muon hypothesis), then propagation
       double T[3] = {sth * cph, sth * sph, cth};
-      double lam = p[4], th0sq;
-      status |= material(sp, a.mat, a.opt.mass, T, lam, th0sq);
-      if (status & kFatal) break;
+      double lam = p[4], th0sq = 0.0;
+      if (!bwd) {
+        status |= material(sp, a.mat, a.opt.mass, T, lam, th0sq);
+        if (status & kFatal) break;
+      }
       double r[3];
       for (int j = 0; j < 3; ++j) r[j] = sp.c[j] + p[0] * sp.u[j] + p[1] * sp.v[j];
       double dr[kCols][3], dT[kCols][3];
@@ -981,16 +1256,20 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
       p[3] = 0.0;
       p[4] = lam;
       // ---- C_pred = J (C + Q) J^T, Q = diag(0, 0, th0^2/sin^2(theta), th0^2, 0)
-      C[S(2, 2)] += th0sq / (sth * sth);
-      C[S(3, 3)] += th0sq;
+      if (!bwd) {
+        C[S(2, 2)] += th0sq / (sth * sth);
+        C[S(3, 3)] += th0sq;
+      }
       transport_cov<kG>(J, C, gl, gmask);
       } else {
       // ---- mixed precision: material, propagation, Jacobian and covariance transport in FP32
       const float Tm[3] = {d2f(sth * cph), d2f(sth * sph), d2f(cth)};
       double lam = p[4];
-      float th0sq;
-      status |= material_mixed(sp, a.mat, a.opt, Tm, lam, th0sq);
-      if (status & kFatal) break;
+      float th0sq = 0.0f;
+      if (!bwd) {
+        status |= material_mixed(sp, a.mat, a.opt, Tm, lam, th0sq);
+        if (status & kFatal) break;
+      }
       double T[3] = {sth * cph, sth * sph, cth};
       double r[3];
       for (int j = 0; j < 3; ++j) r[j] = sp.c[j] + p[0] * sp.u[j] + p[1] * sp.v[j];
@@ -1068,8 +1347,10 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
       float Cf[15];
 #pragma unroll
       for (int j = 0; j < 15; ++j) Cf[j] = cov_to_f(C[j]);
-      Cf[S(2, 2)] += th0sq / (fsth * fsth);
-      Cf[S(3, 3)] += th0sq;
+      if (!bwd) {
+        Cf[S(2, 2)] += th0sq / (fsth * fsth);
+        Cf[S(3, 3)] += th0sq;
+      }
       transport_cov<kG>(Jf, Cf, gl, gmask);
 #pragma unroll
       for (int j = 0; j < 15; ++j) C[j] = cov_from_f<U>(Cf[j]);
@@ -1078,8 +1359,13 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
 #pragma unroll
         for (int c0 = 0; c0 < 5; ++c0) J[r0][c0] = cov_from_f<U>(Jf[r0][c0]);
       }
+      if (bwd) {  // the material of the surface reached, crossed against the flight direction
+        status |= arrival_material<kPrec>(a, s, sp2, cp2, st2, ct2, p, C);
+        if (status & kFatal) break;
+      }
       // ---- smoother: R = P J^T (in place; J row 4 is e_4)
-      if constexpr (kG == 1) {
+      if constexpr (kSmooth == 1) {
+      } else if constexpr (kG == 1) {
 #pragma unroll
       for (int r0 = 0; r0 < 5; ++r0) {
         U row[5];
@@ -1125,70 +1411,11 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
 #pragma unroll
     for (int j = 0; j < 5; ++j) K[j][0] = K[j][1] = U(0);
     if (measured) {
-    const double m0 = a.loc0[m], m1 = a.loc1[m];
-    const U V00 = cov_from_d<U>(a.v00[m]), V01 = cov_from_d<U>(a.v01[m]), V11 = cov_from_d<U>(a.v11[m]);
-    const U S00 = C[S(0, 0)] + V00, S01 = C[S(0, 1)] + V01, S11 = C[S(1, 1)] + V11;
-    const U det = S00 * S11 - S01 * S01;
-    if (!(S00 > U(0) && det > U(0))) {
-      status |= TKF_TRACK_UPDATE_NOT_SPD;
-      break;
-    }
-    const U idet = U(1) / det;
-    Si00 = S11 * idet;
-    Si01 = -S01 * idet;
-    Si11 = S00 * idet;
-    r0 = cov_from_d<U>(m0 - p[0]);
-    r1 = cov_from_d<U>(m1 - p[1]);
-    chi2 += cov_to_d(r0 * (Si00 * r0 + Si01 * r1) + r1 * (Si01 * r0 + Si11 * r1));
-#pragma unroll
-    for (int j = 0; j < 5; ++j) {
-      const U U0 = C[S(j, 0)], U1 = C[S(j, 1)];
-      K[j][0] = U0 * Si00 + U1 * Si01;
-      K[j][1] = U0 * Si01 + U1 * Si11;
-    }
-#pragma unroll
-    for (int j = 0; j < 5; ++j) p[j] += cov_to_d(K[j][0] * r0 + K[j][1] * r1);
-    if constexpr (kG == 1) {
-      // X = (I - K H) C ; C' = X - (X H^T - K V) K^T
-      U X[5][5];
-#pragma unroll
-      for (int r_ = 0; r_ < 5; ++r_)
-#pragma unroll
-        for (int c_ = 0; c_ < 5; ++c_) X[r_][c_] = C[S(r_, c_)] - K[r_][0] * C[S(0, c_)] - K[r_][1] * C[S(1, c_)];
-      U Y[5][2];
-#pragma unroll
-      for (int r_ = 0; r_ < 5; ++r_) {
-        Y[r_][0] = X[r_][0] - (K[r_][0] * V00 + K[r_][1] * V01);
-        Y[r_][1] = X[r_][1] - (K[r_][0] * V01 + K[r_][1] * V11);
-      }
-#pragma unroll
-      for (int r_ = 0; r_ < 5; ++r_)
-#pragma unroll
-        for (int c_ = r_; c_ < 5; ++c_) C[S(r_, c_)] = X[r_][c_] - Y[r_][0] * K[c_][0] - Y[r_][1] * K[c_][1];
-    } else {
-      // the same, row gl in lane gl and row 4 in every lane, then exchanged
-      const U Kg0 = pick4(gl, K[0][0], K[1][0], K[2][0], K[3][0]);
-      const U Kg1 = pick4(gl, K[0][1], K[1][1], K[2][1], K[3][1]);
-      U Xg[5], X4[5], Cn[5];
-#pragma unroll
-      for (int c_ = 0; c_ < 5; ++c_) {
-        const U Cgc = pick4(gl, C[S(0, c_)], C[S(1, c_)], C[S(2, c_)], C[S(3, c_)]);
-        Xg[c_] = Cgc - Kg0 * C[S(0, c_)] - Kg1 * C[S(1, c_)];
-        X4[c_] = C[S(4, c_)] - K[4][0] * C[S(0, c_)] - K[4][1] * C[S(1, c_)];
-      }
-      const U Yg0 = Xg[0] - (Kg0 * V00 + Kg1 * V01), Yg1 = Xg[1] - (Kg0 * V01 + Kg1 * V11);
-      const U Y40 = X4[0] - (K[4][0] * V00 + K[4][1] * V01), Y41 = X4[1] - (K[4][0] * V01 + K[4][1] * V11);
-#pragma unroll
-      for (int c_ = 0; c_ < 5; ++c_) Cn[c_] = Xg[c_] - Yg0 * K[c_][0] - Yg1 * K[c_][1];
-      const U C44 = X4[4] - Y40 * K[4][0] - Y41 * K[4][1];
-#pragma unroll
-      for (int r_ = 0; r_ < 4; ++r_)
-#pragma unroll
-        for (int c_ = r_; c_ < 5; ++c_) C[S(r_, c_)] = gshfl<kG>(gmask, Cn[c_], r_);
-      C[S(4, 4)] = C44;
-    }
+      // the track's chi2 is the forward filter's; the backward filter's goes to chi2_bwd
+      status |= kalman_update<kG>(a, m, p, C, K, Si00, Si01, Si11, r0, r1, bwd ? chi2_bwd : chi2, gl, gmask);
+      if (status & kFatal) break;
     }  // measured
-    if (k == 0) {
+    if (!bwd && k == 0) {
       if (p[2] > kPi) p[2] -= 2.0 * kPi;
       if (p[2] <= -kPi) p[2] += 2.0 * kPi;
       if (!(p[3] > 0.0 && p[3] < kPi)) {
@@ -1198,7 +1425,8 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
       sincos(p[2], &sph, &cph);
       sincos(p[3], &sth, &cth);
       // p_0|0 and C_0|0 start the smoothed sums; P_0 = C_0|0
-      if constexpr (kG == 1) {
+      if constexpr (kSmooth == 1) {
+      } else if constexpr (kG == 1) {
 #pragma unroll
       for (int j = 0; j < 5; ++j) st.dl(j) = p[j];
 #pragma unroll
@@ -1219,30 +1447,13 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
       }
     } else {
       // filtered direction: predicted angles plus the update's increments p[2], p[3]
-      if constexpr (!kMixed) {
-        double sd, cd, se, ce;
-        small_sincos(p[2], sd, cd);
-        small_sincos(p[3], se, ce);
-        sph = sp2 * cd + cp2 * sd;
-        cph = cp2 * cd - sp2 * sd;
-        sth = st2 * ce + ct2 * se;
-        cth = ct2 * ce - st2 * se;
-      } else {
-        // sin and (cos - 1) of the small increments in FP32, applied to the FP64 anchors
-        double sd, cd1, se, ce1;
-        small_sincos_m1(p[2], sd, cd1);
-        small_sincos_m1(p[3], se, ce1);
-        sph = sp2 + (sp2 * cd1 + cp2 * sd);
-        cph = cp2 + (cp2 * cd1 - sp2 * sd);
-        sth = st2 + (st2 * ce1 + ct2 * se);
-        cth = ct2 + (ct2 * ce1 - st2 * se);
-      }
-      if (!(sth > 0.0)) {  // theta left (0, pi)
+      if (!turn_direction<kMixed>(p, sp2, cp2, st2, ct2, sph, cph, sth, cth)) {  // theta left (0, pi)
         status |= TKF_TRACK_NON_FINITE;
         break;
       }
       // W = R H^T S^-1; p_0|N += W r; C_0|N -= W (R H^T)^T; P = R - R H^T K^T
-      if constexpr (kG == 1) {
+      if constexpr (kSmooth == 1) {
+      } else if constexpr (kG == 1) {
       U W[5][2];
 #pragma unroll
       for (int j = 0; j < 5; ++j) {
@@ -1286,6 +1497,10 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
       }
     }
     sp = s;
+  }
+  }  // passes
+  if constexpr (kSmooth == 1) {
+    if (!(status & kFatal)) status |= combine_with_seed(a, i, p, C, sph, cph, sth, cth, st);
   }
   if constexpr (kG > 1) {
     // the smoothed sums into every lane's full store (rows 0..3 from their lanes)
@@ -1365,7 +1580,7 @@ __host__ __device__ constexpr int reg_state_place(int regs) { return regs == 128
 
 // kG lanes a track (1, or 4 for the group-per-track mapping): a warp takes tpw <= 32 / kG tracks
 // at a time, lanes g kG .. g kG + kG - 1 fit track base + g together.
-template <int kPrec, int kMode, int kRegs, int kG, class F>
+template <int kPrec, int kMode, int kRegs, int kG, int kSmooth, class F>
 __global__ void __launch_bounds__(reg_block_threads(kRegs), reg_min_blocks(kRegs))
     fit_persistent_kernel(FitArgs a, F fld, const uint32_t* __restrict__ perm, uint32_t* __restrict__ counter,
                           uint32_t tpw) {
@@ -1382,7 +1597,7 @@ __global__ void __launch_bounds__(reg_block_threads(kRegs), reg_min_blocks(kRegs
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= a.n_tracks) break;
     const uint32_t j = base + g;
-    if (g < tpw && j < a.n_tracks) fit_track<kPrec, kMode, kG>(a, fld, perm[j], st, gl, gmask);
+    if (g < tpw && j < a.n_tracks) fit_track<kPrec, kMode, kG, kPlace, kSmooth>(a, fld, perm[j], st, gl, gmask);
   }
 }
 
@@ -1695,43 +1910,44 @@ inline cudaError_t propose_fields(const FitArgs& a, const FieldDev& f, float* h0
   return launch_propose(a, grid_policy(f), h0, stream);
 }
 
-// Launches the persistent fit for one precision, step mode, lanes a track and field.
-template <int kPrec, int kMode, int kRegs, int kG, class F>
+// Launches the persistent fit for one precision, step mode, lanes a track, smoother and field.
+template <int kPrec, int kMode, int kRegs, int kG, int kSmooth, class F>
 cudaError_t launch_persistent(const FitArgs& a, const F& fld, const uint32_t* perm, uint32_t* counter,
                               LaunchShape shape, cudaStream_t stream) {
   if (shape.threads > reg_block_threads(kRegs) || shape.tracks_per_warp * kG > 32) return cudaErrorInvalidConfiguration;
   const int place = kPrec == 2 ? 0 : reg_state_place(kRegs);
   const size_t smem = size_t(shape.threads) * state_doubles(place) * sizeof(double);
-  fit_persistent_kernel<kPrec, kMode, kRegs, kG>
+  fit_persistent_kernel<kPrec, kMode, kRegs, kG, kSmooth>
       <<<shape.blocks, shape.threads, smem, stream>>>(a, fld, perm, counter, uint32_t(shape.tracks_per_warp));
   return cudaGetLastError();
 }
 
 // Record capture (training only) is built with the full register file and one lane a track.
-template <int kPrec, int kRegs, int kG, class F>
+template <int kPrec, int kRegs, int kG, int kSmooth, class F>
 cudaError_t launch_mode(const FitArgs& a, const F& fld, int mode, const uint32_t* perm, uint32_t* counter,
                         LaunchShape shape, cudaStream_t stream) {
-  if (mode == kLearned) return launch_persistent<kPrec, kLearned, kRegs, kG>(a, fld, perm, counter, shape, stream);
+  if (mode == kLearned)
+    return launch_persistent<kPrec, kLearned, kRegs, kG, kSmooth>(a, fld, perm, counter, shape, stream);
   if (mode == kRecord) {
-    if constexpr (kRegs == 255 && kPrec != 2 && kG == 1)
-      return launch_persistent<kPrec, kRecord, kRegs, kG>(a, fld, perm, counter, shape, stream);
+    if constexpr (kRegs == 255 && kPrec != 2 && kG == 1 && kSmooth == 0)
+      return launch_persistent<kPrec, kRecord, kRegs, kG, kSmooth>(a, fld, perm, counter, shape, stream);
     return cudaErrorInvalidValue;
   }
-  return launch_persistent<kPrec, kPlain, kRegs, kG>(a, fld, perm, counter, shape, stream);
+  return launch_persistent<kPrec, kPlain, kRegs, kG, kSmooth>(a, fld, perm, counter, shape, stream);
 }
 
-template <int kPrec, int kRegs, int kG = 1>
+template <int kPrec, int kRegs, int kG = 1, int kSmooth = 0>
 cudaError_t launch_fields(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm, uint32_t* counter,
                           LaunchShape shape, cudaStream_t stream) {
   if (f.kind == TKF_FIELD_UNIFORM) {
     if (f.b[0] == 0.0 && f.b[1] == 0.0)
-      return launch_mode<kPrec, kRegs, kG>(a, FieldUniformZ{f.b[2], float(f.b[2])}, mode, perm, counter, shape,
+      return launch_mode<kPrec, kRegs, kG, kSmooth>(a, FieldUniformZ{f.b[2], float(f.b[2])}, mode, perm, counter, shape,
                                            stream);
-    return launch_mode<kPrec, kRegs, kG>(
+    return launch_mode<kPrec, kRegs, kG, kSmooth>(
         a, FieldUniform{{f.b[0], f.b[1], f.b[2]}, {float(f.b[0]), float(f.b[1]), float(f.b[2])}}, mode, perm, counter,
         shape, stream);
   }
-  return launch_mode<kPrec, kRegs, kG>(a, grid_policy(f), mode, perm, counter, shape, stream);
+  return launch_mode<kPrec, kRegs, kG, kSmooth>(a, grid_policy(f), mode, perm, counter, shape, stream);
 }
 
 }  // namespace

@@ -61,6 +61,8 @@ struct FitArgs {
   const double* __restrict__ seed_par;
   const double* __restrict__ seed_cov;
   double seed_cov_scale;  // factor on every seed covariance element (1: as given)
+  int smoother;               // TKF_SMOOTHER_RTS or TKF_SMOOTHER_TWO_FILTER
+  double backward_inflation;  // two-filter: factor on the backward filter's starting covariance
   double* __restrict__ par;
   double* __restrict__ cov;
   double* __restrict__ chi2;
@@ -171,6 +173,13 @@ cudaError_t launch_fit_mixed32(const FitArgs& a, const FieldDev& f, int mode, co
                                LaunchShape shape, cudaStream_t stream);
 cudaError_t launch_fit_group(const FitArgs& a, const FieldDev& f, int precision, int mode, const uint32_t* perm,
                              uint32_t* counter, LaunchShape shape, cudaStream_t stream);
+// Two-filter smoother (a.smoother == TKF_SMOOTHER_TWO_FILTER): one lane a track, 255 registers.
+cudaError_t launch_fit_two_filter(const FitArgs& a, const FieldDev& f, int precision, int mode, const uint32_t* perm,
+                                  uint32_t* counter, LaunchShape shape, cudaStream_t stream);
+cudaError_t launch_fit_two_filter_mixed(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm,
+                                        uint32_t* counter, LaunchShape shape, cudaStream_t stream);
+cudaError_t launch_fit_two_filter_mixed32(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm,
+                                          uint32_t* counter, LaunchShape shape, cudaStream_t stream);
 
 // Enqueues the fit of every track in `a` on `stream`: track ordering, then the persistent fit.
 // With `timing`, events timing[0] and timing[1] are recorded right before and after the

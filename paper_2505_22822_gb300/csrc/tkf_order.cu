@@ -98,7 +98,9 @@ cudaError_t launch_fit(const FitArgs& a, const FieldDev& f, int precision, const
     b.h0 = ws.h0;
   }
   if (timing && (e = cudaEventRecord(timing[0], stream)) != cudaSuccess) return e;
-  e = shape.group == 4              ? launch_fit_group(b, f, precision, mode, ws.perm, ws.counter, shape, stream)
+  e = a.smoother == TKF_SMOOTHER_TWO_FILTER
+          ? launch_fit_two_filter(b, f, precision, mode, ws.perm, ws.counter, shape, stream)
+      : shape.group == 4            ? launch_fit_group(b, f, precision, mode, ws.perm, ws.counter, shape, stream)
       : precision == TKF_MIXED      ? launch_fit_mixed(b, f, mode, ws.perm, ws.counter, shape, stream)
       : precision == TKF_MIXED_FP32 ? launch_fit_mixed32(b, f, mode, ws.perm, ws.counter, shape, stream)
                                     : launch_fit_fp64(b, f, mode, ws.perm, ws.counter, shape, stream);

@@ -180,8 +180,9 @@ std::string graph_key(const FitArgs& a, const FieldDev& f, int precision, const 
   k.put(a.n_surf);
   k.put(a.record_capacity);
   k.put(a.test_stall_proposals);
+  k.put(a.smoother);
   const double dm[] = {a.mat.z_over_a, a.mat.i_ev, a.mat.rho, a.mat.hwp_ev, a.mat.log_hwp_over_i, a.mat.bg2_density,
-                       a.opt.tol, a.opt.h_max, a.opt.h_min, a.opt.surf_tol, a.opt.mass, a.seed_cov_scale, f.b[0], f.b[1], f.b[2],
+                       a.opt.tol, a.opt.h_max, a.opt.h_min, a.opt.surf_tol, a.opt.mass, a.seed_cov_scale, a.backward_inflation, f.b[0], f.b[1], f.b[2],
                        f.r0, f.dr, f.z0, f.dz, f.inv_dr, f.inv_dz};
   for (double d : dm) k.put(d);
   const float fm[] = {a.mat.log_hwp_over_i_f, a.mat.bg2_density_f, a.mat.two_me_over_i2_f, a.mat.dedx_scale_f,
@@ -265,6 +266,15 @@ cudaError_t resolve_shape(tkf_context ctx, const FitArgs& a, const FieldDev& f, 
   if (o->tracks_per_warp) shape[2] = int(o->tracks_per_warp);
   if (o->max_registers) shape[3] = int(o->max_registers);
   *out = make_shape(shape, ctx->sm_count);
+  if (a.smoother == TKF_SMOOTHER_TWO_FILTER) {  // one kernel variant: 255 registers, one lane a track
+    if (!explicit_block) {
+      out->threads = 128;
+      out->blocks = 2 * ctx->sm_count;
+    }
+    out->regs = 255;
+    out->group = 1;
+    return cudaSuccess;
+  }
   const bool any_explicit = explicit_block || o->tracks_per_warp || o->max_registers || o->lanes_per_track;
   if (any_explicit || !(o->flags & TKF_FIT_AUTOTUNE) || a.records) return cudaSuccess;
   const std::string key = tune_key(a, f, precision, ctx->sm_count);

@@ -79,7 +79,7 @@ def compare(g: dict, o: "oracle.FitResult", tol: float, idx=None):
     return ok, same_steps, stats
 
 
-def self_sensitivity(w, track: int, trials: int = 8, seed: int = 0) -> float:
+def self_sensitivity(w, track: int, trials: int = 8, seed: int = 0, opts=None) -> float:
     """How far the oracle's own result for one track moves, in the metric above, when its seed
     parameters and measured positions change by one unit in the last place (random signs): the
     resolution to which the track's FP64 result is determined at all. Two correct FP64
@@ -87,7 +87,7 @@ def self_sensitivity(w, track: int, trials: int = 8, seed: int = 0) -> float:
     t = w.tracks
     sub = t.subset(np.array([track]))
     fo = oracle.field_from(w.field)
-    opts = oracle.Options(mass=w.mass)
+    opts = opts or oracle.Options(mass=w.mass)
     base = oracle.fit(w.geometry.table, fo, opts, sub.offsets, sub.meas, sub.sid, sub.seed_par, sub.seed_cov)
     rng = np.random.default_rng(seed)
     worst = 0.0
