@@ -60,7 +60,7 @@ FLOPS_MAP = {
 # ncu capture, divided by the capture's tracks; traffic grows with the tracks of a launch).
 # Keyed by (workload, variant, register cap of the launched kernel); a kernel change voids the
 # entry. Barrel, learned start, 64 registers: 20-event batch, 279,450 tracks, 128 x 8 blocks.
-TRAFFIC_PER_TRACK = {("barrel", "mixed_learned", 64): (5.724735e9 + 4.941866e9) / 279450}
+TRAFFIC_PER_TRACK = {("barrel", "mixed_learned", 64): (5.732764e9 + 4.978447e9) / 279450}
 TRAFFIC_CAPTURE = {("barrel", "mixed_learned", 64): "ncu capture of 279,450 tracks (20 events), scaled by tracks"}
 
 
@@ -809,9 +809,10 @@ def main():
     head_shape = hv["shape"] or [None] * 5
     # the captured kernel: one lane a track (a group shape is another kernel)
     traffic_key = (args.workload, head, head_shape[3]) if (head_shape[4:] or [1])[0] == 1 else None
-    achieved = hv["flops"] / (hv["kernel_ms"] * 1e-3) / 1e12
+    # no FP64 flop count for the two-filter variants: their roofline stays null
+    achieved = hv["flops"] / (hv["kernel_ms"] * 1e-3) / 1e12 if hv["flops"] is not None else None
     roof = {"bound": "alu", "kernel": f"fit_persistent_kernel<{head}>", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak,
+            "unit": "TFLOP/s", "frac": achieved / peak if achieved is not None else None,
             "traffic": (TRAFFIC_PER_TRACK[traffic_key] * n_tracks if traffic_key in TRAFFIC_PER_TRACK else None),
             "traffic_note": (TRAFFIC_CAPTURE.get(traffic_key, "no capture for this kernel variant") +
                              "; algorithmic bytes (inputs + outputs) per launch: "

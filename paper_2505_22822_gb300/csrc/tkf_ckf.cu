@@ -367,7 +367,13 @@ __global__ void __launch_bounds__(kCkfBlock) find_tracks_kernel(const CkfArgs a,
         uint32_t km[kCkfChildren];
         int nk = 0;
         const uint32_t m_end = a.meas_off[target + 1] < a.n_meas ? a.meas_off[target + 1] : a.n_meas;
+        // chi2 = r^T S^-1 r >= r0^2 / S00 and >= r1^2 / S11 (S positive definite): a measurement
+        // whose residual fails the gate in one coordinate alone is skipped before the full chi2.
+        // The margin keeps the skip exact under rounding (the full test would reject it too).
+        const double gate = a.chi2_max * (1.0 + 1e-6);
         for (uint32_t mi = a.meas_off[target]; mi < m_end; ++mi) {
+          const double q0 = a.loc0[mi] - pp[0], q1 = a.loc1[mi] - pp[1];
+          if (q0 * q0 > gate * (Cp[S(0, 0)] + a.v00[mi]) || q1 * q1 > gate * (Cp[S(1, 1)] + a.v11[mi])) continue;
           double c2;
           if (!meas_chi2(pp, Cp, a.loc0[mi], a.loc1[mi], a.v00[mi], a.v01[mi], a.v11[mi], c2)) continue;
           if (!(c2 < a.chi2_max)) continue;
