@@ -35,8 +35,12 @@ WORKLOAD = "barrel_endcap_50ev_uniform2T_pions"
 WORKLOAD_MAP = "solenoid_map_100k_muons"
 
 # Algorithmic FP64 flops per unit of the fit kernels, counted from the kernel source
-# (add/sub/mul = 1, fma = 2, each div/sqrt/log/sin/cos = 1; derivation in the design doc):
+# (add/sub/mul = 1, fma = 2, each div/sqrt/log/sin/cos = 1):
 # (accepted RKN step, rejected step attempt, propagated measurement k >= 1, track).
+# Two-filter: the step counters hold both passes; per measurement, the forward filter without
+# the RTS terms (R = P J^T 180, smoother sums 210) plus the backward filter's prediction and
+# update; per track, the backward start (update, reversal, direction) and the weighted mean
+# with the seed (L D L^T 65, gain 225, parameters 52, covariance 800: 1,182).
 FLOPS = {
     "fp64": (493, 111, 1494, 330),
     # mixed: only the FP64 anchors, the Joseph update and the smoother count
@@ -44,6 +48,8 @@ FLOPS = {
     "mixed_learned": (20, 8, 749, 330),
     # experimental FP32 covariance algebra: only the anchors and the smoothed sums stay FP64
     "mixed_fp32": (20, 8, 45, 30),
+    "fp64_two_filter": (493, 111, 2209, 1837),
+    "mixed_two_filter": (20, 8, 722, 1837),
 }
 # r-z field map: every attempt adds two stage positions and three bilinear lookups (FP64 in
 # the plain path: 32 flops each incl. one square root and one division), every propagated
@@ -53,6 +59,8 @@ FLOPS_MAP = {
     "mixed": (20, 8, 749, 330),
     "mixed_learned": (20, 8, 749, 330),
     "mixed_fp32": (20, 8, 45, 30),
+    "fp64_two_filter": (619, 237, 2337, 1837),
+    "mixed_two_filter": (20, 8, 722, 1837),
 }
 
 
@@ -297,11 +305,12 @@ def seed_stage(ctx, geo, fld, dev, t, opts, stream, steps: int, warmup: int, flu
     return seeds, chain_line
 
 
-def ckf_stage(ctx, fld, w, stream, steps: int, warmup: int, events: int = 5):
+def ckf_stage(ctx, fld, w, stream, steps: int, warmup: int, events: int = 5, precision: int = 0):
     """Track finding on the first `events` events of the batch, one event per launch pair: seed
     estimation from triplets (the first measurements of each simulated track on three distinct
     layers, a stand-in for triplet seeding), then the combinatorial Kalman filter over the
-    event's measurements grouped by surface. Efficiency and purity against the simulation."""
+    event's measurements grouped by surface (FP64, or mixed: FP32 propagation and transport).
+    Efficiency and purity against the simulation."""
     import torch
     import paper_2505_22822_gb300 as tkf
     g = w.geometry
@@ -324,7 +333,7 @@ def ckf_stage(ctx, fld, w, stream, steps: int, warmup: int, events: int = 5):
                           "seed_sid": T(sub.sid[sub.offsets[:-1]].astype(np.int32), torch.int32),
                           "moff": T(mc.offsets.astype(np.int32), torch.int32),
                           "cols": [T(mc.meas[:, k]) for k in range(5)]})
-    opts = tkf.Options(mass=w.mass)
+    opts = tkf.Options(mass=w.mass, precision=precision)
     results = [None] * events
 
     def step():
@@ -360,7 +369,7 @@ def ckf_stage(ctx, fld, w, stream, steps: int, warmup: int, events: int = 5):
             "seeds_per_s": n_seeds / (ms * 1e-3), "hit_efficiency": float(eff.mean()),
             "tracks_90pct_hits": float((eff >= 0.9).mean()), "purity": float(pur.mean()),
             "stages": "seed estimation (triplets) + combinatorial Kalman filter, beam 3, chi2 < 15, 2 holes",
-            "launches_per_step": 2 * events}
+            "precision": {0: "fp64", 1: "mixed"}[precision], "launches_per_step": 2 * events}
 
 
 def cpu_baseline(w, max_seconds: float = 20.0):
@@ -760,12 +769,13 @@ def main():
                             "pulls": pull_stats(out, t)}
     head = variants[-1]
     opts = results[head]["opts"]
-    seeds = chain = ckf = None
+    seeds = chain = ckf = ckf_mixed = None
     if not args.no_seeds:
         copts = results["mixed"]["opts"] if "mixed" in results else opts
         seeds, chain = seed_stage(ctx, geo, fld, dev, t, copts, stream, args.steps, args.warmup, flush)
         if args.workload == "barrel":
             ckf = ckf_stage(ctx, fld, w, stream, max(1, args.steps // 2), 1)
+            ckf_mixed = ckf_stage(ctx, fld, w, stream, max(1, args.steps // 2), 1, precision=tkf.MIXED)
     ms, ms_max, clocks = results[head]["ms"], results[head]["ms_max"], results[head]["clocks"]
     for k, v in results.items():
         counts = (FLOPS_MAP if args.workload == "map" else FLOPS).get(k)  # no count for the two-filter form
@@ -870,6 +880,7 @@ def main():
         line["chain_from_estimated_seeds"] = chain
     if ckf:
         line["track_finding"] = ckf
+        line["track_finding_mixed"] = ckf_mixed
     if e2e:
         line["e2e"] = e2e
     if not args.no_cpu_baseline:

@@ -468,8 +468,10 @@ typedef struct tkf_ckf_outputs {
 } tkf_ckf_outputs;
 
 /* Finds the candidate of every seed, asynchronously on `stream`. fit_opts gives the propagation
- * and material options (precision TKF_FP64 and step mode TKF_STEP_ADAPTIVE required; launch
- * policy fields ignored). The branch store (about 7.4 KB a seed at beam 3) is a workspace of the
+ * and material options (step mode TKF_STEP_ADAPTIVE; launch policy fields ignored) and the
+ * precision: TKF_FP64, or TKF_MIXED with the propagation, material and covariance transport in
+ * FP32 around FP64 anchors as in the fit's mixed path (navigation, chi2 gate and update stay
+ * FP64). The branch store (about 7.4 KB a seed at beam 3) is a workspace of the
  * context, grown on demand (the call then synchronizes the stream). Errors: TKF_ERR_BAD_HANDLE,
  * TKF_ERR_INVALID_ARG (NULL pointers, options out of range, no layer structure), TKF_ERR_OOM,
  * TKF_ERR_DEVICE. */
@@ -479,8 +481,8 @@ tkf_status tkf_find_tracks(tkf_context ctx, tkf_geometry geo, tkf_field field, c
 
 /* ---------------------------------------------------------------------------- learned step proposer */
 
-/* The benchmark spec's learned part (the paper has no learned component): before a track's first
- * RKN step, where the step-size control has no error estimate yet, a network proposes the
+/* A learned addition to the paper's method (which has no learned component): before a track's
+ * first RKN step, where the step-size control has no error estimate yet, a network proposes the
  * control's starting value from the seed state and the field at the first surface, toward the
  * second (the plain control starts from h_max and sheds it by rejected steps). From then on the
  * plain control adapts the value from the error estimates, and every step is accepted only if
@@ -541,8 +543,8 @@ tkf_status tkf_mlp_forward(tkf_context ctx, const float* params, const float* x,
  * the second; 0.9 exp(output rounded to a 1/32 grid), clamped to [h_min, h_max]; h_max for
  * tracks with fewer than two measurements or a bad surface id; -1 if the pre-pass timed out
  * waiting for its tensor-core work. For inspection and tests; asynchronous on `stream`.
- * Errors: as tkf_fit, TKF_ERR_INVALID_ARG for a NULL h0. The benchmark spec's learned step
- * proposer has no counterpart in the paper. */
+ * Errors: as tkf_fit, TKF_ERR_INVALID_ARG for a NULL h0. The learned step proposer has no
+ * counterpart in the paper. */
 tkf_status tkf_propose_start(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf_fit_options* opts,
                              const tkf_fit_inputs* in, float* h0, void* stream);
 

@@ -74,7 +74,7 @@ struct Field {
   const float* Bz;  // [nz][nr]
 };
 
-// Learned step proposer (the benchmark spec, not in the paper): an MLP 12 -> 64 -> 64 -> 1 with SiLU
+// Learned step proposer (an addition, not in the paper): an MLP 12 -> 64 -> 64 -> 1 with SiLU
 // activations whose weights are BF16 values; the forward pass is FP32 arithmetic.
 struct Mlp {
   float W1[64][12], b1[64], W2[64][64], b2[64], w3[64], b3;

@@ -1,6 +1,6 @@
 """Test infrastructure, not product code: plain FP64 reference of the learned step proposer.
 
-The network (the benchmark spec, learned part; the paper has no learned component) maps 12 inputs
+The network (the learned addition; the paper has no learned component) maps 12 inputs
 (local position, direction, q/p, field, last step, distance to the target plane) through two
 hidden layers of 64 SiLU units to one output, ln of the largest step within the RKN
 tolerance. Parameters are packed as W1 [64, 12], b1 [64], W2 [64, 64], b2 [64], w3 [64],

@@ -599,8 +599,8 @@ tkf_status tkf_find_tracks(tkf_context ctx, tkf_geometry geo, tkf_field field, c
   if (!geo || !field || geo->ctx != ctx || field->ctx != ctx)
     return fail(ctx, TKF_ERR_BAD_HANDLE, std::string(fn) + ": geometry or field handle NULL or from another context");
   if (!o || !co || !in || !out) return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": NULL argument");
-  if (o->precision != TKF_FP64 || o->step_mode != TKF_STEP_ADAPTIVE)
-    return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": needs TKF_FP64 and TKF_STEP_ADAPTIVE");
+  if (!(o->precision == TKF_FP64 || o->precision == TKF_MIXED) || o->step_mode != TKF_STEP_ADAPTIVE)
+    return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": needs TKF_FP64 or TKF_MIXED, and TKF_STEP_ADAPTIVE");
   if (!(o->tol > 0) || !(o->h_max > 0) || !(o->h_min > 0) || !(o->h_min <= o->h_max) || !(o->surf_tol > 0) ||
       o->max_steps == 0 || !(o->mass > 0) || !isfinite(o->h_max))
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": fit options out of range");
@@ -658,6 +658,7 @@ tkf_status tkf_find_tracks(tkf_context ctx, tkf_geometry geo, tkf_field field, c
   a.beam = co->beam;
   a.max_holes = co->max_holes;
   a.max_entries = co->max_entries;
+  a.mixed = o->precision == TKF_MIXED;
   a.n_entries = out->n_entries;
   a.n_meas_out = out->n_meas;
   a.chi2 = out->chi2;

@@ -2,8 +2,9 @@
 // Sec. 2 between seeding and fitting; the algorithm and the navigation read for this library
 // are stated in include/tkf.h at tkf_find_tracks).
 //
-// One thread per seed, FP64 throughout (the fit's RKN propagation, material and gain-matrix
-// update). Each thread keeps its beam of branches, their children and its best ended branch in
+// One thread per seed: the fit's RKN propagation, material and gain-matrix update; FP64
+// throughout, or (kMixed) with the propagation, material and covariance transport in FP32
+// around FP64 anchors as in the fit's mixed path (navigation, gate and update stay FP64). Each thread keeps its beam of branches, their children and its best ended branch in
 // a workspace slot of global memory (a branch: state, covariance, counters and up to 32 entries,
 // 464 bytes); the branches are read and written once per step, the geometry, layer tables and
 // measurements are gathered through L1/L2.
@@ -31,7 +32,7 @@ struct CkfBranch {
   int32_t e_meas[TKF_CKF_MAX_ENTRIES];
 };
 
-__device__ __forceinline__ uint32_t slots_per_seed(uint32_t beam) { return beam * (kCkfChildren + 2) + 1; }
+__host__ __device__ __forceinline__ uint32_t slots_per_seed(uint32_t beam) { return beam * (kCkfChildren + 2) + 1; }
 
 // ranking of branches: more measurements, fewer consecutive holes, lower chi2, created earlier
 __device__ __forceinline__ bool better(const CkfBranch& a, const CkfBranch& b) {
@@ -206,7 +207,7 @@ __device__ int navigate(const CkfArgs& a, int cur, const double x[3], const doub
 
 // From a branch's filtered state on its surface: material, navigation, RKN propagation and
 // covariance transport to the next module; returns its id (-1: none ahead, or stopped).
-template <class F>
+template <bool kMixed, class F>
 __device__ int predict(const CkfArgs& a, const F& fld, const CkfBranch& br, double pp[5], double Cp[15],
                        double& h_ctrl) {
   Surf sc;
@@ -216,7 +217,14 @@ __device__ int predict(const CkfArgs& a, const F& fld, const CkfBranch& br, doub
   sincos(br.p[3], &sth, &cth);
   const double T0[3] = {sth * cph, sth * sph, cth};
   double lam = br.p[4], th0sq;
-  if (material(sc, a.mat, a.opt.mass, T0, lam, th0sq) & ~(TKF_TRACK_OUT_OF_FIELD)) return -1;
+  if constexpr (kMixed) {
+    const float Tm[3] = {d2f(T0[0]), d2f(T0[1]), d2f(T0[2])};
+    float th0sq_f;
+    if (material_mixed(sc, a.mat, a.opt, Tm, lam, th0sq_f) & ~(TKF_TRACK_OUT_OF_FIELD)) return -1;
+    th0sq = f2d(th0sq_f);
+  } else {
+    if (material(sc, a.mat, a.opt.mass, T0, lam, th0sq) & ~(TKF_TRACK_OUT_OF_FIELD)) return -1;
+  }
   double x[3];
   for (int j = 0; j < 3; ++j) x[j] = sc.c[j] + br.p[0] * sc.u[j] + br.p[1] * sc.v[j];
   double B[3];
@@ -232,48 +240,99 @@ __device__ int predict(const CkfArgs& a, const F& fld, const CkfBranch& br, doub
     if (m < 0) return -1;
     Surf s;
     load_surf(a.surf, uint32_t(m), s);
-    double r[3] = {x[0], x[1], x[2]}, T[3] = {T0[0], T0[1], T0[2]};
-    double dr[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    double dT[3][3] = {{-sth * sph, sth * cph, 0.0}, {cth * cph, cth * sph, -sth}, {0, 0, 0}};
-    double kend[3], h = br.h_ctrl;
-    uint32_t att = 0, rej = 0;
-    StepLearn learn{nullptr, 0, nullptr, 0.0f};
-    const uint32_t st = propagate<kPlain, 3>(fld, a.opt, s, r, T, lam, dr, dT, 0.0, h, att, rej, kend, learn);
-    const double d[3] = {r[0] - s.c[0], r[1] - s.c[1], r[2] - s.c[2]};
-    double hu, hv;
-    module_half(a, uint32_t(m), hu, hv);
-    if ((st & ~TKF_TRACK_OUT_OF_FIELD) || fabs(dot3(s.u, d)) > hu || fabs(dot3(s.v, d)) > hv) {
-      skip[nskip++] = uint32_t(m);
-      continue;
-    }
-    // bound parameters and the transport Jacobian at the target (path correction)
-    const double inv_norm = 1.0 / sqrt(dot3(T, T));
-    const double tn[3] = {T[0] * inv_norm, T[1] * inv_norm, T[2] * inv_norm};
-    const double st2 = sqrt(tn[0] * tn[0] + tn[1] * tn[1]), inv_st = 1.0 / st2;
-    const double ct2 = tn[2], cp2 = tn[0] * inv_st, sp2 = tn[1] * inv_st;
-    const double inv_nT = 1.0 / dot3(s.n, T);
-    double J[5][5];
-    for (int c = 0; c < 5; ++c) {
-      double xx[3], tt[3], out[4];
-      for (int j = 0; j < 3; ++j) {
-        xx[j] = (c == 0) ? sc.u[j] : (c == 1) ? sc.v[j] : dr[c - 2][j];
-        tt[j] = (c < 2) ? 0.0 : dT[c - 2][j];
+    if constexpr (kMixed) {
+      double r[3] = {x[0], x[1], x[2]}, T[3] = {T0[0], T0[1], T0[2]};
+      const float fsth = d2f(sth), fcth = d2f(cth), fsph = d2f(sph), fcph = d2f(cph);
+      float dr[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+      float dT[3][3] = {{-fsth * fsph, fsth * fcph, 0.0f}, {fcth * fcph, fcth * fsph, -fsth}, {0, 0, 0}};
+      float kend[3], h = float(br.h_ctrl);
+      uint32_t att = 0, rej = 0;
+      StepLearn learn{nullptr, 0, nullptr, 0.0f};
+      const uint32_t st =
+          propagate_mixed<kPlain, 3>(fld, a.opt, s, s.nf, r, T, lam, dr, dT, 0.0f, h, att, rej, kend, learn);
+      const double d[3] = {r[0] - s.c[0], r[1] - s.c[1], r[2] - s.c[2]};
+      double hu, hv;
+      module_half(a, uint32_t(m), hu, hv);
+      if ((st & ~TKF_TRACK_OUT_OF_FIELD) || fabs(dot3(s.u, d)) > hu || fabs(dot3(s.v, d)) > hv) {
+        skip[nskip++] = uint32_t(m);
+        continue;
       }
-      jac_column(s.n, s.u, s.v, T, kend, inv_nT, sp2, cp2, st2, ct2, inv_st, xx, tt, out);
-      for (int rr = 0; rr < 4; ++rr) J[rr][c] = out[rr];
-      J[4][c] = (c == 4) ? 1.0 : 0.0;
+      // bound parameters (FP64 from the anchors) and the transport Jacobian in FP32
+      const double inv_norm = 1.0 / sqrt(dot3(T, T));
+      const double tn[3] = {T[0] * inv_norm, T[1] * inv_norm, T[2] * inv_norm};
+      const double st2 = sqrt(tn[0] * tn[0] + tn[1] * tn[1]), inv_st = 1.0 / st2;
+      const double ct2 = tn[2], cp2 = tn[0] * inv_st, sp2 = tn[1] * inv_st;
+      const float Tf[3] = {d2f(T[0]), d2f(T[1]), d2f(T[2])};
+      const float inv_nT = 1.0f / dotr(s.nf, Tf);
+      const float fst = d2f(st2), fct = d2f(ct2), fcp = d2f(cp2), fsp = d2f(sp2), finv_st = d2f(inv_st);
+      float J[5][5];
+      for (int c = 0; c < 5; ++c) {
+        float xx[3], tt[3], out[4];
+        for (int j = 0; j < 3; ++j) {
+          xx[j] = (c == 0) ? sc.uf[j] : (c == 1) ? sc.vf[j] : dr[c - 2][j];
+          tt[j] = (c < 2) ? 0.0f : dT[c - 2][j];
+        }
+        jac_column(s.nf, s.uf, s.vf, Tf, kend, inv_nT, fsp, fcp, fst, fct, finv_st, xx, tt, out);
+        for (int rr = 0; rr < 4; ++rr) J[rr][c] = out[rr];
+        J[4][c] = (c == 4) ? 1.0f : 0.0f;
+      }
+      pp[0] = dot3(s.u, d);
+      pp[1] = dot3(s.v, d);
+      pp[2] = atan2(tn[1], tn[0]);
+      pp[3] = acos(tn[2]);
+      pp[4] = lam;
+      float Cf[15];
+      for (int j = 0; j < 15; ++j) Cf[j] = d2f(br.C[j]);
+      Cf[S(2, 2)] += d2f(th0sq) / (fsth * fsth);
+      Cf[S(3, 3)] += d2f(th0sq);
+      transport_cov<1>(J, Cf, 0u, 0xffffffffu);
+      for (int j = 0; j < 15; ++j) Cp[j] = f2d(Cf[j]);
+      h_ctrl = double(h);
+      return m;
+    } else {
+      double r[3] = {x[0], x[1], x[2]}, T[3] = {T0[0], T0[1], T0[2]};
+      double dr[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+      double dT[3][3] = {{-sth * sph, sth * cph, 0.0}, {cth * cph, cth * sph, -sth}, {0, 0, 0}};
+      double kend[3], h = br.h_ctrl;
+      uint32_t att = 0, rej = 0;
+      StepLearn learn{nullptr, 0, nullptr, 0.0f};
+      const uint32_t st = propagate<kPlain, 3>(fld, a.opt, s, r, T, lam, dr, dT, 0.0, h, att, rej, kend, learn);
+      const double d[3] = {r[0] - s.c[0], r[1] - s.c[1], r[2] - s.c[2]};
+      double hu, hv;
+      module_half(a, uint32_t(m), hu, hv);
+      if ((st & ~TKF_TRACK_OUT_OF_FIELD) || fabs(dot3(s.u, d)) > hu || fabs(dot3(s.v, d)) > hv) {
+        skip[nskip++] = uint32_t(m);
+        continue;
+      }
+      // bound parameters and the transport Jacobian at the target (path correction)
+      const double inv_norm = 1.0 / sqrt(dot3(T, T));
+      const double tn[3] = {T[0] * inv_norm, T[1] * inv_norm, T[2] * inv_norm};
+      const double st2 = sqrt(tn[0] * tn[0] + tn[1] * tn[1]), inv_st = 1.0 / st2;
+      const double ct2 = tn[2], cp2 = tn[0] * inv_st, sp2 = tn[1] * inv_st;
+      const double inv_nT = 1.0 / dot3(s.n, T);
+      double J[5][5];
+      for (int c = 0; c < 5; ++c) {
+        double xx[3], tt[3], out[4];
+        for (int j = 0; j < 3; ++j) {
+          xx[j] = (c == 0) ? sc.u[j] : (c == 1) ? sc.v[j] : dr[c - 2][j];
+          tt[j] = (c < 2) ? 0.0 : dT[c - 2][j];
+        }
+        jac_column(s.n, s.u, s.v, T, kend, inv_nT, sp2, cp2, st2, ct2, inv_st, xx, tt, out);
+        for (int rr = 0; rr < 4; ++rr) J[rr][c] = out[rr];
+        J[4][c] = (c == 4) ? 1.0 : 0.0;
+      }
+      pp[0] = dot3(s.u, d);
+      pp[1] = dot3(s.v, d);
+      pp[2] = atan2(tn[1], tn[0]);
+      pp[3] = acos(tn[2]);
+      pp[4] = lam;
+      for (int j = 0; j < 15; ++j) Cp[j] = br.C[j];
+      Cp[S(2, 2)] += th0sq / (sth * sth);
+      Cp[S(3, 3)] += th0sq;
+      transport_cov<1>(J, Cp, 0u, 0xffffffffu);
+      h_ctrl = h;
+      return m;
     }
-    pp[0] = dot3(s.u, d);
-    pp[1] = dot3(s.v, d);
-    pp[2] = atan2(tn[1], tn[0]);
-    pp[3] = acos(tn[2]);
-    pp[4] = lam;
-    for (int j = 0; j < 15; ++j) Cp[j] = br.C[j];
-    Cp[S(2, 2)] += th0sq / (sth * sth);
-    Cp[S(3, 3)] += th0sq;
-    transport_cov<1>(J, Cp, 0u, 0xffffffffu);
-    h_ctrl = h;
-    return m;
   }
   return -1;
 }
@@ -320,7 +379,7 @@ __device__ void update(double p[5], double C[15], double m0, double m1, double V
   if (p[2] <= -kPi) p[2] += 2.0 * kPi;
 }
 
-template <class F>
+template <bool kMixed, class F>
 __global__ void __launch_bounds__(kCkfBlock) find_tracks_kernel(const CkfArgs a, const F fld) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n_seeds) return;
@@ -353,7 +412,7 @@ __global__ void __launch_bounds__(kCkfBlock) find_tracks_kernel(const CkfArgs a,
           for (int j = 0; j < 5; ++j) pp[j] = br.p[j];
           for (int j = 0; j < 15; ++j) Cp[j] = br.C[j];
         } else {
-          target = br.n_entries >= a.max_entries ? -1 : predict(a, fld, br, pp, Cp, h);
+          target = br.n_entries >= a.max_entries ? -1 : predict<kMixed>(a, fld, br, pp, Cp, h);
         }
         if (target < 0) {  // the branch ends
           if (!have_best || better(br, *best)) {
@@ -450,7 +509,10 @@ template <class F>
 cudaError_t launch_ckf(const CkfArgs& a_in, const F& fld, cudaStream_t stream) {
   CkfArgs a = a_in;
   if (a.opt.max_steps > kCkfMaxSteps) a.opt.max_steps = kCkfMaxSteps;
-  find_tracks_kernel<<<(a.n_seeds + kCkfBlock - 1) / kCkfBlock, kCkfBlock, 0, stream>>>(a, fld);
+  if (a.mixed)
+    find_tracks_kernel<true><<<(a.n_seeds + kCkfBlock - 1) / kCkfBlock, kCkfBlock, 0, stream>>>(a, fld);
+  else
+    find_tracks_kernel<false><<<(a.n_seeds + kCkfBlock - 1) / kCkfBlock, kCkfBlock, 0, stream>>>(a, fld);
   return cudaGetLastError();
 }
 

@@ -139,6 +139,7 @@ struct CkfArgs {
   OptionsDev opt;
   double chi2_max;
   uint32_t beam, max_holes, max_entries;
+  bool mixed;  // TKF_MIXED: propagation, material and covariance transport in FP32
   uint32_t* __restrict__ n_entries;
   uint32_t* __restrict__ n_meas_out;
   double* __restrict__ chi2;

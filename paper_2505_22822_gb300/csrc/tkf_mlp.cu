@@ -7,7 +7,7 @@
 //   backward  (one thread per sample; dL/dz of both hidden layers and of the output),
 //   reduce    (one thread per parameter; sums over the batch, no atomics: deterministic),
 //   adam      (one thread per parameter).
-// The paper has no learned component; this is the benchmark spec's learned step proposer.
+// The paper has no learned component; the learned step proposer is an addition to its method.
 
 #include <math.h>
 
