@@ -1172,7 +1172,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
   // (unrolled: each pass is compiled with its own direction)
   constexpr int kPasses = kSmooth == 1 ? 2 : 1;
   double chi2_bwd = 0.0;
-#pragma unroll
+#pragma unroll 1
   for (int pass = 0; pass < kPasses; ++pass) {
   const bool bwd = pass == 1;
   if (bwd) {
