@@ -306,11 +306,11 @@ def seed_stage(ctx, geo, fld, dev, t, opts, stream, steps: int, warmup: int, flu
 
 
 def ckf_stage(ctx, fld, w, stream, steps: int, warmup: int, events: int = 5, precision: int = 0):
-    """Track finding on the first `events` events of the batch, one event per launch pair: seed
+    """Track finding on the first `events` events of the batch, all in one launch pair: seed
     estimation from triplets (the first measurements of each simulated track on three distinct
-    layers, a stand-in for triplet seeding), then the combinatorial Kalman filter over the
-    event's measurements grouped by surface (FP64, or mixed: FP32 propagation and transport).
-    Efficiency and purity against the simulation."""
+    layers, a stand-in for triplet seeding), then the combinatorial Kalman filter, each seed over
+    its own event's measurements grouped by surface (FP64, or mixed: FP32 propagation and
+    transport). Efficiency and purity against the simulation."""
     import torch
     import paper_2505_22822_gb300 as tkf
     g = w.geometry
@@ -321,26 +321,35 @@ def ckf_stage(ctx, fld, w, stream, steps: int, warmup: int, events: int = 5, pre
         return torch.from_numpy(np.ascontiguousarray(x)).to(dt).to(dev)
 
     t = w.tracks
-    per_event = []
+    subs, mcs, offs, cols, bases, seed_ev = [], [], [], [[] for _ in range(5)], [], []
+    base = 0
     for e in range(events):
-        idx = np.flatnonzero(t.event == e)
-        sub = t.subset(idx)
+        sub = t.subset(np.flatnonzero(t.event == e))
         mc = synth.measurement_container(sub, g.n)
-        offs, meas, sid = synth.triplet_seed_hits(sub, g)
-        n = sub.n_tracks
-        sb = tkf.Batch.from_arrays(offs, meas, sid, np.zeros((n, 5)), np.zeros((n, 15))).to(dev)
-        per_event.append({"sub": sub, "mc": mc, "seed_batch": sb,
-                          "seed_sid": T(sub.sid[sub.offsets[:-1]].astype(np.int32), torch.int32),
-                          "moff": T(mc.offsets.astype(np.int32), torch.int32),
-                          "cols": [T(mc.meas[:, k]) for k in range(5)]})
+        subs.append(sub)
+        mcs.append(mc)
+        offs.append(mc.offsets.astype(np.int64) + base)
+        for k in range(5):
+            cols[k].append(mc.meas[:, k])
+        bases.append(base)
+        seed_ev.append(np.full(sub.n_tracks, e))
+        base += mc.meas.shape[0]
+    # the same tracks, event by event in the order above
+    allsub = t.subset(np.concatenate([np.flatnonzero(t.event == e) for e in range(events)]))
+    s_off, s_meas, s_sid = synth.triplet_seed_hits(allsub, g)
+    n_seeds = allsub.n_tracks
+    seed_batch = tkf.Batch.from_arrays(s_off, s_meas, s_sid, np.zeros((n_seeds, 5)), np.zeros((n_seeds, 15))).to(dev)
+    seed_sid = T(allsub.sid[allsub.offsets[:-1]].astype(np.int32), torch.int32)
+    seed_event = T(np.concatenate(seed_ev).astype(np.int32), torch.int32)
+    moff = T(np.stack(offs).astype(np.int32), torch.int32)
+    mcols = [T(np.concatenate(c)) for c in cols]
     opts = tkf.Options(mass=w.mass, precision=precision)
-    results = [None] * events
+    result = [None]
 
     def step():
-        for k, ev in enumerate(per_event):
-            se = tkf.estimate_seeds(ctx, geo, fld, ev["seed_batch"], tkf.SEED_FIRST_THREE, stream=stream)
-            results[k] = tkf.find_tracks(ctx, geo, fld, ev["seed_sid"], se.par, se.cov, ev["moff"], *ev["cols"], opts,
-                                         stream=stream)
+        se = tkf.estimate_seeds(ctx, geo, fld, seed_batch, tkf.SEED_FIRST_THREE, stream=stream)
+        result[0] = tkf.find_tracks(ctx, geo, fld, seed_sid, se.par, se.cov, moff, *mcols, opts, stream=stream,
+                                    seed_event=seed_event)
 
     for _ in range(warmup):
         step()
@@ -352,24 +361,26 @@ def ckf_stage(ctx, fld, w, stream, steps: int, warmup: int, events: int = 5, pre
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
-    n_seeds = sum(ev["sub"].n_tracks for ev in per_event)
+    r = result[0]
+    nm_all, em_all = r.n_entries.cpu().numpy(), r.entry_meas.cpu().numpy()
     eff, pur = [], []
-    for ev, r in zip(per_event, results):
-        nm, ne = r.n_entries.cpu().numpy(), r.entry_meas.cpu().numpy()
-        sub, mc = ev["sub"], ev["mc"]
+    k = 0
+    for sub, mc, b in zip(subs, mcs, bases):
         ntrue = np.diff(sub.offsets.astype(np.int64))
         for i in range(sub.n_tracks):
-            ms_i = ne[: nm[i], i]
-            ms_i = ms_i[ms_i >= 0]
+            ms_i = em_all[: nm_all[k], k]
+            ms_i = ms_i[ms_i >= 0] - b
             good = int((mc.track[ms_i] == i).sum())
             eff.append(good / ntrue[i])
             pur.append(good / max(len(ms_i), 1))
+            k += 1
     eff, pur = np.array(eff), np.array(pur)
     return {"events": events, "seeds": n_seeds, "ms_per_step": ms, "ms_per_event": ms / events,
             "seeds_per_s": n_seeds / (ms * 1e-3), "hit_efficiency": float(eff.mean()),
             "tracks_90pct_hits": float((eff >= 0.9).mean()), "purity": float(pur.mean()),
-            "stages": "seed estimation (triplets) + combinatorial Kalman filter, beam 3, chi2 < 15, 2 holes",
-            "precision": {0: "fp64", 1: "mixed"}[precision], "launches_per_step": 2 * events}
+            "stages": "seed estimation (triplets) + combinatorial Kalman filter, beam 3, chi2 < 15, 2 holes; "
+                      "all events in one launch each",
+            "precision": {0: "fp64", 1: "mixed"}[precision], "launches_per_step": 2}
 
 
 def cpu_baseline(w, max_seconds: float = 20.0):

@@ -439,7 +439,12 @@ void tkf_ckf_options_default(tkf_ckf_options* o);
 /* Inputs, DEVICE pointers owned by the caller (read only): seeds (surface id, parameters 5 x n,
  * packed covariance 15 x n, the fit's seed layout) and the measurements of the event grouped by
  * surface: those of surface s are meas_offsets[s] .. meas_offsets[s+1]-1 (n_surfaces + 1
- * offsets, non-decreasing). */
+ * offsets, non-decreasing). Several events in one call (n_events > 1): meas_offsets holds
+ * n_events consecutive arrays of n_surfaces + 1 offsets, all into the same measurement arrays,
+ * and seed_event[i] (DEVICE, n_seeds) is the event of seed i, whose measurements alone it
+ * searches; a seed whose event is >= n_events gets no candidate. One launch over the seeds of
+ * many events fills the GPU where one event's seeds leave most of it idle. n_events 0 or 1
+ * with seed_event NULL: one event. */
 typedef struct tkf_ckf_inputs {
   uint32_t n_seeds;
   const uint32_t* seed_sid;
@@ -452,6 +457,8 @@ typedef struct tkf_ckf_inputs {
   const double* v00;
   const double* v01;
   const double* v11;
+  uint32_t n_events;
+  const uint32_t* seed_event;
 } tkf_ckf_inputs;
 
 /* Outputs, DEVICE pointers owned by the caller (written): per seed the candidate's entry count,

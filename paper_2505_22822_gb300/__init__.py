@@ -156,7 +156,8 @@ class CkfInputs(ctypes.Structure):
     _fields_ = [("n_seeds", ctypes.c_uint32), ("seed_sid", ctypes.c_void_p), ("seed_par", ctypes.c_void_p),
                 ("seed_cov", ctypes.c_void_p), ("n_meas", ctypes.c_uint32), ("meas_offsets", ctypes.c_void_p),
                 ("loc0", ctypes.c_void_p), ("loc1", ctypes.c_void_p), ("v00", ctypes.c_void_p),
-                ("v01", ctypes.c_void_p), ("v11", ctypes.c_void_p)]
+                ("v01", ctypes.c_void_p), ("v11", ctypes.c_void_p), ("n_events", ctypes.c_uint32),
+                ("seed_event", ctypes.c_void_p)]
 
 
 class CkfOutputs(ctypes.Structure):
@@ -608,10 +609,12 @@ class CkfResult:
 
 def find_tracks(ctx: Context, geo: Geometry, field: Field, seed_sid, seed_par, seed_cov, meas_offsets, loc0, loc1, v00,
                 v01, v11, opts: Options | None = None, chi2_max: float = 15.0, beam: int = 3, max_holes: int = 2,
-                max_entries: int = 24, stream=None) -> CkfResult:
+                max_entries: int = 24, stream=None, seed_event=None) -> CkfResult:
     """tkf_find_tracks on CUDA tensors: seeds (surface ids [n], parameters [5, n], covariances
     [15, n]) and the event's measurements grouped by surface (offsets [n_surfaces + 1] and the
-    SoA measurement arrays). Enqueued on ``stream`` (default: torch's current stream)."""
+    SoA measurement arrays). Several events in one launch: ``meas_offsets`` [n_events,
+    n_surfaces + 1] into shared measurement arrays and ``seed_event`` [n] (int32) the event of
+    each seed. Enqueued on ``stream`` (default: torch's current stream)."""
     import torch
     dev = seed_par.device
     n = int(seed_sid.shape[0])
@@ -629,6 +632,9 @@ def find_tracks(ctx: Context, geo: Geometry, field: Field, seed_sid, seed_par, s
     ci.seed_sid, ci.seed_par, ci.seed_cov = _ptr(seed_sid), _ptr(seed_par), _ptr(seed_cov)
     ci.meas_offsets, ci.loc0, ci.loc1 = _ptr(meas_offsets), _ptr(loc0), _ptr(loc1)
     ci.v00, ci.v01, ci.v11 = _ptr(v00), _ptr(v01), _ptr(v11)
+    if seed_event is not None:
+        ci.n_events = int(meas_offsets.shape[0]) if meas_offsets.dim() == 2 else 1
+        ci.seed_event = _ptr(seed_event)
     cout = CkfOutputs()
     cout.n_entries, cout.n_meas, cout.chi2 = _ptr(out.n_entries), _ptr(out.n_meas), _ptr(out.chi2)
     cout.entry_sid, cout.entry_meas = _ptr(out.entry_sid), _ptr(out.entry_meas)

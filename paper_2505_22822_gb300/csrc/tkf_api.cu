@@ -615,6 +615,8 @@ tkf_status tkf_find_tracks(tkf_context ctx, tkf_geometry geo, tkf_field field, c
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": NULL required pointer");
   if (in->n_meas > 0 && (!in->loc0 || !in->loc1 || !in->v00 || !in->v01 || !in->v11))
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": NULL measurement pointer");
+  if (in->n_events > 1 && !in->seed_event)
+    return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": several events need seed_event");
   const void* ptrs[] = {in->seed_par, in->seed_cov, in->loc0, in->loc1, in->v00, in->v01, in->v11, out->chi2};
   for (const void* p : ptrs)
     if (!aligned8(p)) return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": pointer not 8-byte aligned");
@@ -641,6 +643,8 @@ tkf_status tkf_find_tracks(tkf_context ctx, tkf_geometry geo, tkf_field field, c
   a.seed_cov = in->seed_cov;
   a.meas_off = in->meas_offsets;
   a.n_meas = in->n_meas;
+  a.seed_event = in->seed_event;
+  a.n_events = in->seed_event ? (in->n_events > 1 ? in->n_events : 1u) : 1u;
   a.loc0 = in->loc0;
   a.loc1 = in->loc1;
   a.v00 = in->v00;

@@ -389,7 +389,9 @@ __global__ void __launch_bounds__(kCkfBlock) find_tracks_kernel(const CkfArgs a,
   CkfBranch* best = kids + B * (kCkfChildren + 1);
   bool have_best = false;
   const uint32_t seed_sid = a.seed_sid[i];
-  if (seed_sid < a.n_surf) {
+  const uint32_t ev = a.seed_event ? a.seed_event[i] : 0u;
+  const uint32_t* __restrict__ moff = a.meas_off + size_t(ev) * (a.n_surf + 1);  // this event's offsets
+  if (seed_sid < a.n_surf && ev < a.n_events) {
     CkfBranch& b0 = act[0];
     for (int j = 0; j < 5; ++j) b0.p[j] = a.seed_par[size_t(j) * n + i];
     for (int j = 0; j < 15; ++j) b0.C[j] = a.seed_cov[size_t(j) * n + i];
@@ -425,12 +427,12 @@ __global__ void __launch_bounds__(kCkfBlock) find_tracks_kernel(const CkfArgs a,
         double kc2[kCkfChildren];
         uint32_t km[kCkfChildren];
         int nk = 0;
-        const uint32_t m_end = a.meas_off[target + 1] < a.n_meas ? a.meas_off[target + 1] : a.n_meas;
+        const uint32_t m_end = moff[target + 1] < a.n_meas ? moff[target + 1] : a.n_meas;
         // chi2 = r^T S^-1 r >= r0^2 / S00 and >= r1^2 / S11 (S positive definite): a measurement
         // whose residual fails the gate in one coordinate alone is skipped before the full chi2.
         // The margin keeps the skip exact under rounding (the full test would reject it too).
         const double gate = a.chi2_max * (1.0 + 1e-6);
-        for (uint32_t mi = a.meas_off[target]; mi < m_end; ++mi) {
+        for (uint32_t mi = moff[target]; mi < m_end; ++mi) {
           const double q0 = a.loc0[mi] - pp[0], q1 = a.loc1[mi] - pp[1];
           if (q0 * q0 > gate * (Cp[S(0, 0)] + a.v00[mi]) || q1 * q1 > gate * (Cp[S(1, 1)] + a.v11[mi])) continue;
           double c2;

@@ -122,8 +122,10 @@ struct CkfArgs {
   const uint32_t* __restrict__ seed_sid;
   const double* __restrict__ seed_par;  // [5][n_seeds]
   const double* __restrict__ seed_cov;  // [15][n_seeds]
-  const uint32_t* __restrict__ meas_off;
+  const uint32_t* __restrict__ meas_off;    // [n_events][n_surf + 1]
   uint32_t n_meas;  // measurement rows: offsets beyond are clamped (never read past the arrays)
+  const uint32_t* __restrict__ seed_event;  // event of each seed, or null (one event)
+  uint32_t n_events;
   const double* __restrict__ loc0;
   const double* __restrict__ loc1;
   const double* __restrict__ v00;

@@ -209,3 +209,60 @@ def test_ckf_mixed_precision(ctx, workload):
     print({"eff": eff.mean(), "eff_oracle": eff_o.mean(), "purity": pur.mean(), "purity_oracle": pur_o.mean()})
     assert abs(eff.mean() - eff_o.mean()) < 2e-3 and abs(pur.mean() - pur_o.mean()) < 2e-3
 
+
+
+def test_ckf_events_batched_in_one_launch(ctx):
+    """Seeds of several events in one launch, each searching its own event's measurements
+    (offsets [n_events, n_surfaces + 1] into shared arrays): the same candidates, bit for bit,
+    as one launch per event; a seed of a missing event gets none."""
+    w = synth.barrel_workload(n_events=3, lo=800, hi=1200, seed=35)
+    t, g = w.tracks, w.geometry
+    d = "cuda:0"
+
+    def T(x, dt=torch.float64):
+        return torch.from_numpy(np.ascontiguousarray(x)).to(dt).to(d)
+
+    singles, offs, cols, sids, pars, covs, evs, bases = [], [], [[] for _ in range(5)], [], [], [], [], []
+    base = 0
+    for e in range(3):
+        sub = t.subset(np.flatnonzero(t.event == e))
+        mc = synth.measurement_container(sub, g.n)
+        ws = synth.Workload(w.name, g, w.field, sub, w.mass)
+        seed_sid, par, cov, _ = _seeds(ws)
+        singles.append(gpu_find(ctx, ws, mc, seed_sid, par, cov))
+        offs.append(mc.offsets.astype(np.int64) + base)
+        for k in range(5):
+            cols[k].append(mc.meas[:, k])
+        sids.append(seed_sid)
+        pars.append(par)
+        covs.append(cov)
+        evs.append(np.full(len(seed_sid), e))
+        bases.append(base)
+        base += mc.meas.shape[0]
+    sid_all, ev_all = np.concatenate(sids), np.concatenate(evs)
+    ev_all[0] = 3  # no such event
+    geo = tkf.Geometry.from_table(ctx, g.table).set_layers(g.layers, g.rings)
+    fld = tkf.Field.from_desc(ctx, w.field)
+    r = tkf.find_tracks(ctx, geo, fld, T(sid_all.astype(np.int32), torch.int32), T(np.concatenate(pars).T),
+                        T(np.concatenate(covs).T), T(np.stack(offs).astype(np.int32), torch.int32),
+                        *[T(np.concatenate(c)) for c in cols], tkf.Options(mass=w.mass),
+                        seed_event=T(ev_all.astype(np.int32), torch.int32))
+    torch.cuda.synchronize()
+    ne, nm, c2 = r.n_entries.cpu().numpy(), r.n_meas.cpu().numpy(), r.chi2.cpu().numpy()
+    es, em = r.entry_sid.cpu().numpy().view(np.uint32).T, r.entry_meas.cpu().numpy().T
+    assert ne[0] == 0 and nm[0] == 0
+    k = 0
+    for e in range(3):
+        s = singles[e]
+        n = len(s["n_entries"])
+        sl = slice(k, k + n)
+        lo = 1 if e == 0 else 0  # seed 0 was moved to a missing event
+        np.testing.assert_array_equal(ne[sl][lo:], s["n_entries"][lo:])
+        np.testing.assert_array_equal(nm[sl][lo:], s["n_meas"][lo:])
+        np.testing.assert_array_equal(c2[sl][lo:], s["chi2"][lo:])
+        for j in range(lo, n):
+            q = s["n_entries"][j]
+            np.testing.assert_array_equal(es[k + j][:q], s["sid"][j][:q])
+            sm = s["meas"][j][:q]
+            np.testing.assert_array_equal(em[k + j][:q], np.where(sm >= 0, sm + bases[e], -1))
+        k += n
