@@ -379,12 +379,52 @@ __device__ void update(double p[5], double C[15], double m0, double m1, double V
   if (p[2] <= -kPi) p[2] += 2.0 * kPi;
 }
 
+// Seeds in the order of their direction, so that the lanes of a warp cross the same modules and
+// diverge less: a counting sort over 32 x 32 bins of (theta, phi). The order within a bin is the
+// atomics' and affects no result: every seed is found on its own and written at its own index.
+constexpr int kCkfOrderBins = 1024;
+
+__device__ __forceinline__ uint32_t direction_bin(const double* __restrict__ seed_par, uint32_t n, uint32_t i) {
+  const double ph = (seed_par[2 * size_t(n) + i] + kPi) * (16.0 / kPi), th = seed_par[3 * size_t(n) + i] * (32.0 / kPi);
+  const uint32_t bp = ph >= 0.0 && ph < 32.0 ? uint32_t(ph) : (ph >= 32.0 ? 31u : 0u);  // NaN: bin 0
+  const uint32_t bt = th >= 0.0 && th < 32.0 ? uint32_t(th) : (th >= 32.0 ? 31u : 0u);
+  return bt * 32u + bp;
+}
+
+__global__ void ckf_order_hist_kernel(const double* __restrict__ seed_par, uint32_t n, uint32_t* __restrict__ hist) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    atomicAdd(&hist[direction_bin(seed_par, n, i)], 1u);
+}
+
+// exclusive prefix sum of the bins, one block of kCkfOrderBins threads
+__global__ void __launch_bounds__(kCkfOrderBins) ckf_order_scan_kernel(uint32_t* __restrict__ hist) {
+  __shared__ uint32_t v[kCkfOrderBins];
+  const uint32_t t = threadIdx.x;
+  const uint32_t own = hist[t];
+  v[t] = own;
+  __syncthreads();
+  for (uint32_t d = 1; d < uint32_t(kCkfOrderBins); d <<= 1) {
+    const uint32_t add = t >= d ? v[t - d] : 0u;
+    __syncthreads();
+    v[t] += add;
+    __syncthreads();
+  }
+  hist[t] = v[t] - own;
+}
+
+__global__ void ckf_order_scatter_kernel(const double* __restrict__ seed_par, uint32_t n, uint32_t* __restrict__ hist,
+                                         uint32_t* __restrict__ perm) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    perm[atomicAdd(&hist[direction_bin(seed_par, n, i)], 1u)] = i;
+}
+
 template <bool kMixed, class F>
 __global__ void __launch_bounds__(kCkfBlock) find_tracks_kernel(const CkfArgs a, const F fld) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n_seeds) return;
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.n_seeds) return;
+  const uint32_t i = a.perm[t];  // the seed this thread finds (the branch slots are the thread's)
   const uint32_t n = a.n_seeds, B = a.beam;
-  CkfBranch* act = static_cast<CkfBranch*>(a.ws) + size_t(i) * slots_per_seed(B);
+  CkfBranch* act = static_cast<CkfBranch*>(a.ws) + size_t(t) * slots_per_seed(B);
   CkfBranch* kids = act + B;
   CkfBranch* best = kids + B * (kCkfChildren + 1);
   bool have_best = false;
@@ -511,6 +551,17 @@ template <class F>
 cudaError_t launch_ckf(const CkfArgs& a_in, const F& fld, cudaStream_t stream) {
   CkfArgs a = a_in;
   if (a.opt.max_steps > kCkfMaxSteps) a.opt.max_steps = kCkfMaxSteps;
+  // the seed order: histogram, scan and scatter into the workspace after the branch slots
+  char* base = static_cast<char*>(a.ws) + size_t(a.n_seeds) * slots_per_seed(a.beam) * sizeof(CkfBranch);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(base);
+  uint32_t* perm = hist + kCkfOrderBins;
+  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kCkfOrderBins, stream);
+  if (e != cudaSuccess) return e;
+  const unsigned og = (a.n_seeds + 255) / 256 < 1024 ? (a.n_seeds + 255) / 256 : 1024;
+  ckf_order_hist_kernel<<<og, 256, 0, stream>>>(a.seed_par, a.n_seeds, hist);
+  ckf_order_scan_kernel<<<1, kCkfOrderBins, 0, stream>>>(hist);
+  ckf_order_scatter_kernel<<<og, 256, 0, stream>>>(a.seed_par, a.n_seeds, hist, perm);
+  a.perm = perm;
   if (a.mixed)
     find_tracks_kernel<true><<<(a.n_seeds + kCkfBlock - 1) / kCkfBlock, kCkfBlock, 0, stream>>>(a, fld);
   else
@@ -521,7 +572,9 @@ cudaError_t launch_ckf(const CkfArgs& a_in, const F& fld, cudaStream_t stream) {
 }  // namespace
 
 size_t ckf_workspace_bytes(uint32_t n_seeds, uint32_t beam) {
-  return size_t(n_seeds) * (beam * (kCkfChildren + 2) + 1) * sizeof(CkfBranch);
+  // branch slots, then the seed-order histogram and permutation
+  return size_t(n_seeds) * (beam * (kCkfChildren + 2) + 1) * sizeof(CkfBranch) +
+         sizeof(uint32_t) * (kCkfOrderBins + size_t(n_seeds));
 }
 
 cudaError_t launch_find_tracks(const CkfArgs& a, const FieldDev& f, cudaStream_t stream) {

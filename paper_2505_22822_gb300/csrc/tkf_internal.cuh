@@ -147,7 +147,8 @@ struct CkfArgs {
   double* __restrict__ chi2;
   uint32_t* __restrict__ entry_sid;   // [max_entries][n_seeds]
   int32_t* __restrict__ entry_meas;   // [max_entries][n_seeds]
-  void* ws;                           // branch store
+  void* ws;                           // branch store, then the seed order
+  const uint32_t* __restrict__ perm;  // seed found by each thread (set by the launch)
 };
 size_t ckf_workspace_bytes(uint32_t n_seeds, uint32_t beam);
 cudaError_t launch_find_tracks(const CkfArgs& a, const FieldDev& f, cudaStream_t stream);
