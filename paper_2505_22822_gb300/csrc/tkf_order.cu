@@ -7,12 +7,14 @@ namespace tkf {
 namespace {
 
 // ------------------------------------------------------------------ track ordering
-// Counting sort of the tracks by key = (most measurements first, then lowest seed pT first):
-// warps then hold tracks with the same number of measurements and similar step counts, and
-// the work queue hands out the longest tracks first.
-constexpr int kPtBins = 16;
-constexpr int kNBins = 64;
-constexpr int kKeyBins = kPtBins * kNBins;
+// Counting sort of the tracks by key = (most measurements first, then lowest seed pT first,
+// then |cos theta|): warps then hold tracks with the same number of measurements, similar step
+// counts and similar distances between surfaces (barrel or endcap), and the work queue hands
+// out the longest tracks first.
+constexpr int kPtBins = 8;
+constexpr int kNBins = 32;
+constexpr int kEtaBins = 4;
+constexpr int kKeyBins = kPtBins * kNBins * kEtaBins;
 
 __global__ void __launch_bounds__(256) order_keys_kernel(const uint32_t* __restrict__ offsets,
                                                          const double* __restrict__ seed_par, uint32_t n,
@@ -26,11 +28,14 @@ __global__ void __launch_bounds__(256) order_keys_kernel(const uint32_t* __restr
     const uint32_t b0 = offsets[i], b1 = offsets[i + 1];
     const uint32_t nh = b1 >= b0 ? min(b1 - b0, uint32_t(kNBins - 1)) : 0u;
     const float qop = float(seed_par[size_t(4) * stride + i]);
-    const float sth = fabsf(sinf(float(seed_par[size_t(3) * stride + i])));
+    const float th = float(seed_par[size_t(3) * stride + i]);
+    const float sth = fabsf(sinf(th));
     const float pt = (qop != 0.0f) ? sth / fabsf(qop) : 1e30f;
-    int pb = (pt > 0.0f) ? int(floorf(log2f(pt))) + 4 : 0;  // octaves from 1/16 GeV
+    int pb = (pt > 0.0f) ? int(floorf(log2f(pt))) + 2 : 0;  // octaves from 1/4 GeV
     pb = pb < 0 ? 0 : (pb >= kPtBins ? kPtBins - 1 : pb);
-    const uint32_t key = (uint32_t(kNBins - 1) - nh) * kPtBins + uint32_t(pb);
+    const float ac = fabsf(cosf(th)) * float(kEtaBins);
+    const int eb = ac >= 0.0f && ac < float(kEtaBins) ? int(ac) : kEtaBins - 1;  // NaN: last bin
+    const uint32_t key = ((uint32_t(kNBins - 1) - nh) * kPtBins + uint32_t(pb)) * kEtaBins + uint32_t(eb);
     keys[i] = key;
     atomicAdd(&h[key], 1u);
   }
