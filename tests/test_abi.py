@@ -35,6 +35,12 @@ def test_option_defaults():
         (0, 0, 1e-4, 1000.0, 1e-4, 1e-2, 10000)
     assert abs(o.mass - 0.1056583755) < 1e-12
     assert o.seed_cov_scale == 1.0 and o.kernel_events is None
+    assert (o.lanes_per_track, o.smoother, o.backward_inflation) == (0, tkf.SMOOTHER_RTS, 1e3)
+    c = tkf.CkfOptions()
+    tkf.lib().tkf_ckf_options_default(ctypes.byref(c))
+    assert (c.chi2_max, c.beam, c.max_holes, c.max_entries) == (15.0, 3, 2, 24)
+    # the C structs and their ctypes mirrors agree in size
+    assert ctypes.sizeof(tkf.CkfInputs) == 8 * 13 and ctypes.sizeof(tkf.FitOptions) % 8 == 0
 
 
 def test_null_and_handle_errors_need_no_device():
@@ -48,6 +54,7 @@ def test_null_and_handle_errors_need_no_device():
     assert L.tkf_fit(None, None, None, ctypes.byref(o), None, None, None) == 2
     assert L.tkf_fit_host(None, None, None, ctypes.byref(o), None, None, None) == 2
     assert L.tkf_estimate_seeds(None, None, None, 0, None, None, None) == 2
+    assert L.tkf_find_tracks(None, None, None, ctypes.byref(o), None, None, None, None) == 2
     L.tkf_context_destroy(None)
     L.tkf_geometry_destroy(None)
     L.tkf_field_destroy(None)

@@ -157,3 +157,22 @@ def test_two_filter_graph_key_and_options(ctx):
             tkf.fit(ctx, geo, fld, b, tkf.Options(smoother=tkf.SMOOTHER_TWO_FILTER, **bad))
     with pytest.raises(tkf.TkfError, match="smoother"):
         tkf.fit(ctx, geo, fld, b, tkf.Options(smoother=7))
+
+
+def test_two_filter_host_and_noalloc_entry_points(ctx):
+    """The host-buffer and the allocation-free entry points run the two-filter smoother too,
+    with the device entry point's results bit for bit."""
+    w = WORKLOADS["telescope"]()
+    t = w.tracks
+    geo = tkf.Geometry.from_table(ctx, w.geometry.table)
+    fld = tkf.Field.from_desc(ctx, w.field)
+    host = tkf.Batch.from_arrays(t.offsets, t.meas, t.sid, t.seed_par, t.seed_cov)
+    b = host.to("cuda:0")
+    opts = tkf.Options(precision=tkf.MIXED, smoother=tkf.SMOOTHER_TWO_FILTER)
+    r = tkf.fit(ctx, geo, fld, b, opts)
+    out = tkf.alloc_outputs(t.n_tracks, b.offsets.device)
+    tkf.fit_noalloc(ctx, geo, fld, b, out, opts)
+    h = tkf.fit_host(ctx, geo, fld, host, opts)
+    torch.cuda.synchronize()
+    assert torch.equal(r.par, out.par) and torch.equal(r.cov, out.cov) and torch.equal(r.chi2, out.chi2)
+    assert torch.equal(r.par.cpu(), h.par) and torch.equal(r.cov.cpu(), h.cov)
