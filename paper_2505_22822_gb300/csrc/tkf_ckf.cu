@@ -93,20 +93,27 @@ __device__ int layer_candidates(const CkfArgs& a, uint32_t li, const double q[3]
   return n;
 }
 
+// outer face radius of a barrel layer (its flat modules reach sqrt((r + 1)^2 + half_u^2))
+__device__ __forceinline__ double barrel_face(const double* l) { return sqrt((l[1] + 1.0) * (l[1] + 1.0) + l[6] * l[6]); }
+
 // straight-line path to the outer face of layer li if ahead and within its extent, else -1
-__device__ double layer_path(const CkfArgs& a, uint32_t li, const double x[3], const double T[3]) {
+// (face_r: the barrel layers' outer face radii, computed once a block)
+__device__ double layer_path(const CkfArgs& a, uint32_t li, const double x[3], const double T[3],
+                             const double* face_r) {
   const double* l = a.layers + 8 * li;
   double s;
   if (l[0] == 0.0) {
     const double aa = T[0] * T[0] + T[1] * T[1], b = x[0] * T[0] + x[1] * T[1];
-    const double rf = sqrt((l[1] + 1.0) * (l[1] + 1.0) + l[6] * l[6]);
+    const double rf = face_r[li];
     const double c = x[0] * x[0] + x[1] * x[1] - rf * rf;
     if (!(aa > 0.0) || c >= 0.0) return -1.0;
     s = (-b + sqrt(b * b - aa * c)) / aa;
     if (fabs(x[2] + s * T[2]) > 0.5 * l[3] * l[4] + 10.0) return -1.0;
   } else {
-    if (T[2] == 0.0) return -1.0;
-    s = (l[1] + (l[1] > 0.0 ? 1.0 : -1.0) - x[2]) / T[2];
+    const double dz = l[1] + (l[1] > 0.0 ? 1.0 : -1.0) - x[2];
+    // behind or parallel (opposite or zero signs): the quotient would not be > 0
+    if (!((dz > 0.0 && T[2] > 0.0) || (dz < 0.0 && T[2] < 0.0))) return -1.0;
+    s = dz / T[2];
     if (!(s > 0.0)) return -1.0;
     const double r = hypot(x[0] + s * T[0], x[1] + s * T[1]);
     if (r < l[5] - 10.0 || r > l[5] + l[2] * l[4] + 10.0) return -1.0;
@@ -161,7 +168,7 @@ __device__ int nearest_crossed(const CkfArgs& a, const uint32_t* cand, int nc, c
 // the next module from (x, T) on surface `cur`: the nearest crossing among the current layer's
 // modules around x and the modules of the layers ahead (in order of face path)
 __device__ int navigate(const CkfArgs& a, int cur, const double x[3], const double T[3], const double k[3],
-                        double bend, const uint32_t* skip, int nskip) {
+                        double bend, const uint32_t* skip, int nskip, const double* face_r) {
   uint32_t cand[9];
   int best = -1;
   double best_s = 0.0;
@@ -174,7 +181,7 @@ __device__ int navigate(const CkfArgs& a, int cur, const double x[3], const doub
     best = nearest_crossed(a, cand, nc, x, T, k, bend, sk, nskip + 1, best_s);
   }
   double ls[kCkfMaxLayers];
-  for (uint32_t li = 0; li < a.n_layers; ++li) ls[li] = int(li) == cur_layer ? -1.0 : layer_path(a, li, x, T);
+  for (uint32_t li = 0; li < a.n_layers; ++li) ls[li] = int(li) == cur_layer ? -1.0 : layer_path(a, li, x, T, face_r);
   // layers in order of face path (ties: lower index first), as a repeated minimum search
   double last_s = -1.0;
   int last_li = -1;
@@ -208,7 +215,8 @@ __device__ int navigate(const CkfArgs& a, int cur, const double x[3], const doub
 // From a branch's filtered state on its surface: material, navigation, RKN propagation and
 // covariance transport to the next module; returns its id (-1: none ahead, or stopped).
 template <bool kMixed, class F>
-__device__ int predict(const CkfArgs& a, const F& fld, const CkfBranch& br, double pp[5], double Cp[15],
+__device__ int predict(const CkfArgs& a, const F& fld, const double* face_r, const CkfBranch& br, double pp[5],
+                       double Cp[15],
                        double& h_ctrl) {
   Surf sc;
   load_surf(a.surf, uint32_t(br.sid), sc);
@@ -236,7 +244,7 @@ __device__ int predict(const CkfArgs& a, const F& fld, const CkfBranch& br, doub
   uint32_t skip[4];
   int nskip = 0;
   for (int tries = 0; tries < 4; ++tries) {
-    const int m = navigate(a, br.sid, x, T0, kc, bend, skip, nskip);
+    const int m = navigate(a, br.sid, x, T0, kc, bend, skip, nskip, face_r);
     if (m < 0) return -1;
     Surf s;
     load_surf(a.surf, uint32_t(m), s);
@@ -420,6 +428,12 @@ __global__ void ckf_order_scatter_kernel(const double* __restrict__ seed_par, ui
 
 template <bool kMixed, class F>
 __global__ void __launch_bounds__(kCkfBlock) find_tracks_kernel(const CkfArgs a, const F fld) {
+  __shared__ double face_r[kCkfMaxLayers];
+  for (uint32_t li = threadIdx.x; li < a.n_layers; li += blockDim.x) {
+    const double* l = a.layers + 8 * li;
+    face_r[li] = l[0] == 0.0 ? barrel_face(l) : 0.0;
+  }
+  __syncthreads();
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= a.n_seeds) return;
   const uint32_t i = a.perm[t];  // the seed this thread finds (the branch slots are the thread's)
@@ -454,7 +468,7 @@ __global__ void __launch_bounds__(kCkfBlock) find_tracks_kernel(const CkfArgs a,
           for (int j = 0; j < 5; ++j) pp[j] = br.p[j];
           for (int j = 0; j < 15; ++j) Cp[j] = br.C[j];
         } else {
-          target = br.n_entries >= a.max_entries ? -1 : predict<kMixed>(a, fld, br, pp, Cp, h);
+          target = br.n_entries >= a.max_entries ? -1 : predict<kMixed>(a, fld, face_r, br, pp, Cp, h);
         }
         if (target < 0) {  // the branch ends
           if (!have_best || better(br, *best)) {
