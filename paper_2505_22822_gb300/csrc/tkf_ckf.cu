@@ -180,24 +180,25 @@ __device__ int navigate(const CkfArgs& a, int cur, const double x[3], const doub
     const int nc = layer_candidates(a, uint32_t(cur_layer), x, cand);
     best = nearest_crossed(a, cand, nc, x, T, k, bend, sk, nskip + 1, best_s);
   }
-  double ls[kCkfMaxLayers];
-  for (uint32_t li = 0; li < a.n_layers; ++li) ls[li] = int(li) == cur_layer ? -1.0 : layer_path(a, li, x, T, face_r);
-  // layers in order of face path (ties: lower index first), as a repeated minimum search
-  double last_s = -1.0;
-  int last_li = -1;
-  for (uint32_t it = 0; it < a.n_layers; ++it) {
-    int pick = -1;
-    for (uint32_t li = 0; li < a.n_layers; ++li) {
-      const double s = ls[li];
-      if (!(s > 0.0)) continue;
-      const bool after = s > last_s || (s == last_s && int(li) > last_li);
-      if (!after) continue;
-      if (pick < 0 || s < ls[pick]) pick = int(li);
+  // the layers ahead in order of face path (ties: lower index first), by insertion as their
+  // paths are computed in index order
+  double vs[kCkfMaxLayers];
+  int vl[kCkfMaxLayers];
+  int nv = 0;
+  for (uint32_t li = 0; li < a.n_layers; ++li) {
+    const double s = int(li) == cur_layer ? -1.0 : layer_path(a, li, x, T, face_r);
+    if (!(s > 0.0)) continue;
+    int pos = nv++;
+    for (; pos > 0 && vs[pos - 1] > s; --pos) {
+      vs[pos] = vs[pos - 1];
+      vl[pos] = vl[pos - 1];
     }
-    if (pick < 0) break;
-    const double sl = ls[pick];
-    last_s = sl;
-    last_li = pick;
+    vs[pos] = s;
+    vl[pos] = int(li);
+  }
+  for (int j = 0; j < nv; ++j) {
+    const int pick = vl[j];
+    const double sl = vs[j];
     if (best >= 0 && sl > best_s + 20.0) break;
     const double h = 0.5 * sl * sl;
     const double q[3] = {x[0] + sl * T[0] + h * k[0], x[1] + sl * T[1] + h * k[1], x[2] + sl * T[2] + h * k[2]};
