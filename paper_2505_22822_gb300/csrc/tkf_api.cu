@@ -623,7 +623,7 @@ tkf_status tkf_find_tracks(tkf_context ctx, tkf_geometry geo, tkf_field field, c
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(ctx, TKF_ERR_DEVICE, std::string(fn) + ": cudaSetDevice failed");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const size_t need = tkf::ckf_workspace_bytes(in->n_seeds, co->beam);
+  const size_t need = tkf::ckf_workspace_bytes(in->n_seeds, co->beam, in->n_meas);
   if (need > ctx->ckf_ws_bytes) {
     cudaError_t e = cudaStreamSynchronize(st);  // the old store may still be in use
     if (e != cudaSuccess) return cuda_fail(ctx, e, (std::string(fn) + ": stream synchronize").c_str());

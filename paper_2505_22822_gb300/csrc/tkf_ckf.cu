@@ -427,6 +427,13 @@ __global__ void ckf_order_scatter_kernel(const double* __restrict__ seed_par, ui
     perm[atomicAdd(&hist[direction_bin(seed_par, n, i)], 1u)] = i;
 }
 
+__global__ void ckf_meas_f32_kernel(const double* __restrict__ loc0, const double* __restrict__ loc1,
+                                    const double* __restrict__ v00, const double* __restrict__ v11, uint32_t n,
+                                    float4* __restrict__ out) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = make_float4(float(loc0[i]), float(loc1[i]), float(v00[i]), float(v11[i]));
+}
+
 template <bool kMixed, class F>
 __global__ void __launch_bounds__(kCkfBlock) find_tracks_kernel(const CkfArgs a, const F fld) {
   __shared__ double face_r[kCkfMaxLayers];
@@ -487,7 +494,18 @@ __global__ void __launch_bounds__(kCkfBlock) find_tracks_kernel(const CkfArgs a,
         // whose residual fails the gate in one coordinate alone is skipped before the full chi2.
         // The margin keeps the skip exact under rounding (the full test would reject it too).
         const double gate = a.chi2_max * (1.0 + 1e-6);
+        // the same bound first in FP32, on FP32 copies of the measurements: it skips only where
+        // the rounding of every FP32 operand (at most 1e-6 of |loc| + |p| + |r| in the residual,
+        // 1e-4 of S) cannot bring the residual back inside the gate
+        const float p0f = d2f(pp[0]), p1f = d2f(pp[1]), c00f = d2f(Cp[S(0, 0)]), c11f = d2f(Cp[S(1, 1)]);
+        const float gatef = float(a.chi2_max) * 1.0001f;
         for (uint32_t mi = moff[target]; mi < m_end; ++mi) {
+          const float4 mf = a.meas_f[mi];  // loc0, loc1, V00, V11
+          const float r0f = mf.x - p0f, r1f = mf.y - p1f;
+          const float e0 = fabsf(r0f) - 1e-6f * (fabsf(mf.x) + fabsf(p0f) + fabsf(r0f));
+          const float e1 = fabsf(r1f) - 1e-6f * (fabsf(mf.y) + fabsf(p1f) + fabsf(r1f));
+          if ((e0 > 0.0f && e0 * e0 > gatef * (c00f + mf.z)) || (e1 > 0.0f && e1 * e1 > gatef * (c11f + mf.w)))
+            continue;
           const double q0 = a.loc0[mi] - pp[0], q1 = a.loc1[mi] - pp[1];
           if (q0 * q0 > gate * (Cp[S(0, 0)] + a.v00[mi]) || q1 * q1 > gate * (Cp[S(1, 1)] + a.v11[mi])) continue;
           double c2;
@@ -577,6 +595,14 @@ cudaError_t launch_ckf(const CkfArgs& a_in, const F& fld, cudaStream_t stream) {
   ckf_order_scan_kernel<<<1, kCkfOrderBins, 0, stream>>>(hist);
   ckf_order_scatter_kernel<<<og, 256, 0, stream>>>(a.seed_par, a.n_seeds, hist, perm);
   a.perm = perm;
+  // FP32 copies of the measurements for the gate's first bound (16-byte aligned after the order)
+  float4* mf = reinterpret_cast<float4*>(
+      base + ((sizeof(uint32_t) * (kCkfOrderBins + size_t(a.n_seeds)) + 15) & ~size_t(15)));
+  if (a.n_meas > 0) {
+    const unsigned mg = (a.n_meas + 255) / 256 < 4096 ? (a.n_meas + 255) / 256 : 4096;
+    ckf_meas_f32_kernel<<<mg, 256, 0, stream>>>(a.loc0, a.loc1, a.v00, a.v11, a.n_meas, mf);
+  }
+  a.meas_f = mf;
   if (a.mixed)
     find_tracks_kernel<true><<<(a.n_seeds + kCkfBlock - 1) / kCkfBlock, kCkfBlock, 0, stream>>>(a, fld);
   else
@@ -586,10 +612,10 @@ cudaError_t launch_ckf(const CkfArgs& a_in, const F& fld, cudaStream_t stream) {
 
 }  // namespace
 
-size_t ckf_workspace_bytes(uint32_t n_seeds, uint32_t beam) {
-  // branch slots, then the seed-order histogram and permutation
+size_t ckf_workspace_bytes(uint32_t n_seeds, uint32_t beam, uint32_t n_meas) {
+  // branch slots, the seed-order histogram and permutation, then FP32 copies of the measurements
   return size_t(n_seeds) * (beam * (kCkfChildren + 2) + 1) * sizeof(CkfBranch) +
-         sizeof(uint32_t) * (kCkfOrderBins + size_t(n_seeds));
+         ((sizeof(uint32_t) * (kCkfOrderBins + size_t(n_seeds)) + 15) & ~size_t(15)) + sizeof(float4) * size_t(n_meas);
 }
 
 cudaError_t launch_find_tracks(const CkfArgs& a, const FieldDev& f, cudaStream_t stream) {

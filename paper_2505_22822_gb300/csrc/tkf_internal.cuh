@@ -149,8 +149,9 @@ struct CkfArgs {
   int32_t* __restrict__ entry_meas;   // [max_entries][n_seeds]
   void* ws;                           // branch store, then the seed order
   const uint32_t* __restrict__ perm;  // seed found by each thread (set by the launch)
+  const float4* __restrict__ meas_f;  // FP32 loc0, loc1, V00, V11 (set by the launch)
 };
-size_t ckf_workspace_bytes(uint32_t n_seeds, uint32_t beam);
+size_t ckf_workspace_bytes(uint32_t n_seeds, uint32_t beam, uint32_t n_meas);
 cudaError_t launch_find_tracks(const CkfArgs& a, const FieldDev& f, cudaStream_t stream);
 
 // Launch shape of the persistent fit: threads per block, blocks in the grid, tracks a warp
