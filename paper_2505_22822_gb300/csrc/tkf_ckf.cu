@@ -127,18 +127,53 @@ __device__ __forceinline__ bool listed(const uint32_t* v, int n, uint32_t id) {
   return false;
 }
 
+// True when the parabola x + s T + s^2/2 k surely crosses the plane of a module (centre at x + d,
+// FP32 copies u, v, n of its frame) outside its half extents plus the helix margin: an FP32
+// evaluation whose every rounding is covered by `err` (below), so that the FP64 test of
+// nearest_crossed rejects the module too. Grazing incidence (|n.T| <= 0.05) and near-tangent
+// solutions (disc <= an^2 / 4) are left to FP64.
+__device__ __forceinline__ bool surely_outside(const float* __restrict__ f, const double d[3], const float Tf[3],
+                                               const float kf[3], float knorm, float bendf, double hu, double hv) {
+  const float uf[3] = {f[0], f[1], f[2]}, vf[3] = {f[3], f[4], f[5]}, nf[3] = {f[6], f[7], f[8]};
+  const float df[3] = {d2f(d[0]), d2f(d[1]), d2f(d[2])};
+  const float an = dotr(nf, Tf);
+  if (!(fabsf(an) > 0.05f)) return false;
+  const float dist = dotr(nf, df), bn = dotr(nf, kf);
+  const float disc = an * an + 2.0f * bn * dist;
+  if (!(disc > 0.25f * an * an)) return false;
+  const float sf = 2.0f * dist / (an + copysignf(sqrtf(disc), an));
+  if (!isfinite(sf)) return false;
+  const float as = fabsf(sf), h = 0.5f * sf * sf;
+  const float q[3] = {-df[0] + sf * Tf[0] + h * kf[0], -df[1] + sf * Tf[1] + h * kf[1], -df[2] + sf * Tf[2] + h * kf[2]};
+  const float dn = fabsf(df[0]) + fabsf(df[1]) + fabsf(df[2]), qn = fabsf(q[0]) + fabsf(q[1]) + fabsf(q[2]);
+  // error of s: relative 1e-5 plus the propagated rounding of dist (through an and disc), then
+  // that of q (d, the products, the sums) and of the projections
+  const float rs = 1e-5f + 2e-6f * fabsf(bn) * dn / (an * an);
+  const float ds = rs * as + 1e-5f * dn / fabsf(an);
+  const float err = 1e-3f + ds * (1.0f + (as + ds) * knorm) + 1e-6f * (dn + qn);
+  const float sup = (as + ds) * 1.00001f;
+  const float margin = (1.0f + sup * sup * sup * bendf * bendf / 6.0f) * 1.00001f;
+  return fabsf(dotr(uf, q)) - err > float(hu) + margin || fabsf(dotr(vf, q)) - err > float(hv) + margin;
+}
+
 // nearest of `cand` crossed by the parabola x + s T + s^2/2 k within bounds and margin
 __device__ int nearest_crossed(const CkfArgs& a, const uint32_t* cand, int nc, const double x[3], const double T[3],
                                const double k[3], double bend, const uint32_t* skip, int nskip, double& s_out) {
   int best = -1;
   double best_s = 0.0;
+  const float Tf[3] = {d2f(T[0]), d2f(T[1]), d2f(T[2])}, kf[3] = {d2f(k[0]), d2f(k[1]), d2f(k[2])};
+  const float knorm = (fabsf(kf[0]) + fabsf(kf[1]) + fabsf(kf[2])) * 1.00001f, bendf = d2f(bend) * 1.00001f;
   for (int j = 0; j < nc; ++j) {
     const uint32_t id = cand[j];
     if (id >= a.n_surf || listed(skip, nskip, id)) continue;
     const double* rec = a.surf + size_t(id) * kSurfStride;
-    const double u[3] = {rec[0], rec[1], rec[2]}, v[3] = {rec[3], rec[4], rec[5]};
-    const double n[3] = {rec[6], rec[7], rec[8]}, c[3] = {rec[9], rec[10], rec[11]};
+    const double c[3] = {rec[9], rec[10], rec[11]};
     const double d[3] = {c[0] - x[0], c[1] - x[1], c[2] - x[2]};
+    double hu, hv;
+    module_half(a, id, hu, hv);
+    if (surely_outside(reinterpret_cast<const float*>(rec + 16), d, Tf, kf, knorm, bendf, hu, hv)) continue;
+    const double u[3] = {rec[0], rec[1], rec[2]}, v[3] = {rec[3], rec[4], rec[5]};
+    const double n[3] = {rec[6], rec[7], rec[8]};
     const double dist = dot3(n, d), an = dot3(n, T), bn = dot3(n, k);
     if (an == 0.0) continue;
     double s = dist / an;
@@ -152,8 +187,6 @@ __device__ int nearest_crossed(const CkfArgs& a, const uint32_t* cand, int nc, c
     const double q[3] = {x[0] + s * T[0] + h * k[0] - c[0], x[1] + s * T[1] + h * k[1] - c[1],
                          x[2] + s * T[2] + h * k[2] - c[2]};
     const double margin = 1.0 + s * s * s * bend * bend / 6.0;
-    double hu, hv;
-    module_half(a, id, hu, hv);
     if (fabs(dot3(u, q)) > hu + margin || fabs(dot3(v, q)) > hv + margin) continue;
     // crossings within 1e-6 mm of each other (coplanar overlapping modules): the lower id
     if (best < 0 || s < best_s - 1e-6 || (fabs(s - best_s) <= 1e-6 && id < uint32_t(best))) {
