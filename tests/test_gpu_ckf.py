@@ -266,3 +266,17 @@ def test_ckf_events_batched_in_one_launch(ctx):
             sm = s["meas"][j][:q]
             np.testing.assert_array_equal(em[k + j][:q], np.where(sm >= 0, sm + bases[e], -1))
         k += n
+
+
+@pytest.mark.parametrize("precision", [tkf.FP64, tkf.MIXED])
+def test_ckf_dense_event_full_size(ctx, precision):
+    """A bench-density event (18,000 pions, ~150 measurements a module on the inner layer):
+    the candidates of every seed against the oracle's, in both precisions (the FP32 screens of
+    the gate and of the module crossings skip only what the FP64 tests reject)."""
+    w = synth.barrel_workload(n_events=1, lo=18000, hi=18000, seed=2)
+    t, g = w.tracks, w.geometry
+    mc = synth.measurement_container(t, g.n)
+    seed_sid, par, cov, idx = _seeds(w)
+    gr = gpu_find(ctx, w, mc, seed_sid, par, cov, precision=precision)
+    orr = oracle_find(w, mc, seed_sid, par, cov)
+    compare(gr, orr, min_same=0.995, chi2_tol=1e-8 if precision == tkf.FP64 else 1e-3)
