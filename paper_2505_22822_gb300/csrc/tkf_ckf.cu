@@ -65,7 +65,7 @@ __device__ __forceinline__ void module_half(const CkfArgs& a, uint32_t id, doubl
 }
 
 // modules of layer li around the point q: phi bin and row (barrel) or ring (disk), +-1 each
-__device__ int layer_candidates(const CkfArgs& a, uint32_t li, const double q[3], uint32_t out[9]) {
+__device__ __noinline__ int layer_candidates(const CkfArgs& a, uint32_t li, const double q[3], uint32_t out[9]) {
   const double* l = a.layers + 8 * li;
   double phi = atan2(q[1], q[0]);
   if (phi < 0.0) phi += 2.0 * kPi;
@@ -157,7 +157,7 @@ __device__ __forceinline__ bool surely_outside(const float* __restrict__ f, cons
 }
 
 // nearest of `cand` crossed by the parabola x + s T + s^2/2 k within bounds and margin
-__device__ int nearest_crossed(const CkfArgs& a, const uint32_t* cand, int nc, const double x[3], const double T[3],
+__device__ __noinline__ int nearest_crossed(const CkfArgs& a, const uint32_t* cand, int nc, const double x[3], const double T[3],
                                const double k[3], double bend, const uint32_t* skip, int nskip, double& s_out) {
   int best = -1;
   double best_s = 0.0;
