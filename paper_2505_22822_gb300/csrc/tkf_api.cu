@@ -47,7 +47,6 @@ bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0
 
 // Host-buffer entry point: the batch is cut into at most kHostChunksMax chunks of at least
 // kHostChunkMinTracks tracks, whose copies overlap the fits of their neighbours.
-constexpr int kHostChunksMax = 6;
 constexpr size_t kHostChunkMinTracks = 65536;
 
 }  // namespace
@@ -89,7 +88,7 @@ void tkf_context_destroy(tkf_context ctx) {
   if (ctx->stage || ctx->ws || ctx->train_ws || ctx->graph_exec || ctx->h2d_stream || ctx->ckf_ws) {
     DeviceGuard g(ctx->device);
     tkf::release_graph(ctx);
-    for (int c = 0; c < 8; ++c) {
+    for (int c = 0; c < kHostChunksMax; ++c) {
       if (ctx->chunk_in[c]) cudaEventDestroy(ctx->chunk_in[c]);
       if (ctx->chunk_fit[c]) cudaEventDestroy(ctx->chunk_fit[c]);
     }

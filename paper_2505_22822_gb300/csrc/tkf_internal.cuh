@@ -194,6 +194,9 @@ cudaError_t launch_fit(const FitArgs& a, const FieldDev& field, int precision, c
 
 }  // namespace tkf
 
+// chunks of the host-buffer pipeline (tkf_fit_host) at most
+constexpr int kHostChunksMax = 4;
+
 struct tkf_context_s;
 
 namespace tkf {
@@ -230,7 +233,7 @@ struct tkf_context_s {
   std::string graph_key, pending_key;
   // host-buffer entry point: copy streams and events of its chunk pipeline (created on first use)
   cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr, fit2_stream = nullptr;
-  cudaEvent_t chunk_in[8] = {}, chunk_fit[8] = {};
+  cudaEvent_t chunk_in[kHostChunksMax] = {}, chunk_fit[kHostChunksMax] = {};
   // fit workspace (ordering scratch), grown on demand and reused by later calls
   void* ws = nullptr;
   size_t ws_bytes = 0;
