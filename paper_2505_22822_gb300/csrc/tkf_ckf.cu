@@ -5,8 +5,8 @@
 // One thread per seed: the fit's RKN propagation, material and gain-matrix update; FP64
 // throughout, or (kMixed) with the propagation, material and covariance transport in FP32
 // around FP64 anchors as in the fit's mixed path (navigation, gate and update stay FP64). Each thread keeps its beam of branches, their children and its best ended branch in
-// a workspace slot of global memory (a branch: state, covariance, counters and up to 32 entries,
-// 464 bytes); the branches are read and written once per step, the geometry, layer tables and
+// a workspace slot of global memory (a branch: state, direction, covariance, counters and up to 32
+// entries, 496 bytes); the branches are read and written once per step, the geometry, layer tables and
 // measurements are gathered through L1/L2.
 
 #include "tkf_fit_impl.cuh"
@@ -22,7 +22,8 @@ constexpr int kCkfBlock = 128;
 constexpr uint32_t kCkfMaxSteps = 100;
 
 struct CkfBranch {
-  double p[5];
+  double p[5];     // l0, l1, (angle increments, 0 between steps), q/p
+  double dir[4];   // filtered direction: sin phi, cos phi, sin theta, cos theta
   double C[15];
   double h_ctrl, chi2;
   uint32_t n_meas, holes, n_entries, order;
@@ -44,6 +45,7 @@ __device__ __forceinline__ bool better(const CkfBranch& a, const CkfBranch& b) {
 
 __device__ __forceinline__ void copy_branch(CkfBranch& d, const CkfBranch& s, uint32_t n_entries) {
   for (int j = 0; j < 5; ++j) d.p[j] = s.p[j];
+  for (int j = 0; j < 4; ++j) d.dir[j] = s.dir[j];
   for (int j = 0; j < 15; ++j) d.C[j] = s.C[j];
   d.h_ctrl = s.h_ctrl;
   d.chi2 = s.chi2;
@@ -250,13 +252,10 @@ __device__ int navigate(const CkfArgs& a, int cur, const double x[3], const doub
 // covariance transport to the next module; returns its id (-1: none ahead, or stopped).
 template <bool kMixed, class F>
 __device__ int predict(const CkfArgs& a, const F& fld, const double* face_r, const CkfBranch& br, double pp[5],
-                       double Cp[15],
-                       double& h_ctrl) {
+                       double pdir[4], double Cp[15], double& h_ctrl) {
   Surf sc;
   load_surf(a.surf, uint32_t(br.sid), sc);
-  double sph, cph, sth, cth;
-  sincos(br.p[2], &sph, &cph);
-  sincos(br.p[3], &sth, &cth);
+  const double sph = br.dir[0], cph = br.dir[1], sth = br.dir[2], cth = br.dir[3];
   const double T0[3] = {sth * cph, sth * sph, cth};
   double lam = br.p[4], th0sq;
   if constexpr (kMixed) {
@@ -320,8 +319,12 @@ __device__ int predict(const CkfArgs& a, const F& fld, const double* face_r, con
       }
       pp[0] = dot3(s.u, d);
       pp[1] = dot3(s.v, d);
-      pp[2] = atan2(tn[1], tn[0]);
-      pp[3] = acos(tn[2]);
+      pp[2] = 0.0;  // the angles as the predicted direction (increments from here on)
+      pp[3] = 0.0;
+      pdir[0] = sp2;
+      pdir[1] = cp2;
+      pdir[2] = st2;
+      pdir[3] = ct2;
       pp[4] = lam;
       float Cf[15];
       for (int j = 0; j < 15; ++j) Cf[j] = d2f(br.C[j]);
@@ -365,8 +368,12 @@ __device__ int predict(const CkfArgs& a, const F& fld, const double* face_r, con
       }
       pp[0] = dot3(s.u, d);
       pp[1] = dot3(s.v, d);
-      pp[2] = atan2(tn[1], tn[0]);
-      pp[3] = acos(tn[2]);
+      pp[2] = 0.0;  // the angles as the predicted direction (increments from here on)
+      pp[3] = 0.0;
+      pdir[0] = sp2;
+      pdir[1] = cp2;
+      pdir[2] = st2;
+      pdir[3] = ct2;
       pp[4] = lam;
       for (int j = 0; j < 15; ++j) Cp[j] = br.C[j];
       Cp[S(2, 2)] += th0sq / (sth * sth);
@@ -489,6 +496,10 @@ __global__ void __launch_bounds__(kCkfBlock) find_tracks_kernel(const CkfArgs a,
   if (seed_sid < a.n_surf && ev < a.n_events) {
     CkfBranch& b0 = act[0];
     for (int j = 0; j < 5; ++j) b0.p[j] = a.seed_par[size_t(j) * n + i];
+    sincos(b0.p[2], &b0.dir[0], &b0.dir[1]);
+    sincos(b0.p[3], &b0.dir[2], &b0.dir[3]);
+    b0.p[2] = 0.0;
+    b0.p[3] = 0.0;
     for (int j = 0; j < 15; ++j) b0.C[j] = a.seed_cov[size_t(j) * n + i];
     b0.h_ctrl = a.opt.h_max;
     b0.chi2 = 0.0;
@@ -502,14 +513,15 @@ __global__ void __launch_bounds__(kCkfBlock) find_tracks_kernel(const CkfArgs a,
       uint32_t n_kids = 0;
       for (uint32_t bi = 0; bi < n_act; ++bi) {
         const CkfBranch& br = act[bi];
-        double pp[5], Cp[15], h = br.h_ctrl;
+        double pp[5], pdir[4], Cp[15], h = br.h_ctrl;
         int target;
         if (first) {
           target = int(seed_sid);
           for (int j = 0; j < 5; ++j) pp[j] = br.p[j];
+          for (int j = 0; j < 4; ++j) pdir[j] = br.dir[j];
           for (int j = 0; j < 15; ++j) Cp[j] = br.C[j];
         } else {
-          target = br.n_entries >= a.max_entries ? -1 : predict<kMixed>(a, fld, face_r, br, pp, Cp, h);
+          target = br.n_entries >= a.max_entries ? -1 : predict<kMixed>(a, fld, face_r, br, pp, pdir, Cp, h);
         }
         if (target < 0) {  // the branch ends
           if (!have_best || better(br, *best)) {
@@ -563,6 +575,16 @@ __global__ void __launch_bounds__(kCkfBlock) find_tracks_kernel(const CkfArgs a,
           const uint32_t mi = km[q];
           double c2;
           update(ch.p, ch.C, a.loc0[mi], a.loc1[mi], a.v00[mi], a.v01[mi], a.v11[mi], c2);
+          // filtered direction: the predicted one turned by the update's angle increments
+          double sd, cd, se, ce;
+          small_sincos(ch.p[2], sd, cd);
+          small_sincos(ch.p[3], se, ce);
+          ch.dir[0] = pdir[0] * cd + pdir[1] * sd;
+          ch.dir[1] = pdir[1] * cd - pdir[0] * sd;
+          ch.dir[2] = pdir[2] * ce + pdir[3] * se;
+          ch.dir[3] = pdir[3] * ce - pdir[2] * se;
+          ch.p[2] = 0.0;
+          ch.p[3] = 0.0;
           ch.h_ctrl = h;
           ch.chi2 += c2;
           ch.n_meas += 1;
@@ -577,6 +599,7 @@ __global__ void __launch_bounds__(kCkfBlock) find_tracks_kernel(const CkfArgs a,
           CkfBranch& ch = kids[n_kids++];
           copy_branch(ch, br, br.n_entries);
           for (int j = 0; j < 5; ++j) ch.p[j] = pp[j];
+          for (int j = 0; j < 4; ++j) ch.dir[j] = pdir[j];
           for (int j = 0; j < 15; ++j) ch.C[j] = Cp[j];
           ch.h_ctrl = h;
           ch.holes += 1;
