@@ -10,6 +10,7 @@ import paper_2505_22822_gb300 as tkf
 import synth
 from oracle import mlp
 from tests import parity
+from tests.test_gpu_parity import MIXED_TOL_CHI2, MIXED_TOL_SIGMA, TOL64, check, check_mixed, mixed_deviation
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -109,25 +110,51 @@ def test_records_are_sane_and_training_converges(trained):
     assert losses[-1] < 0.3 * losses[0]
 
 
+def _subset(o, idx):
+    return oracle.FitResult(*(getattr(o, f)[idx] for f in ("par", "cov", "chi2", "ndf", "status", "steps", "cov_filt0")))
+
+
 @pytest.mark.parametrize("precision", [tkf.MIXED, tkf.FP64])
 def test_learned_fit_matches_the_oracle_with_the_same_proposals(ctx, trained, precision):
+    """Every track against the oracle running the same network. The proposals are integers on a
+    1/32 grid of ln h decided in FP32 on both sides; the tensor cores' accumulation order may put
+    an output that lies within rounding of a grid boundary on the other side of it (both
+    proposals are then valid, one grid step apart). Tracks whose proposal equals the oracle's are
+    held to the plain parity rule of their precision (FP64: 1e-10 with the step-sequence and
+    conditioning rules of `check`; mixed: 1e-3 sigma); a track whose proposal differs starts from
+    another valid step and is held to the mixed-path tolerance."""
     fld, _, theta, _ = trained
     wbf = mlp.to_bf16(theta)
     m = tkf.Mlp(ctx, wbf)
     w = synth.solenoid_muon_workload(3000, seed=3, fld=fld)
-    res = _fit(ctx, w, tkf.Options(precision=precision, step_mode=tkf.STEP_LEARNED, mlp=m))
+    t = w.tracks
+    opts = tkf.Options(precision=precision, step_mode=tkf.STEP_LEARNED, mlp=m)
+    res = _fit(ctx, w, opts)
     g = parity.gpu_to_track_major(res)
-    o = oracle.fit(w.geometry.table, oracle.field_from(w.field), oracle.Options(mlp=wbf), w.tracks.offsets,
-                   w.tracks.meas, w.tracks.sid, w.tracks.seed_par, w.tracks.seed_cov, n_threads=8)
-    assert np.mean(g["status"] == o.status) > 0.999
-    good = (o.status == 0) & (g["status"] == 0)
-    C = oracle.unpack(o.cov[good])
-    sig = np.sqrt(np.einsum("nii->ni", C))
-    dp = g["par"][good] - o.par[good]
-    dp[:, 2] = (dp[:, 2] + np.pi) % (2 * np.pi) - np.pi
-    ds = (np.abs(dp) / sig).max(1)
-    tol = 1e-3 if precision == tkf.MIXED else 1e-8
-    assert np.mean(ds > tol) < 2e-3, (np.quantile(ds, [0.5, 0.99, 1.0]))
+    oopts = oracle.Options(mlp=wbf)
+    o = oracle.fit(w.geometry.table, oracle.field_from(w.field), oopts, t.offsets,
+                   t.meas, t.sid, t.seed_par, t.seed_cov, n_threads=8)
+    geo = tkf.Geometry.from_table(ctx, w.geometry.table)
+    f = tkf.Field.from_desc(ctx, w.field)
+    b = tkf.Batch.from_arrays(t.offsets, t.meas, t.sid, t.seed_par, t.seed_cov).to("cuda:0")
+    h_gpu = tkf.propose_start(ctx, geo, f, b, opts).cpu().numpy().astype(np.float64)
+    h_orc = oracle.propose_start(w.geometry.table, oracle.field_from(w.field), oopts, t.offsets, t.sid,
+                                 t.seed_par, t.n_hits)
+    same_prop = np.abs(np.log(h_gpu / h_orc)) * 32.0 < 1e-3
+    print({"tracks": t.n_tracks, "other_proposal": int((~same_prop).sum())})
+    assert np.mean(~same_prop) <= 1e-3
+    np.testing.assert_array_equal(g["status"], o.status)
+    idx = np.flatnonzero(same_prop)
+    gs = {k: (v[idx] if v is not None else None) for k, v in g.items()}
+    os_ = _subset(o, idx)
+    if precision == tkf.FP64:
+        check(gs, os_, TOL64, w=w, tracks=idx,
+              sensitivity=lambda js: np.array([parity.self_sensitivity(w, int(k), opts=oopts) for k in js]))
+    else:
+        check_mixed(gs, os_)
+    other = ~same_prop & ((o.status & 0x39F) == 0)
+    ds, dchi = mixed_deviation(g, o, other)
+    assert ds.max(initial=0) <= MIXED_TOL_SIGMA and dchi.max(initial=0) <= MIXED_TOL_CHI2
 
 
 @pytest.mark.parametrize("precision", [tkf.MIXED, tkf.FP64])
