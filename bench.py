@@ -91,7 +91,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="the default launch shape instead of the tuned one")
     ap.add_argument("--shape", default=None,
                     help="fixed launch shape 'threads,blocks_per_sm,tracks_per_warp,registers[,lanes]' for every "
-                         "variant (registers 128 or 64 apply to the mixed variants; FP64 keeps 255; lanes 1 or 4)")
+                         "variant (registers 128 or 64 apply to FP64 and mixed, 128 to mixed_fp32; lanes 1 or 4)")
     ap.add_argument("--no-seeds", action="store_true",
                     help="skip the seed-estimation kernel, the chain from estimated seeds and track finding")
     ap.add_argument("--streams", action="store_true",
@@ -716,8 +716,7 @@ def main():
         if args.shape:
             th, bps, tpw, regs, *lanes = (int(x) for x in args.shape.split(","))
             opts.block_threads, opts.blocks_per_sm, opts.tracks_per_warp = th, bps, tpw
-            opts.max_registers = (255 if base == "fp64" or two_filter or (base == "mixed_fp32" and regs == 64)
-                                  else regs)
+            opts.max_registers = 255 if two_filter or (base == "mixed_fp32" and regs == 64) else regs
             opts.lanes_per_track = lanes[0] if lanes and base != "mixed_fp32" and not two_filter else 0
         if variant.endswith("learned"):
             opts.step_mode, opts.mlp = tkf.STEP_LEARNED, proposer

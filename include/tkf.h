@@ -180,9 +180,10 @@ typedef struct tkf_fit_options {
    * (32, 64, 128 or 256) and blocks_per_sm (1..32) fix the persistent kernel's block shape
    * when both are nonzero (with the full register file unless max_registers says otherwise);
    * tracks_per_warp (1..32) fixes how many tracks a warp takes at a time, one per lane, when
-   * nonzero; max_registers (255, or 128 / 64 for TKF_MIXED without record capture, blocks of
-   * at most 128 threads) picks the kernel variant capped at that many registers a thread,
-   * which keeps part of the per-track state in local memory and holds more warps per SM. With
+   * nonzero; max_registers (255, or 128 / 64 for TKF_FP64 and TKF_MIXED and 128 for
+   * TKF_MIXED_FP32, without record capture, blocks of at most 128 threads) picks the kernel
+   * variant capped at that many registers a thread, which keeps part of the per-track state in
+   * local memory (at 128 the smoother state in shared memory) and holds more warps per SM. With
    * all four 0 the shape is the tuned one of this launch class when TKF_FIT_AUTOTUNE is set,
    * else FP64: 128 threads x 2 blocks per SM, 255 registers; mixed: 128 x 4, 128 registers;
    * 32 tracks per warp. An explicit part disables tuning; the other parts take defaults. */
@@ -234,8 +235,8 @@ typedef struct tkf_fit_options {
 
 /* Autotuning: the first call of a launch class (precision, step mode, field kind, batch size
  * rounded down to a power of two, SM count) times every candidate launch shape on the call's
- * own inputs (six block shapes at 255 registers, and for the mixed path three each at 128 and
- * 64 registers; below one track per lane of every resident warp also 16, 8 and 4 tracks per
+ * own inputs (six block shapes at 255 registers, and for the FP64 and mixed paths three each at
+ * 128 and 64 registers; below one track per lane of every resident warp also 16, 8 and 4 tracks per
  * warp; each candidate runs the whole fit into the call's outputs, then the call runs with the
  * fastest shape) and keeps the winner in the context. The call synchronizes its stream while
  * tuning. If the environment variable TKF_AUTOTUNE_CACHE names a file when the context is
@@ -566,13 +567,16 @@ tkf_status tkf_propose_start(tkf_context ctx, tkf_geometry geo, tkf_field field,
  * loads the library until the process exits.
  *   - Batches are limited to TKF_NOALLOC_MAX_TRACKS tracks; a larger n_tracks returns
  *     TKF_ERR_INVALID_ARG with a message, and nothing is enqueued.
- *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- *     once for that device; make that first call before any stream capture.
+ *   - tkf_context_create looks up the array's device address on the context's device
+ *     (cudaGetSymbolAddress) and keeps it in the context; the calls themselves look up nothing.
  *   - Every call on a device shares the one array: calls whose work overlaps on the GPU
  *     (different streams, or different contexts, without ordering) race and give wrong
  *     results. Serialize them.
- *   - It ignores the flags TKF_FIT_AUTOTUNE and TKF_FIT_GRAPH (both allocate); an explicit
- *     launch shape is used.
+ *   - It ignores the flags TKF_FIT_AUTOTUNE and TKF_FIT_GRAPH (both allocate); it launches with
+ *     the shape tkf_fit uses without tuning (the explicit one of the options, else the default).
+ *   - Learned step mode (TKF_STEP_LEARNED) returns TKF_ERR_UNSUPPORTED: it needs a per-track
+ *     starting step, for which the static scratch has no room.
+ *   - TKF_ERR_DEVICE if the array's address was not found when the context was created.
  * Arguments, outputs and the other errors are those of tkf_fit. */
 #define TKF_NOALLOC_MAX_TRACKS 2097152u
 tkf_status tkf_fit_noalloc(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf_fit_options* opts,

@@ -24,7 +24,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _ROOT = os.path.dirname(_HERE)
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "libtkf.so")
-_SOURCES = ["tkf_api.cu", "tkf_order.cu", "tkf_policy.cu", "tkf_fit_fp64.cu", "tkf_fit_mixed.cu",
+_SOURCES = ["tkf_api.cu", "tkf_order.cu", "tkf_policy.cu", "tkf_fit_fp64.cu", "tkf_fit_fp64_r128.cu",
+            "tkf_fit_fp64_r64.cu", "tkf_fit_mixed.cu",
             "tkf_fit_mixed_r128.cu", "tkf_fit_mixed_r64.cu", "tkf_fit_mixed32.cu", "tkf_mlp.cu", "tkf_seed.cu",
             "tkf_fit_group.cu", "tkf_ckf.cu", "tkf_fit_two_filter.cu", "tkf_fit_two_filter_mixed.cu",
             "tkf_fit_two_filter_mixed32.cu"]

@@ -5,7 +5,6 @@
 #include <stdio.h>
 #include <string.h>
 
-#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -45,6 +44,10 @@ struct DeviceGuard {
 
 bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
 
+// Device address of the allocation-free entry point's static scratch on the current device
+// (defined with the array, at the end of this file).
+cudaError_t noalloc_scratch_address(void** out);
+
 // Host-buffer entry point: the batch is cut into at most kHostChunksMax chunks of at least
 // kHostChunkMinTracks tracks, whose copies overlap the fits of their neighbours.
 constexpr size_t kHostChunkMinTracks = 65536;
@@ -78,6 +81,16 @@ tkf_status tkf_context_create(int device, tkf_context* out) {
   if (!c) return fail(nullptr, TKF_ERR_OOM, "tkf_context_create: host allocation failed");
   c->device = device;
   c->sm_count = prop.multiProcessorCount;
+  {
+    // the allocation-free entry point's scratch: its device address in this device's context
+    // (host code cannot use the array's name as a device address); a failure only disables
+    // tkf_fit_noalloc on this context
+    DeviceGuard g(device);
+    if (!g.ok || noalloc_scratch_address(&c->noalloc_scratch) != cudaSuccess) {
+      c->noalloc_scratch = nullptr;
+      cudaGetLastError();
+    }
+  }
   tkf::load_tune_cache(c);
   *out = c;
   return TKF_OK;
@@ -966,24 +979,9 @@ constexpr size_t kNoallocWords = 1 + 1024 + 2 * size_t(kNoallocMaxTracks) + 64;
 
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoallocWords];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mutex;
-void* g_noalloc_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on `device` (which must be current); looked up once per
-// device. Host code cannot use the array's name as a device address.
-cudaError_t noalloc_scratch(int device, void** out) {
-  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[device]) {
-    void* ptr = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_noalloc_ptr[device] = ptr;
-  }
-  *out = g_noalloc_ptr[device];
-  return cudaSuccess;
-}
+// Looked up by tkf_context_create, with the context's device current, and kept in the context
+// (a context is tied to one device; a new context after a device reset looks it up again).
+cudaError_t noalloc_scratch_address(void** out) { return cudaGetSymbolAddress(out, g_noalloc_scratch); }
 
 }  // namespace
 
@@ -996,33 +994,24 @@ extern "C" tkf_status tkf_fit_noalloc(tkf_context ctx, tkf_geometry geo, tkf_fie
                 "tkf_fit_noalloc: n_tracks " + std::to_string(in->n_tracks) + " exceeds the maximum " +
                     std::to_string(kNoallocMaxTracks) + " of the static scratch; use tkf_fit or split the batch");
   if (o->step_mode == TKF_STEP_LEARNED)
-    return fail(ctx, TKF_ERR_UNSUPPORTED, "tkf_fit_noalloc: learned step proposals are not available in this build");
+    return fail(ctx, TKF_ERR_UNSUPPORTED,
+                "tkf_fit_noalloc: learned step mode needs a per-track starting step, for which the static "
+                "scratch has no room; use tkf_fit");
+  if (!ctx->noalloc_scratch)
+    return fail(ctx, TKF_ERR_DEVICE, "tkf_fit_noalloc: the static scratch's device address was not found when "
+                                     "the context was created");
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(ctx, TKF_ERR_DEVICE, "tkf_fit_noalloc: cudaSetDevice failed");
-  void* scratch = nullptr;
-  cudaError_t e = noalloc_scratch(ctx->device, &scratch);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_noalloc: cudaGetSymbolAddress");
   tkf::FitArgs a = make_args(geo, o, in, out);
   // the launch clears the counter and histogram before use (the array keeps the last call's data)
-  tkf::Workspace ws = tkf::carve_workspace(scratch, in->n_tracks, false);
-  tkf::LaunchShape shape = tkf::default_launch_shape(o->precision, false, ctx->sm_count);
-  if (o->block_threads && o->blocks_per_sm) {
-    shape.threads = int(o->block_threads);
-    shape.blocks = int(o->blocks_per_sm) * ctx->sm_count;
-    shape.regs = 255;
-  }
-  if (o->lanes_per_track > 1) {
-    shape.group = int(o->lanes_per_track);
-    shape.regs = 255;
-    shape.tracks_per_warp = 32 / shape.group;
-  }
-  if (o->tracks_per_warp) shape.tracks_per_warp = int(o->tracks_per_warp);
-  if (o->max_registers) shape.regs = int(o->max_registers);
-  if (o->smoother == TKF_SMOOTHER_TWO_FILTER && !(o->block_threads && o->blocks_per_sm)) {
-    shape.threads = 128;  // the two-filter kernels run at 255 registers: two 128-thread blocks an SM
-    shape.blocks = 2 * ctx->sm_count;
-    shape.regs = 255;
-  }
+  tkf::Workspace ws = tkf::carve_workspace(ctx->noalloc_scratch, in->n_tracks, false);
+  // the launch shape of tkf_fit for these options, without tuning (tuning and graphs allocate)
+  tkf_fit_options untuned = *o;
+  untuned.flags &= ~uint32_t(TKF_FIT_AUTOTUNE);
+  tkf::LaunchShape shape;
+  cudaError_t e = tkf::resolve_shape(ctx, a, field->f, o->precision, ws, &untuned, static_cast<cudaStream_t>(stream),
+                                     &shape);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_noalloc: launch shape");
   e = tkf::launch_fit(a, field->f, o->precision, ws, shape, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_noalloc: launch");
   return TKF_OK;

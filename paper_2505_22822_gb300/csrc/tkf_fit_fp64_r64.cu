@@ -1,0 +1,12 @@
+// tkf_fit_fp64_r64.cu -- the FP64 persistent fit kernels capped at 64 registers a thread (a
+// translation unit of their own, so that the variants compile in parallel).
+#include "tkf_fit_impl.cuh"
+
+namespace tkf {
+
+cudaError_t launch_fit_fp64_r64(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm,
+                                uint32_t* counter, LaunchShape shape, cudaStream_t stream) {
+  return launch_fields<0, 64>(a, f, mode, perm, counter, shape, stream);
+}
+
+}  // namespace tkf

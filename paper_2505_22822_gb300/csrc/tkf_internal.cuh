@@ -168,6 +168,10 @@ struct LaunchShape {
 // Persistent fit launches per precision; mode 0 plain, 1 learned proposals, 2 record capture.
 cudaError_t launch_fit_fp64(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm, uint32_t* counter,
                             LaunchShape shape, cudaStream_t stream);
+cudaError_t launch_fit_fp64_r128(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm,
+                                 uint32_t* counter, LaunchShape shape, cudaStream_t stream);
+cudaError_t launch_fit_fp64_r64(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm,
+                                uint32_t* counter, LaunchShape shape, cudaStream_t stream);
 cudaError_t launch_fit_mixed(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm, uint32_t* counter,
                              LaunchShape shape, cudaStream_t stream);
 cudaError_t launch_fit_mixed_r128(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm,
@@ -246,6 +250,8 @@ struct tkf_context_s {
   // branch store of track finding
   void* ckf_ws = nullptr;
   size_t ckf_ws_bytes = 0;
+  // device address of tkf_fit_noalloc's static scratch on this context's device (NULL: not found)
+  void* noalloc_scratch = nullptr;
 };
 
 struct tkf_geometry_s {

@@ -20,10 +20,10 @@ namespace {
 
 // Candidates: (threads per block, blocks per SM, registers a thread). With 255 registers an SM
 // holds 8 warps: the first four shapes fill it, the next two use half of it (less contention
-// for the FP64 pipe and the L1 per warp). The mixed path also has kernels capped at 128 and 64
-// registers (16 and 32 warps an SM, part of the per-track state in local memory): more warps
-// hide more of the latency between its FP64 and FP32 phases, at the cost of spill traffic, and
-// which balance wins depends on the field and the tracks.
+// for the FP64 pipe and the L1 per warp). The FP64 and mixed paths also have kernels capped at
+// 128 and 64 registers (16 and 32 warps an SM, part of the per-track state in local memory, the
+// smoother state in shared memory at 128): more warps hide more latency, at the cost of spill
+// traffic, and which balance wins depends on the precision, the field and the tracks.
 struct Candidate {
   int threads, blocks_per_sm, regs;
 };
@@ -56,7 +56,7 @@ bool has_group(int precision, bool record, int group) {
 // Register caps the kernels of a precision exist at.
 bool has_regs(int precision, int regs) {
   if (regs == 255) return true;
-  if (precision == TKF_MIXED) return regs == 128 || regs == 64;
+  if (precision == TKF_MIXED || precision == TKF_FP64) return regs == 128 || regs == 64;
   if (precision == TKF_MIXED_FP32) return regs == 128;
   return false;
 }
