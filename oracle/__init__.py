@@ -94,6 +94,9 @@ def lib():
         L.orc_fit.argtypes = [vp, u32, ctypes.POINTER(OField), ctypes.POINTER(OOpts), u32, ctypes.c_uint64,
                               vp, vp, vp,
                               vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int]
+        L.orc_fit_all_states.restype = ctypes.c_int
+        L.orc_fit_all_states.argtypes = [vp, u32, ctypes.POINTER(OField), ctypes.POINTER(OOpts), u32, ctypes.c_uint64,
+                                         vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int]
         L.orc_field_at.argtypes = [ctypes.POINTER(OField), vp, u32, vp, vp]
         L.orc_rkn_fixed.argtypes = [ctypes.POINTER(OField), vp, vp, d, d, u32, vp, vp, vp]
         L.orc_rkn_step.argtypes = [ctypes.POINTER(OField), vp, vp, d, d, vp, vp, vp]
@@ -169,11 +172,16 @@ class FitResult:
     status: np.ndarray
     steps: np.ndarray
     cov_filt0: np.ndarray
+    states_par: np.ndarray | None = None       # [n_meas, 5] smoothed parameters of every entry
+    states_cov: np.ndarray | None = None       # [n_meas, 15] smoothed covariances (packed)
+    states_cov_filt: np.ndarray | None = None  # [n_meas, 15] filtered covariances (packed)
 
 
 def fit(surfaces: np.ndarray, fld: OField, opts: Options, offsets, meas, sid, seed_par, seed_cov,
-        n_threads: int = 1) -> FitResult:
-    """Fits every track. ``meas`` [m, 5], ``seed_par`` [n, 5], ``seed_cov`` [n, 15] (packed)."""
+        n_threads: int = 1, states: bool = False) -> FitResult:
+    """Fits every track. ``meas`` [m, 5], ``seed_par`` [n, 5], ``seed_cov`` [n, 15] (packed).
+    With ``states`` the result also holds every entry's smoothed state and filtered covariance
+    (NaN for tracks with a fatal status)."""
     L = lib()
     s = surfaces14(surfaces)
     offsets = np.ascontiguousarray(offsets, dtype=np.uint32)
@@ -186,10 +194,17 @@ def fit(surfaces: np.ndarray, fld: OField, opts: Options, offsets, meas, sid, se
     status, steps = np.zeros(n, np.uint32), np.zeros((n, 2), np.uint32)
     cf0 = np.zeros((n, 15))
     o = opts._c()
-    L.orc_fit(_p(s), s.shape[0], ctypes.byref(fld), ctypes.byref(o), n, meas.shape[0], _p(offsets), _p(meas),
-              _p(sid), _p(seed_par), _p(seed_cov), _p(par), _p(cov), _p(chi2), _p(ndf), _p(status),
-              _p(steps), _p(cf0), int(n_threads))
-    return FitResult(par, cov, chi2, ndf, status, steps, cf0)
+    if not states:
+        L.orc_fit(_p(s), s.shape[0], ctypes.byref(fld), ctypes.byref(o), n, meas.shape[0], _p(offsets), _p(meas),
+                  _p(sid), _p(seed_par), _p(seed_cov), _p(par), _p(cov), _p(chi2), _p(ndf), _p(status),
+                  _p(steps), _p(cf0), int(n_threads))
+        return FitResult(par, cov, chi2, ndf, status, steps, cf0)
+    m = meas.shape[0]
+    sp, sc, scf = np.zeros((m, 5)), np.zeros((m, 15)), np.zeros((m, 15))
+    L.orc_fit_all_states(_p(s), s.shape[0], ctypes.byref(fld), ctypes.byref(o), n, m, _p(offsets), _p(meas), _p(sid),
+                     _p(seed_par), _p(seed_cov), _p(par), _p(cov), _p(chi2), _p(ndf), _p(status), _p(steps), _p(cf0),
+                     _p(sp), _p(sc), _p(scf), int(n_threads))
+    return FitResult(par, cov, chi2, ndf, status, steps, cf0, sp, sc, scf)
 
 
 def fit_tracks(workload, opts: Options | None = None, n_threads: int = 1, tracks=None) -> FitResult:

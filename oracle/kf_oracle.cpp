@@ -1447,19 +1447,26 @@ static std::vector<Surface> to_surfaces(const double* s, uint32_t n) {
 // seed_cov [n][15] packed upper triangle; outputs in the same AoS layouts.
 // steps (nullable): [n][2] = step attempts, rejected attempts. cov_filt0 (nullable): [n][15]
 // filtered covariance at the first surface. n_threads >= 1.
-int orc_fit(const double* surfaces, uint32_t n_surf, const orc_field* field, const orc_opts* opts,
-            uint32_t n_tracks, uint64_t n_meas, const uint32_t* offsets, const double* meas, const uint32_t* sid,
-            const double* seed_par, const double* seed_cov, double* out_par, double* out_cov, double* chi2,
-            int32_t* ndf, uint32_t* status, uint32_t* steps, double* cov_filt0, int n_threads) {
+// Fits every track; with `states_par` [n_meas][5] and `states_cov`, `states_cov_filt`
+// [n_meas][15] (packed) not NULL it also writes every entry's smoothed state and filtered
+// covariance (rows indexed like the measurements; NaN for a track whose status is fatal).
+static int fit_batch(const double* surfaces, uint32_t n_surf, const orc_field* field, const orc_opts* opts,
+                     uint32_t n_tracks, uint64_t n_meas, const uint32_t* offsets, const double* meas,
+                     const uint32_t* sid, const double* seed_par, const double* seed_cov, double* out_par,
+                     double* out_cov, double* chi2, int32_t* ndf, uint32_t* status, uint32_t* steps,
+                     double* cov_filt0, double* states_par, double* states_cov, double* states_cov_filt,
+                     int n_threads) {
   std::vector<Surface> surf = to_surfaces(surfaces, n_surf);
   Field F = to_field(field);
   Mlp mlp_store;
   Opts O = to_opts(opts, &mlp_store);
+  const bool want_states = states_par && states_cov && states_cov_filt;
   auto work = [&](uint32_t lo, uint32_t hi) {
     for (uint32_t i = lo; i < hi; ++i) {
       TrackIn in;
       uint32_t a = offsets[i], b = offsets[i + 1];
       TrackOut out;
+      States keep;
       if (b < a || b > n_meas) {
         fill_nan(out);
         for (int j = 0; j < 15; ++j) out.cov_filt0[j] = std::nan("");
@@ -1472,7 +1479,20 @@ int orc_fit(const double* surfaces, uint32_t n_surf, const orc_field* field, con
         in.sid = sid + a;
         in.seed_par = seed_par + 5 * size_t(i);
         in.seed_cov = seed_cov + 15 * size_t(i);
-        fit_track(surf.data(), n_surf, F, O, in, out);
+        fit_track(surf.data(), n_surf, F, O, in, out, want_states ? &keep : nullptr);
+        if (want_states) {
+          const bool ok = !(out.status & kFatal) && !keep.ps.empty();
+          for (uint32_t k = 0; k < b - a; ++k) {
+            const size_t e = size_t(a) + k;
+            for (int j = 0; j < 5; ++j) states_par[5 * e + j] = ok ? keep.ps[5 * k + j] : std::nan("");
+            if (ok) {
+              pack_cov(&keep.Cs[25 * k], states_cov + 15 * e);
+              pack_cov(&keep.Cf[25 * k], states_cov_filt + 15 * e);
+            } else {
+              for (int j = 0; j < 15; ++j) states_cov[15 * e + j] = states_cov_filt[15 * e + j] = std::nan("");
+            }
+          }
+        }
       }
       std::memcpy(out_par + 5 * size_t(i), out.par, sizeof(double) * 5);
       std::memcpy(out_cov + 15 * size_t(i), out.cov, sizeof(double) * 15);
@@ -1498,6 +1518,25 @@ int orc_fit(const double* surfaces, uint32_t n_surf, const orc_field* field, con
   }
   for (auto& x : th) x.join();
   return 0;
+}
+
+int orc_fit(const double* surfaces, uint32_t n_surf, const orc_field* field, const orc_opts* opts,
+            uint32_t n_tracks, uint64_t n_meas, const uint32_t* offsets, const double* meas, const uint32_t* sid,
+            const double* seed_par, const double* seed_cov, double* out_par, double* out_cov, double* chi2,
+            int32_t* ndf, uint32_t* status, uint32_t* steps, double* cov_filt0, int n_threads) {
+  return fit_batch(surfaces, n_surf, field, opts, n_tracks, n_meas, offsets, meas, sid, seed_par, seed_cov, out_par,
+                   out_cov, chi2, ndf, status, steps, cov_filt0, nullptr, nullptr, nullptr, n_threads);
+}
+
+// orc_fit that also writes the smoothed state (and the filtered covariance) of every entry.
+int orc_fit_all_states(const double* surfaces, uint32_t n_surf, const orc_field* field, const orc_opts* opts,
+                   uint32_t n_tracks, uint64_t n_meas, const uint32_t* offsets, const double* meas,
+                   const uint32_t* sid, const double* seed_par, const double* seed_cov, double* out_par,
+                   double* out_cov, double* chi2, int32_t* ndf, uint32_t* status, uint32_t* steps,
+                   double* cov_filt0, double* states_par, double* states_cov, double* states_cov_filt,
+                   int n_threads) {
+  return fit_batch(surfaces, n_surf, field, opts, n_tracks, n_meas, offsets, meas, sid, seed_par, seed_cov, out_par,
+                   out_cov, chi2, ndf, status, steps, cov_filt0, states_par, states_cov, states_cov_filt, n_threads);
 }
 
 // ---- component entry points used by the oracle's own pins

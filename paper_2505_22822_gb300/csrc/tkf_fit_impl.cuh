@@ -232,6 +232,10 @@ __device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.0f + _
 
 // Step modes: plain adaptive control, learned proposals, or plain control with record capture.
 constexpr int kPlain = 0, kLearned = 1, kRecord = 2;
+// kStates: plain adaptive stepping that also stores every entry's filtered state (into the
+// caller's all-states arrays) and predicted state with its transport Jacobian (into the
+// workspace), for the backward RTS pass of tkf_states.cu.
+constexpr int kStates = 3;
 
 // Where learned proposals and training records go during one track's propagation.
 struct StepLearn {
@@ -1098,6 +1102,41 @@ __device__ __forceinline__ uint32_t combine_with_seed(const FitArgs& a, uint32_t
   return 0;
 }
 
+// ---- all-states mode: the forward pass stores what the backward RTS pass needs.
+// Filtered state of entry m into the all-states arrays (SoA [5][n_meas], [15][n_meas]); at
+// the first entry p holds the angles, later the direction is carried as sines and cosines.
+template <class U>
+__device__ __forceinline__ void store_filtered(const FitArgs& a, uint32_t m, const double p[5], const U C[15],
+                                               bool first, double sph, double cph, double sth, double cth) {
+  const size_t nm = size_t(a.n_meas);
+  a.states_par[m] = p[0];
+  a.states_par[nm + m] = p[1];
+  a.states_par[2 * nm + m] = first ? p[2] : atan2(sph, cph);
+  a.states_par[3 * nm + m] = first ? p[3] : atan2(sth, cth);
+  a.states_par[4 * nm + m] = p[4];
+#pragma unroll
+  for (int j = 0; j < 15; ++j) a.states_cov[size_t(j) * nm + m] = cov_to_d(C[j]);
+}
+
+// Predicted state, packed covariance and transport Jacobian (row-major) of entry m into the
+// workspace: 45 doubles an entry, entry-major (kStatesScratch).
+template <class U>
+__device__ __forceinline__ void store_predicted(const FitArgs& a, uint32_t m, const double p[5], const U C[15],
+                                                const U J[5][5], double sp2, double cp2, double st2, double ct2) {
+  double* w = a.states_scratch + size_t(m) * kStatesScratch;
+  w[0] = p[0];
+  w[1] = p[1];
+  w[2] = atan2(sp2, cp2);
+  w[3] = atan2(st2, ct2);
+  w[4] = p[4];
+#pragma unroll
+  for (int j = 0; j < 15; ++j) w[5 + j] = cov_to_d(C[j]);
+#pragma unroll
+  for (int r = 0; r < 5; ++r)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) w[20 + 5 * r + c] = cov_to_d(J[r][c]);
+}
+
 template <int kPrec, int kMode, int kG, int kPlace, int kSmooth, class F>
 __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
                           SmootherStore<kPlace, typename CovType<kPrec>::type> st, uint32_t gl = 0,
@@ -1105,6 +1144,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
   constexpr bool kMixed = kPrec != 0;
   static_assert(kG == 1 || kMode != kRecord, "record capture runs one lane per track");
   static_assert(kSmooth == 0 || (kG == 1 && kMode != kRecord), "the two-filter smoother runs one lane a track");
+  static_assert(kMode != kStates || (kG == 1 && kSmooth == 0), "all-states output: one lane a track, RTS");
   const bool writer = kG == 1 || gl == 0;  // the lane that writes the group's results
   using U = typename CovType<kPrec>::type;
   const uint32_t n = a.stride;  // SoA row stride of seeds and outputs
@@ -1363,6 +1403,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
         status |= arrival_material<kPrec>(a, s, sp2, cp2, st2, ct2, p, C);
         if (status & kFatal) break;
       }
+      if constexpr (kMode == kStates) store_predicted(a, m, p, C, J, sp2, cp2, st2, ct2);
       // ---- smoother: R = P J^T (in place; J row 4 is e_4)
       if constexpr (kSmooth == 1) {
       } else if constexpr (kG == 1) {
@@ -1496,6 +1537,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
         }
       }
     }
+    if constexpr (kMode == kStates) store_filtered(a, m, p, C, k == 0, sph, cph, sth, cth);
     sp = s;
   }
   }  // passes
@@ -1922,7 +1964,8 @@ cudaError_t launch_persistent(const FitArgs& a, const F& fld, const uint32_t* pe
   return cudaGetLastError();
 }
 
-// Record capture (training only) is built with the full register file and one lane a track.
+// Record capture (training only) and the all-states mode are built with the full register file
+// and one lane a track.
 template <int kPrec, int kRegs, int kG, int kSmooth, class F>
 cudaError_t launch_mode(const FitArgs& a, const F& fld, int mode, const uint32_t* perm, uint32_t* counter,
                         LaunchShape shape, cudaStream_t stream) {
@@ -1931,6 +1974,11 @@ cudaError_t launch_mode(const FitArgs& a, const F& fld, int mode, const uint32_t
   if (mode == kRecord) {
     if constexpr (kRegs == 255 && kPrec != 2 && kG == 1 && kSmooth == 0)
       return launch_persistent<kPrec, kRecord, kRegs, kG, kSmooth>(a, fld, perm, counter, shape, stream);
+    return cudaErrorInvalidValue;
+  }
+  if (mode == kStates) {  // all-states output: full register file, one lane a track, RTS
+    if constexpr (kRegs == 255 && kG == 1 && kSmooth == 0)
+      return launch_persistent<kPrec, kStates, kRegs, kG, kSmooth>(a, fld, perm, counter, shape, stream);
     return cudaErrorInvalidValue;
   }
   return launch_persistent<kPrec, kPlain, kRegs, kG, kSmooth>(a, fld, perm, counter, shape, stream);

@@ -79,7 +79,16 @@ struct FitArgs {
   uint32_t record_capacity;
   uint32_t* __restrict__ record_count;
   bool test_stall_proposals;  // test of the timeout path: the pre-pass issues no tensor-core work
+  // all-states output (or null): every entry's smoothed state, SoA [5][n_meas] and [15][n_meas];
+  // the forward pass writes the filtered states there first
+  double* __restrict__ states_par;
+  double* __restrict__ states_cov;
+  double* __restrict__ states_scratch;  // workspace: kStatesScratch doubles per entry
 };
+
+// Per entry for the backward RTS pass: predicted parameters (5), packed covariance (15) and the
+// transport Jacobian from the previous entry (25, row-major).
+constexpr int kStatesScratch = 45;
 
 constexpr int kMlpParams = TKF_MLP_PARAMS;
 constexpr int kMlpRecord = TKF_MLP_RECORD;
@@ -91,9 +100,12 @@ struct Workspace {
   uint32_t* keys = nullptr;
   uint32_t* perm = nullptr;
   float* h0 = nullptr;  // learned mode: per-track starting step size (only when space was reserved)
+  double* states = nullptr;  // all-states output: kStatesScratch doubles per entry (when reserved)
 };
-size_t workspace_bytes(uint32_t n_tracks, bool learned);
-Workspace carve_workspace(void* base, uint32_t n_tracks, bool learned);
+size_t workspace_bytes(uint32_t n_tracks, bool learned, uint64_t states_entries = 0);
+Workspace carve_workspace(void* base, uint32_t n_tracks, bool learned, uint64_t states_entries = 0);
+// Backward RTS pass of the all-states output (tkf_states.cu), after the fit on the same stream.
+cudaError_t launch_smooth_states(const FitArgs& a, cudaStream_t stream);
 cudaError_t launch_propose_start(const FitArgs& a, const FieldDev& f, float* h0, cudaStream_t stream);
 
 // Seed parameter estimation (tkf_seed.cu): one thread per track, outputs in the fit's seed layout.

@@ -67,11 +67,19 @@ __global__ void __launch_bounds__(256) order_scatter_kernel(const uint32_t* __re
 
 }  // namespace
 
-size_t workspace_bytes(uint32_t n_tracks, bool learned) {
-  return 256 + sizeof(uint32_t) * (kKeyBins + (learned ? 3 : 2) * size_t(n_tracks)) + 256;
+namespace {
+// bytes of the ordering scratch (and the learned mode's starting steps), rounded up to 256
+size_t order_bytes(uint32_t n_tracks, bool learned) {
+  const size_t b = 256 + sizeof(uint32_t) * (kKeyBins + (learned ? 3 : 2) * size_t(n_tracks)) + 256;
+  return (b + 255) / 256 * 256;
+}
+}  // namespace
+
+size_t workspace_bytes(uint32_t n_tracks, bool learned, uint64_t states_entries) {
+  return order_bytes(n_tracks, learned) + sizeof(double) * kStatesScratch * size_t(states_entries);
 }
 
-Workspace carve_workspace(void* base, uint32_t n_tracks, bool learned) {
+Workspace carve_workspace(void* base, uint32_t n_tracks, bool learned, uint64_t states_entries) {
   Workspace w;
   uint32_t* p = static_cast<uint32_t*>(base);
   w.counter = p;          // 1 word, followed directly by the histogram (one memset clears both)
@@ -79,6 +87,8 @@ Workspace carve_workspace(void* base, uint32_t n_tracks, bool learned) {
   w.keys = p + 1 + kKeyBins;
   w.perm = w.keys + n_tracks;
   if (learned) w.h0 = reinterpret_cast<float*>(w.perm + n_tracks);
+  if (states_entries)
+    w.states = reinterpret_cast<double*>(static_cast<char*>(base) + order_bytes(n_tracks, learned));
   return w;
 }
 
@@ -94,8 +104,13 @@ cudaError_t launch_fit(const FitArgs& a, const FieldDev& f, int precision, const
   order_scatter_kernel<<<g256, 256, 0, stream>>>(ws.keys, n, ws.hist, ws.perm);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int mode = a.mlp ? 1 : (a.records ? 2 : 0);  // learned, record capture, or plain
+  // learned, record capture, all-states output, or plain
+  const int mode = a.mlp ? 1 : (a.records ? 2 : (a.states_par ? 3 : 0));
   FitArgs b = a;
+  if (mode == 3) {
+    if (!ws.states) return cudaErrorInvalidValue;
+    b.states_scratch = ws.states;
+  }
   if (mode == 1) {  // network proposals of each track's starting step size
     if (!ws.h0) return cudaErrorInvalidValue;
     e = launch_propose_start(a, f, ws.h0, stream);
@@ -110,7 +125,8 @@ cudaError_t launch_fit(const FitArgs& a, const FieldDev& f, int precision, const
       : precision == TKF_MIXED_FP32 ? launch_fit_mixed32(b, f, mode, ws.perm, ws.counter, shape, stream)
                                     : launch_fit_fp64(b, f, mode, ws.perm, ws.counter, shape, stream);
   if (e != cudaSuccess) return e;
-  if (timing) e = cudaEventRecord(timing[1], stream);
+  if (timing && (e = cudaEventRecord(timing[1], stream)) != cudaSuccess) return e;
+  if (mode == 3) e = launch_smooth_states(b, stream);  // backward RTS over the stored states
   return e;
 }
 

@@ -162,7 +162,7 @@ def test_graph_and_autotune_with_learned_proposals(setup):
 @pytest.mark.parametrize("kw", [dict(block_threads=96, blocks_per_sm=1), dict(block_threads=128, blocks_per_sm=0),
                                 dict(block_threads=0, blocks_per_sm=2), dict(block_threads=512, blocks_per_sm=1),
                                 dict(block_threads=64, blocks_per_sm=33), dict(tracks_per_warp=33),
-                                dict(max_registers=100, precision=tkf.MIXED), dict(max_registers=64),
+                                dict(max_registers=100, precision=tkf.MIXED), dict(max_registers=64, precision=tkf.MIXED_FP32),
                                 dict(max_registers=128, precision=tkf.MIXED, block_threads=256, blocks_per_sm=1)])
 def test_bad_block_shapes_are_rejected(setup, kw):
     ctx, geo, fld, b, _ = setup

@@ -476,3 +476,38 @@ def test_zero_field_no_material_fit_is_the_weighted_least_squares_line():
     print(worst)
     assert worst[1.0] < 1e-2 and worst[0.1] < 1e-3 and worst[1e-3] < 1e-5
     assert 0.05 < worst[0.1] / worst[1.0] < 0.2 and 0.005 < worst[1e-3] / worst[0.1] < 0.02
+
+
+# ------------------------------------------------------------------ every entry's smoothed state
+def test_noise_free_tracks_fit_back_to_truth_at_every_entry(n_threads):
+    """The smoothed state of every entry (the backward RTS pass over stored states) of
+    noise-free tracks with energy loss and 20 % entries without a measurement sits on the true
+    trajectory: local positions at every surface within 1e-7 mm of the simulation's."""
+    w = synth.barrel_workload(n_events=1, lo=400, hi=400, seed=23, mass=synth.MUON_MASS, ms=0,
+                              sigma_hit=0.0, seed_smear=0, p_hole=0.2)
+    t = w.tracks
+    r = oracle.fit(w.geometry.table, oracle.field_from(w.field), oracle.Options(tol=1e-9), t.offsets, t.meas,
+                   t.sid, t.seed_par, t.seed_cov, n_threads=n_threads, states=True)
+    assert np.all(r.status == 0)
+    assert np.max(np.abs(r.states_par[:, :2] - t.hit_truth)) < 1e-7
+    # the first entry's state is the first-surface result
+    np.testing.assert_array_equal(r.states_par[t.offsets[:-1]], r.par)
+
+
+def test_smoothed_positions_at_every_entry_have_unit_pulls(n_threads):
+    """Smeared muons in the solenoid map: the smoothed local positions at every surface, each
+    using every measurement of its track, have unit-normal pulls against the true crossing
+    points."""
+    w = synth.solenoid_muon_workload(20000, seed=13)
+    t = w.tracks
+    r = oracle.fit(w.geometry.table, oracle.field_from(w.field), oracle.Options(), t.offsets, t.meas, t.sid,
+                   t.seed_par, t.seed_cov, n_threads=n_threads, states=True)
+    ok_t = r.status == 0
+    assert ok_t.mean() > 0.999
+    ok = np.repeat(ok_t, np.diff(t.offsets.astype(np.int64)))
+    C = oracle.unpack(r.states_cov[ok])
+    sig = np.sqrt(np.einsum("nii->ni", C))[:, :2]
+    pull = (r.states_par[ok, :2] - t.hit_truth[ok]) / sig
+    print({"entries": int(ok.sum()), "mean": pull.mean(0), "std": pull.std(0)})
+    assert np.all(np.abs(pull.mean(0)) < 0.01)
+    assert np.all(np.abs(pull.std(0) - 1.0) < 0.015)
