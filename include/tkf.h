@@ -289,7 +289,24 @@ typedef struct tkf_fit_inputs {
  * the smoothed parameters and covariance on the surface of the first measurement; chi2 is
  * the sum over measurements of the predicted-residual chi2, the first one taken against the
  * seed; ndf = 2 * (number of measurements) (the seed enters as a prior). steps, if not NULL,
- * receives 2 x n counters: step attempts [0, n) and rejected attempts [n, 2n). */
+ * receives 2 x n counters: step attempts [0, n) and rejected attempts [n, 2n).
+ *
+ * Optional all-states output (paper Sec. 2: the smoother lets every state use every
+ * measurement): states_par (5 x n_meas) and states_cov (15 x n_meas, packed like cov), both
+ * NULL or both set, receive the smoothed parameters and covariance at EVERY entry of every
+ * track, in the measurements' indexing (entry k of track i at column offsets[i] + k; phi in
+ * (-pi, pi], angles at entries without a measurement too). They come from the
+ * Rauch-Tung-Striebel backward pass over stored filtered and predicted states and transport
+ * Jacobians (A_k = C_k|k J_{k+1}^T C_{k+1|k}^-1, Cholesky), FP64, in a second kernel after the
+ * fit; the context's workspace then also holds 360 bytes per measurement row. The entry-0 state
+ * equals par / cov up to rounding (par / cov come from the forward-evaluated smoother). Rows of
+ * a track whose status is fatal, or that has no measurement, are NaN; a predicted covariance that
+ * is not positive definite in the backward pass sets TKF_TRACK_SMOOTHER_NOT_SPD (and NaN outputs)
+ * as it does in the textbook smoother. Requires TKF_STEP_ADAPTIVE without record capture, the
+ * RTS smoother and tkf_fit (not tkf_fit_host or tkf_fit_noalloc); it launches with the default
+ * block shape at 255 registers and one lane a track (TKF_FIT_AUTOTUNE and the explicit shape
+ * options other than block_threads / blocks_per_sm are ignored; TKF_ERR_UNSUPPORTED otherwise).
+ * NULL keeps the default path, unchanged and as fast. */
 typedef struct tkf_fit_outputs {
   double* par;
   double* cov;
@@ -297,6 +314,8 @@ typedef struct tkf_fit_outputs {
   int32_t* ndf;
   uint32_t* status;
   uint32_t* steps;
+  double* states_par;
+  double* states_cov;
 } tkf_fit_outputs;
 
 /* Fits every track of the batch, asynchronously on `stream` (a cudaStream_t; NULL is the

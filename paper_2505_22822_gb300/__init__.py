@@ -28,7 +28,7 @@ _SOURCES = ["tkf_api.cu", "tkf_order.cu", "tkf_policy.cu", "tkf_fit_fp64.cu", "t
             "tkf_fit_fp64_r64.cu", "tkf_fit_mixed.cu",
             "tkf_fit_mixed_r128.cu", "tkf_fit_mixed_r64.cu", "tkf_fit_mixed32.cu", "tkf_mlp.cu", "tkf_seed.cu",
             "tkf_fit_group.cu", "tkf_ckf.cu", "tkf_fit_two_filter.cu", "tkf_fit_two_filter_mixed.cu",
-            "tkf_fit_two_filter_mixed32.cu"]
+            "tkf_fit_two_filter_mixed32.cu", "tkf_states.cu"]
 _lib = None
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
@@ -141,7 +141,8 @@ class FitInputs(ctypes.Structure):
 
 class FitOutputs(ctypes.Structure):
     _fields_ = [("par", ctypes.c_void_p), ("cov", ctypes.c_void_p), ("chi2", ctypes.c_void_p),
-                ("ndf", ctypes.c_void_p), ("status", ctypes.c_void_p), ("steps", ctypes.c_void_p)]
+                ("ndf", ctypes.c_void_p), ("status", ctypes.c_void_p), ("steps", ctypes.c_void_p),
+                ("states_par", ctypes.c_void_p), ("states_cov", ctypes.c_void_p)]
 
 
 class SeedOutputs(ctypes.Structure):
@@ -497,35 +498,45 @@ class Result:
     ndf: object      # [n]
     status: object   # [n]
     steps: object    # [2, n] or None
+    states_par: object = None  # [5, n_meas]: every entry's smoothed parameters, or None
+    states_cov: object = None  # [15, n_meas]: every entry's smoothed covariance (packed), or None
 
 
-def alloc_outputs(n: int, device, steps: bool = True) -> Result:
+def alloc_outputs(n: int, device, steps: bool = True, states_meas: int | None = None) -> Result:
+    """Output tensors for n tracks; with ``states_meas`` also the all-states arrays for that many
+    measurement rows."""
     import torch
     kw = dict(device=device)
+    st = states_meas is not None
     return Result(torch.empty((5, n), dtype=torch.float64, **kw),
                   torch.empty((15, n), dtype=torch.float64, **kw),
                   torch.empty((n,), dtype=torch.float64, **kw),
                   torch.empty((n,), dtype=torch.int32, **kw),
                   torch.empty((n,), dtype=torch.int32, **kw),
-                  torch.empty((2, n), dtype=torch.int32, **kw) if steps else None)
+                  torch.empty((2, n), dtype=torch.int32, **kw) if steps else None,
+                  torch.empty((5, states_meas), dtype=torch.float64, **kw) if st else None,
+                  torch.empty((15, states_meas), dtype=torch.float64, **kw) if st else None)
 
 
 def _outputs_struct(r: Result) -> FitOutputs:
     s = FitOutputs()
     s.par, s.cov, s.chi2 = _ptr(r.par), _ptr(r.cov), _ptr(r.chi2)
     s.ndf, s.status, s.steps = _ptr(r.ndf), _ptr(r.status), _ptr(r.steps)
+    s.states_par, s.states_cov = _ptr(r.states_par), _ptr(r.states_cov)
     return s
 
 
 def fit(ctx: Context, geo: Geometry, field: Field, batch: Batch, opts: Options | None = None,
-        out: Result | None = None, stream=None, steps: bool = True) -> Result:
+        out: Result | None = None, stream=None, steps: bool = True, states: bool = False) -> Result:
     """Enqueues the fit of a batch of CUDA tensors on ``stream`` (default: torch's current
-    stream) and returns the output tensors (valid once the stream reaches the work)."""
+    stream) and returns the output tensors (valid once the stream reaches the work). With
+    ``states`` the result also holds every entry's smoothed state (``states_par``,
+    ``states_cov``)."""
     import torch
     dev = batch.offsets.device
     if dev.type != "cuda":
         raise TkfError("fit() needs CUDA tensors; use fit_host() for host arrays")
-    out = out or alloc_outputs(batch.n_tracks, dev, steps)
+    out = out or alloc_outputs(batch.n_tracks, dev, steps, batch.n_meas if states else None)
     if stream is None:
         stream = torch.cuda.current_stream(dev)
     o = (opts or Options()).c()

@@ -450,6 +450,15 @@ static tkf_status check_common(tkf_context ctx, tkf_geometry geo, tkf_field fiel
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": NULL required pointer");
   if (out && (!out->par || !out->cov || !out->chi2 || !out->ndf || !out->status))
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": NULL required pointer");
+  if (out && (!out->states_par != !out->states_cov))
+    return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": states_par and states_cov must both be set or both NULL");
+  if (out && out->states_par &&
+      (o->step_mode != TKF_STEP_ADAPTIVE || o->records || o->smoother != TKF_SMOOTHER_RTS))
+    return fail(ctx, TKF_ERR_UNSUPPORTED,
+                std::string(fn) + ": the all-states output needs TKF_STEP_ADAPTIVE without record capture and the "
+                                  "RTS smoother");
+  if (out && (!aligned8(out->states_par) || !aligned8(out->states_cov)))
+    return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": states pointer not 8-byte aligned");
   if (in->n_meas > 0 && (!in->loc0 || !in->loc1 || !in->v00 || !in->v01 || !in->v11 || !in->sid))
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": NULL measurement pointer");
   const void* ptrs[] = {in->loc0, in->loc1, in->v00, in->v01, in->v11, in->seed_par, in->seed_cov,
@@ -484,6 +493,8 @@ static tkf::FitArgs make_args(tkf_geometry geo, const tkf_fit_options* o, const 
     a.ndf = out->ndf;
     a.status = out->status;
     a.steps = out->steps;
+    a.states_par = out->states_par;
+    a.states_cov = out->states_cov;
   }
   a.surf = geo->d_surf;
   a.n_surf = geo->n;
@@ -513,7 +524,8 @@ static tkf::FitArgs make_args(tkf_geometry geo, const tkf_fit_options* o, const 
 static tkf_status fit_enqueue(tkf_context ctx, tkf_field field, const tkf_fit_options* o, const tkf::FitArgs& a,
                               cudaStream_t st, bool allow_graph, const char* fn) {
   const bool learned = o->step_mode == TKF_STEP_LEARNED;
-  const size_t need = tkf::workspace_bytes(a.n_tracks, learned);
+  const uint64_t states = a.states_par ? a.n_meas : 0;  // rows of the all-states scratch
+  const size_t need = tkf::workspace_bytes(a.n_tracks, learned, states);
   if (need > ctx->ws_bytes) {
     // the old workspace may still be in use by earlier work on this context's stream
     cudaError_t e = cudaStreamSynchronize(st);
@@ -525,7 +537,7 @@ static tkf_status fit_enqueue(tkf_context ctx, tkf_field field, const tkf_fit_op
     if (e != cudaSuccess) return cuda_fail(ctx, e, (std::string(fn) + ": workspace cudaMalloc").c_str());
     ctx->ws_bytes = need;
   }
-  tkf::Workspace ws = tkf::carve_workspace(ctx->ws, a.n_tracks, learned);
+  tkf::Workspace ws = tkf::carve_workspace(ctx->ws, a.n_tracks, learned, states);
   tkf::LaunchShape shape;
   cudaError_t e = tkf::resolve_shape(ctx, a, field->f, o->precision, ws, o, st, &shape);
   if (e != cudaSuccess) return cuda_fail(ctx, e, (std::string(fn) + ": autotune").c_str());
@@ -689,6 +701,8 @@ tkf_status tkf_find_tracks(tkf_context ctx, tkf_geometry geo, tkf_field field, c
 tkf_status tkf_fit_host(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf_fit_options* o,
                         const tkf_fit_inputs* hin, const tkf_fit_outputs* hout, void* stream) {
   tkf_status s = check_common(ctx, geo, field, o, hin, hout, "tkf_fit_host");
+  if (s == TKF_OK && hout->states_par)
+    return fail(ctx, TKF_ERR_UNSUPPORTED, "tkf_fit_host: the all-states output is available through tkf_fit");
   if (s != TKF_OK || hin->n_tracks == 0) return s;
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(ctx, TKF_ERR_DEVICE, "tkf_fit_host: cudaSetDevice failed");
@@ -988,6 +1002,8 @@ cudaError_t noalloc_scratch_address(void** out) { return cudaGetSymbolAddress(ou
 extern "C" tkf_status tkf_fit_noalloc(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf_fit_options* o,
                                       const tkf_fit_inputs* in, const tkf_fit_outputs* out, void* stream) {
   tkf_status s = check_common(ctx, geo, field, o, in, out, "tkf_fit_noalloc");
+  if (s == TKF_OK && out->states_par)
+    return fail(ctx, TKF_ERR_UNSUPPORTED, "tkf_fit_noalloc: the all-states output needs workspace; use tkf_fit");
   if (s != TKF_OK || in->n_tracks == 0) return s;
   if (in->n_tracks > kNoallocMaxTracks)
     return fail(ctx, TKF_ERR_INVALID_ARG,

@@ -66,7 +66,7 @@ int field_class(const FieldDev& f) {
   return (f.b[0] == 0.0 && f.b[1] == 0.0) ? 0 : 1;
 }
 
-int fit_mode(const FitArgs& a) { return a.mlp ? 1 : (a.records ? 2 : 0); }
+int fit_mode(const FitArgs& a) { return a.mlp ? 1 : (a.records ? 2 : (a.states_par ? 3 : 0)); }
 
 std::string tune_key(const FitArgs& a, const FieldDev& f, int precision, int sm_count) {
   static const char* kField[] = {"uz", "u", "grid"};
@@ -175,7 +175,8 @@ std::string graph_key(const FitArgs& a, const FieldDev& f, int precision, const 
   const void* ptrs[] = {a.offsets, a.loc0,   a.loc1,  a.v00,      a.v01,     a.v11,
                         a.sid,     a.seed_par, a.seed_cov, a.par,   a.cov,     a.chi2,
                         a.ndf,     a.status, a.steps, a.surf,     a.mlp,     a.records,
-                        a.record_count, ws.counter, ws.hist, ws.keys, ws.perm, ws.h0, f.grid};
+                        a.record_count, ws.counter, ws.hist, ws.keys, ws.perm, ws.h0, f.grid,
+                        a.states_par, a.states_cov, ws.states};
   for (const void* p : ptrs) k.put(p);
   k.put(a.n_surf);
   k.put(a.record_capacity);
@@ -251,7 +252,9 @@ bool valid_block_shape(uint32_t threads, uint32_t blocks_per_sm, uint32_t tracks
 
 cudaError_t resolve_shape(tkf_context ctx, const FitArgs& a, const FieldDev& f, int precision, const Workspace& ws,
                           const tkf_fit_options* o, cudaStream_t stream, LaunchShape* out) {
-  std::array<int, 5> shape = default_shape(precision, a.records != nullptr);
+  // record capture and the all-states output exist at 255 registers, one lane a track
+  const bool full_file = a.records != nullptr || a.states_par != nullptr;
+  std::array<int, 5> shape = default_shape(precision, full_file);
   const bool explicit_block = o->block_threads && o->blocks_per_sm;
   if (explicit_block) {
     shape[0] = int(o->block_threads);
@@ -266,6 +269,16 @@ cudaError_t resolve_shape(tkf_context ctx, const FitArgs& a, const FieldDev& f, 
   if (o->tracks_per_warp) shape[2] = int(o->tracks_per_warp);
   if (o->max_registers) shape[3] = int(o->max_registers);
   *out = make_shape(shape, ctx->sm_count);
+  if (a.states_par) {
+    if (!explicit_block) {
+      out->threads = 128;
+      out->blocks = 2 * ctx->sm_count;
+    }
+    out->regs = 255;
+    out->group = 1;
+    out->tracks_per_warp = 32;
+    return cudaSuccess;
+  }
   if (a.smoother == TKF_SMOOTHER_TWO_FILTER) {  // one kernel variant: 255 registers, one lane a track
     if (!explicit_block) {
       out->threads = 128;

@@ -142,3 +142,65 @@ def chain_self_sensitivity(w, tracks, scale: float = 100.0, trials: int = 32, se
         _, _, st = compare(g, base, np.inf)
         worst = np.where(same, np.maximum(worst, st["dev"]), worst)
     return worst
+
+
+def states_to_entry_major(res):
+    """The all-states output of a GPU result (SoA [5][n_meas], [15][n_meas]) -> entry-major numpy."""
+    def host(x):
+        return x.detach().cpu().numpy() if hasattr(x, "detach") else np.asarray(x)
+    return host(res.states_par).T.copy(), host(res.states_cov).T.copy()
+
+
+def compare_states(sp, sc, o: "oracle.FitResult", offsets):
+    """Every entry's smoothed state against the oracle's (`o` from oracle.fit(..., states=True)),
+    in the metric above with the entry's own filtered covariance as the covariance scale (the
+    backward pass at entry k subtracts terms of that size). Returns each track's largest
+    deviation (0 for tracks whose rows are NaN on both sides) and whether NaN rows agree."""
+    offsets = np.asarray(offsets, dtype=np.int64)
+    op, oc, ocf = o.states_par, o.states_cov, o.states_cov_filt
+    nan_g = np.isnan(sp).any(1)
+    nan_o = np.isnan(op).any(1)
+    C = unpack_safe(oc)
+    sig = np.sqrt(np.abs(np.einsum("nii->ni", C)))
+    dp = sp - op
+    dp[:, 2] = (dp[:, 2] + np.pi) % (2 * np.pi) - np.pi
+    rel_p = np.abs(dp) / np.maximum(np.abs(op), sig)
+    Cf = unpack_safe(ocf)
+    d0 = np.sqrt(np.abs(np.einsum("nii->ni", Cf)))
+    rel_c = np.abs(unpack_safe(sc) - C) / np.einsum("ni,nj->nij", d0, d0)
+    dev_e = np.maximum(rel_p.max(1), rel_c.reshape(len(sp), -1).max(1))
+    dev_e = np.where(nan_g & nan_o, 0.0, dev_e)
+    dev_e = np.where(nan_g != nan_o, np.inf, dev_e)
+    n = len(offsets) - 1
+    dev_t = np.zeros(n)
+    if len(dev_e):
+        idx = np.repeat(np.arange(n), np.diff(offsets))
+        np.maximum.at(dev_t, idx, np.nan_to_num(dev_e, nan=np.inf))
+    return dev_t, bool(np.array_equal(nan_g, nan_o))
+
+
+def unpack_safe(cov15):
+    return oracle.unpack(np.nan_to_num(cov15, nan=0.0)) if len(cov15) else np.zeros((0, 5, 5))
+
+
+def states_self_sensitivity(w, track: int, trials: int = 8, seed: int = 0, opts=None) -> float:
+    """`self_sensitivity` for every entry's smoothed state: how far the oracle's all-states
+    result of one track moves under one-ulp changes of its seed and measured positions."""
+    t = w.tracks
+    sub = t.subset(np.array([track]))
+    fo = oracle.field_from(w.field)
+    opts = opts or oracle.Options(mass=w.mass)
+    base = oracle.fit(w.geometry.table, fo, opts, sub.offsets, sub.meas, sub.sid, sub.seed_par, sub.seed_cov,
+                      states=True)
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    for _ in range(trials):
+        sp = sub.seed_par * (1 + rng.choice([-1.0, 1.0], size=sub.seed_par.shape) * 2.0 ** -52)
+        m = sub.meas.copy()
+        m[:, :2] *= 1 + rng.choice([-1.0, 1.0], size=m[:, :2].shape) * 2.0 ** -52
+        o = oracle.fit(w.geometry.table, fo, opts, sub.offsets, m, sub.sid, sp, sub.seed_cov, states=True)
+        if not np.array_equal(o.steps, base.steps):
+            continue
+        dev, _ = compare_states(o.states_par, o.states_cov, base, sub.offsets)
+        worst = max(worst, float(dev[0]))
+    return worst
