@@ -158,6 +158,11 @@ def compare_states(sp, sc, o: "oracle.FitResult", offsets):
     deviation (0 for tracks whose rows are NaN on both sides) and whether NaN rows agree."""
     offsets = np.asarray(offsets, dtype=np.int64)
     op, oc, ocf = o.states_par, o.states_cov, o.states_cov_filt
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return _compare_states(sp, sc, op, oc, ocf, offsets)
+
+
+def _compare_states(sp, sc, op, oc, ocf, offsets):
     nan_g = np.isnan(sp).any(1)
     nan_o = np.isnan(op).any(1)
     C = unpack_safe(oc)

@@ -143,7 +143,7 @@ def test_edge_tracks_rows(ctx, precision):
     print(dev)
     ok = (o.status & 0x39F) == 0
     if precision == tkf.FP64:
-        assert dev[ok].max() <= 1e-9  # track 1 of the edge set keeps two measurements (conditioning)
+        assert dev[ok].max() <= TOL64
     else:
         ds = _mixed_states_dev(sp, o, tr.offsets)
         assert ds.max() <= tol
