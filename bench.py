@@ -80,7 +80,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--variant", default="auto", choices=["auto", "fp64", "mixed_fp32", "mixed", "mixed_learned",
                                                           "fp64_two_filter", "mixed_two_filter",
-                                                          "mixed_fp32_two_filter"])
+                                                          "mixed_fp32_two_filter", "fp64_all_states",
+                                                          "mixed_all_states"])
     ap.add_argument("--events", type=int, default=50)
     ap.add_argument("--workload", default="barrel", choices=["barrel", "map"],
                     help="barrel: events in the barrel + endcap detector, uniform 2 T; map: 1e5 muons "
@@ -384,7 +385,9 @@ def ckf_stage(ctx, fld, w, stream, steps: int, warmup: int, events: int = 5, pre
 
 
 def cpu_baseline(w, max_seconds: float = 20.0):
-    """The CPU oracle as it stands on this host's cores, on a bounded sample of the workload."""
+    """The CPU oracle as it stands on this host's cores, on a bounded sample of the workload.
+    Returns the baseline line, the sample's track indices and the oracle's results for them
+    (which the accuracy table below compares the GPU variants with)."""
     import oracle
     t = w.tracks
     cores = os.cpu_count() or 1
@@ -394,14 +397,54 @@ def cpu_baseline(w, max_seconds: float = 20.0):
         idx = np.sort(rng.choice(t.n_tracks, size=min(n_try, t.n_tracks), replace=False))
         sub = t.subset(idx)
         t0 = time.perf_counter()
-        oracle.fit_tracks(w, tracks=sub, n_threads=cores)
+        res = oracle.fit_tracks(w, tracks=sub, n_threads=cores)
         dt = time.perf_counter() - t0
         if dt > 0.25 * max_seconds or n_try >= t.n_tracks:
             break
         n_try = int(min(t.n_tracks, n_try * max(2.0, 0.3 * max_seconds / max(dt, 1e-3))))
-    return {"value": len(idx) / dt, "unit": "tracks/s", "cores": cores, "kind": "oracle",
+    line = {"value": len(idx) / dt, "unit": "tracks/s", "cores": cores, "kind": "oracle",
             "sample": f"{len(idx)} tracks drawn uniformly from the {t.n_tracks}-track batch, "
                       f"fit in {dt:.2f} s on {cores} threads"}
+    return line, idx, res
+
+
+PARAMS = ("l0", "l1", "phi", "theta", "qop")
+MATCH_TOLS = (1e-4, 1e-3, 1e-2, 5e-2)
+
+
+def accuracy_vs_oracle(g: dict, o, idx) -> dict:
+    """One variant's fitted tracks (host arrays, track-major) against the FP64 oracle on the
+    sample `idx`: for each parameter the largest and the 99th-percentile |dp_i| / sigma_i (sigma
+    from the oracle's covariance; phi wrapped), the largest covariance error relative to
+    sqrt(C_ii C_jj), the largest relative chi2 difference, and the paper's Table-1 matching
+    ratios: the fraction of tracks with the oracle's status whose five parameters all lie within
+    the relative tolerance |dp_i| <= r |p_i| (r = 0.01 %, 0.1 %, 1 %, 5 %)."""
+    st_g, st_o = g["status"][idx], o.status
+    same_status = st_g == st_o
+    fitted = same_status & ((st_o & 0x39F) == 0)
+    iu = np.triu_indices(5)
+    C = np.zeros((len(idx), 5, 5))
+    C[:, iu[0], iu[1]] = o.cov
+    C[:, iu[1], iu[0]] = o.cov
+    sig = np.sqrt(np.abs(np.einsum("nii->ni", C)))
+    dp = g["par"][idx] - o.par
+    dp[:, 2] = (dp[:, 2] + np.pi) % (2 * np.pi) - np.pi
+    ds = np.abs(dp[fitted]) / sig[fitted]
+    Cg = np.zeros_like(C)
+    Cg[:, iu[0], iu[1]] = g["cov"][idx]
+    Cg[:, iu[1], iu[0]] = g["cov"][idx]
+    scale = np.einsum("ni,nj->nij", sig, sig)
+    dc = (np.abs(Cg - C) / scale)[fitted].reshape(int(fitted.sum()), -1)
+    dchi = np.abs(g["chi2"][idx] - o.chi2)[fitted] / np.maximum(np.abs(o.chi2[fitted]), 1.0)
+    rel = np.abs(dp) / np.maximum(np.abs(o.par), 1e-300)
+    out = {"tracks": int(len(idx)), "same_status": float(np.mean(same_status)),
+           "dp_over_sigma_max": {k: float(ds[:, i].max(initial=0)) for i, k in enumerate(PARAMS)},
+           "dp_over_sigma_p99": {k: float(np.quantile(ds[:, i], 0.99)) if len(ds) else 0.0
+                                 for i, k in enumerate(PARAMS)},
+           "cov_rel_max": float(dc.max(initial=0)), "chi2_rel_max": float(dchi.max(initial=0)),
+           "match_ratio": {f"{100 * r:g}%": float(np.mean(fitted & np.all(rel <= r, axis=1)))
+                           for r in MATCH_TOLS}}
+    return out
 
 
 def run_reference(args, ws, rank):
@@ -456,7 +499,7 @@ def setup_tune_cache() -> str:
 def tuned_shape(path: str, variant: str, n_tracks: int, field: str, disabled: bool):
     """[threads, blocks per SM, tracks per warp, registers, lanes a track] the autotuner chose
     for this class."""
-    if variant.endswith("_two_filter"):  # one kernel variant, not tuned
+    if variant.endswith("_two_filter") or variant.endswith("_all_states"):  # one kernel variant, not tuned
         return [128, 2, 32, 255, 1]
     if disabled:
         return [128, 2, 32, 255, 1] if variant in ("fp64", "mixed_fp32") else [128, 4, 32, 128, 1]
@@ -686,7 +729,9 @@ def main():
     dev = host.to(f"cuda:{local}")
     # the headline is the last: mixed + learned; mixed_fp32 is the experimental FP32 covariance algebra
     # *_two_filter: the optimal (two-filter) smoother instead of RTS
-    variants = (["fp64", "fp64_two_filter", "mixed_fp32", "mixed_two_filter", "mixed", "mixed_learned"]
+    # *_all_states: every entry's smoothed state too (backward RTS pass over stored states)
+    variants = (["fp64", "fp64_two_filter", "fp64_all_states", "mixed_fp32", "mixed_two_filter", "mixed_all_states",
+                 "mixed", "mixed_learned"]
                 if args.variant == "auto" else [args.variant])
     # a side stream: CUDA graphs cannot be captured on the legacy default stream
     stream = torch.cuda.Stream()
@@ -709,7 +754,8 @@ def main():
              if host.nbytes() < 2 * L2_BYTES else None)
     for variant in variants:
         two_filter = variant.endswith("_two_filter")
-        base = variant.replace("_two_filter", "")
+        all_states = variant.endswith("_all_states")
+        base = variant.replace("_two_filter", "").replace("_all_states", "")
         opts = tkf.Options(precision={"fp64": tkf.FP64, "mixed_fp32": tkf.MIXED_FP32}.get(base, tkf.MIXED),
                            mass=w.mass, smoother=tkf.SMOOTHER_TWO_FILTER if two_filter else tkf.SMOOTHER_RTS,
                            graph=not args.no_graph, autotune=not args.no_autotune and args.shape is None)
@@ -720,7 +766,7 @@ def main():
             opts.lanes_per_track = lanes[0] if lanes and base != "mixed_fp32" and not two_filter else 0
         if variant.endswith("learned"):
             opts.step_mode, opts.mlp = tkf.STEP_LEARNED, proposer
-        out = tkf.alloc_outputs(n_tracks, dev.offsets.device, steps=True)
+        out = tkf.alloc_outputs(n_tracks, dev.offsets.device, steps=True, states_meas=n_meas if all_states else None)
         # warm-up: the first call tunes the block shape, the second captures the graph
         for _ in range(args.warmup):
             tkf.fit(ctx, geo, fld, dev, opts, out=out, stream=stream)
@@ -769,7 +815,10 @@ def main():
             kms.append(kev[0].elapsed_time(kev[1]))
         kernel_ms = statistics.mean(kms)
         ms_max = max_over_ranks(ms, dist, f"cuda:{local}")
+        host_out = {"par": out.par.cpu().numpy().T.copy(), "cov": out.cov.cpu().numpy().T.copy(),
+                    "chi2": out.chi2.cpu().numpy(), "status": out.status.cpu().numpy().view(np.uint32)}
         results[variant] = {"ms": ms, "ms_max": ms_max, "kernel_ms": kernel_ms, "clocks": clk.summary(), "opts": opts,
+                            "host_out": host_out,
                             "shape": ([opts.block_threads, opts.blocks_per_sm, opts.tracks_per_warp, opts.max_registers,
                                        opts.lanes_per_track or 1]
                                       if args.shape else
@@ -894,7 +943,10 @@ def main():
     if e2e:
         line["e2e"] = e2e
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w)
+        line["cpu_baseline"], idx, ores = cpu_baseline(w)
+        # each variant's error against the FP64 oracle on the baseline's sample (the paper's
+        # CPU-GPU agreement study, Sec. 3.1, Table 1)
+        line["accuracy_vs_oracle"] = {k: accuracy_vs_oracle(v["host_out"], ores, idx) for k, v in results.items()}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

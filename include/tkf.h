@@ -531,10 +531,33 @@ tkf_status tkf_find_tracks(tkf_context ctx, tkf_geometry geo, tkf_field field, c
 #define TKF_MLP_RECORD 13
 #define TKF_MLP_PARAMS 5057
 
-/* Uploads BF16 weights (host, TKF_MLP_PARAMS 16-bit patterns) into a handle for
- * tkf_fit_options.mlp. Errors: TKF_ERR_INVALID_ARG, TKF_ERR_OOM, TKF_ERR_DEVICE. */
-tkf_status tkf_mlp_load(tkf_context ctx, const uint16_t* bf16_weights, tkf_mlp* out);
+/* Uploads BF16 weights (host, n = TKF_MLP_PARAMS 16-bit patterns) into a handle for
+ * tkf_fit_options.mlp. Errors: TKF_ERR_INVALID_ARG (NULL, n != TKF_MLP_PARAMS, a non-finite
+ * weight), TKF_ERR_OOM, TKF_ERR_DEVICE. */
+tkf_status tkf_mlp_load(tkf_context ctx, const uint16_t* bf16_weights, size_t n, tkf_mlp* out);
+/* The same from trained FP32 parameters (DEVICE, n = TKF_MLP_PARAMS): each is rounded to BF16
+ * (nearest, ties to even) by a kernel on `stream`; the call waits for it. Errors as
+ * tkf_mlp_load (a non-finite parameter: TKF_ERR_INVALID_ARG, no handle). */
+tkf_status tkf_mlp_load_f32(tkf_context ctx, const float* params, size_t n, tkf_mlp* out, void* stream);
 void tkf_mlp_destroy(tkf_mlp mlp);
+
+/* Initial FP32 parameters (DEVICE, n = TKF_MLP_PARAMS) for training, on `stream`: weights
+ * uniform in (-1/sqrt(fan_in), 1/sqrt(fan_in)) from SplitMix64 of (seed, parameter index)
+ * (fan_in 12 for W1, 64 for W2 and w3), biases 0. Deterministic for a seed. */
+tkf_status tkf_mlp_init(tkf_context ctx, float* params, size_t n, uint64_t seed, void* stream);
+
+/* Calibration after training: shifts the output bias b3 of the FP32 parameters (DEVICE, in
+ * place) by the `quantile` (0..1) of the residuals label - output over the training records
+ * (DEVICE [n][TKF_MLP_RECORD]), so that proposals 0.9 exp(output) rarely exceed the largest
+ * step within tolerance (a rejected proposal costs an attempt, a short one only a little
+ * length). The network's outputs and the residuals are FP32; the quantile interpolates
+ * linearly between the order statistics at positions floor and ceil of quantile (n - 1),
+ * which a radix select finds on the device; the shift is added to b3 in FP64 and rounded to
+ * FP32, and returned in *shift (HOST). Waits for the work on `stream`. Scratch comes from the
+ * context. Errors: TKF_ERR_INVALID_ARG (NULL, n = 0, quantile outside [0, 1]), TKF_ERR_OOM,
+ * TKF_ERR_DEVICE. */
+tkf_status tkf_mlp_calibrate(tkf_context ctx, float* params, const float* records, uint32_t n, double quantile,
+                             double* shift, void* stream);
 
 typedef struct tkf_mlp_train_options {
   uint32_t batch;   /* records per Adam step (1..8192); the last partial batch is dropped */

@@ -97,6 +97,9 @@ def lib():
         L.orc_fit_all_states.restype = ctypes.c_int
         L.orc_fit_all_states.argtypes = [vp, u32, ctypes.POINTER(OField), ctypes.POINTER(OOpts), u32, ctypes.c_uint64,
                                          vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int]
+        L.orc_record_steps.restype = ctypes.c_uint64
+        L.orc_record_steps.argtypes = [vp, u32, ctypes.POINTER(OField), ctypes.POINTER(OOpts), u32, ctypes.c_uint64,
+                                       vp, vp, vp, vp, vp, vp, ctypes.c_uint64]
         L.orc_field_at.argtypes = [ctypes.POINTER(OField), vp, u32, vp, vp]
         L.orc_rkn_fixed.argtypes = [ctypes.POINTER(OField), vp, vp, d, d, u32, vp, vp, vp]
         L.orc_rkn_step.argtypes = [ctypes.POINTER(OField), vp, vp, d, d, vp, vp, vp]
@@ -213,6 +216,22 @@ def fit_tracks(workload, opts: Options | None = None, n_threads: int = 1, tracks
     o = opts or Options(mass=workload.mass)
     return fit(workload.geometry.table, field_from(workload.field), o, t.offsets, t.meas, t.sid,
                t.seed_par, t.seed_cov, n_threads)
+
+
+def record_steps(surfaces: np.ndarray, fld: OField, opts: Options, offsets, meas, sid, seed_par, seed_cov,
+                 capacity: int = 2_000_000) -> np.ndarray:
+    """Training records [n, 13] of the step proposer (12 network inputs, label) from the
+    oracle's plain adaptive fit: every accepted step that the step-size control limited."""
+    s = surfaces14(surfaces)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint32)
+    meas, seed_par, seed_cov = _f64(meas), _f64(seed_par), _f64(seed_cov)
+    sid = np.ascontiguousarray(sid, dtype=np.uint32)
+    rec = np.zeros((capacity, 13), np.float32)
+    o = opts._c()
+    n = lib().orc_record_steps(_p(s), s.shape[0], ctypes.byref(fld), ctypes.byref(o), offsets.shape[0] - 1,
+                               meas.shape[0], _p(offsets), _p(meas), _p(sid), _p(seed_par), _p(seed_cov), _p(rec),
+                               capacity)
+    return rec[:min(int(n), capacity)].copy()
 
 
 def field_at(fld: OField, x: np.ndarray):

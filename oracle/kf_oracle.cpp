@@ -92,6 +92,7 @@ struct Opts {
   int smoother = 0;              // 0: RTS; 1: two-filter (forward filter, backward filter, weighted mean)
   double inflation = 1e3;        // two-filter: the backward filter starts from the last filtered
                                  // covariance times this factor
+  std::vector<float>* records = nullptr;  // training records of the step proposer, when not null
 };
 
 // ---------------------------------------------------------------- dense algebra
@@ -332,6 +333,7 @@ struct PropState {
   uint32_t rejected;  // rejected attempts, this track
   double h_last;      // last accepted step length (an MLP input)
   bool use_mlp;       // unused by the oracle's propagation (the proposal is made per track)
+  std::vector<float>* records = nullptr;  // training records (12 inputs, label), when not null
 };
 
 // MLP inputs at the start of a step, FP32: position (u, v, n components of r - c) / 1000 mm,
@@ -498,6 +500,8 @@ uint32_t propagate(const Field& f, const Opts& o, const Surface& s, double r[3],
     double limit = ps.h_ctrl;
     bool limited = !(std::fabs(sp) < limit);
     double h = limited ? std::copysign(limit, sp) : sp;
+    float feat[12];
+    if (ps.records) mlp_features(s, r, T, lam, B0, ps.h_last, sl, feat);
     Step st;
     bool oof = false;
     rkn_step(f, r, T, lam, h, st, &oof);
@@ -513,6 +517,13 @@ uint32_t propagate(const Field& f, const Opts& o, const Surface& s, double r[3],
       T[i] = st.T[i];
     }
     matmul(st.D, Dtot, Dtot, 7, 7, 7);
+    // Training record (learned step proposer): an accepted step that the control limited gives
+    // the inputs at its start and the label ln(|h| (tol/eps)^(1/4)), the largest step within
+    // tolerance at this step's error constant.
+    if (ps.records && limited && st.eps > 0.0) {
+      ps.records->insert(ps.records->end(), feat, feat + 12);
+      ps.records->push_back(float(std::log(std::fabs(h) * std::sqrt(std::sqrt(o.tol / st.eps)))));
+    }
     if (limited) {
       double fac = (st.eps > 0.0) ? step_factor(o.tol / st.eps, 0.25, 4.0) : 4.0;
       ps.h_ctrl = std::min(o.h_max, std::fabs(h) * fac);
@@ -909,7 +920,7 @@ void fit_track(const Surface* surf, uint32_t n_surf, const Field& f, const Opts&
   std::vector<double> pp(N * 5), Cp(N * 25), pf(N * 5), Cf(N * 25), J(N * 25, 0.0), ps(N * 5), Cs(N * 25);
   std::memcpy(&pp[0], in.seed_par, sizeof(double) * 5);
   unpack_cov(in.seed_cov, &Cp[0]);
-  PropState prop{o.h_max, 0, 0, o.h_max, true};
+  PropState prop{o.h_max, 0, 0, o.h_max, true, o.records};
   if (o.mlp && N >= 2) {
     // Reading (learned mode): the step-size control has no error estimate before the first step,
     // so the network proposes its starting value (instead of h_max) from the seed state at the
@@ -1537,6 +1548,37 @@ int orc_fit_all_states(const double* surfaces, uint32_t n_surf, const orc_field*
                    int n_threads) {
   return fit_batch(surfaces, n_surf, field, opts, n_tracks, n_meas, offsets, meas, sid, seed_par, seed_cov, out_par,
                    out_cov, chi2, ndf, status, steps, cov_filt0, states_par, states_cov, states_cov_filt, n_threads);
+}
+
+// Training records of the step proposer from the oracle's plain adaptive fit of every track,
+// in track order: rec [cap][13] (12 inputs, label); returns the number of records (at most cap
+// are written).
+uint64_t orc_record_steps(const double* surfaces, uint32_t n_surf, const orc_field* field, const orc_opts* opts,
+                          uint32_t n_tracks, uint64_t n_meas, const uint32_t* offsets, const double* meas,
+                          const uint32_t* sid, const double* seed_par, const double* seed_cov, float* rec,
+                          uint64_t cap) {
+  std::vector<Surface> surf = to_surfaces(surfaces, n_surf);
+  Field F = to_field(field);
+  Mlp mlp_store;
+  Opts O = to_opts(opts, &mlp_store);
+  O.mlp = nullptr;  // the plain control makes the records
+  std::vector<float> all;
+  O.records = &all;
+  for (uint32_t i = 0; i < n_tracks; ++i) {
+    uint32_t a = offsets[i], b = offsets[i + 1];
+    if (b < a || b > n_meas) continue;
+    TrackIn in;
+    in.N = b - a;
+    in.meas = meas + 5 * size_t(a);
+    in.sid = sid + a;
+    in.seed_par = seed_par + 5 * size_t(i);
+    in.seed_cov = seed_cov + 15 * size_t(i);
+    TrackOut out;
+    fit_track(surf.data(), n_surf, F, O, in, out);
+  }
+  const uint64_t n = all.size() / 13;
+  std::memcpy(rec, all.data(), sizeof(float) * 13 * size_t(std::min(n, cap)));
+  return n;
 }
 
 // ---- component entry points used by the oracle's own pins

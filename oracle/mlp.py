@@ -121,3 +121,14 @@ def to_bf16(theta) -> np.ndarray:
 
 def from_bf16(b) -> np.ndarray:
     return (np.asarray(b, dtype=np.uint16).astype(np.uint32) << 16).view(np.float32)
+
+
+def calibrate(theta, X, y, quantile: float = 0.05):
+    """The output bias shifted by the `quantile` of the residuals y - output (FP32 forward
+    outputs as the library computes them are not needed here: FP64 throughout); returns the new
+    parameters and the shift."""
+    out, _ = forward(theta, np.asarray(X, dtype=np.float64))
+    q = float(np.quantile(np.asarray(y, dtype=np.float64) - out, quantile))
+    th = np.array(theta, dtype=np.float64)
+    th[-1] += q
+    return th, q

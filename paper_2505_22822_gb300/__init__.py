@@ -194,7 +194,11 @@ _SIGNATURES = {
                                        ctypes.POINTER(CkfInputs), ctypes.POINTER(CkfOutputs), _VP]),
     "tkf_propose_start": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(FitOptions), ctypes.POINTER(FitInputs),
                                          _VP, _VP]),
-    "tkf_mlp_load": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(_VP)]),
+    "tkf_mlp_load": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t, ctypes.POINTER(_VP)]),
+    "tkf_mlp_load_f32": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t, ctypes.POINTER(_VP), _VP]),
+    "tkf_mlp_init": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t, ctypes.c_uint64, _VP]),
+    "tkf_mlp_calibrate": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_uint32, ctypes.c_double,
+                                         ctypes.POINTER(ctypes.c_double), _VP]),
     "tkf_mlp_destroy": (None, [_VP]),
     "tkf_mlp_train": (ctypes.c_int, [_VP, _VP, ctypes.c_uint32, ctypes.POINTER(MlpTrainOptions), _VP, _VP,
                                      ctypes.POINTER(ctypes.c_uint32), _VP, _VP]),
@@ -344,15 +348,27 @@ class Field:
 
 
 class Mlp:
-    """Step-proposer network handle (BF16 weights uploaded to the device)."""
+    """Step-proposer network handle (BF16 weights on the device): from host BF16 bit patterns
+    (tkf_mlp_load), or, with ``from_params``, from trained FP32 parameters in a CUDA tensor that
+    the library rounds to BF16 (tkf_mlp_load_f32)."""
 
-    def __init__(self, ctx: Context, bf16_weights):
-        w = np.ascontiguousarray(bf16_weights, dtype=np.uint16)
-        if w.size != MLP_PARAMS:
-            raise TkfError(f"expected {MLP_PARAMS} BF16 weights, got {w.size}")
+    def __init__(self, ctx: Context, bf16_weights=None, params=None, stream=None):
         h = _VP()
-        _check(lib().tkf_mlp_load(ctx.handle, w.ctypes.data_as(_VP), ctypes.byref(h)), ctx.handle, "tkf_mlp_load")
+        if params is not None:
+            import torch
+            if stream is None:
+                stream = torch.cuda.current_stream(params.device)
+            _check(lib().tkf_mlp_load_f32(ctx.handle, _VP(params.data_ptr()), int(params.numel()), ctypes.byref(h),
+                                          _VP(stream.cuda_stream)), ctx.handle, "tkf_mlp_load_f32")
+        else:
+            w = np.ascontiguousarray(bf16_weights, dtype=np.uint16)
+            _check(lib().tkf_mlp_load(ctx.handle, w.ctypes.data_as(_VP), w.size, ctypes.byref(h)), ctx.handle,
+                   "tkf_mlp_load")
         self.handle, self.ctx = h, ctx
+
+    @classmethod
+    def from_params(cls, ctx: Context, params, stream=None) -> "Mlp":
+        return cls(ctx, params=params, stream=stream)
 
     def __del__(self):
         try:
@@ -715,6 +731,29 @@ def mlp_forward(ctx: Context, params, x, stream=None):
     _check(lib().tkf_mlp_forward(ctx.handle, _VP(params.data_ptr()), _VP(x.data_ptr()), x.shape[0],
                                  _VP(out.data_ptr()), _VP(stream.cuda_stream)), ctx.handle, "tkf_mlp_forward")
     return out
+
+
+def mlp_init(ctx: Context, params, seed: int, stream=None):
+    """tkf_mlp_init: seeded initial FP32 parameters into ``params`` (CUDA tensor [5057])."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(params.device)
+    _check(lib().tkf_mlp_init(ctx.handle, _VP(params.data_ptr()), int(params.numel()), int(seed),
+                              _VP(stream.cuda_stream)), ctx.handle, "tkf_mlp_init")
+    return params
+
+
+def mlp_calibrate(ctx: Context, params, records, quantile: float, stream=None) -> float:
+    """tkf_mlp_calibrate: shifts the output bias of ``params`` (CUDA [5057], in place) by the
+    ``quantile`` of the residuals over ``records`` (CUDA [n, 13]); returns the shift."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(params.device)
+    shift = ctypes.c_double()
+    _check(lib().tkf_mlp_calibrate(ctx.handle, _VP(params.data_ptr()), _VP(records.data_ptr()), records.shape[0],
+                                   float(quantile), ctypes.byref(shift), _VP(stream.cuda_stream)), ctx.handle,
+           "tkf_mlp_calibrate")
+    return shift.value
 
 
 def exported_symbols() -> list[str]:

@@ -874,10 +874,27 @@ tkf_status tkf_fit_host(tkf_context ctx, tkf_geometry geo, tkf_field field, cons
 // ============================================================================ learned step proposer
 extern "C" {
 
-tkf_status tkf_mlp_load(tkf_context ctx, const uint16_t* w, tkf_mlp* out) {
+// A handle around device FP32 weights that hold BF16 values (takes ownership of `dev`).
+static tkf_status make_mlp(tkf_context ctx, float* dev, tkf_mlp* out, const char* fn) {
+  tkf_mlp h = new (std::nothrow) tkf_mlp_s();
+  if (!h) {
+    cudaFree(dev);
+    return fail(ctx, TKF_ERR_OOM, std::string(fn) + ": host allocation failed");
+  }
+  h->ctx = ctx;
+  h->device = ctx->device;
+  h->d_weights = dev;
+  *out = h;
+  return TKF_OK;
+}
+
+tkf_status tkf_mlp_load(tkf_context ctx, const uint16_t* w, size_t n, tkf_mlp* out) {
   if (!ctx) return fail(nullptr, TKF_ERR_BAD_HANDLE, "tkf_mlp_load: NULL context");
   if (!w || !out) return fail(ctx, TKF_ERR_INVALID_ARG, "tkf_mlp_load: NULL pointer");
   *out = nullptr;
+  if (n != TKF_MLP_PARAMS)
+    return fail(ctx, TKF_ERR_INVALID_ARG, "tkf_mlp_load: expected " + std::to_string(TKF_MLP_PARAMS) +
+                                              " BF16 weights, got " + std::to_string(n));
   float host[TKF_MLP_PARAMS];
   for (int k = 0; k < TKF_MLP_PARAMS; ++k) {
     const uint32_t u = uint32_t(w[k]) << 16;
@@ -895,15 +912,74 @@ tkf_status tkf_mlp_load(tkf_context ctx, const uint16_t* w, tkf_mlp* out) {
     cudaFree(dev);
     return cuda_fail(ctx, e, "tkf_mlp_load: cudaMemcpy");
   }
-  tkf_mlp h = new (std::nothrow) tkf_mlp_s();
-  if (!h) {
+  return make_mlp(ctx, dev, out, "tkf_mlp_load");
+}
+
+tkf_status tkf_mlp_load_f32(tkf_context ctx, const float* params, size_t n, tkf_mlp* out, void* stream) {
+  if (!ctx) return fail(nullptr, TKF_ERR_BAD_HANDLE, "tkf_mlp_load_f32: NULL context");
+  if (!params || !out) return fail(ctx, TKF_ERR_INVALID_ARG, "tkf_mlp_load_f32: NULL pointer");
+  *out = nullptr;
+  if (n != TKF_MLP_PARAMS)
+    return fail(ctx, TKF_ERR_INVALID_ARG, "tkf_mlp_load_f32: expected " + std::to_string(TKF_MLP_PARAMS) +
+                                              " FP32 parameters, got " + std::to_string(n));
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float* dev = nullptr;
+  cudaError_t e = cudaMalloc(&dev, sizeof(float) * TKF_MLP_PARAMS + 16);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_mlp_load_f32: cudaMalloc");
+  uint32_t* bad = reinterpret_cast<uint32_t*>(dev + TKF_MLP_PARAMS);
+  uint32_t bad_h = 0;
+  e = cudaMemsetAsync(bad, 0, sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = tkf::mlp_round_bf16(params, dev, bad, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad_h, bad, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
     cudaFree(dev);
-    return fail(ctx, TKF_ERR_OOM, "tkf_mlp_load: host allocation failed");
+    return cuda_fail(ctx, e, "tkf_mlp_load_f32: rounding");
   }
-  h->ctx = ctx;
-  h->device = ctx->device;
-  h->d_weights = dev;
-  *out = h;
+  if (bad_h) {
+    cudaFree(dev);
+    return fail(ctx, TKF_ERR_INVALID_ARG, "tkf_mlp_load_f32: non-finite parameter");
+  }
+  return make_mlp(ctx, dev, out, "tkf_mlp_load_f32");
+}
+
+tkf_status tkf_mlp_init(tkf_context ctx, float* params, size_t n, uint64_t seed, void* stream) {
+  if (!ctx) return fail(nullptr, TKF_ERR_BAD_HANDLE, "tkf_mlp_init: NULL context");
+  if (!params) return fail(ctx, TKF_ERR_INVALID_ARG, "tkf_mlp_init: NULL pointer");
+  if (n != TKF_MLP_PARAMS)
+    return fail(ctx, TKF_ERR_INVALID_ARG, "tkf_mlp_init: expected " + std::to_string(TKF_MLP_PARAMS) + " parameters");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = tkf::mlp_init(params, seed, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_mlp_init: launch");
+  return TKF_OK;
+}
+
+tkf_status tkf_mlp_calibrate(tkf_context ctx, float* params, const float* records, uint32_t n, double quantile,
+                             double* shift, void* stream) {
+  if (!ctx) return fail(nullptr, TKF_ERR_BAD_HANDLE, "tkf_mlp_calibrate: NULL context");
+  if (!params || !records || !shift) return fail(ctx, TKF_ERR_INVALID_ARG, "tkf_mlp_calibrate: NULL pointer");
+  if (n == 0 || !(quantile >= 0.0 && quantile <= 1.0))
+    return fail(ctx, TKF_ERR_INVALID_ARG, "tkf_mlp_calibrate: need n > 0 and 0 <= quantile <= 1");
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t need = tkf::mlp_calibrate_scratch_bytes(n) + 64;  // the shift, then the scratch
+  if (need > ctx->train_bytes) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_mlp_calibrate: scratch");
+    if (ctx->train_ws) cudaFree(ctx->train_ws);
+    ctx->train_ws = nullptr;
+    ctx->train_bytes = 0;
+    e = cudaMalloc(&ctx->train_ws, need);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_mlp_calibrate: scratch");
+    ctx->train_bytes = need;
+  }
+  double* d_shift = reinterpret_cast<double*>(ctx->train_ws);
+  void* scratch = static_cast<char*>(ctx->train_ws) + 64;
+  cudaError_t e = tkf::mlp_calibrate(params, records, n, quantile, d_shift, scratch, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(shift, d_shift, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_mlp_calibrate: launch");
   return TKF_OK;
 }
 

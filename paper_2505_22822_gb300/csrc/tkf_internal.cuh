@@ -301,4 +301,10 @@ cudaError_t mlp_train(const float* records, uint32_t n, uint32_t batch, uint32_t
                       float beta2, float eps, float* params, float* moments, uint32_t* adam_t, float* epoch_loss,
                       void* scratch, cudaStream_t stream);
 cudaError_t mlp_forward(const float* params, const float* x, uint32_t n, float* out, cudaStream_t stream);
+cudaError_t mlp_init(float* params, uint64_t seed, cudaStream_t stream);
+size_t mlp_calibrate_scratch_bytes(uint32_t n);
+// shift: DEVICE double receiving the bias shift
+cudaError_t mlp_calibrate(float* params, const float* records, uint32_t n, double quantile, double* shift,
+                          void* scratch, cudaStream_t stream);
+cudaError_t mlp_round_bf16(const float* in, float* out, uint32_t* bad, cudaStream_t stream);
 }  // namespace tkf

@@ -7,6 +7,9 @@
 //   backward  (one thread per sample; dL/dz of both hidden layers and of the output),
 //   reduce    (one thread per parameter; sums over the batch, no atomics: deterministic),
 //   adam      (one thread per parameter).
+// Around training: seeded initialisation, calibration of the output bias (a quantile of the
+// training residuals, by a radix select on the device) and rounding to the BF16 weights the
+// fit's inference uses.
 // The paper has no learned component; the learned step proposer is an addition to its method.
 
 #include <math.h>
@@ -190,7 +193,135 @@ cudaError_t batch_grad(const float* params, const float* x, int x_stride, const 
   return cudaGetLastError();
 }
 
+// ---- initialisation: W ~ U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from SplitMix64 of (seed, index), b = 0
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+__global__ void __launch_bounds__(256) mlp_init_kernel(float* __restrict__ p, uint64_t seed) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= kMlpParams) return;
+  const bool weight = k < oB1 || (k >= oW2 && k < oB2) || (k >= oW3 && k < oB3);
+  if (!weight) {
+    p[k] = 0.0f;
+    return;
+  }
+  const float fan_in = k < oB1 ? float(kIn) : float(kHid);
+  const uint64_t r = splitmix64(seed * 0x100000001B3ull + uint64_t(k));
+  const float u = float(r >> 40) * (1.0f / 16777216.0f);  // [0, 1), 24 bits
+  p[k] = (2.0f * u - 1.0f) * rsqrtf(fan_in);
+}
+
+// ---- calibration: residual = label - output, shifted bias b3 += quantile of the residuals
+// order-preserving map of an FP32 value to an unsigned key, and back
+__device__ __forceinline__ uint32_t order_key(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float from_order_key(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+__global__ void __launch_bounds__(256) residual_keys_kernel(const float* __restrict__ rec, uint32_t n,
+                                                            const float* __restrict__ out, uint32_t* __restrict__ keys) {
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) keys[s] = order_key(rec[size_t(s) * kMlpRecord + 12] - out[s]);
+}
+
+// The k0-th and k1-th smallest keys (0-based) by a radix select, 8 bits a pass from the top:
+// each pass counts the keys that share the digits chosen so far by their next digit and keeps
+// the bucket that holds the wanted rank. One block; every loop is bounded by n or 256.
+__global__ void __launch_bounds__(1024) select_kernel(const uint32_t* __restrict__ keys, uint32_t n, uint32_t k0,
+                                                      uint32_t k1, uint32_t* __restrict__ sel) {
+  __shared__ uint32_t hist[256];
+  __shared__ uint32_t s_prefix, s_rank;
+  for (int which = 0; which < 2; ++which) {
+    uint32_t prefix = 0, mask = 0, rank = which ? k1 : k0;
+    for (int pass = 0; pass < 4; ++pass) {
+      const int shift = 24 - 8 * pass;
+      for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint32_t key = keys[i];
+        if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        int d = 0;
+        for (; d < 255; ++d) {
+          if (acc + hist[d] > rank) break;
+          acc += hist[d];
+        }
+        s_prefix = prefix | (uint32_t(d) << shift);
+        s_rank = rank - acc;
+      }
+      __syncthreads();
+      prefix = s_prefix;
+      rank = s_rank;
+      mask |= 255u << shift;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) sel[which] = prefix;
+    __syncthreads();
+  }
+}
+
+// The quantile by linear interpolation between the two order statistics around
+// position q (n - 1) (FP64), added to the output bias (FP64, rounded to FP32).
+__global__ void shift_bias_kernel(float* __restrict__ p, const uint32_t* __restrict__ sel, double frac,
+                                  double* __restrict__ shift) {
+  const double v0 = from_order_key(sel[0]), v1 = from_order_key(sel[1]);
+  const double q = v0 + frac * (v1 - v0);
+  p[oB3] = float(double(p[oB3]) + q);
+  *shift = q;
+}
+
+// ---- BF16 weights: round to nearest even; a non-finite value sets *bad
+__global__ void __launch_bounds__(256) round_bf16_kernel(const float* __restrict__ in, float* __restrict__ out,
+                                                         uint32_t* __restrict__ bad) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= kMlpParams) return;
+  const float x = in[k];
+  if (!isfinite(x)) atomicOr(bad, 1u);
+  const uint32_t u = __float_as_uint(x);
+  out[k] = __uint_as_float((u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u);
+}
+
 }  // namespace
+
+cudaError_t mlp_init(float* params, uint64_t seed, cudaStream_t stream) {
+  mlp_init_kernel<<<(kMlpParams + 255) / 256, 256, 0, stream>>>(params, seed);
+  return cudaGetLastError();
+}
+
+size_t mlp_calibrate_scratch_bytes(uint32_t n) { return sizeof(float) * 2 * size_t(n) + 64; }
+
+cudaError_t mlp_calibrate(float* params, const float* records, uint32_t n, double quantile, double* shift,
+                          void* scratch, cudaStream_t stream) {
+  float* out = static_cast<float*>(scratch);
+  uint32_t* keys = reinterpret_cast<uint32_t*>(out + n);
+  uint32_t* sel = keys + n;
+  Act act{};
+  act.out = out;
+  const unsigned g = (n + 255) / 256;
+  mlp_forward_kernel<<<(n + 127) / 128, 128, 0, stream>>>(params, records, kMlpRecord, n, act);
+  residual_keys_kernel<<<g, 256, 0, stream>>>(records, n, out, keys);
+  const double pos = quantile * double(n - 1);
+  const uint32_t k0 = uint32_t(floor(pos));
+  const uint32_t k1 = k0 + 1 < n ? k0 + 1 : k0;
+  select_kernel<<<1, 1024, 0, stream>>>(keys, n, k0, k1, sel);
+  shift_bias_kernel<<<1, 1, 0, stream>>>(params, sel, pos - double(k0), shift);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_round_bf16(const float* in, float* out, uint32_t* bad, cudaStream_t stream) {
+  round_bf16_kernel<<<(kMlpParams + 255) / 256, 256, 0, stream>>>(in, out, bad);
+  return cudaGetLastError();
+}
 
 size_t mlp_train_scratch_bytes(uint32_t batch) {
   return sizeof(float) * (size_t(batch) * (6 * kHid + 3) + kMlpParams) + 256;

@@ -10,8 +10,7 @@ import pytest
 import oracle
 import paper_2505_22822_gb300 as tkf
 import synth
-from paper_2505_22822_gb300 import learn
-from tests import parity
+from tests import parity, proposer
 from tests.test_gpu_parity import TOL64, check, check_mixed
 
 torch = pytest.importorskip("torch")
@@ -79,14 +78,16 @@ def test_mixed_full_batch(barrel):
 
 
 def test_mixed_learned_full_batch(barrel):
+    """Learned mode on the whole bench batch with a network trained without the CUDA path
+    (oracle records of a seed-disjoint event, numpy training): sampled tracks against the
+    oracle running the same network."""
     ctx, w, geo, fld, b, idx = barrel
-    tt = synth.barrel_workload(n_events=5, seed=10_002).tracks  # seed-disjoint training tracks
-    tb = tkf.Batch.from_arrays(tt.offsets, tt.meas, tt.sid, tt.seed_par, tt.seed_cov).to("cuda:0")
-    m, info = learn.build_proposer(ctx, geo, fld, tb, tkf.MIXED, mass=w.mass)
+    wbf, info = proposer.barrel_proposer()
+    m = tkf.Mlp(ctx, wbf)
     g = _bench_like_fit(ctx, geo, fld, b, tkf.Options(precision=tkf.MIXED, mass=w.mass, step_mode=tkf.STEP_LEARNED,
                                                       mlp=m))
     _whole_batch_properties(g, w)
-    o = _oracle_sample(w, idx, oracle.Options(mass=w.mass, mlp=info["weights_bf16"]))
+    o = _oracle_sample(w, idx, oracle.Options(mass=w.mass, mlp=wbf))
     check_mixed({k: (v[idx] if v is not None else None) for k, v in g.items()}, o)
     # the proposals cut the plain control's rejected attempts on the whole batch
     plain = _bench_like_fit(ctx, geo, fld, b, tkf.Options(precision=tkf.MIXED, mass=w.mass))

@@ -9,7 +9,7 @@ import oracle
 import paper_2505_22822_gb300 as tkf
 import synth
 from oracle import mlp
-from tests import parity
+from tests import parity, proposer
 from tests.test_gpu_parity import MIXED_TOL_CHI2, MIXED_TOL_SIGMA, TOL64, check, check_mixed, mixed_deviation
 
 torch = pytest.importorskip("torch")
@@ -79,7 +79,8 @@ def _fit(ctx, w, opts, tracks=None):
 
 
 def train_proposer(ctx, fld, n_tracks=20000, epochs=8, seed=1000):
-    """Records from the plain stepper on seed-disjoint tracks, training on the GPU, calibration."""
+    """The library's own pipeline: records from the plain stepper on seed-disjoint tracks,
+    initialisation, training and calibration on the GPU, BF16 rounding on loading."""
     from paper_2505_22822_gb300 import learn
     w = synth.solenoid_muon_workload(n_tracks, seed=seed, fld=fld)
     t = w.tracks
@@ -88,26 +89,106 @@ def train_proposer(ctx, fld, n_tracks=20000, epochs=8, seed=1000):
     b = tkf.Batch.from_arrays(t.offsets, t.meas, t.sid, t.seed_par, t.seed_cov).to("cuda:0")
     rec = learn.record_steps(ctx, geo, f, b, tkf.MIXED)
     assert rec.shape[0] > 5000
-    theta, losses = learn.train(ctx, rec, epochs=epochs)
-    cal, q = learn.calibrate(ctx, theta, rec)
+    params, losses = learn.train(ctx, rec, epochs=epochs)
+    q = learn.calibrate(ctx, params, rec)
+    losses = losses.cpu().numpy()
     print({"records": int(rec.shape[0]), "losses": [round(float(x), 4) for x in losses], "bias_shift": q})
-    return rec, cal, losses
+    return rec, params, losses
 
 
 @pytest.fixture(scope="module")
 def trained(ctx):
+    """GPU-trained network (for the gain and timeout tests)."""
     fld = synth.solenoid_map()
-    rec, theta, losses = train_proposer(ctx, fld)
-    return fld, rec, theta, losses
+    rec, params, losses = train_proposer(ctx, fld)
+    return fld, rec, params, losses
+
+
+@pytest.fixture(scope="module")
+def reference_weights():
+    """BF16 weights trained without the CUDA path (oracle records, numpy training): the network
+    both sides run in the parity tests."""
+    fld = synth.solenoid_map()
+    w, info = proposer.map_proposer(fld)
+    print(info)
+    return fld, w
 
 
 def test_records_are_sane_and_training_converges(trained):
-    fld, rec, theta, losses = trained
+    fld, rec, params, losses = trained
     r = rec.cpu().numpy()
     assert np.all(np.isfinite(r))
     assert np.all(np.abs(r[:, 3:6]) <= 1.0 + 1e-3)           # direction components
     assert np.all((r[:, 12] > np.log(1e-4)) & (r[:, 12] < 12))  # ln(step / mm)
     assert losses[-1] < 0.3 * losses[0]
+    assert torch.all(torch.isfinite(params))
+
+
+def test_initialisation_is_seeded_and_bounded(ctx):
+    a = tkf.mlp_init(ctx, torch.empty(tkf.MLP_PARAMS, dtype=torch.float32, device="cuda:0"), 3).cpu().numpy()
+    b = tkf.mlp_init(ctx, torch.empty(tkf.MLP_PARAMS, dtype=torch.float32, device="cuda:0"), 3).cpu().numpy()
+    c = tkf.mlp_init(ctx, torch.empty(tkf.MLP_PARAMS, dtype=torch.float32, device="cuda:0"), 4).cpu().numpy()
+    np.testing.assert_array_equal(a, b)
+    assert not np.array_equal(a, c)
+    p = mlp.unpack(a.astype(np.float64))
+    for name, fan_in in (("W1", 12), ("W2", 64), ("w3", 64)):
+        x = p[name].ravel()
+        assert np.all(np.abs(x) <= 1 / np.sqrt(fan_in))
+        # uniform on (-1/sqrt(fan_in), 1/sqrt(fan_in)): mean ~ 0, variance ~ 1 / (3 fan_in)
+        assert abs(x.mean()) < 4 * np.sqrt(1 / (3 * fan_in) / x.size)
+        assert abs(x.var() * 3 * fan_in - 1.0) < 0.2
+    for name in ("b1", "b2", "b3"):
+        assert np.all(p[name] == 0.0)
+
+
+def test_calibration_shifts_the_bias_by_the_residual_quantile(ctx, reference_weights):
+    """tkf_mlp_calibrate against the numpy reference: the shift is the 5 % quantile of
+    label - output over the records (FP64 reference forward; the library's is FP32, so the two
+    agree to ~1e-5), added to the output bias only."""
+    fld, _ = reference_weights
+    w = synth.solenoid_muon_workload(1500, seed=1001, fld=fld)
+    t = w.tracks
+    rec = oracle.record_steps(w.geometry.table, oracle.field_from(w.field), oracle.Options(), t.offsets, t.meas,
+                              t.sid, t.seed_par, t.seed_cov)
+    rng = np.random.default_rng(9)
+    theta = (mlp.init(5) + 0.05 * rng.normal(size=mlp.N_PARAMS)).astype(np.float32)
+    p = _cuda(theta)
+    shift = tkf.mlp_calibrate(ctx, p, _cuda(rec), 0.05)
+    ref_theta, ref_q = mlp.calibrate(theta.astype(np.float64), rec[:, :12], rec[:, 12], 0.05)
+    print({"records": len(rec), "shift": shift, "reference": ref_q})
+    assert abs(shift - ref_q) < 1e-5
+    got = p.cpu().numpy()
+    np.testing.assert_array_equal(got[:-1], theta[:-1])
+    assert got[-1] == np.float32(np.float64(theta[-1]) + shift)
+    # the quantile is an order statistic: a fraction 0.05 of the residuals lies below it
+    out = tkf.mlp_forward(ctx, _cuda(theta), _cuda(rec[:, :12])).cpu().numpy()
+    frac = np.mean(rec[:, 12] - out < shift)
+    assert abs(frac - 0.05) < 2.0 / len(rec)
+
+
+def test_loading_fp32_parameters_rounds_them_to_bf16(ctx, reference_weights):
+    """tkf_mlp_load_f32 (the library rounds on the device) gives the network of tkf_mlp_load with
+    the reference's BF16 rounding: identical proposals on 5000 tracks; a non-finite parameter
+    is rejected."""
+    fld, _ = reference_weights
+    rng = np.random.default_rng(11)
+    theta = (mlp.init(6) + 0.05 * rng.normal(size=mlp.N_PARAMS)).astype(np.float32)
+    m32 = tkf.Mlp.from_params(ctx, _cuda(theta))
+    m16 = tkf.Mlp(ctx, mlp.to_bf16(theta))
+    w = synth.solenoid_muon_workload(5000, seed=1002, fld=fld)
+    t = w.tracks
+    geo = tkf.Geometry.from_table(ctx, w.geometry.table)
+    f = tkf.Field.from_desc(ctx, w.field)
+    b = tkf.Batch.from_arrays(t.offsets, t.meas, t.sid, t.seed_par, t.seed_cov).to("cuda:0")
+    h32 = tkf.propose_start(ctx, geo, f, b, tkf.Options(precision=tkf.MIXED, step_mode=tkf.STEP_LEARNED, mlp=m32))
+    h16 = tkf.propose_start(ctx, geo, f, b, tkf.Options(precision=tkf.MIXED, step_mode=tkf.STEP_LEARNED, mlp=m16))
+    assert torch.equal(h32, h16)
+    bad = theta.copy()
+    bad[100] = np.nan
+    with pytest.raises(tkf.TkfError, match="non-finite"):
+        tkf.Mlp.from_params(ctx, _cuda(bad))
+    with pytest.raises(tkf.TkfError, match="expected"):
+        tkf.Mlp(ctx, mlp.to_bf16(theta)[:-1])
 
 
 def _subset(o, idx):
@@ -115,7 +196,7 @@ def _subset(o, idx):
 
 
 @pytest.mark.parametrize("precision", [tkf.MIXED, tkf.FP64])
-def test_learned_fit_matches_the_oracle_with_the_same_proposals(ctx, trained, precision):
+def test_learned_fit_matches_the_oracle_with_the_same_proposals(ctx, reference_weights, precision):
     """Every track against the oracle running the same network. The proposals are integers on a
     1/32 grid of ln h decided in FP32 on both sides; the tensor cores' accumulation order may put
     an output that lies within rounding of a grid boundary on the other side of it (both
@@ -123,8 +204,7 @@ def test_learned_fit_matches_the_oracle_with_the_same_proposals(ctx, trained, pr
     held to the plain parity rule of their precision (FP64: 1e-10 with the step-sequence and
     conditioning rules of `check`; mixed: 1e-3 sigma); a track whose proposal differs starts from
     another valid step and is held to the mixed-path tolerance."""
-    fld, _, theta, _ = trained
-    wbf = mlp.to_bf16(theta)
+    fld, wbf = reference_weights
     m = tkf.Mlp(ctx, wbf)
     w = synth.solenoid_muon_workload(3000, seed=3, fld=fld)
     t = w.tracks
@@ -161,8 +241,8 @@ def test_learned_fit_matches_the_oracle_with_the_same_proposals(ctx, trained, pr
 def test_learned_fit_with_four_lanes_a_track_is_bit_identical(ctx, trained, precision):
     """The learned mode under the group-per-track mapping: the same proposals (one pre-pass per
     track) and the same results as one lane a track."""
-    fld, _, theta, _ = trained
-    m = tkf.Mlp(ctx, mlp.to_bf16(theta))
+    fld, _, params, _ = trained
+    m = tkf.Mlp.from_params(ctx, params)
     w = synth.solenoid_muon_workload(2000, seed=3, fld=fld)
     one = _fit(ctx, w, tkf.Options(precision=precision, step_mode=tkf.STEP_LEARNED, mlp=m, lanes_per_track=1))
     four = _fit(ctx, w, tkf.Options(precision=precision, step_mode=tkf.STEP_LEARNED, mlp=m, lanes_per_track=4))
@@ -171,8 +251,8 @@ def test_learned_fit_with_four_lanes_a_track_is_bit_identical(ctx, trained, prec
 
 
 def test_learned_proposals_save_step_attempts_at_equal_tolerance(ctx, trained):
-    fld, _, theta, _ = trained
-    m = tkf.Mlp(ctx, mlp.to_bf16(theta))
+    fld, _, params, _ = trained
+    m = tkf.Mlp.from_params(ctx, params)
     w = synth.solenoid_muon_workload(20000, seed=3, fld=fld)
     plain = _fit(ctx, w, tkf.Options(precision=tkf.MIXED))
     learn = _fit(ctx, w, tkf.Options(precision=tkf.MIXED, step_mode=tkf.STEP_LEARNED, mlp=m))
@@ -193,12 +273,11 @@ def test_learned_proposals_save_step_attempts_at_equal_tolerance(ctx, trained):
     assert sl[0] <= sp[0]
 
 
-def test_tensor_core_proposals_match_the_oracle(ctx, trained):
+def test_tensor_core_proposals_match_the_oracle(ctx, reference_weights):
     """The pre-pass's two dense layers run on the tensor cores (BF16 operands, FP32 accumulate);
     its proposals sit on a 1/32 grid of ln h, so they equal the oracle's except where an
     accumulation-order difference flips a rounding (then by one grid step)."""
-    fld, _, theta, _ = trained
-    wbf = mlp.to_bf16(theta)
+    fld, wbf = reference_weights
     m = tkf.Mlp(ctx, wbf)
     w = synth.solenoid_muon_workload(20000, seed=33, fld=fld)
     t = w.tracks
@@ -227,8 +306,8 @@ def test_pre_pass_timeout_falls_back_to_the_plain_start(ctx, trained):
     work, so nothing ever arrives on its mbarrier; its bounded waits run out, it frees its tensor
     memory and returns, and the fit starts every track from h_max with PROPOSAL_FALLBACK, which
     gives the plain adaptive fit's results. The context stays usable."""
-    fld, _, theta, _ = trained
-    m = tkf.Mlp(ctx, mlp.to_bf16(theta))
+    fld, _, params, _ = trained
+    m = tkf.Mlp.from_params(ctx, params)
     w = synth.solenoid_muon_workload(2000, seed=34, fld=fld)
     stalled = _fit(ctx, w, tkf.Options(precision=tkf.MIXED, step_mode=tkf.STEP_LEARNED, mlp=m,
                                        test_proposal_timeout=True))

@@ -145,8 +145,8 @@ def test_graph_flag_on_the_legacy_stream_launches_directly(setup):
 def test_graph_and_autotune_with_learned_proposals(setup):
     ctx, geo, fld, b, _ = setup
     rng = np.random.default_rng(5)
-    from paper_2505_22822_gb300 import learn
-    w = learn.to_bf16(learn.init_params(3) + 0.01 * rng.normal(size=tkf.MLP_PARAMS).astype(np.float32))
+    from oracle import mlp
+    w = mlp.to_bf16(mlp.init(3) + 0.01 * rng.normal(size=tkf.MLP_PARAMS))
     m = tkf.Mlp(ctx, w)
     ref = _run(ctx, geo, fld, b, precision=tkf.MIXED, step_mode=tkf.STEP_LEARNED, mlp=m)
     s = torch.cuda.Stream()

@@ -112,3 +112,24 @@ def test_proposal_grid_ties_and_clamps_in_closed_form():
         else:
             expect = float(np.float32(0.9) * np.exp(np.float32(k / 32.0), dtype=np.float32))
         np.testing.assert_allclose(h[1:], expect, rtol=2e-7)
+
+
+def test_oracle_training_records_are_consistent():
+    """The oracle's record capture: finite inputs, a unit direction in the target frame, the
+    clamped straight-line path, labels above ln(h_min); the same records on a second run; and
+    a network trained on them by the reference explains most of the labels' variance."""
+    import oracle
+    import synth
+    w = synth.solenoid_muon_workload(600, seed=1003)
+    t = w.tracks
+    args = (w.geometry.table, oracle.field_from(w.field), oracle.Options(), t.offsets, t.meas, t.sid, t.seed_par,
+            t.seed_cov)
+    rec = oracle.record_steps(*args)
+    assert len(rec) > 1000 and np.all(np.isfinite(rec))
+    np.testing.assert_array_equal(rec, oracle.record_steps(*args))
+    d2 = (rec[:, 3:6].astype(np.float64) ** 2).sum(1)
+    assert np.all(np.abs(d2 - 1.0) < 1e-5)
+    assert np.all(np.abs(rec[:, 11]) <= 2.0) and np.all(rec[:, 12] > np.log(1e-4))
+    X, y = rec[:, :12].astype(np.float64), rec[:, 12].astype(np.float64)
+    theta, losses = mlp.train(mlp.init(1), X, y, batch=128, epochs=6, lr=2e-3)
+    assert losses[-1] < 0.2 * np.var(y)
