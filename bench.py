@@ -945,8 +945,16 @@ def main():
     if not args.no_cpu_baseline:
         line["cpu_baseline"], idx, ores = cpu_baseline(w)
         # each variant's error against the FP64 oracle on the baseline's sample (the paper's
-        # CPU-GPU agreement study, Sec. 3.1, Table 1)
-        line["accuracy_vs_oracle"] = {k: accuracy_vs_oracle(v["host_out"], ores, idx) for k, v in results.items()}
+        # CPU-GPU agreement study, Sec. 3.1, Table 1); the two-filter variants against the
+        # oracle's two-filter smoother
+        ores2 = None
+        if any(k.endswith("_two_filter") for k in results):
+            import oracle
+            ores2 = oracle.fit_tracks(w, oracle.Options(mass=w.mass, smoother=1), tracks=t.subset(idx),
+                                      n_threads=os.cpu_count() or 1)
+        line["accuracy_vs_oracle"] = {k: accuracy_vs_oracle(v["host_out"], ores2 if k.endswith("_two_filter") else ores,
+                                                            idx)
+                                      for k, v in results.items()}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

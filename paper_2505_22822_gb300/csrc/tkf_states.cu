@@ -65,16 +65,17 @@ __global__ void __launch_bounds__(128) smooth_states_kernel(FitArgs a) {
       for (int j = 0; j < 15; ++j) Cp[j] = w[5 + j];
       for (int r = 0; r < 5; ++r)
         for (int c = 0; c < 5; ++c) J[r][c] = w[20 + 5 * r + c];
-      // B = J Cf, then X = Cp^-1 B = A^T (Cp, Cf symmetric)
+      // B = J Cf, then X = Cp^-1 B = A^T (Cp, Cf symmetric); row 4 of J is e_4
       double X[5][5];
-      for (int r = 0; r < 5; ++r)
+      for (int r = 0; r < 4; ++r)
         for (int c = 0; c < 5; ++c) {
           double acc = 0.0;
           for (int q = 0; q < 5; ++q) acc += J[r][q] * Cf[P(q, c)];
           X[r][c] = acc;
         }
-      // Cholesky Cp = L L^T (lower triangle in place of the packed upper one, by rows)
-      double L[5][5];
+      for (int c = 0; c < 5; ++c) X[4][c] = Cf[P(4, c)];
+      // Cholesky Cp = L L^T, with the reciprocals of its diagonal (one division a row)
+      double L[5][5], inv[5];
       for (int r = 0; r < 5; ++r)
         for (int c = 0; c <= r; ++c) {
           double acc = Cp[P(r, c)];
@@ -82,8 +83,9 @@ __global__ void __launch_bounds__(128) smooth_states_kernel(FitArgs a) {
           if (r == c) {
             spd = spd && acc > 0.0;
             L[r][r] = sqrt(acc);
+            inv[r] = 1.0 / L[r][r];
           } else {
-            L[r][c] = acc / L[c][c];
+            L[r][c] = acc * inv[c];
           }
         }
       if (!spd) break;
@@ -91,12 +93,12 @@ __global__ void __launch_bounds__(128) smooth_states_kernel(FitArgs a) {
         for (int r = 0; r < 5; ++r) {
           double acc = X[r][c];
           for (int q = 0; q < r; ++q) acc -= L[r][q] * X[q][c];
-          X[r][c] = acc / L[r][r];
+          X[r][c] = acc * inv[r];
         }
         for (int r = 4; r >= 0; --r) {
           double acc = X[r][c];
           for (int q = r + 1; q < 5; ++q) acc -= L[q][r] * X[q][c];
-          X[r][c] = acc / L[r][r];
+          X[r][c] = acc * inv[r];
         }
       }
       // A = X^T: A[r][c] = X[c][r]
