@@ -754,6 +754,21 @@ __device__ __forceinline__ double cov_to_d(float x) { return f2d(x); }
 __device__ __forceinline__ float cov_to_f(double x) { return d2f(x); }
 __device__ __forceinline__ float cov_to_f(float x) { return x; }
 
+// acc - (a0 b0 + a1 b1) as two fused multiply-adds (no separate multiply and add).
+__device__ __forceinline__ double sub2(double acc, double a0, double b0, double a1, double b1) {
+  return fma(-a1, b1, fma(-a0, b0, acc));
+}
+__device__ __forceinline__ float sub2(float acc, float a0, float b0, float a1, float b1) {
+  return fmaf(-a1, b1, fmaf(-a0, b0, acc));
+}
+// acc + (a0 b0 + a1 b1) into an FP64 accumulator: fused in FP64, or the FP32 sum added.
+__device__ __forceinline__ double add2d(double acc, double a0, double b0, double a1, double b1) {
+  return fma(a1, b1, fma(a0, b0, acc));
+}
+__device__ __forceinline__ double add2d(double acc, float a0, float b0, float a1, float b1) {
+  return acc + f2d(a0 * b0 + a1 * b1);
+}
+
 __host__ __device__ constexpr int state_doubles(int place) { return place == 0 ? 0 : (place == 1 ? 25 : 45); }
 
 // ------------------------------------------------------------------ group-per-track helpers
@@ -880,7 +895,7 @@ __device__ __forceinline__ uint32_t kalman_update(const FitArgs& a, uint32_t m, 
     K[j][1] = U0 * Si01 + U1 * Si11;
   }
 #pragma unroll
-  for (int j = 0; j < 5; ++j) p[j] += cov_to_d(K[j][0] * r0 + K[j][1] * r1);
+  for (int j = 0; j < 5; ++j) p[j] = add2d(p[j], K[j][0], r0, K[j][1], r1);
   if constexpr (kG == 1) {
     // X = (I - K H) C ; C' = X - (X H^T - K V) K^T
     U X[5][5];
@@ -891,8 +906,8 @@ __device__ __forceinline__ uint32_t kalman_update(const FitArgs& a, uint32_t m, 
     U Y[5][2];
 #pragma unroll
     for (int r_ = 0; r_ < 5; ++r_) {
-      Y[r_][0] = X[r_][0] - (K[r_][0] * V00 + K[r_][1] * V01);
-      Y[r_][1] = X[r_][1] - (K[r_][0] * V01 + K[r_][1] * V11);
+      Y[r_][0] = sub2(X[r_][0], K[r_][0], V00, K[r_][1], V01);
+      Y[r_][1] = sub2(X[r_][1], K[r_][0], V01, K[r_][1], V11);
     }
 #pragma unroll
     for (int r_ = 0; r_ < 5; ++r_)
@@ -909,8 +924,8 @@ __device__ __forceinline__ uint32_t kalman_update(const FitArgs& a, uint32_t m, 
       Xg[c_] = Cgc - Kg0 * C[S(0, c_)] - Kg1 * C[S(1, c_)];
       X4[c_] = C[S(4, c_)] - K[4][0] * C[S(0, c_)] - K[4][1] * C[S(1, c_)];
     }
-    const U Yg0 = Xg[0] - (Kg0 * V00 + Kg1 * V01), Yg1 = Xg[1] - (Kg0 * V01 + Kg1 * V11);
-    const U Y40 = X4[0] - (K[4][0] * V00 + K[4][1] * V01), Y41 = X4[1] - (K[4][0] * V01 + K[4][1] * V11);
+    const U Yg0 = sub2(Xg[0], Kg0, V00, Kg1, V01), Yg1 = sub2(Xg[1], Kg0, V01, Kg1, V11);
+    const U Y40 = sub2(X4[0], K[4][0], V00, K[4][1], V01), Y41 = sub2(X4[1], K[4][0], V01, K[4][1], V11);
 #pragma unroll
     for (int c_ = 0; c_ < 5; ++c_) Cn[c_] = Xg[c_] - Yg0 * K[c_][0] - Yg1 * K[c_][1];
     const U C44 = X4[4] - Y40 * K[4][0] - Y41 * K[4][1];
@@ -1500,24 +1515,25 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
       for (int j = 0; j < 5; ++j) {
         W[j][0] = st.P(j, 0) * Si00 + st.P(j, 1) * Si01;
         W[j][1] = st.P(j, 0) * Si01 + st.P(j, 1) * Si11;
-        st.dl(j) += cov_to_d(W[j][0] * r0 + W[j][1] * r1);
+        st.dl(j) = add2d(st.dl(j), W[j][0], r0, W[j][1], r1);
       }
 #pragma unroll
       for (int r_ = 0; r_ < 5; ++r_)
 #pragma unroll
-        for (int c_ = r_; c_ < 5; ++c_) st.E(S(r_, c_)) -= W[r_][0] * st.P(c_, 0) + W[r_][1] * st.P(c_, 1);
+        for (int c_ = r_; c_ < 5; ++c_)
+          st.E(S(r_, c_)) = sub2(st.E(S(r_, c_)), W[r_][0], st.P(c_, 0), W[r_][1], st.P(c_, 1));
 #pragma unroll
       for (int r_ = 0; r_ < 5; ++r_) {
         const U R0 = st.P(r_, 0), R1 = st.P(r_, 1);
 #pragma unroll
-        for (int c_ = 0; c_ < 5; ++c_) st.P(r_, c_) -= R0 * K[c_][0] + R1 * K[c_][1];
+        for (int c_ = 0; c_ < 5; ++c_) st.P(r_, c_) = sub2(st.P(r_, c_), R0, K[c_][0], R1, K[c_][1]);
       }
       } else {
         // rows gl and 4; columns 0 and 1 of R from every row's lane
         const U Wg0 = Pg[0] * Si00 + Pg[1] * Si01, Wg1 = Pg[0] * Si01 + Pg[1] * Si11;
         const U W40 = P4[0] * Si00 + P4[1] * Si01, W41 = P4[0] * Si01 + P4[1] * Si11;
-        dlg += cov_to_d(Wg0 * r0 + Wg1 * r1);
-        dl4 += cov_to_d(W40 * r0 + W41 * r1);
+        dlg = add2d(dlg, Wg0, r0, Wg1, r1);
+        dl4 = add2d(dl4, W40, r0, W41, r1);
         U R0c[5], R1c[5];
 #pragma unroll
         for (int c_ = 0; c_ < 4; ++c_) {
@@ -1527,13 +1543,13 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
         R0c[4] = P4[0];
         R1c[4] = P4[1];
 #pragma unroll
-        for (int c_ = 0; c_ < 5; ++c_) Eg[c_] -= Wg0 * R0c[c_] + Wg1 * R1c[c_];
-        E44 -= W40 * R0c[4] + W41 * R1c[4];
+        for (int c_ = 0; c_ < 5; ++c_) Eg[c_] = sub2(Eg[c_], Wg0, R0c[c_], Wg1, R1c[c_]);
+        E44 = sub2(E44, W40, R0c[4], W41, R1c[4]);
         const U Rg0 = Pg[0], Rg1 = Pg[1], R40 = P4[0], R41 = P4[1];
 #pragma unroll
         for (int c_ = 0; c_ < 5; ++c_) {
-          Pg[c_] -= Rg0 * K[c_][0] + Rg1 * K[c_][1];
-          P4[c_] -= R40 * K[c_][0] + R41 * K[c_][1];
+          Pg[c_] = sub2(Pg[c_], Rg0, K[c_][0], Rg1, K[c_][1]);
+          P4[c_] = sub2(P4[c_], R40, K[c_][0], R41, K[c_][1]);
         }
       }
     }
