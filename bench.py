@@ -64,12 +64,31 @@ FLOPS_MAP = {
 }
 
 
-# DRAM bytes per track of the fit kernel (dram__bytes_read.sum + dram__bytes_write.sum of one
-# ncu capture, divided by the capture's tracks; traffic grows with the tracks of a launch).
-# Keyed by (workload, variant, register cap of the launched kernel); a kernel change voids the
-# entry. Barrel, learned start, 64 registers: 20-event batch, 279,450 tracks, 128 x 8 blocks.
-TRAFFIC_PER_TRACK = {("barrel", "mixed_learned", 64): (5.732764e9 + 4.978447e9) / 279450}
-TRAFFIC_CAPTURE = {("barrel", "mixed_learned", 64): "ncu capture of 279,450 tracks (20 events), scaled by tracks"}
+# Hardware counts of one ncu capture of the fit kernel on a 20-event batch (279,450 tracks,
+# 3,243,973 measurements; `--events 20 --shape ...`, one launch after three warm-ups): DRAM bytes
+# (dram__bytes_read.sum + dram__bytes_write.sum), executed FP64 flops (2 dfma + dadd + dmul,
+# thread-level) and executed FP32 flops (2 ffma + fadd + fmul + 4 ffma2 + 2 fadd2 + 2 fmul2), with
+# the FLOPS model's count for the same launch. Traffic and FP32 flops grow with the tracks of a
+# launch and are scaled by tracks to a full launch. Keyed by (workload, variant, register cap of
+# the launched kernel); a kernel change voids the entries (profiles/ keeps the commands).
+CAPTURES = {
+    ("barrel", "mixed_learned", 128): {"tracks": 279450, "hits_after_first": 2964523, "attempts": 5100711,
+                                       "rejected": 19373, "shape": "128,4,32,128", "dram_bytes": 2020045568,
+                                       "fp64_exec": 2525591617, "fp64_model": 2414427971, "fp32_exec": 5245145883},
+    ("barrel", "mixed", 128): {"tracks": 279450, "hits_after_first": 2964523, "attempts": 5014955, "rejected": 143604,
+                               "shape": "64,8,32,128", "dram_bytes": 1952446720,
+                               "fp64_exec": 2522392577, "fp64_model": 2411222079, "fp32_exec": 5161190452},
+    ("barrel", "fp64", 128): {"tracks": 279450, "hits_after_first": 2964523, "attempts": 5014958, "rejected": 143611,
+                              "shape": "128,4,32,128", "dram_bytes": 2871720960,
+                              "fp64_exec": 8183930686, "fp64_model": 6938730754, "fp32_exec": 71595040},
+}
+
+
+def fp32_peak_tflops(sm_mhz: float | None):
+    """FP32 (CUDA-core) peak of GB300 from unit counts and clock: 152 SMs x 128 FP32 lanes x
+    2 flop/clk (80.5 TFLOP/s at the 2070 MHz maximum clock)."""
+    mhz = sm_mhz or 2070.0
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
 
 
 def parse():
@@ -93,6 +112,8 @@ def parse():
     ap.add_argument("--shape", default=None,
                     help="fixed launch shape 'threads,blocks_per_sm,tracks_per_warp,registers[,lanes]' for every "
                          "variant (registers 128 or 64 apply to FP64 and mixed, 128 to mixed_fp32; lanes 1 or 4)")
+    ap.add_argument("--tol", type=float, default=None,
+                    help="RKN local error tolerance in mm for every variant (default: the library's 1e-4)")
     ap.add_argument("--no-seeds", action="store_true",
                     help="skip the seed-estimation kernel, the chain from estimated seeds and track finding")
     ap.add_argument("--streams", action="store_true",
@@ -744,7 +765,7 @@ def main():
         tt = make_training_batch(args, rank)
         tb = tkf.Batch.from_arrays(tt.offsets, tt.meas, tt.sid, tt.seed_par, tt.seed_cov).to(f"cuda:{local}")
         t0 = time.perf_counter()
-        proposer, info = learn.build_proposer(ctx, geo, fld, tb, tkf.MIXED, mass=w.mass)
+        proposer, info = learn.build_proposer(ctx, geo, fld, tb, tkf.MIXED, mass=w.mass, tol=args.tol)
         learn_info = {"records": info["records"], "final_loss": round(info["epoch_loss"][-1], 4),
                       "bias_shift": round(info["bias_shift"], 4), "train_s": round(time.perf_counter() - t0, 2),
                       "tracks": tt.n_tracks}
@@ -764,6 +785,8 @@ def main():
             opts.block_threads, opts.blocks_per_sm, opts.tracks_per_warp = th, bps, tpw
             opts.max_registers = 255 if two_filter or (base == "mixed_fp32" and regs == 64) else regs
             opts.lanes_per_track = lanes[0] if lanes and base != "mixed_fp32" and not two_filter else 0
+        if args.tol is not None:
+            opts.tol = args.tol
         if variant.endswith("learned"):
             opts.step_mode, opts.mlp = tkf.STEP_LEARNED, proposer
         out = tkf.alloc_outputs(n_tracks, dev.offsets.device, steps=True, states_meas=n_meas if all_states else None)
@@ -877,19 +900,30 @@ def main():
     hv = results[head]
     head_shape = hv["shape"] or [None] * 5
     # the captured kernel: one lane a track (a group shape is another kernel)
-    traffic_key = (args.workload, head, head_shape[3]) if (head_shape[4:] or [1])[0] == 1 else None
+    cap_key = (args.workload, head, head_shape[3]) if (head_shape[4:] or [1])[0] == 1 else None
+    cap = CAPTURES.get(cap_key)
     # no FP64 flop count for the two-filter variants: their roofline stays null
-    achieved = hv["flops"] / (hv["kernel_ms"] * 1e-3) / 1e12 if hv["flops"] is not None else None
+    kernel_s = hv["kernel_ms"] * 1e-3
+    achieved = hv["flops"] / kernel_s / 1e12 if hv["flops"] is not None else None
+    algo_bytes = host.nbytes() + n_tracks * (5 * 8 + 15 * 8 + 8 + 4 + 4 + 8)
     roof = {"bound": "alu", "kernel": f"fit_persistent_kernel<{head}>", "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak if achieved is not None else None,
-            "traffic": (TRAFFIC_PER_TRACK[traffic_key] * n_tracks if traffic_key in TRAFFIC_PER_TRACK else None),
-            "traffic_note": (TRAFFIC_CAPTURE.get(traffic_key, "no capture for this kernel variant") +
-                             "; algorithmic bytes (inputs + outputs) per launch: "
-                             f"{host.nbytes() + n_tracks * (5 * 8 + 15 * 8 + 8 + 4 + 4 + 8)}; above them: local-memory "
-                             "spill traffic of the register-capped kernel"),
+            "traffic": cap["dram_bytes"] / cap["tracks"] * n_tracks if cap else None,
+            "traffic_note": ((f"ncu capture of {cap['tracks']} tracks (20 events, shape {cap['shape']}), scaled by "
+                              "tracks" if cap else "no capture for this kernel variant") +
+                             f"; algorithmic bytes (inputs + outputs) per launch: {algo_bytes}; above them: "
+                             "local-memory spill traffic of the register-capped kernel"),
             "fp64_flop_per_launch": hv["flops"],
+            "fp64_executed_over_algorithmic": cap["fp64_exec"] / cap["fp64_model"] if cap else None,
             "note": "FP64 CUDA-core pipe (the bound of both variants); peak derived from "
                     "152 SMs x 4 flop/clk x 2070 MHz; 1.20 TFLOP/s measured by an FMA probe"}
+    if cap:
+        f32 = cap["fp32_exec"] / cap["tracks"] * n_tracks
+        p32 = fp32_peak_tflops(None)
+        roof["fp32"] = {"achieved": f32 / kernel_s / 1e12, "peak": p32, "unit": "TFLOP/s",
+                        "frac": f32 / kernel_s / 1e12 / p32, "flop_per_launch": f32,
+                        "note": "executed FP32 flops of the ncu capture scaled by tracks; peak derived from "
+                                "152 SMs x 128 lanes x 2 flop/clk x 2070 MHz"}
     line = {
         "metric": METRIC,
         "value": aggregate_throughput(n_tracks, ws, ms_max * 1e-3),
@@ -911,7 +945,8 @@ def main():
                    "l2": (f"inputs {host.nbytes() / 1e9:.2f} GB > L2, no flush" if flush is None else
                           f"inputs {host.nbytes() / 1e9:.3f} GB: L2 flushed (258 MB write) before every step, "
                           "steps timed one by one"),
-                   "step_mode": "learned starting step + adaptive" if head.endswith("learned") else "adaptive"},
+                   "step_mode": "learned starting step + adaptive" if head.endswith("learned") else "adaptive",
+                   "tol_mm": args.tol if args.tol is not None else 1e-4},
         # per step: key, scan and scatter kernels of the ordering, the proposal pre-pass
         # (learned), the persistent fit (plus one memset node)
         "gpu_launches": (5 if head.endswith("learned") else 4) * args.steps,

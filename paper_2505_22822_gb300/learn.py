@@ -19,7 +19,7 @@ from __future__ import annotations
 from . import MLP_PARAMS, MLP_RECORD, Mlp, Options, STEP_ADAPTIVE, fit, mlp_calibrate, mlp_init, mlp_train
 
 
-def record_steps(ctx, geo, field, batch, precision: int, capacity: int = 2_000_000, mass=None):
+def record_steps(ctx, geo, field, batch, precision: int, capacity: int = 2_000_000, mass=None, tol=None):
     """Training records [n, 13] (CUDA float32) from the plain stepper on ``batch``."""
     import torch
     dev = batch.offsets.device
@@ -28,6 +28,8 @@ def record_steps(ctx, geo, field, batch, precision: int, capacity: int = 2_000_0
     opts = Options(precision=precision, step_mode=STEP_ADAPTIVE, records=rec, record_count=cnt)
     if mass is not None:
         opts.mass = mass
+    if tol is not None:
+        opts.tol = tol
     fit(ctx, geo, field, batch, opts)
     torch.cuda.synchronize()
     n = min(int(cnt.item()), capacity)
@@ -56,9 +58,10 @@ def calibrate(ctx, params, records, quantile: float = 0.05) -> float:
 
 
 def build_proposer(ctx, geo, field, batch, precision: int, epochs: int = 8, quantile: float = 0.05,
-                   mass=None) -> tuple[Mlp, dict]:
-    """Records -> training -> calibration -> BF16 handle, with a summary of the run."""
-    rec = record_steps(ctx, geo, field, batch, precision, mass=mass)
+                   mass=None, tol=None) -> tuple[Mlp, dict]:
+    """Records (at the RKN tolerance `tol`, default the library's) -> training -> calibration ->
+    BF16 handle, with a summary of the run."""
+    rec = record_steps(ctx, geo, field, batch, precision, mass=mass, tol=tol)
     params, losses = train(ctx, rec, epochs=epochs)
     q = calibrate(ctx, params, rec, quantile)
     return Mlp.from_params(ctx, params), {"records": int(rec.shape[0]),
