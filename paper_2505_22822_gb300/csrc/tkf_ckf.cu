@@ -474,27 +474,67 @@ __global__ void ckf_meas_f32_kernel(const double* __restrict__ loc0, const doubl
     out[i] = make_float4(float(loc0[i]), float(loc1[i]), float(v00[i]), float(v11[i]));
 }
 
-template <bool kMixed, class F>
-__global__ void __launch_bounds__(kCkfBlock) find_tracks_kernel(const CkfArgs a, const F fld) {
-  __shared__ double face_r[kCkfMaxLayers];
-  for (uint32_t li = threadIdx.x; li < a.n_layers; li += blockDim.x) {
-    const double* l = a.layers + 8 * li;
-    face_r[li] = l[0] == 0.0 ? barrel_face(l) : 0.0;
+// ---- the search as phases: every step of every seed is three launches over all seeds,
+// (1) one thread per branch slot predicts its branch to the next module, (2) one thread per slot
+// gates that module's measurements and makes the branch's children, (3) one thread per seed
+// numbers the children in creation order, keeps the best ended branch and the beam. Every
+// thread of a launch runs the same phase, so the lanes of a warp stay in step (one thread per
+// seed running all phases of its branches in turn left two thirds of the lanes idle), and the
+// branches of a seed are predicted in parallel. The arithmetic of every branch, the order in
+// which children are made and the ranking are those of the sequential search, so the candidates
+// are the same.
+
+// One branch's prediction for the current step, and the children it made.
+struct CkfPred {
+  double pp[5], pdir[4], Cp[15], h;
+  int32_t target;  // next module; -1: the branch ends (nothing ahead, or the entries are full); -2: no branch
+  uint32_t nk;     // children with a measurement
+  uint32_t hole;   // 1: a child with a hole
+  uint32_t pad;
+};
+
+// Per-seed search state.
+struct CkfSeed {
+  uint32_t n_act;   // branches in the beam (0: the search is over)
+  uint32_t order;   // creation counter of the children
+  uint32_t have_best;
+  uint32_t first;   // 1 before the first step (the seed's own surface)
+};
+
+struct CkfWork {
+  CkfBranch* slots;  // per seed: beam B, children B (C + 1), best 1
+  CkfPred* pred;     // per seed: B
+  CkfSeed* seeds;    // per seed
+};
+
+__device__ __forceinline__ CkfBranch* seed_slots(const CkfWork& w, uint32_t t, uint32_t B) {
+  return w.slots + size_t(t) * slots_per_seed(B);
+}
+
+// Outputs of seed i from its best ended branch.
+__device__ void write_candidate(const CkfArgs& a, uint32_t i, const CkfBranch* best, bool have_best) {
+  const uint32_t n = a.n_seeds;
+  const uint32_t ne = have_best ? best->n_entries : 0;
+  a.n_entries[i] = ne;
+  a.n_meas_out[i] = have_best ? best->n_meas : 0;
+  a.chi2[i] = have_best ? best->chi2 : 0.0;
+  for (uint32_t j = 0; j < a.max_entries; ++j) {
+    a.entry_sid[size_t(j) * n + i] = j < ne ? best->e_sid[j] : 0u;
+    a.entry_meas[size_t(j) * n + i] = j < ne ? best->e_meas[j] : -1;
   }
-  __syncthreads();
+}
+
+// The seed's starting branch (thread t finds seed perm[t]); a seed on a missing surface or event
+// gets no candidate at once.
+__global__ void __launch_bounds__(kCkfBlock) ckf_init_kernel(const CkfArgs a, CkfWork w) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= a.n_seeds) return;
-  const uint32_t i = a.perm[t];  // the seed this thread finds (the branch slots are the thread's)
-  const uint32_t n = a.n_seeds, B = a.beam;
-  CkfBranch* act = static_cast<CkfBranch*>(a.ws) + size_t(t) * slots_per_seed(B);
-  CkfBranch* kids = act + B;
-  CkfBranch* best = kids + B * (kCkfChildren + 1);
-  bool have_best = false;
+  const uint32_t i = a.perm[t], n = a.n_seeds;
+  CkfSeed st{0u, 1u, 0u, 1u};
   const uint32_t seed_sid = a.seed_sid[i];
   const uint32_t ev = a.seed_event ? a.seed_event[i] : 0u;
-  const uint32_t* __restrict__ moff = a.meas_off + size_t(ev) * (a.n_surf + 1);  // this event's offsets
   if (seed_sid < a.n_surf && ev < a.n_events) {
-    CkfBranch& b0 = act[0];
+    CkfBranch& b0 = seed_slots(w, t, a.beam)[0];
     for (int j = 0; j < 5; ++j) b0.p[j] = a.seed_par[size_t(j) * n + i];
     sincos(b0.p[2], &b0.dir[0], &b0.dir[1]);
     sincos(b0.p[3], &b0.dir[2], &b0.dir[3]);
@@ -506,134 +546,204 @@ __global__ void __launch_bounds__(kCkfBlock) find_tracks_kernel(const CkfArgs a,
     b0.n_meas = b0.holes = b0.n_entries = 0;
     b0.order = 0;
     b0.sid = -1;
-    uint32_t n_act = 1, order = 1;
-    bool first = true;
-    // every step adds an entry to each surviving branch: at most max_entries + 1 steps
-    for (uint32_t step = 0; n_act > 0 && step <= a.max_entries + 1; ++step) {
-      uint32_t n_kids = 0;
-      for (uint32_t bi = 0; bi < n_act; ++bi) {
-        const CkfBranch& br = act[bi];
-        double pp[5], pdir[4], Cp[15], h = br.h_ctrl;
-        int target;
-        if (first) {
-          target = int(seed_sid);
-          for (int j = 0; j < 5; ++j) pp[j] = br.p[j];
-          for (int j = 0; j < 4; ++j) pdir[j] = br.dir[j];
-          for (int j = 0; j < 15; ++j) Cp[j] = br.C[j];
-        } else {
-          target = br.n_entries >= a.max_entries ? -1 : predict<kMixed>(a, fld, face_r, br, pp, pdir, Cp, h);
-        }
-        if (target < 0) {  // the branch ends
-          if (!have_best || better(br, *best)) {
-            copy_branch(*best, br, br.n_entries);
-            have_best = true;
-          }
-          continue;
-        }
-        // the (at most 3) compatible measurements with the lowest chi2 (ties: lower index)
-        double kc2[kCkfChildren];
-        uint32_t km[kCkfChildren];
-        int nk = 0;
-        const uint32_t m_end = moff[target + 1] < a.n_meas ? moff[target + 1] : a.n_meas;
-        // chi2 = r^T S^-1 r >= r0^2 / S00 and >= r1^2 / S11 (S positive definite): a measurement
-        // whose residual fails the gate in one coordinate alone is skipped before the full chi2.
-        // The margin keeps the skip exact under rounding (the full test would reject it too).
-        const double gate = a.chi2_max * (1.0 + 1e-6);
-        // the same bound first in FP32, on FP32 copies of the measurements: it skips only where
-        // the rounding of every FP32 operand (at most 1e-6 of |loc| + |p| + |r| in the residual,
-        // 1e-4 of S) cannot bring the residual back inside the gate
-        const float p0f = d2f(pp[0]), p1f = d2f(pp[1]), c00f = d2f(Cp[S(0, 0)]), c11f = d2f(Cp[S(1, 1)]);
-        const float gatef = float(a.chi2_max) * 1.0001f;
-        for (uint32_t mi = moff[target]; mi < m_end; ++mi) {
-          const float4 mf = a.meas_f[mi];  // loc0, loc1, V00, V11
-          const float r0f = mf.x - p0f, r1f = mf.y - p1f;
-          const float e0 = fabsf(r0f) - 1e-6f * (fabsf(mf.x) + fabsf(p0f) + fabsf(r0f));
-          const float e1 = fabsf(r1f) - 1e-6f * (fabsf(mf.y) + fabsf(p1f) + fabsf(r1f));
-          if ((e0 > 0.0f && e0 * e0 > gatef * (c00f + mf.z)) || (e1 > 0.0f && e1 * e1 > gatef * (c11f + mf.w)))
-            continue;
-          const double q0 = a.loc0[mi] - pp[0], q1 = a.loc1[mi] - pp[1];
-          if (q0 * q0 > gate * (Cp[S(0, 0)] + a.v00[mi]) || q1 * q1 > gate * (Cp[S(1, 1)] + a.v11[mi])) continue;
-          double c2;
-          if (!meas_chi2(pp, Cp, a.loc0[mi], a.loc1[mi], a.v00[mi], a.v01[mi], a.v11[mi], c2)) continue;
-          if (!(c2 < a.chi2_max)) continue;
-          int pos = nk;
-          while (pos > 0 && (c2 < kc2[pos - 1] || (c2 == kc2[pos - 1] && mi < km[pos - 1]))) --pos;
-          if (pos >= kCkfChildren) continue;
-          for (int q = (nk < kCkfChildren ? nk : kCkfChildren - 1); q > pos; --q) {
-            kc2[q] = kc2[q - 1];
-            km[q] = km[q - 1];
-          }
-          kc2[pos] = c2;
-          km[pos] = mi;
-          if (nk < kCkfChildren) ++nk;
-        }
-        for (int q = 0; q < nk; ++q) {
-          CkfBranch& ch = kids[n_kids++];
-          copy_branch(ch, br, br.n_entries);
-          for (int j = 0; j < 5; ++j) ch.p[j] = pp[j];
-          for (int j = 0; j < 15; ++j) ch.C[j] = Cp[j];
-          const uint32_t mi = km[q];
-          double c2;
-          update(ch.p, ch.C, a.loc0[mi], a.loc1[mi], a.v00[mi], a.v01[mi], a.v11[mi], c2);
-          // filtered direction: the predicted one turned by the update's angle increments
-          double sd, cd, se, ce;
-          small_sincos(ch.p[2], sd, cd);
-          small_sincos(ch.p[3], se, ce);
-          ch.dir[0] = pdir[0] * cd + pdir[1] * sd;
-          ch.dir[1] = pdir[1] * cd - pdir[0] * sd;
-          ch.dir[2] = pdir[2] * ce + pdir[3] * se;
-          ch.dir[3] = pdir[3] * ce - pdir[2] * se;
-          ch.p[2] = 0.0;
-          ch.p[3] = 0.0;
-          ch.h_ctrl = h;
-          ch.chi2 += c2;
-          ch.n_meas += 1;
-          ch.holes = 0;
-          ch.sid = target;
-          ch.e_sid[ch.n_entries] = uint32_t(target);
-          ch.e_meas[ch.n_entries] = int32_t(mi);
-          ch.n_entries += 1;
-          ch.order = order++;
-        }
-        if (br.holes < a.max_holes) {
-          CkfBranch& ch = kids[n_kids++];
-          copy_branch(ch, br, br.n_entries);
-          for (int j = 0; j < 5; ++j) ch.p[j] = pp[j];
-          for (int j = 0; j < 4; ++j) ch.dir[j] = pdir[j];
-          for (int j = 0; j < 15; ++j) ch.C[j] = Cp[j];
-          ch.h_ctrl = h;
-          ch.holes += 1;
-          ch.sid = target;
-          ch.e_sid[ch.n_entries] = uint32_t(target) | TKF_SID_NO_MEASUREMENT;
-          ch.e_meas[ch.n_entries] = -1;
-          ch.n_entries += 1;
-          ch.order = order++;
-        } else if (nk == 0 && (!have_best || better(br, *best))) {
-          copy_branch(*best, br, br.n_entries);  // one hole too many: ends before this surface
-          have_best = true;
-        }
-      }
-      first = false;
-      // the beam: the best B children, in rank order (at most 8 x 4 children: a bit mask of the taken)
-      n_act = n_kids < B ? n_kids : B;
-      uint32_t taken = 0;
-      for (uint32_t q = 0; q < n_act; ++q) {
-        int pick = -1;
-        for (uint32_t j = 0; j < n_kids; ++j)
-          if (!((taken >> j) & 1u) && (pick < 0 || better(kids[j], kids[pick]))) pick = int(j);
-        taken |= 1u << pick;
-        copy_branch(act[q], kids[pick], kids[pick].n_entries);
-      }
+    st.n_act = 1;
+  } else {
+    write_candidate(a, i, nullptr, false);
+  }
+  w.seeds[t] = st;
+}
+
+// Phase 1: the prediction of branch bi of seed slot t (thread t B + bi).
+template <bool kMixed, class F>
+__global__ void __launch_bounds__(kCkfBlock) ckf_predict_kernel(const CkfArgs a, const F fld, CkfWork w) {
+  __shared__ double face_r[kCkfMaxLayers];
+  for (uint32_t li = threadIdx.x; li < a.n_layers; li += blockDim.x) {
+    const double* l = a.layers + 8 * li;
+    face_r[li] = l[0] == 0.0 ? barrel_face(l) : 0.0;
+  }
+  __syncthreads();
+  const uint32_t B = a.beam;
+  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= a.n_seeds * B) return;
+  const uint32_t t = g / B, bi = g % B;
+  const CkfSeed st = w.seeds[t];
+  CkfPred& pr = w.pred[g];
+  if (bi >= st.n_act) {
+    pr.target = -2;
+    return;
+  }
+  const CkfBranch& br = seed_slots(w, t, B)[bi];
+  int target;
+  if (st.first) {
+    target = int(a.seed_sid[a.perm[t]]);
+    for (int j = 0; j < 5; ++j) pr.pp[j] = br.p[j];
+    for (int j = 0; j < 4; ++j) pr.pdir[j] = br.dir[j];
+    for (int j = 0; j < 15; ++j) pr.Cp[j] = br.C[j];
+    pr.h = br.h_ctrl;
+  } else {
+    double pp[5], pdir[4], Cp[15], h = br.h_ctrl;
+    target = br.n_entries >= a.max_entries ? -1 : predict<kMixed>(a, fld, face_r, br, pp, pdir, Cp, h);
+    if (target >= 0) {
+      for (int j = 0; j < 5; ++j) pr.pp[j] = pp[j];
+      for (int j = 0; j < 4; ++j) pr.pdir[j] = pdir[j];
+      for (int j = 0; j < 15; ++j) pr.Cp[j] = Cp[j];
+      pr.h = h;
     }
   }
-  const uint32_t ne = have_best ? best->n_entries : 0;
-  a.n_entries[i] = ne;
-  a.n_meas_out[i] = have_best ? best->n_meas : 0;
-  a.chi2[i] = have_best ? best->chi2 : 0.0;
-  for (uint32_t j = 0; j < a.max_entries; ++j) {
-    a.entry_sid[size_t(j) * n + i] = j < ne ? best->e_sid[j] : 0u;
-    a.entry_meas[size_t(j) * n + i] = j < ne ? best->e_meas[j] : -1;
+  pr.target = target;
+}
+
+// Phase 2: the gate over the predicted module's measurements and the children of branch bi.
+__global__ void __launch_bounds__(kCkfBlock) ckf_gate_kernel(const CkfArgs a, CkfWork w) {
+  const uint32_t B = a.beam;
+  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= a.n_seeds * B) return;
+  const uint32_t t = g / B, bi = g % B;
+  CkfPred& pr = w.pred[g];
+  const int target = pr.target;
+  if (target < 0) {
+    pr.nk = 0;
+    pr.hole = 0;
+    return;
   }
+  const uint32_t i = a.perm[t];
+  const uint32_t ev = a.seed_event ? a.seed_event[i] : 0u;
+  const uint32_t* __restrict__ moff = a.meas_off + size_t(ev) * (a.n_surf + 1);  // this event's offsets
+  CkfBranch* slots = seed_slots(w, t, B);
+  const CkfBranch& br = slots[bi];
+  CkfBranch* kids = slots + B + bi * (kCkfChildren + 1);
+  double pp[5], pdir[4], Cp[15];
+  for (int j = 0; j < 5; ++j) pp[j] = pr.pp[j];
+  for (int j = 0; j < 4; ++j) pdir[j] = pr.pdir[j];
+  for (int j = 0; j < 15; ++j) Cp[j] = pr.Cp[j];
+  const double h = pr.h;
+  // the (at most 3) compatible measurements with the lowest chi2 (ties: lower index)
+  double kc2[kCkfChildren];
+  uint32_t km[kCkfChildren];
+  int nk = 0;
+  const uint32_t m_end = moff[target + 1] < a.n_meas ? moff[target + 1] : a.n_meas;
+  // chi2 = r^T S^-1 r >= r0^2 / S00 and >= r1^2 / S11 (S positive definite): a measurement
+  // whose residual fails the gate in one coordinate alone is skipped before the full chi2.
+  // The margin keeps the skip exact under rounding (the full test would reject it too).
+  const double gate = a.chi2_max * (1.0 + 1e-6);
+  // the same bound first in FP32, on FP32 copies of the measurements: it skips only where
+  // the rounding of every FP32 operand (at most 1e-6 of |loc| + |p| + |r| in the residual,
+  // 1e-4 of S) cannot bring the residual back inside the gate
+  const float p0f = d2f(pp[0]), p1f = d2f(pp[1]), c00f = d2f(Cp[S(0, 0)]), c11f = d2f(Cp[S(1, 1)]);
+  const float gatef = float(a.chi2_max) * 1.0001f;
+  for (uint32_t mi = moff[target]; mi < m_end; ++mi) {
+    const float4 mf = a.meas_f[mi];  // loc0, loc1, V00, V11
+    const float r0f = mf.x - p0f, r1f = mf.y - p1f;
+    const float e0 = fabsf(r0f) - 1e-6f * (fabsf(mf.x) + fabsf(p0f) + fabsf(r0f));
+    const float e1 = fabsf(r1f) - 1e-6f * (fabsf(mf.y) + fabsf(p1f) + fabsf(r1f));
+    if ((e0 > 0.0f && e0 * e0 > gatef * (c00f + mf.z)) || (e1 > 0.0f && e1 * e1 > gatef * (c11f + mf.w))) continue;
+    const double q0 = a.loc0[mi] - pp[0], q1 = a.loc1[mi] - pp[1];
+    if (q0 * q0 > gate * (Cp[S(0, 0)] + a.v00[mi]) || q1 * q1 > gate * (Cp[S(1, 1)] + a.v11[mi])) continue;
+    double c2;
+    if (!meas_chi2(pp, Cp, a.loc0[mi], a.loc1[mi], a.v00[mi], a.v01[mi], a.v11[mi], c2)) continue;
+    if (!(c2 < a.chi2_max)) continue;
+    int pos = nk;
+    while (pos > 0 && (c2 < kc2[pos - 1] || (c2 == kc2[pos - 1] && mi < km[pos - 1]))) --pos;
+    if (pos >= kCkfChildren) continue;
+    for (int q = (nk < kCkfChildren ? nk : kCkfChildren - 1); q > pos; --q) {
+      kc2[q] = kc2[q - 1];
+      km[q] = km[q - 1];
+    }
+    kc2[pos] = c2;
+    km[pos] = mi;
+    if (nk < kCkfChildren) ++nk;
+  }
+  for (int q = 0; q < nk; ++q) {
+    CkfBranch& ch = kids[q];
+    copy_branch(ch, br, br.n_entries);
+    for (int j = 0; j < 5; ++j) ch.p[j] = pp[j];
+    for (int j = 0; j < 15; ++j) ch.C[j] = Cp[j];
+    const uint32_t mi = km[q];
+    double c2;
+    update(ch.p, ch.C, a.loc0[mi], a.loc1[mi], a.v00[mi], a.v01[mi], a.v11[mi], c2);
+    // filtered direction: the predicted one turned by the update's angle increments
+    double sd, cd, se, ce;
+    small_sincos(ch.p[2], sd, cd);
+    small_sincos(ch.p[3], se, ce);
+    ch.dir[0] = pdir[0] * cd + pdir[1] * sd;
+    ch.dir[1] = pdir[1] * cd - pdir[0] * sd;
+    ch.dir[2] = pdir[2] * ce + pdir[3] * se;
+    ch.dir[3] = pdir[3] * ce - pdir[2] * se;
+    ch.p[2] = 0.0;
+    ch.p[3] = 0.0;
+    ch.h_ctrl = h;
+    ch.chi2 += c2;
+    ch.n_meas += 1;
+    ch.holes = 0;
+    ch.sid = target;
+    ch.e_sid[ch.n_entries] = uint32_t(target);
+    ch.e_meas[ch.n_entries] = int32_t(mi);
+    ch.n_entries += 1;
+  }
+  uint32_t hole = 0;
+  if (br.holes < a.max_holes) {
+    CkfBranch& ch = kids[nk];
+    copy_branch(ch, br, br.n_entries);
+    for (int j = 0; j < 5; ++j) ch.p[j] = pp[j];
+    for (int j = 0; j < 4; ++j) ch.dir[j] = pdir[j];
+    for (int j = 0; j < 15; ++j) ch.C[j] = Cp[j];
+    ch.h_ctrl = h;
+    ch.holes += 1;
+    ch.sid = target;
+    ch.e_sid[ch.n_entries] = uint32_t(target) | TKF_SID_NO_MEASUREMENT;
+    ch.e_meas[ch.n_entries] = -1;
+    ch.n_entries += 1;
+    hole = 1;
+  }
+  pr.nk = uint32_t(nk);
+  pr.hole = hole;
+}
+
+// Phase 3, one thread per seed: the children numbered in creation order (branch by branch,
+// measurements by chi2, then the hole), the best ended branch, the beam of the best B children.
+// `last`: the final step; the candidate is written when the search is over.
+__global__ void __launch_bounds__(kCkfBlock) ckf_beam_kernel(const CkfArgs a, CkfWork w, uint32_t last) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.n_seeds) return;
+  CkfSeed st = w.seeds[t];
+  if (st.n_act == 0) return;  // over (candidate written)
+  const uint32_t B = a.beam;
+  CkfBranch* act = seed_slots(w, t, B);
+  CkfBranch* kids = act + B;
+  CkfBranch* best = kids + B * (kCkfChildren + 1);
+  const CkfPred* pr = w.pred + size_t(t) * B;
+  uint32_t kid_at[8 * (kCkfChildren + 1)];
+  uint32_t n_kids = 0;
+  for (uint32_t bi = 0; bi < st.n_act; ++bi) {
+    const CkfBranch& br = act[bi];
+    const uint32_t nc = pr[bi].target < 0 ? 0u : pr[bi].nk + pr[bi].hole;
+    for (uint32_t q = 0; q < nc; ++q) {
+      const uint32_t k = bi * (kCkfChildren + 1) + q;
+      kids[k].order = st.order++;
+      kid_at[n_kids++] = k;
+    }
+    // a branch ends when nothing lies ahead, or when one hole too many would follow with no
+    // compatible measurement
+    const bool ends = pr[bi].target < 0 || (pr[bi].nk == 0 && pr[bi].hole == 0);
+    if (ends && (!st.have_best || better(br, *best))) {
+      copy_branch(*best, br, br.n_entries);
+      st.have_best = 1;
+    }
+  }
+  st.first = 0;
+  // the beam: the best B children, in rank order
+  const uint32_t n_act = n_kids < B ? n_kids : B;
+  uint32_t taken = 0;
+  for (uint32_t q = 0; q < n_act; ++q) {
+    int pick = -1;
+    for (uint32_t j = 0; j < n_kids; ++j)
+      if (!((taken >> j) & 1u) && (pick < 0 || better(kids[kid_at[j]], kids[kid_at[pick]]))) pick = int(j);
+    taken |= 1u << pick;
+    copy_branch(act[q], kids[kid_at[pick]], kids[kid_at[pick]].n_entries);
+  }
+  st.n_act = last ? 0u : n_act;
+  if (st.n_act == 0) write_candidate(a, a.perm[t], best, st.have_best != 0);
+  w.seeds[t] = st;
 }
 
 template <class F>
@@ -652,26 +762,43 @@ cudaError_t launch_ckf(const CkfArgs& a_in, const F& fld, cudaStream_t stream) {
   ckf_order_scatter_kernel<<<og, 256, 0, stream>>>(a.seed_par, a.n_seeds, hist, perm);
   a.perm = perm;
   // FP32 copies of the measurements for the gate's first bound (16-byte aligned after the order)
-  float4* mf = reinterpret_cast<float4*>(
-      base + ((sizeof(uint32_t) * (kCkfOrderBins + size_t(a.n_seeds)) + 15) & ~size_t(15)));
+  char* mf_base = base + ((sizeof(uint32_t) * (kCkfOrderBins + size_t(a.n_seeds)) + 15) & ~size_t(15));
+  float4* mf = reinterpret_cast<float4*>(mf_base);
   if (a.n_meas > 0) {
     const unsigned mg = (a.n_meas + 255) / 256 < 4096 ? (a.n_meas + 255) / 256 : 4096;
     ckf_meas_f32_kernel<<<mg, 256, 0, stream>>>(a.loc0, a.loc1, a.v00, a.v11, a.n_meas, mf);
   }
   a.meas_f = mf;
-  if (a.mixed)
-    find_tracks_kernel<true><<<(a.n_seeds + kCkfBlock - 1) / kCkfBlock, kCkfBlock, 0, stream>>>(a, fld);
-  else
-    find_tracks_kernel<false><<<(a.n_seeds + kCkfBlock - 1) / kCkfBlock, kCkfBlock, 0, stream>>>(a, fld);
+  // predictions and per-seed states after the FP32 measurements (8-byte aligned)
+  CkfWork w;
+  w.slots = static_cast<CkfBranch*>(a.ws);
+  char* p = mf_base + sizeof(float4) * size_t(a.n_meas);
+  w.pred = reinterpret_cast<CkfPred*>(p);
+  w.seeds = reinterpret_cast<CkfSeed*>(p + sizeof(CkfPred) * size_t(a.n_seeds) * a.beam);
+  const unsigned gs = (a.n_seeds + kCkfBlock - 1) / kCkfBlock;
+  const unsigned gb = unsigned((size_t(a.n_seeds) * a.beam + kCkfBlock - 1) / kCkfBlock);
+  ckf_init_kernel<<<gs, kCkfBlock, 0, stream>>>(a, w);
+  // every step adds an entry to each surviving branch: at most max_entries + 2 steps
+  const uint32_t n_steps = a.max_entries + 2;
+  for (uint32_t step = 0; step < n_steps; ++step) {
+    if (a.mixed)
+      ckf_predict_kernel<true><<<gb, kCkfBlock, 0, stream>>>(a, fld, w);
+    else
+      ckf_predict_kernel<false><<<gb, kCkfBlock, 0, stream>>>(a, fld, w);
+    ckf_gate_kernel<<<gb, kCkfBlock, 0, stream>>>(a, w);
+    ckf_beam_kernel<<<gs, kCkfBlock, 0, stream>>>(a, w, step + 1 == n_steps ? 1u : 0u);
+  }
   return cudaGetLastError();
 }
 
 }  // namespace
 
 size_t ckf_workspace_bytes(uint32_t n_seeds, uint32_t beam, uint32_t n_meas) {
-  // branch slots, the seed-order histogram and permutation, then FP32 copies of the measurements
+  // branch slots, the seed-order histogram and permutation, FP32 copies of the measurements,
+  // then the predictions of every branch slot and the per-seed states
   return size_t(n_seeds) * (beam * (kCkfChildren + 2) + 1) * sizeof(CkfBranch) +
-         ((sizeof(uint32_t) * (kCkfOrderBins + size_t(n_seeds)) + 15) & ~size_t(15)) + sizeof(float4) * size_t(n_meas);
+         ((sizeof(uint32_t) * (kCkfOrderBins + size_t(n_seeds)) + 15) & ~size_t(15)) + sizeof(float4) * size_t(n_meas) +
+         sizeof(CkfPred) * size_t(n_seeds) * beam + sizeof(CkfSeed) * size_t(n_seeds);
 }
 
 cudaError_t launch_find_tracks(const CkfArgs& a, const FieldDev& f, cudaStream_t stream) {
