@@ -505,7 +505,29 @@ struct CkfWork {
   CkfBranch* slots;  // per seed: beam B, children B (C + 1), best 1
   CkfPred* pred;     // per seed: B
   CkfSeed* seeds;    // per seed
+  uint32_t* list;    // the branch slots (t B + bi) in the beam, for the next step's phases 1 and 2
+  uint32_t* count;   // their number
 };
+
+// Appends each seed's beam slots to the list for the next step: in seed order within a block
+// (an exclusive scan of the beam sizes), blocks in any order. Every thread of the block calls it.
+__device__ void append_beam(const CkfWork& w, uint32_t t, uint32_t n_act, uint32_t B) {
+  __shared__ uint32_t part[kCkfBlock];
+  __shared__ uint32_t base;
+  const uint32_t tid = threadIdx.x;
+  part[tid] = n_act;
+  __syncthreads();
+  for (uint32_t d = 1; d < kCkfBlock; d <<= 1) {
+    const uint32_t add = tid >= d ? part[tid - d] : 0u;
+    __syncthreads();
+    part[tid] += add;
+    __syncthreads();
+  }
+  if (tid == kCkfBlock - 1) base = part[tid] ? atomicAdd(w.count, part[tid]) : 0u;
+  __syncthreads();
+  const uint32_t at = base + part[tid] - n_act;
+  for (uint32_t q = 0; q < n_act; ++q) w.list[at + q] = t * B + q;
+}
 
 __device__ __forceinline__ CkfBranch* seed_slots(const CkfWork& w, uint32_t t, uint32_t B) {
   return w.slots + size_t(t) * slots_per_seed(B);
@@ -524,13 +546,21 @@ __device__ void write_candidate(const CkfArgs& a, uint32_t i, const CkfBranch* b
   }
 }
 
+__device__ void init_seed(const CkfArgs& a, const CkfWork& w, uint32_t t, CkfSeed& st);
+__device__ uint32_t beam_seed(const CkfArgs& a, const CkfWork& w, uint32_t t, uint32_t last);
+
 // The seed's starting branch (thread t finds seed perm[t]); a seed on a missing surface or event
 // gets no candidate at once.
 __global__ void __launch_bounds__(kCkfBlock) ckf_init_kernel(const CkfArgs a, CkfWork w) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= a.n_seeds) return;
-  const uint32_t i = a.perm[t], n = a.n_seeds;
+  const bool live = t < a.n_seeds;
   CkfSeed st{0u, 1u, 0u, 1u};
+  if (live) init_seed(a, w, t, st);
+  append_beam(w, t, st.n_act, a.beam);
+}
+
+__device__ void init_seed(const CkfArgs& a, const CkfWork& w, uint32_t t, CkfSeed& st) {
+  const uint32_t i = a.perm[t], n = a.n_seeds;
   const uint32_t seed_sid = a.seed_sid[i];
   const uint32_t ev = a.seed_event ? a.seed_event[i] : 0u;
   if (seed_sid < a.n_surf && ev < a.n_events) {
@@ -563,15 +593,12 @@ __global__ void __launch_bounds__(kCkfBlock) ckf_predict_kernel(const CkfArgs a,
   }
   __syncthreads();
   const uint32_t B = a.beam;
-  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= a.n_seeds * B) return;
+  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= *w.count) return;
+  const uint32_t g = w.list[k];  // a branch slot in the beam
   const uint32_t t = g / B, bi = g % B;
   const CkfSeed st = w.seeds[t];
   CkfPred& pr = w.pred[g];
-  if (bi >= st.n_act) {
-    pr.target = -2;
-    return;
-  }
   const CkfBranch& br = seed_slots(w, t, B)[bi];
   int target;
   if (st.first) {
@@ -596,8 +623,9 @@ __global__ void __launch_bounds__(kCkfBlock) ckf_predict_kernel(const CkfArgs a,
 // Phase 2: the gate over the predicted module's measurements and the children of branch bi.
 __global__ void __launch_bounds__(kCkfBlock) ckf_gate_kernel(const CkfArgs a, CkfWork w) {
   const uint32_t B = a.beam;
-  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= a.n_seeds * B) return;
+  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= *w.count) return;
+  const uint32_t g = w.list[k];
   const uint32_t t = g / B, bi = g % B;
   CkfPred& pr = w.pred[g];
   const int target = pr.target;
@@ -704,9 +732,15 @@ __global__ void __launch_bounds__(kCkfBlock) ckf_gate_kernel(const CkfArgs a, Ck
 // `last`: the final step; the candidate is written when the search is over.
 __global__ void __launch_bounds__(kCkfBlock) ckf_beam_kernel(const CkfArgs a, CkfWork w, uint32_t last) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= a.n_seeds) return;
+  uint32_t n_next = 0;
+  if (t < a.n_seeds) n_next = beam_seed(a, w, t, last);
+  append_beam(w, t, n_next, a.beam);
+}
+
+// The beam of seed slot t after a step; returns its size (0: the search is over).
+__device__ uint32_t beam_seed(const CkfArgs& a, const CkfWork& w, uint32_t t, uint32_t last) {
   CkfSeed st = w.seeds[t];
-  if (st.n_act == 0) return;  // over (candidate written)
+  if (st.n_act == 0) return 0;  // over (candidate written)
   const uint32_t B = a.beam;
   CkfBranch* act = seed_slots(w, t, B);
   CkfBranch* kids = act + B;
@@ -744,6 +778,7 @@ __global__ void __launch_bounds__(kCkfBlock) ckf_beam_kernel(const CkfArgs a, Ck
   st.n_act = last ? 0u : n_act;
   if (st.n_act == 0) write_candidate(a, a.perm[t], best, st.have_best != 0);
   w.seeds[t] = st;
+  return st.n_act;
 }
 
 template <class F>
@@ -775,8 +810,11 @@ cudaError_t launch_ckf(const CkfArgs& a_in, const F& fld, cudaStream_t stream) {
   char* p = mf_base + sizeof(float4) * size_t(a.n_meas);
   w.pred = reinterpret_cast<CkfPred*>(p);
   w.seeds = reinterpret_cast<CkfSeed*>(p + sizeof(CkfPred) * size_t(a.n_seeds) * a.beam);
+  w.list = reinterpret_cast<uint32_t*>(w.seeds + a.n_seeds);
+  w.count = w.list + size_t(a.n_seeds) * a.beam;
   const unsigned gs = (a.n_seeds + kCkfBlock - 1) / kCkfBlock;
   const unsigned gb = unsigned((size_t(a.n_seeds) * a.beam + kCkfBlock - 1) / kCkfBlock);
+  if ((e = cudaMemsetAsync(w.count, 0, sizeof(uint32_t), stream)) != cudaSuccess) return e;
   ckf_init_kernel<<<gs, kCkfBlock, 0, stream>>>(a, w);
   // every step adds an entry to each surviving branch: at most max_entries + 2 steps
   const uint32_t n_steps = a.max_entries + 2;
@@ -786,6 +824,7 @@ cudaError_t launch_ckf(const CkfArgs& a_in, const F& fld, cudaStream_t stream) {
     else
       ckf_predict_kernel<false><<<gb, kCkfBlock, 0, stream>>>(a, fld, w);
     ckf_gate_kernel<<<gb, kCkfBlock, 0, stream>>>(a, w);
+    if ((e = cudaMemsetAsync(w.count, 0, sizeof(uint32_t), stream)) != cudaSuccess) return e;
     ckf_beam_kernel<<<gs, kCkfBlock, 0, stream>>>(a, w, step + 1 == n_steps ? 1u : 0u);
   }
   return cudaGetLastError();
@@ -798,7 +837,8 @@ size_t ckf_workspace_bytes(uint32_t n_seeds, uint32_t beam, uint32_t n_meas) {
   // then the predictions of every branch slot and the per-seed states
   return size_t(n_seeds) * (beam * (kCkfChildren + 2) + 1) * sizeof(CkfBranch) +
          ((sizeof(uint32_t) * (kCkfOrderBins + size_t(n_seeds)) + 15) & ~size_t(15)) + sizeof(float4) * size_t(n_meas) +
-         sizeof(CkfPred) * size_t(n_seeds) * beam + sizeof(CkfSeed) * size_t(n_seeds);
+         sizeof(CkfPred) * size_t(n_seeds) * beam + sizeof(CkfSeed) * size_t(n_seeds) +
+         sizeof(uint32_t) * (size_t(n_seeds) * beam + 1);
 }
 
 cudaError_t launch_find_tracks(const CkfArgs& a, const FieldDev& f, cudaStream_t stream) {
