@@ -200,10 +200,54 @@ __device__ __noinline__ int nearest_crossed(const CkfArgs& a, const uint32_t* ca
   return best;
 }
 
+// Layer tables of a block, in shared memory: the barrel layers' outer face radii, and the layer
+// ids in the order in which a straight line meets them: barrel layers by face radius, disks by
+// face z (ties: lower id first).
+struct NavTables {
+  double face_r[kCkfMaxLayers];
+  int bar[kCkfMaxLayers], dsk[kCkfMaxLayers];
+  int nbar, ndsk;
+};
+
+__device__ void build_nav_tables(const CkfArgs& a, NavTables& nt) {
+  for (uint32_t li = threadIdx.x; li < a.n_layers; li += blockDim.x) {
+    const double* l = a.layers + 8 * li;
+    nt.face_r[li] = l[0] == 0.0 ? barrel_face(l) : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int nb = 0, nd = 0;
+    for (uint32_t li = 0; li < a.n_layers; ++li) {  // insertion in id order: stable for ties
+      const double* l = a.layers + 8 * li;
+      if (l[0] == 0.0) {
+        int pos = nb++;
+        for (; pos > 0 && nt.face_r[nt.bar[pos - 1]] > nt.face_r[li]; --pos) nt.bar[pos] = nt.bar[pos - 1];
+        nt.bar[pos] = int(li);
+      } else {
+        const double z = l[1] + (l[1] > 0.0 ? 1.0 : -1.0);
+        int pos = nd++;
+        for (; pos > 0; --pos) {
+          const double* lp = a.layers + 8 * nt.dsk[pos - 1];
+          if (!(lp[1] + (lp[1] > 0.0 ? 1.0 : -1.0) > z)) break;
+          nt.dsk[pos] = nt.dsk[pos - 1];
+        }
+        nt.dsk[pos] = int(li);
+      }
+    }
+    nt.nbar = nb;
+    nt.ndsk = nd;
+  }
+  __syncthreads();
+}
+
 // the next module from (x, T) on surface `cur`: the nearest crossing among the current layer's
-// modules around x and the modules of the layers ahead (in order of face path)
+// modules around x and the modules of the layers ahead, taken in order of face path (ties:
+// lower index first) until a layer's face lies more than 20 mm beyond the nearest crossing
+// found. A straight line meets the barrel faces in order of radius and the disk faces in
+// order of z (ascending for T_z > 0, descending for T_z < 0), so the layers ahead come from
+// merging those two orders, and a face path is computed only when the merge reaches it.
 __device__ int navigate(const CkfArgs& a, int cur, const double x[3], const double T[3], const double k[3],
-                        double bend, const uint32_t* skip, int nskip, const double* face_r) {
+                        double bend, const uint32_t* skip, int nskip, const NavTables& nt) {
   uint32_t cand[9];
   int best = -1;
   double best_s = 0.0;
@@ -215,25 +259,46 @@ __device__ int navigate(const CkfArgs& a, int cur, const double x[3], const doub
     const int nc = layer_candidates(a, uint32_t(cur_layer), x, cand);
     best = nearest_crossed(a, cand, nc, x, T, k, bend, sk, nskip + 1, best_s);
   }
-  // the layers ahead in order of face path (ties: lower index first), by insertion as their
-  // paths are computed in index order
-  double vs[kCkfMaxLayers];
-  int vl[kCkfMaxLayers];
-  int nv = 0;
-  for (uint32_t li = 0; li < a.n_layers; ++li) {
-    const double s = int(li) == cur_layer ? -1.0 : layer_path(a, li, x, T, face_r);
-    if (!(s > 0.0)) continue;
-    int pos = nv++;
-    for (; pos > 0 && vs[pos - 1] > s; --pos) {
-      vs[pos] = vs[pos - 1];
-      vl[pos] = vl[pos - 1];
+  // the head of each order: the next layer ahead (face path > 0, within its extent) and its path
+  int pb = 0, pd = 0, lb = -1, ld = -1;
+  double sb = 0.0, sd = 0.0;
+  const int dstep = T[2] > 0.0 ? 1 : -1;  // direction of the disk order
+  int dpos = T[2] > 0.0 ? 0 : nt.ndsk - 1;
+  const bool disks = T[2] != 0.0;
+  auto next_barrel = [&]() {
+    lb = -1;
+    while (pb < nt.nbar) {
+      const int li = nt.bar[pb++];
+      if (li == cur_layer) continue;
+      const double s = layer_path(a, uint32_t(li), x, T, nt.face_r);
+      if (s > 0.0) {
+        lb = li;
+        sb = s;
+        return;
+      }
     }
-    vs[pos] = s;
-    vl[pos] = int(li);
-  }
-  for (int j = 0; j < nv; ++j) {
-    const int pick = vl[j];
-    const double sl = vs[j];
+  };
+  auto next_disk = [&]() {
+    ld = -1;
+    while (disks && pd < nt.ndsk) {
+      const int li = nt.dsk[dpos];
+      dpos += dstep;
+      ++pd;
+      if (li == cur_layer) continue;
+      const double s = layer_path(a, uint32_t(li), x, T, nt.face_r);
+      if (s > 0.0) {
+        ld = li;
+        sd = s;
+        return;
+      }
+    }
+  };
+  next_barrel();
+  next_disk();
+  while (lb >= 0 || ld >= 0) {
+    const bool take_b = ld < 0 || (lb >= 0 && (sb < sd || (sb == sd && lb < ld)));
+    const int pick = take_b ? lb : ld;
+    const double sl = take_b ? sb : sd;
     if (best >= 0 && sl > best_s + 20.0) break;
     const double h = 0.5 * sl * sl;
     const double q[3] = {x[0] + sl * T[0] + h * k[0], x[1] + sl * T[1] + h * k[1], x[2] + sl * T[2] + h * k[2]};
@@ -244,6 +309,10 @@ __device__ int navigate(const CkfArgs& a, int cur, const double x[3], const doub
       best = m;
       best_s = sm;
     }
+    if (take_b)
+      next_barrel();
+    else
+      next_disk();
   }
   return best;
 }
@@ -251,7 +320,7 @@ __device__ int navigate(const CkfArgs& a, int cur, const double x[3], const doub
 // From a branch's filtered state on its surface: material, navigation, RKN propagation and
 // covariance transport to the next module; returns its id (-1: none ahead, or stopped).
 template <bool kMixed, class F>
-__device__ int predict(const CkfArgs& a, const F& fld, const double* face_r, const CkfBranch& br, double pp[5],
+__device__ int predict(const CkfArgs& a, const F& fld, const NavTables& nt, const CkfBranch& br, double pp[5],
                        double pdir[4], double Cp[15], double& h_ctrl) {
   Surf sc;
   load_surf(a.surf, uint32_t(br.sid), sc);
@@ -277,7 +346,7 @@ __device__ int predict(const CkfArgs& a, const F& fld, const double* face_r, con
   uint32_t skip[4];
   int nskip = 0;
   for (int tries = 0; tries < 4; ++tries) {
-    const int m = navigate(a, br.sid, x, T0, kc, bend, skip, nskip, face_r);
+    const int m = navigate(a, br.sid, x, T0, kc, bend, skip, nskip, nt);
     if (m < 0) return -1;
     Surf s;
     load_surf(a.surf, uint32_t(m), s);
@@ -586,12 +655,8 @@ __device__ void init_seed(const CkfArgs& a, const CkfWork& w, uint32_t t, CkfSee
 // Phase 1: the prediction of branch bi of seed slot t (thread t B + bi).
 template <bool kMixed, class F>
 __global__ void __launch_bounds__(kCkfBlock) ckf_predict_kernel(const CkfArgs a, const F fld, CkfWork w) {
-  __shared__ double face_r[kCkfMaxLayers];
-  for (uint32_t li = threadIdx.x; li < a.n_layers; li += blockDim.x) {
-    const double* l = a.layers + 8 * li;
-    face_r[li] = l[0] == 0.0 ? barrel_face(l) : 0.0;
-  }
-  __syncthreads();
+  __shared__ NavTables nt;
+  build_nav_tables(a, nt);
   const uint32_t B = a.beam;
   const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= *w.count) return;
@@ -609,7 +674,7 @@ __global__ void __launch_bounds__(kCkfBlock) ckf_predict_kernel(const CkfArgs a,
     pr.h = br.h_ctrl;
   } else {
     double pp[5], pdir[4], Cp[15], h = br.h_ctrl;
-    target = br.n_entries >= a.max_entries ? -1 : predict<kMixed>(a, fld, face_r, br, pp, pdir, Cp, h);
+    target = br.n_entries >= a.max_entries ? -1 : predict<kMixed>(a, fld, nt, br, pp, pdir, Cp, h);
     if (target >= 0) {
       for (int j = 0; j < 5; ++j) pr.pp[j] = pp[j];
       for (int j = 0; j < 4; ++j) pr.pdir[j] = pdir[j];
