@@ -59,10 +59,27 @@ __global__ void __launch_bounds__(kKeyBins) order_scan_kernel(uint32_t* __restri
   hist[t] = v[t] - hist[t];
 }
 
+// Scatter in two levels: the tracks of a block take consecutive ranks per key in shared memory,
+// then one global atomic per (block, key) reserves the block's range of that key (the per-track
+// global atomics contended on the few most common keys). Tracks of a key land in block order of
+// arrival; the fit of a track does not depend on its place.
 __global__ void __launch_bounds__(256) order_scatter_kernel(const uint32_t* __restrict__ keys, uint32_t n,
                                                             uint32_t* __restrict__ base, uint32_t* __restrict__ perm) {
+  __shared__ uint32_t cnt[kKeyBins];
+  __shared__ uint32_t off[kKeyBins];
+  for (int b = threadIdx.x; b < kKeyBins; b += blockDim.x) cnt[b] = 0;
+  __syncthreads();
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) perm[atomicAdd(&base[keys[i]], 1u)] = i;
+  uint32_t key = 0, rank = 0;
+  if (i < n) {
+    key = keys[i];
+    rank = atomicAdd(&cnt[key], 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < kKeyBins; b += blockDim.x)
+    if (cnt[b]) off[b] = atomicAdd(&base[b], cnt[b]);
+  __syncthreads();
+  if (i < n) perm[off[key] + rank] = i;
 }
 
 }  // namespace
