@@ -112,6 +112,8 @@ def parse():
     ap.add_argument("--shape", default=None,
                     help="fixed launch shape 'threads,blocks_per_sm,tracks_per_warp,registers[,lanes]' for every "
                          "variant (registers 128 or 64 apply to FP64 and mixed, 128 to mixed_fp32; lanes 1 or 4)")
+    ap.add_argument("--proposer-quantile", type=float, default=0.05,
+                    help="calibration quantile of the learned step proposer's output bias (0..1)")
     ap.add_argument("--tol", type=float, default=None,
                     help="RKN local error tolerance in mm for every variant (default: the library's 1e-4)")
     ap.add_argument("--no-seeds", action="store_true",
@@ -765,7 +767,8 @@ def main():
         tt = make_training_batch(args, rank)
         tb = tkf.Batch.from_arrays(tt.offsets, tt.meas, tt.sid, tt.seed_par, tt.seed_cov).to(f"cuda:{local}")
         t0 = time.perf_counter()
-        proposer, info = learn.build_proposer(ctx, geo, fld, tb, tkf.MIXED, mass=w.mass, tol=args.tol)
+        proposer, info = learn.build_proposer(ctx, geo, fld, tb, tkf.MIXED, mass=w.mass, tol=args.tol,
+                                              quantile=args.proposer_quantile)
         learn_info = {"records": info["records"], "final_loss": round(info["epoch_loss"][-1], 4),
                       "bias_shift": round(info["bias_shift"], 4), "train_s": round(time.perf_counter() - t0, 2),
                       "tracks": tt.n_tracks}
