@@ -566,7 +566,13 @@ typedef struct tkf_mlp_train_options {
 } tkf_mlp_train_options;
 
 /* Trains FP32 parameters in place with mean-squared-error loss and Adam, with the library's
- * own forward, backward and update kernels, on `stream`. All pointers are DEVICE memory:
+ * own forward, backward and update kernels, on `stream`. Every dense contraction of a step
+ * runs on the tensor cores with BF16 operands (rounded to nearest even from FP32) and FP32
+ * accumulation: the two layers, the backpropagation through layer 2 (dA1 = dZ2 W2), and the
+ * weight and bias gradients of both layers (dW2 = dZ2^T A1, dW1 = dZ1^T X, sums of dZ2 and dZ1);
+ * bias, SiLU, its derivative, the output layer and its gradient, and Adam are FP32 on the CUDA
+ * cores; partial gradients of 128-sample tiles are summed in a fixed order (deterministic).
+ * All pointers are DEVICE memory:
  * records [n][TKF_MLP_RECORD] (inputs, label), params [TKF_MLP_PARAMS], adam_moments
  * [2][TKF_MLP_PARAMS] (first and second moments; zero them before the first call),
  * epoch_loss [epochs] (mean loss of each epoch). *adam_t (HOST) counts the Adam steps taken so
@@ -577,8 +583,9 @@ tkf_status tkf_mlp_train(tkf_context ctx, const float* records, uint32_t n, cons
                          float* params, float* adam_moments, uint32_t* adam_t, float* epoch_loss, void* stream);
 
 /* Mean squared error of the network on n samples (x [n][TKF_MLP_INPUTS], y [n], DEVICE) and
- * its gradient grad [TKF_MLP_PARAMS] (DEVICE); loss is one DEVICE float. For checks of the
- * training kernels. Errors as tkf_mlp_train. */
+ * its gradient grad [TKF_MLP_PARAMS] (DEVICE), by the training kernels of tkf_mlp_train (BF16
+ * operands in the contractions); loss is one DEVICE float. For checks of the training
+ * kernels. Errors as tkf_mlp_train. */
 tkf_status tkf_mlp_loss_grad(tkf_context ctx, const float* params, const float* x, const float* y, uint32_t n,
                              float* grad, float* loss, void* stream);
 

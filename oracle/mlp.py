@@ -63,24 +63,67 @@ def forward(theta, X):
     return out, (X, z1, a1, z2, a2)
 
 
-def loss_and_grad(theta, X, y):
-    """Mean squared error over the batch and its gradient (backpropagation written out)."""
+def bf16_round(a):
+    """Values rounded to BF16 (through FP32, nearest, ties to even), returned as FP64."""
+    f = np.ascontiguousarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    r = (((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16).astype(np.uint32)
+    return r.view(np.float32).astype(np.float64)
+
+
+def loss_and_grad(theta, X, y, bf16_operands: bool = False):
+    """Mean squared error over the batch and its gradient (backpropagation written out).
+    With `bf16_operands` every operand of a dense contraction is rounded to BF16 first (the
+    inputs and W1 for layer 1; the first activations and W2 for layer 2; dL/dZ2 and W2 for the
+    backpropagation through layer 2; dL/dZ2, dL/dZ1, the first activations and the inputs for
+    the weight and bias gradients), the rest stays exact: the mixed-precision training that
+    runs its contractions on BF16 tensor cores."""
     X = np.asarray(X, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
     p = unpack(np.asarray(theta, dtype=np.float64))
-    out, (X, z1, a1, z2, a2) = forward(theta, X)
+    rnd = bf16_round if bf16_operands else (lambda a: a)
+    Xb, W1b, W2b = rnd(X), rnd(p["W1"]), rnd(p["W2"])
+    z1 = Xb @ W1b.T + p["b1"]
+    a1 = silu(z1)
+    a1b = rnd(a1)
+    z2 = a1b @ W2b.T + p["b2"]
+    a2 = silu(z2)
+    out = a2 @ p["w3"] + p["b3"][0]
     n = X.shape[0]
     r = out - y
     loss = np.mean(r * r)
     dout = 2.0 * r / n
     g = {"w3": a2.T @ dout, "b3": np.array([dout.sum()])}
-    dz2 = np.outer(dout, p["w3"]) * dsilu(z2)
-    g["W2"] = dz2.T @ a1
+    dz2 = rnd(np.outer(dout, p["w3"]) * dsilu(z2))
+    g["W2"] = dz2.T @ a1b
     g["b2"] = dz2.sum(0)
-    dz1 = (dz2 @ p["W2"]) * dsilu(z1)
-    g["W1"] = dz1.T @ X
+    dz1 = rnd((dz2 @ W2b) * dsilu(z1))
+    g["W1"] = dz1.T @ Xb
     g["b1"] = dz1.sum(0)
     return loss, pack(g)
+
+
+def grad_term_scale(theta, X, y):
+    """For each gradient element of the BF16-operand scheme, the sum over the samples of the
+    absolute values of its product terms (|dZ2|^T |A1| for W2, |dZ1|^T |X| for W1, the sums
+    of |dZ| for the biases, |A2|^T |dout| and the sum of |dout| for the output layer): two
+    evaluations whose BF16 operands differ by at most one unit (2^-7 of the value) differ by
+    at most 2^-7 times this in that element."""
+    X = np.asarray(X, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    p = unpack(np.asarray(theta, dtype=np.float64))
+    Xb, W1b, W2b = bf16_round(X), bf16_round(p["W1"]), bf16_round(p["W2"])
+    z1 = Xb @ W1b.T + p["b1"]
+    a1b = bf16_round(silu(z1))
+    z2 = a1b @ W2b.T + p["b2"]
+    a2 = silu(z2)
+    out = a2 @ p["w3"] + p["b3"][0]
+    dout = 2.0 * (out - y) / X.shape[0]
+    dz2 = bf16_round(np.outer(dout, p["w3"]) * dsilu(z2))
+    dz1 = bf16_round((dz2 @ W2b) * dsilu(z1))
+    t = {"W1": np.abs(dz1).T @ np.abs(Xb), "b1": np.abs(dz1).sum(0), "W2": np.abs(dz2).T @ np.abs(a1b),
+         "b2": np.abs(dz2).sum(0), "w3": np.abs(a2).T @ np.abs(dout), "b3": np.array([np.abs(dout).sum()])}
+    return pack(t)
 
 
 def adam_step(theta, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
@@ -92,7 +135,7 @@ def adam_step(theta, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
     return theta - lr * mhat / (np.sqrt(vhat) + eps), m, v
 
 
-def train(theta, X, y, batch, epochs, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+def train(theta, X, y, batch, epochs, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, bf16_operands: bool = False):
     """Mini-batches in record order (the last partial batch is dropped); returns theta and the
     mean loss of each epoch."""
     theta = np.array(theta, dtype=np.float64)
@@ -103,7 +146,7 @@ def train(theta, X, y, batch, epochs, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8)
         acc = 0.0
         for b in range(nb):
             sl = slice(b * batch, (b + 1) * batch)
-            loss, g = loss_and_grad(theta, X[sl], y[sl])
+            loss, g = loss_and_grad(theta, X[sl], y[sl], bf16_operands)
             t += 1
             theta, m, v = adam_step(theta, g, m, v, t, lr, beta1, beta2, eps)
             acc += loss

@@ -134,3 +134,22 @@ def test_oracle_training_records_are_consistent():
     theta, losses = mlp.train(mlp.init(1), X, y, batch=128, epochs=8, lr=2e-3)
     print({"records": len(y), "label_var": float(np.var(y)), "losses": losses})
     assert losses[-1] < 0.75 * np.var(y) and losses[-1] < losses[1]
+
+
+def test_bf16_operand_gradient_stays_close_to_the_exact_one():
+    """The BF16-operand reference (the tensor-core training's arithmetic) against the exact FP64
+    gradient: rounding every contraction operand to 8 significant bits moves the loss by well
+    under 1 % and the gradient by a few per mille of its scale, and it rounds exactly the
+    values that BF16 cannot represent (BF16 values themselves pass through unchanged)."""
+    rng = np.random.default_rng(3)
+    theta = mlp.init(2) + 0.05 * rng.normal(size=mlp.N_PARAMS)
+    X = rng.normal(size=(512, 12))
+    y = np.sin(X[:, 0]) + 0.3 * X[:, 5]
+    l0, g0 = mlp.loss_and_grad(theta, X, y)
+    l1, g1 = mlp.loss_and_grad(theta, X, y, bf16_operands=True)
+    assert abs(l1 / l0 - 1.0) < 1e-2
+    assert np.max(np.abs(g1 - g0)) < 2e-2 * np.max(np.abs(g0))
+    assert np.corrcoef(g0, g1)[0, 1] > 0.999
+    b = mlp.bf16_round(X)
+    np.testing.assert_array_equal(mlp.bf16_round(b), b)
+    assert np.max(np.abs(b / X - 1.0)) <= 2.0 ** -8  # half a unit of the 7 stored bits
