@@ -80,6 +80,34 @@ __device__ __forceinline__ void load_surf(const double* __restrict__ g, uint32_t
   s.tf = f2.y; s.t_x0f = f2.z;
 }
 
+// Frame vectors of a surface read again from its record after the propagation, so that they do
+// not stay in registers across it (the fit's register budget is capped). The loads are volatile:
+// the compiler may not reuse the values of the earlier load, which would keep them live.
+__device__ __forceinline__ double2 ld_nc_d2(const double2* p) {
+  double2 v;
+  asm volatile("ld.global.nc.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float4 ld_nc_f4(const float4* p) {
+  float4 v;
+  asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+  return v;
+}
+// u and v in FP64
+__device__ __forceinline__ void reload_uv(const double* __restrict__ g, uint32_t id, double u[3], double v[3]) {
+  const double2* p = reinterpret_cast<const double2*>(g + size_t(id) * kSurfStride);
+  const double2 a0 = ld_nc_d2(p), a1 = ld_nc_d2(p + 1), a2 = ld_nc_d2(p + 2);
+  u[0] = a0.x; u[1] = a0.y; u[2] = a1.x;
+  v[0] = a1.y; v[1] = a2.x; v[2] = a2.y;
+}
+// u and v in FP32
+__device__ __forceinline__ void reload_uvf(const double* __restrict__ g, uint32_t id, float u[3], float v[3]) {
+  const float4* q = reinterpret_cast<const float4*>(g + size_t(id) * kSurfStride + 16);
+  const float4 f0 = ld_nc_f4(q), f1 = ld_nc_f4(q + 1);
+  u[0] = f0.x; u[1] = f0.y; u[2] = f0.z;
+  v[0] = f0.w; v[1] = f1.x; v[2] = f1.y;
+}
+
 __device__ __forceinline__ double dot3(const double a[3], const double b[3]) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
@@ -1201,7 +1229,8 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
     if (!fin) status = TKF_TRACK_NON_FINITE;
   }
 
-  Surf sp;                       // surface of the previous measurement
+  Surf sp;                       // surface of the previous measurement (FP64 path)
+  uint32_t sid_prev = 0;         // its id (the mixed path reads the record again when needed)
   double sph = 0.0, cph = 1.0, sth = 1.0, cth = 0.0;  // filtered direction at sp
   // learned mode: the step-size control starts from the network's proposal for this track
   // (a negative value: the proposal pre-pass gave up; start from h_max and flag the track)
@@ -1240,7 +1269,8 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
     Surf s;
     const uint32_t sid_m = a.sid[m];
     const bool measured = (sid_m & TKF_SID_NO_MEASUREMENT) == 0;
-    load_surf(a.surf, sid_m & ~TKF_SID_NO_MEASUREMENT, s);
+    const uint32_t sid = sid_m & ~TKF_SID_NO_MEASUREMENT;
+    load_surf(a.surf, sid, s);
     U J[5][5];
     double sp2 = 0.0, cp2 = 1.0, st2 = 1.0, ct2 = 0.0;  // predicted direction at s (ent >= 1)
     if (bwd && ent == 0) {  // the backward filter starts on this surface: no prediction
@@ -1317,7 +1347,11 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
       }
       transport_cov<kG>(J, C, gl, gmask);
       } else {
-      // ---- mixed precision: material, propagation, Jacobian and covariance transport in FP32
+      // ---- mixed precision: material, propagation, Jacobian and covariance transport in FP32.
+      // Only the ids of both surfaces stay live: their frames are read again after the
+      // propagation, which keeps the state carried through it within the register cap.
+      Surf sp;
+      load_surf(a.surf, sid_prev, sp);
       const float Tm[3] = {d2f(sth * cph), d2f(sth * sph), d2f(cth)};
       double lam = p[4];
       float th0sq = 0.0f;
@@ -1341,6 +1375,14 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
         }
       const float qcol = gl == 2 ? 1.0f : 0.0f;
       const float* nf = s.nf;
+      // C + Q in FP32, formed before the propagation: only the FP32 copy is transported
+      float Cf[15];
+#pragma unroll
+      for (int j = 0; j < 15; ++j) Cf[j] = cov_to_f(C[j]);
+      if (!bwd) {
+        Cf[S(2, 2)] += th0sq / (fsth * fsth);
+        Cf[S(3, 3)] += th0sq;
+      }
       float kend[3];
       status |= propagate_mixed<kMode == kRecord ? kRecord : kPlain, kCols>(fld, a.opt, s, nf, r, T, lam, dr, dT, qcol,
                                                                             h_ctrl_f, attempts, rejected, kend, learn);
@@ -1368,8 +1410,9 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
       cp2 = tn[0] * inv_st;
       sp2 = tn[1] * inv_st;
       const float Tf[3] = {d2f(T[0]), d2f(T[1]), d2f(T[2])};
-      const float* uf = s.uf;
-      const float* vf = s.vf;
+      float uf[3], vf[3], puf[3], pvf[3];
+      reload_uvf(a.surf, sid, uf, vf);
+      reload_uvf(a.surf, sid_prev, puf, pvf);
       const float inv_nT = 1.0f / dotr(nf, Tf);
       const float fst = d2f(st2), fct = d2f(ct2), fcp = d2f(cp2), fsp = d2f(sp2), finv_st = d2f(inv_st);
       float Jf[5][5];
@@ -1377,7 +1420,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
       for (int c = 0; c < 2 + kCols; ++c) {  // u, v, then this lane's derivative columns
         float x[3], t[3], out[4];
         for (int j = 0; j < 3; ++j) {
-          x[j] = (c == 0) ? sp.uf[j] : (c == 1) ? sp.vf[j] : dr[c - 2][j];
+          x[j] = (c == 0) ? puf[j] : (c == 1) ? pvf[j] : dr[c - 2][j];
           t[j] = (c < 2) ? 0.0f : dT[c - 2][j];
         }
         jac_column(nf, uf, vf, Tf, kend, inv_nT, fsp, fcp, fst, fct, finv_st, x, t, out);
@@ -1393,19 +1436,14 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
 #pragma unroll
       for (int c = 0; c < 5; ++c) Jf[4][c] = (c == 4) ? 1.0f : 0.0f;
       const double d[3] = {r[0] - s.c[0], r[1] - s.c[1], r[2] - s.c[2]};
-      p[0] = dot3(s.u, d);
-      p[1] = dot3(s.v, d);
+      double su[3], sv[3];
+      reload_uv(a.surf, sid, su, sv);
+      p[0] = dot3(su, d);
+      p[1] = dot3(sv, d);
       p[2] = 0.0;
       p[3] = 0.0;
       p[4] = lam;
       // C_pred = J (C + Q) J^T in FP32
-      float Cf[15];
-#pragma unroll
-      for (int j = 0; j < 15; ++j) Cf[j] = cov_to_f(C[j]);
-      if (!bwd) {
-        Cf[S(2, 2)] += th0sq / (fsth * fsth);
-        Cf[S(3, 3)] += th0sq;
-      }
       transport_cov<kG>(Jf, Cf, gl, gmask);
 #pragma unroll
       for (int j = 0; j < 15; ++j) C[j] = cov_from_f<U>(Cf[j]);
@@ -1554,7 +1592,8 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
       }
     }
     if constexpr (kMode == kStates) store_filtered(a, m, p, C, k == 0, sph, cph, sth, cth);
-    sp = s;
+    if constexpr (!kMixed) sp = s;
+    sid_prev = sid;
   }
   }  // passes
   if constexpr (kSmooth == 1) {
