@@ -498,7 +498,7 @@ typedef struct tkf_ckf_outputs {
  * and material options (step mode TKF_STEP_ADAPTIVE; launch policy fields ignored) and the
  * precision: TKF_FP64, or TKF_MIXED with the propagation, material and covariance transport in
  * FP32 around FP64 anchors as in the fit's mixed path (navigation, chi2 gate and update stay
- * FP64). The branch store (about 7.9 KB a seed at beam 3) is a workspace of the
+ * FP64). The branch store (about 7 KB a seed at beam 3: branches and their history) is a workspace of the
  * context, grown on demand (the call then synchronizes the stream). Errors: TKF_ERR_BAD_HANDLE,
  * TKF_ERR_INVALID_ARG (NULL pointers, options out of range, no layer structure), TKF_ERR_OOM,
  * TKF_ERR_DEVICE. */

@@ -647,7 +647,7 @@ tkf_status tkf_find_tracks(tkf_context ctx, tkf_geometry geo, tkf_field field, c
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(ctx, TKF_ERR_DEVICE, std::string(fn) + ": cudaSetDevice failed");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const size_t need = tkf::ckf_workspace_bytes(in->n_seeds, co->beam, in->n_meas);
+  const size_t need = tkf::ckf_workspace_bytes(in->n_seeds, co->beam, in->n_meas, co->max_entries);
   if (need > ctx->ckf_ws_bytes) {
     cudaError_t e = cudaStreamSynchronize(st);  // the old store may still be in use
     if (e != cudaSuccess) return cuda_fail(ctx, e, (std::string(fn) + ": stream synchronize").c_str());
@@ -679,6 +679,7 @@ tkf_status tkf_find_tracks(tkf_context ctx, tkf_geometry geo, tkf_field field, c
   a.layers = geo->d_layers;
   a.n_layers = geo->n_layers;
   a.rings = geo->d_rings;
+  a.n_rings = geo->n_rings;
   a.layer_of = geo->d_layer_of;
   a.mat = fa.mat;
   a.opt = fa.opt;

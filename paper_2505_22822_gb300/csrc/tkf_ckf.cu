@@ -2,12 +2,14 @@
 // Sec. 2 between seeding and fitting; the algorithm and the navigation read for this library
 // are stated in include/tkf.h at tkf_find_tracks).
 //
-// One thread per seed: the fit's RKN propagation, material and gain-matrix update; FP64
-// throughout, or (kMixed) with the propagation, material and covariance transport in FP32
-// around FP64 anchors as in the fit's mixed path (navigation, gate and update stay FP64). Each thread keeps its beam of branches, their children and its best ended branch in
-// a workspace slot of global memory (a branch: state, direction, covariance, counters and up to 32
-// entries, 496 bytes); the branches are read and written once per step, the geometry, layer tables and
-// measurements are gathered through L1/L2.
+// The search runs as phases over all seeds (below): the fit's RKN propagation, material and
+// gain-matrix update; FP64 throughout, or (kMixed) with the propagation, material and covariance
+// transport in FP32 around FP64 anchors as in the fit's mixed path (navigation, gate and update
+// stay FP64). A seed's branches live in a workspace of global memory (a branch: state, direction,
+// covariance and counters, 240 bytes); a branch's entries are not copied with it: each entry is a
+// node of the seed's history tree (surface, measurement, parent node), written once when the
+// beam keeps the branch, and the candidate's entries are read back along the parent links. The
+// geometry, layer tables and measurements are gathered through L1/L2.
 
 #include "tkf_fit_impl.cuh"
 
@@ -27,13 +29,25 @@ struct CkfBranch {
   double C[15];
   double h_ctrl, chi2;
   uint32_t n_meas, holes, n_entries, order;
-  int32_t sid;  // current surface, -1 before the seed surface
-  uint32_t pad;
-  uint32_t e_sid[TKF_CKF_MAX_ENTRIES];
-  int32_t e_meas[TKF_CKF_MAX_ENTRIES];
+  int32_t sid;     // current surface, -1 before the seed surface
+  int32_t node;    // history node of its last entry (-1: no entry yet)
+  uint32_t e_sid;  // a child's own entry (surface, measurement or -1), made into a node when
+  int32_t e_meas;  // the beam keeps the child
 };
 
-__host__ __device__ __forceinline__ uint32_t slots_per_seed(uint32_t beam) { return beam * (kCkfChildren + 2) + 1; }
+// An entry of a seed's history tree: node (step, q) is the entry of the q-th branch the beam
+// kept after that step.
+struct CkfNode {
+  uint32_t sid;
+  int32_t meas;
+  int32_t parent;  // node of the previous entry, -1: none
+};
+
+// Per seed: two areas of children (a step's beam lives in one, its children are written to the
+// other), then the best ended branch.
+__host__ __device__ __forceinline__ uint32_t area_slots(uint32_t beam) { return beam * (kCkfChildren + 1); }
+__host__ __device__ __forceinline__ uint32_t slots_per_seed(uint32_t beam) { return 2 * area_slots(beam) + 1; }
+__host__ __device__ __forceinline__ uint32_t ckf_steps(uint32_t max_entries) { return max_entries + 2; }
 
 // ranking of branches: more measurements, fewer consecutive holes, lower chi2, created earlier
 __device__ __forceinline__ bool better(const CkfBranch& a, const CkfBranch& b) {
@@ -43,7 +57,7 @@ __device__ __forceinline__ bool better(const CkfBranch& a, const CkfBranch& b) {
   return a.order < b.order;
 }
 
-__device__ __forceinline__ void copy_branch(CkfBranch& d, const CkfBranch& s, uint32_t n_entries) {
+__device__ __forceinline__ void copy_branch(CkfBranch& d, const CkfBranch& s) {
   for (int j = 0; j < 5; ++j) d.p[j] = s.p[j];
   for (int j = 0; j < 4; ++j) d.dir[j] = s.dir[j];
   for (int j = 0; j < 15; ++j) d.C[j] = s.C[j];
@@ -54,55 +68,151 @@ __device__ __forceinline__ void copy_branch(CkfBranch& d, const CkfBranch& s, ui
   d.n_entries = s.n_entries;
   d.order = s.order;
   d.sid = s.sid;
-  for (uint32_t j = 0; j < n_entries; ++j) {
-    d.e_sid[j] = s.e_sid[j];
-    d.e_meas[j] = s.e_meas[j];
+  d.node = s.node;
+  d.e_sid = s.e_sid;
+  d.e_meas = s.e_meas;
+}
+
+constexpr int kCkfMaxRings = 256;  // ring rows kept in shared memory (more: read from global)
+
+// Navigation tables of a block, in shared memory: the layer rows, the ring rows (when they fit),
+// the barrel layers' outer face radii, and the layer ids in the order in which a straight line
+// meets them: barrel layers by face radius, disks by face z (ties: lower id first).
+struct NavTables {
+  double lay[kCkfMaxLayers * 8];
+  double ring[kCkfMaxRings * 4];
+  double face_r[kCkfMaxLayers];
+  const double* rings;  // `ring`, or the global table when it does not fit
+  int bar[kCkfMaxLayers], dsk[kCkfMaxLayers];
+  int nbar, ndsk;
+};
+
+// outer face radius of a barrel layer (its flat modules reach sqrt((r + 1)^2 + half_u^2))
+__device__ __forceinline__ double barrel_face(const double* l) { return sqrt((l[1] + 1.0) * (l[1] + 1.0) + l[6] * l[6]); }
+
+__device__ void build_nav_tables(const CkfArgs& a, NavTables& nt) {
+  const bool ring_fit = a.n_rings <= uint32_t(kCkfMaxRings);
+  for (uint32_t j = threadIdx.x; j < 8 * a.n_layers; j += blockDim.x) nt.lay[j] = a.layers[j];
+  if (ring_fit)
+    for (uint32_t j = threadIdx.x; j < 4 * a.n_rings; j += blockDim.x) nt.ring[j] = a.rings[j];
+  if (threadIdx.x == 0) nt.rings = ring_fit ? nt.ring : a.rings;
+  __syncthreads();
+  for (uint32_t li = threadIdx.x; li < a.n_layers; li += blockDim.x) {
+    const double* l = nt.lay + 8 * li;
+    nt.face_r[li] = l[0] == 0.0 ? barrel_face(l) : 0.0;
   }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int nb = 0, nd = 0;
+    for (uint32_t li = 0; li < a.n_layers; ++li) {  // insertion in id order: stable for ties
+      const double* l = nt.lay + 8 * li;
+      if (l[0] == 0.0) {
+        int pos = nb++;
+        for (; pos > 0 && nt.face_r[nt.bar[pos - 1]] > nt.face_r[li]; --pos) nt.bar[pos] = nt.bar[pos - 1];
+        nt.bar[pos] = int(li);
+      } else {
+        const double z = l[1] + (l[1] > 0.0 ? 1.0 : -1.0);
+        int pos = nd++;
+        for (; pos > 0; --pos) {
+          const double* lp = nt.lay + 8 * nt.dsk[pos - 1];
+          if (!(lp[1] + (lp[1] > 0.0 ? 1.0 : -1.0) > z)) break;
+          nt.dsk[pos] = nt.dsk[pos - 1];
+        }
+        nt.dsk[pos] = int(li);
+      }
+    }
+    nt.nbar = nb;
+    nt.ndsk = nd;
+  }
+  __syncthreads();
 }
 
-__device__ __forceinline__ void module_half(const CkfArgs& a, uint32_t id, double& hu, double& hv) {
+__device__ __forceinline__ void module_half(const CkfArgs& a, const NavTables& nt, uint32_t id, double& hu,
+                                            double& hv) {
   const int li = a.layer_of[id];
-  hu = li >= 0 ? a.layers[8 * li + 6] : 1e300;
-  hv = li >= 0 ? a.layers[8 * li + 7] : 1e300;
+  hu = li >= 0 ? nt.lay[8 * li + 6] : 1e300;
+  hv = li >= 0 ? nt.lay[8 * li + 7] : 1e300;
 }
 
-// modules of layer li around the point q: phi bin and row (barrel) or ring (disk), +-1 each
-__device__ __noinline__ int layer_candidates(const CkfArgs& a, uint32_t li, const double q[3], uint32_t out[9]) {
-  const double* l = a.layers + 8 * li;
-  double phi = atan2(q[1], q[0]);
-  if (phi < 0.0) phi += 2.0 * kPi;
+// floor(v) from an FP32 evaluation vf within `err` of the FP64 value v: decided (true, in `out`)
+// when vf lies farther than err from every integer, so that floor(v) = floor(vf); else the
+// caller evaluates v in FP64. (vf - floor(vf) and floor(vf) + 1 - vf are exact for |vf| < 2^23.)
+__device__ __forceinline__ bool floor_sure(float vf, float err, int& out) {
+  const float f = floorf(vf);
+  if (fabsf(vf) < 8388608.0f && vf - f > err && f + 1.0f - vf > err) {
+    out = int(f);
+    return true;
+  }
+  return false;
+}
+
+// ip0 + d taken modulo nphi, as ((ip0 + d) % nphi + nphi) % nphi
+__device__ __forceinline__ uint32_t wrap_bin(int ip0, int d, int nphi) {
+  int ip = ip0 + d;
+  if (ip0 >= 0 && ip0 <= nphi) {
+    if (ip < 0) ip += nphi;
+    if (ip >= nphi) ip -= nphi;
+    return uint32_t(ip);
+  }
+  return uint32_t((ip % nphi + nphi) % nphi);
+}
+
+// modules of layer li around the point q: phi bin and row (barrel) or ring (disk), +-1 each.
+// Each bin index is floor() of an FP64 expression (the angle phi in [0, 2 pi) from atan2, the row
+// z / pitch + rows / 2, the ring (hypot - r0) / pitch); it is first evaluated in FP32 with a bound
+// on the difference from the FP64 value (the FP32 inputs, atan2f / hypotf within 3 ulp, the wrap
+// by 2 pi and the products and sums: a few 1e-7 relative, bounded here by 4e-6 of the bin count
+// or of the magnitudes), and the FP64 value is computed only when the FP32 one lies within that
+// bound of a bin edge. Near phi = 0 the two may wrap differently (bin 0 against bin nphi): the
+// modules +-1 around either are the same, taken in the same order.
+__device__ __noinline__ int layer_candidates(const NavTables& nt, uint32_t li, const double q[3], uint32_t out[9]) {
+  const double* l = nt.lay + 8 * li;
+  const float phf0 = atan2f(d2f(q[1]), d2f(q[0]));
+  const float phf = phf0 < 0.0f ? phf0 + float(2.0 * kPi) : phf0;
+  double phi = -1.0;  // the FP64 angle in [0, 2 pi), on first need
+  auto phi_bin = [&](int nphi) -> int {
+    int b;
+    if (floor_sure(phf * float(double(nphi) / (2.0 * kPi)) + 0.5f, 4e-6f * float(nphi + 1), b)) return b;
+    if (phi < 0.0) {
+      phi = atan2(q[1], q[0]);
+      if (phi < 0.0) phi += 2.0 * kPi;
+    }
+    return int(floor(phi / (2.0 * kPi / nphi) + 0.5));
+  };
   int n = 0;
   if (l[0] == 0.0) {
     const int nphi = int(l[2]), nrows = int(l[3]);
-    const int ip0 = int(floor(phi / (2.0 * kPi / nphi) + 0.5));
-    const int iz0 = int(floor(q[2] / l[4] + 0.5 * nrows));
+    const int ip0 = phi_bin(nphi);
+    const float zq = d2f(q[2]) / d2f(l[4]);
+    int iz0;
+    if (!floor_sure(zq + 0.5f * float(nrows), 4e-6f * (1.0f + fabsf(zq) + float(nrows)), iz0))
+      iz0 = int(floor(q[2] / l[4] + 0.5 * nrows));
     for (int iz = iz0 - 1; iz <= iz0 + 1; ++iz) {
       if (iz < 0 || iz >= nrows) continue;
-      for (int d = -1; d <= 1; ++d) out[n++] = uint32_t(l[5]) + uint32_t(iz * nphi + ((ip0 + d) % nphi + nphi) % nphi);
+      for (int d = -1; d <= 1; ++d) out[n++] = uint32_t(l[5]) + uint32_t(iz * nphi) + wrap_bin(ip0, d, nphi);
     }
   } else {
     const int nr = int(l[2]);
-    const double r = hypot(q[0], q[1]);
-    const int k0 = int(floor((r - l[5]) / l[4]));
+    const float rq = hypotf(d2f(q[0]), d2f(q[1])), r0f = d2f(l[5]), pf = d2f(l[4]);
+    int k0;
+    if (!floor_sure((rq - r0f) / pf, 4e-6f * (1.0f + (rq + fabsf(r0f)) / pf), k0))
+      k0 = int(floor((hypot(q[0], q[1]) - l[5]) / l[4]));
     for (int k = k0 - 1; k <= k0 + 1; ++k) {
       if (k < 0 || k >= nr) continue;
-      const double* rg = a.rings + 4 * (uint32_t(l[3]) + uint32_t(k));
+      const double* rg = nt.rings + 4 * (uint32_t(l[3]) + uint32_t(k));
       const int nphi = int(rg[1]);
-      const int ip0 = int(floor(phi / (2.0 * kPi / nphi) + 0.5));
-      for (int d = -1; d <= 1; ++d) out[n++] = uint32_t(rg[2]) + uint32_t(((ip0 + d) % nphi + nphi) % nphi);
+      const int ip0 = phi_bin(nphi);
+      for (int d = -1; d <= 1; ++d) out[n++] = uint32_t(rg[2]) + wrap_bin(ip0, d, nphi);
     }
   }
   return n;
 }
 
-// outer face radius of a barrel layer (its flat modules reach sqrt((r + 1)^2 + half_u^2))
-__device__ __forceinline__ double barrel_face(const double* l) { return sqrt((l[1] + 1.0) * (l[1] + 1.0) + l[6] * l[6]); }
-
 // straight-line path to the outer face of layer li if ahead and within its extent, else -1
 // (face_r: the barrel layers' outer face radii, computed once a block)
-__device__ double layer_path(const CkfArgs& a, uint32_t li, const double x[3], const double T[3],
-                             const double* face_r) {
-  const double* l = a.layers + 8 * li;
+__device__ double layer_path(const NavTables& nt, uint32_t li, const double x[3], const double T[3]) {
+  const double* l = nt.lay + 8 * li;
+  const double* face_r = nt.face_r;
   double s;
   if (l[0] == 0.0) {
     const double aa = T[0] * T[0] + T[1] * T[1], b = x[0] * T[0] + x[1] * T[1];
@@ -159,8 +269,9 @@ __device__ __forceinline__ bool surely_outside(const float* __restrict__ f, cons
 }
 
 // nearest of `cand` crossed by the parabola x + s T + s^2/2 k within bounds and margin
-__device__ __noinline__ int nearest_crossed(const CkfArgs& a, const uint32_t* cand, int nc, const double x[3], const double T[3],
-                               const double k[3], double bend, const uint32_t* skip, int nskip, double& s_out) {
+__device__ __noinline__ int nearest_crossed(const CkfArgs& a, const NavTables& nt, const uint32_t* cand, int nc,
+                                            const double x[3], const double T[3], const double k[3], double bend,
+                                            const uint32_t* skip, int nskip, double& s_out) {
   int best = -1;
   double best_s = 0.0;
   const float Tf[3] = {d2f(T[0]), d2f(T[1]), d2f(T[2])}, kf[3] = {d2f(k[0]), d2f(k[1]), d2f(k[2])};
@@ -172,7 +283,7 @@ __device__ __noinline__ int nearest_crossed(const CkfArgs& a, const uint32_t* ca
     const double c[3] = {rec[9], rec[10], rec[11]};
     const double d[3] = {c[0] - x[0], c[1] - x[1], c[2] - x[2]};
     double hu, hv;
-    module_half(a, id, hu, hv);
+    module_half(a, nt, id, hu, hv);
     if (surely_outside(reinterpret_cast<const float*>(rec + 16), d, Tf, kf, knorm, bendf, hu, hv)) continue;
     const double u[3] = {rec[0], rec[1], rec[2]}, v[3] = {rec[3], rec[4], rec[5]};
     const double n[3] = {rec[6], rec[7], rec[8]};
@@ -200,46 +311,6 @@ __device__ __noinline__ int nearest_crossed(const CkfArgs& a, const uint32_t* ca
   return best;
 }
 
-// Layer tables of a block, in shared memory: the barrel layers' outer face radii, and the layer
-// ids in the order in which a straight line meets them: barrel layers by face radius, disks by
-// face z (ties: lower id first).
-struct NavTables {
-  double face_r[kCkfMaxLayers];
-  int bar[kCkfMaxLayers], dsk[kCkfMaxLayers];
-  int nbar, ndsk;
-};
-
-__device__ void build_nav_tables(const CkfArgs& a, NavTables& nt) {
-  for (uint32_t li = threadIdx.x; li < a.n_layers; li += blockDim.x) {
-    const double* l = a.layers + 8 * li;
-    nt.face_r[li] = l[0] == 0.0 ? barrel_face(l) : 0.0;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int nb = 0, nd = 0;
-    for (uint32_t li = 0; li < a.n_layers; ++li) {  // insertion in id order: stable for ties
-      const double* l = a.layers + 8 * li;
-      if (l[0] == 0.0) {
-        int pos = nb++;
-        for (; pos > 0 && nt.face_r[nt.bar[pos - 1]] > nt.face_r[li]; --pos) nt.bar[pos] = nt.bar[pos - 1];
-        nt.bar[pos] = int(li);
-      } else {
-        const double z = l[1] + (l[1] > 0.0 ? 1.0 : -1.0);
-        int pos = nd++;
-        for (; pos > 0; --pos) {
-          const double* lp = a.layers + 8 * nt.dsk[pos - 1];
-          if (!(lp[1] + (lp[1] > 0.0 ? 1.0 : -1.0) > z)) break;
-          nt.dsk[pos] = nt.dsk[pos - 1];
-        }
-        nt.dsk[pos] = int(li);
-      }
-    }
-    nt.nbar = nb;
-    nt.ndsk = nd;
-  }
-  __syncthreads();
-}
-
 // the next module from (x, T) on surface `cur`: the nearest crossing among the current layer's
 // modules around x and the modules of the layers ahead, taken in order of face path (ties:
 // lower index first) until a layer's face lies more than 20 mm beyond the nearest crossing
@@ -256,8 +327,8 @@ __device__ int navigate(const CkfArgs& a, int cur, const double x[3], const doub
     uint32_t sk[5];
     for (int j = 0; j < nskip; ++j) sk[j] = skip[j];
     sk[nskip] = uint32_t(cur);
-    const int nc = layer_candidates(a, uint32_t(cur_layer), x, cand);
-    best = nearest_crossed(a, cand, nc, x, T, k, bend, sk, nskip + 1, best_s);
+    const int nc = layer_candidates(nt, uint32_t(cur_layer), x, cand);
+    best = nearest_crossed(a, nt, cand, nc, x, T, k, bend, sk, nskip + 1, best_s);
   }
   // the head of each order: the next layer ahead (face path > 0, within its extent) and its path
   int pb = 0, pd = 0, lb = -1, ld = -1;
@@ -270,7 +341,7 @@ __device__ int navigate(const CkfArgs& a, int cur, const double x[3], const doub
     while (pb < nt.nbar) {
       const int li = nt.bar[pb++];
       if (li == cur_layer) continue;
-      const double s = layer_path(a, uint32_t(li), x, T, nt.face_r);
+      const double s = layer_path(nt, uint32_t(li), x, T);
       if (s > 0.0) {
         lb = li;
         sb = s;
@@ -285,7 +356,7 @@ __device__ int navigate(const CkfArgs& a, int cur, const double x[3], const doub
       dpos += dstep;
       ++pd;
       if (li == cur_layer) continue;
-      const double s = layer_path(a, uint32_t(li), x, T, nt.face_r);
+      const double s = layer_path(nt, uint32_t(li), x, T);
       if (s > 0.0) {
         ld = li;
         sd = s;
@@ -302,9 +373,9 @@ __device__ int navigate(const CkfArgs& a, int cur, const double x[3], const doub
     if (best >= 0 && sl > best_s + 20.0) break;
     const double h = 0.5 * sl * sl;
     const double q[3] = {x[0] + sl * T[0] + h * k[0], x[1] + sl * T[1] + h * k[1], x[2] + sl * T[2] + h * k[2]};
-    const int nc = layer_candidates(a, uint32_t(pick), q, cand);
+    const int nc = layer_candidates(nt, uint32_t(pick), q, cand);
     double sm = 0.0;
-    const int m = nearest_crossed(a, cand, nc, x, T, k, bend, skip, nskip, sm);
+    const int m = nearest_crossed(a, nt, cand, nc, x, T, k, bend, skip, nskip, sm);
     if (m >= 0 && (best < 0 || sm < best_s)) {
       best = m;
       best_s = sm;
@@ -362,7 +433,7 @@ __device__ int predict(const CkfArgs& a, const F& fld, const NavTables& nt, cons
           propagate_mixed<kPlain, 3>(fld, a.opt, s, s.nf, r, T, lam, dr, dT, 0.0f, h, att, rej, kend, learn);
       const double d[3] = {r[0] - s.c[0], r[1] - s.c[1], r[2] - s.c[2]};
       double hu, hv;
-      module_half(a, uint32_t(m), hu, hv);
+      module_half(a, nt, uint32_t(m), hu, hv);
       if ((st & ~TKF_TRACK_OUT_OF_FIELD) || fabs(dot3(s.u, d)) > hu || fabs(dot3(s.v, d)) > hv) {
         skip[nskip++] = uint32_t(m);
         continue;
@@ -413,7 +484,7 @@ __device__ int predict(const CkfArgs& a, const F& fld, const NavTables& nt, cons
       const uint32_t st = propagate<kPlain, 3>(fld, a.opt, s, r, T, lam, dr, dT, 0.0, h, att, rej, kend, learn);
       const double d[3] = {r[0] - s.c[0], r[1] - s.c[1], r[2] - s.c[2]};
       double hu, hv;
-      module_half(a, uint32_t(m), hu, hv);
+      module_half(a, nt, uint32_t(m), hu, hv);
       if ((st & ~TKF_TRACK_OUT_OF_FIELD) || fabs(dot3(s.u, d)) > hu || fabs(dot3(s.v, d)) > hv) {
         skip[nskip++] = uint32_t(m);
         continue;
@@ -568,14 +639,17 @@ struct CkfSeed {
   uint32_t order;   // creation counter of the children
   uint32_t have_best;
   uint32_t first;   // 1 before the first step (the seed's own surface)
+  uint32_t area;    // the children area that holds the beam (0 or 1)
+  uint8_t act[8];   // the beam's slots, in rank order
 };
 
 struct CkfWork {
-  CkfBranch* slots;  // per seed: beam B, children B (C + 1), best 1
+  CkfBranch* slots;  // per seed: two areas of B (C + 1) children, then the best ended branch
   CkfPred* pred;     // per seed: B
   CkfSeed* seeds;    // per seed
   uint32_t* list;    // the branch slots (t B + bi) in the beam, for the next step's phases 1 and 2
   uint32_t* count;   // their number
+  CkfNode* nodes;    // per seed: ckf_steps(max_entries) x B history nodes
 };
 
 // Appends each seed's beam slots to the list for the next step: in seed order within a block
@@ -602,28 +676,44 @@ __device__ __forceinline__ CkfBranch* seed_slots(const CkfWork& w, uint32_t t, u
   return w.slots + size_t(t) * slots_per_seed(B);
 }
 
-// Outputs of seed i from its best ended branch.
-__device__ void write_candidate(const CkfArgs& a, uint32_t i, const CkfBranch* best, bool have_best) {
+__device__ __forceinline__ CkfNode* seed_nodes(const CkfArgs& a, const CkfWork& w, uint32_t t) {
+  return w.nodes + size_t(t) * ckf_steps(a.max_entries) * a.beam;
+}
+
+// Outputs of seed i from its best ended branch: its entries read back along the history tree
+// from its last node (slot t's nodes).
+__device__ void write_candidate(const CkfArgs& a, const CkfWork& w, uint32_t t, uint32_t i, const CkfBranch* best,
+                                bool have_best) {
   const uint32_t n = a.n_seeds;
   const uint32_t ne = have_best ? best->n_entries : 0;
   a.n_entries[i] = ne;
   a.n_meas_out[i] = have_best ? best->n_meas : 0;
   a.chi2[i] = have_best ? best->chi2 : 0.0;
-  for (uint32_t j = 0; j < a.max_entries; ++j) {
-    a.entry_sid[size_t(j) * n + i] = j < ne ? best->e_sid[j] : 0u;
-    a.entry_meas[size_t(j) * n + i] = j < ne ? best->e_meas[j] : -1;
+  for (uint32_t j = ne; j < a.max_entries; ++j) {
+    a.entry_sid[size_t(j) * n + i] = 0u;
+    a.entry_meas[size_t(j) * n + i] = -1;
+  }
+  const CkfNode* nodes = seed_nodes(a, w, t);
+  const uint32_t n_nodes = ckf_steps(a.max_entries) * a.beam;
+  int32_t at = have_best ? best->node : -1;
+  for (uint32_t j = ne; j-- > 0;) {
+    const bool ok = at >= 0 && uint32_t(at) < n_nodes;
+    const CkfNode nd = ok ? nodes[at] : CkfNode{0u, -1, -1};
+    a.entry_sid[size_t(j) * n + i] = nd.sid;
+    a.entry_meas[size_t(j) * n + i] = nd.meas;
+    at = nd.parent;
   }
 }
 
 __device__ void init_seed(const CkfArgs& a, const CkfWork& w, uint32_t t, CkfSeed& st);
-__device__ uint32_t beam_seed(const CkfArgs& a, const CkfWork& w, uint32_t t, uint32_t last);
+__device__ uint32_t beam_seed(const CkfArgs& a, const CkfWork& w, uint32_t t, uint32_t step, uint32_t last);
 
 // The seed's starting branch (thread t finds seed perm[t]); a seed on a missing surface or event
 // gets no candidate at once.
 __global__ void __launch_bounds__(kCkfBlock) ckf_init_kernel(const CkfArgs a, CkfWork w) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = t < a.n_seeds;
-  CkfSeed st{0u, 1u, 0u, 1u};
+  CkfSeed st{0u, 1u, 0u, 1u, 0u, {0, 0, 0, 0, 0, 0, 0, 0}};
   if (live) init_seed(a, w, t, st);
   append_beam(w, t, st.n_act, a.beam);
 }
@@ -645,9 +735,12 @@ __device__ void init_seed(const CkfArgs& a, const CkfWork& w, uint32_t t, CkfSee
     b0.n_meas = b0.holes = b0.n_entries = 0;
     b0.order = 0;
     b0.sid = -1;
+    b0.node = -1;
     st.n_act = 1;
+    st.area = 0;
+    st.act[0] = 0;
   } else {
-    write_candidate(a, i, nullptr, false);
+    write_candidate(a, w, t, i, nullptr, false);
   }
   w.seeds[t] = st;
 }
@@ -664,7 +757,7 @@ __global__ void __launch_bounds__(kCkfBlock) ckf_predict_kernel(const CkfArgs a,
   const uint32_t t = g / B, bi = g % B;
   const CkfSeed st = w.seeds[t];
   CkfPred& pr = w.pred[g];
-  const CkfBranch& br = seed_slots(w, t, B)[bi];
+  const CkfBranch& br = seed_slots(w, t, B)[st.act[bi]];
   int target;
   if (st.first) {
     target = int(a.seed_sid[a.perm[t]]);
@@ -702,9 +795,14 @@ __global__ void __launch_bounds__(kCkfBlock) ckf_gate_kernel(const CkfArgs a, Ck
   const uint32_t i = a.perm[t];
   const uint32_t ev = a.seed_event ? a.seed_event[i] : 0u;
   const uint32_t* __restrict__ moff = a.meas_off + size_t(ev) * (a.n_surf + 1);  // this event's offsets
+  const CkfSeed st = w.seeds[t];
   CkfBranch* slots = seed_slots(w, t, B);
-  const CkfBranch& br = slots[bi];
-  CkfBranch* kids = slots + B + bi * (kCkfChildren + 1);
+  const CkfBranch& br = slots[st.act[bi]];
+  // the children go to the other area: the beam kernel keeps its choice there
+  CkfBranch* kids = slots + (st.area ^ 1u) * area_slots(B) + bi * (kCkfChildren + 1);
+  const double br_chi2 = br.chi2;
+  const uint32_t br_meas = br.n_meas, br_holes = br.holes, br_entries = br.n_entries;
+  const int32_t br_node = br.node;
   double pp[5], pdir[4], Cp[15];
   for (int j = 0; j < 5; ++j) pp[j] = pr.pp[j];
   for (int j = 0; j < 4; ++j) pdir[j] = pr.pdir[j];
@@ -747,45 +845,50 @@ __global__ void __launch_bounds__(kCkfBlock) ckf_gate_kernel(const CkfArgs a, Ck
     if (nk < kCkfChildren) ++nk;
   }
   for (int q = 0; q < nk; ++q) {
-    CkfBranch& ch = kids[q];
-    copy_branch(ch, br, br.n_entries);
-    for (int j = 0; j < 5; ++j) ch.p[j] = pp[j];
-    for (int j = 0; j < 15; ++j) ch.C[j] = Cp[j];
+    double p[5], C[15];
+    for (int j = 0; j < 5; ++j) p[j] = pp[j];
+    for (int j = 0; j < 15; ++j) C[j] = Cp[j];
     const uint32_t mi = km[q];
     double c2;
-    update(ch.p, ch.C, a.loc0[mi], a.loc1[mi], a.v00[mi], a.v01[mi], a.v11[mi], c2);
+    update(p, C, a.loc0[mi], a.loc1[mi], a.v00[mi], a.v01[mi], a.v11[mi], c2);
     // filtered direction: the predicted one turned by the update's angle increments
     double sd, cd, se, ce;
-    small_sincos(ch.p[2], sd, cd);
-    small_sincos(ch.p[3], se, ce);
+    small_sincos(p[2], sd, cd);
+    small_sincos(p[3], se, ce);
+    CkfBranch& ch = kids[q];
     ch.dir[0] = pdir[0] * cd + pdir[1] * sd;
     ch.dir[1] = pdir[1] * cd - pdir[0] * sd;
     ch.dir[2] = pdir[2] * ce + pdir[3] * se;
     ch.dir[3] = pdir[3] * ce - pdir[2] * se;
-    ch.p[2] = 0.0;
-    ch.p[3] = 0.0;
+    p[2] = 0.0;
+    p[3] = 0.0;
+    for (int j = 0; j < 5; ++j) ch.p[j] = p[j];
+    for (int j = 0; j < 15; ++j) ch.C[j] = C[j];
     ch.h_ctrl = h;
-    ch.chi2 += c2;
-    ch.n_meas += 1;
+    ch.chi2 = br_chi2 + c2;
+    ch.n_meas = br_meas + 1;
     ch.holes = 0;
+    ch.n_entries = br_entries + 1;
     ch.sid = target;
-    ch.e_sid[ch.n_entries] = uint32_t(target);
-    ch.e_meas[ch.n_entries] = int32_t(mi);
-    ch.n_entries += 1;
+    ch.node = br_node;
+    ch.e_sid = uint32_t(target);
+    ch.e_meas = int32_t(mi);
   }
   uint32_t hole = 0;
-  if (br.holes < a.max_holes) {
+  if (br_holes < a.max_holes) {
     CkfBranch& ch = kids[nk];
-    copy_branch(ch, br, br.n_entries);
     for (int j = 0; j < 5; ++j) ch.p[j] = pp[j];
     for (int j = 0; j < 4; ++j) ch.dir[j] = pdir[j];
     for (int j = 0; j < 15; ++j) ch.C[j] = Cp[j];
     ch.h_ctrl = h;
-    ch.holes += 1;
+    ch.chi2 = br_chi2;
+    ch.n_meas = br_meas;
+    ch.holes = br_holes + 1;
+    ch.n_entries = br_entries + 1;
     ch.sid = target;
-    ch.e_sid[ch.n_entries] = uint32_t(target) | TKF_SID_NO_MEASUREMENT;
-    ch.e_meas[ch.n_entries] = -1;
-    ch.n_entries += 1;
+    ch.node = br_node;
+    ch.e_sid = uint32_t(target) | TKF_SID_NO_MEASUREMENT;
+    ch.e_meas = -1;
     hole = 1;
   }
   pr.nk = uint32_t(nk);
@@ -794,27 +897,32 @@ __global__ void __launch_bounds__(kCkfBlock) ckf_gate_kernel(const CkfArgs a, Ck
 
 // Phase 3, one thread per seed: the children numbered in creation order (branch by branch,
 // measurements by chi2, then the hole), the best ended branch, the beam of the best B children.
-// `last`: the final step; the candidate is written when the search is over.
-__global__ void __launch_bounds__(kCkfBlock) ckf_beam_kernel(const CkfArgs a, CkfWork w, uint32_t last) {
+// `step`: the step's index (the row of history nodes it writes); `last`: the final step; the
+// candidate is written when the search is over.
+__global__ void __launch_bounds__(kCkfBlock) ckf_beam_kernel(const CkfArgs a, CkfWork w, uint32_t step,
+                                                             uint32_t last) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t n_next = 0;
-  if (t < a.n_seeds) n_next = beam_seed(a, w, t, last);
+  if (t < a.n_seeds) n_next = beam_seed(a, w, t, step, last);
   append_beam(w, t, n_next, a.beam);
 }
 
-// The beam of seed slot t after a step; returns its size (0: the search is over).
-__device__ uint32_t beam_seed(const CkfArgs& a, const CkfWork& w, uint32_t t, uint32_t last) {
+// The beam of seed slot t after a step; returns its size (0: the search is over). The kept
+// children stay where the gate wrote them (the other area becomes the beam's); each gets its
+// entry as history node (step, rank).
+__device__ uint32_t beam_seed(const CkfArgs& a, const CkfWork& w, uint32_t t, uint32_t step, uint32_t last) {
   CkfSeed st = w.seeds[t];
   if (st.n_act == 0) return 0;  // over (candidate written)
   const uint32_t B = a.beam;
-  CkfBranch* act = seed_slots(w, t, B);
-  CkfBranch* kids = act + B;
-  CkfBranch* best = kids + B * (kCkfChildren + 1);
+  CkfBranch* slots = seed_slots(w, t, B);
+  const uint32_t kid_area = (st.area ^ 1u) * area_slots(B);
+  CkfBranch* kids = slots + kid_area;
+  CkfBranch* best = slots + 2 * area_slots(B);
   const CkfPred* pr = w.pred + size_t(t) * B;
   uint32_t kid_at[8 * (kCkfChildren + 1)];
   uint32_t n_kids = 0;
   for (uint32_t bi = 0; bi < st.n_act; ++bi) {
-    const CkfBranch& br = act[bi];
+    const CkfBranch& br = slots[st.act[bi]];
     const uint32_t nc = pr[bi].target < 0 ? 0u : pr[bi].nk + pr[bi].hole;
     for (uint32_t q = 0; q < nc; ++q) {
       const uint32_t k = bi * (kCkfChildren + 1) + q;
@@ -825,34 +933,57 @@ __device__ uint32_t beam_seed(const CkfArgs& a, const CkfWork& w, uint32_t t, ui
     // compatible measurement
     const bool ends = pr[bi].target < 0 || (pr[bi].nk == 0 && pr[bi].hole == 0);
     if (ends && (!st.have_best || better(br, *best))) {
-      copy_branch(*best, br, br.n_entries);
+      copy_branch(*best, br);
       st.have_best = 1;
     }
   }
   st.first = 0;
   // the beam: the best B children, in rank order
   const uint32_t n_act = n_kids < B ? n_kids : B;
+  CkfNode* nodes = seed_nodes(a, w, t) + size_t(step) * B;
   uint32_t taken = 0;
   for (uint32_t q = 0; q < n_act; ++q) {
     int pick = -1;
     for (uint32_t j = 0; j < n_kids; ++j)
       if (!((taken >> j) & 1u) && (pick < 0 || better(kids[kid_at[j]], kids[kid_at[pick]]))) pick = int(j);
     taken |= 1u << pick;
-    copy_branch(act[q], kids[kid_at[pick]], kids[kid_at[pick]].n_entries);
+    CkfBranch& k = kids[kid_at[pick]];
+    nodes[q] = CkfNode{k.e_sid, k.e_meas, k.node};
+    k.node = int32_t(step * B + q);
+    st.act[q] = uint8_t(kid_area + kid_at[pick]);
   }
+  st.area ^= 1u;
   st.n_act = last ? 0u : n_act;
-  if (st.n_act == 0) write_candidate(a, a.perm[t], best, st.have_best != 0);
+  if (st.n_act == 0) write_candidate(a, w, t, a.perm[t], best, st.have_best != 0);
   w.seeds[t] = st;
   return st.n_act;
 }
+
+// Workspace layout (byte offsets): branch slots, the seed-order histogram and permutation, FP32
+// copies of the measurements (16-byte aligned), the predictions of every beam slot, the per-seed
+// states, the list of beam slots and its count, the history nodes.
+struct CkfLayout {
+  size_t hist, meas_f, pred, seeds, list, count, nodes, total;
+  CkfLayout(uint32_t n_seeds, uint32_t beam, uint32_t n_meas, uint32_t max_entries) {
+    hist = size_t(n_seeds) * slots_per_seed(beam) * sizeof(CkfBranch);
+    meas_f = hist + ((sizeof(uint32_t) * (kCkfOrderBins + size_t(n_seeds)) + 15) & ~size_t(15));
+    pred = meas_f + sizeof(float4) * size_t(n_meas);
+    seeds = pred + sizeof(CkfPred) * size_t(n_seeds) * beam;
+    list = (seeds + sizeof(CkfSeed) * size_t(n_seeds) + 7) & ~size_t(7);
+    count = list + sizeof(uint32_t) * size_t(n_seeds) * beam;
+    nodes = count + sizeof(uint32_t);
+    total = nodes + sizeof(CkfNode) * size_t(n_seeds) * ckf_steps(max_entries) * beam;
+  }
+};
 
 template <class F>
 cudaError_t launch_ckf(const CkfArgs& a_in, const F& fld, cudaStream_t stream) {
   CkfArgs a = a_in;
   if (a.opt.max_steps > kCkfMaxSteps) a.opt.max_steps = kCkfMaxSteps;
-  // the seed order: histogram, scan and scatter into the workspace after the branch slots
-  char* base = static_cast<char*>(a.ws) + size_t(a.n_seeds) * slots_per_seed(a.beam) * sizeof(CkfBranch);
-  uint32_t* hist = reinterpret_cast<uint32_t*>(base);
+  const CkfLayout L(a.n_seeds, a.beam, a.n_meas, a.max_entries);
+  char* base = static_cast<char*>(a.ws);
+  // the seed order: histogram, scan and scatter
+  uint32_t* hist = reinterpret_cast<uint32_t*>(base + L.hist);
   uint32_t* perm = hist + kCkfOrderBins;
   cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kCkfOrderBins, stream);
   if (e != cudaSuccess) return e;
@@ -861,28 +992,26 @@ cudaError_t launch_ckf(const CkfArgs& a_in, const F& fld, cudaStream_t stream) {
   ckf_order_scan_kernel<<<1, kCkfOrderBins, 0, stream>>>(hist);
   ckf_order_scatter_kernel<<<og, 256, 0, stream>>>(a.seed_par, a.n_seeds, hist, perm);
   a.perm = perm;
-  // FP32 copies of the measurements for the gate's first bound (16-byte aligned after the order)
-  char* mf_base = base + ((sizeof(uint32_t) * (kCkfOrderBins + size_t(a.n_seeds)) + 15) & ~size_t(15));
-  float4* mf = reinterpret_cast<float4*>(mf_base);
+  // FP32 copies of the measurements for the gate's first bound
+  float4* mf = reinterpret_cast<float4*>(base + L.meas_f);
   if (a.n_meas > 0) {
     const unsigned mg = (a.n_meas + 255) / 256 < 4096 ? (a.n_meas + 255) / 256 : 4096;
     ckf_meas_f32_kernel<<<mg, 256, 0, stream>>>(a.loc0, a.loc1, a.v00, a.v11, a.n_meas, mf);
   }
   a.meas_f = mf;
-  // predictions and per-seed states after the FP32 measurements (8-byte aligned)
   CkfWork w;
-  w.slots = static_cast<CkfBranch*>(a.ws);
-  char* p = mf_base + sizeof(float4) * size_t(a.n_meas);
-  w.pred = reinterpret_cast<CkfPred*>(p);
-  w.seeds = reinterpret_cast<CkfSeed*>(p + sizeof(CkfPred) * size_t(a.n_seeds) * a.beam);
-  w.list = reinterpret_cast<uint32_t*>(w.seeds + a.n_seeds);
-  w.count = w.list + size_t(a.n_seeds) * a.beam;
+  w.slots = reinterpret_cast<CkfBranch*>(base);
+  w.pred = reinterpret_cast<CkfPred*>(base + L.pred);
+  w.seeds = reinterpret_cast<CkfSeed*>(base + L.seeds);
+  w.list = reinterpret_cast<uint32_t*>(base + L.list);
+  w.count = reinterpret_cast<uint32_t*>(base + L.count);
+  w.nodes = reinterpret_cast<CkfNode*>(base + L.nodes);
   const unsigned gs = (a.n_seeds + kCkfBlock - 1) / kCkfBlock;
   const unsigned gb = unsigned((size_t(a.n_seeds) * a.beam + kCkfBlock - 1) / kCkfBlock);
   if ((e = cudaMemsetAsync(w.count, 0, sizeof(uint32_t), stream)) != cudaSuccess) return e;
   ckf_init_kernel<<<gs, kCkfBlock, 0, stream>>>(a, w);
   // every step adds an entry to each surviving branch: at most max_entries + 2 steps
-  const uint32_t n_steps = a.max_entries + 2;
+  const uint32_t n_steps = ckf_steps(a.max_entries);
   for (uint32_t step = 0; step < n_steps; ++step) {
     if (a.mixed)
       ckf_predict_kernel<true><<<gb, kCkfBlock, 0, stream>>>(a, fld, w);
@@ -890,20 +1019,15 @@ cudaError_t launch_ckf(const CkfArgs& a_in, const F& fld, cudaStream_t stream) {
       ckf_predict_kernel<false><<<gb, kCkfBlock, 0, stream>>>(a, fld, w);
     ckf_gate_kernel<<<gb, kCkfBlock, 0, stream>>>(a, w);
     if ((e = cudaMemsetAsync(w.count, 0, sizeof(uint32_t), stream)) != cudaSuccess) return e;
-    ckf_beam_kernel<<<gs, kCkfBlock, 0, stream>>>(a, w, step + 1 == n_steps ? 1u : 0u);
+    ckf_beam_kernel<<<gs, kCkfBlock, 0, stream>>>(a, w, step, step + 1 == n_steps ? 1u : 0u);
   }
   return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t ckf_workspace_bytes(uint32_t n_seeds, uint32_t beam, uint32_t n_meas) {
-  // branch slots, the seed-order histogram and permutation, FP32 copies of the measurements,
-  // then the predictions of every branch slot and the per-seed states
-  return size_t(n_seeds) * (beam * (kCkfChildren + 2) + 1) * sizeof(CkfBranch) +
-         ((sizeof(uint32_t) * (kCkfOrderBins + size_t(n_seeds)) + 15) & ~size_t(15)) + sizeof(float4) * size_t(n_meas) +
-         sizeof(CkfPred) * size_t(n_seeds) * beam + sizeof(CkfSeed) * size_t(n_seeds) +
-         sizeof(uint32_t) * (size_t(n_seeds) * beam + 1);
+size_t ckf_workspace_bytes(uint32_t n_seeds, uint32_t beam, uint32_t n_meas, uint32_t max_entries) {
+  return CkfLayout(n_seeds, beam, n_meas, max_entries).total;
 }
 
 cudaError_t launch_find_tracks(const CkfArgs& a, const FieldDev& f, cudaStream_t stream) {

@@ -148,6 +148,7 @@ struct CkfArgs {
   const double* __restrict__ layers;
   uint32_t n_layers;
   const double* __restrict__ rings;
+  uint32_t n_rings;
   const int32_t* __restrict__ layer_of;
   MaterialDev mat;
   OptionsDev opt;
@@ -163,7 +164,7 @@ struct CkfArgs {
   const uint32_t* __restrict__ perm;  // seed found by each thread (set by the launch)
   const float4* __restrict__ meas_f;  // FP32 loc0, loc1, V00, V11 (set by the launch)
 };
-size_t ckf_workspace_bytes(uint32_t n_seeds, uint32_t beam, uint32_t n_meas);
+size_t ckf_workspace_bytes(uint32_t n_seeds, uint32_t beam, uint32_t n_meas, uint32_t max_entries);
 cudaError_t launch_find_tracks(const CkfArgs& a, const FieldDev& f, cudaStream_t stream);
 
 // Launch shape of the persistent fit: threads per block, blocks in the grid, tracks a warp
