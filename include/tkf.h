@@ -332,11 +332,12 @@ tkf_status tkf_fit(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf
 
 /* The same fit from HOST arrays: copies the inputs to a device staging area owned by the
  * context (grown on demand), fits, and copies the outputs back; returns when the outputs are
- * in host memory. Batches of at least 131,072 tracks whose offsets never decrease are cut
- * into up to 4 chunks pipelined over two copy streams of the context, `stream` and a second
- * compute stream (a chunk fits while its predecessor finishes its tail): the
- * copy-in of a chunk and the copy-out of the previous one overlap the fit of the current one
- * (results identical to one piece). Page-locked host memory gives asynchronous copies.
+ * in host memory. Batches of at least 131,072 tracks are cut into up to 8 chunks of
+ * consecutive tracks pipelined over two copy streams of the context, `stream` and a second
+ * compute stream (a chunk fits while its predecessor finishes its tail): the copy-in of a chunk
+ * and the copy-out of the previous one overlap the fit of the current one (results identical
+ * to one piece). A chunk copies the measurements between the least and the greatest of its
+ * tracks' offsets, grown onto what earlier chunks copied as one interval (no byte twice). Page-locked host memory gives asynchronous copies.
  * `stream` is synchronized first (its earlier work must not use the staging area) and at the
  * end. Pointers as in tkf_fit_inputs / tkf_fit_outputs but in host memory. Errors as tkf_fit,
  * plus TKF_ERR_OOM. */

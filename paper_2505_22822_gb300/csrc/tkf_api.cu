@@ -746,9 +746,9 @@ tkf_status tkf_fit_host(tkf_context ctx, tkf_geometry geo, tkf_field field, cons
   dout.steps = hout->steps ? reinterpret_cast<uint32_t*>(take(b_steps)) : nullptr;
   // Pipeline over chunks of tracks: the copy-in of chunk c + 1 (h2d stream) and the copy-out of
   // chunk c - 1 (d2h stream) overlap the fit of chunk c (the caller's stream). Each chunk is the
-  // tracks [t0, t1) with their measurements [offsets[t0], offsets[t1]), copied to the same
-  // positions of full-size staging arrays, so offsets stay absolute; seeds and outputs are SoA
-  // rows of the full batch, so a chunk's fit runs with the batch's row stride.
+  // tracks [t0, t1) with the measurements they can reference, copied to the same positions of
+  // full-size staging arrays, so offsets stay absolute; seeds and outputs are SoA rows of the
+  // full batch, so a chunk's fit runs with the batch's row stride.
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaSuccess;
   if (!ctx->h2d_stream) {
@@ -761,16 +761,10 @@ tkf_status tkf_fit_host(tkf_context ctx, tkf_geometry geo, tkf_field field, cons
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_host: stream or event creation");
   }
-  uint32_t chunks = n >= size_t(kHostChunkMinTracks) * 2
-                        ? uint32_t(kHostChunksMax < n / kHostChunkMinTracks ? kHostChunksMax : n / kHostChunkMinTracks)
-                        : 1u;
-  if (chunks > 1) {
-    // a chunk carries the measurements between its first and last offset: only when the offsets
-    // never decrease does that hold every measurement its tracks can reference
-    bool monotone = true;
-    for (size_t i = 0; i < n; ++i) monotone &= hin->offsets[i + 1] >= hin->offsets[i];
-    if (!monotone) chunks = 1;
-  }
+  const uint32_t chunks =
+      n >= size_t(kHostChunkMinTracks) * 2
+          ? uint32_t(kHostChunksMax < n / kHostChunkMinTracks ? kHostChunksMax : n / kHostChunkMinTracks)
+          : 1u;
   tkf::FitArgs full = make_args(geo, o, &din, &dout);
   const bool learned = o->step_mode == TKF_STEP_LEARNED;
   // one workspace per chunk (a chunk has at most n / chunks + 1 tracks)
@@ -808,19 +802,40 @@ tkf_status tkf_fit_host(tkf_context ctx, tkf_geometry geo, tkf_field field, cons
     if (e == cudaSuccess && cols)
       e = cudaMemcpy2DAsync(dst, n * 8, src, n * 8, cols * 8, rows, cudaMemcpyDeviceToHost, ctx->d2h_stream);
   };
+  // measurements copied so far: one interval [cov_lo, cov_hi), grown by every chunk, so that no
+  // byte is copied twice while an earlier chunk's fit may read it
+  size_t cov_lo = 0, cov_hi = 0;
+  auto h2d_meas = [&](size_t a0, size_t a1) {
+    if (a1 <= a0) return;
+    const size_t k = a1 - a0;
+    h2d(const_cast<double*>(din.loc0) + a0, hin->loc0 + a0, k * 8);
+    h2d(const_cast<double*>(din.loc1) + a0, hin->loc1 + a0, k * 8);
+    h2d(const_cast<double*>(din.v00) + a0, hin->v00 + a0, k * 8);
+    h2d(const_cast<double*>(din.v01) + a0, hin->v01 + a0, k * 8);
+    h2d(const_cast<double*>(din.v11) + a0, hin->v11 + a0, k * 8);
+    h2d(const_cast<uint32_t*>(din.sid) + a0, hin->sid + a0, k * 4);
+  };
   for (uint32_t c = 0; c < chunks; ++c) {
     const size_t t0 = n * c / chunks, t1 = n * (c + 1) / chunks, nt = t1 - t0;
-    // one chunk: every measurement; offsets beyond n_meas are the kernel's to flag
-    const size_t m0 = chunks == 1 ? 0 : hin->offsets[t0];
-    const size_t m1 = chunks == 1 ? m : (hin->offsets[t1] <= m ? hin->offsets[t1] : m);
-    const size_t mc = m1 > m0 ? m1 - m0 : 0;
-    h2d(const_cast<uint32_t*>(din.offsets) + t0, hin->offsets + t0, (nt + 1) * 4);
-    h2d(const_cast<double*>(din.loc0) + m0, hin->loc0 + m0, mc * 8);
-    h2d(const_cast<double*>(din.loc1) + m0, hin->loc1 + m0, mc * 8);
-    h2d(const_cast<double*>(din.v00) + m0, hin->v00 + m0, mc * 8);
-    h2d(const_cast<double*>(din.v01) + m0, hin->v01 + m0, mc * 8);
-    h2d(const_cast<double*>(din.v11) + m0, hin->v11 + m0, mc * 8);
-    h2d(const_cast<uint32_t*>(din.sid) + m0, hin->sid + m0, mc * 4);
+    // the measurements the chunk's tracks can reference lie between the least and the greatest
+    // of their offsets (a track whose range is reversed or beyond n_meas reads none: the kernel
+    // flags it); scanned here, while the earlier chunks' copies and fits run
+    size_t lo = m, hi = 0;
+    for (size_t i = t0; i <= t1; ++i) {
+      const size_t v = hin->offsets[i] < m ? hin->offsets[i] : m;
+      lo = v < lo ? v : lo;
+      hi = v > hi ? v : hi;
+    }
+    if (c == 0) {
+      cov_lo = cov_hi = lo;
+    }
+    const size_t new_lo = lo < cov_lo ? lo : cov_lo, new_hi = hi > cov_hi ? hi : cov_hi;
+    // offsets [t0, t1]: offsets[t0] came with the previous chunk
+    h2d(const_cast<uint32_t*>(din.offsets) + t0 + (c ? 1 : 0), hin->offsets + t0 + (c ? 1 : 0), (nt + (c ? 0 : 1)) * 4);
+    h2d_meas(new_lo, cov_lo);
+    h2d_meas(cov_hi, new_hi);
+    cov_lo = new_lo;
+    cov_hi = new_hi;
     // the chunk's columns of the SoA seed matrices: one strided copy each
     h2d_rows(const_cast<double*>(din.seed_par) + t0, hin->seed_par + t0, nt, 5);
     h2d_rows(const_cast<double*>(din.seed_cov) + t0, hin->seed_cov + t0, nt, 15);

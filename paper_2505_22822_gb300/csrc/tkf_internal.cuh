@@ -212,7 +212,7 @@ cudaError_t launch_fit(const FitArgs& a, const FieldDev& field, int precision, c
 }  // namespace tkf
 
 // chunks of the host-buffer pipeline (tkf_fit_host) at most
-constexpr int kHostChunksMax = 4;
+constexpr int kHostChunksMax = 8;
 
 struct tkf_context_s;
 

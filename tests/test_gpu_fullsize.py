@@ -138,7 +138,7 @@ def _host_vs_device(ctx, geo, fld, hb, opts):
 
 @pytest.mark.parametrize("precision", [tkf.FP64, tkf.MIXED])
 def test_host_entry_point_pipelines_chunks_with_identical_results(barrel, precision):
-    """605,172 tracks through tkf_fit_host: four chunks whose copies overlap the fits, results
+    """605,172 tracks through tkf_fit_host: eight chunks whose copies overlap the fits, results
     bit for bit those of the device entry point."""
     ctx, w, geo, fld, _, _ = barrel
     t = w.tracks
@@ -146,13 +146,19 @@ def test_host_entry_point_pipelines_chunks_with_identical_results(barrel, precis
     _host_vs_device(ctx, geo, fld, hb, tkf.Options(precision=precision, mass=w.mass))
 
 
-def test_host_entry_point_with_decreasing_offsets_fits_in_one_piece(barrel):
-    """Offsets that decrease somewhere cannot be chunked by measurement ranges: the call copies
-    everything and still matches the device entry point (the decreasing pair flags BAD_INPUT)."""
+def test_host_entry_point_with_decreasing_offsets_matches_the_device_entry_point(barrel):
+    """Offsets that decrease somewhere: each chunk copies the measurements between the least and
+    the greatest of its tracks' offsets, and the copied range grows as one interval (below and
+    above what earlier chunks copied) with no byte copied twice; the results still match the
+    device entry point, and the reversed ranges are flagged BAD_INPUT."""
     ctx, w, geo, fld, _, _ = barrel
-    sub = w.tracks.subset(np.arange(140_000))
+    sub = w.tracks.subset(np.arange(200_000))  # three chunks
     offsets = sub.offsets.astype(np.uint32).copy()
-    offsets[70_000] = offsets[70_001] + 3  # track 69,999 ends after track 70,000 starts
+    assert offsets[1] >= 5
+    offsets[0] = 5                              # the first chunk's range starts at 5
+    offsets[70_000] = offsets[70_001] + 3       # track 69,999 ends after track 70,000 starts
+    offsets[-1] = 2                             # the last track's range is reversed, below 5
     hb = tkf.Batch.from_arrays(offsets, sub.meas, sub.sid, sub.seed_par, sub.seed_cov)
     h = _host_vs_device(ctx, geo, fld, hb, tkf.Options(precision=tkf.MIXED, mass=w.mass))
     assert h.status[70_000] & tkf.TRACK_STATUS["BAD_INPUT"]
+    assert h.status[-1] & tkf.TRACK_STATUS["BAD_INPUT"]
