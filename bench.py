@@ -528,13 +528,15 @@ def setup_tune_cache() -> str:
 def tuned_shape(path: str, variant: str, n_tracks: int, field: str, disabled: bool):
     """[threads, blocks per SM, tracks per warp, registers, lanes a track] the autotuner chose
     for this class."""
-    if variant.endswith("_two_filter") or variant.endswith("_all_states"):  # one kernel variant, not tuned
+    if variant.endswith("_all_states"):  # one kernel variant, not tuned
         return [128, 2, 32, 255, 1]
+    two_filter = variant.endswith("_two_filter")
+    base = variant.replace("_two_filter", "")
     if disabled:
-        return [128, 2, 32, 255, 1] if variant in ("fp64", "mixed_fp32") else [128, 4, 32, 128, 1]
-    prec = variant if variant in ("fp64", "mixed_fp32") else "mixed"
+        return [128, 2, 32, 255, 1] if two_filter or base in ("fp64", "mixed_fp32") else [128, 4, 32, 128, 1]
+    prec = base if base in ("fp64", "mixed_fp32") else "mixed"
     mode = "learned" if variant.endswith("learned") else "adaptive"
-    prefix = f"{prec}.{mode}.{field}.n{int(n_tracks).bit_length() - 1}."
+    prefix = f"{prec}{'_two_filter' if two_filter else ''}.{mode}.{field}.n{int(n_tracks).bit_length() - 1}."
     try:
         with open(path) as fh:
             table = json.load(fh)
@@ -792,7 +794,7 @@ def main():
         if args.shape:
             th, bps, tpw, regs, *lanes = (int(x) for x in args.shape.split(","))
             opts.block_threads, opts.blocks_per_sm, opts.tracks_per_warp = th, bps, tpw
-            opts.max_registers = 255 if two_filter or (base == "mixed_fp32" and regs == 64) else regs
+            opts.max_registers = 255 if base == "mixed_fp32" and (two_filter or regs == 64) else regs
             opts.lanes_per_track = lanes[0] if lanes and base != "mixed_fp32" and not two_filter else 0
         if args.tol is not None:
             opts.tol = args.tol

@@ -219,9 +219,11 @@ typedef struct tkf_fit_options {
    * earlier entry propagates to it and applies that surface's material (the scattering
    * variance; the mean energy loss given back). The result is the weighted mean of the
    * backward filtered state at the first surface and the seed. It propagates every track twice;
-   * no per-measurement state is kept. One lane a track at 255 registers (lanes_per_track 0 or 1,
-   * max_registers 0 or 255), no record capture; TKF_FIT_AUTOTUNE is ignored (the default block
-   * shape, 128 threads x 2 blocks per SM, unless one is given). */
+   * no per-measurement state is kept. One lane a track (lanes_per_track 0 or 1), no record
+   * capture; 255 registers, or max_registers 128 / 64 in TKF_FP64 and TKF_MIXED. Default block
+   * shape 128 threads x 2 blocks per SM (x 4 or x 8 when capped at 128 / 64) unless one is
+   * given; TKF_FIT_AUTOTUNE times the block shapes and register caps as for RTS (one lane a
+   * track), cached apart from RTS. */
   int smoother;
   /* TKF_SMOOTHER_TWO_FILTER: factor on the last filtered covariance that starts the backward
    * filter (default 1e3; finite and >= 1). The start then holds 1/backward_inflation of the

@@ -28,7 +28,8 @@ _SOURCES = ["tkf_api.cu", "tkf_order.cu", "tkf_policy.cu", "tkf_fit_fp64.cu", "t
             "tkf_fit_fp64_r64.cu", "tkf_fit_mixed.cu",
             "tkf_fit_mixed_r128.cu", "tkf_fit_mixed_r64.cu", "tkf_fit_mixed32.cu", "tkf_mlp.cu", "tkf_seed.cu",
             "tkf_fit_group.cu", "tkf_ckf.cu", "tkf_fit_two_filter.cu", "tkf_fit_two_filter_mixed.cu",
-            "tkf_fit_two_filter_mixed32.cu", "tkf_states.cu"]
+            "tkf_fit_two_filter_mixed32.cu", "tkf_fit_two_filter_capped_mixed.cu",
+            "tkf_fit_two_filter_capped_fp64.cu", "tkf_states.cu"]
 _lib = None
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",

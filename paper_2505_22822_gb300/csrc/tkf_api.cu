@@ -429,10 +429,12 @@ static tkf_status check_common(tkf_context ctx, tkf_geometry geo, tkf_field fiel
   if (o->smoother == TKF_SMOOTHER_TWO_FILTER) {
     if (!(o->backward_inflation >= 1.0) || !isfinite(o->backward_inflation))
       return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": backward_inflation must be finite and >= 1");
-    if (o->records || o->lanes_per_track > 1 || (o->max_registers != 0 && o->max_registers != 255))
+    const bool capped = o->max_registers == 128 || o->max_registers == 64;
+    if (o->records || o->lanes_per_track > 1 || (o->max_registers != 0 && o->max_registers != 255 && !capped) ||
+        (capped && o->precision == TKF_MIXED_FP32))
       return fail(ctx, TKF_ERR_UNSUPPORTED,
-                  std::string(fn) + ": TKF_SMOOTHER_TWO_FILTER runs one lane a track at 255 registers, "
-                                    "without record capture");
+                  std::string(fn) + ": TKF_SMOOTHER_TWO_FILTER runs one lane a track without record capture, at "
+                                    "255 registers (or 128 / 64 in TKF_FP64 and TKF_MIXED)");
   }
   if ((o->flags & ~(TKF_FIT_AUTOTUNE | TKF_FIT_GRAPH | TKF_FIT_TEST_PROPOSAL_TIMEOUT)) != 0)
     return fail(ctx, TKF_ERR_INVALID_ARG, std::string(fn) + ": unknown flag");

@@ -195,9 +195,14 @@ cudaError_t launch_fit_mixed32(const FitArgs& a, const FieldDev& f, int mode, co
                                LaunchShape shape, cudaStream_t stream);
 cudaError_t launch_fit_group(const FitArgs& a, const FieldDev& f, int precision, int mode, const uint32_t* perm,
                              uint32_t* counter, LaunchShape shape, cudaStream_t stream);
-// Two-filter smoother (a.smoother == TKF_SMOOTHER_TWO_FILTER): one lane a track, 255 registers.
+// Two-filter smoother (a.smoother == TKF_SMOOTHER_TWO_FILTER): one lane a track; 255 registers,
+// or 128 / 64 (shape.regs) in FP64 and mixed precision.
 cudaError_t launch_fit_two_filter(const FitArgs& a, const FieldDev& f, int precision, int mode, const uint32_t* perm,
                                   uint32_t* counter, LaunchShape shape, cudaStream_t stream);
+cudaError_t launch_fit_two_filter_mixed_capped(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm,
+                                               uint32_t* counter, LaunchShape shape, cudaStream_t stream);
+cudaError_t launch_fit_two_filter_fp64_capped(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm,
+                                              uint32_t* counter, LaunchShape shape, cudaStream_t stream);
 cudaError_t launch_fit_two_filter_mixed(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm,
                                         uint32_t* counter, LaunchShape shape, cudaStream_t stream);
 cudaError_t launch_fit_two_filter_mixed32(const FitArgs& a, const FieldDev& f, int mode, const uint32_t* perm,

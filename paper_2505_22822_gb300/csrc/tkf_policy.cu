@@ -61,6 +61,11 @@ bool has_regs(int precision, int regs) {
   return false;
 }
 
+// The two-filter smoother's register caps: 255, and 128 / 64 in FP64 and mixed precision.
+bool has_two_filter_regs(int precision, int regs) {
+  return regs == 255 || ((precision == TKF_MIXED || precision == TKF_FP64) && (regs == 128 || regs == 64));
+}
+
 int field_class(const FieldDev& f) {
   if (f.kind != TKF_FIELD_UNIFORM) return 2;
   return (f.b[0] == 0.0 && f.b[1] == 0.0) ? 0 : 1;
@@ -73,8 +78,9 @@ std::string tune_key(const FitArgs& a, const FieldDev& f, int precision, int sm_
   int lg = 0;
   while ((2u << lg) <= a.n_tracks && lg < 31) ++lg;
   char buf[96];
-  snprintf(buf, sizeof(buf), "%s.%s.%s.n%d.sm%d",
+  snprintf(buf, sizeof(buf), "%s%s.%s.%s.n%d.sm%d",
            precision == TKF_MIXED ? "mixed" : (precision == TKF_MIXED_FP32 ? "mixed_fp32" : "fp64"),
+           a.smoother == TKF_SMOOTHER_TWO_FILTER ? "_two_filter" : "",
            fit_mode(a) == 1 ? "learned" : (fit_mode(a) == 2 ? "record" : "adaptive"), kField[field_class(f)], lg,
            sm_count);
   return buf;
@@ -119,17 +125,19 @@ cudaError_t tune(tkf_context ctx, const FitArgs& a, const FieldDev& f, int preci
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   float best_ms = INFINITY;
-  *best = default_shape(precision, a.records != nullptr);
+  const bool two_filter = a.smoother == TKF_SMOOTHER_TWO_FILTER;  // one lane a track, its own caps
+  *best = two_filter ? std::array<int, 5>{128, 2, 32, 255, 1} : default_shape(precision, a.records != nullptr);
   if (e == cudaSuccess) e = launch_fit(a, f, precision, ws, make_shape(*best, ctx->sm_count), stream);
   const bool small = a.n_tracks < uint32_t(32 * kResidentWarpsPerSm * ctx->sm_count);
   const bool record = a.records != nullptr;
   for (int group : {1, 4}) {
-    if (group != 1 && (!small || !has_group(precision, record, group))) break;
+    if (group != 1 && (two_filter || !small || !has_group(precision, record, group))) break;
     for (const int tpw : (group == 1 ? kTracksPerWarp : kGroupTracksPerWarp)) {
     if (group == 1 && tpw != 32 && !small) break;
     for (const Candidate& c : kCandidates) {
       if (e != cudaSuccess) break;
       if (!has_regs(precision, c.regs) || (group != 1 && c.regs != 255)) continue;
+      if (two_filter && !has_two_filter_regs(precision, c.regs)) continue;
       const std::array<int, 5> cand = {c.threads, c.blocks_per_sm, tpw, c.regs, group};
       const LaunchShape s = make_shape(cand, ctx->sm_count);
       for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
@@ -279,14 +287,15 @@ cudaError_t resolve_shape(tkf_context ctx, const FitArgs& a, const FieldDev& f, 
     out->tracks_per_warp = 32;
     return cudaSuccess;
   }
-  if (a.smoother == TKF_SMOOTHER_TWO_FILTER) {  // one kernel variant: 255 registers, one lane a track
+  if (a.smoother == TKF_SMOOTHER_TWO_FILTER) {  // one lane a track; 255 registers unless capped
     if (!explicit_block) {
       out->threads = 128;
       out->blocks = 2 * ctx->sm_count;
     }
-    out->regs = 255;
+    out->regs = o->max_registers && has_two_filter_regs(precision, int(o->max_registers)) ? int(o->max_registers) : 255;
     out->group = 1;
-    return cudaSuccess;
+    if (out->regs != 255 && !explicit_block)  // a capped kernel: 128 threads, the SM's registers full
+      out->blocks = (65536 / (out->regs * 128)) * ctx->sm_count;
   }
   const bool any_explicit = explicit_block || o->tracks_per_warp || o->max_registers || o->lanes_per_track;
   if (any_explicit || !(o->flags & TKF_FIT_AUTOTUNE) || a.records) return cudaSuccess;

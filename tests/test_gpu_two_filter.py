@@ -67,6 +67,22 @@ def test_two_filter_mixed_within_1e3_sigma(ctx, workload):
     check_mixed(g, o)
 
 
+@pytest.mark.parametrize("workload", ["barrel", "map"])
+def test_two_filter_register_caps(ctx, workload):
+    """The two-filter kernels capped at 128 and 64 registers (the tuner's candidates): mixed
+    precision bit for bit the 255-register kernel's results; FP64 within the parity tolerance
+    of the oracle (the FP64 instantiations may fuse a product of a two-term sum differently)."""
+    w = WORKLOADS[workload]()
+    ref = run_gpu(ctx, w, opts=_opts(w, tkf.MIXED))
+    o = run_oracle(w, opts=_oopts(w))
+    for regs in (128, 64):
+        g = run_gpu(ctx, w, opts=_opts(w, tkf.MIXED, max_registers=regs))
+        for k in ("par", "cov", "chi2", "ndf", "status"):
+            np.testing.assert_array_equal(np.nan_to_num(g[k], nan=7.0), np.nan_to_num(ref[k], nan=7.0), err_msg=f"{regs} {k}")
+        g64 = run_gpu(ctx, w, opts=_opts(w, max_registers=regs))
+        check(g64, o, TOL64, w=w, tracks=np.arange(w.tracks.n_tracks), sensitivity=_sensitivity(w))
+
+
 @pytest.mark.parametrize("precision", [tkf.FP64, tkf.MIXED, tkf.MIXED_FP32])
 def test_two_filter_edge_tracks(ctx, precision):
     w, tr = _edge_tracks()
@@ -151,8 +167,8 @@ def test_two_filter_graph_key_and_options(ctx):
     for sm in outs:
         assert torch.equal(outs[sm][0], outs[sm][1])
     assert not torch.equal(outs[tkf.SMOOTHER_RTS][0], outs[tkf.SMOOTHER_TWO_FILTER][0])
-    for bad in (dict(lanes_per_track=4), dict(max_registers=128, precision=tkf.MIXED), dict(backward_inflation=0.5),
-                dict(backward_inflation=float("inf"))):
+    for bad in (dict(lanes_per_track=4), dict(max_registers=128, precision=tkf.MIXED_FP32),
+                dict(backward_inflation=0.5), dict(backward_inflation=float("inf"))):
         with pytest.raises(tkf.TkfError, match="TWO_FILTER|backward_inflation"):
             tkf.fit(ctx, geo, fld, b, tkf.Options(smoother=tkf.SMOOTHER_TWO_FILTER, **bad))
     with pytest.raises(tkf.TkfError, match="smoother"):
