@@ -822,27 +822,40 @@ __global__ void __launch_bounds__(kCkfBlock) ckf_gate_kernel(const CkfArgs a, Ck
   // 1e-4 of S) cannot bring the residual back inside the gate
   const float p0f = d2f(pp[0]), p1f = d2f(pp[1]), c00f = d2f(Cp[S(0, 0)]), c11f = d2f(Cp[S(1, 1)]);
   const float gatef = float(a.chi2_max) * 1.0001f;
-  for (uint32_t mi = moff[target]; mi < m_end; ++mi) {
-    const float4 mf = a.meas_f[mi];  // loc0, loc1, V00, V11
-    const float r0f = mf.x - p0f, r1f = mf.y - p1f;
-    const float e0 = fabsf(r0f) - 1e-6f * (fabsf(mf.x) + fabsf(p0f) + fabsf(r0f));
-    const float e1 = fabsf(r1f) - 1e-6f * (fabsf(mf.y) + fabsf(p1f) + fabsf(r1f));
-    if ((e0 > 0.0f && e0 * e0 > gatef * (c00f + mf.z)) || (e1 > 0.0f && e1 * e1 > gatef * (c11f + mf.w))) continue;
-    const double q0 = a.loc0[mi] - pp[0], q1 = a.loc1[mi] - pp[1];
-    if (q0 * q0 > gate * (Cp[S(0, 0)] + a.v00[mi]) || q1 * q1 > gate * (Cp[S(1, 1)] + a.v11[mi])) continue;
-    double c2;
-    if (!meas_chi2(pp, Cp, a.loc0[mi], a.loc1[mi], a.v00[mi], a.v01[mi], a.v11[mi], c2)) continue;
-    if (!(c2 < a.chi2_max)) continue;
-    int pos = nk;
-    while (pos > 0 && (c2 < kc2[pos - 1] || (c2 == kc2[pos - 1] && mi < km[pos - 1]))) --pos;
-    if (pos >= kCkfChildren) continue;
-    for (int q = (nk < kCkfChildren ? nk : kCkfChildren - 1); q > pos; --q) {
-      kc2[q] = kc2[q - 1];
-      km[q] = km[q - 1];
+  // eight measurements at a time: their FP32 copies loaded together (the loop waits on the
+  // loads, not the arithmetic), screened into a mask, the survivors taken in index order
+  for (uint32_t base = moff[target]; base < m_end; base += 8) {
+    float4 mf[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) mf[u] = base + u < m_end ? a.meas_f[base + u] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    uint32_t pass = 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float r0f = mf[u].x - p0f, r1f = mf[u].y - p1f;
+      const float e0 = fabsf(r0f) - 1e-6f * (fabsf(mf[u].x) + fabsf(p0f) + fabsf(r0f));
+      const float e1 = fabsf(r1f) - 1e-6f * (fabsf(mf[u].y) + fabsf(p1f) + fabsf(r1f));
+      const bool out = (e0 > 0.0f && e0 * e0 > gatef * (c00f + mf[u].z)) || (e1 > 0.0f && e1 * e1 > gatef * (c11f + mf[u].w));
+      if (base + u < m_end && !out) pass |= 1u << u;
     }
-    kc2[pos] = c2;
-    km[pos] = mi;
-    if (nk < kCkfChildren) ++nk;
+    while (pass) {
+      const uint32_t mi = base + uint32_t(__ffs(pass) - 1);
+      pass &= pass - 1u;
+      const double q0 = a.loc0[mi] - pp[0], q1 = a.loc1[mi] - pp[1];
+      if (q0 * q0 > gate * (Cp[S(0, 0)] + a.v00[mi]) || q1 * q1 > gate * (Cp[S(1, 1)] + a.v11[mi])) continue;
+      double c2;
+      if (!meas_chi2(pp, Cp, a.loc0[mi], a.loc1[mi], a.v00[mi], a.v01[mi], a.v11[mi], c2)) continue;
+      if (!(c2 < a.chi2_max)) continue;
+      int pos = nk;
+      while (pos > 0 && (c2 < kc2[pos - 1] || (c2 == kc2[pos - 1] && mi < km[pos - 1]))) --pos;
+      if (pos >= kCkfChildren) continue;
+      for (int q = (nk < kCkfChildren ? nk : kCkfChildren - 1); q > pos; --q) {
+        kc2[q] = kc2[q - 1];
+        km[q] = km[q - 1];
+      }
+      kc2[pos] = c2;
+      km[pos] = mi;
+      if (nk < kCkfChildren) ++nk;
+    }
   }
   for (int q = 0; q < nk; ++q) {
     double p[5], C[15];
