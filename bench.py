@@ -528,14 +528,14 @@ def setup_tune_cache() -> str:
 def tuned_shape(path: str, variant: str, n_tracks: int, field: str, disabled: bool):
     """[threads, blocks per SM, tracks per warp, registers, lanes a track] the autotuner chose
     for this class."""
-    if variant.endswith("_all_states"):  # one kernel variant, not tuned
-        return [128, 2, 32, 255, 1]
     two_filter = variant.endswith("_two_filter")
-    base = variant.replace("_two_filter", "")
+    all_states = variant.endswith("_all_states")
+    base = variant.replace("_two_filter", "").replace("_all_states", "")
     if disabled:
-        return [128, 2, 32, 255, 1] if two_filter or base in ("fp64", "mixed_fp32") else [128, 4, 32, 128, 1]
+        return ([128, 2, 32, 255, 1] if two_filter or all_states or base in ("fp64", "mixed_fp32")
+                else [128, 4, 32, 128, 1])
     prec = base if base in ("fp64", "mixed_fp32") else "mixed"
-    mode = "learned" if variant.endswith("learned") else "adaptive"
+    mode = "learned" if variant.endswith("learned") else ("states" if all_states else "adaptive")
     prefix = f"{prec}{'_two_filter' if two_filter else ''}.{mode}.{field}.n{int(n_tracks).bit_length() - 1}."
     try:
         with open(path) as fh:

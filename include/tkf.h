@@ -305,9 +305,10 @@ typedef struct tkf_fit_inputs {
  * a track whose status is fatal, or that has no measurement, are NaN; a predicted covariance that
  * is not positive definite in the backward pass sets TKF_TRACK_SMOOTHER_NOT_SPD (and NaN outputs)
  * as it does in the textbook smoother. Requires TKF_STEP_ADAPTIVE without record capture, the
- * RTS smoother and tkf_fit (not tkf_fit_host or tkf_fit_noalloc); it launches with the default
- * block shape at 255 registers and one lane a track (TKF_FIT_AUTOTUNE and the explicit shape
- * options other than block_threads / blocks_per_sm are ignored; TKF_ERR_UNSUPPORTED otherwise).
+ * RTS smoother and tkf_fit (not tkf_fit_host or tkf_fit_noalloc; TKF_ERR_UNSUPPORTED otherwise).
+ * It runs one lane a track (lanes_per_track is ignored): by default 128 threads x 2 blocks per
+ * SM at 255 registers; max_registers 128 / 64 (x 4 / x 8 blocks) where the precision has them;
+ * TKF_FIT_AUTOTUNE times the one-lane shapes and register caps, cached apart from the plain fit.
  * NULL keeps the default path, unchanged and as fast. */
 typedef struct tkf_fit_outputs {
   double* par;

@@ -2033,8 +2033,8 @@ cudaError_t launch_persistent(const FitArgs& a, const F& fld, const uint32_t* pe
   return cudaGetLastError();
 }
 
-// Record capture (training only) and the all-states mode are built with the full register file
-// and one lane a track.
+// Record capture (training only) is built with the full register file and one lane a track; the
+// all-states mode with one lane a track at every register cap.
 template <int kPrec, int kRegs, int kG, int kSmooth, class F>
 cudaError_t launch_mode(const FitArgs& a, const F& fld, int mode, const uint32_t* perm, uint32_t* counter,
                         LaunchShape shape, cudaStream_t stream) {
@@ -2045,8 +2045,8 @@ cudaError_t launch_mode(const FitArgs& a, const F& fld, int mode, const uint32_t
       return launch_persistent<kPrec, kRecord, kRegs, kG, kSmooth>(a, fld, perm, counter, shape, stream);
     return cudaErrorInvalidValue;
   }
-  if (mode == kStates) {  // all-states output: full register file, one lane a track, RTS
-    if constexpr (kRegs == 255 && kG == 1 && kSmooth == 0)
+  if (mode == kStates) {  // all-states output: one lane a track, RTS, any register cap
+    if constexpr (kG == 1 && kSmooth == 0)
       return launch_persistent<kPrec, kStates, kRegs, kG, kSmooth>(a, fld, perm, counter, shape, stream);
     return cudaErrorInvalidValue;
   }

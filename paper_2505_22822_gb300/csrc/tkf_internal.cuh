@@ -104,8 +104,9 @@ struct Workspace {
 };
 size_t workspace_bytes(uint32_t n_tracks, bool learned, uint64_t states_entries = 0);
 Workspace carve_workspace(void* base, uint32_t n_tracks, bool learned, uint64_t states_entries = 0);
-// Backward RTS pass of the all-states output (tkf_states.cu), after the fit on the same stream.
-cudaError_t launch_smooth_states(const FitArgs& a, cudaStream_t stream);
+// Backward RTS pass of the all-states output (tkf_states.cu), after the fit on the same stream;
+// perm: the fit's track order.
+cudaError_t launch_smooth_states(const FitArgs& a, const uint32_t* perm, cudaStream_t stream);
 cudaError_t launch_propose_start(const FitArgs& a, const FieldDev& f, float* h0, cudaStream_t stream);
 
 // Seed parameter estimation (tkf_seed.cu): one thread per track, outputs in the fit's seed layout.

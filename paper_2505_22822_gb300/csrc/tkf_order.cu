@@ -143,7 +143,7 @@ cudaError_t launch_fit(const FitArgs& a, const FieldDev& f, int precision, const
                                     : launch_fit_fp64(b, f, mode, ws.perm, ws.counter, shape, stream);
   if (e != cudaSuccess) return e;
   if (timing && (e = cudaEventRecord(timing[1], stream)) != cudaSuccess) return e;
-  if (mode == 3) e = launch_smooth_states(b, stream);  // backward RTS over the stored states
+  if (mode == 3) e = launch_smooth_states(b, ws.perm, stream);  // backward RTS over the stored states
   return e;
 }
 

@@ -81,7 +81,8 @@ std::string tune_key(const FitArgs& a, const FieldDev& f, int precision, int sm_
   snprintf(buf, sizeof(buf), "%s%s.%s.%s.n%d.sm%d",
            precision == TKF_MIXED ? "mixed" : (precision == TKF_MIXED_FP32 ? "mixed_fp32" : "fp64"),
            a.smoother == TKF_SMOOTHER_TWO_FILTER ? "_two_filter" : "",
-           fit_mode(a) == 1 ? "learned" : (fit_mode(a) == 2 ? "record" : "adaptive"), kField[field_class(f)], lg,
+           fit_mode(a) == 1 ? "learned" : (fit_mode(a) == 2 ? "record" : (fit_mode(a) == 3 ? "states" : "adaptive")),
+           kField[field_class(f)], lg,
            sm_count);
   return buf;
 }
@@ -126,12 +127,13 @@ cudaError_t tune(tkf_context ctx, const FitArgs& a, const FieldDev& f, int preci
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   float best_ms = INFINITY;
   const bool two_filter = a.smoother == TKF_SMOOTHER_TWO_FILTER;  // one lane a track, its own caps
-  *best = two_filter ? std::array<int, 5>{128, 2, 32, 255, 1} : default_shape(precision, a.records != nullptr);
+  const bool one_lane = two_filter || a.states_par != nullptr;     // the all-states mode: one lane too
+  *best = one_lane ? std::array<int, 5>{128, 2, 32, 255, 1} : default_shape(precision, a.records != nullptr);
   if (e == cudaSuccess) e = launch_fit(a, f, precision, ws, make_shape(*best, ctx->sm_count), stream);
   const bool small = a.n_tracks < uint32_t(32 * kResidentWarpsPerSm * ctx->sm_count);
   const bool record = a.records != nullptr;
   for (int group : {1, 4}) {
-    if (group != 1 && (two_filter || !small || !has_group(precision, record, group))) break;
+    if (group != 1 && (one_lane || !small || !has_group(precision, record, group))) break;
     for (const int tpw : (group == 1 ? kTracksPerWarp : kGroupTracksPerWarp)) {
     if (group == 1 && tpw != 32 && !small) break;
     for (const Candidate& c : kCandidates) {
@@ -260,7 +262,7 @@ bool valid_block_shape(uint32_t threads, uint32_t blocks_per_sm, uint32_t tracks
 
 cudaError_t resolve_shape(tkf_context ctx, const FitArgs& a, const FieldDev& f, int precision, const Workspace& ws,
                           const tkf_fit_options* o, cudaStream_t stream, LaunchShape* out) {
-  // record capture and the all-states output exist at 255 registers, one lane a track
+  // record capture exists at 255 registers, one lane a track; the all-states output defaults to it
   const bool full_file = a.records != nullptr || a.states_par != nullptr;
   std::array<int, 5> shape = default_shape(precision, full_file);
   const bool explicit_block = o->block_threads && o->blocks_per_sm;
@@ -277,15 +279,15 @@ cudaError_t resolve_shape(tkf_context ctx, const FitArgs& a, const FieldDev& f, 
   if (o->tracks_per_warp) shape[2] = int(o->tracks_per_warp);
   if (o->max_registers) shape[3] = int(o->max_registers);
   *out = make_shape(shape, ctx->sm_count);
-  if (a.states_par) {
+  if (a.states_par) {  // one lane a track; 255 registers unless capped
     if (!explicit_block) {
       out->threads = 128;
       out->blocks = 2 * ctx->sm_count;
     }
-    out->regs = 255;
+    out->regs = o->max_registers && has_regs(precision, int(o->max_registers)) ? int(o->max_registers) : 255;
     out->group = 1;
-    out->tracks_per_warp = 32;
-    return cudaSuccess;
+    if (out->regs != 255 && !explicit_block)  // a capped kernel: 128 threads, the SM's registers full
+      out->blocks = (65536 / (out->regs * 128)) * ctx->sm_count;
   }
   if (a.smoother == TKF_SMOOTHER_TWO_FILTER) {  // one lane a track; 255 registers unless capped
     if (!explicit_block) {

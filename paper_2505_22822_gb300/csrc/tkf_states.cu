@@ -37,9 +37,12 @@ __device__ void nan_entries(const FitArgs& a, uint32_t b0, uint32_t b1) {
   }
 }
 
-__global__ void __launch_bounds__(128) smooth_states_kernel(FitArgs a) {
+// Thread k takes track perm[k]: the fit's order (most entries first), so that the lanes of a warp
+// run backward passes of the same length.
+__global__ void __launch_bounds__(128) smooth_states_kernel(FitArgs a, const uint32_t* __restrict__ perm) {
   const size_t nm = size_t(a.n_meas);
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n_tracks; i += gridDim.x * blockDim.x) {
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n_tracks; k += gridDim.x * blockDim.x) {
+    const uint32_t i = perm[k];
     const uint32_t b0 = a.offsets[i], b1 = a.offsets[i + 1];
     if (b1 < b0 || b1 > a.n_meas) continue;  // bad offsets: the track has no entries to write
     const uint32_t N = b1 - b0;
@@ -141,10 +144,10 @@ __global__ void __launch_bounds__(128) smooth_states_kernel(FitArgs a) {
 
 }  // namespace
 
-cudaError_t launch_smooth_states(const FitArgs& a, cudaStream_t stream) {
+cudaError_t launch_smooth_states(const FitArgs& a, const uint32_t* perm, cudaStream_t stream) {
   if (a.n_tracks == 0) return cudaSuccess;
   const unsigned blocks = (a.n_tracks + 127) / 128;
-  smooth_states_kernel<<<blocks, 128, 0, stream>>>(a);
+  smooth_states_kernel<<<blocks, 128, 0, stream>>>(a, perm);
   return cudaGetLastError();
 }
 

@@ -4,6 +4,8 @@ RTS pass, element by element (FP64: 1e-10 in the metric of tests/parity.py with 
 filtered covariance as the scale; mixed: 1e-3 sigma), plus the first-surface consistency,
 unchanged default outputs, edge tracks and argument errors."""
 
+import json
+
 import numpy as np
 import pytest
 
@@ -61,8 +63,10 @@ def _mixed_states_dev(sp, o, offsets):
 def test_every_entry_fp64_matches_the_oracle(ctx, name):
     w = WORKLOADS[name]()
     t = w.tracks
-    r = _gpu(ctx, w, t, tkf.Options(mass=w.mass))
-    o = _oracle(w, t)
+    _check_fp64_states(w, t, _gpu(ctx, w, t, tkf.Options(mass=w.mass)), _oracle(w, t))
+
+
+def _check_fp64_states(w, t, r, o):
     g = parity.gpu_to_track_major(r)
     # the first-surface outputs keep the parity of the default path
     check(g, o, TOL64, w=w, tracks=np.arange(t.n_tracks))
@@ -98,6 +102,33 @@ def test_every_entry_mixed_within_1e3_sigma(ctx, name):
     ds = _mixed_states_dev(sp, o, t.offsets)
     print({"entries": int(len(ds)), "max_dp_over_sigma": float(ds.max()), "p99": float(np.quantile(ds, 0.99))})
     assert ds.max() <= MIXED_TOL_SIGMA
+
+
+def test_register_caps_and_autotune(ctx, tmp_path, monkeypatch):
+    """The all-states kernels capped at 128 and 64 registers, and the autotuned call: in mixed
+    precision every output, every entry's state included, bit for bit the 255-register result;
+    in FP64 every entry within the parity tolerance of the oracle (the FP64 instantiations may
+    fuse a product of a two-term sum differently); the tuned shape is cached under the
+    all-states class."""
+    w = WORKLOADS["barrel"]()
+    t = w.tracks
+    keys = ("par", "cov", "chi2", "ndf", "status", "steps", "states_par", "states_cov")
+    ref = _gpu(ctx, w, t, tkf.Options(precision=tkf.MIXED, mass=w.mass))
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("TKF_AUTOTUNE_CACHE", str(cache))
+    ctx2 = tkf.Context(0)
+    runs = [(regs, _gpu(ctx, w, t, tkf.Options(precision=tkf.MIXED, mass=w.mass, max_registers=regs)))
+            for regs in (128, 64)]
+    runs.append(("tuned", _gpu(ctx2, w, t, tkf.Options(precision=tkf.MIXED, mass=w.mass, autotune=True))))
+    for label, r in runs:
+        for k in keys:
+            a, b = getattr(r, k), getattr(ref, k)
+            assert torch.equal(torch.nan_to_num(a, nan=7.0), torch.nan_to_num(b, nan=7.0)), (label, k)
+    (key,) = json.loads(cache.read_text())
+    assert key.startswith("mixed.states.uz.")
+    o = _oracle(w, t)
+    for regs in (128, 64):
+        _check_fp64_states(w, t, _gpu(ctx, w, t, tkf.Options(mass=w.mass, max_registers=regs)), o)
 
 
 def test_first_entry_is_the_first_surface_result_and_defaults_are_unchanged(ctx):
