@@ -122,6 +122,14 @@ def parse():
                     help="calibration quantile of the learned step proposer's output bias (0..1)")
     ap.add_argument("--tol", type=float, default=None,
                     help="RKN local error tolerance in mm for every variant (default: the library's 1e-4)")
+    ap.add_argument("--tracks", type=int, default=0, help="fit only the first N tracks of the batch (default: all)")
+    ap.add_argument("--muons", type=int, default=100_000, help="muons of the solenoid-map batch")
+    ap.add_argument("--train-events", type=int, default=5,
+                    help="barrel events of the step proposer's seed-disjoint training batch")
+    ap.add_argument("--train-muons", type=int, default=100_000,
+                    help="muons of the step proposer's training batch in the solenoid map")
+    ap.add_argument("--max-records", type=int, default=0,
+                    help="train the step proposer on at most N of its records (default: all)")
     ap.add_argument("--no-seeds", action="store_true",
                     help="skip the seed-estimation kernel, the chain from estimated seeds and track finding")
     ap.add_argument("--streams", action="store_true",
@@ -144,18 +152,23 @@ def shard_seed(rank: int) -> int:
     return 2 + 1000 * rank
 
 
-def make_workload(workload: str, events: int, rank: int, **kw):
-    """The timed batch: the barrel + endcap events in 2 T, or 1e5 muons in the solenoid map."""
+def make_workload(workload: str, events: int, rank: int, muons: int = 100_000, tracks: int = 0, **kw):
+    """The timed batch: the barrel + endcap events in 2 T, or `muons` muons in the solenoid map;
+    with `tracks`, its first `tracks` tracks."""
     if workload == "map":
-        return synth.solenoid_muon_workload(100_000, seed=3 + shard_seed(rank), **kw)
-    return synth.barrel_workload(n_events=events, seed=shard_seed(rank), **kw)
+        w = synth.solenoid_muon_workload(muons, seed=3 + shard_seed(rank), **kw)
+    else:
+        w = synth.barrel_workload(n_events=events, seed=shard_seed(rank), **kw)
+    if tracks and tracks < w.tracks.n_tracks:
+        w = synth.Workload(w.name, w.geometry, w.field, w.tracks.subset(np.arange(tracks)), w.mass)
+    return w
 
 
 def make_training_batch(args, rank: int):
     """Seed-disjoint tracks of the same kind for the step proposer's training records."""
     if args.workload == "map":
-        return synth.solenoid_muon_workload(100_000, seed=10_003 + shard_seed(rank)).tracks
-    return synth.barrel_workload(n_events=5, seed=10_000 + shard_seed(rank)).tracks
+        return synth.solenoid_muon_workload(args.train_muons, seed=10_003 + shard_seed(rank)).tracks
+    return synth.barrel_workload(n_events=args.train_events, seed=10_000 + shard_seed(rank)).tracks
 
 
 def max_over_ranks(x: float, dist, device) -> float:
@@ -750,7 +763,7 @@ def main():
     if args.streams:
         run_streams(args, local, rank)
         return
-    w = make_workload(args.workload, args.events, rank)
+    w = make_workload(args.workload, args.events, rank, muons=args.muons, tracks=args.tracks)
     t = w.tracks
     n_tracks, n_meas = t.n_tracks, t.n_hits
     ctx = tkf.Context(local)
@@ -776,7 +789,8 @@ def main():
         tb = tkf.Batch.from_arrays(tt.offsets, tt.meas, tt.sid, tt.seed_par, tt.seed_cov).to(f"cuda:{local}")
         t0 = time.perf_counter()
         proposer, info = learn.build_proposer(ctx, geo, fld, tb, tkf.MIXED, mass=w.mass, tol=args.tol,
-                                              quantile=args.proposer_quantile)
+                                              quantile=args.proposer_quantile,
+                                              max_records=args.max_records or None)
         learn_info = {"records": info["records"], "final_loss": round(info["epoch_loss"][-1], 4),
                       "bias_shift": round(info["bias_shift"], 4), "train_s": round(time.perf_counter() - t0, 2),
                       "tracks": tt.n_tracks}

@@ -58,10 +58,12 @@ def calibrate(ctx, params, records, quantile: float = 0.05) -> float:
 
 
 def build_proposer(ctx, geo, field, batch, precision: int, epochs: int = 8, quantile: float = 0.05,
-                   mass=None, tol=None) -> tuple[Mlp, dict]:
-    """Records (at the RKN tolerance `tol`, default the library's) -> training -> calibration ->
-    BF16 handle, with a summary of the run."""
+                   mass=None, tol=None, max_records: int | None = None) -> tuple[Mlp, dict]:
+    """Records (at the RKN tolerance `tol`, default the library's; at most ``max_records``) ->
+    training -> calibration -> BF16 handle, with a summary of the run."""
     rec = record_steps(ctx, geo, field, batch, precision, mass=mass, tol=tol)
+    if max_records is not None:
+        rec = rec[:max_records]
     params, losses = train(ctx, rec, epochs=epochs)
     q = calibrate(ctx, params, rec, quantile)
     return Mlp.from_params(ctx, params), {"records": int(rec.shape[0]),
