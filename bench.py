@@ -447,6 +447,14 @@ def cpu_baseline(w, max_seconds: float = 20.0):
     line = {"value": len(idx) / dt, "unit": "tracks/s", "cores": cores, "kind": "oracle",
             "sample": f"{len(idx)} tracks drawn uniformly from the {t.n_tracks}-track batch, "
                       f"fit in {dt:.2f} s on {cores} threads"}
+    # the same oracle on one thread, on the first sixteenth of the sample (on 16 cores about as
+    # long as the threaded run)
+    n1 = max(1, len(idx) // 16)
+    t0 = time.perf_counter()
+    oracle.fit_tracks(w, tracks=t.subset(idx[:n1]), n_threads=1)
+    dt1 = time.perf_counter() - t0
+    line["single_thread"] = {"value": n1 / dt1, "unit": "tracks/s",
+                             "sample": f"{n1} tracks of the sample, {dt1:.2f} s on 1 thread"}
     return line, idx, res
 
 
