@@ -464,7 +464,9 @@ __device__ __forceinline__ float parabolic_path_f(float d, float a, float b) {
   return s;
 }
 
-template <int kMode, int kCols, class F>
+// kRoll: the derivative-column loops are kept rolled (smaller code; the 64-register kernel,
+// whose column state is in local memory anyway, runs faster so: measured).
+template <int kMode, int kCols, class F, bool kRoll = false>
 __device__ uint32_t propagate_mixed(const F& fld, const OptionsDev& o, const Surf& s, const float nf[3], double r[3],
                                     double T[3], double lam, float dr[kCols][3], float dT[kCols][3], float qcol,
                                     float& h_ctrl,
@@ -489,7 +491,7 @@ __device__ uint32_t propagate_mixed(const F& fld, const OptionsDev& o, const Sur
     if (fabsf(df) <= surf_tol) {
       if (oof) st |= TKF_TRACK_OUT_OF_FIELD;
       const float sp = parabolic_path_f(df, a, dotr(nf, k1)), sp2 = 0.5f * sp * sp;
-#pragma unroll
+#pragma unroll(kRoll ? 1 : kCols)
       for (int c = 0; c < kCols; ++c) {
         float q[3];
         cross(dT[c], Bt1, q);
@@ -558,7 +560,7 @@ __device__ uint32_t propagate_mixed(const F& fld, const OptionsDev& o, const Sur
     if (oof) st |= TKF_TRACK_OUT_OF_FIELD;
     if constexpr (kMode == kRecord)  // steps the control limited: the proposals' domain
       if (limited && eps > 0.0f) put_record(L, x, logf(fabsf(h) * sqrtf(sqrtf(tol / eps))));
-#pragma unroll
+#pragma unroll(kRoll ? 1 : kCols)
     for (int c = 0; c < kCols; ++c) {
       float q1[3], q2[3], q3[3], q4[3], u2[3], u3[3], u4[3];
       cross(dT[c], Bt1, q1);
@@ -1180,7 +1182,7 @@ __device__ __forceinline__ void store_predicted(const FitArgs& a, uint32_t m, co
     for (int c = 0; c < 5; ++c) w[20 + 5 * r + c] = cov_to_d(J[r][c]);
 }
 
-template <int kPrec, int kMode, int kG, int kPlace, int kSmooth, class F>
+template <int kPrec, int kMode, int kG, int kPlace, int kSmooth, bool kRoll, class F>
 __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
                           SmootherStore<kPlace, typename CovType<kPrec>::type> st, uint32_t gl = 0,
                           uint32_t gmask = 0xffffffffu) {
@@ -1384,8 +1386,8 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
         Cf[S(3, 3)] += th0sq;
       }
       float kend[3];
-      status |= propagate_mixed<kMode == kRecord ? kRecord : kPlain, kCols>(fld, a.opt, s, nf, r, T, lam, dr, dT, qcol,
-                                                                            h_ctrl_f, attempts, rejected, kend, learn);
+      status |= propagate_mixed<kMode == kRecord ? kRecord : kPlain, kCols, F, kRoll>(
+          fld, a.opt, s, nf, r, T, lam, dr, dT, qcol, h_ctrl_f, attempts, rejected, kend, learn);
       if (status & kFatal) break;
       // direction at the target in FP64 from FP32-seeded Newton steps (relative error ~1e-14)
       const double t2 = dot3(T, T), e2 = t2 - 1.0;
@@ -1694,7 +1696,8 @@ __global__ void __launch_bounds__(reg_block_threads(kRegs), reg_min_blocks(kRegs
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= a.n_tracks) break;
     const uint32_t j = base + g;
-    if (g < tpw && j < a.n_tracks) fit_track<kPrec, kMode, kG, kPlace, kSmooth>(a, fld, perm[j], st, gl, gmask);
+    if (g < tpw && j < a.n_tracks)
+      fit_track<kPrec, kMode, kG, kPlace, kSmooth, kRegs == 64>(a, fld, perm[j], st, gl, gmask);
   }
 }
 
