@@ -340,7 +340,9 @@ tkf_status tkf_fit(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf
  * compute stream (a chunk fits while its predecessor finishes its tail): the copy-in of a chunk
  * and the copy-out of the previous one overlap the fit of the current one (results identical
  * to one piece). A chunk copies the measurements between the least and the greatest of its
- * tracks' offsets, grown onto what earlier chunks copied as one interval (no byte twice). Page-locked host memory gives asynchronous copies.
+ * tracks' offsets, grown onto what earlier chunks copied as one interval (no byte twice). In
+ * TKF_STEP_LEARNED the offsets, surface ids and seed parameters of the whole batch go first and
+ * one proposal pre-pass serves every chunk. Page-locked host memory gives asynchronous copies.
  * `stream` is synchronized first (its earlier work must not use the staging area) and at the
  * end. Pointers as in tkf_fit_inputs / tkf_fit_outputs but in host memory. Errors as tkf_fit,
  * plus TKF_ERR_OOM. */

@@ -105,6 +105,8 @@ void tkf_context_destroy(tkf_context ctx) {
       if (ctx->chunk_in[c]) cudaEventDestroy(ctx->chunk_in[c]);
       if (ctx->chunk_fit[c]) cudaEventDestroy(ctx->chunk_fit[c]);
     }
+    if (ctx->props_in) cudaEventDestroy(ctx->props_in);
+    if (ctx->props_done) cudaEventDestroy(ctx->props_done);
     if (ctx->h2d_stream) cudaStreamDestroy(ctx->h2d_stream);
     if (ctx->d2h_stream) cudaStreamDestroy(ctx->d2h_stream);
     if (ctx->fit2_stream) cudaStreamDestroy(ctx->fit2_stream);
@@ -713,8 +715,10 @@ tkf_status tkf_fit_host(tkf_context ctx, tkf_geometry geo, tkf_field field, cons
   auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
   const size_t b_off = up((n + 1) * 4), b_meas = up(m * 8), b_sid = up(m * 4), b_seedp = up(5 * n * 8),
                b_seedc = up(15 * n * 8), b_par = up(5 * n * 8), b_cov = up(15 * n * 8), b_n8 = up(n * 8),
-               b_n4 = up(n * 4), b_steps = hout->steps ? up(2 * n * 4) : 0;
-  const size_t total = b_off + 5 * b_meas + b_sid + b_seedp + b_seedc + b_par + b_cov + b_n8 + 2 * b_n4 + b_steps;
+               b_n4 = up(n * 4), b_steps = hout->steps ? up(2 * n * 4) : 0,
+               b_h0 = o->step_mode == TKF_STEP_LEARNED ? up(n * 4) : 0;
+  const size_t total =
+      b_off + 5 * b_meas + b_sid + b_seedp + b_seedc + b_par + b_cov + b_n8 + 2 * b_n4 + b_steps + b_h0;
   if (total > ctx->stage_bytes) {
     if (ctx->stage) cudaFree(ctx->stage);
     ctx->stage = nullptr;
@@ -746,6 +750,7 @@ tkf_status tkf_fit_host(tkf_context ctx, tkf_geometry geo, tkf_field field, cons
   dout.ndf = reinterpret_cast<int32_t*>(take(b_n4));
   dout.status = reinterpret_cast<uint32_t*>(take(b_n4));
   dout.steps = hout->steps ? reinterpret_cast<uint32_t*>(take(b_steps)) : nullptr;
+  float* h0_all = b_h0 ? reinterpret_cast<float*>(take(b_h0)) : nullptr;  // learned mode: the proposals
   // Pipeline over chunks of tracks: the copy-in of chunk c + 1 (h2d stream) and the copy-out of
   // chunk c - 1 (d2h stream) overlap the fit of chunk c (the caller's stream). Each chunk is the
   // tracks [t0, t1) with the measurements they can reference, copied to the same positions of
@@ -761,6 +766,8 @@ tkf_status tkf_fit_host(tkf_context ctx, tkf_geometry geo, tkf_field field, cons
       e = cudaEventCreateWithFlags(&ctx->chunk_in[c], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->chunk_fit[c], cudaEventDisableTiming);
     }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->props_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->props_done, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_host: stream or event creation");
   }
   const uint32_t chunks =
@@ -807,6 +814,23 @@ tkf_status tkf_fit_host(tkf_context ctx, tkf_geometry geo, tkf_field field, cons
   // measurements copied so far: one interval [cov_lo, cov_hi), grown by every chunk, so that no
   // byte is copied twice while an earlier chunk's fit may read it
   size_t cov_lo = 0, cov_hi = 0;
+  // Learned mode in chunks: the proposals of the whole batch come first, from the offsets,
+  // surface ids and seed parameters copied ahead of everything else, in one pre-pass while the
+  // GPU has nothing else to do; the chunks' fits then follow one another with no pre-pass
+  // between them (a pre-pass could start only in the tail of the previous chunk's fit, which
+  // holds every SM).
+  const bool props_first = h0_all && chunks > 1;
+  if (props_first) {
+    h2d(const_cast<uint32_t*>(din.offsets), hin->offsets, (n + 1) * 4);
+    h2d(const_cast<uint32_t*>(din.sid), hin->sid, m * 4);
+    h2d(const_cast<double*>(din.seed_par), hin->seed_par, 5 * n * 8);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->props_in, ctx->h2d_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->props_in, 0);
+    if (e == cudaSuccess) e = tkf::launch_propose_start(full, field->f, h0_all, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->props_done, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->fit2_stream, ctx->props_done, 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_host: proposal pre-pass");
+  }
   auto h2d_meas = [&](size_t a0, size_t a1) {
     if (a1 <= a0) return;
     const size_t k = a1 - a0;
@@ -815,7 +839,7 @@ tkf_status tkf_fit_host(tkf_context ctx, tkf_geometry geo, tkf_field field, cons
     h2d(const_cast<double*>(din.v00) + a0, hin->v00 + a0, k * 8);
     h2d(const_cast<double*>(din.v01) + a0, hin->v01 + a0, k * 8);
     h2d(const_cast<double*>(din.v11) + a0, hin->v11 + a0, k * 8);
-    h2d(const_cast<uint32_t*>(din.sid) + a0, hin->sid + a0, k * 4);
+    if (!props_first) h2d(const_cast<uint32_t*>(din.sid) + a0, hin->sid + a0, k * 4);
   };
   for (uint32_t c = 0; c < chunks; ++c) {
     const size_t t0 = n * c / chunks, t1 = n * (c + 1) / chunks, nt = t1 - t0;
@@ -832,14 +856,16 @@ tkf_status tkf_fit_host(tkf_context ctx, tkf_geometry geo, tkf_field field, cons
       cov_lo = cov_hi = lo;
     }
     const size_t new_lo = lo < cov_lo ? lo : cov_lo, new_hi = hi > cov_hi ? hi : cov_hi;
-    // offsets [t0, t1]: offsets[t0] came with the previous chunk
-    h2d(const_cast<uint32_t*>(din.offsets) + t0 + (c ? 1 : 0), hin->offsets + t0 + (c ? 1 : 0), (nt + (c ? 0 : 1)) * 4);
+    // offsets [t0, t1]: offsets[t0] came with the previous chunk (all of them first in learned mode)
+    if (!props_first)
+      h2d(const_cast<uint32_t*>(din.offsets) + t0 + (c ? 1 : 0), hin->offsets + t0 + (c ? 1 : 0),
+          (nt + (c ? 0 : 1)) * 4);
     h2d_meas(new_lo, cov_lo);
     h2d_meas(cov_hi, new_hi);
     cov_lo = new_lo;
     cov_hi = new_hi;
     // the chunk's columns of the SoA seed matrices: one strided copy each
-    h2d_rows(const_cast<double*>(din.seed_par) + t0, hin->seed_par + t0, nt, 5);
+    if (!props_first) h2d_rows(const_cast<double*>(din.seed_par) + t0, hin->seed_par + t0, nt, 5);
     h2d_rows(const_cast<double*>(din.seed_cov) + t0, hin->seed_cov + t0, nt, 15);
     // chunks alternate between the caller's stream and a second compute stream, each with a
     // workspace of its own, so that a chunk's fit fills the SMs its predecessor's tail leaves
@@ -865,7 +891,8 @@ tkf_status tkf_fit_host(tkf_context ctx, tkf_geometry geo, tkf_field field, cons
       const tkf::Workspace wsc = tkf::carve_workspace(static_cast<char*>(ctx->ws) + c * chunk_ws, nt, learned);
       if (c == 0 && (e = tkf::resolve_shape(ctx, a, field->f, o->precision, wsc, o, st, &chunk_shape)) != cudaSuccess)
         return cuda_fail(ctx, e, "tkf_fit_host: autotune");
-      if ((e = tkf::launch_fit(a, field->f, o->precision, wsc, chunk_shape, cs)) != cudaSuccess)
+      if ((e = tkf::launch_fit(a, field->f, o->precision, wsc, chunk_shape, cs, nullptr,
+                               props_first ? h0_all + t0 : nullptr)) != cudaSuccess)
         return cuda_fail(ctx, e, "tkf_fit_host: launch");
     }
     e = cudaEventRecord(ctx->chunk_fit[c], cs);

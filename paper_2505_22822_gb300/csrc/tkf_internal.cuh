@@ -211,9 +211,10 @@ cudaError_t launch_fit_two_filter_mixed32(const FitArgs& a, const FieldDev& f, i
 
 // Enqueues the fit of every track in `a` on `stream`: track ordering, then the persistent fit.
 // With `timing`, events timing[0] and timing[1] are recorded right before and after the
-// persistent fit kernel.
+// persistent fit kernel. Learned mode: the starting proposals come from the pre-pass, or, with
+// `h0_given`, from that array (one per track of `a`, written by an earlier pre-pass on the device).
 cudaError_t launch_fit(const FitArgs& a, const FieldDev& field, int precision, const Workspace& ws, LaunchShape shape,
-                       cudaStream_t stream, const cudaEvent_t* timing = nullptr);
+                       cudaStream_t stream, const cudaEvent_t* timing = nullptr, const float* h0_given = nullptr);
 
 }  // namespace tkf
 
@@ -257,6 +258,7 @@ struct tkf_context_s {
   // host-buffer entry point: copy streams and events of its chunk pipeline (created on first use)
   cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr, fit2_stream = nullptr;
   cudaEvent_t chunk_in[kHostChunksMax] = {}, chunk_fit[kHostChunksMax] = {};
+  cudaEvent_t props_in = nullptr, props_done = nullptr;  // learned mode: the batch's proposal pre-pass
   // fit workspace (ordering scratch), grown on demand and reused by later calls
   void* ws = nullptr;
   size_t ws_bytes = 0;

@@ -110,7 +110,7 @@ Workspace carve_workspace(void* base, uint32_t n_tracks, bool learned, uint64_t 
 }
 
 cudaError_t launch_fit(const FitArgs& a, const FieldDev& f, int precision, const Workspace& ws, LaunchShape shape,
-                       cudaStream_t stream, const cudaEvent_t* timing) {
+                       cudaStream_t stream, const cudaEvent_t* timing, const float* h0_given) {
   if (a.n_tracks == 0) return cudaSuccess;
   const uint32_t n = a.n_tracks;
   cudaError_t e = cudaMemsetAsync(ws.counter, 0, sizeof(uint32_t) * (1 + kKeyBins), stream);
@@ -128,7 +128,9 @@ cudaError_t launch_fit(const FitArgs& a, const FieldDev& f, int precision, const
     if (!ws.states) return cudaErrorInvalidValue;
     b.states_scratch = ws.states;
   }
-  if (mode == 1) {  // network proposals of each track's starting step size
+  if (mode == 1 && h0_given) {  // proposals already made for these tracks
+    b.h0 = h0_given;
+  } else if (mode == 1) {  // network proposals of each track's starting step size
     if (!ws.h0) return cudaErrorInvalidValue;
     e = launch_propose_start(a, f, ws.h0, stream);
     if (e != cudaSuccess) return e;

@@ -146,6 +146,20 @@ def test_host_entry_point_pipelines_chunks_with_identical_results(barrel, precis
     _host_vs_device(ctx, geo, fld, hb, tkf.Options(precision=precision, mass=w.mass))
 
 
+def test_host_entry_point_learned_mode_with_identical_results(barrel):
+    """Learned mode through tkf_fit_host on the whole batch: the proposals of every track come
+    from one pre-pass over the batch's offsets, surface ids and seeds (copied first), then the
+    chunks are fitted; results bit for bit those of the device entry point, whose fit runs the
+    pre-pass itself."""
+    ctx, w, geo, fld, _, _ = barrel
+    t = w.tracks
+    wbf, _ = proposer.barrel_proposer()
+    m = tkf.Mlp(ctx, wbf)
+    hb = tkf.Batch.from_arrays(t.offsets, t.meas, t.sid, t.seed_par, t.seed_cov)
+    _host_vs_device(ctx, geo, fld, hb, tkf.Options(precision=tkf.MIXED, mass=w.mass, step_mode=tkf.STEP_LEARNED,
+                                                   mlp=m))
+
+
 def test_host_entry_point_with_decreasing_offsets_matches_the_device_entry_point(barrel):
     """Offsets that decrease somewhere: each chunk copies the measurements between the least and
     the greatest of its tracks' offsets, and the copied range grows as one interval (below and
