@@ -72,12 +72,12 @@ FLOPS_MAP = {
 # launch and are scaled by tracks to a full launch. Keyed by (workload, variant, register cap of
 # the launched kernel); a kernel change voids the entries (profiles/ keeps the commands).
 CAPTURES = {
-    ("barrel", "mixed_learned", 64): {"tracks": 279450, "hits_after_first": 2964523, "attempts": 5099946,
-                                      "rejected": 20326, "shape": "32,32,32,64", "dram_bytes": 9529840640,
-                                      "fp64_exec": 2525621897, "fp64_model": 2414401235, "fp32_exec": 5306933302},
+    ("barrel", "mixed_learned", 64): {"tracks": 279450, "hits_after_first": 2964523, "attempts": 5100784,
+                                      "rejected": 19284, "shape": "32,32,32,64", "dram_bytes": 9393538560,
+                                      "fp64_exec": 2525670037, "fp64_model": 2414430499, "fp32_exec": 5174997610},
     ("barrel", "mixed", 64): {"tracks": 279450, "hits_after_first": 2964523, "attempts": 5014955, "rejected": 143604,
-                              "shape": "32,32,32,64", "dram_bytes": 9532920064,
-                              "fp64_exec": 2522392577, "fp64_model": 2411222079, "fp32_exec": 5190418558},
+                              "shape": "32,32,32,64", "dram_bytes": 9377217792,
+                              "fp64_exec": 2522392577, "fp64_model": 2411222079, "fp32_exec": 5089310192},
     ("barrel", "mixed_learned", 128): {"tracks": 279450, "hits_after_first": 2964523, "attempts": 5099946,
                                        "rejected": 20326, "shape": "128,4,32,128", "dram_bytes": 1424030976,
                                        "fp64_exec": 2525581629, "fp64_model": 2414401235, "fp32_exec": 5307514410},
