@@ -86,7 +86,7 @@ def eff_pur(r, mc, t, idx):
     return eff, pur
 
 
-@pytest.mark.parametrize("beam", [1, 3])
+@pytest.mark.parametrize("beam", [1, 3, 8])
 def test_ckf_parity_pion_event(ctx, beam):
     w = synth.barrel_workload(n_events=1, lo=3000, hi=3000, seed=31)
     t, g = w.tracks, w.geometry
@@ -98,6 +98,20 @@ def test_ckf_parity_pion_event(ctx, beam):
     eff, pur = eff_pur(gr, mc, t, idx)
     print({"eff": eff.mean(), "eff90": (eff >= 0.9).mean(), "purity": pur.mean()})
     assert eff.mean() > 0.99 and pur.mean() > 0.999
+
+
+def test_ckf_parity_short_candidates(ctx):
+    """A short entry limit (8) and one hole at most, beam 5: branches that reach the limit end on
+    the last step and the history of every kept branch is read back from the tree; candidates
+    identical to the oracle's."""
+    w = synth.barrel_workload(n_events=1, lo=2000, hi=2000, seed=37)
+    mc = synth.measurement_container(w.tracks, w.geometry.n)
+    seed_sid, par, cov, _ = _seeds(w)
+    kw = dict(beam=5, max_entries=8, max_holes=1)
+    gr = gpu_find(ctx, w, mc, seed_sid, par, cov, **kw)
+    orr = oracle_find(w, mc, seed_sid, par, cov, **kw)
+    compare(gr, orr)
+    assert gr["n_entries"].max() == 8
 
 
 def test_ckf_parity_field_map(ctx):
