@@ -113,11 +113,16 @@ __device__ __forceinline__ double dot3(const double a[3], const double b[3]) {
 }
 
 // ------------------------------------------------------------------ field policies
-// Uniform field along z (the solenoid axis): T x B has no z component.
+// Uniform field along z (the solenoid axis): T x B has no z component, so T_z, and with it
+// theta, is constant along the path: the theta row of the transport Jacobian of the motion is
+// exactly e_3 (kAlongZ). The FP64 path keeps the derivative of the discrete RKN map (whose
+// final normalisation of T moves that row by the integration error, ~1e-9); the mixed path,
+// whose FP32 Jacobian carries ~1e-7 of rounding there, sets the row to e_3.
 struct FieldUniformZ {
   double bz;
   float bzf;
   static constexpr bool kUniform = true;
+  static constexpr bool kAlongZ = true;
   __device__ __forceinline__ void at(const double*, double B[3], bool&) const {
     B[0] = 0.0; B[1] = 0.0; B[2] = bz;
   }
@@ -130,6 +135,7 @@ struct FieldUniform {
   double b[3];
   float bf[3];
   static constexpr bool kUniform = true;
+  static constexpr bool kAlongZ = false;
   __device__ __forceinline__ void at(const double*, double B[3], bool&) const {
     B[0] = b[0]; B[1] = b[1]; B[2] = b[2];
   }
@@ -145,6 +151,7 @@ struct FieldGrid {
   double r0, z0, inv_dr, inv_dz;
   float r0f, z0f, inv_drf, inv_dzf, rmaxf, zmaxf;  // FP32 copies: origin, 1/spacing, nr-1, nz-1
   static constexpr bool kUniform = false;
+  static constexpr bool kAlongZ = false;
   __device__ __forceinline__ void at(const double* x, double B[3], bool& oof) const {
     double r = sqrt(x[0] * x[0] + x[1] * x[1]);
     double fr = (r - r0) * inv_dr;
@@ -842,7 +849,8 @@ __device__ __forceinline__ void jac_column(const R n[3], const R u[3], const R v
 
 // C <- J C J^T for the 5x5 packed symmetric C (J row 4 = e_4), over rows 0..3 of J; with kG = 4
 // lane gl computes row gl and the group exchanges the results.
-template <int kG, class R>
+// kZ: row 3 of J is e_3 (theta conserved, a field along z): that row and column are copies.
+template <int kG, class R, bool kZ = false>
 __device__ __forceinline__ void transport_cov(const R J[5][5], R Cw[15], uint32_t gl, uint32_t gmask) {
   if constexpr (kG == 1) {
     R M[5][5];
@@ -850,6 +858,10 @@ __device__ __forceinline__ void transport_cov(const R J[5][5], R Cw[15], uint32_
     for (int r0 = 0; r0 < 4; ++r0)
 #pragma unroll
       for (int c0 = 0; c0 < 5; ++c0) {
+        if (kZ && r0 == 3) {
+          M[3][c0] = Cw[S(3, c0)];
+          continue;
+        }
         R acc = R(0);
 #pragma unroll
         for (int q = 0; q < 5; ++q) acc += J[r0][q] * Cw[S(q, c0)];
@@ -864,6 +876,8 @@ __device__ __forceinline__ void transport_cov(const R J[5][5], R Cw[15], uint32_
         R acc;
         if (c0 == 4) {
           acc = M[r0][4];
+        } else if (kZ && c0 == 3) {
+          acc = M[r0][3];
         } else {
           acc = R(0);
 #pragma unroll
@@ -1437,6 +1451,10 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
       }
 #pragma unroll
       for (int c = 0; c < 5; ++c) Jf[4][c] = (c == 4) ? 1.0f : 0.0f;
+      if constexpr (F::kAlongZ) {  // theta is conserved: its row is e_3 (FP32 noise otherwise)
+#pragma unroll
+        for (int c = 0; c < 5; ++c) Jf[3][c] = (c == 3) ? 1.0f : 0.0f;
+      }
       const double d[3] = {r[0] - s.c[0], r[1] - s.c[1], r[2] - s.c[2]};
       double su[3], sv[3];
       reload_uv(a.surf, sid, su, sv);
@@ -1446,7 +1464,7 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
       p[3] = 0.0;
       p[4] = lam;
       // C_pred = J (C + Q) J^T in FP32
-      transport_cov<kG>(Jf, Cf, gl, gmask);
+      transport_cov<kG, float, F::kAlongZ>(Jf, Cf, gl, gmask);
 #pragma unroll
       for (int j = 0; j < 15; ++j) C[j] = cov_from_f<U>(Cf[j]);
 #pragma unroll
@@ -1468,6 +1486,10 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
         U row[5];
 #pragma unroll
         for (int c0 = 0; c0 < 4; ++c0) {
+          if (kMixed && F::kAlongZ && c0 == 3) {  // J row 3 is e_3 (mixed path, field along z)
+            row[3] = st.P(r0, 3);
+            continue;
+          }
           U acc = 0;
 #pragma unroll
           for (int q = 0; q < 5; ++q) acc += st.P(r0, q) * J[c0][q];
@@ -1481,6 +1503,11 @@ __device__ void fit_track(const FitArgs& a, const F& fld, uint32_t i,
         U rg[5], r4[5];
 #pragma unroll
         for (int c0 = 0; c0 < 4; ++c0) {
+          if (kMixed && F::kAlongZ && c0 == 3) {  // J row 3 is e_3 (mixed path, field along z)
+            rg[3] = Pg[3];
+            r4[3] = P4[3];
+            continue;
+          }
           U acc = 0, acc4 = 0;
 #pragma unroll
           for (int q = 0; q < 5; ++q) {
