@@ -23,8 +23,10 @@ __global__ void __launch_bounds__(256) order_keys_kernel(const uint32_t* __restr
   __shared__ uint32_t h[kKeyBins];
   for (int b = threadIdx.x; b < kKeyBins; b += blockDim.x) h[b] = 0;
   __syncthreads();
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) {
+  // each block takes one contiguous range of the tracks (one histogram flush a block)
+  const uint32_t per = (n + gridDim.x - 1) / gridDim.x;
+  const uint32_t r0 = blockIdx.x * per, r1 = min(n, r0 + per);
+  for (uint32_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
     const uint32_t b0 = offsets[i], b1 = offsets[i + 1];
     const uint32_t nh = b1 >= b0 ? min(b1 - b0, uint32_t(kNBins - 1)) : 0u;
     const float qop = float(seed_par[size_t(4) * stride + i]);
@@ -59,27 +61,29 @@ __global__ void __launch_bounds__(kKeyBins) order_scan_kernel(uint32_t* __restri
   hist[t] = v[t] - hist[t];
 }
 
-// Scatter in two levels: the tracks of a block take consecutive ranks per key in shared memory,
-// then one global atomic per (block, key) reserves the block's range of that key (the per-track
-// global atomics contended on the few most common keys). Tracks of a key land in block order of
-// arrival; the fit of a track does not depend on its place.
+// Scatter in two levels: each block takes one contiguous range of the tracks, counts its keys in
+// shared memory, reserves its range of every key with one global atomic (the per-track global
+// atomics contended on the few most common keys), then places its tracks within those ranges.
+// Tracks of a key land in block order of arrival; the fit of a track does not depend on its place.
 __global__ void __launch_bounds__(256) order_scatter_kernel(const uint32_t* __restrict__ keys, uint32_t n,
                                                             uint32_t* __restrict__ base, uint32_t* __restrict__ perm) {
   __shared__ uint32_t cnt[kKeyBins];
   __shared__ uint32_t off[kKeyBins];
   for (int b = threadIdx.x; b < kKeyBins; b += blockDim.x) cnt[b] = 0;
   __syncthreads();
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  uint32_t key = 0, rank = 0;
-  if (i < n) {
-    key = keys[i];
-    rank = atomicAdd(&cnt[key], 1u);
+  const uint32_t per = (n + gridDim.x - 1) / gridDim.x;
+  const uint32_t r0 = blockIdx.x * per, r1 = min(n, r0 + per);
+  for (uint32_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) atomicAdd(&cnt[keys[i]], 1u);
+  __syncthreads();
+  for (int b = threadIdx.x; b < kKeyBins; b += blockDim.x) {
+    if (cnt[b]) off[b] = atomicAdd(&base[b], cnt[b]);
+    cnt[b] = 0;  // from here on: the next free rank of the key within the block's range
   }
   __syncthreads();
-  for (int b = threadIdx.x; b < kKeyBins; b += blockDim.x)
-    if (cnt[b]) off[b] = atomicAdd(&base[b], cnt[b]);
-  __syncthreads();
-  if (i < n) perm[off[key] + rank] = i;
+  for (uint32_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    const uint32_t key = keys[i];
+    perm[off[key] + atomicAdd(&cnt[key], 1u)] = i;
+  }
 }
 
 }  // namespace
@@ -115,7 +119,8 @@ cudaError_t launch_fit(const FitArgs& a, const FieldDev& f, int precision, const
   const uint32_t n = a.n_tracks;
   cudaError_t e = cudaMemsetAsync(ws.counter, 0, sizeof(uint32_t) * (1 + kKeyBins), stream);
   if (e != cudaSuccess) return e;
-  const unsigned g256 = (n + 255) / 256;
+  // at most 1,216 blocks (8 an SM on GB300), each over one contiguous range of the tracks
+  const unsigned g256 = (n + 255) / 256 < 1216u ? (n + 255) / 256 : 1216u;
   order_keys_kernel<<<g256, 256, 0, stream>>>(a.offsets, a.seed_par, n, a.stride, ws.keys, ws.hist);
   order_scan_kernel<<<1, kKeyBins, 0, stream>>>(ws.hist);
   order_scatter_kernel<<<g256, 256, 0, stream>>>(ws.keys, n, ws.hist, ws.perm);
