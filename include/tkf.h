@@ -335,8 +335,9 @@ tkf_status tkf_fit(tkf_context ctx, tkf_geometry geo, tkf_field field, const tkf
 
 /* The same fit from HOST arrays: copies the inputs to a device staging area owned by the
  * context (grown on demand), fits, and copies the outputs back; returns when the outputs are
- * in host memory. Batches of at least 131,072 tracks are cut into up to 8 chunks of
- * consecutive tracks pipelined over two copy streams of the context, `stream` and a second
+ * in host memory. Batches of at least 131,072 tracks are cut into chunks of consecutive tracks
+ * (a twentieth of the batch first, then up to four equal chunks, each with its own launch
+ * shape) pipelined over two copy streams of the context, `stream` and a second
  * compute stream (a chunk fits while its predecessor finishes its tail): the copy-in of a chunk
  * and the copy-out of the previous one overlap the fit of the current one (results identical
  * to one piece). A chunk copies the measurements between the least and the greatest of its

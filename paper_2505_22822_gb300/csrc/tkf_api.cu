@@ -48,8 +48,9 @@ bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0
 // (defined with the array, at the end of this file).
 cudaError_t noalloc_scratch_address(void** out);
 
-// Host-buffer entry point: the batch is cut into at most kHostChunksMax chunks of at least
-// kHostChunkMinTracks tracks, whose copies overlap the fits of their neighbours.
+// Host-buffer entry point: a batch of at least two kHostChunkMinTracks is cut into a small first
+// chunk and up to four chunks of at least kHostChunkMinTracks tracks, whose copies overlap the
+// fits of their neighbours.
 constexpr size_t kHostChunkMinTracks = 65536;
 
 }  // namespace
@@ -770,14 +771,24 @@ tkf_status tkf_fit_host(tkf_context ctx, tkf_geometry geo, tkf_field field, cons
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->props_done, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tkf_fit_host: stream or event creation");
   }
-  const uint32_t chunks =
-      n >= size_t(kHostChunkMinTracks) * 2
-          ? uint32_t(kHostChunksMax < n / kHostChunkMinTracks ? kHostChunksMax : n / kHostChunkMinTracks)
-          : 1u;
+  // chunk schedule: a small first chunk (a twentieth of the batch), so that the first fit starts
+  // soon after the first copies, then up to four equal chunks (large chunks keep the persistent
+  // fit's tail short)
+  uint32_t chunks = 1;
+  size_t bound[kHostChunksMax + 1] = {0, n};
+  if (n >= size_t(kHostChunkMinTracks) * 2) {
+    const size_t big = n / kHostChunkMinTracks < 4 ? n / kHostChunkMinTracks : 4;
+    const size_t first = n / 20;
+    chunks = uint32_t(big) + 1;
+    bound[1] = first;
+    for (size_t c = 1; c <= big; ++c) bound[c + 1] = first + (n - first) * c / big;
+  }
+  size_t max_chunk = 0;
+  for (uint32_t c = 0; c < chunks; ++c) max_chunk = bound[c + 1] - bound[c] > max_chunk ? bound[c + 1] - bound[c] : max_chunk;
   tkf::FitArgs full = make_args(geo, o, &din, &dout);
   const bool learned = o->step_mode == TKF_STEP_LEARNED;
-  // one workspace per chunk (a chunk has at most n / chunks + 1 tracks)
-  const size_t chunk_ws = (tkf::workspace_bytes(uint32_t(n / chunks + 1), learned) + 255) & ~size_t(255);
+  // one workspace per chunk (sized for the largest)
+  const size_t chunk_ws = (tkf::workspace_bytes(uint32_t(max_chunk + 1), learned) + 255) & ~size_t(255);
   tkf::LaunchShape chunk_shape;
   if (chunks > 1 && chunks * chunk_ws > ctx->ws_bytes) {
     e = cudaStreamSynchronize(st);
@@ -842,7 +853,7 @@ tkf_status tkf_fit_host(tkf_context ctx, tkf_geometry geo, tkf_field field, cons
     if (!props_first) h2d(const_cast<uint32_t*>(din.sid) + a0, hin->sid + a0, k * 4);
   };
   for (uint32_t c = 0; c < chunks; ++c) {
-    const size_t t0 = n * c / chunks, t1 = n * (c + 1) / chunks, nt = t1 - t0;
+    const size_t t0 = bound[c], t1 = bound[c + 1], nt = t1 - t0;
     // the measurements the chunk's tracks can reference lie between the least and the greatest
     // of their offsets (a track whose range is reversed or beyond n_meas reads none: the kernel
     // flags it); scanned here, while the earlier chunks' copies and fits run
@@ -889,7 +900,11 @@ tkf_status tkf_fit_host(tkf_context ctx, tkf_geometry geo, tkf_field field, cons
       if (s != TKF_OK) return s;
     } else {
       const tkf::Workspace wsc = tkf::carve_workspace(static_cast<char*>(ctx->ws) + c * chunk_ws, nt, learned);
-      if (c == 0 && (e = tkf::resolve_shape(ctx, a, field->f, o->precision, wsc, o, st, &chunk_shape)) != cudaSuccess)
+      // each chunk its own launch shape (the small first chunk and the large ones tune apart); a
+      // tuning run launches on `stream`, which therefore waits for the chunk's inputs first
+      if (c > 0 && (e = cudaStreamWaitEvent(st, ctx->chunk_in[c], 0)) != cudaSuccess)
+        return cuda_fail(ctx, e, "tkf_fit_host: stream wait");
+      if ((e = tkf::resolve_shape(ctx, a, field->f, o->precision, wsc, o, st, &chunk_shape)) != cudaSuccess)
         return cuda_fail(ctx, e, "tkf_fit_host: autotune");
       if ((e = tkf::launch_fit(a, field->f, o->precision, wsc, chunk_shape, cs, nullptr,
                                props_first ? h0_all + t0 : nullptr)) != cudaSuccess)

@@ -138,7 +138,8 @@ def _host_vs_device(ctx, geo, fld, hb, opts):
 
 @pytest.mark.parametrize("precision", [tkf.FP64, tkf.MIXED])
 def test_host_entry_point_pipelines_chunks_with_identical_results(barrel, precision):
-    """605,172 tracks through tkf_fit_host: eight chunks whose copies overlap the fits, results
+    """605,172 tracks through tkf_fit_host: five chunks (a small first one, then four) whose copies
+    overlap the fits, results
     bit for bit those of the device entry point."""
     ctx, w, geo, fld, _, _ = barrel
     t = w.tracks
