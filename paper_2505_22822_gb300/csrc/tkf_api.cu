@@ -187,7 +187,9 @@ tkf_status tkf_geometry_create(tkf_context ctx, const tkf_surface_desc* s, uint3
     }
     f[9] = float(d.thickness);
     f[10] = float(d.thickness / d.x0);
-    for (int k = 11; k < 16; ++k) f[k] = 0.0f;
+    for (int r = 0; r < 3; ++r) f[11 + r] = float(d.center[r]);
+    f[14] = 0.0f;
+    f[15] = 0.0f;
   }
   DeviceGuard g(ctx->device);
   if (!g.ok) {

@@ -77,15 +77,26 @@ constexpr int kCkfMaxRings = 256;  // ring rows kept in shared memory (more: rea
 
 // Navigation tables of a block, in shared memory: the layer rows, the ring rows (when they fit),
 // the barrel layers' outer face radii, and the layer ids in the order in which a straight line
-// meets them: barrel layers by face radius, disks by face z (ties: lower id first).
+// meets them: barrel layers by face radius, disks by face z (ties: lower id first). The FP32
+// screens read their operands from FP32 rows, the same values as converting the FP64 rows at each
+// use: per layer float(n_phi / 2 pi) (barrels), the pitch, the inner radius (disks) and the
+// modules' half extents, the outer face radius (barrels), the radial extent test's bounds (disks);
+// per ring float(n_phi / 2 pi).
+constexpr int kLayF = 8;  // floats a layer: phi bins a radian, pitch, r_inner, half_u, half_v, face_r,
+                          // r_inner - 10, r_inner + n_rings ring_pitch + 10
 struct NavTables {
   double lay[kCkfMaxLayers * 8];
   double ring[kCkfMaxRings * 4];
   double face_r[kCkfMaxLayers];
-  const double* rings;  // `ring`, or the global table when it does not fit
+  float lay_f[kCkfMaxLayers * kLayF];
+  float ring_f[kCkfMaxRings];
+  const double* rings;     // `ring`, or the global table when it does not fit
+  const float* rings_f;    // `ring_f`, or NULL when the rings do not fit
   int bar[kCkfMaxLayers], dsk[kCkfMaxLayers];
   int nbar, ndsk;
 };
+
+__device__ __forceinline__ float phi_bins_per_radian(double n_phi) { return float(n_phi / (2.0 * kPi)); }
 
 // outer face radius of a barrel layer (its flat modules reach sqrt((r + 1)^2 + half_u^2))
 __device__ __forceinline__ double barrel_face(const double* l) { return sqrt((l[1] + 1.0) * (l[1] + 1.0) + l[6] * l[6]); }
@@ -95,12 +106,26 @@ __device__ void build_nav_tables(const CkfArgs& a, NavTables& nt) {
   for (uint32_t j = threadIdx.x; j < 8 * a.n_layers; j += blockDim.x) nt.lay[j] = a.layers[j];
   if (ring_fit)
     for (uint32_t j = threadIdx.x; j < 4 * a.n_rings; j += blockDim.x) nt.ring[j] = a.rings[j];
-  if (threadIdx.x == 0) nt.rings = ring_fit ? nt.ring : a.rings;
+  if (threadIdx.x == 0) {
+    nt.rings = ring_fit ? nt.ring : a.rings;
+    nt.rings_f = ring_fit ? nt.ring_f : nullptr;
+  }
   __syncthreads();
   for (uint32_t li = threadIdx.x; li < a.n_layers; li += blockDim.x) {
     const double* l = nt.lay + 8 * li;
     nt.face_r[li] = l[0] == 0.0 ? barrel_face(l) : 0.0;
+    float* lf = nt.lay_f + kLayF * li;
+    lf[0] = l[0] == 0.0 ? phi_bins_per_radian(double(int(l[2]))) : 0.0f;
+    lf[1] = d2f(l[4]);
+    lf[2] = d2f(l[5]);
+    lf[3] = d2f(l[6]);
+    lf[4] = d2f(l[7]);
+    lf[5] = d2f(nt.face_r[li]);
+    lf[6] = l[0] == 0.0 ? 0.0f : d2f(l[5] - 10.0);
+    lf[7] = l[0] == 0.0 ? 0.0f : d2f(l[5] + l[2] * l[4] + 10.0);
   }
+  if (ring_fit)
+    for (uint32_t k = threadIdx.x; k < a.n_rings; k += blockDim.x) nt.ring_f[k] = phi_bins_per_radian(double(int(nt.ring[4 * k + 1])));
   __syncthreads();
   if (threadIdx.x == 0) {
     int nb = 0, nd = 0;
@@ -170,9 +195,10 @@ __device__ __noinline__ int layer_candidates(const NavTables& nt, uint32_t li, c
   const float phf0 = atan2f(d2f(q[1]), d2f(q[0]));
   const float phf = phf0 < 0.0f ? phf0 + float(2.0 * kPi) : phf0;
   double phi = -1.0;  // the FP64 angle in [0, 2 pi), on first need
-  auto phi_bin = [&](int nphi) -> int {
+  const float* lf = nt.lay_f + kLayF * li;
+  auto phi_bin = [&](int nphi, float per_rad) -> int {
     int b;
-    if (floor_sure(phf * float(double(nphi) / (2.0 * kPi)) + 0.5f, 4e-6f * float(nphi + 1), b)) return b;
+    if (floor_sure(phf * per_rad + 0.5f, 4e-6f * float(nphi + 1), b)) return b;
     if (phi < 0.0) {
       phi = atan2(q[1], q[0]);
       if (phi < 0.0) phi += 2.0 * kPi;
@@ -182,8 +208,8 @@ __device__ __noinline__ int layer_candidates(const NavTables& nt, uint32_t li, c
   int n = 0;
   if (l[0] == 0.0) {
     const int nphi = int(l[2]), nrows = int(l[3]);
-    const int ip0 = phi_bin(nphi);
-    const float zq = d2f(q[2]) / d2f(l[4]);
+    const int ip0 = phi_bin(nphi, lf[0]);
+    const float zq = d2f(q[2]) / lf[1];
     int iz0;
     if (!floor_sure(zq + 0.5f * float(nrows), 4e-6f * (1.0f + fabsf(zq) + float(nrows)), iz0))
       iz0 = int(floor(q[2] / l[4] + 0.5 * nrows));
@@ -193,15 +219,16 @@ __device__ __noinline__ int layer_candidates(const NavTables& nt, uint32_t li, c
     }
   } else {
     const int nr = int(l[2]);
-    const float rq = hypotf(d2f(q[0]), d2f(q[1])), r0f = d2f(l[5]), pf = d2f(l[4]);
+    const float rq = hypotf(d2f(q[0]), d2f(q[1])), r0f = lf[2], pf = lf[1];
     int k0;
     if (!floor_sure((rq - r0f) / pf, 4e-6f * (1.0f + (rq + fabsf(r0f)) / pf), k0))
       k0 = int(floor((hypot(q[0], q[1]) - l[5]) / l[4]));
     for (int k = k0 - 1; k <= k0 + 1; ++k) {
       if (k < 0 || k >= nr) continue;
-      const double* rg = nt.rings + 4 * (uint32_t(l[3]) + uint32_t(k));
+      const uint32_t row = uint32_t(l[3]) + uint32_t(k);
+      const double* rg = nt.rings + 4 * row;
       const int nphi = int(rg[1]);
-      const int ip0 = phi_bin(nphi);
+      const int ip0 = phi_bin(nphi, nt.rings_f ? nt.rings_f[row] : phi_bins_per_radian(double(nphi)));
       for (int d = -1; d <= 1; ++d) out[n++] = uint32_t(rg[2]) + wrap_bin(ip0, d, nphi);
     }
   }
@@ -209,14 +236,22 @@ __device__ __noinline__ int layer_candidates(const NavTables& nt, uint32_t li, c
 }
 
 // straight-line path to the outer face of layer li if ahead and within its extent, else -1
-// (face_r: the barrel layers' outer face radii, computed once a block)
-__device__ double layer_path(const NavTables& nt, uint32_t li, const double x[3], const double T[3]) {
+// (face_r: the barrel layers' outer face radii, computed once a block). xf, Tf: FP32 copies of x
+// and T for two screens that return -1 only where the FP64 evaluation surely does: a barrel face
+// the point lies outside (|x_perp|^2 - r_face^2 >= 0), and a disk face reached outside its radial
+// extent. Each FP32 quantity is within a few 2^-24 of its magnitudes of the FP64 one (the copies,
+// one rounding an operation, sqrtf and the division correctly rounded); the bounds below take
+// 1e-6 relative (about 17 units) plus 1e-3 mm for the rounding of the stored bounds.
+__device__ double layer_path(const NavTables& nt, uint32_t li, const double x[3], const double T[3],
+                             const float xf[3], const float Tf[3]) {
   const double* l = nt.lay + 8 * li;
-  const double* face_r = nt.face_r;
+  const float* lf = nt.lay_f + kLayF * li;
   double s;
   if (l[0] == 0.0) {
+    const float p2f = xf[0] * xf[0] + xf[1] * xf[1], f2f = lf[5] * lf[5];
+    if (p2f - f2f > 1e-6f * (p2f + f2f)) return -1.0;
     const double aa = T[0] * T[0] + T[1] * T[1], b = x[0] * T[0] + x[1] * T[1];
-    const double rf = face_r[li];
+    const double rf = nt.face_r[li];
     const double c = x[0] * x[0] + x[1] * x[1] - rf * rf;
     if (!(aa > 0.0) || c >= 0.0) return -1.0;
     s = (-b + sqrt(b * b - aa * c)) / aa;
@@ -225,6 +260,12 @@ __device__ double layer_path(const NavTables& nt, uint32_t li, const double x[3]
     const double dz = l[1] + (l[1] > 0.0 ? 1.0 : -1.0) - x[2];
     // behind or parallel (opposite or zero signs): the quotient would not be > 0
     if (!((dz > 0.0 && T[2] > 0.0) || (dz < 0.0 && T[2] < 0.0))) return -1.0;
+    // the radius where the line meets the face, in FP32 (an overflow or NaN screens nothing)
+    const float sf = d2f(dz) / Tf[2];
+    const float px = fmaf(sf, Tf[0], xf[0]), py = fmaf(sf, Tf[1], xf[1]);
+    const float rq = sqrtf(px * px + py * py);
+    const float e = 1e-6f * (fabsf(xf[0]) + fabsf(xf[1]) + fabsf(sf) * (fabsf(Tf[0]) + fabsf(Tf[1])) + rq) + 1e-3f;
+    if (rq + e < lf[6] || rq - e > lf[7]) return -1.0;
     s = dz / T[2];
     if (!(s > 0.0)) return -1.0;
     const double r = hypot(x[0] + s * T[0], x[1] + s * T[1]);
@@ -239,15 +280,22 @@ __device__ __forceinline__ bool listed(const uint32_t* v, int n, uint32_t id) {
   return false;
 }
 
-// True when the parabola x + s T + s^2/2 k surely crosses the plane of a module (centre at x + d,
-// FP32 copies u, v, n of its frame) outside its half extents plus the helix margin: an FP32
-// evaluation whose every rounding is covered by `err` (below), so that the FP64 test of
-// nearest_crossed rejects the module too. Grazing incidence (|n.T| <= 0.05) and near-tangent
-// solutions (disc <= an^2 / 4) are left to FP64.
-__device__ __forceinline__ bool surely_outside(const float* __restrict__ f, const double d[3], const float Tf[3],
-                                               const float kf[3], float knorm, float bendf, double hu, double hv) {
+// True when the parabola x + s T + s^2/2 k surely crosses the plane of a module outside its half
+// extents plus the helix margin: an FP32 evaluation whose every rounding is covered by `err`
+// (below), so that the FP64 test of nearest_crossed rejects the module too. `f`: the record's
+// FP32 block (frame u, v, n at 0, 3, 6; centre c at 11); xf: the FP32 copy of x, xn its L1 norm.
+// The offset d = c - x is formed in FP32 from the two copies: besides the rounding of the
+// difference (relative 2^-24, as a conversion of the FP64 offset would have), it carries the
+// copies' rounding, at most 2^-24 (|c|_1 + |x|_1) in L1 norm (ecx, taken twice over). That error
+// moves q by as much, and the crossing's path by at most ecx / |an + bn s| <= 2 ecx / |an| (the
+// screen keeps disc = (an + bn s)^2 above an^2 / 4; taken as 2.5 ecx / |an|). Grazing incidence
+// (|n.T| <= 0.05) and near-tangent solutions (disc <= an^2 / 4) are left to FP64.
+__device__ __forceinline__ bool surely_outside(const float* __restrict__ f, const float xf[3], float xn,
+                                               const float Tf[3], const float kf[3], float knorm, float bendf,
+                                               float huf, float hvf) {
   const float uf[3] = {f[0], f[1], f[2]}, vf[3] = {f[3], f[4], f[5]}, nf[3] = {f[6], f[7], f[8]};
-  const float df[3] = {d2f(d[0]), d2f(d[1]), d2f(d[2])};
+  const float cf[3] = {f[11], f[12], f[13]};
+  const float df[3] = {cf[0] - xf[0], cf[1] - xf[1], cf[2] - xf[2]};
   const float an = dotr(nf, Tf);
   if (!(fabsf(an) > 0.05f)) return false;
   const float dist = dotr(nf, df), bn = dotr(nf, kf);
@@ -258,43 +306,55 @@ __device__ __forceinline__ bool surely_outside(const float* __restrict__ f, cons
   const float as = fabsf(sf), h = 0.5f * sf * sf;
   const float q[3] = {-df[0] + sf * Tf[0] + h * kf[0], -df[1] + sf * Tf[1] + h * kf[1], -df[2] + sf * Tf[2] + h * kf[2]};
   const float dn = fabsf(df[0]) + fabsf(df[1]) + fabsf(df[2]), qn = fabsf(q[0]) + fabsf(q[1]) + fabsf(q[2]);
-  // error of s: relative 1e-5 plus the propagated rounding of dist (through an and disc), then
-  // that of q (d, the products, the sums) and of the projections
+  const float ecx = 1.2e-7f * (fabsf(cf[0]) + fabsf(cf[1]) + fabsf(cf[2]) + xn);
+  // error of s: relative 1e-5 plus the propagated rounding of dist (through an and disc) and the
+  // copies' error ecx, then that of q (d, the products, the sums) and of the projections
   const float rs = 1e-5f + 2e-6f * fabsf(bn) * dn / (an * an);
-  const float ds = rs * as + 1e-5f * dn / fabsf(an);
-  const float err = 1e-3f + ds * (1.0f + (as + ds) * knorm) + 1e-6f * (dn + qn);
+  const float ds = rs * as + (1e-5f * dn + 2.5f * ecx) / fabsf(an);
+  const float err = 1e-3f + ecx + ds * (1.0f + (as + ds) * knorm) + 1e-6f * (dn + qn);
   const float sup = (as + ds) * 1.00001f;
   const float margin = (1.0f + sup * sup * sup * bendf * bendf / 6.0f) * 1.00001f;
-  return fabsf(dotr(uf, q)) - err > float(hu) + margin || fabsf(dotr(vf, q)) - err > float(hv) + margin;
+  return fabsf(dotr(uf, q)) - err > huf + margin || fabsf(dotr(vf, q)) - err > hvf + margin;
 }
 
 // nearest of `cand` crossed by the parabola x + s T + s^2/2 k within bounds and margin
+// (xf, Tf, kf: FP32 copies of x, T, k)
 __device__ __noinline__ int nearest_crossed(const CkfArgs& a, const NavTables& nt, const uint32_t* cand, int nc,
                                             const double x[3], const double T[3], const double k[3], double bend,
+                                            const float xf[3], const float Tf[3], const float kf[3],
                                             const uint32_t* skip, int nskip, double& s_out) {
   int best = -1;
   double best_s = 0.0;
-  const float Tf[3] = {d2f(T[0]), d2f(T[1]), d2f(T[2])}, kf[3] = {d2f(k[0]), d2f(k[1]), d2f(k[2])};
   const float knorm = (fabsf(kf[0]) + fabsf(kf[1]) + fabsf(kf[2])) * 1.00001f, bendf = d2f(bend) * 1.00001f;
+  const float xn = fabsf(xf[0]) + fabsf(xf[1]) + fabsf(xf[2]);
   for (int j = 0; j < nc; ++j) {
     const uint32_t id = cand[j];
     if (id >= a.n_surf || listed(skip, nskip, id)) continue;
     const double* rec = a.surf + size_t(id) * kSurfStride;
+    // half extents of the module's layer (outside the layer structure: unbounded)
+    const int li = a.layer_of[id];
+    const float huf = li >= 0 ? nt.lay_f[kLayF * li + 3] : INFINITY, hvf = li >= 0 ? nt.lay_f[kLayF * li + 4] : INFINITY;
+    if (surely_outside(reinterpret_cast<const float*>(rec + 16), xf, xn, Tf, kf, knorm, bendf, huf, hvf)) continue;
+    const double hu = li >= 0 ? nt.lay[8 * li + 6] : 1e300, hv = li >= 0 ? nt.lay[8 * li + 7] : 1e300;
     const double c[3] = {rec[9], rec[10], rec[11]};
     const double d[3] = {c[0] - x[0], c[1] - x[1], c[2] - x[2]};
-    double hu, hv;
-    module_half(a, nt, id, hu, hv);
-    if (surely_outside(reinterpret_cast<const float*>(rec + 16), d, Tf, kf, knorm, bendf, hu, hv)) continue;
     const double u[3] = {rec[0], rec[1], rec[2]}, v[3] = {rec[3], rec[4], rec[5]};
     const double n[3] = {rec[6], rec[7], rec[8]};
     const double dist = dot3(n, d), an = dot3(n, T), bn = dot3(n, k);
     if (an == 0.0) continue;
-    double s = dist / an;
+    // the nearer root of an s + bn s^2 / 2 = dist, else (no real root, or an overflow) the
+    // straight-line path dist / an
+    double s;
+    bool root = false;
     const double disc = an * an + 2.0 * bn * dist;
     if (disc >= 0.0) {
       const double q2 = 2.0 * dist / (an + copysign(sqrt(disc), an));
-      if (isfinite(q2)) s = q2;
+      if (isfinite(q2)) {
+        s = q2;
+        root = true;
+      }
     }
+    if (!root) s = dist / an;
     if (!(s > 1e-3)) continue;
     const double h = 0.5 * s * s;
     const double q[3] = {x[0] + s * T[0] + h * k[0] - c[0], x[1] + s * T[1] + h * k[1] - c[1],
@@ -322,13 +382,15 @@ __device__ int navigate(const CkfArgs& a, int cur, const double x[3], const doub
   uint32_t cand[9];
   int best = -1;
   double best_s = 0.0;
+  const float xf[3] = {d2f(x[0]), d2f(x[1]), d2f(x[2])}, Tf[3] = {d2f(T[0]), d2f(T[1]), d2f(T[2])};
+  const float kf[3] = {d2f(k[0]), d2f(k[1]), d2f(k[2])};
   const int cur_layer = cur >= 0 ? a.layer_of[cur] : -1;
   if (cur_layer >= 0) {
     uint32_t sk[5];
     for (int j = 0; j < nskip; ++j) sk[j] = skip[j];
     sk[nskip] = uint32_t(cur);
     const int nc = layer_candidates(nt, uint32_t(cur_layer), x, cand);
-    best = nearest_crossed(a, nt, cand, nc, x, T, k, bend, sk, nskip + 1, best_s);
+    best = nearest_crossed(a, nt, cand, nc, x, T, k, bend, xf, Tf, kf, sk, nskip + 1, best_s);
   }
   // the head of each order: the next layer ahead (face path > 0, within its extent) and its path
   int pb = 0, pd = 0, lb = -1, ld = -1;
@@ -341,7 +403,7 @@ __device__ int navigate(const CkfArgs& a, int cur, const double x[3], const doub
     while (pb < nt.nbar) {
       const int li = nt.bar[pb++];
       if (li == cur_layer) continue;
-      const double s = layer_path(nt, uint32_t(li), x, T);
+      const double s = layer_path(nt, uint32_t(li), x, T, xf, Tf);
       if (s > 0.0) {
         lb = li;
         sb = s;
@@ -356,7 +418,7 @@ __device__ int navigate(const CkfArgs& a, int cur, const double x[3], const doub
       dpos += dstep;
       ++pd;
       if (li == cur_layer) continue;
-      const double s = layer_path(nt, uint32_t(li), x, T);
+      const double s = layer_path(nt, uint32_t(li), x, T, xf, Tf);
       if (s > 0.0) {
         ld = li;
         sd = s;
@@ -375,7 +437,7 @@ __device__ int navigate(const CkfArgs& a, int cur, const double x[3], const doub
     const double q[3] = {x[0] + sl * T[0] + h * k[0], x[1] + sl * T[1] + h * k[1], x[2] + sl * T[2] + h * k[2]};
     const int nc = layer_candidates(nt, uint32_t(pick), q, cand);
     double sm = 0.0;
-    const int m = nearest_crossed(a, nt, cand, nc, x, T, k, bend, skip, nskip, sm);
+    const int m = nearest_crossed(a, nt, cand, nc, x, T, k, bend, xf, Tf, kf, skip, nskip, sm);
     if (m >= 0 && (best < 0 || sm < best_s)) {
       best = m;
       best_s = sm;

@@ -17,7 +17,8 @@ namespace tkf {
 //   [0..2] u, [3..5] v, [6..8] n, [9..11] c, [12] thickness, [13] x0, [14] t / x0,
 //   [15] sqrt(t / x0) (1 + 0.038 ln(t / x0)) (the Highland factor at normal incidence, beta = 1;
 //   0 without material),
-//   then 16 floats: u, v, n, thickness, t / x0 (FP32 copies for the mixed path), 5 x 0.
+//   then 16 floats: u, v, n, thickness, t / x0 (FP32 copies for the mixed path), c (FP32 copy for
+//   the navigation's screens), 2 x 0.
 constexpr int kSurfStride = 24;
 
 // Material constants folded for the kernels.
