@@ -83,8 +83,9 @@ constexpr int kCkfMaxRings = 256;  // ring rows kept in shared memory (more: rea
 // modules' half extents, the outer face radius (barrels), the radial extent test's bounds (disks);
 // per ring float(n_phi / 2 pi).
 constexpr int kLayF = 8;  // floats a layer: phi bins a radian, pitch, r_inner, half_u, half_v, face_r,
-                          // r_inner - 10, r_inner + n_rings ring_pitch + 10
-struct NavTables {
+                          // then the extent test's bounds: barrels n_rows row_pitch / 2 + 10, 0;
+                          // disks r_inner - 10, r_inner + n_rings ring_pitch + 10
+struct alignas(16) NavTables {
   double lay[kCkfMaxLayers * 8];
   double ring[kCkfMaxRings * 4];
   double face_r[kCkfMaxLayers];
@@ -121,7 +122,7 @@ __device__ void build_nav_tables(const CkfArgs& a, NavTables& nt) {
     lf[3] = d2f(l[6]);
     lf[4] = d2f(l[7]);
     lf[5] = d2f(nt.face_r[li]);
-    lf[6] = l[0] == 0.0 ? 0.0f : d2f(l[5] - 10.0);
+    lf[6] = l[0] == 0.0 ? d2f(0.5 * l[3] * l[4] + 10.0) : d2f(l[5] - 10.0);
     lf[7] = l[0] == 0.0 ? 0.0f : d2f(l[5] + l[2] * l[4] + 10.0);
   }
   if (ring_fit)
@@ -237,11 +238,19 @@ __device__ __noinline__ int layer_candidates(const NavTables& nt, uint32_t li, c
 
 // straight-line path to the outer face of layer li if ahead and within its extent, else -1
 // (face_r: the barrel layers' outer face radii, computed once a block). xf, Tf: FP32 copies of x
-// and T for two screens that return -1 only where the FP64 evaluation surely does: a barrel face
-// the point lies outside (|x_perp|^2 - r_face^2 >= 0), and a disk face reached outside its radial
-// extent. Each FP32 quantity is within a few 2^-24 of its magnitudes of the FP64 one (the copies,
-// one rounding an operation, sqrtf and the division correctly rounded); the bounds below take
-// 1e-6 relative (about 17 units) plus 1e-3 mm for the rounding of the stored bounds.
+// and T for three screens that return -1 only where the FP64 evaluation surely does: a barrel face
+// the point lies outside (|x_perp|^2 - r_face^2 >= 0); a barrel face reached beyond the layer's
+// z extent; a disk face reached outside its radial extent. Each FP32 quantity is within a few
+// 2^-24 of its magnitudes of the FP64 one (the copies, one rounding an operation, sqrtf and the
+// division correctly rounded); the bounds below take 1e-6 relative (about 17 units) plus 1e-3 mm
+// for the rounding of the stored bounds.
+//
+// The z extent: where the line, in its direction of travel, passes z_l = +-(z_max + 1e-3 mm +
+// 1e-6 |z|), it is still surely inside the face radius. The squared distance from the axis is a
+// convex function of the path, so from inside at the start (c < 0; else the FP64 test returns -1
+// anyway) the face is met beyond z_l, past z_max by more than the FP64 rounding of x_z + s T_z.
+// Reached at path (z_l - x_z) / T_z; the error of that path carries the rounding of z_l - x_z
+// divided by |T_z| into the transverse position.
 __device__ double layer_path(const NavTables& nt, uint32_t li, const double x[3], const double T[3],
                              const float xf[3], const float Tf[3]) {
   const double* l = nt.lay + 8 * li;
@@ -250,6 +259,17 @@ __device__ double layer_path(const NavTables& nt, uint32_t li, const double x[3]
   if (l[0] == 0.0) {
     const float p2f = xf[0] * xf[0] + xf[1] * xf[1], f2f = lf[5] * lf[5];
     if (p2f - f2f > 1e-6f * (p2f + f2f)) return -1.0;
+    if (Tf[2] != 0.0f) {
+      const float zl = copysignf(lf[6] + 1e-3f + 1e-6f * fabsf(xf[2]), Tf[2]);
+      const float dzf = zl - xf[2];
+      if (Tf[2] > 0.0f ? dzf <= 0.0f : dzf >= 0.0f) return -1.0;  // beyond z_l already, moving away
+      const float szf = dzf / Tf[2], tp = fabsf(Tf[0]) + fabsf(Tf[1]);
+      const float px = fmaf(szf, Tf[0], xf[0]), py = fmaf(szf, Tf[1], xf[1]);
+      const float rq = sqrtf(px * px + py * py);
+      const float e = 1e-6f * (fabsf(xf[0]) + fabsf(xf[1]) + szf * tp + rq +
+                               (fabsf(zl) + fabsf(xf[2])) * tp / fabsf(Tf[2])) + 1e-3f;
+      if (rq + e < lf[5]) return -1.0;
+    }
     const double aa = T[0] * T[0] + T[1] * T[1], b = x[0] * T[0] + x[1] * T[1];
     const double rf = nt.face_r[li];
     const double c = x[0] * x[0] + x[1] * x[1] - rf * rf;
@@ -687,13 +707,71 @@ __global__ void ckf_meas_f32_kernel(const double* __restrict__ loc0, const doubl
 // are the same.
 
 // One branch's prediction for the current step, and the children it made.
-struct CkfPred {
+struct alignas(16) CkfPred {
   double pp[5], pdir[4], Cp[15], h;
   int32_t target;  // next module; -1: the branch ends (nothing ahead, or the entries are full); -2: no branch
   uint32_t nk;     // children with a measurement
   uint32_t hole;   // 1: a child with a hole
   uint32_t pad;
 };
+
+// The doubles of a prediction (pp, pdir, Cp, h) and of a branch (p, dir, C, h_ctrl, chi2) are
+// contiguous from the start of their 16-byte aligned records: a thread moves them with 16-byte
+// accesses, which a warp of scattered records issues in half the memory transactions.
+static_assert(offsetof(CkfPred, h) == 24 * sizeof(double), "prediction doubles contiguous");
+static_assert(offsetof(CkfBranch, chi2) == 25 * sizeof(double) && sizeof(CkfBranch) % 16 == 0,
+              "branch doubles contiguous, records 16-byte aligned");
+
+__device__ __forceinline__ void load_pred(const CkfPred& pr, double pp[5], double pdir[4], double Cp[15], double& h) {
+  const double2* q = reinterpret_cast<const double2*>(&pr);
+  double v[26];
+#pragma unroll
+  for (int j = 0; j < 12; ++j) {
+    const double2 w = q[j];
+    v[2 * j] = w.x;
+    v[2 * j + 1] = w.y;
+  }
+  v[24] = pr.h;
+#pragma unroll
+  for (int j = 0; j < 5; ++j) pp[j] = v[j];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) pdir[j] = v[5 + j];
+#pragma unroll
+  for (int j = 0; j < 15; ++j) Cp[j] = v[9 + j];
+  h = v[24];
+}
+
+__device__ __forceinline__ void store_pred(CkfPred& pr, const double pp[5], const double pdir[4], const double Cp[15],
+                                           double h) {
+  double v[24];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) v[j] = pp[j];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) v[5 + j] = pdir[j];
+#pragma unroll
+  for (int j = 0; j < 15; ++j) v[9 + j] = Cp[j];
+  double2* q = reinterpret_cast<double2*>(&pr);
+#pragma unroll
+  for (int j = 0; j < 12; ++j) q[j] = make_double2(v[2 * j], v[2 * j + 1]);
+  pr.h = h;
+}
+
+// a child's doubles: parameters, direction, covariance, step control and chi2
+__device__ __forceinline__ void store_child(CkfBranch& ch, const double p[5], const double dir[4], const double C[15],
+                                            double h, double chi2) {
+  double v[26];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) v[j] = p[j];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) v[5 + j] = dir[j];
+#pragma unroll
+  for (int j = 0; j < 15; ++j) v[9 + j] = C[j];
+  v[24] = h;
+  v[25] = chi2;
+  double2* q = reinterpret_cast<double2*>(&ch);
+#pragma unroll
+  for (int j = 0; j < 13; ++j) q[j] = make_double2(v[2 * j], v[2 * j + 1]);
+}
 
 // Per-seed search state.
 struct CkfSeed {
@@ -711,7 +789,9 @@ struct CkfWork {
   CkfSeed* seeds;    // per seed
   uint32_t* list;    // the branch slots (t B + bi) in the beam, for the next step's phases 1 and 2
   uint32_t* count;   // their number
+  uint32_t* next;    // the prediction's next chunk of the list (reset with count)
   CkfNode* nodes;    // per seed: ckf_steps(max_entries) x B history nodes
+  const NavTables* nav;  // the navigation tables, built once a call (pointers fixed up per block)
 };
 
 // Appends each seed's beam slots to the list for the next step: in seed order within a block
@@ -807,14 +887,20 @@ __device__ void init_seed(const CkfArgs& a, const CkfWork& w, uint32_t t, CkfSee
   w.seeds[t] = st;
 }
 
-// Phase 1: the prediction of branch bi of seed slot t (thread t B + bi).
-template <bool kMixed, class F>
-__global__ void __launch_bounds__(kCkfBlock) ckf_predict_kernel(const CkfArgs a, const F fld, CkfWork w) {
+// The navigation tables, built by one block once a call; the prediction's blocks copy them.
+__global__ void __launch_bounds__(kCkfBlock) ckf_nav_kernel(const CkfArgs a, NavTables* __restrict__ out) {
   __shared__ NavTables nt;
   build_nav_tables(a, nt);
+  const uint4* src = reinterpret_cast<const uint4*>(&nt);
+  uint4* dst = reinterpret_cast<uint4*>(out);
+  for (uint32_t j = threadIdx.x; j < sizeof(NavTables) / 16; j += blockDim.x) dst[j] = src[j];
+}
+
+// Phase 1: the prediction of the branch at list entry k (beam slot g = t B + bi).
+template <bool kMixed, class F>
+__device__ __forceinline__ void predict_branch(const CkfArgs& a, const F& fld, const NavTables& nt, const CkfWork& w,
+                                               uint32_t k) {
   const uint32_t B = a.beam;
-  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= *w.count) return;
   const uint32_t g = w.list[k];  // a branch slot in the beam
   const uint32_t t = g / B, bi = g % B;
   const CkfSeed st = w.seeds[t];
@@ -823,25 +909,45 @@ __global__ void __launch_bounds__(kCkfBlock) ckf_predict_kernel(const CkfArgs a,
   int target;
   if (st.first) {
     target = int(a.seed_sid[a.perm[t]]);
-    for (int j = 0; j < 5; ++j) pr.pp[j] = br.p[j];
-    for (int j = 0; j < 4; ++j) pr.pdir[j] = br.dir[j];
-    for (int j = 0; j < 15; ++j) pr.Cp[j] = br.C[j];
-    pr.h = br.h_ctrl;
+    store_pred(pr, br.p, br.dir, br.C, br.h_ctrl);
   } else {
     double pp[5], pdir[4], Cp[15], h = br.h_ctrl;
     target = br.n_entries >= a.max_entries ? -1 : predict<kMixed>(a, fld, nt, br, pp, pdir, Cp, h);
-    if (target >= 0) {
-      for (int j = 0; j < 5; ++j) pr.pp[j] = pp[j];
-      for (int j = 0; j < 4; ++j) pr.pdir[j] = pdir[j];
-      for (int j = 0; j < 15; ++j) pr.Cp[j] = Cp[j];
-      pr.h = h;
-    }
+    if (target >= 0) store_pred(pr, pp, pdir, Cp, h);
   }
   pr.target = target;
 }
 
+// One wave of resident blocks: each copies the navigation tables once, then takes chunks of
+// blockDim.x list entries from a counter until the list is done (branches differ in their work,
+// so the chunks balance the blocks). No block waits on another.
+template <bool kMixed, class F>
+__global__ void __launch_bounds__(kCkfBlock) ckf_predict_kernel(const CkfArgs a, const F fld, CkfWork w) {
+  __shared__ NavTables nt;
+  __shared__ uint32_t chunk;
+  const uint32_t count = *w.count;
+  if (blockIdx.x * blockDim.x >= count) return;  // more blocks than chunks: none for this one
+  const uint4* src = reinterpret_cast<const uint4*>(w.nav);
+  uint4* dst = reinterpret_cast<uint4*>(&nt);
+  for (uint32_t j = threadIdx.x; j < sizeof(NavTables) / 16; j += blockDim.x) dst[j] = src[j];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const bool ring_fit = a.n_rings <= uint32_t(kCkfMaxRings);
+    nt.rings = ring_fit ? nt.ring : a.rings;
+    nt.rings_f = ring_fit ? nt.ring_f : nullptr;
+  }
+  for (;;) {
+    if (threadIdx.x == 0) chunk = atomicAdd(w.next, blockDim.x);
+    __syncthreads();  // (the first one also publishes the ring pointers)
+    const uint32_t b0 = chunk;
+    __syncthreads();
+    if (b0 >= count) break;
+    if (b0 + threadIdx.x < count) predict_branch<kMixed>(a, fld, nt, w, b0 + threadIdx.x);
+  }
+}
+
 // Phase 2: the gate over the predicted module's measurements and the children of branch bi.
-__global__ void __launch_bounds__(kCkfBlock) ckf_gate_kernel(const CkfArgs a, CkfWork w) {
+__global__ void __launch_bounds__(kCkfBlock, 4) ckf_gate_kernel(const CkfArgs a, CkfWork w) {
   const uint32_t B = a.beam;
   const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= *w.count) return;
@@ -865,11 +971,8 @@ __global__ void __launch_bounds__(kCkfBlock) ckf_gate_kernel(const CkfArgs a, Ck
   const double br_chi2 = br.chi2;
   const uint32_t br_meas = br.n_meas, br_holes = br.holes, br_entries = br.n_entries;
   const int32_t br_node = br.node;
-  double pp[5], pdir[4], Cp[15];
-  for (int j = 0; j < 5; ++j) pp[j] = pr.pp[j];
-  for (int j = 0; j < 4; ++j) pdir[j] = pr.pdir[j];
-  for (int j = 0; j < 15; ++j) Cp[j] = pr.Cp[j];
-  const double h = pr.h;
+  double pp[5], pdir[4], Cp[15], h;
+  load_pred(pr, pp, pdir, Cp, h);
   // the (at most 3) compatible measurements with the lowest chi2 (ties: lower index)
   double kc2[kCkfChildren];
   uint32_t km[kCkfChildren];
@@ -931,16 +1034,11 @@ __global__ void __launch_bounds__(kCkfBlock) ckf_gate_kernel(const CkfArgs a, Ck
     small_sincos(p[2], sd, cd);
     small_sincos(p[3], se, ce);
     CkfBranch& ch = kids[q];
-    ch.dir[0] = pdir[0] * cd + pdir[1] * sd;
-    ch.dir[1] = pdir[1] * cd - pdir[0] * sd;
-    ch.dir[2] = pdir[2] * ce + pdir[3] * se;
-    ch.dir[3] = pdir[3] * ce - pdir[2] * se;
+    const double dir[4] = {pdir[0] * cd + pdir[1] * sd, pdir[1] * cd - pdir[0] * sd, pdir[2] * ce + pdir[3] * se,
+                           pdir[3] * ce - pdir[2] * se};
     p[2] = 0.0;
     p[3] = 0.0;
-    for (int j = 0; j < 5; ++j) ch.p[j] = p[j];
-    for (int j = 0; j < 15; ++j) ch.C[j] = C[j];
-    ch.h_ctrl = h;
-    ch.chi2 = br_chi2 + c2;
+    store_child(ch, p, dir, C, h, br_chi2 + c2);
     ch.n_meas = br_meas + 1;
     ch.holes = 0;
     ch.n_entries = br_entries + 1;
@@ -952,11 +1050,7 @@ __global__ void __launch_bounds__(kCkfBlock) ckf_gate_kernel(const CkfArgs a, Ck
   uint32_t hole = 0;
   if (br_holes < a.max_holes) {
     CkfBranch& ch = kids[nk];
-    for (int j = 0; j < 5; ++j) ch.p[j] = pp[j];
-    for (int j = 0; j < 4; ++j) ch.dir[j] = pdir[j];
-    for (int j = 0; j < 15; ++j) ch.C[j] = Cp[j];
-    ch.h_ctrl = h;
-    ch.chi2 = br_chi2;
+    store_child(ch, pp, pdir, Cp, h, br_chi2);
     ch.n_meas = br_meas;
     ch.holes = br_holes + 1;
     ch.n_entries = br_entries + 1;
@@ -1036,9 +1130,10 @@ __device__ uint32_t beam_seed(const CkfArgs& a, const CkfWork& w, uint32_t t, ui
 
 // Workspace layout (byte offsets): branch slots, the seed-order histogram and permutation, FP32
 // copies of the measurements (16-byte aligned), the predictions of every beam slot, the per-seed
-// states, the list of beam slots and its count, the history nodes.
+// states, the list of beam slots, its count and the prediction's chunk counter, the history nodes,
+// the navigation tables (16-byte aligned).
 struct CkfLayout {
-  size_t hist, meas_f, pred, seeds, list, count, nodes, total;
+  size_t hist, meas_f, pred, seeds, list, count, nodes, nav, total;
   CkfLayout(uint32_t n_seeds, uint32_t beam, uint32_t n_meas, uint32_t max_entries) {
     hist = size_t(n_seeds) * slots_per_seed(beam) * sizeof(CkfBranch);
     meas_f = hist + ((sizeof(uint32_t) * (kCkfOrderBins + size_t(n_seeds)) + 15) & ~size_t(15));
@@ -1046,8 +1141,9 @@ struct CkfLayout {
     seeds = pred + sizeof(CkfPred) * size_t(n_seeds) * beam;
     list = (seeds + sizeof(CkfSeed) * size_t(n_seeds) + 7) & ~size_t(7);
     count = list + sizeof(uint32_t) * size_t(n_seeds) * beam;
-    nodes = count + sizeof(uint32_t);
-    total = nodes + sizeof(CkfNode) * size_t(n_seeds) * ckf_steps(max_entries) * beam;
+    nodes = count + 2 * sizeof(uint32_t);
+    nav = (nodes + sizeof(CkfNode) * size_t(n_seeds) * ckf_steps(max_entries) * beam + 15) & ~size_t(15);
+    total = nav + sizeof(NavTables);
   }
 };
 
@@ -1080,20 +1176,33 @@ cudaError_t launch_ckf(const CkfArgs& a_in, const F& fld, cudaStream_t stream) {
   w.seeds = reinterpret_cast<CkfSeed*>(base + L.seeds);
   w.list = reinterpret_cast<uint32_t*>(base + L.list);
   w.count = reinterpret_cast<uint32_t*>(base + L.count);
+  w.next = w.count + 1;
   w.nodes = reinterpret_cast<CkfNode*>(base + L.nodes);
+  NavTables* nav = reinterpret_cast<NavTables*>(base + L.nav);
+  w.nav = nav;
   const unsigned gs = (a.n_seeds + kCkfBlock - 1) / kCkfBlock;
   const unsigned gb = unsigned((size_t(a.n_seeds) * a.beam + kCkfBlock - 1) / kCkfBlock);
-  if ((e = cudaMemsetAsync(w.count, 0, sizeof(uint32_t), stream)) != cudaSuccess) return e;
+  // the prediction: one wave of resident blocks at most
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  e = a.mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ckf_predict_kernel<true, F>, kCkfBlock, 0)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ckf_predict_kernel<false, F>, kCkfBlock, 0);
+  if (e != cudaSuccess) return e;
+  const unsigned wave = unsigned(sms > 0 ? sms : 1) * unsigned(per_sm > 0 ? per_sm : 1);
+  const unsigned gp = gb < wave ? gb : wave;
+  if ((e = cudaMemsetAsync(w.count, 0, 2 * sizeof(uint32_t), stream)) != cudaSuccess) return e;
+  ckf_nav_kernel<<<1, kCkfBlock, 0, stream>>>(a, nav);
   ckf_init_kernel<<<gs, kCkfBlock, 0, stream>>>(a, w);
   // every step adds an entry to each surviving branch: at most max_entries + 2 steps
   const uint32_t n_steps = ckf_steps(a.max_entries);
   for (uint32_t step = 0; step < n_steps; ++step) {
     if (a.mixed)
-      ckf_predict_kernel<true><<<gb, kCkfBlock, 0, stream>>>(a, fld, w);
+      ckf_predict_kernel<true><<<gp, kCkfBlock, 0, stream>>>(a, fld, w);
     else
-      ckf_predict_kernel<false><<<gb, kCkfBlock, 0, stream>>>(a, fld, w);
+      ckf_predict_kernel<false><<<gp, kCkfBlock, 0, stream>>>(a, fld, w);
     ckf_gate_kernel<<<gb, kCkfBlock, 0, stream>>>(a, w);
-    if ((e = cudaMemsetAsync(w.count, 0, sizeof(uint32_t), stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w.count, 0, 2 * sizeof(uint32_t), stream)) != cudaSuccess) return e;
     ckf_beam_kernel<<<gs, kCkfBlock, 0, stream>>>(a, w, step, step + 1 == n_steps ? 1u : 0u);
   }
   return cudaGetLastError();
