@@ -5,11 +5,13 @@
 // The search runs as phases over all seeds (below): the fit's RKN propagation, material and
 // gain-matrix update; FP64 throughout, or (kMixed) with the propagation, material and covariance
 // transport in FP32 around FP64 anchors as in the fit's mixed path (navigation, gate and update
-// stay FP64). A seed's branches live in a workspace of global memory (a branch: state, direction,
+// decide in FP64; FP32 screens with error bounds skip FP64 evaluations whose outcome is already
+// certain). A seed's branches live in a workspace of global memory (a branch: state, direction,
 // covariance and counters, 240 bytes); a branch's entries are not copied with it: each entry is a
 // node of the seed's history tree (surface, measurement, parent node), written once when the
 // beam keeps the branch, and the candidate's entries are read back along the parent links. The
-// geometry, layer tables and measurements are gathered through L1/L2.
+// navigation tables are built once a call and copied into each prediction block's shared memory;
+// the module records and measurements are gathered through L1/L2.
 
 #include "tkf_fit_impl.cuh"
 
