@@ -19,9 +19,12 @@
 // loop; no structure (sparsity, symmetry, packing) is exploited, so that a reader can
 // check each line against the textbook formula.
 //
-// Parity unpinned (conventions fixed by reading, the same on both sides):
-//   * the density-effect term of the Bethe formula (high-energy asymptote);
-//   * the field gradient dB/dr, neglected in the Jacobian (exact in a uniform field).
+// Conventions fixed by reading, the same on both sides, each pinned by an invariant rather
+// than by a printed value:
+//   * the density-effect term of the Bethe formula (high-energy form): above its threshold
+//     the mean excitation energy cancels and the loss takes the plasma-energy plateau form;
+//   * the field gradient dB/dr, neglected in the Jacobian (exact in a uniform field): in a
+//     map the Jacobian differs from finite differences only by a term linear in the gradient.
 
 #include <algorithm>
 #include <cmath>

@@ -303,6 +303,34 @@ def test_bethe_minimum_ionisation_silicon():
     assert abs(dedx[k] / ref["dEdx_min_MeV_cm2_g"] - 1.0) < 0.02
 
 
+def test_bethe_density_effect_replaces_the_excitation_energy_at_high_energy():
+    """Reading: the density correction in its high-energy form, delta/2 = ln(hbar w_p / I) +
+    ln(beta gamma) - 1/2 (PDG), taken wherever it is positive. Then the mean excitation energy I
+    cancels from the Bethe bracket and the ln(beta gamma) rise stops: the loss depends on the
+    plasma energy and the kinematics alone, (K Z/A / beta^2) [ln(sqrt(2 m_e W_max) / hbar w_p) +
+    1/2 - beta^2]. So above the correction's threshold (beta gamma > e^0.5 I / hbar w_p, about 9
+    in silicon) changing I leaves the loss unchanged, while below it a lower I raises the loss.
+    A wrong sign or factor on either log term of the correction breaks the cancellation."""
+    plane = synth.telescope_geometry().table[0]
+    ZA, I, rho, hwp = oracle.SI
+    m, me, K = oracle.MUON_MASS, 0.51099895e-3, 0.307075
+
+    def dedx(p, I_eV):
+        return oracle.material(plane, oracle.Options(material=(ZA, I_eV, rho, hwp)), [0, 0, 0, np.pi / 2, 1.0 / p])[2]
+
+    for p in (5.0, 20.0, 100.0, 1000.0):  # beta gamma 47 .. 9,500
+        vals = [dedx(p, Ix) for Ix in (I, 0.8 * I, 1.3 * I)]
+        assert max(vals) - min(vals) < 1e-12 * vals[0], (p, vals)
+        E = np.hypot(p, m)
+        beta2, gamma, bg = (p / E) ** 2, E / m, p / m
+        wmax = 2.0 * me * bg ** 2 / (1.0 + 2.0 * gamma * me / m + (me / m) ** 2)
+        plateau = K * ZA / beta2 * (np.log(np.sqrt(2.0 * me * wmax) / (hwp * 1e-9)) + 0.5 - beta2)
+        assert abs(vals[0] / plateau - 1.0) < 1e-12, (p, vals[0], plateau)
+    # below the threshold (beta gamma 2.8 .. 4.7) the loss does depend on I
+    for p in (0.3, 0.5):
+        assert dedx(p, 0.8 * I) > dedx(p, I) * 1.01 and dedx(p, 1.3 * I) < dedx(p, I) * 0.99
+
+
 def test_highland_scales_as_inverse_beta_p_and_energy_loss_lowers_momentum():
     plane = synth.telescope_geometry().table[0]
     opts = oracle.Options()
@@ -344,6 +372,45 @@ def test_field_lookup_bilinear_is_exact_for_linear_maps():
     np.testing.assert_allclose(B[inside, 2], (2.0 - 0.0002 * rr + 0.0001 * x[:, 2])[inside], rtol=1e-6)
     assert np.all(oof[~inside] == 1) and np.all(oof[inside] == 0)
     assert np.all(B[~inside] == 0)
+
+
+def test_map_jacobian_neglects_only_the_field_gradient():
+    """Reading: in a field map the transported Jacobian carries no field-gradient term (dB/dx
+    times the position derivatives), exact in a uniform field. In a map with B_z = 2 T +
+    g (z + r / 2), which bilinear interpolation reproduces exactly, against central finite
+    differences of the oracle's own propagator: at g = 0 the Jacobian agrees to the differences'
+    precision (the map's lookup path, not the uniform field's); otherwise the deviation is linear
+    in g (doubling g doubles it) and the position block's stays within kappa |q/p| |grad B| s^2
+    for the path s, the size of the neglected term integrated twice along the path."""
+    g = synth.telescope_geometry()
+    surf = g.table
+    opts = oracle.Options(tol=1e-10)
+    par = np.array([1.3, -2.1, 0.05, np.pi / 2 - 0.03, 1.0 / 1.7])
+    scale = np.array([1.0, 1.0, 1e-3, 1e-3, 1e-2 * abs(par[4])])
+    steps = np.array([1e-3, 1e-3, 1e-6, 1e-6, 1e-6 * abs(par[4])])
+
+    def mapped(grad):
+        nr, nz = 61, 61
+        Rg, Zg = np.meshgrid(np.arange(nr) * 10.0, -300.0 + np.arange(nz) * 10.0)
+        Bz = (2.0 + grad * (Zg + 0.5 * Rg)).astype(np.float32)
+        return oracle.make_field(1, (0, 0, 0), nr, nz, 0.0, 10.0, -300.0, 10.0, np.zeros_like(Bz), Bz)
+
+    for a, b in [(0, 1), (2, 5), (0, 8)]:
+        dev = {}
+        for grad in (0.0, 1e-4, 2e-4):  # T / mm
+            fld = mapped(grad)
+            _, J, st, _ = oracle.transport(surf, a, b, fld, opts, par)
+            assert st == 0
+            dev[grad] = J - _fd_jacobian(surf, a, b, fld, opts, par, steps)
+        Jn = J * scale[None, :] / scale[:, None]
+        d0 = dev[0.0] * scale[None, :] / scale[:, None]
+        assert np.all(np.abs(d0) <= 1e-6 * np.maximum(1.0, np.abs(Jn))), (a, b, np.abs(d0).max())
+        d1, d2 = dev[1e-4], dev[2e-4]
+        big = np.abs(d2) > 1e-3 * np.abs(d2).max()
+        assert np.abs(d2).max() > 1e-5 and np.all(np.abs(d2[big] / d1[big] - 2.0) < 0.05), (a, b)
+        path = 50.0 * (b - a) / (np.cos(par[2]) * np.sin(par[3]))
+        bound = KAPPA * abs(par[4]) * 2e-4 * np.sqrt(1.25) * path ** 2
+        assert np.abs(d2[0:2, 0:2]).max() < bound, (a, b, np.abs(d2[0:2, 0:2]).max(), bound)
 
 
 def test_highland_spot_values_from_the_printed_formula():
