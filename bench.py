@@ -461,6 +461,46 @@ def cpu_baseline(w, max_seconds: float = 20.0):
     return line, idx, res
 
 
+def stage_oracles(w, max_seconds: float = 6.0, track_finding: bool = True):
+    """The CPU oracle beside the seed-estimation and track-finding stages, each as it stands on
+    that stage's own inputs: seed estimation (the oracle runs it on one thread) on the whole
+    batch; track finding (FP64, all cores) on a sample of the
+    first event's seeds over all of that event's measurements, with the stage's options (beam 3,
+    chi2 < 15, 2 holes, 24 entries)."""
+    import oracle
+    t, g = w.tracks, w.geometry
+    cores = os.cpu_count() or 1
+    fo = oracle.field_from(w.field)
+    rng = np.random.default_rng(1)
+    t0 = time.perf_counter()
+    oracle.estimate_seeds(g.table, fo, t.offsets, t.meas, t.sid)
+    dt = time.perf_counter() - t0
+    seeds = {"value": t.n_tracks / dt, "unit": "tracks/s", "cores": 1, "kind": "oracle",
+             "sample": f"the whole batch, {t.n_tracks} tracks, {dt:.2f} s on 1 thread"}
+    if not track_finding:
+        return seeds, None
+    ev = t.subset(np.flatnonzero(t.event == 0))
+    mc = synth.measurement_container(ev, g.n)
+    s_off, s_meas, s_sid = synth.triplet_seed_hits(ev, g)
+    par, cov, _ = oracle.estimate_seeds(g.table, fo, s_off, s_meas, s_sid, first_three=True)
+    seed_sid = ev.sid[ev.offsets[:-1]].astype(np.uint32)
+    opts = oracle.Options(mass=w.mass)
+    k = min(ev.n_tracks, 500)
+    while True:
+        sel = np.sort(rng.choice(ev.n_tracks, size=k, replace=False))
+        t0 = time.perf_counter()
+        oracle.find_tracks(g.table, fo, opts, g.layers, g.rings, mc.offsets, mc.meas, seed_sid[sel], par[sel],
+                           cov[sel], n_threads=cores)
+        dt = time.perf_counter() - t0
+        if dt > 0.25 * max_seconds or k >= ev.n_tracks:
+            break
+        k = int(min(ev.n_tracks, k * max(2.0, 0.3 * max_seconds / max(dt, 1e-3))))
+    ckf = {"value": k / dt, "unit": "seeds/s", "cores": cores, "kind": "oracle", "precision": "fp64",
+           "sample": f"{k} of the first event's {ev.n_tracks} seeds over all its measurements, "
+                     f"{dt:.2f} s on {cores} threads"}
+    return seeds, ckf
+
+
 PARAMS = ("l0", "l1", "phi", "theta", "qop")
 MATCH_TOLS = (1e-4, 1e-3, 1e-2, 5e-2)
 
@@ -1015,6 +1055,10 @@ def main():
         line["e2e"] = e2e
     if not args.no_cpu_baseline:
         line["cpu_baseline"], idx, ores = cpu_baseline(w)
+        if seeds:
+            seeds["cpu_oracle"], ckf_oracle = stage_oracles(w, track_finding=ckf is not None)
+            if ckf is not None:
+                ckf["cpu_oracle"] = ckf_oracle
         # each variant's error against the FP64 oracle on the baseline's sample (the paper's
         # CPU-GPU agreement study, Sec. 3.1, Table 1); the two-filter variants against the
         # oracle's two-filter smoother
