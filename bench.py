@@ -458,6 +458,14 @@ def cpu_baseline(w, max_seconds: float = 20.0):
     dt1 = time.perf_counter() - t0
     line["single_thread"] = {"value": n1 / dt1, "unit": "tracks/s",
                              "sample": f"{n1} tracks of the sample, {dt1:.2f} s on 1 thread"}
+    # the oracle's two-filter smoother (backward filter and weighted mean) beside the GPU's
+    # two-filter variants, on the first quarter of the sample
+    n2 = max(1, len(idx) // 4)
+    t0 = time.perf_counter()
+    oracle.fit_tracks(w, opts=oracle.Options(mass=w.mass, smoother=1), tracks=t.subset(idx[:n2]), n_threads=cores)
+    dt2 = time.perf_counter() - t0
+    line["two_filter"] = {"value": n2 / dt2, "unit": "tracks/s", "cores": cores,
+                          "sample": f"{n2} tracks of the sample, {dt2:.2f} s on {cores} threads"}
     return line, idx, res
 
 
